@@ -1,0 +1,162 @@
+"""Seeded synthetic inputs shaped like the paper's test problems.
+
+This module holds no arithmetic of the solver: it only draws matrices with a
+prescribed singular spectrum, right-hand sides and batches.  The oracle and
+the GPU path both consume exactly the arrays produced here.
+
+Constructions
+-------------
+* Haar-distributed orthogonal factors: QR of a Gaussian matrix with the signs
+  of diag(R) folded into Q (Mezzadri's correction), as the paper draws "the
+  unitary factors from the QR factorization of randomly generated matrices"
+  (Sec. 6.1).
+* ``svd_matrix``: U diag(sigma) V^T with Haar U, V.
+* ``lse_paper`` / ``gls_paper``: [A^T, B^T] = W1 Sigma W2 (resp. [W, V]) with a
+  prescribed kappa_2, logarithmically spaced singular values (the paper uses
+  xLATM1; the spacing mode is not stated, geometric spacing is used here).
+* ``lse_small`` (m=200, n=100, p=20), ``gls_ar1`` (W 4096x1024 with cond 1e3,
+  V the Cholesky factor of an AR(1) covariance, rho=0.9), ``lse_large``
+  (m=16384, n=8192, p=1024), ``lse_batch`` (uneven batch): the workloads the
+  benchmark and the parity tests use.
+
+Every generator takes an integer seed and returns float64 arrays in
+column-major (Fortran) order.
+"""
+import numpy as np
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(int(seed)))
+
+
+def haar(g, rows, cols=None):
+    """rows x cols matrix with orthonormal columns, Haar-distributed."""
+    cols = rows if cols is None else cols
+    X = g.standard_normal((rows, cols))
+    Q, R = np.linalg.qr(X)
+    s = np.sign(np.diag(R))
+    s[s == 0] = 1.0
+    return Q * s
+
+
+def logspace_sigma(k, cond, top=1.0):
+    """k singular values from top down to top/cond, geometrically spaced."""
+    if k <= 1:
+        return np.full(max(k, 0), top)
+    return top * np.logspace(0.0, -np.log10(cond), k)
+
+
+def svd_matrix(g, rows, cols, sigma):
+    """U diag(sigma) V^T, U rows x r, V cols x r, r = len(sigma)."""
+    r = len(sigma)
+    U = haar(g, rows, r)
+    V = haar(g, cols, r)
+    return np.asfortranarray((U * sigma) @ V.T)
+
+
+# ------------------------------------------------------------------ LSE --
+
+def lse_paper(seed, m, n, p, kappa):
+    """[A^T, B^T] = W1 Sigma W2 with kappa_2([A; B]) = kappa (Sec. 6.2)."""
+    g = rng(seed)
+    sigma = logspace_sigma(n, kappa)
+    AB = svd_matrix(g, m + p, n, sigma)
+    A = np.asfortranarray(AB[:m])
+    B = np.asfortranarray(AB[m:])
+    x = g.standard_normal(n)
+    b = A @ x + g.standard_normal(m)
+    d = B @ x
+    return dict(A=A, B=B, b=b, d=d)
+
+
+def lse_svd(seed, m, n, p, cond_a, cond_b, noise=1.0):
+    """A = U diag(logspace) V^T with cond(A) = cond_a, B likewise with
+    cond_b; d = B x_true, b = A x_true + noise * N(0,1)."""
+    g = rng(seed)
+    A = svd_matrix(g, m, n, logspace_sigma(min(m, n), cond_a))
+    B = svd_matrix(g, p, n, logspace_sigma(p, cond_b)) if p > 0 else np.zeros((0, n), order="F")
+    x = g.standard_normal(n)
+    d = B @ x
+    b = A @ x + noise * g.standard_normal(m)
+    return dict(A=A, B=np.asfortranarray(B), b=b, d=d, x_true=x)
+
+
+def lse_small(seed=20241623):
+    """LSE m=200, n=100, p=20: A = U diag(logspace(0,-2,100)) V^T,
+    B = U' diag(logspace(0,-1,20)) V'^T, d = B x_true,
+    b = A x_true + 1e-3 r with x_true, r ~ N(0,1)."""
+    g = rng(seed)
+    m, n, p = 200, 100, 20
+    A = svd_matrix(g, m, n, np.logspace(0, -2, n))
+    B = svd_matrix(g, p, n, np.logspace(0, -1, p))
+    x = g.standard_normal(n)
+    d = B @ x
+    b = A @ x + 1e-3 * g.standard_normal(m)
+    return dict(A=A, B=B, b=b, d=d, x_true=x)
+
+
+def lse_large(seed=20243623, cond_a=1e4, cond_b=1e2, m=16384, n=8192, p=1024):
+    """LSE m=16384, n=8192, p=1024 with cond(A) in {1e1, 1e4, 1e8} and
+    cond(B) = 1e2 (same construction as lse_svd, b = A x + N(0,1))."""
+    return lse_svd(seed, m, n, p, cond_a, cond_b)
+
+
+def lse_batch(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_hi=1e6):
+    """Uneven batch: m ~ U[m_lo, m_hi], n ~ U[16, m/2], p ~ U[1, n/4],
+    cond(A) log-uniform in [cond_lo, cond_hi], cond(B) = 10."""
+    g = rng(seed)
+    out = []
+    for i in range(count):
+        m = int(g.integers(m_lo, m_hi + 1))
+        n = int(g.integers(16, max(16, m // 2) + 1))
+        p = int(g.integers(1, max(1, n // 4) + 1))
+        c = float(np.exp(g.uniform(np.log(cond_lo), np.log(cond_hi))))
+        out.append(lse_svd(int(g.integers(1 << 62)), m, n, p, c, 10.0))
+    return out
+
+
+# ------------------------------------------------------------------ GLS --
+
+def ar1_cholesky(n, rho):
+    """Lower-triangular Cholesky factor L of Sigma_ij = rho^|i-j| in closed
+    form: L[i,0] = rho^i, L[i,j] = rho^(i-j) sqrt(1-rho^2) for 1 <= j <= i."""
+    i = np.arange(n)[:, None]
+    j = np.arange(n)[None, :]
+    L = np.where(i >= j, rho ** np.clip(i - j, 0, None) * np.sqrt(1.0 - rho * rho), 0.0)
+    L[:, 0] = rho ** np.arange(n)
+    return np.asfortranarray(L)
+
+
+def gls_ar1(seed=20242623, n=4096, m=1024, cond_w=1e3, rho=0.9):
+    """GLS in the xGGGLM convention: W n x m with cond(W) = cond_w (SVD
+    construction), V the n x n Cholesky factor of an AR(1) covariance,
+    d = W x_true + V y_true with x_true, y_true ~ N(0,1)."""
+    g = rng(seed)
+    W = svd_matrix(g, n, m, logspace_sigma(m, cond_w))
+    V = ar1_cholesky(n, rho)
+    x = g.standard_normal(m)
+    y = g.standard_normal(n)
+    d = W @ x + V @ y
+    return dict(W=W, V=V, d=d)
+
+
+def gls_paper(seed, n, m, p, kappa):
+    """[W, V] = W1 Sigma W2 with kappa_2([W, V]) = kappa (Sec. 6.3)."""
+    g = rng(seed)
+    sigma = logspace_sigma(n, kappa)
+    WV = svd_matrix(g, n, m + p, sigma)
+    W = np.asfortranarray(WV[:, :m])
+    V = np.asfortranarray(WV[:, m:])
+    d = g.standard_normal(n)
+    return dict(W=W, V=V, d=d)
+
+
+def gls_svd(seed, n, m, p, cond_w, cond_v):
+    """W n x m with cond_w, V n x p with cond_v, d = W x + V y."""
+    g = rng(seed)
+    W = svd_matrix(g, n, m, logspace_sigma(m, cond_w))
+    V = svd_matrix(g, n, p, logspace_sigma(min(n, p), cond_v))
+    x = g.standard_normal(m)
+    y = g.standard_normal(p)
+    d = W @ x + V @ y
+    return dict(W=W, V=V, d=d)
