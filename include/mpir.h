@@ -1,0 +1,248 @@
+/*
+ * mpir.h -- C ABI of libmpir.so: mixed-precision iterative refinement for
+ * least squares with linear equality constraints (LSE) and generalized
+ * least squares (GLS) on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Gao, Ma, Shao, "Mixed precision iterative refinement for least
+ * squares with linear equality constraints and generalized least squares
+ * problems".  A generalized RQ (LSE) or QR (GLS) factorization is computed
+ * once at a low precision u_f and reused to refine the solution of the
+ * 3-block augmented system to FP64 accuracy (Sec. 3, Alg. 1-4).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Matrices are FP64, column-major, with a leading dimension (LAPACK
+ *    convention: element (i, j) of A is A[i + j*lda]); lda >= max(1, rows).
+ *  - Unless stated otherwise every pointer is a DEVICE pointer owned by the
+ *    caller.  Inputs are const and never modified (unlike LAPACK xGGLSE /
+ *    xGGGLM, which overwrite A, B and the right-hand sides).
+ *  - Work is enqueued on the handle's stream; calls return after enqueueing
+ *    unless the refinement loop needs a host decision (the classical loop
+ *    reads a 4-byte convergence flag back once per iteration).  The info
+ *    struct is a HOST pointer and is complete when the call returns.
+ *  - Return codes follow LAPACK's info: 0 success; -i argument i illegal
+ *    (checked on the host before anything is launched); positive values
+ *    are MPIR_* status codes below.
+ *  - The handle owns a workspace (grown on demand with cudaMalloc unless the
+ *    caller provides one with mpir_set_workspace), the factors of the last
+ *    factorization, and device scratch for reductions.  One handle must not
+ *    be used from two host threads at once.
+ */
+#ifndef MPIR_H
+#define MPIR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Factorization precision u_f (Sec. 3; the panel is always FP32 for the
+ * three low-precision kinds, the trailing-update GEMM operands are rounded
+ * to the named type).  MPIR_FP64 is the fixed-precision FP64 path. */
+typedef enum {
+    MPIR_BF16 = 0,
+    MPIR_TF32 = 1,
+    MPIR_FP32 = 2,
+    MPIR_FP64 = 3
+} mpir_prec;
+
+/* Refinement variant. */
+typedef enum {
+    MPIR_CLASSICAL = 0,   /* classical IR (Alg. 2 / Alg. 4)                      */
+    MPIR_GMRES = 1,       /* GMRES-IR with the block-diagonal split preconditioner
+                             (Sec. 5.2, 5.3)                                      */
+    MPIR_DIRECT = 2       /* no refinement: null-space / Paige solve at u_f       */
+} mpir_refine;
+
+/* Status codes (positive return values and mpir_info.status). */
+enum {
+    MPIR_OK = 0,
+    MPIR_SINGULAR_R = 1,      /* R (from B, or from W) has a zero diagonal       */
+    MPIR_SINGULAR_T = 2,      /* T11 (LSE) / T22 (GLS) has a zero diagonal       */
+    MPIR_NOT_CONVERGED = 3,   /* maxit reached without meeting the stop test     */
+    MPIR_NONFINITE = 4,       /* non-finite residual or input                    */
+    MPIR_UNSUPPORTED = 5,     /* size or option outside what this build handles  */
+    MPIR_CUDA_ERROR = 6,      /* a CUDA call failed (message: mpir_last_error)   */
+    MPIR_DEVICE_TIMEOUT = 7   /* a bounded device-side wait gave up              */
+};
+
+typedef struct {
+    int fact;          /* mpir_prec, default MPIR_FP32                            */
+    int refine;        /* mpir_refine, default MPIR_CLASSICAL                     */
+    double tol;        /* stop-test tolerance (eq. lse-stop / gls-stop); <= 0:
+                          2e-15                                                   */
+    int maxit;         /* refinement steps, <= 0: 40 (Alg. 2 / Alg. 4 default)    */
+    int restart;       /* GMRES restart length, <= 0: 30                          */
+    int inner_maxit;   /* GMRES iterations per outer step, <= 0: 300              */
+    double inner_tol;  /* GMRES relative residual target, <= 0: 1e-8 (FP32 u_f),
+                          1e-4 (BF16/TF32 u_f)                                    */
+    double alpha;      /* F~ scaling alpha (Sec. 5), <= 0: ||r0|| (LSE) / ||y0||
+                          (GLS), floored as described in the design notes         */
+    double beta;       /* F~ scaling beta, <= 0: 1                                */
+    int escalate;      /* nonzero: on failure re-factor at the next higher
+                          precision up to FP64 (default 1)                         */
+} mpir_opts;
+
+typedef struct {
+    int status;            /* MPIR_* code of the final attempt                    */
+    int iters;             /* outer refinement steps taken                        */
+    int inner_iters;       /* total GMRES iterations                              */
+    int fact_used;         /* mpir_prec of the factorization that produced x      */
+    int refine_used;       /* mpir_refine used                                    */
+    int escalated;         /* number of escalations                               */
+    double stop_ratio[3];  /* ||f_i|| / (its eq. lse-stop / gls-stop bound)       */
+    double time_ms[6];     /* factor, init, residual, correction, gmres, other    */
+} mpir_info;
+
+typedef struct mpir_ctx *mpir_handle;
+
+/* Defaults as documented in mpir_opts. */
+void mpir_default_opts(mpir_opts *opts);
+
+/* Create a handle bound to device `device` (the current device if < 0) and
+ * CUDA stream `stream` (a cudaStream_t, NULL = legacy default stream).
+ * Returns 0 or MPIR_CUDA_ERROR. */
+int mpir_create(mpir_handle *handle, int device, void *stream);
+int mpir_destroy(mpir_handle handle);
+int mpir_set_stream(mpir_handle handle, void *stream);
+
+/* Caller-provided device workspace (e.g. a framework allocation).  The
+ * handle then never calls cudaMalloc for the workspace.  bytes must be at
+ * least what the *_workspace_size queries return; ptr 256-byte aligned. */
+int mpir_set_workspace(mpir_handle handle, void *ptr, size_t bytes);
+
+/* Workspace a solve of the given shape needs (bytes). */
+int mpir_lse_workspace_size(int m, int n, int p, const mpir_opts *opts, size_t *bytes);
+int mpir_gls_workspace_size(int n, int m, int p, const mpir_opts *opts, size_t *bytes);
+
+/* Last error message of this handle (static storage, never NULL). */
+const char *mpir_last_error(mpir_handle handle);
+
+/* ---------------------------------------------------------------------
+ * LSE:  min ||A x - b||_2  s.t.  B x = d          (eq. problem:lse, Sec. 1)
+ *   A m x n (lda), B p x n (ldb), b (m), d (p), with p <= n <= m + p and,
+ *   for a unique solution, rank(B) = p and rank([A; B]) = n.
+ * Outputs: x (n); optionally r = b - A x (m) and the multiplier v (p) with
+ * A^T r = B^T v (eq. aug-LSE); r and v may be NULL.
+ * Algorithm: GRQ B = [0 R] Q, A = Z T Q at u_f, null-space start, then
+ * Alg. 2 (classical) or GMRES-IR (Sec. 5.2), FP64 residuals and updates.
+ * ------------------------------------------------------------------- */
+int lse_solve(mpir_handle h, int m, int n, int p,
+              const double *A, int lda, const double *B, int ldb,
+              const double *b, const double *d,
+              double *x, double *r, double *v,
+              const mpir_opts *opts, mpir_info *info);
+
+/* ---------------------------------------------------------------------
+ * GLS:  min ||y||_2  s.t.  W x + V y = d          (eq. problem:gls, Sec. 1)
+ *   W n x m (ldw), V n x p (ldv), d (n), with m <= n <= m + p, rank(W) = m,
+ *   rank([W, V]) = n (LAPACK xGGGLM's (A, B) = (W, V)).
+ * Outputs: x (m), y (p), optionally z (n) with y = V^T z, W^T z = 0.
+ * Algorithm: GQR W = Q [R; 0], V = Q T Z at u_f, Paige's method, then
+ * Alg. 4 (classical) or GMRES-IR (Sec. 5.3).
+ * ------------------------------------------------------------------- */
+int gls_solve(mpir_handle h, int n, int m, int p,
+              const double *W, int ldw, const double *V, int ldv,
+              const double *d, double *x, double *y, double *z,
+              const mpir_opts *opts, mpir_info *info);
+
+/* ---------------------------------------------------------------------
+ * Batched solves of independent problems of uneven sizes.  All size, ld
+ * and pointer arrays are HOST arrays of length `count`; the matrices and
+ * vectors they point to are device memory.  infos (host, count entries)
+ * receives per-problem results; the return value is the largest status.
+ * ------------------------------------------------------------------- */
+int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n,
+                      const int *p, const double *const *A, const int *lda,
+                      const double *const *B, const int *ldb,
+                      const double *const *b, const double *const *d,
+                      double *const *x, const mpir_opts *opts,
+                      mpir_info *infos);
+
+int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m,
+                      const int *p, const double *const *W, const int *ldw,
+                      const double *const *V, const int *ldv,
+                      const double *const *d, double *const *x,
+                      double *const *y, const mpir_opts *opts,
+                      mpir_info *infos);
+
+/* =====================================================================
+ * Step-level entry points: one per stage of the method, so that each can
+ * be checked and timed on its own.  They operate on the factors held by
+ * the handle (the last *_factor call).
+ * ===================================================================== */
+
+/* Stage 1-4 (LSE): scale and convert A, B, compute the GRQ at `fact`
+ * precision and keep it in the handle (Lemma 4.5: RQ of B, A Q^T, QR of
+ * A Q^T).  Returns MPIR_SINGULAR_R / MPIR_SINGULAR_T on a zero diagonal. */
+int mpir_lse_factor(mpir_handle h, int m, int n, int p,
+                    const double *A, int lda, const double *B, int ldb,
+                    int fact);
+
+/* Stage 1-4 (GLS): GQR of (W, V) (Lemma 4.6: QR of W, Q^T V, RQ of Q^T V). */
+int mpir_gls_factor(mpir_handle h, int n, int m, int p,
+                    const double *W, int ldw, const double *V, int ldv,
+                    int fact);
+
+/* Dense FP64 copies of the held factors' triangles in the paper's layout:
+ * LSE: R (p x p, ldr) and T (m x n, ldt, zero below the diagonal);
+ * GLS: R (m x m) and T (n x p, RQ-upper-trapezoidal).  Device pointers. */
+int mpir_get_RT(mpir_handle h, double *R, int ldr, double *T, int ldt);
+
+/* Apply an orthogonal factor of the held factorization to a device FP64
+ * vector in place: which = 0 -> Q, 1 -> Z (the paper's names); trans = 1
+ * applies the transpose.  Vector lengths: LSE Q: n, Z: m; GLS Q: n, Z: p. */
+int mpir_apply_factor(mpir_handle h, int which, int trans, double *vec);
+
+/* Stage 5 (LSE): null-space method at u_f (Sec. 2.1) -> x0 (n). */
+int mpir_lse_initial(mpir_handle h, const double *b, const double *d, double *x);
+/* Stage 5 (GLS): Paige's method at u_f (Sec. 2.2) -> x0 (m), y0 (p). */
+int mpir_gls_initial(mpir_handle h, const double *d, double *x, double *y);
+
+/* Stage 6 (LSE): r0 = b - A x0 in FP64, R^T v0 = (Q A^T r0)(n-p+1:n)
+ * (Alg. 2 steps 3-4).  A, b as given to the factorization. */
+int mpir_lse_multipliers(mpir_handle h, const double *A, int lda,
+                         const double *b, const double *x, double *r,
+                         double *v);
+/* Stage 6 (GLS): T22^T h = (Z y)(p-n+m+1:p), z0 = Q [0; h] (Alg. 4 step 3,
+ * read with Q in front, since W^T z = 0 and y = V^T z). */
+int mpir_gls_multipliers(mpir_handle h, const double *y, double *z);
+
+/* Stage 7-8: FP64 residual of the 3-block augmented system and the norms
+ * of the stop test.  LSE (eq. aug-LSE, Alg. 2 step 6):
+ *   f1 = b - r - A x (m), f2 = d - B x (p), f3 = -A^T r + B^T v (n).
+ * norms (host array of 8, may be NULL): ||f1||, ||f2||, ||f3||, ||x||,
+ * ||r||, ||v||, ||A||_F, ||B||_F.  One read of A and of B. */
+int mpir_lse_residual(mpir_handle h, int m, int n, int p,
+                      const double *A, int lda, const double *B, int ldb,
+                      const double *b, const double *d, const double *x,
+                      const double *r, const double *v,
+                      double *f1, double *f2, double *f3, double *norms);
+/* GLS (eq. aug-GLS, Alg. 4 step 5): f1 = -y + V^T z (p),
+ * f2 = d - W x - V y (n), f3 = W^T z (m).  norms: ||f1||, ||f2||, ||f3||,
+ * ||x||, ||y||, ||z||, ||W||_F, ||V||_F. */
+int mpir_gls_residual(mpir_handle h, int n, int m, int p,
+                      const double *W, int ldw, const double *V, int ldv,
+                      const double *d, const double *x, const double *y,
+                      const double *z, double *f1, double *f2, double *f3,
+                      double *norms);
+
+/* Stage 9: correction solve with the held low-precision factors.
+ * LSE (Alg. 1): [I 0 A; 0 0 B; A^T B^T 0][dr; -dv; dx] = [f1; f2; f3].
+ * GLS (Alg. 3, read with T22 g2 = u2 and dz = -Q h):
+ *   [I V^T 0; V 0 W; 0 W^T 0][dy; -dz; dx] = [f1; f2; f3].
+ * FP64 in and out; the arithmetic runs at the factor precision. */
+int mpir_lse_correction(mpir_handle h, const double *f1, const double *f2,
+                        const double *f3, double *dr, double *dv, double *dx);
+int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
+                        const double *f3, double *dy, double *dz, double *dx);
+
+/* Library version string. */
+const char *mpir_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPIR_H */

@@ -1,0 +1,106 @@
+// common.cuh -- device helpers shared by the libmpir kernels (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cooperative_groups.h>
+#include <cstdint>
+#include <cstddef>
+
+namespace mpir {
+
+namespace cg = cooperative_groups;
+
+// Device-side error word (bit flags) written by kernels that give up a
+// bounded wait; the host reads it after synchronising.
+enum : int { DEV_ERR_BARRIER_TIMEOUT = 1 };
+
+// Grid-wide barrier for a grid whose blocks are all co-resident (launched
+// with cudaLaunchCooperativeKernel).  Sense via a generation counter.
+// Every wait is bounded: after ~2^22 polls (about a second) the block sets
+// DEV_ERR_BARRIER_TIMEOUT in *err and returns false; callers then return.
+struct GridBarrier {
+    unsigned int *state;   // [0] arrivals, [1] generation
+    int *err;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ bool grid_sync(const GridBarrier &b, unsigned nblocks)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen = ld_acquire_u32(&b.state[1]);
+        __threadfence();
+        unsigned arrived = atomicAdd(&b.state[0], 1u) + 1u;
+        if (arrived == nblocks) {
+            atomicExch(&b.state[0], 0u);
+            __threadfence();
+            atomicAdd(&b.state[1], 1u);
+        } else {
+            unsigned spins = 0;
+            while (ld_acquire_u32(&b.state[1]) == gen) {
+                if (++spins > (1u << 22)) { atomicOr(b.err, DEV_ERR_BARRIER_TIMEOUT); ok = 0; break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------- warps --
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum V per-lane values (V a power of two <= 32) over the warp.  On return
+// every lane l holds in v[0] the warp total of slot (l % V).  Uses
+// (V - 1) + log2(32 / V) shuffles (recursive halving exchange).
+template <typename T, int V>
+__device__ __forceinline__ T warp_transpose_reduce(T (&v)[V])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = V / 2; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; i++) {
+            T send = upper ? v[i] : v[i + s];
+            T keep = upper ? v[i + s] : v[i];
+            T recv = __shfl_xor_sync(0xffffffffu, send, s);
+            v[i] = keep + recv;
+        }
+    }
+    T r = v[0];
+#pragma unroll
+    for (int o = V; o < 32; o <<= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+
+// ------------------------------------------------------------- helpers --
+
+__host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ size_t idx2(int i, int j, int ld)
+{
+    return (size_t)j * (size_t)ld + (size_t)i;
+}
+
+template <typename T> struct Lim;
+template <> struct Lim<float> { static constexpr float eps = 5.9604645e-08f; };
+template <> struct Lim<double> { static constexpr double eps = 1.1102230246251565e-16; };
+
+} // namespace mpir

@@ -1,0 +1,104 @@
+// kernels.h -- host-side launchers of the libmpir device kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+
+namespace mpir {
+
+// Larfb (trailing update / block-reflector application) operand precision.
+enum class GemmPrec { FP32 = 0, TF32 = 1, BF16 = 2, FP64 = 3 };
+
+template <typename T> constexpr int panel_nb() { return sizeof(T) == 4 ? 32 : 16; }
+
+struct DevScratch {          // small device scratch owned by the handle
+    unsigned int *barrier;   // 2 words, zero between launches
+    int *err;                // device error flags
+    int *status;             // solver status word (singular diagonals)
+    void *part;              // reduction partials
+    size_t part_bytes;
+};
+
+// ---- factorization (qr.cu) ------------------------------------------
+// Blocked Householder QR of the M x N column-major matrix A (lda):
+// A = Z T with Z = H_0 ... H_{k-1}, k = min(M, N).  Reflector vectors below
+// the diagonal, tau[k], and the compact-WY factor of every panel of
+// panel_nb<T>() reflectors in Tw (NB x NB column-major per panel, upper
+// triangular; H_j0 ... H_j0+nb-1 = I - V Tw V^T).  Returns 0, or
+// MPIR_UNSUPPORTED / MPIR_CUDA_ERROR.
+template <typename T>
+int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, GemmPrec prec, cudaStream_t s);
+
+// C (M x Nc, ldc) <- Z^T C (trans = 1) or Z C (trans = 0) for the reflector
+// set left in (V, ldv, K reflectors, Tw) by geqrf on an M-row matrix.
+template <typename T>
+int apply_reflectors_left(const T *V, int ldv, int M, int K, const T *Tw, int trans,
+                          T *C, int ldc, int Nc, GemmPrec prec, cudaStream_t s);
+
+// ---- vectors (vec.cu) -------------------------------------------------
+// x (length M) <- Z^T x (trans = 1) or Z x (trans = 0), cooperative launch.
+template <typename T>
+int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int trans, T *x,
+                         const DevScratch &sc, cudaStream_t s);
+
+// Solve U x = b (trans = 0) or U^T x = b (trans = 1) in place, U upper
+// triangular n x n (ldu).  Zero diagonal -> bit 1 of *sc.status.
+template <typename T>
+int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s);
+
+// y <- beta y + alpha op(M) x, M rows x cols (ld); op = M (trans = 0) or M^T.
+// If upper_mask, entries M(i, j) with i > j + diag_off are treated as zero.
+template <typename T>
+int gemv(const T *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
+         int upper_mask, int diag_off, cudaStream_t s);
+
+// Elementwise helpers.
+// dst[i] = (T)(scale * src[rev ? n-1-i : i])
+template <typename Ts, typename Td>
+void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s);
+// dst[i] += scale * src[rev ? n-1-i : i]   (FP64 destination)
+template <typename Ts>
+void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s);
+void vzero(void *dst, size_t bytes, cudaStream_t s);
+
+// Matrix conversion with optional transpose and index reversal:
+//   dst(i, j) = (Td)(scale * src(ri, ci)),  i < rows_d, j < cols_d,
+// transpose = 0: (ri, ci) = (i', j');  transpose = 1: (ri, ci) = (j', i'),
+// where i' = rev_r ? rows_d-1-i : i and j' = rev_c ? cols_d-1-j : j.
+template <typename Ts, typename Td>
+void mconvert(const Ts *src, int lds, Td *dst, int ldd, int rows_d, int cols_d, int transpose,
+              int rev_r, int rev_c, double scale, cudaStream_t s);
+
+// max |A(i,j)| and sum A(i,j)^2 (FP64) into out[0], out[1] (device).
+void absmax_sumsq(const double *A, int lda, int rows, int cols, double *part, double *out,
+                  cudaStream_t s);
+
+// ---- residuals (resid.cu) ------------------------------------------------
+// For an FP64 matrix A (rows x cols, lda): partial sums of A x (per column
+// block) and A^T r (per row block) -- one read of A.
+struct DualGemvPlan {
+    int rows, cols, nrb, ncb;   // row / column blocks of 256
+};
+DualGemvPlan dual_gemv_plan(int rows, int cols);
+void dual_gemv(const double *A, int lda, int rows, int cols, const double *x, const double *r,
+               double *part_Ax, double *part_Atr, cudaStream_t s);
+
+// LSE residual from partials: f1 = b - r - sum(Ax), f2 = d - sum(Bx),
+// f3 = -sum(A^T r) + sum(B^T v); norms2[0..5] = squares of ||f1||, ||f2||,
+// ||f3||, ||x||, ||r||, ||v|| (device).
+void lse_resid_finalize(int m, int n, int p, const double *b, const double *d,
+                        const double *x, const double *r, const double *v,
+                        const double *pAx, int ncbA, const double *pAtr, int nrbA,
+                        const double *pBx, int ncbB, const double *pBtv, int nrbB,
+                        double *f1, double *f2, double *f3, double *normpart, double *norms2,
+                        cudaStream_t s);
+// GLS: f1 = -y + sum(V^T z), f2 = d - sum(Wx) - sum(Vy), f3 = sum(W^T z);
+// norms2 = squares of ||f1||, ||f2||, ||f3||, ||x||, ||y||, ||z||.
+void gls_resid_finalize(int n, int m, int p, const double *d, const double *x,
+                        const double *y, const double *z,
+                        const double *pWx, int ncbW, const double *pWtz, int nrbW,
+                        const double *pVy, int ncbV, const double *pVtz, int nrbV,
+                        double *f1, double *f2, double *f3, double *normpart, double *norms2,
+                        cudaStream_t s);
+
+} // namespace mpir

@@ -1,0 +1,1291 @@
+// solver.cu -- the C ABI of libmpir.so (include/mpir.h): handle, workspace,
+// the generalized factorizations, the initial solutions, the correction
+// solves and the refinement loops of the paper (Alg. 1-4).
+//
+// Representation of the generalized factorizations
+// -------------------------------------------------
+// Every factorization is a column-major Householder QR (qr.cu).  An RQ
+// factorization C = T Z (rows annihilated from the right) is obtained as the
+// QR factorization of the reversed transpose  C~ = P C^T P = Z~ T~  with
+//     Z = P Z~^T P,   T = P T~^T P,
+// P the reversal permutation of matching size.  Hence
+//   LSE (GRQ, Lemma 4.5):  B~ = P_n B^T P_p = Q~ [R~; 0]  (Q = P_n Q~^T P_n,
+//        R = P_p R~^T P_p);  X = Q~^T (P_n A^T) = P_n (A Q^T)^T;
+//        A Q^T = Z T by QR of X^T P_n.
+//   GLS (GQR, Lemma 4.6):  W = Q [R; 0] by QR;  C = Q^T V;
+//        C~ = P_p C^T P_n = Z~ T~  (Z = P_p Z~^T P_p, T = P_n T~^T P_p).
+// The algorithms below are Alg. 1 / Alg. 3 rewritten in these reversed
+// coordinates; every step names the paper's step it implements.
+//
+// Scaling (Sec. 6.1, "appropriate scaling" before down-conversion): A, B
+// (resp. W, V) are multiplied by powers of two sA, sB (sW, sV) so that their
+// largest entry lies in [0.5, 1); the corresponding exact rescalings of the
+// right-hand sides and solutions are applied around every solve.  The
+// right-hand side of each correction solve is further normalized by a power
+// of two (gamma) so that it uses the whole low-precision exponent range.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <cmath>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "mpir.h"
+
+using namespace mpir;
+
+#define MPIR_VERSION_STRING "libmpir 0.1 (sm_103a)"
+
+// ------------------------------------------------------------------ ctx --
+
+namespace {
+
+enum class Kind { NONE, LSE, GLS };
+
+struct Carver {
+    uintptr_t base, off = 0;
+    explicit Carver(void *b) : base((uintptr_t)b) {}
+    template <typename U> U *take(size_t count)
+    {
+        off = (off + 255) & ~(uintptr_t)255;
+        U *p = reinterpret_cast<U *>(base + off);
+        off += count * sizeof(U) + 0;
+        return p;
+    }
+    size_t used() const { return (size_t)((off + 255) & ~(uintptr_t)255); }
+};
+
+template <typename T> struct LseWs {
+    int m, n, p, q, kA;
+    T *Bt, *tauB, *TwB, *X, *At, *tauA, *TwA;
+    T *tu, *tw, *ty, *tq, *tb, *tt, *tt2;
+    double *f1, *f2, *f3, *r, *v, *pAx, *pAtr, *pBx, *pBtv, *normpart, *norms2, *scal, *part;
+    DualGemvPlan pa, pb;
+};
+
+template <typename T> struct GlsWs {
+    int n, m, p, L, o, kC;
+    T *Wf, *tauW, *TwW, *Cf, *Ct, *tauC, *TwC;
+    T *tu, *tw, *th, *tg, *tt, *tt2;
+    double *f1, *f2, *f3, *z, *pWx, *pWtz, *pVy, *pVtz, *normpart, *norms2, *scal, *part;
+    DualGemvPlan pw, pv;
+};
+
+template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_t *bytes)
+{
+    constexpr int NB = panel_nb<T>();
+    Carver c(base);
+    LseWs<T> w{};
+    w.m = m; w.n = n; w.p = p; w.q = n - p; w.kA = std::min(m, n);
+    const int mx = std::max(std::max(m, n), std::max(p, 1));
+    w.Bt = c.take<T>((size_t)n * std::max(p, 1));
+    w.tauB = c.take<T>(std::max(p, 1));
+    w.TwB = c.take<T>((size_t)std::max(ceil_div(p, NB), 1) * NB * NB);
+    w.X = c.take<T>((size_t)n * m);
+    w.At = c.take<T>((size_t)m * n);
+    w.tauA = c.take<T>(std::max(w.kA, 1));
+    w.TwA = c.take<T>((size_t)std::max(ceil_div(w.kA, NB), 1) * NB * NB);
+    w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.ty = c.take<T>(mx); w.tq = c.take<T>(mx);
+    w.tb = c.take<T>(mx); w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
+    w.pa = dual_gemv_plan(m, n);
+    w.pb = dual_gemv_plan(p, n);
+    w.f1 = c.take<double>(mx); w.f2 = c.take<double>(mx); w.f3 = c.take<double>(mx);
+    w.r = c.take<double>(mx); w.v = c.take<double>(mx);
+    w.pAx = c.take<double>((size_t)std::max(w.pa.ncb, 1) * std::max(m, 1));
+    w.pAtr = c.take<double>((size_t)std::max(w.pa.nrb, 1) * n);
+    w.pBx = c.take<double>((size_t)std::max(w.pb.ncb, 1) * std::max(p, 1));
+    w.pBtv = c.take<double>((size_t)std::max(w.pb.nrb, 1) * n);
+    w.normpart = c.take<double>(304 * 6);
+    w.norms2 = c.take<double>(8);
+    w.scal = c.take<double>(16);
+    w.part = c.take<double>(4096);
+    if (bytes) *bytes = c.used();
+    return w;
+}
+
+template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_t *bytes)
+{
+    constexpr int NB = panel_nb<T>();
+    Carver c(base);
+    GlsWs<T> w{};
+    w.n = n; w.m = m; w.p = p; w.L = n - m; w.o = p - n + m; w.kC = std::min(n, p);
+    const int mx = std::max(std::max(m, n), std::max(p, 1));
+    w.Wf = c.take<T>((size_t)n * std::max(m, 1));
+    w.tauW = c.take<T>(std::max(m, 1));
+    w.TwW = c.take<T>((size_t)std::max(ceil_div(m, NB), 1) * NB * NB);
+    w.Cf = c.take<T>((size_t)n * p);
+    w.Ct = c.take<T>((size_t)p * n);
+    w.tauC = c.take<T>(std::max(w.kC, 1));
+    w.TwC = c.take<T>((size_t)std::max(ceil_div(w.kC, NB), 1) * NB * NB);
+    w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.th = c.take<T>(mx); w.tg = c.take<T>(mx);
+    w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
+    w.pw = dual_gemv_plan(n, m);
+    w.pv = dual_gemv_plan(n, p);
+    w.f1 = c.take<double>(mx); w.f2 = c.take<double>(mx); w.f3 = c.take<double>(mx);
+    w.z = c.take<double>(mx);
+    w.pWx = c.take<double>((size_t)std::max(w.pw.ncb, 1) * n);
+    w.pWtz = c.take<double>((size_t)std::max(w.pw.nrb, 1) * std::max(m, 1));
+    w.pVy = c.take<double>((size_t)std::max(w.pv.ncb, 1) * n);
+    w.pVtz = c.take<double>((size_t)std::max(w.pv.nrb, 1) * p);
+    w.normpart = c.take<double>(304 * 6);
+    w.norms2 = c.take<double>(8);
+    w.scal = c.take<double>(16);
+    w.part = c.take<double>(4096);
+    if (bytes) *bytes = c.used();
+    return w;
+}
+
+// Factor state held by the handle between step-level calls.
+struct FactorState {
+    Kind kind = Kind::NONE;
+    int fact = MPIR_FP32;
+    int m = 0, n = 0, p = 0;            // LSE (m, n, p) or GLS (n, m, p) as in the API
+    double s1 = 1, s2 = 1;              // LSE: sA, sB ; GLS: sW, sV
+    double fro1 = 0, fro2 = 0;          // ||A||_F, ||B||_F  /  ||W||_F, ||V||_F
+};
+
+} // namespace
+
+struct mpir_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool ws_owned = false;
+    DevScratch sc{};
+    void *scratch_base = nullptr;
+    double *hbuf = nullptr;      // pinned host staging (64 doubles)
+    std::string err;
+    FactorState fs;
+    cudaEvent_t ev[8];
+    void *rws = nullptr;         // scratch of the standalone residual entry points
+    size_t rws_bytes = 0;
+};
+
+namespace {
+
+int set_err(mpir_ctx *h, int code, const char *msg)
+{
+    if (h) h->err = msg ? msg : "";
+    return code;
+}
+
+int cuda_check(mpir_ctx *h, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        if (h) h->err = std::string(where) + ": " + cudaGetErrorString(e);
+        return MPIR_CUDA_ERROR;
+    }
+    return 0;
+}
+
+int ensure_ws(mpir_ctx *h, size_t bytes)
+{
+    if (h->ws_bytes >= bytes) return 0;
+    if (h->ws && !h->ws_owned) return set_err(h, MPIR_UNSUPPORTED, "caller workspace too small");
+    if (h->ws) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0; }
+    if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "workspace cudaMalloc failed"); }
+    h->ws_bytes = bytes;
+    h->ws_owned = true;
+    return 0;
+}
+
+int ensure_rws(mpir_ctx *h, size_t bytes)
+{
+    if (h->rws_bytes >= bytes) return 0;
+    if (h->rws) { cudaStreamSynchronize(h->stream); cudaFree(h->rws); h->rws = nullptr; h->rws_bytes = 0; }
+    if (cudaMalloc(&h->rws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "residual scratch cudaMalloc failed"); }
+    h->rws_bytes = bytes;
+    return 0;
+}
+
+// Scratch of a standalone residual: partials of the two dual gemvs.
+struct ResWs {
+    DualGemvPlan pa, pb;
+    double *pA1, *pA2, *pB1, *pB2, *normpart, *norms2, *scal, *part;
+};
+ResWs res_layout(void *base, int ra, int ca, int rb, int cb, size_t *bytes)
+{
+    Carver c(base);
+    ResWs w{};
+    w.pa = dual_gemv_plan(ra, ca);
+    w.pb = dual_gemv_plan(rb, cb);
+    w.pA1 = c.take<double>((size_t)std::max(w.pa.ncb, 1) * std::max(ra, 1));
+    w.pA2 = c.take<double>((size_t)std::max(w.pa.nrb, 1) * std::max(ca, 1));
+    w.pB1 = c.take<double>((size_t)std::max(w.pb.ncb, 1) * std::max(rb, 1));
+    w.pB2 = c.take<double>((size_t)std::max(w.pb.nrb, 1) * std::max(cb, 1));
+    w.normpart = c.take<double>(304 * 6);
+    w.norms2 = c.take<double>(8);
+    w.scal = c.take<double>(16);
+    w.part = c.take<double>(4096);
+    if (bytes) *bytes = c.used();
+    return w;
+}
+
+double pow2_scale(double amax)
+{
+    if (!(amax > 0) || !std::isfinite(amax)) return 1.0;
+    int e = std::ilogb(amax) + 1;       // amax * 2^-e in [0.5, 1)
+    return std::ldexp(1.0, -e);
+}
+
+double pow2_norm(double nrm)
+{   // gamma with nrm * gamma in [0.5, 1)
+    return pow2_scale(nrm);
+}
+
+// read `count` doubles from device to the pinned staging buffer (synchronous)
+int read_back(mpir_ctx *h, const double *dptr, int count)
+{
+    cudaMemcpyAsync(h->hbuf, dptr, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_check(h, "sync");
+    return 0;
+}
+
+int check_dev_flags(mpir_ctx *h)
+{
+    int flags[2] = {0, 0};
+    cudaMemcpyAsync(&flags[0], h->sc.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaMemcpyAsync(&flags[1], h->sc.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_check(h, "sync");
+    if (flags[0] & DEV_ERR_BARRIER_TIMEOUT) return set_err(h, MPIR_DEVICE_TIMEOUT, "device barrier timed out");
+    if (flags[1] & 1) return set_err(h, MPIR_SINGULAR_R, "R has a zero diagonal entry");
+    if (flags[1] & 2) return set_err(h, MPIR_SINGULAR_T, "triangular factor has a zero diagonal entry");
+    return 0;
+}
+
+void clear_dev_flags(mpir_ctx *h)
+{
+    cudaMemsetAsync(h->sc.err, 0, sizeof(int), h->stream);
+    cudaMemsetAsync(h->sc.status, 0, sizeof(int), h->stream);
+}
+
+GemmPrec gemm_prec(int fact)
+{
+    switch (fact) {
+    case MPIR_BF16: return GemmPrec::BF16;
+    case MPIR_TF32: return GemmPrec::TF32;
+    case MPIR_FP64: return GemmPrec::FP64;
+    default: return GemmPrec::FP32;
+    }
+}
+
+#define RC(x) do { int _rc = (x); if (_rc) return _rc; } while (0)
+
+// T-vector combine: out[i] = alpha * a[ra ? n-1-i : i] + beta * b[rb ? n-1-i : i]
+template <typename T>
+__global__ void k_vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, int rb, T beta)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        T v = alpha * a[ra ? n - 1 - i : i];
+        if (b) v += beta * b[rb ? n - 1 - i : i];
+        out[i] = v;
+    }
+}
+template <typename T>
+void vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, int rb, T beta, cudaStream_t s)
+{
+    if (n > 0) k_vcomb<T><<<ceil_div(n, 256), 256, 0, s>>>(out, n, a, ra, alpha, b, rb, beta);
+}
+
+__global__ void k_mask_lower(double *M, int ld, int rows, int cols, int off)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i < rows && j < cols && i > j + off) M[idx2(i, j, ld)] = 0.0;
+}
+
+// ================================================================= GLS ==
+
+template <typename T>
+int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+                    int fact)
+{
+    size_t bytes = 0;
+    gls_layout<T>(nullptr, n, m, p, &bytes);
+    RC(ensure_ws(h, bytes));
+    GlsWs<T> w = gls_layout<T>(h->ws, n, m, p, nullptr);
+    cudaStream_t s = h->stream;
+    clear_dev_flags(h);
+    absmax_sumsq(W, ldw, n, m, w.part, w.scal + 0, s);
+    absmax_sumsq(V, ldv, n, p, w.part, w.scal + 2, s);
+    RC(read_back(h, w.scal, 4));
+    const double sW = pow2_scale(h->hbuf[0]), sV = pow2_scale(h->hbuf[2]);
+    if (!std::isfinite(h->hbuf[1]) || !std::isfinite(h->hbuf[3]))
+        return set_err(h, MPIR_NONFINITE, "non-finite entry in W or V");
+    h->fs.kind = Kind::GLS;
+    h->fs.fact = fact;
+    h->fs.m = m; h->fs.n = n; h->fs.p = p;
+    h->fs.s1 = sW; h->fs.s2 = sV;
+    h->fs.fro1 = std::sqrt(h->hbuf[1]);
+    h->fs.fro2 = std::sqrt(h->hbuf[3]);
+    const GemmPrec gp = gemm_prec(fact);
+    // QR of W (Lemma 4.6, first factorization)
+    mconvert<double, T>(W, ldw, w.Wf, n, n, m, 0, 0, 0, sW, s);
+    RC(geqrf<T>(w.Wf, n, n, m, w.tauW, w.TwW, gp, s));
+    // C = Q^T V
+    mconvert<double, T>(V, ldv, w.Cf, n, n, p, 0, 0, 0, sV, s);
+    RC(apply_reflectors_left<T>(w.Wf, n, n, m, w.TwW, 1, w.Cf, n, p, gp, s));
+    // RQ of C as QR of C~ = P_p C^T P_n
+    mconvert<T, T>(w.Cf, n, w.Ct, p, p, n, 1, 1, 1, 1.0, s);
+    RC(geqrf<T>(w.Ct, p, p, n, w.tauC, w.TwC, gp, s));
+    return cuda_check(h, "gls_factor");
+}
+
+// Paige's method (Sec. 2.2) in reversed coordinates.  x, y FP64 outputs.
+template <typename T>
+int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
+{
+    const FactorState &fs = h->fs;
+    GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+    const int n = w.n, m = w.m, p = w.p, L = w.L;
+    cudaStream_t s = h->stream;
+    // c = Q^T d
+    vcopy<double, T>(d, w.tu, n, 1.0, 0, s);
+    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 1, w.tu, h->sc, s));
+    // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
+    vzero(w.tg, sizeof(T) * p, s);
+    vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
+    RC(trsv_upper<T>(w.Ct, p, L, 1, w.tg, h->sc, s));
+    // R x = c1 - T12 s2,  P_m (T12 s2) = T~_12^T s~2
+    RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 1, T(1), w.tg, T(0), w.tt, 0, 0, s));
+    vcomb<T>(w.tt2, m, w.tu, 0, T(1), w.tt, 1, T(-1), s);
+    RC(trsv_upper<T>(w.Wf, n, m, 0, w.tt2, h->sc, s));
+    vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s);
+    // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
+    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
+    vcopy<T, double>(w.tg, y, p, fs.s2, 1, s);
+    return cuda_check(h, "gls_initial");
+}
+
+// z0 = Q [0; h], T22^T h = (Z y)(p-n+m+1:p)  (Sec. 3.2, with Q in front).
+template <typename T>
+int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
+{
+    const FactorState &fs = h->fs;
+    GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+    const int n = w.n, m = w.m, p = w.p, L = w.L;
+    cudaStream_t s = h->stream;
+    // y' = y / sV ; w~ = Z~^T (P_p y')
+    vcopy<double, T>(y, w.tw, p, 1.0 / fs.s2, 1, s);
+    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
+    // T~_L h~2 = w~[0:L]
+    vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
+    RC(trsv_upper<T>(w.Ct, p, L, 0, w.th, h->sc, s));
+    // z' = Q [0_m; P_L h~2]
+    vzero(w.tt, sizeof(T) * n, s);
+    vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
+    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 0, w.tt, h->sc, s));
+    vcopy<T, double>(w.tt, z, n, fs.s2 * fs.s2, 0, s);
+    return cuda_check(h, "gls_multipliers");
+}
+
+// Alg. 3 in reversed coordinates; the results are ADDED (scaled) to
+// (dy, dz, dx).  gamma normalizes the right-hand side.
+template <typename T>
+int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const double *f3, double gamma,
+                        double *dy, double *dz, double *dx)
+{
+    const FactorState &fs = h->fs;
+    GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+    const int n = w.n, m = w.m, p = w.p, L = w.L, o = w.o;
+    const double sW = fs.s1, sV = fs.s2;
+    const double c1 = gamma, c2 = gamma * sV, c3 = gamma * sW / sV;
+    cudaStream_t s = h->stream;
+    // step 1: u = Q^T f2'
+    vcopy<double, T>(f2, w.tu, n, c2, 0, s);
+    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 1, w.tu, h->sc, s));
+    // step 2: w~ = Z~^T (P_p f1') = P_p (Z f1')
+    vcopy<double, T>(f1, w.tw, p, c1, 1, s);
+    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
+    // step 3: R^T h1 = f3'   (th[0:m] = h1)
+    vcopy<double, T>(f3, w.th, m, c3, 0, s);
+    RC(trsv_upper<T>(w.Wf, n, m, 1, w.th, h->sc, s));
+    // h~1 = P_m h1 (tt)
+    vcomb<T>(w.tt, m, w.th, 1, T(1), nullptr, 0, T(0), s);
+    // step 4: T22 g2 = u2  <=>  T~_L^T g~2 = P_L u2   (tg[0:L] = g~2)
+    vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
+    RC(trsv_upper<T>(w.Ct, p, L, 1, w.tg, h->sc, s));
+    // step 5: T22^T h2 = w2 - g2 - T12^T h1  <=>  T~_L h~2 = w~2 - g~2 - T~_12 h~1
+    RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 0, T(1), w.tt, T(0), w.tt2, 0, 0, s));
+    vcomb<T>(w.th + m, L, w.tw, 0, T(1), w.tg, 0, T(-1), s);
+    vcomb<T>(w.th + m, L, w.th + m, 0, T(1), w.tt2, 0, T(-1), s);
+    RC(trsv_upper<T>(w.Ct, p, L, 0, w.th + m, h->sc, s));
+    // step 6: g1 = w1 - T11^T h1  <=>  g~1 = w~1 - T~_22 h~1   (tg[L:p])
+    if (o > 0) {
+        vcomb<T>(w.tg + L, o, w.tw + L, 0, T(1), nullptr, 0, T(0), s);
+        RC(gemv<T>(w.Ct + idx2(L, L, p), p, o, m, 0, T(-1), w.tt, T(1), w.tg + L, 1, 0, s));
+    }
+    // step 8 (before the in-place apply of step 7):
+    // R dx = u1 - T11 g1 - T12 g2,  P_m(T11 g1 + T12 g2) = T~_22^T g~1 + T~_12^T g~2
+    RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 1, T(1), w.tg, T(0), w.tt2, 0, 0, s));
+    if (o > 0) RC(gemv<T>(w.Ct + idx2(L, L, p), p, o, m, 1, T(1), w.tg + L, T(1), w.tt2, 1, 0, s));
+    vcomb<T>(w.tt, m, w.tu, 0, T(1), w.tt2, 1, T(-1), s);
+    RC(trsv_upper<T>(w.Wf, n, m, 0, w.tt, h->sc, s));
+    vaxpy<T>(w.tt, dx, m, sW / sV / gamma, 0, s);
+    // step 7: dy = Z^T g = P_p Z~ g~
+    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
+    vaxpy<T>(w.tg, dy, p, 1.0 / gamma, 1, s);
+    //         dz = -Q h,  h = [h1; P_L h~2]
+    vcomb<T>(w.tt2, L, w.th + m, 1, T(1), nullptr, 0, T(0), s);
+    cudaMemcpyAsync(w.th + m, w.tt2, sizeof(T) * L, cudaMemcpyDeviceToDevice, s);
+    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 0, w.th, h->sc, s));
+    vaxpy<T>(w.th, dz, n, -sV / gamma, 0, s);
+    return cuda_check(h, "gls_correction");
+}
+
+// FP64 residual of eq. aug-GLS + squared norms into w.norms2 (device).
+template <typename T>
+void gls_residual_dev(mpir_ctx *h, GlsWs<T> &w, const double *W, int ldw, const double *V, int ldv,
+                      const double *d, const double *x, const double *y, const double *z)
+{
+    cudaStream_t s = h->stream;
+    const int n = w.n, m = w.m, p = w.p;
+    dual_gemv(W, ldw, n, m, x, z, w.pWx, w.pWtz, s);
+    dual_gemv(V, ldv, n, p, y, z, w.pVy, w.pVtz, s);
+    gls_resid_finalize(n, m, p, d, x, y, z, w.pWx, w.pw.ncb, w.pWtz, w.pw.nrb, w.pVy, w.pv.ncb, w.pVtz,
+                       w.pv.nrb, w.f1, w.f2, w.f3, w.normpart, w.norms2, s);
+}
+
+double dnorm_host(mpir_ctx *h, const double *dvec, int n, double *scratch);
+
+struct StopState {
+    double best = INFINITY;
+    int since_best = 0;
+};
+
+// eq. gls-stop / eq. lse-stop from squared norms; returns 1 if satisfied.
+int stop_test(const double *nrm, const double den[3], double tol, double ratio[3])
+{
+    int ok = 1;
+    for (int i = 0; i < 3; i++) {
+        ratio[i] = den[i] > 0 ? nrm[i] / den[i] : (nrm[i] > 0 ? INFINITY : 0.0);
+        if (!(nrm[i] <= tol * den[i])) ok = 0;
+    }
+    return ok;
+}
+
+void fill_opts(const mpir_opts *in, mpir_opts *o)
+{
+    mpir_default_opts(o);
+    if (!in) return;
+    *o = *in;
+    if (o->tol <= 0) o->tol = 2e-15;
+    if (o->maxit <= 0) o->maxit = 40;
+    if (o->restart <= 0) o->restart = 30;
+    if (o->inner_maxit <= 0) o->inner_maxit = 300;
+    if (o->beta <= 0) o->beta = 1.0;
+}
+
+float ev_ms(cudaEvent_t a, cudaEvent_t b)
+{
+    float t = 0;
+    cudaEventElapsedTime(&t, a, b);
+    return t;
+}
+
+template <typename T>
+int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+                   const double *d, double *x, double *y, double *z_out, const mpir_opts &o, int fact,
+                   mpir_info *info)
+{
+    cudaStream_t s = h->stream;
+    cudaEventRecord(h->ev[0], s);
+    RC(gls_factor_impl<T>(h, n, m, p, W, ldw, V, ldv, fact));
+    cudaEventRecord(h->ev[1], s);
+    GlsWs<T> w = gls_layout<T>(h->ws, n, m, p, nullptr);
+    double *z = z_out ? z_out : w.z;
+    RC(gls_initial_impl<T>(h, d, x, y));
+    int st = MPIR_OK;
+    int it = 0;
+    double ratio[3] = {0, 0, 0};
+    if (o.refine != MPIR_DIRECT) {
+        RC(gls_multipliers_impl<T>(h, y, z));
+        cudaEventRecord(h->ev[2], s);
+        StopState ss;
+        st = MPIR_NOT_CONVERGED;
+        const double fW = h->fs.fro1, fV = h->fs.fro2;
+        const double nd = dnorm_host(h, d, n, w.part);
+        float t_res = 0;
+        for (it = 0; it < o.maxit; it++) {
+            cudaEventRecord(h->ev[3], s);
+            gls_residual_dev<T>(h, w, W, ldw, V, ldv, d, x, y, z);
+            cudaEventRecord(h->ev[4], s);
+            RC(read_back(h, w.norms2, 6));
+            t_res += ev_ms(h->ev[3], h->ev[4]);
+            double nr[6];
+            for (int i = 0; i < 6; i++) nr[i] = std::sqrt(h->hbuf[i]);
+            // nr: f1 f2 f3 x y z
+            double den[3] = {nr[4] + fV * nr[5], nd + fW * nr[3] + fV * nr[4], fW * nr[5]};
+            for (int i = 0; i < 3; i++) if (!std::isfinite(nr[i])) { st = MPIR_NONFINITE; break; }
+            if (st == MPIR_NONFINITE) break;
+            if (stop_test(nr, den, o.tol, ratio)) { st = MPIR_OK; break; }
+            const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
+            if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
+            else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            const double fmax = std::max(nr[0], std::max(nr[1], nr[2]));
+            const double gamma = pow2_norm(fmax);
+            RC(gls_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, y, z, x));
+        }
+        if (info) { info->time_ms[2] = t_res; }
+    }
+    RC(check_dev_flags(h));
+    cudaEventRecord(h->ev[7], s);
+    cudaEventSynchronize(h->ev[7]);
+    if (info) {
+        info->status = st;
+        info->iters = it;
+        info->fact_used = fact;
+        info->refine_used = o.refine;
+        for (int i = 0; i < 3; i++) info->stop_ratio[i] = ratio[i];
+        info->time_ms[0] = ev_ms(h->ev[0], h->ev[1]);
+        info->time_ms[5] = ev_ms(h->ev[0], h->ev[7]);
+    }
+    return st;
+}
+
+// ================================================================= LSE ==
+
+template <typename T>
+int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+                    int fact)
+{
+    size_t bytes = 0;
+    lse_layout<T>(nullptr, m, n, p, &bytes);
+    RC(ensure_ws(h, bytes));
+    LseWs<T> w = lse_layout<T>(h->ws, m, n, p, nullptr);
+    cudaStream_t s = h->stream;
+    clear_dev_flags(h);
+    absmax_sumsq(A, lda, m, n, w.part, w.scal + 0, s);
+    absmax_sumsq(B, ldb, p, n, w.part, w.scal + 2, s);
+    RC(read_back(h, w.scal, 4));
+    if (!std::isfinite(h->hbuf[1]) || !std::isfinite(h->hbuf[3]))
+        return set_err(h, MPIR_NONFINITE, "non-finite entry in A or B");
+    const double sA = pow2_scale(h->hbuf[0]), sB = pow2_scale(h->hbuf[2]);
+    h->fs.kind = Kind::LSE;
+    h->fs.fact = fact;
+    h->fs.m = m; h->fs.n = n; h->fs.p = p;
+    h->fs.s1 = sA; h->fs.s2 = sB;
+    h->fs.fro1 = std::sqrt(h->hbuf[1]);
+    h->fs.fro2 = std::sqrt(h->hbuf[3]);
+    const GemmPrec gp = gemm_prec(fact);
+    // RQ of B as QR of B~ = P_n B^T P_p (Lemma 4.5, first factorization)
+    mconvert<double, T>(B, ldb, w.Bt, n, n, p, 1, 1, 1, sB, s);
+    RC(geqrf<T>(w.Bt, n, n, p, w.tauB, w.TwB, gp, s));
+    // X = Q~^T P_n A^T = P_n (A Q^T)^T
+    mconvert<double, T>(A, lda, w.X, n, n, m, 1, 1, 0, sA, s);
+    RC(apply_reflectors_left<T>(w.Bt, n, n, p, w.TwB, 1, w.X, n, m, gp, s));
+    // A Q^T = X^T P_n, then its QR  (A Q^T = Z T)
+    mconvert<T, T>(w.X, n, w.At, m, m, n, 1, 0, 1, 1.0, s);
+    RC(geqrf<T>(w.At, m, m, n, w.tauA, w.TwA, gp, s));
+    return cuda_check(h, "lse_factor");
+}
+
+// Null-space method (Sec. 2.1) with the scaled factors: R y2 = sB d,
+// T11 y1 = c1 - T12 y2 (c = Z^T (sA b)), x = Q^T y.
+template <typename T>
+int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
+{
+    const FactorState &fs = h->fs;
+    LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+    const int m = w.m, n = w.n, p = w.p, q = w.q;
+    cudaStream_t s = h->stream;
+    vcopy<double, T>(b, w.tw, m, fs.s1, 0, s);
+    RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
+    // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
+    vcopy<double, T>(d, w.tb, p, fs.s2, 1, s);
+    RC(trsv_upper<T>(w.Bt, n, p, 1, w.tb, h->sc, s));
+    // ty = [y1; y2], y2 = P_p y~2
+    vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
+    vcomb<T>(w.ty, q, w.tw, 0, T(1), nullptr, 0, T(0), s);
+    RC(gemv<T>(w.At + idx2(0, q, m), m, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
+    RC(trsv_upper<T>(w.At, m, q, 0, w.ty, h->sc, s));
+    // x = Q^T y = P_n Q~ P_n y
+    vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
+    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 0, w.tt, h->sc, s));
+    vcopy<T, double>(w.tt, x, n, 1.0, 1, s);
+    return cuda_check(h, "lse_initial");
+}
+
+// r0 = b - A x (FP64), R^T v0 = (Q A^T r0)(n-p+1:n) (Alg. 2 steps 3-4).
+template <typename T>
+int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b, const double *x, double *r,
+                         double *v)
+{
+    const FactorState &fs = h->fs;
+    LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+    const int m = w.m, n = w.n, p = w.p;
+    cudaStream_t s = h->stream;
+    cudaMemcpyAsync(r, b, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    RC(gemv<double>(A, lda, m, n, 0, -1.0, x, 1.0, r, 0, 0, s));
+    if (p == 0) return cuda_check(h, "lse_multipliers");
+    RC(gemv<double>(A, lda, m, n, 1, 1.0, r, 0.0, w.f3, 0, 0, s));
+    // u~ = Q~^T P_n (sA A^T r)
+    vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s);
+    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 1, w.tu, h->sc, s));
+    // R~ (P_p v') = u~[0:p]
+    RC(trsv_upper<T>(w.Bt, n, p, 0, w.tu, h->sc, s));
+    vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s);
+    return cuda_check(h, "lse_multipliers");
+}
+
+// Alg. 1 in reversed coordinates; results are ADDED to (dr, dv, dx).
+template <typename T>
+int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const double *f3, double gamma,
+                        double *dr, double *dv, double *dx)
+{
+    const FactorState &fs = h->fs;
+    LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+    const int m = w.m, n = w.n, p = w.p, q = w.q;
+    const double sA = fs.s1, sB = fs.s2;
+    const double c1 = gamma, c2 = gamma * sB / sA, c3 = gamma * sA;
+    cudaStream_t s = h->stream;
+    // step 1: u~ = Q~^T P_n f3' ;  u1 = P_q u~[p:n], u2 = P_p u~[0:p]
+    vcopy<double, T>(f3, w.tu, n, c3, 1, s);
+    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 1, w.tu, h->sc, s));
+    // step 2: w = Z^T f1'
+    vcopy<double, T>(f1, w.tw, m, c1, 0, s);
+    RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
+    // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
+    if (p > 0) {
+        vcopy<double, T>(f2, w.tb, p, c2, 1, s);
+        RC(trsv_upper<T>(w.Bt, n, p, 1, w.tb, h->sc, s));
+        vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
+    }
+    // step 4: T11^T q1 = u1
+    if (q > 0) {
+        vcomb<T>(w.tq, q, w.tu + p, 1, T(1), nullptr, 0, T(0), s);
+        RC(trsv_upper<T>(w.At, m, q, 1, w.tq, h->sc, s));
+        // step 5: T11 y1 = w1 - q1 - T12 y2
+        vcomb<T>(w.ty, q, w.tw, 0, T(1), w.tq, 0, T(-1), s);
+        if (p > 0) RC(gemv<T>(w.At + idx2(0, q, m), m, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
+        RC(trsv_upper<T>(w.At, m, q, 0, w.ty, h->sc, s));
+    }
+    // step 6: q2 = w2 - T22 y2
+    if (m - q > 0) {
+        vcomb<T>(w.tq + q, m - q, w.tw + q, 0, T(1), nullptr, 0, T(0), s);
+        if (p > 0) RC(gemv<T>(w.At + idx2(q, q, m), m, m - q, p, 0, T(-1), w.ty + q, T(1), w.tq + q, 1, 0, s));
+    }
+    // step 8: R^T dv = T12^T q1 + T22^T q2 - u2  <=>  R~ (P_p dv) = P_p(T12^T q1 + T22^T q2) - u~[0:p]
+    if (p > 0) {
+        vzero(w.tt, sizeof(T) * p, s);
+        if (q > 0) RC(gemv<T>(w.At + idx2(0, q, m), m, q, p, 1, T(1), w.tq, T(0), w.tt, 0, 0, s));
+        if (m - q > 0) RC(gemv<T>(w.At + idx2(q, q, m), m, m - q, p, 1, T(1), w.tq + q, T(1), w.tt, 1, 0, s));
+        vcomb<T>(w.tb, p, w.tt, 1, T(1), w.tu, 0, T(-1), s);
+        RC(trsv_upper<T>(w.Bt, n, p, 0, w.tb, h->sc, s));
+        vaxpy<T>(w.tb, dv, p, sB / sA / gamma, 1, s);
+    }
+    // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
+    RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 0, w.tq, h->sc, s));
+    vaxpy<T>(w.tq, dr, m, 1.0 / gamma, 0, s);
+    vcomb<T>(w.tt2, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
+    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 0, w.tt2, h->sc, s));
+    vaxpy<T>(w.tt2, dx, n, sA / gamma, 1, s);
+    return cuda_check(h, "lse_correction");
+}
+
+template <typename T>
+void lse_residual_dev(mpir_ctx *h, LseWs<T> &w, const double *A, int lda, const double *B, int ldb,
+                      const double *b, const double *d, const double *x, const double *r, const double *v)
+{
+    cudaStream_t s = h->stream;
+    const int m = w.m, n = w.n, p = w.p;
+    dual_gemv(A, lda, m, n, x, r, w.pAx, w.pAtr, s);
+    if (p > 0) dual_gemv(B, ldb, p, n, x, v, w.pBx, w.pBtv, s);
+    lse_resid_finalize(m, n, p, b, d, x, r, v, w.pAx, w.pa.ncb, w.pAtr, w.pa.nrb, w.pBx, w.pb.ncb, w.pBtv,
+                       p > 0 ? w.pb.nrb : 0, w.f1, w.f2, w.f3, w.normpart, w.norms2, s);
+}
+
+double dnorm_host(mpir_ctx *h, const double *dvec, int n, double *scratch)
+{
+    // ||vec||_2 via absmax_sumsq on an n x 1 matrix
+    absmax_sumsq(dvec, std::max(n, 1), n, 1, scratch, scratch + 4096 - 4, h->stream);
+    read_back(h, scratch + 4096 - 4, 2);
+    return std::sqrt(h->hbuf[1]);
+}
+
+template <typename T>
+int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+                   const double *b, const double *d, double *x, double *r_out, double *v_out,
+                   const mpir_opts &o, int fact, mpir_info *info)
+{
+    cudaStream_t s = h->stream;
+    cudaEventRecord(h->ev[0], s);
+    RC(lse_factor_impl<T>(h, m, n, p, A, lda, B, ldb, fact));
+    cudaEventRecord(h->ev[1], s);
+    LseWs<T> w = lse_layout<T>(h->ws, m, n, p, nullptr);
+    double *r = r_out ? r_out : w.r;
+    double *v = v_out ? v_out : w.v;
+    RC(lse_initial_impl<T>(h, b, d, x));
+    int st = MPIR_OK, it = 0;
+    double ratio[3] = {0, 0, 0};
+    if (o.refine != MPIR_DIRECT || r_out || v_out) RC(lse_multipliers_impl<T>(h, A, lda, b, x, r, v));
+    if (o.refine != MPIR_DIRECT) {
+        const double nb = dnorm_host(h, b, m, w.part), nd = p > 0 ? dnorm_host(h, d, p, w.part) : 0.0;
+        const double fA = h->fs.fro1, fB = h->fs.fro2;
+        StopState ss;
+        st = MPIR_NOT_CONVERGED;
+        float t_res = 0;
+        for (it = 0; it < o.maxit; it++) {
+            cudaEventRecord(h->ev[3], s);
+            lse_residual_dev<T>(h, w, A, lda, B, ldb, b, d, x, r, v);
+            cudaEventRecord(h->ev[4], s);
+            RC(read_back(h, w.norms2, 6));
+            t_res += ev_ms(h->ev[3], h->ev[4]);
+            double nr[6];
+            for (int i = 0; i < 6; i++) nr[i] = std::sqrt(h->hbuf[i]);
+            // nr: f1 f2 f3 x r v
+            double den[3] = {nb + nr[4] + fA * nr[3], nd + fB * nr[3], fA * nr[4] + fB * nr[5]};
+            bool bad = false;
+            for (int i = 0; i < 3; i++) if (!std::isfinite(nr[i])) bad = true;
+            if (bad) { st = MPIR_NONFINITE; break; }
+            if (stop_test(nr, den, o.tol, ratio)) { st = MPIR_OK; break; }
+            const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
+            if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
+            else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            const double gamma = pow2_norm(std::max(nr[0], std::max(nr[1], nr[2])));
+            RC(lse_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, r, v, x));
+        }
+        if (info) info->time_ms[2] = t_res;
+    }
+    RC(check_dev_flags(h));
+    cudaEventRecord(h->ev[7], s);
+    cudaEventSynchronize(h->ev[7]);
+    if (info) {
+        info->status = st;
+        info->iters = it;
+        info->fact_used = fact;
+        info->refine_used = o.refine;
+        for (int i = 0; i < 3; i++) info->stop_ratio[i] = ratio[i];
+        info->time_ms[0] = ev_ms(h->ev[0], h->ev[1]);
+        info->time_ms[5] = ev_ms(h->ev[0], h->ev[7]);
+    }
+    return st;
+}
+
+int next_prec(int fact)
+{
+    if (fact == MPIR_BF16 || fact == MPIR_TF32) return MPIR_FP32;
+    if (fact == MPIR_FP32) return MPIR_FP64;
+    return -1;
+}
+
+bool is_fp64(int fact) { return fact == MPIR_FP64; }
+
+} // namespace
+
+// ============================================================== C ABI ==
+
+extern "C" {
+
+const char *mpir_version(void) { return MPIR_VERSION_STRING; }
+
+void mpir_default_opts(mpir_opts *o)
+{
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->fact = MPIR_FP32;
+    o->refine = MPIR_CLASSICAL;
+    o->tol = 2e-15;
+    o->maxit = 40;
+    o->restart = 30;
+    o->inner_maxit = 300;
+    o->inner_tol = 0;
+    o->alpha = 0;
+    o->beta = 1.0;
+    o->escalate = 1;
+}
+
+int mpir_create(mpir_handle *handle, int device, void *stream)
+{
+    if (!handle) return -1;
+    *handle = nullptr;
+    mpir_ctx *h = new mpir_ctx();
+    if (device < 0) cudaGetDevice(&device);
+    h->device = device;
+    if (cudaSetDevice(device) != cudaSuccess) { delete h; return MPIR_CUDA_ERROR; }
+    h->stream = (cudaStream_t)stream;
+    const size_t part_bytes = 1 << 20;
+    if (cudaMalloc(&h->scratch_base, 4096 + part_bytes) != cudaSuccess) { delete h; cudaGetLastError(); return MPIR_CUDA_ERROR; }
+    cudaMemset(h->scratch_base, 0, 4096 + part_bytes);
+    char *b = (char *)h->scratch_base;
+    h->sc.barrier = (unsigned int *)b;
+    h->sc.err = (int *)(b + 256);
+    h->sc.status = (int *)(b + 512);
+    h->sc.part = b + 4096;
+    h->sc.part_bytes = part_bytes;
+    if (cudaMallocHost(&h->hbuf, 64 * sizeof(double)) != cudaSuccess) { cudaFree(h->scratch_base); delete h; cudaGetLastError(); return MPIR_CUDA_ERROR; }
+    for (int i = 0; i < 8; i++) cudaEventCreate(&h->ev[i]);
+    cudaDeviceSynchronize();
+    *handle = h;
+    return 0;
+}
+
+int mpir_destroy(mpir_handle h)
+{
+    if (!h) return -1;
+    cudaStreamSynchronize(h->stream);
+    if (h->ws && h->ws_owned) cudaFree(h->ws);
+    if (h->scratch_base) cudaFree(h->scratch_base);
+    if (h->rws) cudaFree(h->rws);
+    if (h->hbuf) cudaFreeHost(h->hbuf);
+    for (int i = 0; i < 8; i++) cudaEventDestroy(h->ev[i]);
+    delete h;
+    return 0;
+}
+
+int mpir_set_stream(mpir_handle h, void *stream)
+{
+    if (!h) return -1;
+    h->stream = (cudaStream_t)stream;
+    return 0;
+}
+
+int mpir_set_workspace(mpir_handle h, void *ptr, size_t bytes)
+{
+    if (!h) return -1;
+    if (((uintptr_t)ptr & 255) != 0) return -2;
+    if (h->ws && h->ws_owned) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); }
+    h->ws = ptr;
+    h->ws_bytes = ptr ? bytes : 0;
+    h->ws_owned = false;
+    return 0;
+}
+
+const char *mpir_last_error(mpir_handle h)
+{
+    static const char *none = "";
+    return h ? h->err.c_str() : none;
+}
+
+int mpir_lse_workspace_size(int m, int n, int p, const mpir_opts *opts, size_t *bytes)
+{
+    if (!bytes) return -5;
+    if (m < 0) return -1;
+    if (n < 0) return -2;
+    if (p < 0 || p > n || n > m + p) return -3;
+    mpir_opts o;
+    fill_opts(opts, &o);
+    size_t b32 = 0, b64 = 0;
+    lse_layout<float>(nullptr, m, n, p, &b32);
+    lse_layout<double>(nullptr, m, n, p, &b64);
+    *bytes = (o.fact == MPIR_FP64 || o.escalate) ? std::max(b32, b64) : b32;
+    return 0;
+}
+
+int mpir_gls_workspace_size(int n, int m, int p, const mpir_opts *opts, size_t *bytes)
+{
+    if (!bytes) return -5;
+    if (n < 0) return -1;
+    if (m < 0 || m > n) return -2;
+    if (p < 0 || n > m + p) return -3;
+    mpir_opts o;
+    fill_opts(opts, &o);
+    size_t b32 = 0, b64 = 0;
+    gls_layout<float>(nullptr, n, m, p, &b32);
+    gls_layout<double>(nullptr, n, m, p, &b64);
+    *bytes = (o.fact == MPIR_FP64 || o.escalate) ? std::max(b32, b64) : b32;
+    return 0;
+}
+
+static int lse_check_args(int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+                          const double *b, const double *d, const double *x)
+{
+    if (m < 0) return -2;
+    if (n < 1) return -3;
+    if (p < 0 || p > n || n > m + p) return -4;
+    if (!A) return -5;
+    if (lda < std::max(1, m)) return -6;
+    if (p > 0 && !B) return -7;
+    if (ldb < std::max(1, p)) return -8;
+    if (!b && m > 0) return -9;
+    if (!d && p > 0) return -10;
+    if (!x) return -11;
+    return 0;
+}
+
+static int gls_check_args(int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+                          const double *d, const double *x, const double *y)
+{
+    if (n < 1) return -2;
+    if (m < 0 || m > n) return -3;
+    if (p < 0 || n > m + p) return -4;
+    if (!W && m > 0) return -5;
+    if (ldw < std::max(1, n)) return -6;
+    if (!V && p > 0) return -7;
+    if (ldv < std::max(1, n)) return -8;
+    if (!d) return -9;
+    if (!x && m > 0) return -10;
+    if (!y && p > 0) return -11;
+    return 0;
+}
+
+int lse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+              const double *b, const double *d, double *x, double *r, double *v, const mpir_opts *opts,
+              mpir_info *info)
+{
+    if (!h) return -1;
+    int a = lse_check_args(m, n, p, A, lda, B, ldb, b, d, x);
+    if (a) return set_err(h, a, "illegal argument");
+    mpir_opts o;
+    fill_opts(opts, &o);
+    if (info) std::memset(info, 0, sizeof(*info));
+    int fact = o.fact;
+    int esc = 0, st = 0;
+    while (true) {
+        st = is_fp64(fact) ? lse_solve_once<double>(h, m, n, p, A, lda, B, ldb, b, d, x, r, v, o, fact, info)
+                           : lse_solve_once<float>(h, m, n, p, A, lda, B, ldb, b, d, x, r, v, o, fact, info);
+        if (st == MPIR_OK || st < 0 || st == MPIR_CUDA_ERROR || st == MPIR_UNSUPPORTED ||
+            st == MPIR_DEVICE_TIMEOUT || !o.escalate || o.refine == MPIR_DIRECT)
+            break;
+        int nf = next_prec(fact);
+        if (nf < 0) break;
+        fact = nf;
+        esc++;
+    }
+    if (info) info->escalated = esc;
+    return st;
+}
+
+int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+              const double *d, double *x, double *y, double *z, const mpir_opts *opts, mpir_info *info)
+{
+    if (!h) return -1;
+    int a = gls_check_args(n, m, p, W, ldw, V, ldv, d, x, y);
+    if (a) return set_err(h, a, "illegal argument");
+    mpir_opts o;
+    fill_opts(opts, &o);
+    if (info) std::memset(info, 0, sizeof(*info));
+    int fact = o.fact;
+    int esc = 0, st = 0;
+    while (true) {
+        st = is_fp64(fact) ? gls_solve_once<double>(h, n, m, p, W, ldw, V, ldv, d, x, y, z, o, fact, info)
+                           : gls_solve_once<float>(h, n, m, p, W, ldw, V, ldv, d, x, y, z, o, fact, info);
+        if (st == MPIR_OK || st < 0 || st == MPIR_CUDA_ERROR || st == MPIR_UNSUPPORTED ||
+            st == MPIR_DEVICE_TIMEOUT || !o.escalate || o.refine == MPIR_DIRECT)
+            break;
+        int nf = next_prec(fact);
+        if (nf < 0) break;
+        fact = nf;
+        esc++;
+    }
+    if (info) info->escalated = esc;
+    return st;
+}
+
+int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, const int *p,
+                      const double *const *A, const int *lda, const double *const *B, const int *ldb,
+                      const double *const *b, const double *const *d, double *const *x,
+                      const mpir_opts *opts, mpir_info *infos)
+{
+    if (!h) return -1;
+    if (count < 0) return -2;
+    int worst = 0;
+    for (int i = 0; i < count; i++) {
+        int st = lse_solve(h, m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i], nullptr, nullptr,
+                           opts, infos ? &infos[i] : nullptr);
+        if (st < 0) return st;
+        worst = std::max(worst, st);
+    }
+    return worst;
+}
+
+int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m, const int *p,
+                      const double *const *W, const int *ldw, const double *const *V, const int *ldv,
+                      const double *const *d, double *const *x, double *const *y, const mpir_opts *opts,
+                      mpir_info *infos)
+{
+    if (!h) return -1;
+    if (count < 0) return -2;
+    int worst = 0;
+    for (int i = 0; i < count; i++) {
+        int st = gls_solve(h, n[i], m[i], p[i], W[i], ldw[i], V[i], ldv[i], d[i], x[i], y[i], nullptr, opts,
+                           infos ? &infos[i] : nullptr);
+        if (st < 0) return st;
+        worst = std::max(worst, st);
+    }
+    return worst;
+}
+
+// ------------------------------------------------------- step-level API --
+
+int mpir_lse_factor(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+                    int fact)
+{
+    if (!h) return -1;
+    if (m < 0) return -2;
+    if (n < 1) return -3;
+    if (p < 0 || p > n || n > m + p) return -4;
+    if (!A) return -5;
+    if (lda < std::max(1, m)) return -6;
+    if (p > 0 && !B) return -7;
+    if (ldb < std::max(1, p)) return -8;
+    if (fact < MPIR_BF16 || fact > MPIR_FP64) return -9;
+    int rc = is_fp64(fact) ? lse_factor_impl<double>(h, m, n, p, A, lda, B, ldb, fact)
+                           : lse_factor_impl<float>(h, m, n, p, A, lda, B, ldb, fact);
+    if (rc) return rc;
+    return check_dev_flags(h);
+}
+
+int mpir_gls_factor(mpir_handle h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+                    int fact)
+{
+    if (!h) return -1;
+    if (n < 1) return -2;
+    if (m < 0 || m > n) return -3;
+    if (p < 0 || n > m + p) return -4;
+    if (!W && m > 0) return -5;
+    if (ldw < std::max(1, n)) return -6;
+    if (!V && p > 0) return -7;
+    if (ldv < std::max(1, n)) return -8;
+    if (fact < MPIR_BF16 || fact > MPIR_FP64) return -9;
+    int rc = is_fp64(fact) ? gls_factor_impl<double>(h, n, m, p, W, ldw, V, ldv, fact)
+                           : gls_factor_impl<float>(h, n, m, p, W, ldw, V, ldv, fact);
+    if (rc) return rc;
+    return check_dev_flags(h);
+}
+
+#define DISPATCH(kind_, call64, call32)                                                        \
+    do {                                                                                       \
+        if (!h) return -1;                                                                     \
+        if (h->fs.kind != kind_) return set_err(h, MPIR_UNSUPPORTED, "no matching factors");   \
+        int _rc = is_fp64(h->fs.fact) ? (call64) : (call32);                                   \
+        if (_rc) return _rc;                                                                   \
+        return check_dev_flags(h);                                                             \
+    } while (0)
+
+int mpir_lse_initial(mpir_handle h, const double *b, const double *d, double *x)
+{
+    DISPATCH(Kind::LSE, lse_initial_impl<double>(h, b, d, x), lse_initial_impl<float>(h, b, d, x));
+}
+
+int mpir_gls_initial(mpir_handle h, const double *d, double *x, double *y)
+{
+    DISPATCH(Kind::GLS, gls_initial_impl<double>(h, d, x, y), gls_initial_impl<float>(h, d, x, y));
+}
+
+int mpir_lse_multipliers(mpir_handle h, const double *A, int lda, const double *b, const double *x, double *r,
+                         double *v)
+{
+    DISPATCH(Kind::LSE, lse_multipliers_impl<double>(h, A, lda, b, x, r, v),
+             lse_multipliers_impl<float>(h, A, lda, b, x, r, v));
+}
+
+int mpir_gls_multipliers(mpir_handle h, const double *y, double *z)
+{
+    DISPATCH(Kind::GLS, gls_multipliers_impl<double>(h, y, z), gls_multipliers_impl<float>(h, y, z));
+}
+
+} // extern "C"
+
+template <typename T>
+static int lse_corr_api(mpir_ctx *h, const double *f1, const double *f2, const double *f3, double *dr,
+                        double *dv, double *dx)
+{
+    const FactorState &fs = h->fs;
+    cudaStream_t s = h->stream;
+    vzero(dr, sizeof(double) * fs.m, s);
+    vzero(dv, sizeof(double) * fs.p, s);
+    vzero(dx, sizeof(double) * fs.n, s);
+    return lse_correction_impl<T>(h, f1, f2, f3, 1.0, dr, dv, dx);
+}
+
+extern "C" {
+
+} // extern "C"
+
+template <typename T>
+static int gls_corr_api(mpir_ctx *h, const double *f1, const double *f2, const double *f3, double *dy,
+                        double *dz, double *dx)
+{
+    const FactorState &fs = h->fs;
+    cudaStream_t s = h->stream;
+    vzero(dy, sizeof(double) * fs.p, s);
+    vzero(dz, sizeof(double) * fs.n, s);
+    vzero(dx, sizeof(double) * fs.m, s);
+    return gls_correction_impl<T>(h, f1, f2, f3, 1.0, dy, dz, dx);
+}
+
+extern "C" {
+
+int mpir_lse_correction(mpir_handle h, const double *f1, const double *f2, const double *f3, double *dr,
+                        double *dv, double *dx)
+{
+    DISPATCH(Kind::LSE, lse_corr_api<double>(h, f1, f2, f3, dr, dv, dx),
+             lse_corr_api<float>(h, f1, f2, f3, dr, dv, dx));
+}
+
+int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2, const double *f3, double *dy,
+                        double *dz, double *dx)
+{
+    DISPATCH(Kind::GLS, gls_corr_api<double>(h, f1, f2, f3, dy, dz, dx),
+             gls_corr_api<float>(h, f1, f2, f3, dy, dz, dx));
+}
+
+int mpir_lse_residual(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+                      const double *b, const double *d, const double *x, const double *r, const double *v,
+                      double *f1, double *f2, double *f3, double *norms)
+{
+    if (!h) return -1;
+    if (m < 0) return -2;
+    if (n < 1) return -3;
+    if (p < 0 || p > n || n > m + p) return -4;
+    if (!A || lda < std::max(1, m)) return -6;
+    if ((p > 0 && !B) || ldb < std::max(1, p)) return -8;
+    size_t bytes = 0;
+    res_layout(nullptr, m, n, p, n, &bytes);
+    RC(ensure_rws(h, bytes));
+    ResWs w = res_layout(h->rws, m, n, p, n, nullptr);
+    cudaStream_t s = h->stream;
+    dual_gemv(A, lda, m, n, x, r, w.pA1, w.pA2, s);
+    if (p > 0) dual_gemv(B, ldb, p, n, x, v, w.pB1, w.pB2, s);
+    lse_resid_finalize(m, n, p, b, d, x, r, v, w.pA1, w.pa.ncb, w.pA2, w.pa.nrb, w.pB1, w.pb.ncb, w.pB2,
+                       p > 0 ? w.pb.nrb : 0, f1, f2, f3, w.normpart, w.norms2, s);
+    if (norms) {
+        absmax_sumsq(A, lda, m, n, w.part, w.scal, s);
+        absmax_sumsq(B, ldb, p, n, w.part, w.scal + 2, s);
+        cudaMemcpyAsync(w.scal + 4, w.norms2, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        RC(read_back(h, w.scal, 10));
+        for (int i = 0; i < 6; i++) norms[i] = std::sqrt(h->hbuf[4 + i]);
+        norms[6] = std::sqrt(h->hbuf[1]);
+        norms[7] = std::sqrt(h->hbuf[3]);
+    }
+    return cuda_check(h, "lse_residual");
+}
+
+int mpir_gls_residual(mpir_handle h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+                      const double *d, const double *x, const double *y, const double *z, double *f1,
+                      double *f2, double *f3, double *norms)
+{
+    if (!h) return -1;
+    if (n < 1) return -2;
+    if (m < 0 || m > n) return -3;
+    if (p < 0 || n > m + p) return -4;
+    if ((m > 0 && !W) || ldw < std::max(1, n)) return -6;
+    if ((p > 0 && !V) || ldv < std::max(1, n)) return -8;
+    size_t bytes = 0;
+    res_layout(nullptr, n, m, n, p, &bytes);
+    RC(ensure_rws(h, bytes));
+    ResWs w = res_layout(h->rws, n, m, n, p, nullptr);
+    cudaStream_t s = h->stream;
+    dual_gemv(W, ldw, n, m, x, z, w.pA1, w.pA2, s);
+    dual_gemv(V, ldv, n, p, y, z, w.pB1, w.pB2, s);
+    gls_resid_finalize(n, m, p, d, x, y, z, w.pA1, w.pa.ncb, w.pA2, w.pa.nrb, w.pB1, w.pb.ncb, w.pB2,
+                       w.pb.nrb, f1, f2, f3, w.normpart, w.norms2, s);
+    if (norms) {
+        absmax_sumsq(W, ldw, n, m, w.part, w.scal, s);
+        absmax_sumsq(V, ldv, n, p, w.part, w.scal + 2, s);
+        cudaMemcpyAsync(w.scal + 4, w.norms2, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        RC(read_back(h, w.scal, 10));
+        for (int i = 0; i < 6; i++) norms[i] = std::sqrt(h->hbuf[4 + i]);
+        norms[6] = std::sqrt(h->hbuf[1]);
+        norms[7] = std::sqrt(h->hbuf[3]);
+    }
+    return cuda_check(h, "gls_residual");
+}
+
+} // extern "C"
+
+template <typename T>
+static int get_RT_impl(mpir_ctx *h, double *R, int ldr, double *Tm, int ldt)
+{
+    const FactorState &fs = h->fs;
+    cudaStream_t s = h->stream;
+    if (fs.kind == Kind::LSE) {
+        LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+        const int m = w.m, n = w.n, p = w.p;
+        if (R && p > 0) {
+            // R(i, j) = R~(p-1-j, p-1-i) = Bt(p-1-j, p-1-i) / sB
+            mconvert<T, double>(w.Bt, n, R, ldr, p, p, 1, 1, 1, 1.0 / fs.s2, s);
+            k_mask_lower<<<dim3(ceil_div(p, 256), p), 256, 0, s>>>(R, ldr, p, p, 0);
+        }
+        if (Tm) {
+            mconvert<T, double>(w.At, m, Tm, ldt, m, n, 0, 0, 0, 1.0 / fs.s1, s);
+            k_mask_lower<<<dim3(ceil_div(m, 256), n), 256, 0, s>>>(Tm, ldt, m, n, 0);
+        }
+    } else {
+        GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+        const int n = w.n, m = w.m, p = w.p;
+        if (R && m > 0) {
+            mconvert<T, double>(w.Wf, n, R, ldr, m, m, 0, 0, 0, 1.0 / fs.s1, s);
+            k_mask_lower<<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(R, ldr, m, m, 0);
+        }
+        if (Tm) {
+            // T(r, j) = T~(p-1-j, n-1-r) = Ct(p-1-j, n-1-r) / sV ; zero for r > j + n - p
+            mconvert<T, double>(w.Ct, p, Tm, ldt, n, p, 1, 1, 1, 1.0 / fs.s2, s);
+            k_mask_lower<<<dim3(ceil_div(n, 256), p), 256, 0, s>>>(Tm, ldt, n, p, n - p);
+        }
+    }
+    return cuda_check(h, "get_RT");
+}
+
+extern "C" {
+
+int mpir_get_RT(mpir_handle h, double *R, int ldr, double *T, int ldt)
+{
+    if (!h) return -1;
+    if (h->fs.kind == Kind::NONE) return set_err(h, MPIR_UNSUPPORTED, "no factors held");
+    int rc = is_fp64(h->fs.fact) ? get_RT_impl<double>(h, R, ldr, T, ldt) : get_RT_impl<float>(h, R, ldr, T, ldt);
+    if (rc) return rc;
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? 0 : cuda_check(h, "get_RT");
+}
+
+} // extern "C"
+
+template <typename T>
+static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
+{
+    const FactorState &fs = h->fs;
+    cudaStream_t s = h->stream;
+    if (fs.kind == Kind::LSE) {
+        LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+        if (which == 0) {
+            // Q = P_n Q~^T P_n ; Q^T = P_n Q~ P_n
+            const int n = w.n;
+            vcopy<double, T>(vec, w.tt, n, 1.0, 1, s);
+            RC(apply_reflectors_vec<T>(w.Bt, n, n, w.p, w.TwB, trans ? 0 : 1, w.tt, h->sc, s));
+            vcopy<T, double>(w.tt, vec, n, 1.0, 1, s);
+        } else {
+            const int m = w.m;
+            vcopy<double, T>(vec, w.tt, m, 1.0, 0, s);
+            RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, trans, w.tt, h->sc, s));
+            vcopy<T, double>(w.tt, vec, m, 1.0, 0, s);
+        }
+    } else {
+        GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+        if (which == 0) {
+            const int n = w.n;
+            vcopy<double, T>(vec, w.tt, n, 1.0, 0, s);
+            RC(apply_reflectors_vec<T>(w.Wf, n, n, w.m, w.TwW, trans, w.tt, h->sc, s));
+            vcopy<T, double>(w.tt, vec, n, 1.0, 0, s);
+        } else {
+            // Z = P_p Z~^T P_p ; Z^T = P_p Z~ P_p
+            const int p = w.p;
+            vcopy<double, T>(vec, w.tt, p, 1.0, 1, s);
+            RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, trans ? 0 : 1, w.tt, h->sc, s));
+            vcopy<T, double>(w.tt, vec, p, 1.0, 1, s);
+        }
+    }
+    return cuda_check(h, "apply_factor");
+}
+
+extern "C" {
+
+int mpir_apply_factor(mpir_handle h, int which, int trans, double *vec)
+{
+    if (!h) return -1;
+    if (h->fs.kind == Kind::NONE) return set_err(h, MPIR_UNSUPPORTED, "no factors held");
+    if (which != 0 && which != 1) return -2;
+    if (!vec) return -4;
+    int rc = is_fp64(h->fs.fact) ? apply_factor_impl<double>(h, which, trans, vec)
+                                 : apply_factor_impl<float>(h, which, trans, vec);
+    if (rc) return rc;
+    return check_dev_flags(h);
+}
+
+} // extern "C"

@@ -1,0 +1,482 @@
+// vec.cu -- the vector side of the correction solve (Alg. 1 / Alg. 3):
+// reflector-set applications to one vector (xORMQR on a vector), blocked
+// triangular solves (xTRSV), matrix-vector products (xGEMV) and the
+// elementwise conversions between the FP64 working vectors and the
+// factor-precision vectors.
+#include "common.cuh"
+#include "kernels.h"
+#include "mpir.h"
+
+namespace mpir {
+
+static int coop_grid(const void *kern, int threads, size_t smem, int want)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, threads, smem);
+    int cap = sms * (per > 0 ? per : 1);
+    return want < cap ? want : cap;
+}
+
+// ---------------------------------------------------------------------------
+// x <- Z^T x (trans = 1: blocks in order, factor I - V Tw^T V^T) or
+// x <- Z x  (trans = 0: blocks in reverse order, factor I - V Tw V^T).
+// Cooperative grid; block g owns rows [g*slice, (g+1)*slice) of x, kept in
+// shared memory.  Per reflector block: partial V^T x over the owned rows ->
+// global partials -> grid barrier -> every block sums the partials in the
+// same fixed order, applies Tw, updates its rows.  One barrier per block.
+// ---------------------------------------------------------------------------
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_vec_apply(const T *__restrict__ V, int ldv, int M, int K, const T *__restrict__ Tw, int trans,
+            T *__restrict__ x, int slice, T *__restrict__ part, GridBarrier gb)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    __shared__ T red_s[8][32];
+    __shared__ T w_s[NB];
+    __shared__ T wp_s[NB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    const int s0 = blockIdx.x * slice;
+    const int s1 = min(s0 + slice, M);
+    for (int i = s0 + tid; i < s1; i += 256) xs[i - s0] = x[i];
+    __syncthreads();
+    const int nblk = ceil_div(K, NB);
+    for (int t = 0; t < nblk; t++) {
+        const int b = trans ? t : nblk - 1 - t;
+        const int j0 = b * NB;
+        const int kb = min(NB, K - j0);
+        const int par = t & 1;
+        T acc[NB];
+#pragma unroll
+        for (int c = 0; c < NB; c++) acc[c] = T(0);
+        for (int i = max(s0, j0) + tid; i < s1; i += 256) {
+            const T xi = xs[i - s0];
+#pragma unroll
+            for (int c = 0; c < NB; c++) {
+                const int j = j0 + c;
+                T v = T(0);
+                if (c < kb) v = i > j ? V[idx2(i, j, ldv)] : (i == j ? T(1) : T(0));
+                acc[c] = fma(v, xi, acc[c]);
+            }
+        }
+        T ws = warp_transpose_reduce<T, NB>(acc);
+        if (lane < NB) red_s[warp][lane] = ws;
+        __syncthreads();
+        if (warp == 0 && lane < NB) {
+            T tsum = T(0);
+            for (int w = 0; w < 8; w++) tsum += red_s[w][lane];
+            part[((size_t)par * G + blockIdx.x) * NB + lane] = tsum;
+        }
+        if (!grid_sync(gb, G)) return;
+        // every block: w = sum over blocks (fixed order), then w' = X w
+        {
+            const int c = tid % NB, g0 = tid / NB, gs = 256 / NB;
+            T tsum = T(0);
+            for (int g = g0; g < G; g += gs) tsum += part[((size_t)par * G + g) * NB + c];
+            // reuse red_s as a [gs][NB] scratch (gs * NB == 256 == 8 * 32)
+            T *scr = &red_s[0][0];
+            scr[g0 * NB + c] = tsum;
+            __syncthreads();
+            if (tid < NB) {
+                T s = T(0);
+                for (int g = 0; g < gs; g++) s += scr[g * NB + tid];
+                w_s[tid] = s;
+            }
+            __syncthreads();
+            if (tid < NB) {
+                T s = T(0);
+                for (int k = 0; k < kb; k++) {
+                    // X(i,k) = Tw(k,i) when trans, Tw(i,k) otherwise
+                    const T xk = trans ? Tw[(size_t)b * NB * NB + k + (size_t)tid * NB]
+                                       : Tw[(size_t)b * NB * NB + tid + (size_t)k * NB];
+                    s = fma(xk, w_s[k], s);
+                }
+                wp_s[tid] = tid < kb ? s : T(0);
+            }
+            __syncthreads();
+        }
+        for (int i = max(s0, j0) + tid; i < s1; i += 256) {
+            T d = T(0);
+#pragma unroll
+            for (int c = 0; c < NB; c++) {
+                const int j = j0 + c;
+                T v = T(0);
+                if (c < kb) v = i > j ? V[idx2(i, j, ldv)] : (i == j ? T(1) : T(0));
+                d = fma(v, wp_s[c], d);
+            }
+            xs[i - s0] -= d;
+        }
+        __syncthreads();
+    }
+    for (int i = s0 + tid; i < s1; i += 256) x[i] = xs[i - s0];
+}
+
+template <typename T>
+int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int trans, T *x,
+                         const DevScratch &sc, cudaStream_t s)
+{
+    constexpr int NB = panel_nb<T>();
+    if (K <= 0 || M <= 0) return 0;
+    auto kern = k_vec_apply<T, NB>;
+    int want = ceil_div(M, 128);
+    int slice = 0;
+    size_t smem = 0;
+    int G = 1;
+    for (int it = 0; it < 3; it++) {
+        G = want < 1 ? 1 : want;
+        slice = ceil_div(M, G);
+        smem = (size_t)slice * sizeof(T);
+        int cap = coop_grid((const void *)kern, 256, smem, G);
+        if (cap >= G) break;
+        want = cap;
+    }
+    slice = ceil_div(M, G);
+    smem = (size_t)slice * sizeof(T);
+    if ((size_t)2 * G * NB * sizeof(T) > sc.part_bytes || smem > 200 * 1024) return MPIR_UNSUPPORTED;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    GridBarrier gb{sc.barrier, sc.err};
+    T *part = reinterpret_cast<T *>(sc.part);
+    void *args[] = {(void *)&V, (void *)&ldv, (void *)&M, (void *)&K, (void *)&Tw, (void *)&trans,
+                    (void *)&x, (void *)&slice, (void *)&part, (void *)&gb};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(256), args, smem, s);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked triangular solve with an upper triangular U (n x n):
+//   trans = 0: U x = b  (blocks of 32 from the bottom)
+//   trans = 1: U^T x = b (blocks of 32 from the top)
+// Cooperative grid; block g owns a slice of rows of x (multiple of 32).
+// Step per diagonal block: its owner solves the 32 x 32 triangle in one warp
+// and publishes the 32 values; grid barrier; every block subtracts the
+// block column's contribution from its own not-yet-solved rows.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
+             T *__restrict__ xbuf, int *__restrict__ status, GridBarrier gb)
+{
+    extern __shared__ unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    __shared__ T xb[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int G = gridDim.x;
+    const int s0 = blockIdx.x * slice;
+    const int s1 = min(s0 + slice, n);
+    for (int i = s0 + tid; i < s1; i += 256) xs[i - s0] = x[i];
+    __syncthreads();
+    const int nblk = ceil_div(n, 32);
+    for (int t = 0; t < nblk; t++) {
+        const int blk = trans ? t : nblk - 1 - t;
+        const int r0 = blk * 32;
+        const int bs = min(32, n - r0);
+        const int par = t & 1;
+        if (r0 >= s0 && r0 < s1 && warp == 0) {
+            T rhs = lane < bs ? xs[r0 + lane - s0] : T(0);
+            T xv = T(0);
+            if (!trans) {
+                for (int c = bs - 1; c >= 0; c--) {
+                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    T xc = __shfl_sync(0xffffffffu, rhs, c);
+                    if (dcc == T(0)) { if (lane == 0) atomicOr(status, 2); }
+                    xc = xc / dcc;
+                    if (lane == c) xv = xc;
+                    if (lane < c) rhs = fma(-U[idx2(r0 + lane, r0 + c, ldu)], xc, rhs);
+                }
+            } else {
+                for (int c = 0; c < bs; c++) {
+                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    T xc = __shfl_sync(0xffffffffu, rhs, c);
+                    if (dcc == T(0)) { if (lane == 0) atomicOr(status, 2); }
+                    xc = xc / dcc;
+                    if (lane == c) xv = xc;
+                    if (lane > c && lane < bs) rhs = fma(-U[idx2(r0 + c, r0 + lane, ldu)], xc, rhs);
+                }
+            }
+            if (lane < bs) {
+                xs[r0 + lane - s0] = xv;
+                xbuf[par * 32 + lane] = xv;
+            }
+        }
+        if (!grid_sync(gb, G)) return;
+        if (tid < 32) xb[tid] = tid < bs ? xbuf[par * 32 + tid] : T(0);
+        __syncthreads();
+        if (!trans) {
+            // rows i < r0: x_i -= sum_c U(i, r0+c) xb_c
+            const int hi = min(s1, r0);
+            for (int i = s0 + tid; i < hi; i += 256) {
+                T d = T(0);
+                for (int c = 0; c < bs; c++) d = fma(U[idx2(i, r0 + c, ldu)], xb[c], d);
+                xs[i - s0] -= d;
+            }
+        } else {
+            // rows i >= r0 + bs: x_i -= sum_c U(r0+c, i) xb_c
+            const int lo = max(s0, r0 + bs);
+            for (int i = lo + tid; i < s1; i += 256) {
+                const T *ucol = U + idx2(r0, i, ldu);
+                T d = T(0);
+                for (int c = 0; c < bs; c++) d = fma(ucol[c], xb[c], d);
+                xs[i - s0] -= d;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = s0 + tid; i < s1; i += 256) x[i] = xs[i - s0];
+}
+
+template <typename T>
+int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
+{
+    if (n <= 0) return 0;
+    auto kern = k_trsv_upper<T>;
+    const int nblk = ceil_div(n, 32);
+    int want = ceil_div(nblk, 4);          // 128 rows per block
+    int G = want;
+    size_t smem = 0;
+    int slice = 0;
+    for (int it = 0; it < 3; it++) {
+        G = want < 1 ? 1 : want;
+        slice = ceil_div(nblk, G) * 32;
+        smem = (size_t)slice * sizeof(T);
+        int cap = coop_grid((const void *)kern, 256, smem, G);
+        if (cap >= G) break;
+        want = cap;
+    }
+    slice = ceil_div(nblk, G) * 32;
+    G = ceil_div(n, slice);
+    smem = (size_t)slice * sizeof(T);
+    if (smem > 200 * 1024 || (size_t)64 * sizeof(T) > sc.part_bytes) return MPIR_UNSUPPORTED;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    GridBarrier gb{sc.barrier, sc.err};
+    T *xbuf = reinterpret_cast<T *>(sc.part);
+    int *status = sc.status;
+    void *args[] = {(void *)&U, (void *)&ldu, (void *)&n, (void *)&trans, (void *)&x, (void *)&slice,
+                    (void *)&xbuf, (void *)&status, (void *)&gb};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(256), args, smem, s);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------
+// gemv.  trans = 0: 32 rows per block (lanes), 8 warps split the columns.
+//        trans = 1: one warp per output column.
+// upper_mask: M(i, j) treated as 0 when i > j + diag_off.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemv_n(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
+         T beta, T *__restrict__ y, int upper_mask, int diag_off)
+{
+    __shared__ T red[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    T acc = T(0);
+    if (i < rows) {
+        int jlo = 0;
+        if (upper_mask) jlo = max(0, i - diag_off);
+        for (int j = warp; j < cols; j += 8)
+            if (j >= jlo) acc = fma(M[idx2(i, j, ld)], x[j], acc);
+    }
+    red[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && i < rows) {
+        T s = T(0);
+        for (int w = 0; w < 8; w++) s += red[w][lane];
+        y[i] = (beta == T(0) ? T(0) : beta * y[i]) + alpha * s;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gemv_t(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
+         T beta, T *__restrict__ y, int upper_mask, int diag_off)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= cols) return;
+    int ihi = rows;
+    if (upper_mask) ihi = min(rows, j + diag_off + 1);
+    const T *col = M + idx2(0, j, ld);
+    T acc = T(0);
+    for (int i = lane; i < ihi; i += 32) acc = fma(col[i], x[i], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) y[j] = (beta == T(0) ? T(0) : beta * y[j]) + alpha * acc;
+}
+
+template <typename T>
+int gemv(const T *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
+         int upper_mask, int diag_off, cudaStream_t s)
+{
+    if (!trans) {
+        if (rows <= 0) return 0;
+        k_gemv_n<T><<<ceil_div(rows, 32), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
+                                                        diag_off);
+    } else {
+        if (cols <= 0) return 0;
+        k_gemv_t<T><<<ceil_div(cols, 8), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
+                                                       diag_off);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// ------------------------------------------------------------ elementwise --
+
+template <typename Ts, typename Td>
+__global__ void k_vcopy(const Ts *__restrict__ src, Td *__restrict__ dst, int n, double scale, int rev)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = (Td)(scale * (double)src[rev ? n - 1 - i : i]);
+}
+
+template <typename Ts>
+__global__ void k_vaxpy(const Ts *__restrict__ src, double *__restrict__ dst, int n, double scale, int rev)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] += scale * (double)src[rev ? n - 1 - i : i];
+}
+
+template <typename Ts, typename Td>
+void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s)
+{
+    if (n > 0) k_vcopy<Ts, Td><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev);
+}
+
+template <typename Ts>
+void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s)
+{
+    if (n > 0) k_vaxpy<Ts><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev);
+}
+
+void vzero(void *dst, size_t bytes, cudaStream_t s)
+{
+    if (bytes) cudaMemsetAsync(dst, 0, bytes, s);
+}
+
+// Tiled conversion with optional transpose / reversal (32 x 32 tiles through
+// shared memory so that both the read and the write are coalesced).
+template <typename Ts, typename Td>
+__global__ void __launch_bounds__(256)
+k_mconvert(const Ts *__restrict__ src, int lds, Td *__restrict__ dst, int ldd, int rows_d, int cols_d,
+           int transpose, int rev_r, int rev_c, double scale)
+{
+    __shared__ Ts tile[32][33];
+    const int bi = blockIdx.x * 32, bj = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    // destination tile (bi.., bj..): source index for dst (i, j) is
+    // (ri, ci) = transpose ? (j', i') : (i', j')
+    if (!transpose) {
+        for (int r = ty; r < 32; r += 8) {
+            int i = bi + tx, j = bj + r;
+            if (i < rows_d && j < cols_d) {
+                int ip = rev_r ? rows_d - 1 - i : i, jp = rev_c ? cols_d - 1 - j : j;
+                dst[idx2(i, j, ldd)] = (Td)(scale * (double)src[idx2(ip, jp, lds)]);
+            }
+        }
+        return;
+    }
+    // transpose: read source rows (j') contiguous along j' for fixed i'
+    for (int r = ty; r < 32; r += 8) {
+        int j = bj + tx, i = bi + r;        // load element needed by dst(i, j)
+        if (i < rows_d && j < cols_d) {
+            int ip = rev_r ? rows_d - 1 - i : i, jp = rev_c ? cols_d - 1 - j : j;
+            tile[r][tx] = src[idx2(jp, ip, lds)];
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        int i = bi + tx, j = bj + r;
+        if (i < rows_d && j < cols_d) dst[idx2(i, j, ldd)] = (Td)(scale * (double)tile[tx][r]);
+    }
+}
+
+template <typename Ts, typename Td>
+void mconvert(const Ts *src, int lds, Td *dst, int ldd, int rows_d, int cols_d, int transpose, int rev_r,
+              int rev_c, double scale, cudaStream_t s)
+{
+    if (rows_d <= 0 || cols_d <= 0) return;
+    dim3 grid(ceil_div(rows_d, 32), ceil_div(cols_d, 32));
+    k_mconvert<Ts, Td><<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows_d, cols_d, transpose, rev_r, rev_c,
+                                           scale);
+}
+
+// max|A| and sum of squares, two-stage deterministic reduction.
+__global__ void __launch_bounds__(256)
+k_absmax_sumsq(const double *__restrict__ A, int lda, int rows, int cols, double *__restrict__ part)
+{
+    __shared__ double smax[8], ssq[8];
+    double mx = 0.0, sq = 0.0;
+    const size_t total = (size_t)rows * cols;
+    for (size_t e = (size_t)blockIdx.x * 256 + threadIdx.x; e < total; e += (size_t)gridDim.x * 256) {
+        const int i = (int)(e % rows), j = (int)(e / rows);
+        const double a = A[idx2(i, j, lda)];
+        mx = fmax(mx, fabs(a));
+        sq = fma(a, a, sq);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    }
+    if ((threadIdx.x & 31) == 0) { smax[threadIdx.x >> 5] = mx; ssq[threadIdx.x >> 5] = sq; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) { mx = fmax(mx, smax[w]); sq += ssq[w]; }
+        part[2 * blockIdx.x] = mx;
+        part[2 * blockIdx.x + 1] = sq;
+    }
+}
+
+__global__ void k_absmax_sumsq_final(const double *__restrict__ part, int nb, double *__restrict__ out)
+{
+    __shared__ double smax[32], ssq[32];
+    double mx = 0.0, sq = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) { mx = fmax(mx, part[2 * b]); sq += part[2 * b + 1]; }
+    smax[threadIdx.x] = mx;
+    ssq[threadIdx.x] = sq;
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 32; w++) { mx = fmax(mx, smax[w]); sq += ssq[w]; }
+        out[0] = mx;
+        out[1] = sq;
+    }
+}
+
+void absmax_sumsq(const double *A, int lda, int rows, int cols, double *part, double *out, cudaStream_t s)
+{
+    if (rows <= 0 || cols <= 0) { cudaMemsetAsync(out, 0, 2 * sizeof(double), s); return; }
+    const size_t total = (size_t)rows * cols;
+    int nb = (int)((total + 256 * 8 - 1) / (256 * 8));
+    if (nb > 1216) nb = 1216;
+    if (nb < 1) nb = 1;
+    k_absmax_sumsq<<<nb, 256, 0, s>>>(A, lda, rows, cols, part);
+    k_absmax_sumsq_final<<<1, 32, 0, s>>>(part, nb, out);
+}
+
+// ---------------------------------------------------------- instantiations --
+template int apply_reflectors_vec<float>(const float *, int, int, int, const float *, int, float *,
+                                         const DevScratch &, cudaStream_t);
+template int apply_reflectors_vec<double>(const double *, int, int, int, const double *, int, double *,
+                                          const DevScratch &, cudaStream_t);
+template int trsv_upper<float>(const float *, int, int, int, float *, const DevScratch &, cudaStream_t);
+template int trsv_upper<double>(const double *, int, int, int, double *, const DevScratch &, cudaStream_t);
+template int gemv<float>(const float *, int, int, int, int, float, const float *, float, float *, int, int,
+                         cudaStream_t);
+template int gemv<double>(const double *, int, int, int, int, double, const double *, double, double *, int,
+                          int, cudaStream_t);
+template void vcopy<double, float>(const double *, float *, int, double, int, cudaStream_t);
+template void vcopy<double, double>(const double *, double *, int, double, int, cudaStream_t);
+template void vcopy<float, double>(const float *, double *, int, double, int, cudaStream_t);
+template void vcopy<float, float>(const float *, float *, int, double, int, cudaStream_t);
+template void vaxpy<float>(const float *, double *, int, double, int, cudaStream_t);
+template void vaxpy<double>(const double *, double *, int, double, int, cudaStream_t);
+template void mconvert<double, float>(const double *, int, float *, int, int, int, int, int, int, double,
+                                      cudaStream_t);
+template void mconvert<double, double>(const double *, int, double *, int, int, int, int, int, int, double,
+                                       cudaStream_t);
+template void mconvert<float, float>(const float *, int, float *, int, int, int, int, int, int, double,
+                                     cudaStream_t);
+template void mconvert<float, double>(const float *, int, double *, int, int, int, int, int, int, double,
+                                      cudaStream_t);
+
+} // namespace mpir

@@ -1,0 +1,255 @@
+"""Thin ctypes binding of libmpir.so (include/mpir.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA
+library.  The C names are kept; tensors are passed as raw device pointers.
+Matrices must be FP64 and column-major (stride(0) == 1); ``colmajor`` makes
+such a tensor.  The library is loaded from the in-tree build; if it is
+missing and cannot be built, importing the solver raises -- there is no CPU
+fallback.
+"""
+import ctypes
+import os
+
+from . import build as _build
+
+_lib = None
+
+PREC = {"bf16": 0, "tf32": 1, "fp32": 2, "fp64": 3}
+REFINE = {"classical": 0, "gmres": 1, "direct": 2}
+STATUS = {0: "ok", 1: "singular R", 2: "singular T", 3: "not converged", 4: "non-finite",
+          5: "unsupported", 6: "cuda error", 7: "device timeout"}
+
+
+class MpirError(RuntimeError):
+    pass
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("fact", ctypes.c_int), ("refine", ctypes.c_int), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("inner_maxit", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("escalate", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iters", ctypes.c_int), ("inner_iters", ctypes.c_int),
+                ("fact_used", ctypes.c_int), ("refine_used", ctypes.c_int), ("escalated", ctypes.c_int),
+                ("stop_ratio", ctypes.c_double * 3), ("time_ms", ctypes.c_double * 6)]
+
+    def as_dict(self):
+        return dict(status=self.status, iters=self.iters, inner_iters=self.inner_iters,
+                    fact_used=self.fact_used, refine_used=self.refine_used, escalated=self.escalated,
+                    stop_ratio=list(self.stop_ratio), time_ms=list(self.time_ms))
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_SIG = {
+    "mpir_version": ([], ctypes.c_char_p),
+    "mpir_default_opts": ([ctypes.POINTER(Opts)], None),
+    "mpir_create": ([ctypes.POINTER(_P), _I, _P], _I),
+    "mpir_destroy": ([_P], _I),
+    "mpir_set_stream": ([_P, _P], _I),
+    "mpir_set_workspace": ([_P, _P, ctypes.c_size_t], _I),
+    "mpir_lse_workspace_size": ([_I, _I, _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)], _I),
+    "mpir_gls_workspace_size": ([_I, _I, _I, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_size_t)], _I),
+    "mpir_last_error": ([_P], ctypes.c_char_p),
+    "lse_solve": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                   ctypes.POINTER(Info)], _I),
+    "gls_solve": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                   ctypes.POINTER(Info)], _I),
+    "lse_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                           ctypes.POINTER(Info)], _I),
+    "gls_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                           ctypes.POINTER(Info)], _I),
+    "mpir_lse_factor": ([_P, _I, _I, _I, _P, _I, _P, _I, _I], _I),
+    "mpir_gls_factor": ([_P, _I, _I, _I, _P, _I, _P, _I, _I], _I),
+    "mpir_get_RT": ([_P, _P, _I, _P, _I], _I),
+    "mpir_apply_factor": ([_P, _I, _I, _P], _I),
+    "mpir_lse_initial": ([_P, _P, _P, _P], _I),
+    "mpir_gls_initial": ([_P, _P, _P, _P], _I),
+    "mpir_lse_multipliers": ([_P, _P, _I, _P, _P, _P, _P], _I),
+    "mpir_gls_multipliers": ([_P, _P, _P], _I),
+    "mpir_lse_residual": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "mpir_gls_residual": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "mpir_lse_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
+    "mpir_gls_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib(build_if_missing=True):
+    """Load libmpir.so; build it in-tree first if it is missing or stale."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and _build.needs_build():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise MpirError("libmpir.so not found at %s (run __graft_entry__.build())" % _build.LIB)
+    L = ctypes.CDLL(_build.LIB)
+    for name, (args, res) in _SIG.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    return list(_SIG.keys())
+
+
+def ptr(t):
+    """Device pointer of a tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def colmajor(t):
+    """Column-major copy of a 2-D tensor (stride(0) == 1)."""
+    return t.t().contiguous().t()
+
+
+def ld(t):
+    if t.dim() != 2 or (t.stride(0) != 1 and t.shape[1] > 1 and t.shape[0] > 1):
+        raise MpirError("matrix must be column-major (stride(0) == 1)")
+    return max(1, t.stride(1) if t.shape[1] > 1 else t.shape[0])
+
+
+def make_opts(fact="fp32", refine="classical", tol=0.0, maxit=0, escalate=True, **kw):
+    o = Opts()
+    lib().mpir_default_opts(ctypes.byref(o))
+    o.fact = PREC[fact] if isinstance(fact, str) else int(fact)
+    o.refine = REFINE[refine] if isinstance(refine, str) else int(refine)
+    if tol:
+        o.tol = tol
+    if maxit:
+        o.maxit = maxit
+    o.escalate = 1 if escalate else 0
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Handle:
+    """Owns an mpir_handle bound to a device and a CUDA stream (the current
+    torch stream by default)."""
+
+    def __init__(self, device=None, stream=None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.h = ctypes.c_void_p()
+        rc = lib().mpir_create(ctypes.byref(self.h), int(device), ctypes.c_void_p(stream))
+        if rc != 0:
+            raise MpirError("mpir_create failed (%d)" % rc)
+
+    def close(self):
+        if self.h:
+            lib().mpir_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self):
+        return lib().mpir_last_error(self.h).decode()
+
+    def check(self, rc, what):
+        if rc < 0:
+            raise MpirError("%s: illegal argument %d (%s)" % (what, -rc, self.last_error()))
+        if rc in (5, 6, 7):
+            raise MpirError("%s: %s (%s)" % (what, STATUS.get(rc, rc), self.last_error()))
+        return rc
+
+    # ---- full solves ------------------------------------------------------
+    def lse_solve(self, A, B, b, d, x, r=None, v=None, opts=None):
+        m, n = A.shape
+        p = B.shape[0]
+        info = Info()
+        o = opts if opts is not None else make_opts()
+        rc = lib().lse_solve(self.h, m, n, p, ptr(A), ld(A), ptr(B), ld(B) if p else 1, ptr(b), ptr(d),
+                             ptr(x), ptr(r), ptr(v), ctypes.byref(o), ctypes.byref(info))
+        return self.check(rc, "lse_solve"), info
+
+    def gls_solve(self, W, V, d, x, y, z=None, opts=None):
+        n, m = W.shape
+        p = V.shape[1]
+        info = Info()
+        o = opts if opts is not None else make_opts()
+        rc = lib().gls_solve(self.h, n, m, p, ptr(W), ld(W), ptr(V), ld(V), ptr(d), ptr(x), ptr(y),
+                             ptr(z), ctypes.byref(o), ctypes.byref(info))
+        return self.check(rc, "gls_solve"), info
+
+    # ---- step-level ---------------------------------------------------------
+    def lse_factor(self, A, B, fact="fp32"):
+        m, n = A.shape
+        p = B.shape[0]
+        rc = lib().mpir_lse_factor(self.h, m, n, p, ptr(A), ld(A), ptr(B), ld(B) if p else 1, PREC[fact])
+        return self.check(rc, "mpir_lse_factor")
+
+    def gls_factor(self, W, V, fact="fp32"):
+        n, m = W.shape
+        p = V.shape[1]
+        rc = lib().mpir_gls_factor(self.h, n, m, p, ptr(W), ld(W), ptr(V), ld(V), PREC[fact])
+        return self.check(rc, "mpir_gls_factor")
+
+    def get_RT(self, R, T):
+        return self.check(lib().mpir_get_RT(self.h, ptr(R), ld(R) if R is not None else 1, ptr(T),
+                                             ld(T) if T is not None else 1), "mpir_get_RT")
+
+    def apply_factor(self, which, trans, vec):
+        return self.check(lib().mpir_apply_factor(self.h, 0 if which == "Q" else 1, 1 if trans else 0,
+                                                  ptr(vec)), "mpir_apply_factor")
+
+    def lse_initial(self, b, d, x):
+        return self.check(lib().mpir_lse_initial(self.h, ptr(b), ptr(d), ptr(x)), "mpir_lse_initial")
+
+    def gls_initial(self, d, x, y):
+        return self.check(lib().mpir_gls_initial(self.h, ptr(d), ptr(x), ptr(y)), "mpir_gls_initial")
+
+    def lse_multipliers(self, A, b, x, r, v):
+        return self.check(lib().mpir_lse_multipliers(self.h, ptr(A), ld(A), ptr(b), ptr(x), ptr(r), ptr(v)),
+                          "mpir_lse_multipliers")
+
+    def gls_multipliers(self, y, z):
+        return self.check(lib().mpir_gls_multipliers(self.h, ptr(y), ptr(z)), "mpir_gls_multipliers")
+
+    def lse_residual(self, A, B, b, d, x, r, v, f1, f2, f3, norms=None):
+        m, n = A.shape
+        p = B.shape[0]
+        buf = (ctypes.c_double * 8)()
+        rc = lib().mpir_lse_residual(self.h, m, n, p, ptr(A), ld(A), ptr(B), ld(B) if p else 1, ptr(b),
+                                     ptr(d), ptr(x), ptr(r), ptr(v), ptr(f1), ptr(f2), ptr(f3),
+                                     ctypes.cast(buf, ctypes.c_void_p))
+        self.check(rc, "mpir_lse_residual")
+        return list(buf)
+
+    def gls_residual(self, W, V, d, x, y, z, f1, f2, f3):
+        n, m = W.shape
+        p = V.shape[1]
+        buf = (ctypes.c_double * 8)()
+        rc = lib().mpir_gls_residual(self.h, n, m, p, ptr(W), ld(W), ptr(V), ld(V), ptr(d), ptr(x), ptr(y),
+                                     ptr(z), ptr(f1), ptr(f2), ptr(f3), ctypes.cast(buf, ctypes.c_void_p))
+        self.check(rc, "mpir_gls_residual")
+        return list(buf)
+
+    def lse_correction(self, f1, f2, f3, dr, dv, dx):
+        return self.check(lib().mpir_lse_correction(self.h, ptr(f1), ptr(f2), ptr(f3), ptr(dr), ptr(dv),
+                                                    ptr(dx)), "mpir_lse_correction")
+
+    def gls_correction(self, f1, f2, f3, dy, dz, dx):
+        return self.check(lib().mpir_gls_correction(self.h, ptr(f1), ptr(f2), ptr(f3), ptr(dy), ptr(dz),
+                                                    ptr(dx)), "mpir_gls_correction")
