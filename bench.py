@@ -1,0 +1,443 @@
+#!/usr/bin/env python3
+"""Benchmark: solves/s of the mixed-precision GLS solve (FP32 GQR + FP64
+classical iterative refinement, Alg. 4) on one GB300, next to the plain FP64
+GQR solve on the same GPU and the CPU oracle on the host cores.
+
+Workload (one "step" = one complete solve, factorization included):
+  GLS in the xGGGLM convention, n = 4096, m = 1024, p = 4096:
+  W 4096 x 1024 with cond 1e3 (seeded SVD construction, logspace spectrum),
+  V the 4096 x 4096 lower-triangular Cholesky factor of an AR(1) covariance
+  (rho = 0.9), d = W x + V y with x, y ~ N(0, 1).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  For N > 1 it is launched with torchrun; each
+rank solves its own independent problem (replicas, no collective on the data
+path); the time is the max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "solves/s at FP64-level accuracy: mixed-precision IR vs FP64 GRQ/GQR, same GB300"
+WORKLOAD = ("GLS n=4096 m=1024 p=4096 (xGGGLM shapes): W cond 1e3 SVD construction, "
+            "V = Cholesky factor of AR(1) covariance rho=0.9, d = W x + V y")
+N_, M_, P_ = 4096, 1024, 4096
+SEED = 20242623
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fact", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+# --------------------------------------------------------------- clocks --
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                rows.append(f)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        out["samples"] = len(rows)
+        out["sm_mhz"] = sm[len(sm) // 2] if sm else None
+        try:
+            out["sm_max_mhz"] = float(rows[0][2])
+        except ValueError:
+            pass
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out["reasons"] = sorted(reasons)
+        return out
+
+
+# ------------------------------------------------------- algorithmic work --
+
+def qr_work(M, N, nb=32):
+    """(panel flops, larfb flops) of the blocked Householder QR of M x N as
+    the library runs it (panels of nb columns, trailing update per panel)."""
+    k = min(M, N)
+    pf = lf = 0.0
+    for j0 in range(0, k, nb):
+        nc = min(nb, N - j0)
+        L = M - j0
+        kb = min(nc, L)
+        pf += 4.0 * L * kb * nc - 2.0 * kb * kb * nc          # panel (unblocked Householder)
+        Nc = N - j0 - nc
+        if Nc > 0:
+            lf += 4.0 * L * kb * Nc + 2.0 * kb * kb * Nc        # V^T C, Tw^T W, C - V W
+    return pf, lf
+
+
+def apply_work(M, K, Nc, nb=32):
+    lf = 0.0
+    for j0 in range(0, K, nb):
+        kb = min(nb, K - j0)
+        L = M - j0
+        lf += 4.0 * L * kb * Nc + 2.0 * kb * kb * Nc
+    return lf
+
+
+def gls_work(n, m, p, nb=32):
+    p1, l1 = qr_work(n, m, nb)
+    l2 = apply_work(n, m, p, nb)
+    p3, l3 = qr_work(p, n, nb)
+    return dict(panel_flops=p1 + p3, larfb_flops=l1 + l2 + l3,
+                factor_flops=p1 + p3 + l1 + l2 + l3,
+                resid_bytes=8.0 * (n * m + n * p), resid_flops=4.0 * (m * n + n * p))
+
+
+def fp32_simt_peak(sm_mhz):
+    """152 SMs x 128 FP32 lanes x 2 flop/FMA at the given SM clock (TFLOP/s)."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0, "_fallback": True}
+
+
+def traffic_record(kind):
+    """Per-launch DRAM traffic of `kind` from the committed ncu summary, if
+    it was taken on the current source of the kernel (else None)."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except Exception:
+        return None
+    r = rec.get(kind)
+    if not r:
+        return None
+    src = os.path.join(ROOT, "paper_2406_16499_gb300", "csrc", r["source"])
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except Exception:
+        return None
+    return r["bytes_per_launch"] if sha == r.get("source_sha") else None
+
+
+# --------------------------------------------------------------- arms --
+
+def make_inputs(rank):
+    from paper_2406_16499_gb300 import inputs as I
+    return I.gls_ar1(seed=SEED + 1000 * rank, n=N_, m=M_)
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    G = make_inputs(0)
+    W, V, d = G["W"], G["V"], G["d"]
+    oracle.lib()
+    t0 = time.perf_counter()
+    out = oracle.gls_solve(W, V, d, fact="fp32")          # warm sample, also sizes the run
+    t_first = time.perf_counter() - t0
+    budget = 150.0
+    warm = max(0, min(args.warmup - 1, int(budget / max(t_first, 1e-3)) // 4))
+    for _ in range(warm):
+        oracle.gls_solve(W, V, d, fact="fp32")
+    steps = max(1, min(args.steps, int(budget / max(t_first, 1e-3))))
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        out = oracle.gls_solve(W, V, d, fact="fp32")
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    met = oracle.gls_metrics(W, V, d, out["x"], out["y"], out["z"])
+    value = 1000.0 / ms
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+        "steps": steps, "warmup": 1 + warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "fact": "fp32", "refine": "classical",
+                   "parallelism": "replicas (rank 0 only for the CPU oracle)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": "%d full solve(s) of the workload by the CPU oracle (Alg. 4: unblocked "
+                                   "FP32 GQR + FP64 classical IR, OpenMP)" % steps},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "accuracy": {"eta": met["eta"], "e_con": met["e_con"], "iters": out["iters"], "status": out["status"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2406_16499_gb300 import mpir
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    G = make_inputs(rank)
+    Wn, Vn, dn = G["W"], G["V"], G["d"]
+    n, m = Wn.shape
+    p = Vn.shape[1]
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
+
+    W, V, d = to_dev(Wn), to_dev(Vn), torch.from_numpy(dn.copy()).to(dev)
+    x = torch.zeros(m, dtype=torch.float64, device=dev)
+    y = torch.zeros(p, dtype=torch.float64, device=dev)
+    z = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    h = mpir.Handle(local, stream.cuda_stream)
+    opts = mpir.make_opts(fact=args.fact, refine="classical")
+
+    def solve(o=opts, xx=x, yy=y, zz=z, WW=W, VV=V, dd=d):
+        st, info = h.gls_solve(WW, VV, dd, xx, yy, zz, o)
+        if st != 0:
+            raise RuntimeError("gls_solve status %d: %s" % (st, h.last_error()))
+        return info
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for _ in range(max(args.warmup, 3)):
+        solve()
+    barrier()
+    launches0 = mpir.launch_count()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    total_ms = 0.0
+    info = None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        info = solve()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    clk = clocks.stop()
+    barrier()
+    gpu_launches = (mpir.launch_count() - launches0) // max(args.steps, 1)
+    ms = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 1000.0 / ms
+
+    # ---- per-kernel device time over a profiled pass of the same steps --
+    mpir.profile(True)
+    kp = max(2, min(args.steps, 4))
+    for _ in range(kp):
+        flush.zero_()
+        solve()
+    torch.cuda.synchronize(dev)
+    prof = mpir.profile_read()
+    mpir.profile(False)
+
+    # ---- accuracy of the last solution (oracle, double-double residual) --
+    acc = {}
+    if rank == 0:
+        import oracle
+        met = oracle.gls_metrics(Wn, Vn, dn, x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy())
+        acc = {"eta": met["eta"], "e_con": met["e_con"], "iters": info.iters,
+               "stop_ratio": list(info.stop_ratio), "fact_used": info.fact_used, "escalated": info.escalated}
+
+    # ---- FP64 GQR direct solve on the same GPU (the fixed-precision path) --
+    o64 = mpir.make_opts(fact="fp64", refine="direct")
+    x64 = torch.zeros_like(x)
+    y64 = torch.zeros_like(y)
+    solve(o64, x64, y64)
+    torch.cuda.synchronize(dev)
+    k64 = 3
+    t64 = 0.0
+    for _ in range(k64):
+        flush.zero_()
+        e0.record(stream)
+        solve(o64, x64, y64)
+        e1.record(stream)
+        e1.synchronize()
+        t64 += e0.elapsed_time(e1)
+    ms64 = t64 / k64
+    fp64 = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_step": ms64,
+            "what": "FP64 GQR + Paige's method, no refinement, same kernels at FP64"}
+    if rank == 0:
+        import oracle
+        met = oracle.gls_metrics(Wn, Vn, dn, x64.cpu().numpy(), y64.cpu().numpy(),
+                                 np.zeros(n))
+        fp64["e_con"] = met["e_con"]
+
+    # ---- end to end from pinned host buffers through the public API --------
+    Wh = torch.from_numpy(np.ascontiguousarray(Wn.T)).pin_memory()
+    Vh = torch.from_numpy(np.ascontiguousarray(Vn.T)).pin_memory()
+    dh = torch.from_numpy(dn.copy()).pin_memory()
+    xh = torch.empty(m, dtype=torch.float64).pin_memory()
+    yh = torch.empty(p, dtype=torch.float64).pin_memory()
+    Wd = torch.empty((m, n), dtype=torch.float64, device=dev)
+    Vd = torch.empty((p, n), dtype=torch.float64, device=dev)
+    dd_ = torch.empty(n, dtype=torch.float64, device=dev)
+    h2d = (Wh.numel() + Vh.numel() + dh.numel()) * 8
+    d2h = (m + p) * 8
+
+    def e2e_step():
+        Wd.copy_(Wh, non_blocking=True)
+        Vd.copy_(Vh, non_blocking=True)
+        dd_.copy_(dh, non_blocking=True)
+        solve(opts, x, y, z, Wd.t(), Vd.t(), dd_)
+        xh.copy_(x, non_blocking=True)
+        yh.copy_(y, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    te = 0.0
+    ke = args.steps
+    for _ in range(ke):
+        flush.zero_()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        e2e_step()
+        torch.cuda.synchronize(dev)
+        te += time.perf_counter() - t0
+    e2e_ms = 1000.0 * te / ke
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    # ---- roofline of the dominant kernel --------------------------------
+    work = gls_work(n, m, p)
+    peaks = measured_peaks()
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_cnt) = dom
+    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    if dom_name == "larfb":
+        alg = work["larfb_flops"] * kp
+        peak = fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 x max SM clock"}
+        achieved = alg / (dom_ms * 1e-3) / 1e12
+    elif dom_name == "panel_qr":
+        alg = work["panel_flops"] * kp
+        peak = fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0))
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_note": "FP32 SIMT at max SM clock"}
+        achieved = alg / (dom_ms * 1e-3) / 1e12
+    else:
+        alg = work["resid_bytes"] * kp * (info.iters if info else 1)
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "unit": "GB/s", "peak_note": "measured HBM copy bandwidth"}
+        achieved = alg / (dom_ms * 1e-3) / 1e9
+    roof.update({"kernel": dom_name, "achieved": achieved, "peak": peak, "frac": achieved / peak,
+                 "launches_per_step": dom_cnt / kp, "ms_per_step": dom_ms / kp,
+                 "traffic": traffic_record(dom_name), "peak_source": "MEASURED_PEAKS.json/unit counts"})
+    kernels = {k: {"ms_per_step": v[0] / kp, "launches_per_step": v[1] / kp} for k, v in prof.items() if v[1]}
+
+    # ---- CPU oracle on the host cores (bounded sample, rank 0, N = 1) ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t0 = time.perf_counter()
+        oracle.gls_solve(Wn, Vn, dn, fact="fp32")
+        tc = time.perf_counter() - t0
+        cpu = {"value": 1.0 / tc, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "1 full solve of the workload (Alg. 4: unblocked FP32 GQR + FP64 IR, OpenMP), "
+                         "%.1f s" % tc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "fact": args.fact, "refine": "classical",
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "l2": "inputs 168 MB > L2; 256 MB L2 flush before every timed step"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * 1000.0 / e2e_ms, "unit": "solves/s", "ms_per_step": e2e_ms,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(gpu_launches),
+            "clocks": clk,
+            "accuracy": acc,
+            "fp64_direct": fp64,
+            "speedup_vs_fp64_direct": value / (world * fp64["value"]),
+            "kernels": kernels,
+            "algorithmic": work,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

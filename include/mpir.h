@@ -241,6 +241,19 @@ int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
 /* Library version string. */
 const char *mpir_version(void);
 
+/* Process-wide launch accounting (every kernel launch of the library is
+ * counted by kind) and optional per-kind device timing: mpir_profile(1)
+ * clears the records and records a CUDA event pair around every launch on
+ * the launch stream; mpir_profile_read synchronizes on the last record and
+ * returns, per kind, the summed event time (ms) and the number of timed
+ * launches.  Kinds: 0 panel_qr, 1 larfb, 2 vec_apply, 3 trsv, 4 gemv,
+ * 5 dual_gemv_fp64, 6 resid_finalize, 7 convert, 8 norm, 9 elementwise.
+ * Not thread-safe; a profiling aid, off by default. */
+int mpir_profile(int enable);
+int mpir_profile_read(double *ms, long long *launches, int nkinds);
+long long mpir_launch_count(int kind);          /* kind < 0: all kinds */
+const char *mpir_kernel_kind_name(int kind);
+
 #ifdef __cplusplus
 }
 #endif

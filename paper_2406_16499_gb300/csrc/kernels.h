@@ -6,6 +6,21 @@
 
 namespace mpir {
 
+// Kernel kinds for the launch counter and the optional per-kind timers.
+enum KernelKind {
+    K_PANEL = 0, K_LARFB, K_VEC_APPLY, K_TRSV, K_GEMV, K_DUAL_GEMV, K_FINALIZE, K_CONVERT, K_NORM,
+    K_ELEMWISE, K_NKINDS
+};
+// Called around every kernel launch: counts the launch and, when timing is
+// enabled (mpir_profile), records a CUDA event pair on the launch stream.
+void prof_begin(int kind, cudaStream_t s);
+void prof_end(int kind, cudaStream_t s);
+struct ProfScope {
+    int k; cudaStream_t s;
+    ProfScope(int kind, cudaStream_t st) : k(kind), s(st) { prof_begin(k, s); }
+    ~ProfScope() { prof_end(k, s); }
+};
+
 // Larfb (trailing update / block-reflector application) operand precision.
 enum class GemmPrec { FP32 = 0, TF32 = 1, BF16 = 2, FP64 = 3 };
 
@@ -53,9 +68,16 @@ int gemv(const T *M, int ld, int rows, int cols, int trans, T alpha, const T *x,
          int upper_mask, int diag_off, cudaStream_t s);
 
 // Elementwise helpers.
-// dst[i] = (T)(scale * src[rev ? n-1-i : i])
+// dst[i] = (T)(scale * g * src[rev ? n-1-i : i]), g = *dscale (device
+// scalar) when dscale != NULL, else 1.
 template <typename Ts, typename Td>
-void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s);
+void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s,
+           const double *dscale = nullptr);
+// Power-of-two normalization of right-hand sides before down-conversion:
+// g = 2^-e with max(|a1 * u|, |a2 * w|) * g in [0.5, 1) (1 if the max is 0 or
+// not finite); out[0] = g, out[1] = 1 / g.  Device only (no host sync).
+void pow2_normalizer(const double *u, int nu, double a1, const double *w, int nw, double a2, double *out,
+                     cudaStream_t s);
 // dst[i] += scale * src[rev ? n-1-i : i]   (FP64 destination)
 template <typename Ts>
 void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s);

@@ -317,6 +317,7 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    ProfScope ps(K_PANEL, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
@@ -327,6 +328,7 @@ static int launch_larfb(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
 {
     constexpr int NB = panel_nb<T>();
     if (Nc <= 0 || L <= 0 || kb <= 0) return 0;
+    ProfScope ps(K_LARFB, s);
     k_larfb_left<T, NB><<<ceil_div(Nc, 32), 256, 0, s>>>(V, ldv, Tw, kb, L, C, ldc, Nc, trans);
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }

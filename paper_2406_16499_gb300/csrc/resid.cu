@@ -81,6 +81,7 @@ void dual_gemv(const double *A, int lda, int rows, int cols, const double *x, co
 {
     if (rows <= 0 || cols <= 0) return;
     dim3 grid(ceil_div(rows, RB), ceil_div(cols, CB));
+    ProfScope ps(K_DUAL_GEMV, s);
     k_dual_gemv<<<grid, 256, 0, s>>>(A, lda, rows, cols, x, r, part_Ax, part_Atr);
 }
 
@@ -176,6 +177,7 @@ void lse_resid_finalize(int m, int n, int p, const double *b, const double *d, c
 {
     const int total = m + p + n + n + m + p;
     const int nb = finalize_blocks(total);
+    ProfScope ps(K_FINALIZE, s);
     k_resid_finalize<0><<<nb, 256, 0, s>>>(m, p, n, n, m, p, b, d, x, r, v, pAx, ncbA, pAtr, nrbA, pBx, ncbB,
                                            pBtv, nrbB, f1, f2, f3, normpart);
     k_norm_final<<<1, 32, 0, s>>>(normpart, nb, norms2);
@@ -188,6 +190,7 @@ void gls_resid_finalize(int n, int m, int p, const double *d, const double *x, c
 {
     const int total = p + n + m + m + p + n;
     const int nb = finalize_blocks(total);
+    ProfScope ps(K_FINALIZE, s);
     k_resid_finalize<1><<<nb, 256, 0, s>>>(p, n, m, m, p, n, d, nullptr, x, y, z, pWx, ncbW, pWtz, nrbW, pVy,
                                            ncbV, pVtz, nrbV, f1, f2, f3, normpart);
     k_norm_final<<<1, 32, 0, s>>>(normpart, nb, norms2);

@@ -37,6 +37,46 @@
 
 using namespace mpir;
 
+// ----------------------------------------------------- launch profiling --
+// Process-wide: a launch counter per kernel kind, and (when enabled) a pool
+// of CUDA event pairs recorded around every launch on its own stream.
+namespace mpir {
+static long long g_launches[K_NKINDS];
+static bool g_prof = false;
+static std::vector<cudaEvent_t> g_ev;
+static std::vector<int> g_kind;
+static size_t g_nrec = 0;
+static bool g_open = false;
+constexpr size_t PROF_CAP = 1 << 16;
+
+void prof_begin(int kind, cudaStream_t s)
+{
+    g_launches[kind]++;
+    if (!g_prof || g_nrec >= PROF_CAP) return;
+    if (g_ev.size() < 2 * (g_nrec + 1)) {
+        size_t old = g_ev.size();
+        g_ev.resize(old + 2048);
+        for (size_t i = old; i < g_ev.size(); i++) cudaEventCreate(&g_ev[i]);
+        g_kind.resize(g_ev.size() / 2);
+    }
+    cudaEventRecord(g_ev[2 * g_nrec], s);
+    g_open = true;
+}
+
+void prof_end(int kind, cudaStream_t s)
+{
+    if (!g_prof || !g_open) return;
+    cudaEventRecord(g_ev[2 * g_nrec + 1], s);
+    g_kind[g_nrec] = kind;
+    g_nrec++;
+    g_open = false;
+}
+} // namespace mpir
+
+static const char *g_kind_names[K_NKINDS] = {"panel_qr", "larfb", "vec_apply", "trsv", "gemv",
+                                             "dual_gemv_fp64", "resid_finalize", "convert", "norm",
+                                             "elementwise"};
+
 #define MPIR_VERSION_STRING "libmpir 0.1 (sm_103a)"
 
 // ------------------------------------------------------------------ ctx --
@@ -290,7 +330,9 @@ __global__ void k_vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, 
 template <typename T>
 void vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, int rb, T beta, cudaStream_t s)
 {
-    if (n > 0) k_vcomb<T><<<ceil_div(n, 256), 256, 0, s>>>(out, n, a, ra, alpha, b, rb, beta);
+    if (n <= 0) return;
+    ProfScope ps(K_ELEMWISE, s);
+    k_vcomb<T><<<ceil_div(n, 256), 256, 0, s>>>(out, n, a, ra, alpha, b, rb, beta);
 }
 
 __global__ void k_mask_lower(double *M, int ld, int rows, int cols, int off)
@@ -345,8 +387,10 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
     const int n = w.n, m = w.m, p = w.p, L = w.L;
     cudaStream_t s = h->stream;
-    // c = Q^T d
-    vcopy<double, T>(d, w.tu, n, 1.0, 0, s);
+    // c = Q^T (g d), g a power-of-two normalizer; x, y = result / g
+    double *g = w.scal + 8;
+    pow2_normalizer(d, n, 1.0, nullptr, 0, 0.0, g, s);
+    vcopy<double, T>(d, w.tu, n, 1.0, 0, s, g);
     RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 1, w.tu, h->sc, s));
     // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
     vzero(w.tg, sizeof(T) * p, s);
@@ -356,10 +400,10 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 1, T(1), w.tg, T(0), w.tt, 0, 0, s));
     vcomb<T>(w.tt2, m, w.tu, 0, T(1), w.tt, 1, T(-1), s);
     RC(trsv_upper<T>(w.Wf, n, m, 0, w.tt2, h->sc, s));
-    vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s);
+    vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s, g + 1);
     // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
     RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
-    vcopy<T, double>(w.tg, y, p, fs.s2, 1, s);
+    vcopy<T, double>(w.tg, y, p, fs.s2, 1, s, g + 1);
     return cuda_check(h, "gls_initial");
 }
 
@@ -371,8 +415,10 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
     const int n = w.n, m = w.m, p = w.p, L = w.L;
     cudaStream_t s = h->stream;
-    // y' = y / sV ; w~ = Z~^T (P_p y')
-    vcopy<double, T>(y, w.tw, p, 1.0 / fs.s2, 1, s);
+    // y' = y / sV ; w~ = Z~^T (P_p g y'), g a power-of-two normalizer
+    double *g = w.scal + 8;
+    pow2_normalizer(y, p, 1.0 / fs.s2, nullptr, 0, 0.0, g, s);
+    vcopy<double, T>(y, w.tw, p, 1.0 / fs.s2, 1, s, g);
     RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
     // T~_L h~2 = w~[0:L]
     vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
@@ -381,7 +427,7 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     vzero(w.tt, sizeof(T) * n, s);
     vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
     RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 0, w.tt, h->sc, s));
-    vcopy<T, double>(w.tt, z, n, fs.s2 * fs.s2, 0, s);
+    vcopy<T, double>(w.tt, z, n, fs.s2 * fs.s2, 0, s, g + 1);
     return cuda_check(h, "gls_multipliers");
 }
 
@@ -595,10 +641,13 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
     const int m = w.m, n = w.n, p = w.p, q = w.q;
     cudaStream_t s = h->stream;
-    vcopy<double, T>(b, w.tw, m, fs.s1, 0, s);
+    // common power-of-two normalization g of (sA b, sB d); x = result / g
+    double *g = w.scal + 8;
+    pow2_normalizer(b, m, fs.s1, d, p, fs.s2, g, s);
+    vcopy<double, T>(b, w.tw, m, fs.s1, 0, s, g);
     RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
     // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
-    vcopy<double, T>(d, w.tb, p, fs.s2, 1, s);
+    vcopy<double, T>(d, w.tb, p, fs.s2, 1, s, g);
     RC(trsv_upper<T>(w.Bt, n, p, 1, w.tb, h->sc, s));
     // ty = [y1; y2], y2 = P_p y~2
     vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
@@ -608,7 +657,7 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     // x = Q^T y = P_n Q~ P_n y
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
     RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 0, w.tt, h->sc, s));
-    vcopy<T, double>(w.tt, x, n, 1.0, 1, s);
+    vcopy<T, double>(w.tt, x, n, 1.0, 1, s, g + 1);
     return cuda_check(h, "lse_initial");
 }
 
@@ -625,12 +674,14 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     RC(gemv<double>(A, lda, m, n, 0, -1.0, x, 1.0, r, 0, 0, s));
     if (p == 0) return cuda_check(h, "lse_multipliers");
     RC(gemv<double>(A, lda, m, n, 1, 1.0, r, 0.0, w.f3, 0, 0, s));
-    // u~ = Q~^T P_n (sA A^T r)
-    vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s);
+    // u~ = Q~^T P_n (g sA A^T r), g a power-of-two normalizer
+    double *g = w.scal + 8;
+    pow2_normalizer(w.f3, n, fs.s1, nullptr, 0, 0.0, g, s);
+    vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s, g);
     RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 1, w.tu, h->sc, s));
     // R~ (P_p v') = u~[0:p]
     RC(trsv_upper<T>(w.Bt, n, p, 0, w.tu, h->sc, s));
-    vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s);
+    vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s, g + 1);
     return cuda_check(h, "lse_multipliers");
 }
 
@@ -784,6 +835,43 @@ bool is_fp64(int fact) { return fact == MPIR_FP64; }
 extern "C" {
 
 const char *mpir_version(void) { return MPIR_VERSION_STRING; }
+
+int mpir_profile(int enable)
+{
+    g_prof = enable != 0;
+    g_nrec = 0;
+    g_open = false;
+    return 0;
+}
+
+int mpir_profile_read(double *ms, long long *launches, int nkinds)
+{
+    if (nkinds > K_NKINDS) nkinds = K_NKINDS;
+    for (int k = 0; k < nkinds; k++) { if (ms) ms[k] = 0.0; if (launches) launches[k] = 0; }
+    if (g_nrec) cudaEventSynchronize(g_ev[2 * g_nrec - 1]);
+    for (size_t i = 0; i < g_nrec; i++) {
+        float t = 0;
+        cudaEventElapsedTime(&t, g_ev[2 * i], g_ev[2 * i + 1]);
+        int k = g_kind[i];
+        if (k < nkinds) { if (ms) ms[k] += t; if (launches) launches[k]++; }
+    }
+    return nkinds;
+}
+
+long long mpir_launch_count(int kind)
+{
+    if (kind < 0) {
+        long long t = 0;
+        for (int k = 0; k < K_NKINDS; k++) t += g_launches[k];
+        return t;
+    }
+    return kind < K_NKINDS ? g_launches[kind] : 0;
+}
+
+const char *mpir_kernel_kind_name(int kind)
+{
+    return (kind >= 0 && kind < K_NKINDS) ? g_kind_names[kind] : "";
+}
 
 void mpir_default_opts(mpir_opts *o)
 {
@@ -1202,23 +1290,23 @@ static int get_RT_impl(mpir_ctx *h, double *R, int ldr, double *Tm, int ldt)
         if (R && p > 0) {
             // R(i, j) = R~(p-1-j, p-1-i) = Bt(p-1-j, p-1-i) / sB
             mconvert<T, double>(w.Bt, n, R, ldr, p, p, 1, 1, 1, 1.0 / fs.s2, s);
-            k_mask_lower<<<dim3(ceil_div(p, 256), p), 256, 0, s>>>(R, ldr, p, p, 0);
+            { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(p, 256), p), 256, 0, s>>>(R, ldr, p, p, 0); }
         }
         if (Tm) {
             mconvert<T, double>(w.At, m, Tm, ldt, m, n, 0, 0, 0, 1.0 / fs.s1, s);
-            k_mask_lower<<<dim3(ceil_div(m, 256), n), 256, 0, s>>>(Tm, ldt, m, n, 0);
+            { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(m, 256), n), 256, 0, s>>>(Tm, ldt, m, n, 0); }
         }
     } else {
         GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
         const int n = w.n, m = w.m, p = w.p;
         if (R && m > 0) {
             mconvert<T, double>(w.Wf, n, R, ldr, m, m, 0, 0, 0, 1.0 / fs.s1, s);
-            k_mask_lower<<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(R, ldr, m, m, 0);
+            { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(R, ldr, m, m, 0); }
         }
         if (Tm) {
             // T(r, j) = T~(p-1-j, n-1-r) = Ct(p-1-j, n-1-r) / sV ; zero for r > j + n - p
             mconvert<T, double>(w.Ct, p, Tm, ldt, n, p, 1, 1, 1, 1.0 / fs.s2, s);
-            k_mask_lower<<<dim3(ceil_div(n, 256), p), 256, 0, s>>>(Tm, ldt, n, p, n - p);
+            { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(n, 256), p), 256, 0, s>>>(Tm, ldt, n, p, n - p); }
         }
     }
     return cuda_check(h, "get_RT");

@@ -141,6 +141,7 @@ int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int tra
     T *part = reinterpret_cast<T *>(sc.part);
     void *args[] = {(void *)&V, (void *)&ldv, (void *)&M, (void *)&K, (void *)&Tw, (void *)&trans,
                     (void *)&x, (void *)&slice, (void *)&part, (void *)&gb};
+    ProfScope ps(K_VEC_APPLY, s);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(256), args, smem, s);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
@@ -255,6 +256,7 @@ int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc
     int *status = sc.status;
     void *args[] = {(void *)&U, (void *)&ldu, (void *)&n, (void *)&trans, (void *)&x, (void *)&slice,
                     (void *)&xbuf, (void *)&status, (void *)&gb};
+    ProfScope ps(K_TRSV, s);
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(256), args, smem, s);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
@@ -309,12 +311,12 @@ template <typename T>
 int gemv(const T *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
          int upper_mask, int diag_off, cudaStream_t s)
 {
+    if ((!trans && rows <= 0) || (trans && cols <= 0)) return 0;
+    ProfScope ps(K_GEMV, s);
     if (!trans) {
-        if (rows <= 0) return 0;
         k_gemv_n<T><<<ceil_div(rows, 32), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
                                                         diag_off);
     } else {
-        if (cols <= 0) return 0;
         k_gemv_t<T><<<ceil_div(cols, 8), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
                                                        diag_off);
     }
@@ -324,10 +326,39 @@ int gemv(const T *M, int ld, int rows, int cols, int trans, T alpha, const T *x,
 // ------------------------------------------------------------ elementwise --
 
 template <typename Ts, typename Td>
-__global__ void k_vcopy(const Ts *__restrict__ src, Td *__restrict__ dst, int n, double scale, int rev)
+__global__ void k_vcopy(const Ts *__restrict__ src, Td *__restrict__ dst, int n, double scale, int rev,
+                        const double *__restrict__ dscale)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] = (Td)(scale * (double)src[rev ? n - 1 - i : i]);
+    const double g = dscale ? scale * dscale[0] : scale;
+    if (i < n) dst[i] = (Td)(g * (double)src[rev ? n - 1 - i : i]);
+}
+
+__global__ void __launch_bounds__(256)
+k_pow2_normalizer(const double *__restrict__ u, int nu, double a1, const double *__restrict__ w, int nw,
+                  double a2, double *__restrict__ out)
+{
+    __shared__ double red[8];
+    double mx = 0.0;
+    for (int i = threadIdx.x; i < nu; i += 256) mx = fmax(mx, fabs(a1 * u[i]));
+    for (int i = threadIdx.x; i < nw; i += 256) mx = fmax(mx, fabs(a2 * w[i]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 1; k < 8; k++) mx = fmax(mx, red[k]);
+        double g = 1.0;
+        if (mx > 0.0 && isfinite(mx)) g = ldexp(1.0, -(ilogb(mx) + 1));
+        out[0] = g;
+        out[1] = 1.0 / g;
+    }
+}
+
+void pow2_normalizer(const double *u, int nu, double a1, const double *w, int nw, double a2, double *out,
+                     cudaStream_t s)
+{
+    ProfScope ps(K_NORM, s);
+    k_pow2_normalizer<<<1, 256, 0, s>>>(u, nu, a1, w, nw, a2, out);
 }
 
 template <typename Ts>
@@ -338,15 +369,19 @@ __global__ void k_vaxpy(const Ts *__restrict__ src, double *__restrict__ dst, in
 }
 
 template <typename Ts, typename Td>
-void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s)
+void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s, const double *dscale)
 {
-    if (n > 0) k_vcopy<Ts, Td><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev);
+    if (n <= 0) return;
+    ProfScope ps(K_ELEMWISE, s);
+    k_vcopy<Ts, Td><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev, dscale);
 }
 
 template <typename Ts>
 void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s)
 {
-    if (n > 0) k_vaxpy<Ts><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev);
+    if (n <= 0) return;
+    ProfScope ps(K_ELEMWISE, s);
+    k_vaxpy<Ts><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev);
 }
 
 void vzero(void *dst, size_t bytes, cudaStream_t s)
@@ -397,6 +432,7 @@ void mconvert(const Ts *src, int lds, Td *dst, int ldd, int rows_d, int cols_d, 
 {
     if (rows_d <= 0 || cols_d <= 0) return;
     dim3 grid(ceil_div(rows_d, 32), ceil_div(cols_d, 32));
+    ProfScope ps(K_CONVERT, s);
     k_mconvert<Ts, Td><<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows_d, cols_d, transpose, rev_r, rev_c,
                                            scale);
 }
@@ -449,6 +485,7 @@ void absmax_sumsq(const double *A, int lda, int rows, int cols, double *part, do
     int nb = (int)((total + 256 * 8 - 1) / (256 * 8));
     if (nb > 1216) nb = 1216;
     if (nb < 1) nb = 1;
+    ProfScope ps(K_NORM, s);
     k_absmax_sumsq<<<nb, 256, 0, s>>>(A, lda, rows, cols, part);
     k_absmax_sumsq_final<<<1, 32, 0, s>>>(part, nb, out);
 }
@@ -464,10 +501,10 @@ template int gemv<float>(const float *, int, int, int, int, float, const float *
                          cudaStream_t);
 template int gemv<double>(const double *, int, int, int, int, double, const double *, double, double *, int,
                           int, cudaStream_t);
-template void vcopy<double, float>(const double *, float *, int, double, int, cudaStream_t);
-template void vcopy<double, double>(const double *, double *, int, double, int, cudaStream_t);
-template void vcopy<float, double>(const float *, double *, int, double, int, cudaStream_t);
-template void vcopy<float, float>(const float *, float *, int, double, int, cudaStream_t);
+template void vcopy<double, float>(const double *, float *, int, double, int, cudaStream_t, const double *);
+template void vcopy<double, double>(const double *, double *, int, double, int, cudaStream_t, const double *);
+template void vcopy<float, double>(const float *, double *, int, double, int, cudaStream_t, const double *);
+template void vcopy<float, float>(const float *, float *, int, double, int, cudaStream_t, const double *);
 template void vaxpy<float>(const float *, double *, int, double, int, cudaStream_t);
 template void vaxpy<double>(const double *, double *, int, double, int, cudaStream_t);
 template void mconvert<double, float>(const double *, int, float *, int, int, int, int, int, int, double,

@@ -74,7 +74,30 @@ _SIG = {
     "mpir_gls_residual": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_lse_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_gls_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
+    "mpir_profile": ([_I], _I),
+    "mpir_profile_read": ([_P, _P, _I], _I),
+    "mpir_launch_count": ([_I], ctypes.c_longlong),
+    "mpir_kernel_kind_name": ([_I], ctypes.c_char_p),
 }
+
+NKINDS = 10
+
+
+def profile(enable):
+    """Enable (and clear) or disable per-launch event timing."""
+    lib().mpir_profile(1 if enable else 0)
+
+
+def profile_read():
+    """{kind name: (ms, launches)} of the launches timed since profile(True)."""
+    ms = (ctypes.c_double * NKINDS)()
+    cnt = (ctypes.c_longlong * NKINDS)()
+    lib().mpir_profile_read(ctypes.cast(ms, ctypes.c_void_p), ctypes.cast(cnt, ctypes.c_void_p), NKINDS)
+    return {lib().mpir_kernel_kind_name(k).decode(): (ms[k], cnt[k]) for k in range(NKINDS)}
+
+
+def launch_count(kind=-1):
+    return int(lib().mpir_launch_count(kind))
 
 
 def library_path():
@@ -104,11 +127,13 @@ def exported_symbols():
 
 
 def ptr(t):
-    """Device pointer of a tensor (None -> NULL)."""
+    """Device pointer of a tensor (None or an empty tensor -> NULL)."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
+    if t.numel() == 0:
+        return None
     return t.data_ptr()
 
 
@@ -118,9 +143,15 @@ def colmajor(t):
 
 
 def ld(t):
-    if t.dim() != 2 or (t.stride(0) != 1 and t.shape[1] > 1 and t.shape[0] > 1):
+    """Leading dimension of a column-major matrix tensor."""
+    if t.dim() != 2:
+        raise MpirError("matrix must be 2-D")
+    rows, cols = t.shape
+    if rows == 0 or cols == 0:
+        return max(1, rows)
+    if t.stride(0) != 1 and rows > 1:
         raise MpirError("matrix must be column-major (stride(0) == 1)")
-    return max(1, t.stride(1) if t.shape[1] > 1 else t.shape[0])
+    return max(1, rows, t.stride(1) if cols > 1 else rows)
 
 
 def make_opts(fact="fp32", refine="classical", tol=0.0, maxit=0, escalate=True, **kw):

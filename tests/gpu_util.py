@@ -11,6 +11,8 @@ def dev(a):
     a = np.asarray(a, dtype=np.float64)
     if a.ndim == 1:
         return torch.from_numpy(a.copy()).cuda()
+    if a.size == 0:
+        return torch.zeros(a.shape, dtype=torch.float64, device="cuda")
     t = torch.from_numpy(np.ascontiguousarray(a.T)).cuda()   # (cols, rows) row-major
     return t.t()                                             # (rows, cols), stride (1, rows)
 
@@ -21,8 +23,7 @@ def host(t):
 
 def zeros(n):
     import torch
-    return torch.zeros(max(n, 1), dtype=torch.float64, device="cuda")[:n] if n else \
-        torch.zeros(1, dtype=torch.float64, device="cuda")
+    return torch.zeros(n, dtype=torch.float64, device="cuda")
 
 
 def rel(a, b):

@@ -29,8 +29,7 @@ def run_lse(h, P, fact="fp32", refine="classical", **kw):
     m, n = A.shape
     p = B.shape[0]
     x, r, v = zeros(n), zeros(m), zeros(p)
-    st, info = h.lse_solve(dev(A), dev(B) if p else zeros(1).reshape(1, 1), dev(b),
-                           dev(d) if p else zeros(1), x, r, v if p else None,
+    st, info = h.lse_solve(dev(A), dev(B), dev(b), dev(d), x, r, v if p else None,
                            mpir.make_opts(fact=fact, refine=refine, **kw))
     return st, info, host(x), host(r), host(v)[:p]
 
