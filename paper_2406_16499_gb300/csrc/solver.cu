@@ -574,7 +574,10 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
             const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
             if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
             else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
-            const double fmax = std::max(nr[0], std::max(nr[1], nr[2]));
+            // normalize the right-hand side of the scaled correction system
+            // (f1, sV f2, sW/sV f3), not the raw blocks
+            const double sW = h->fs.s1, sV = h->fs.s2;
+            const double fmax = std::max(nr[0], std::max(nr[1] * sV, nr[2] * sW / sV));
             const double gamma = pow2_norm(fmax);
             RC(gls_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, y, z, x));
         }
@@ -799,7 +802,10 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
             const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
             if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
             else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
-            const double gamma = pow2_norm(std::max(nr[0], std::max(nr[1], nr[2])));
+            // normalize the right-hand side of the scaled correction system
+            // (f1, sB/sA f2, sA f3), not the raw blocks
+            const double sA = h->fs.s1, sB = h->fs.s2;
+            const double gamma = pow2_norm(std::max(nr[0], std::max(nr[1] * sB / sA, nr[2] * sA)));
             RC(lse_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, r, v, x));
         }
         if (info) info->time_ms[2] = t_res;
