@@ -238,6 +238,18 @@ int mpir_lse_correction(mpir_handle h, const double *f1, const double *f2,
 int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
                         const double *f3, double *dy, double *dz, double *dx);
 
+/* Stage 2-4 building block (xLARFB with a 128-reflector block on the
+ * tensor cores): C <- (I - V X V^T) C with X = T^T (trans = 1) or T
+ * (trans = 0).  V: the unit lower trapezoid of the M x K panel at V (ldv;
+ * entries on and above the diagonal are ignored, the diagonal is taken as
+ * 1), T: K x K upper triangular, column-major with leading dimension 128,
+ * C: M x N (ldc a multiple of 4, C 16-byte aligned).  All FP32 device
+ * arrays, K <= 128.  prec: MPIR_FP32 (three TF32 products, FP32-class) or
+ * MPIR_TF32 (one TF32 product).  Returns 0, a negative argument index, or
+ * MPIR_UNSUPPORTED. */
+int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int ldv,
+               const float *T, int trans, float *C, int ldc);
+
 /* Library version string. */
 const char *mpir_version(void);
 
@@ -247,7 +259,8 @@ const char *mpir_version(void);
  * the launch stream; mpir_profile_read synchronizes on the last record and
  * returns, per kind, the summed event time (ms) and the number of timed
  * launches.  Kinds: 0 panel_qr, 1 larfb, 2 vec_apply, 3 trsv, 4 gemv,
- * 5 dual_gemv_fp64, 6 resid_finalize, 7 convert, 8 norm, 9 elementwise.
+ * 5 dual_gemv_fp64, 6 resid_finalize, 7 convert, 8 norm, 9 elementwise,
+ * 10 larfb_tc (tcgen05 GEMM), 11 larfb_aux (V / W preparation).
  * Not thread-safe; a profiling aid, off by default. */
 int mpir_profile(int enable);
 int mpir_profile_read(double *ms, long long *launches, int nkinds);

@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include "common.cuh"
+#include "gemm_tc.h"
 #include "kernels.h"
 #include "mpir.h"
 
@@ -36,9 +37,6 @@ constexpr int TC_TILE_A = TC_BM * TC_BK * 4;      // 16 KB
 constexpr int TC_TILE_B = TC_BN * TC_BK * 4;      // 16 KB
 constexpr int TC_THREADS = 192;
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
-
-enum { TCM_TF32 = 0, TCM_TF32X3 = 1 };
-enum { TCE_STORE = 0, TCE_SUB = 1 };
 
 // ------------------------------------------------------------------ PTX --
 
@@ -218,6 +216,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     auto tileB = [&](int s) { return smem + (size_t)s * STAGE_BYTES + NA * TC_TILE_A; };
     auto tileB2 = [&](int s) { return smem + (size_t)s * STAGE_BYTES + NA * TC_TILE_A + TC_TILE_B; };
 
+    int issued = 0;   // TMA stages issued by the producer (lane 0 of warp 0)
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
@@ -236,6 +235,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 tma_load_2d(smem_u32(tileB(s)), &tmB, args.b_x0 + kx, args.b_y0 + n_tile * TC_BN, fb);
                 if (b_two)
                     tma_load_2d(smem_u32(tileB2(s)), &tmB2, args.b_x0 + kx, args.b_y0 + n_tile * TC_BN, fb);
+                issued = i + 1;
             }
         }
     } else if (warp == 1) {
@@ -289,8 +289,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
         }
         // epilogue: warp q = warp % 4 owns TMEM lanes (rows) 32q .. 32q+31
-        const bool ok = nk > 0 && mbar_wait(smem_u32(&bar_accum), 0);
-        if (!ok && nk > 0) { atomicOr(args.err, 4); abort_s = 1; }
+        bool ok = nk > 0 && mbar_wait(smem_u32(&bar_accum), 0);
+        ok = __all_sync(0xffffffffu, ok);        // tcgen05.ld below is warp-collective
+        if (!ok && nk > 0 && lane == 0) { atomicOr(args.err, 4); abort_s = 1; }
         tc_fence_after();
         const int q = warp & 3;
         const int row = m_tile * TC_BM + 32 * q + lane;
@@ -314,7 +315,7 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     }
                 }
             }
-        } else if (EPI == TCE_STORE && nk == 0) {
+        } else if (EPI == TCE_STORE && nk <= 0) {
             // an empty split contributes zeros
             if (row < args.M)
                 for (int j = 0; j < TC_BN; j++) {
@@ -325,6 +326,12 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
     tc_fence_before();
     __syncthreads();
+    if (warp == 0 && lane == 0 && *(volatile int *)&abort_s) {
+        // after an abort, wait (bounded) for TMA copies still landing in the
+        // stages that were issued but never consumed
+        for (int i = issued > STAGES ? issued - STAGES : 0; i < issued; i++)
+            mbar_wait(smem_u32(&bar_full[i % STAGES]), (i / STAGES) & 1);
+    }
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)TC_BN)

@@ -9,7 +9,7 @@ namespace mpir {
 // Kernel kinds for the launch counter and the optional per-kind timers.
 enum KernelKind {
     K_PANEL = 0, K_LARFB, K_VEC_APPLY, K_TRSV, K_GEMV, K_DUAL_GEMV, K_FINALIZE, K_CONVERT, K_NORM,
-    K_ELEMWISE, K_NKINDS
+    K_ELEMWISE, K_LARFB_TC, K_LARFB_AUX, K_NKINDS
 };
 // Called around every kernel launch: counts the launch and, when timing is
 // enabled (mpir_profile), records a CUDA event pair on the launch stream.
@@ -25,6 +25,8 @@ struct ProfScope {
 enum class GemmPrec { FP32 = 0, TF32 = 1, BF16 = 2, FP64 = 3 };
 
 template <typename T> constexpr int panel_nb() { return sizeof(T) == 4 ? 32 : 16; }
+constexpr int OUTER_NB = 128;            // reflectors per outer (tensor-core) block
+__host__ __device__ inline int rup32(int x) { return (x + 31) & ~31; }
 
 struct DevScratch {          // small device scratch owned by the handle
     unsigned int *barrier;   // 2 words, zero between launches
@@ -39,16 +41,28 @@ struct DevScratch {          // small device scratch owned by the handle
 // A = Z T with Z = H_0 ... H_{k-1}, k = min(M, N).  Reflector vectors below
 // the diagonal, tau[k], and the compact-WY factor of every panel of
 // panel_nb<T>() reflectors in Tw (NB x NB column-major per panel, upper
-// triangular; H_j0 ... H_j0+nb-1 = I - V Tw V^T).  Returns 0, or
-// MPIR_UNSUPPORTED / MPIR_CUDA_ERROR.
+// triangular; H_j0 ... H_j0+nb-1 = I - V Tw V^T).  For FP32 storage the
+// factorization is two-level: 128-reflector outer blocks whose compact-WY
+// factors go to Tw128 (128 x 128 per block) and whose trailing updates run
+// on the tensor cores (gemm_tc.cu) at `prec`.  lda must be a multiple of 4
+// (16-byte rows for TMA).  ws: geqrf_ws_bytes() of scratch.
+// Returns 0, or MPIR_UNSUPPORTED / MPIR_CUDA_ERROR.
+size_t geqrf_ws_bytes(int M, int N);
 template <typename T>
-int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, GemmPrec prec, cudaStream_t s);
+int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, T *Tw128, GemmPrec prec, void *ws, int *err,
+          cudaStream_t s);
 
 // C (M x Nc, ldc) <- Z^T C (trans = 1) or Z C (trans = 0) for the reflector
-// set left in (V, ldv, K reflectors, Tw) by geqrf on an M-row matrix.
+// set left in (V, ldv, K reflectors, Tw, Tw128) by geqrf on an M-row matrix.
 template <typename T>
-int apply_reflectors_left(const T *V, int ldv, int M, int K, const T *Tw, int trans,
-                          T *C, int ldc, int Nc, GemmPrec prec, cudaStream_t s);
+int apply_reflectors_left(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, int trans,
+                          T *C, int ldc, int Nc, GemmPrec prec, void *ws, int *err, cudaStream_t s);
+
+// C (M x N, ldc) <- (I - V X V^T) C, X = Tb^T (trans) or Tb (K x K upper
+// triangular, ld 128), V = unit lower trapezoid of the M x K panel V (ldv),
+// K <= 128, on the tensor cores.  ws: geqrf_ws_bytes(M, N).
+int larfb_tc(const float *V, int ldv, int M, int K, const float *Tb, int trans, float *C, int ldc, int N,
+             GemmPrec prec, void *ws, int *err, cudaStream_t s);
 
 // ---- vectors (vec.cu) -------------------------------------------------
 // x (length M) <- Z^T x (trans = 1) or Z x (trans = 0), cooperative launch.

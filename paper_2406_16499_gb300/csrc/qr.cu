@@ -5,6 +5,7 @@
 // (the host driver forms that copy), so every reflector is a column of a
 // column-major matrix and every access below is coalesced.
 #include "common.cuh"
+#include "gemm_tc.h"
 #include "kernels.h"
 #include "mpir.h"
 
@@ -288,6 +289,257 @@ k_larfb_left(const T *__restrict__ V, int ldv, const T *__restrict__ Tw, int kb,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Row-parallel inner update (within a 128-wide outer block): the trailing
+// columns of the outer block are few (<= 96) but the panel is tall, so the
+// work is split over row chunks:
+//   k_inner_w      P[chunk] = V_chunk^T C_chunk             (32 x nc)
+//   k_inner_reduce W = Tw^T sum_chunk P[chunk]
+//   k_inner_update C_chunk -= V_chunk W
+// V is the unit lower trapezoid stored in the panel columns.
+// ---------------------------------------------------------------------------
+constexpr int INNER_ROWS = 256;
+constexpr int INNER_MAXC = 96;
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_inner_w(const T *__restrict__ V, int ldv, int kb, int L, const T *__restrict__ C, int ldc, int nc,
+          T *__restrict__ P)
+{
+    __shared__ T Vs[32][NB + 1];
+    __shared__ T Cs[32][INNER_MAXC + 1];
+    const int tid = threadIdx.x;
+    const int r0 = blockIdx.x * INNER_ROWS;
+    // thread owns outputs (i, c) with i = tid % NB, c = tid / NB + 256/NB * s
+    constexpr int CSTEP = 256 / NB;
+    constexpr int NOUT = (INNER_MAXC + CSTEP - 1) / CSTEP;
+    T acc[NOUT];
+#pragma unroll
+    for (int s = 0; s < NOUT; s++) acc[s] = T(0);
+    const int i = tid % NB, cb = tid / NB;
+    for (int rr = 0; rr < INNER_ROWS; rr += 32) {
+        for (int e = tid; e < 32 * NB; e += 256) {
+            const int r = e % 32, c = e / 32, gr = r0 + rr + r;
+            T v = T(0);
+            if (gr < L && c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? T(1) : T(0));
+            Vs[r][c] = v;
+        }
+        for (int e = tid; e < 32 * nc; e += 256) {
+            const int r = e % 32, c = e / 32, gr = r0 + rr + r;
+            Cs[r][c] = gr < L ? C[idx2(gr, c, ldc)] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < 32; r++) {
+            const T v = Vs[r][i];
+#pragma unroll
+            for (int s = 0; s < NOUT; s++) {
+                const int c = cb + CSTEP * s;
+                if (c < nc) acc[s] = fma(v, Cs[r][c], acc[s]);
+            }
+        }
+        __syncthreads();
+    }
+    T *Pc = P + (size_t)blockIdx.x * NB * INNER_MAXC;
+#pragma unroll
+    for (int s = 0; s < NOUT; s++) {
+        const int c = cb + CSTEP * s;
+        if (c < nc) Pc[i + c * NB] = acc[s];
+    }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_inner_reduce(const T *__restrict__ P, int nchunks, const T *__restrict__ Tw, int nc, int trans,
+               T *__restrict__ W)
+{
+    __shared__ T S[NB][INNER_MAXC + 1];
+    __shared__ T X[NB][NB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * nc; e += 256) {
+        const int i = e % NB, c = e / NB;
+        T s = T(0);
+        for (int k = 0; k < nchunks; k++) s += P[(size_t)k * NB * INNER_MAXC + i + c * NB];
+        S[i][c] = s;
+    }
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int i = e % NB, k = e / NB;
+        const T t = Tw[i + k * NB];
+        if (trans) X[k][i] = t; else X[i][k] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * nc; e += 256) {
+        const int i = e % NB, c = e / NB;
+        T s = T(0);
+        for (int k = 0; k < NB; k++) s = fma(X[i][k], S[k][c], s);
+        W[i + c * NB] = s;
+    }
+}
+
+template <typename T, int NB>
+__global__ void __launch_bounds__(256)
+k_inner_update(const T *__restrict__ V, int ldv, int kb, int L, T *__restrict__ C, int ldc, int nc,
+               const T *__restrict__ W)
+{
+    __shared__ T Ws[NB][INNER_MAXC + 1];
+    __shared__ T Vs[32][NB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < NB * nc; e += 256) Ws[e % NB][e / NB] = W[e];
+    const int r0 = blockIdx.x * INNER_ROWS;
+    const int lr = tid & 31, cg0 = tid >> 5;     // 8 column groups
+    for (int rr = 0; rr < INNER_ROWS; rr += 32) {
+        __syncthreads();
+        for (int e = tid; e < 32 * NB; e += 256) {
+            const int r = e % 32, c = e / 32, gr = r0 + rr + r;
+            T v = T(0);
+            if (gr < L && c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? T(1) : T(0));
+            Vs[r][c] = v;
+        }
+        __syncthreads();
+        const int gr = r0 + rr + lr;
+        if (gr < L) {
+            for (int c = cg0; c < nc; c += 8) {
+                T t = T(0);
+#pragma unroll 8
+                for (int k = 0; k < NB; k++) t = fma(Vs[lr][k], Ws[k][c], t);
+                C[idx2(gr, c, ldc)] -= t;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Outer (128-reflector) blocks, FP32 storage.
+//
+// k_prep_v: the unit lower trapezoid V of an outer block (rows j0.., columns
+// j0..j0+nr) in the layouts the tensor-core GEMMs read:
+//   V, Vlo   L x 128 column-major (ld ldv)  -- A operand of W = V^T C
+//   Vt, Vtlo 128 x L column-major (ld 128)  -- A operand of C -= V W
+// with V = Vhi + Vlo, Vhi = TF32(V) when split (TF32X3), else V raw.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_prep_v(const float *__restrict__ X, int ldx, int L, int nr, float *__restrict__ Vh, float *__restrict__ Vl,
+         int ldv, float *__restrict__ Vth, float *__restrict__ Vtl, int split)
+{
+    __shared__ float tile[32][OUTER_NB + 1];
+    const int r0 = blockIdx.x * 32;
+    const int tid = threadIdx.x;
+    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
+        const int r = e % 32, c = e / 32, gr = r0 + r;
+        float v = 0.f;
+        if (gr < L && c < nr) v = gr > c ? X[idx2(gr, c, ldx)] : (gr == c ? 1.f : 0.f);
+        tile[r][c] = v;
+    }
+    __syncthreads();
+    // V / Vlo: column-major, coalesced along rows
+    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
+        const int r = e % 32, c = e / 32, gr = r0 + r;
+        if (gr < ldv) {
+            const float v = tile[r][c];
+            float h = v;
+            if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v)); h = __uint_as_float(u); }
+            Vh[idx2(gr, c, ldv)] = h;
+            if (split) Vl[idx2(gr, c, ldv)] = v - h;
+        }
+    }
+    // Vt / Vtlo: 128 x L, coalesced along the 128 columns of V
+    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
+        const int c = e % OUTER_NB, r = e / OUTER_NB, gr = r0 + r;
+        if (gr < ldv) {
+            const float v = tile[r][c];
+            float h = v;
+            if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v)); h = __uint_as_float(u); }
+            Vth[idx2(c, gr, OUTER_NB)] = h;
+            if (split) Vtl[idx2(c, gr, OUTER_NB)] = v - h;
+        }
+    }
+}
+
+// W = op(Tb) * sum_z P[z] (128 x nc), op = Tb^T (trans), Tb, or identity
+// (Tb == NULL); optionally split into W = Wh + Wl.  One block per 32 columns.
+__global__ void __launch_bounds__(256)
+k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, const float *__restrict__ Tb,
+           int trans, int nc, float *__restrict__ Wh, float *__restrict__ Wl, int ldw, int split)
+{
+    extern __shared__ float sm[];
+    float *S = sm;                                   // [32 cols][128] (column-major 128 x 32)
+    float *Xs = sm + 32 * OUTER_NB;                  // 128 x 128 column-major (x(i,k) at i + 128 k)
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * 32;
+    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
+        const int i = e % OUTER_NB, c = e / OUTER_NB;
+        float s = 0.f;
+        if (c0 + c < nc)
+            for (int z = 0; z < nsplit; z++) s += P[(size_t)z * pstride + (size_t)(c0 + c) * ldp + i];
+        S[i + c * OUTER_NB] = s;
+    }
+    if (Tb) {
+        for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) {
+            const int i = e % OUTER_NB, k = e / OUTER_NB;
+            const float t = Tb[i + k * OUTER_NB];
+            if (trans) Xs[k + i * OUTER_NB] = t; else Xs[i + k * OUTER_NB] = t;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
+        const int i = e % OUTER_NB, c = e / OUTER_NB;
+        if (c0 + c >= nc) continue;
+        float w;
+        if (Tb) {
+            float s = 0.f;
+            for (int k = 0; k < OUTER_NB; k++) s = fmaf(Xs[i + k * OUTER_NB], S[k + c * OUTER_NB], s);
+            w = s;
+        } else {
+            w = S[i + c * OUTER_NB];
+        }
+        float h = w;
+        if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(w)); h = __uint_as_float(u); }
+        Wh[(size_t)(c0 + c) * ldw + i] = h;
+        if (split) Wl[(size_t)(c0 + c) * ldw + i] = w - h;
+    }
+}
+
+// Compact-WY factor of an outer block from its four 32-wide inner factors
+// and the Gram matrix G = V^T V (Tw^{-1} = triu(G, 1) + diag(1/tau)):
+//   T(0:32j, 32j:32j+32) = -T(0:32j, 0:32j) G(0:32j, 32j:32j+32) T_j.
+__global__ void __launch_bounds__(256)
+k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, float *__restrict__ Tb)
+{
+    extern __shared__ float sm[];
+    float *Ts = sm;                                  // 128 x 128 column-major
+    float *Pm = sm + OUTER_NB * OUTER_NB;            // 96 x 32 scratch
+    const int tid = threadIdx.x;
+    for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) Ts[e] = 0.f;
+    __syncthreads();
+    const int nblk = ceil_div(nr, 32);
+    for (int b = 0; b < nblk; b++)
+        for (int e = tid; e < 32 * 32; e += 256) {
+            const int i = e % 32, k = e / 32;
+            Ts[(32 * b + i) + (32 * b + k) * OUTER_NB] = Tw32[(size_t)b * 1024 + i + k * 32];
+        }
+    __syncthreads();
+    for (int j = 1; j < nblk; j++) {
+        const int h = 32 * j;
+        // Pm = G(0:h, h:h+32) * T_j
+        for (int e = tid; e < h * 32; e += 256) {
+            const int i = e % h, c = e / h;
+            float s = 0.f;
+            for (int k = 0; k < 32; k++) s = fmaf(G[i + (h + k) * OUTER_NB], Ts[(h + k) + (h + c) * OUTER_NB], s);
+            Pm[i + c * 96] = s;
+        }
+        __syncthreads();
+        // T(0:h, h:h+32) = -T(0:h, 0:h) * Pm   (T upper triangular)
+        for (int e = tid; e < h * 32; e += 256) {
+            const int i = e % h, c = e / h;
+            float s = 0.f;
+            for (int k = i; k < h; k++) s = fmaf(Ts[i + k * OUTER_NB], Pm[k + c * 96], s);
+            Ts[i + (h + c) * OUTER_NB] = -s;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) Tb[e] = Ts[e];
+}
+
 // ------------------------------------------------------------------ host --
 
 template <typename T>
@@ -324,7 +576,7 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
 
 template <typename T>
 static int launch_larfb(const T *V, int ldv, const T *Tw, int kb, int L, T *C, int ldc, int Nc,
-                        int trans, GemmPrec, cudaStream_t s)
+                        int trans, cudaStream_t s)
 {
     constexpr int NB = panel_nb<T>();
     if (Nc <= 0 || L <= 0 || kb <= 0) return 0;
@@ -333,8 +585,150 @@ static int launch_larfb(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+// Inner update of nc (<= 96) columns: three row-parallel kernels.
 template <typename T>
-int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, GemmPrec prec, cudaStream_t s)
+static int inner_update(const T *V, int ldv, const T *Tw, int kb, int L, T *C, int ldc, int nc, T *P, T *W,
+                        cudaStream_t s)
+{
+    constexpr int NB = panel_nb<T>();
+    if (nc <= 0 || L <= 0 || kb <= 0) return 0;
+    if (nc > INNER_MAXC) return launch_larfb<T>(V, ldv, Tw, kb, L, C, ldc, nc, 1, s);
+    const int nch = ceil_div(L, INNER_ROWS);
+    ProfScope ps(K_LARFB, s);
+    k_inner_w<T, NB><<<nch, 256, 0, s>>>(V, ldv, kb, L, C, ldc, nc, P);
+    k_inner_reduce<T, NB><<<1, 256, 0, s>>>(P, nch, Tw, nc, 1, W);
+    k_inner_update<T, NB><<<nch, 256, 0, s>>>(V, ldv, kb, L, C, ldc, nc, W);
+    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// Scratch of the two-level factorization (FP32 path).
+struct OuterWs {
+    float *V, *Vl, *Vt, *Vtl, *P, *W, *Wl, *G, *innerP, *innerW;
+    int ldv;
+    size_t pcap;
+};
+
+static constexpr int PSPLIT_CAP = 320;   // (column tiles x K splits) of W = V^T C
+
+static OuterWs outer_layout(void *base, int M, int N, size_t *bytes)
+{
+    uintptr_t b = (uintptr_t)base, off = 0;
+    auto take = [&](size_t n) { off = (off + 1023) & ~(uintptr_t)1023; float *p = (float *)(b + off); off += n * 4; return p; };
+    OuterWs w{};
+    w.ldv = rup32(M > 0 ? M : 1);
+    const size_t ncp = (size_t)rup32(N > 0 ? N : 1);
+    w.V = take((size_t)w.ldv * OUTER_NB);
+    w.Vl = take((size_t)w.ldv * OUTER_NB);
+    w.Vt = take((size_t)OUTER_NB * w.ldv);
+    w.Vtl = take((size_t)OUTER_NB * w.ldv);
+    w.pcap = (size_t)OUTER_NB * OUTER_NB * PSPLIT_CAP;
+    const size_t ncp128 = (size_t)ceil_div(N > 0 ? N : 1, OUTER_NB) * OUTER_NB;
+    if (w.pcap < (size_t)OUTER_NB * ncp128) w.pcap = (size_t)OUTER_NB * ncp128;
+    w.P = take(w.pcap);
+    w.W = take((size_t)OUTER_NB * ncp);
+    w.Wl = take((size_t)OUTER_NB * ncp);
+    w.G = take((size_t)OUTER_NB * OUTER_NB);
+    w.innerP = take((size_t)ceil_div(M > 0 ? M : 1, INNER_ROWS) * 32 * INNER_MAXC * 2);
+    w.innerW = take((size_t)32 * INNER_MAXC * 2);
+    if (bytes) *bytes = (size_t)((off + 1023) & ~(uintptr_t)1023);
+    return w;
+}
+
+size_t geqrf_ws_bytes(int M, int N)
+{
+    size_t b = 0;
+    outer_layout(nullptr, M, N, &b);
+    return b;
+}
+
+static int tc_mode(GemmPrec p) { return p == GemmPrec::FP32 ? TCM_TF32X3 : TCM_TF32; }
+
+// Prepares V (and splits) for the outer block whose panel sits at X (ldx),
+// height L, nr reflectors.
+static void prep_v(const float *X, int ldx, int L, int nr, OuterWs &w, int split, cudaStream_t s)
+{
+    ProfScope ps(K_LARFB_AUX, s);
+    k_prep_v<<<ceil_div(w.ldv, 32), 256, 0, s>>>(X, ldx, L, nr, w.V, w.Vl, w.ldv, w.Vt, w.Vtl, split);
+}
+
+// C (L x Nc, ldc) <- (I - V X V^T) C for the prepared outer block, X = Tb^T
+// (trans) or Tb, on the tensor cores:  P = V^T C (split-K),  W = X sum P,
+// C -= V W.
+static int outer_apply(OuterWs &w, const float *Tb, int trans, int L, float *C, int ldc, int Nc, int mode,
+                       int *err, cudaStream_t s)
+{
+    if (Nc <= 0 || L <= 0) return 0;
+    const int split = mode == TCM_TF32X3;
+    CUtensorMap tV, tVl, tC, tVt, tVtl, tW, tWl;
+    int rc = 0;
+    rc |= tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
+    rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
+    rc |= tmap_colmajor(&tC, C, L, Nc, ldc, OUTER_NB);
+    rc |= tmap_colmajor(&tVt, w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
+    rc |= tmap_colmajor(&tVtl, split ? w.Vtl : w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
+    rc |= tmap_colmajor(&tW, w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
+    rc |= tmap_colmajor(&tWl, split ? w.Wl : w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
+    if (rc) return MPIR_UNSUPPORTED;
+    const int ntn = ceil_div(Nc, OUTER_NB);
+    const int ksteps = ceil_div(L, 32);
+    int nsplit = ceil_div(2 * 152, ntn);
+    if (nsplit > PSPLIT_CAP / ntn) nsplit = PSPLIT_CAP / ntn;
+    if (nsplit > ksteps) nsplit = ksteps;
+    if (nsplit < 1) nsplit = 1;
+    if ((size_t)nsplit * OUTER_NB * ntn * OUTER_NB > w.pcap) nsplit = 1;
+    const size_t pstride = (size_t)OUTER_NB * ntn * OUTER_NB;
+    // P[z] = V^T C  (M = 128 rows of V^T, N = Nc, K = L)
+    rc = gemm_tc(mode, split, TCE_STORE, tV, tVl, tC, tC, 0, 0, 0, 0, OUTER_NB, Nc, L, w.P, OUTER_NB, pstride,
+                 nsplit, err, s);
+    if (rc) return rc;
+    {
+        ProfScope ps(K_LARFB_AUX, s);
+        const size_t smem = (size_t)(32 + OUTER_NB) * OUTER_NB * 4;
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_reduce_w<<<ceil_div(Nc, 32), 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, Tb, trans, Nc, w.W, w.Wl,
+                                                        OUTER_NB, split);
+    }
+    // C -= V W  (M = L, N = Nc, K = 128)
+    rc = gemm_tc(mode, 0, TCE_SUB, tVt, tVtl, tW, tWl, 0, 0, 0, 0, L, Nc, OUTER_NB, C, ldc, 0, 1, err, s);
+    return rc ? rc : (cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR);
+}
+
+// G = V^T V of the prepared block, then the outer compact-WY factor Tb.
+static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int mode, int *err, cudaStream_t s)
+{
+    const int split = mode == TCM_TF32X3;
+    CUtensorMap tV, tVl;
+    int rc = tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
+    rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
+    if (rc) return MPIR_UNSUPPORTED;
+    const int ksteps = ceil_div(L, 32);
+    int nsplit = ksteps < 64 ? ksteps : 64;
+    if (nsplit < 1) nsplit = 1;
+    const size_t pstride = (size_t)OUTER_NB * OUTER_NB;
+    // G = V^T V with both operands pre-split (w.V holds only the TF32 part)
+    rc = gemm_tc(mode, 0, TCE_STORE, tV, tVl, tV, tVl, 0, 0, 0, 0, OUTER_NB, OUTER_NB, L, w.P, OUTER_NB,
+                 pstride, nsplit, err, s);
+    if (rc) return rc;
+    ProfScope ps(K_LARFB_AUX, s);
+    {
+        const size_t smem = (size_t)(32 + OUTER_NB) * OUTER_NB * 4;
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_reduce_w<<<OUTER_NB / 32, 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, nullptr, 0, OUTER_NB, w.G,
+                                                     w.G, OUTER_NB, 0);
+    }
+    {
+        const size_t smem = (size_t)(OUTER_NB * OUTER_NB + 96 * 32) * 4;
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_outer_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_outer_T<<<1, 256, smem, s>>>(Tw32, w.G, nr, Tb);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+template <typename T>
+static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, cudaStream_t s)
 {
     constexpr int NB = panel_nb<T>();
     const int k = M < N ? M : N;
@@ -347,36 +741,113 @@ int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, GemmPrec prec, cudaStream_
         const int kb = ncols < L ? ncols : L;
         const int Nc = N - j0 - ncols;
         if (Nc > 0) {
-            rc = launch_larfb<T>(A + idx2(j0, j0, lda), lda, Twb, kb, L, A + idx2(j0, j0 + ncols, lda),
-                                 lda, Nc, 1, prec, s);
+            rc = launch_larfb<T>(A + idx2(j0, j0, lda), lda, Twb, kb, L, A + idx2(j0, j0 + ncols, lda), lda, Nc,
+                                 1, s);
             if (rc) return rc;
         }
     }
     return 0;
 }
 
-template <typename T>
-int apply_reflectors_left(const T *V, int ldv, int M, int K, const T *Tw, int trans, T *C, int ldc,
-                          int Nc, GemmPrec prec, cudaStream_t s)
+template <>
+int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *, int *,
+                  cudaStream_t s)
 {
-    constexpr int NB = panel_nb<T>();
+    return geqrf_simt<double>(A, lda, M, N, tau, Tw, s);
+}
+
+// Two-level QR, FP32 storage: 32-wide register panels inside 128-wide
+// outer blocks; inner updates row-parallel SIMT, outer trailing updates on
+// the tensor cores.
+template <>
+int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *Tw128, GemmPrec prec, void *ws,
+                 int *err, cudaStream_t s)
+{
+    constexpr int NB = 32;
+    const int k = M < N ? M : N;
+    if (lda % 4) return MPIR_UNSUPPORTED;
+    OuterWs w = outer_layout(ws, M, N, nullptr);
+    const int mode = tc_mode(prec);
+    for (int J0 = 0; J0 < k; J0 += OUTER_NB) {
+        const int ncolsO = N - J0 < OUTER_NB ? N - J0 : OUTER_NB;
+        const int L = M - J0;
+        const int nr = ncolsO < L ? ncolsO : L;
+        for (int j0 = J0; j0 < J0 + nr; j0 += NB) {
+            const int ncols = J0 + ncolsO - j0 < NB ? J0 + ncolsO - j0 : NB;
+            const int Li = M - j0;
+            float *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
+            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, s);
+            if (rc) return rc;
+            const int kb = ncols < Li ? ncols : Li;
+            const int nc = J0 + ncolsO - j0 - ncols;
+            if (nc > 0) {
+                rc = inner_update<float>(A + idx2(j0, j0, lda), lda, Twb, kb, Li, A + idx2(j0, j0 + ncols, lda), lda,
+                                         nc, w.innerP, w.innerW, s);
+                if (rc) return rc;
+            }
+        }
+        const int Nc = N - J0 - ncolsO;
+        float *Tb = Tw128 + (size_t)(J0 / OUTER_NB) * OUTER_NB * OUTER_NB;
+        prep_v(A + idx2(J0, J0, lda), lda, L, nr, w, mode == TCM_TF32X3, s);
+        int rc = outer_T(w, Tw + (size_t)(J0 / NB) * NB * NB, L, nr, Tb, mode, err, s);
+        if (rc) return rc;
+        if (Nc > 0) {
+            rc = outer_apply(w, Tb, 1, L, A + idx2(J0, J0 + ncolsO, lda), lda, Nc, mode, err, s);
+            if (rc) return rc;
+        }
+    }
+    return 0;
+}
+
+template <>
+int apply_reflectors_left<double>(const double *V, int ldv, int M, int K, const double *Tw, const double *,
+                                  int trans, double *C, int ldc, int Nc, GemmPrec, void *, int *, cudaStream_t s)
+{
+    constexpr int NB = panel_nb<double>();
     const int nblk = ceil_div(K, NB);
     for (int t = 0; t < nblk; t++) {
         const int b = trans ? t : nblk - 1 - t;
         const int j0 = b * NB;
         const int kb = K - j0 < NB ? K - j0 : NB;
-        int rc = launch_larfb<T>(V + idx2(j0, j0, ldv), ldv, Tw + (size_t)b * NB * NB, kb, M - j0,
-                                 C + j0, ldc, Nc, trans, prec, s);
+        int rc = launch_larfb<double>(V + idx2(j0, j0, ldv), ldv, Tw + (size_t)b * NB * NB, kb, M - j0, C + j0, ldc,
+                                      Nc, trans, s);
         if (rc) return rc;
     }
     return 0;
 }
 
-template int geqrf<float>(float *, int, int, int, float *, float *, GemmPrec, cudaStream_t);
-template int geqrf<double>(double *, int, int, int, double *, double *, GemmPrec, cudaStream_t);
-template int apply_reflectors_left<float>(const float *, int, int, int, const float *, int, float *,
-                                          int, int, GemmPrec, cudaStream_t);
-template int apply_reflectors_left<double>(const double *, int, int, int, const double *, int,
-                                           double *, int, int, GemmPrec, cudaStream_t);
+template <>
+int apply_reflectors_left<float>(const float *V, int ldv, int M, int K, const float *, const float *Tw128,
+                                 int trans, float *C, int ldc, int Nc, GemmPrec prec, void *ws, int *err,
+                                 cudaStream_t s)
+{
+    if (ldc % 4 || ldv % 4) return MPIR_UNSUPPORTED;
+    OuterWs w = outer_layout(ws, M, Nc, nullptr);
+    const int mode = tc_mode(prec);
+    const int nblk = ceil_div(K, OUTER_NB);
+    for (int t = 0; t < nblk; t++) {
+        const int b = trans ? t : nblk - 1 - t;
+        const int J0 = b * OUTER_NB;
+        const int nr = K - J0 < OUTER_NB ? K - J0 : OUTER_NB;
+        const int L = M - J0;
+        prep_v(V + idx2(J0, J0, ldv), ldv, L, nr, w, mode == TCM_TF32X3, s);
+        int rc = outer_apply(w, Tw128 + (size_t)b * OUTER_NB * OUTER_NB, trans, L, C + J0, ldc, Nc, mode, err, s);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+// One block reflector with an explicit compact-WY factor (K <= 128).
+int larfb_tc(const float *V, int ldv, int M, int K, const float *Tb, int trans, float *C, int ldc, int N,
+             GemmPrec prec, void *ws, int *err, cudaStream_t s)
+{
+    if (K > OUTER_NB || K < 0) return MPIR_UNSUPPORTED;
+    if (ldc % 4 || ((uintptr_t)C & 15)) return MPIR_UNSUPPORTED;
+    if (K == 0 || M == 0 || N == 0) return 0;
+    OuterWs w = outer_layout(ws, M, N, nullptr);
+    const int mode = tc_mode(prec);
+    prep_v(V, ldv, M, K, w, mode == TCM_TF32X3, s);
+    return outer_apply(w, Tb, trans, M, C, ldc, N, mode, err, s);
+}
 
 } // namespace mpir

@@ -75,7 +75,7 @@ void prof_end(int kind, cudaStream_t s)
 
 static const char *g_kind_names[K_NKINDS] = {"panel_qr", "larfb", "vec_apply", "trsv", "gemv",
                                              "dual_gemv_fp64", "resid_finalize", "convert", "norm",
-                                             "elementwise"};
+                                             "elementwise", "larfb_tc", "larfb_aux"};
 
 #define MPIR_VERSION_STRING "libmpir 0.1 (sm_103a)"
 
@@ -100,7 +100,9 @@ struct Carver {
 
 template <typename T> struct LseWs {
     int m, n, p, q, kA;
-    T *Bt, *tauB, *TwB, *X, *At, *tauA, *TwA;
+    int ldBt, ldX, ldAt;                 // padded to 32 (TMA rows of 128 bytes)
+    T *Bt, *tauB, *TwB, *X, *At, *tauA, *TwA, *Tw128B, *Tw128A;
+    void *gws;                           // scratch of the two-level factorization
     T *tu, *tw, *ty, *tq, *tb, *tt, *tt2;
     double *f1, *f2, *f3, *r, *v, *pAx, *pAtr, *pBx, *pBtv, *normpart, *norms2, *scal, *part;
     DualGemvPlan pa, pb;
@@ -108,7 +110,9 @@ template <typename T> struct LseWs {
 
 template <typename T> struct GlsWs {
     int n, m, p, L, o, kC;
-    T *Wf, *tauW, *TwW, *Cf, *Ct, *tauC, *TwC;
+    int ldW, ldC, ldCt;                  // padded to 32 (TMA rows of 128 bytes)
+    T *Wf, *tauW, *TwW, *Cf, *Ct, *tauC, *TwC, *Tw128W, *Tw128C;
+    void *gws;                           // scratch of the two-level factorization
     T *tu, *tw, *th, *tg, *tt, *tt2;
     double *f1, *f2, *f3, *z, *pWx, *pWtz, *pVy, *pVtz, *normpart, *norms2, *scal, *part;
     DualGemvPlan pw, pv;
@@ -121,13 +125,18 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
     LseWs<T> w{};
     w.m = m; w.n = n; w.p = p; w.q = n - p; w.kA = std::min(m, n);
     const int mx = std::max(std::max(m, n), std::max(p, 1));
-    w.Bt = c.take<T>((size_t)n * std::max(p, 1));
+    w.ldBt = rup32(std::max(n, 1)); w.ldX = rup32(std::max(n, 1)); w.ldAt = rup32(std::max(m, 1));
+    w.Bt = c.take<T>((size_t)w.ldBt * std::max(p, 1));
     w.tauB = c.take<T>(std::max(p, 1));
     w.TwB = c.take<T>((size_t)std::max(ceil_div(p, NB), 1) * NB * NB);
-    w.X = c.take<T>((size_t)n * m);
-    w.At = c.take<T>((size_t)m * n);
+    w.Tw128B = c.take<T>((size_t)std::max(ceil_div(p, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
+    w.X = c.take<T>((size_t)w.ldX * std::max(m, 1));
+    w.At = c.take<T>((size_t)w.ldAt * n);
     w.tauA = c.take<T>(std::max(w.kA, 1));
     w.TwA = c.take<T>((size_t)std::max(ceil_div(w.kA, NB), 1) * NB * NB);
+    w.Tw128A = c.take<T>((size_t)std::max(ceil_div(w.kA, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
+    w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
+                                           geqrf_ws_bytes(m, n)));
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.ty = c.take<T>(mx); w.tq = c.take<T>(mx);
     w.tb = c.take<T>(mx); w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
     w.pa = dual_gemv_plan(m, n);
@@ -153,13 +162,18 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
     GlsWs<T> w{};
     w.n = n; w.m = m; w.p = p; w.L = n - m; w.o = p - n + m; w.kC = std::min(n, p);
     const int mx = std::max(std::max(m, n), std::max(p, 1));
-    w.Wf = c.take<T>((size_t)n * std::max(m, 1));
+    w.ldW = rup32(n); w.ldC = rup32(n); w.ldCt = rup32(std::max(p, 1));
+    w.Wf = c.take<T>((size_t)w.ldW * std::max(m, 1));
     w.tauW = c.take<T>(std::max(m, 1));
     w.TwW = c.take<T>((size_t)std::max(ceil_div(m, NB), 1) * NB * NB);
-    w.Cf = c.take<T>((size_t)n * p);
-    w.Ct = c.take<T>((size_t)p * n);
+    w.Tw128W = c.take<T>((size_t)std::max(ceil_div(m, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
+    w.Cf = c.take<T>((size_t)w.ldC * std::max(p, 1));
+    w.Ct = c.take<T>((size_t)w.ldCt * n);
     w.tauC = c.take<T>(std::max(w.kC, 1));
     w.TwC = c.take<T>((size_t)std::max(ceil_div(w.kC, NB), 1) * NB * NB);
+    w.Tw128C = c.take<T>((size_t)std::max(ceil_div(w.kC, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
+    w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
+                                           geqrf_ws_bytes(p, n)));
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.th = c.take<T>(mx); w.tg = c.take<T>(mx);
     w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
     w.pw = dual_gemv_plan(n, m);
@@ -293,6 +307,7 @@ int check_dev_flags(mpir_ctx *h)
     cudaMemcpyAsync(&flags[1], h->sc.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_check(h, "sync");
     if (flags[0] & DEV_ERR_BARRIER_TIMEOUT) return set_err(h, MPIR_DEVICE_TIMEOUT, "device barrier timed out");
+    if (flags[0] & 4) return set_err(h, MPIR_DEVICE_TIMEOUT, "tensor-core pipeline wait timed out");
     if (flags[1] & 1) return set_err(h, MPIR_SINGULAR_R, "R has a zero diagonal entry");
     if (flags[1] & 2) return set_err(h, MPIR_SINGULAR_T, "triangular factor has a zero diagonal entry");
     return 0;
@@ -368,14 +383,14 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     h->fs.fro2 = std::sqrt(h->hbuf[3]);
     const GemmPrec gp = gemm_prec(fact);
     // QR of W (Lemma 4.6, first factorization)
-    mconvert<double, T>(W, ldw, w.Wf, n, n, m, 0, 0, 0, sW, s);
-    RC(geqrf<T>(w.Wf, n, n, m, w.tauW, w.TwW, gp, s));
+    mconvert<double, T>(W, ldw, w.Wf, w.ldW, n, m, 0, 0, 0, sW, s);
+    RC(geqrf<T>(w.Wf, w.ldW, n, m, w.tauW, w.TwW, w.Tw128W, gp, w.gws, h->sc.err, s));
     // C = Q^T V
-    mconvert<double, T>(V, ldv, w.Cf, n, n, p, 0, 0, 0, sV, s);
-    RC(apply_reflectors_left<T>(w.Wf, n, n, m, w.TwW, 1, w.Cf, n, p, gp, s));
+    mconvert<double, T>(V, ldv, w.Cf, w.ldC, n, p, 0, 0, 0, sV, s);
+    RC(apply_reflectors_left<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.Cf, w.ldC, p, gp, w.gws, h->sc.err, s));
     // RQ of C as QR of C~ = P_p C^T P_n
-    mconvert<T, T>(w.Cf, n, w.Ct, p, p, n, 1, 1, 1, 1.0, s);
-    RC(geqrf<T>(w.Ct, p, p, n, w.tauC, w.TwC, gp, s));
+    mconvert<T, T>(w.Cf, w.ldC, w.Ct, w.ldCt, p, n, 1, 1, 1, 1.0, s);
+    RC(geqrf<T>(w.Ct, w.ldCt, p, n, w.tauC, w.TwC, w.Tw128C, gp, w.gws, h->sc.err, s));
     return cuda_check(h, "gls_factor");
 }
 
@@ -391,18 +406,18 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     double *g = w.scal + 8;
     pow2_normalizer(d, n, 1.0, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(d, w.tu, n, 1.0, 0, s, g);
-    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 1, w.tu, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 1, w.tu, h->sc, s));
     // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
     vzero(w.tg, sizeof(T) * p, s);
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
-    RC(trsv_upper<T>(w.Ct, p, L, 1, w.tg, h->sc, s));
+    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s));
     // R x = c1 - T12 s2,  P_m (T12 s2) = T~_12^T s~2
-    RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 1, T(1), w.tg, T(0), w.tt, 0, 0, s));
+    RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 1, T(1), w.tg, T(0), w.tt, 0, 0, s));
     vcomb<T>(w.tt2, m, w.tu, 0, T(1), w.tt, 1, T(-1), s);
-    RC(trsv_upper<T>(w.Wf, n, m, 0, w.tt2, h->sc, s));
+    RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s));
     vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s, g + 1);
     // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
-    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
     vcopy<T, double>(w.tg, y, p, fs.s2, 1, s, g + 1);
     return cuda_check(h, "gls_initial");
 }
@@ -419,14 +434,14 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     double *g = w.scal + 8;
     pow2_normalizer(y, p, 1.0 / fs.s2, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(y, w.tw, p, 1.0 / fs.s2, 1, s, g);
-    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
     // T~_L h~2 = w~[0:L]
     vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
-    RC(trsv_upper<T>(w.Ct, p, L, 0, w.th, h->sc, s));
+    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s));
     // z' = Q [0_m; P_L h~2]
     vzero(w.tt, sizeof(T) * n, s);
     vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
-    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 0, w.tt, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, z, n, fs.s2 * fs.s2, 0, s, g + 1);
     return cuda_check(h, "gls_multipliers");
 }
@@ -445,42 +460,42 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     cudaStream_t s = h->stream;
     // step 1: u = Q^T f2'
     vcopy<double, T>(f2, w.tu, n, c2, 0, s);
-    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 1, w.tu, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 1, w.tu, h->sc, s));
     // step 2: w~ = Z~^T (P_p f1') = P_p (Z f1')
     vcopy<double, T>(f1, w.tw, p, c1, 1, s);
-    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
     // step 3: R^T h1 = f3'   (th[0:m] = h1)
     vcopy<double, T>(f3, w.th, m, c3, 0, s);
-    RC(trsv_upper<T>(w.Wf, n, m, 1, w.th, h->sc, s));
+    RC(trsv_upper<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s));
     // h~1 = P_m h1 (tt)
     vcomb<T>(w.tt, m, w.th, 1, T(1), nullptr, 0, T(0), s);
     // step 4: T22 g2 = u2  <=>  T~_L^T g~2 = P_L u2   (tg[0:L] = g~2)
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
-    RC(trsv_upper<T>(w.Ct, p, L, 1, w.tg, h->sc, s));
+    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s));
     // step 5: T22^T h2 = w2 - g2 - T12^T h1  <=>  T~_L h~2 = w~2 - g~2 - T~_12 h~1
-    RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 0, T(1), w.tt, T(0), w.tt2, 0, 0, s));
+    RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 0, T(1), w.tt, T(0), w.tt2, 0, 0, s));
     vcomb<T>(w.th + m, L, w.tw, 0, T(1), w.tg, 0, T(-1), s);
     vcomb<T>(w.th + m, L, w.th + m, 0, T(1), w.tt2, 0, T(-1), s);
-    RC(trsv_upper<T>(w.Ct, p, L, 0, w.th + m, h->sc, s));
+    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 0, w.th + m, h->sc, s));
     // step 6: g1 = w1 - T11^T h1  <=>  g~1 = w~1 - T~_22 h~1   (tg[L:p])
     if (o > 0) {
         vcomb<T>(w.tg + L, o, w.tw + L, 0, T(1), nullptr, 0, T(0), s);
-        RC(gemv<T>(w.Ct + idx2(L, L, p), p, o, m, 0, T(-1), w.tt, T(1), w.tg + L, 1, 0, s));
+        RC(gemv<T>(w.Ct + idx2(L, L, w.ldCt), w.ldCt, o, m, 0, T(-1), w.tt, T(1), w.tg + L, 1, 0, s));
     }
     // step 8 (before the in-place apply of step 7):
     // R dx = u1 - T11 g1 - T12 g2,  P_m(T11 g1 + T12 g2) = T~_22^T g~1 + T~_12^T g~2
-    RC(gemv<T>(w.Ct + idx2(0, L, p), p, L, m, 1, T(1), w.tg, T(0), w.tt2, 0, 0, s));
-    if (o > 0) RC(gemv<T>(w.Ct + idx2(L, L, p), p, o, m, 1, T(1), w.tg + L, T(1), w.tt2, 1, 0, s));
+    RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 1, T(1), w.tg, T(0), w.tt2, 0, 0, s));
+    if (o > 0) RC(gemv<T>(w.Ct + idx2(L, L, w.ldCt), w.ldCt, o, m, 1, T(1), w.tg + L, T(1), w.tt2, 1, 0, s));
     vcomb<T>(w.tt, m, w.tu, 0, T(1), w.tt2, 1, T(-1), s);
-    RC(trsv_upper<T>(w.Wf, n, m, 0, w.tt, h->sc, s));
+    RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s));
     vaxpy<T>(w.tt, dx, m, sW / sV / gamma, 0, s);
     // step 7: dy = Z^T g = P_p Z~ g~
-    RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
     vaxpy<T>(w.tg, dy, p, 1.0 / gamma, 1, s);
     //         dz = -Q h,  h = [h1; P_L h~2]
     vcomb<T>(w.tt2, L, w.th + m, 1, T(1), nullptr, 0, T(0), s);
     cudaMemcpyAsync(w.th + m, w.tt2, sizeof(T) * L, cudaMemcpyDeviceToDevice, s);
-    RC(apply_reflectors_vec<T>(w.Wf, n, n, m, w.TwW, 0, w.th, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 0, w.th, h->sc, s));
     vaxpy<T>(w.th, dz, n, -sV / gamma, 0, s);
     return cuda_check(h, "gls_correction");
 }
@@ -624,14 +639,14 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     h->fs.fro2 = std::sqrt(h->hbuf[3]);
     const GemmPrec gp = gemm_prec(fact);
     // RQ of B as QR of B~ = P_n B^T P_p (Lemma 4.5, first factorization)
-    mconvert<double, T>(B, ldb, w.Bt, n, n, p, 1, 1, 1, sB, s);
-    RC(geqrf<T>(w.Bt, n, n, p, w.tauB, w.TwB, gp, s));
+    mconvert<double, T>(B, ldb, w.Bt, w.ldBt, n, p, 1, 1, 1, sB, s);
+    RC(geqrf<T>(w.Bt, w.ldBt, n, p, w.tauB, w.TwB, w.Tw128B, gp, w.gws, h->sc.err, s));
     // X = Q~^T P_n A^T = P_n (A Q^T)^T
-    mconvert<double, T>(A, lda, w.X, n, n, m, 1, 1, 0, sA, s);
-    RC(apply_reflectors_left<T>(w.Bt, n, n, p, w.TwB, 1, w.X, n, m, gp, s));
+    mconvert<double, T>(A, lda, w.X, w.ldX, n, m, 1, 1, 0, sA, s);
+    RC(apply_reflectors_left<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.X, w.ldX, m, gp, w.gws, h->sc.err, s));
     // A Q^T = X^T P_n, then its QR  (A Q^T = Z T)
-    mconvert<T, T>(w.X, n, w.At, m, m, n, 1, 0, 1, 1.0, s);
-    RC(geqrf<T>(w.At, m, m, n, w.tauA, w.TwA, gp, s));
+    mconvert<T, T>(w.X, w.ldX, w.At, w.ldAt, m, n, 1, 0, 1, 1.0, s);
+    RC(geqrf<T>(w.At, w.ldAt, m, n, w.tauA, w.TwA, w.Tw128A, gp, w.gws, h->sc.err, s));
     return cuda_check(h, "lse_factor");
 }
 
@@ -648,18 +663,18 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     double *g = w.scal + 8;
     pow2_normalizer(b, m, fs.s1, d, p, fs.s2, g, s);
     vcopy<double, T>(b, w.tw, m, fs.s1, 0, s, g);
-    RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
     // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
     vcopy<double, T>(d, w.tb, p, fs.s2, 1, s, g);
-    RC(trsv_upper<T>(w.Bt, n, p, 1, w.tb, h->sc, s));
+    RC(trsv_upper<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s));
     // ty = [y1; y2], y2 = P_p y~2
     vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     vcomb<T>(w.ty, q, w.tw, 0, T(1), nullptr, 0, T(0), s);
-    RC(gemv<T>(w.At + idx2(0, q, m), m, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
-    RC(trsv_upper<T>(w.At, m, q, 0, w.ty, h->sc, s));
+    RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
+    RC(trsv_upper<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s));
     // x = Q^T y = P_n Q~ P_n y
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
-    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 0, w.tt, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, x, n, 1.0, 1, s, g + 1);
     return cuda_check(h, "lse_initial");
 }
@@ -681,9 +696,9 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     double *g = w.scal + 8;
     pow2_normalizer(w.f3, n, fs.s1, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s, g);
-    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 1, w.tu, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 1, w.tu, h->sc, s));
     // R~ (P_p v') = u~[0:p]
-    RC(trsv_upper<T>(w.Bt, n, p, 0, w.tu, h->sc, s));
+    RC(trsv_upper<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s));
     vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s, g + 1);
     return cuda_check(h, "lse_multipliers");
 }
@@ -701,44 +716,44 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     cudaStream_t s = h->stream;
     // step 1: u~ = Q~^T P_n f3' ;  u1 = P_q u~[p:n], u2 = P_p u~[0:p]
     vcopy<double, T>(f3, w.tu, n, c3, 1, s);
-    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 1, w.tu, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 1, w.tu, h->sc, s));
     // step 2: w = Z^T f1'
     vcopy<double, T>(f1, w.tw, m, c1, 0, s);
-    RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
     // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
     if (p > 0) {
         vcopy<double, T>(f2, w.tb, p, c2, 1, s);
-        RC(trsv_upper<T>(w.Bt, n, p, 1, w.tb, h->sc, s));
+        RC(trsv_upper<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s));
         vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     }
     // step 4: T11^T q1 = u1
     if (q > 0) {
         vcomb<T>(w.tq, q, w.tu + p, 1, T(1), nullptr, 0, T(0), s);
-        RC(trsv_upper<T>(w.At, m, q, 1, w.tq, h->sc, s));
+        RC(trsv_upper<T>(w.At, w.ldAt, q, 1, w.tq, h->sc, s));
         // step 5: T11 y1 = w1 - q1 - T12 y2
         vcomb<T>(w.ty, q, w.tw, 0, T(1), w.tq, 0, T(-1), s);
-        if (p > 0) RC(gemv<T>(w.At + idx2(0, q, m), m, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
-        RC(trsv_upper<T>(w.At, m, q, 0, w.ty, h->sc, s));
+        if (p > 0) RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
+        RC(trsv_upper<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s));
     }
     // step 6: q2 = w2 - T22 y2
     if (m - q > 0) {
         vcomb<T>(w.tq + q, m - q, w.tw + q, 0, T(1), nullptr, 0, T(0), s);
-        if (p > 0) RC(gemv<T>(w.At + idx2(q, q, m), m, m - q, p, 0, T(-1), w.ty + q, T(1), w.tq + q, 1, 0, s));
+        if (p > 0) RC(gemv<T>(w.At + idx2(q, q, w.ldAt), w.ldAt, m - q, p, 0, T(-1), w.ty + q, T(1), w.tq + q, 1, 0, s));
     }
     // step 8: R^T dv = T12^T q1 + T22^T q2 - u2  <=>  R~ (P_p dv) = P_p(T12^T q1 + T22^T q2) - u~[0:p]
     if (p > 0) {
         vzero(w.tt, sizeof(T) * p, s);
-        if (q > 0) RC(gemv<T>(w.At + idx2(0, q, m), m, q, p, 1, T(1), w.tq, T(0), w.tt, 0, 0, s));
-        if (m - q > 0) RC(gemv<T>(w.At + idx2(q, q, m), m, m - q, p, 1, T(1), w.tq + q, T(1), w.tt, 1, 0, s));
+        if (q > 0) RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 1, T(1), w.tq, T(0), w.tt, 0, 0, s));
+        if (m - q > 0) RC(gemv<T>(w.At + idx2(q, q, w.ldAt), w.ldAt, m - q, p, 1, T(1), w.tq + q, T(1), w.tt, 1, 0, s));
         vcomb<T>(w.tb, p, w.tt, 1, T(1), w.tu, 0, T(-1), s);
-        RC(trsv_upper<T>(w.Bt, n, p, 0, w.tb, h->sc, s));
+        RC(trsv_upper<T>(w.Bt, w.ldBt, p, 0, w.tb, h->sc, s));
         vaxpy<T>(w.tb, dv, p, sB / sA / gamma, 1, s);
     }
     // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
-    RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, 0, w.tq, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, 0, w.tq, h->sc, s));
     vaxpy<T>(w.tq, dr, m, 1.0 / gamma, 0, s);
     vcomb<T>(w.tt2, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
-    RC(apply_reflectors_vec<T>(w.Bt, n, n, p, w.TwB, 0, w.tt2, h->sc, s));
+    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 0, w.tt2, h->sc, s));
     vaxpy<T>(w.tt2, dx, n, sA / gamma, 1, s);
     return cuda_check(h, "lse_correction");
 }
@@ -1108,6 +1123,26 @@ int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m, cons
 
 // ------------------------------------------------------- step-level API --
 
+int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int ldv, const float *T, int trans,
+               float *C, int ldc)
+{
+    if (!h) return -1;
+    if (prec != MPIR_FP32 && prec != MPIR_TF32 && prec != MPIR_BF16) return -2;
+    if (M < 0) return -3;
+    if (N < 0) return -4;
+    if (K < 0 || K > OUTER_NB || K > M) return -5;
+    if (!V && K > 0) return -6;
+    if (ldv < std::max(1, M)) return -7;
+    if (!T && K > 0) return -8;
+    if (!C && M * N > 0) return -10;
+    if (ldc < std::max(1, M) || ldc % 4) return -11;
+    RC(ensure_ws(h, geqrf_ws_bytes(M, N)));
+    clear_dev_flags(h);
+    RC(larfb_tc(V, ldv, M, K, T, trans, C, ldc, N, gemm_prec(prec), h->ws, h->sc.err, h->stream));
+    RC(cuda_check(h, "mpir_larfb"));
+    return check_dev_flags(h);
+}
+
 int mpir_lse_factor(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
                     int fact)
 {
@@ -1295,23 +1330,23 @@ static int get_RT_impl(mpir_ctx *h, double *R, int ldr, double *Tm, int ldt)
         const int m = w.m, n = w.n, p = w.p;
         if (R && p > 0) {
             // R(i, j) = R~(p-1-j, p-1-i) = Bt(p-1-j, p-1-i) / sB
-            mconvert<T, double>(w.Bt, n, R, ldr, p, p, 1, 1, 1, 1.0 / fs.s2, s);
+            mconvert<T, double>(w.Bt, w.ldBt, R, ldr, p, p, 1, 1, 1, 1.0 / fs.s2, s);
             { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(p, 256), p), 256, 0, s>>>(R, ldr, p, p, 0); }
         }
         if (Tm) {
-            mconvert<T, double>(w.At, m, Tm, ldt, m, n, 0, 0, 0, 1.0 / fs.s1, s);
+            mconvert<T, double>(w.At, w.ldAt, Tm, ldt, m, n, 0, 0, 0, 1.0 / fs.s1, s);
             { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(m, 256), n), 256, 0, s>>>(Tm, ldt, m, n, 0); }
         }
     } else {
         GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
         const int n = w.n, m = w.m, p = w.p;
         if (R && m > 0) {
-            mconvert<T, double>(w.Wf, n, R, ldr, m, m, 0, 0, 0, 1.0 / fs.s1, s);
+            mconvert<T, double>(w.Wf, w.ldW, R, ldr, m, m, 0, 0, 0, 1.0 / fs.s1, s);
             { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(m, 256), m), 256, 0, s>>>(R, ldr, m, m, 0); }
         }
         if (Tm) {
             // T(r, j) = T~(p-1-j, n-1-r) = Ct(p-1-j, n-1-r) / sV ; zero for r > j + n - p
-            mconvert<T, double>(w.Ct, p, Tm, ldt, n, p, 1, 1, 1, 1.0 / fs.s2, s);
+            mconvert<T, double>(w.Ct, w.ldCt, Tm, ldt, n, p, 1, 1, 1, 1.0 / fs.s2, s);
             { ProfScope ps(K_ELEMWISE, s); k_mask_lower<<<dim3(ceil_div(n, 256), p), 256, 0, s>>>(Tm, ldt, n, p, n - p); }
         }
     }
@@ -1342,12 +1377,12 @@ static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
             // Q = P_n Q~^T P_n ; Q^T = P_n Q~ P_n
             const int n = w.n;
             vcopy<double, T>(vec, w.tt, n, 1.0, 1, s);
-            RC(apply_reflectors_vec<T>(w.Bt, n, n, w.p, w.TwB, trans ? 0 : 1, w.tt, h->sc, s));
+            RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, w.p, w.TwB, trans ? 0 : 1, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, n, 1.0, 1, s);
         } else {
             const int m = w.m;
             vcopy<double, T>(vec, w.tt, m, 1.0, 0, s);
-            RC(apply_reflectors_vec<T>(w.At, m, m, w.kA, w.TwA, trans, w.tt, h->sc, s));
+            RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, trans, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, m, 1.0, 0, s);
         }
     } else {
@@ -1355,13 +1390,13 @@ static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
         if (which == 0) {
             const int n = w.n;
             vcopy<double, T>(vec, w.tt, n, 1.0, 0, s);
-            RC(apply_reflectors_vec<T>(w.Wf, n, n, w.m, w.TwW, trans, w.tt, h->sc, s));
+            RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, w.m, w.TwW, trans, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, n, 1.0, 0, s);
         } else {
             // Z = P_p Z~^T P_p ; Z^T = P_p Z~ P_p
             const int p = w.p;
             vcopy<double, T>(vec, w.tt, p, 1.0, 1, s);
-            RC(apply_reflectors_vec<T>(w.Ct, p, p, w.kC, w.TwC, trans ? 0 : 1, w.tt, h->sc, s));
+            RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, trans ? 0 : 1, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, p, 1.0, 1, s);
         }
     }

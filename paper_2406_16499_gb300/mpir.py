@@ -74,13 +74,14 @@ _SIG = {
     "mpir_gls_residual": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_lse_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_gls_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
+    "mpir_larfb": ([_P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
     "mpir_launch_count": ([_I], ctypes.c_longlong),
     "mpir_kernel_kind_name": ([_I], ctypes.c_char_p),
 }
 
-NKINDS = 10
+NKINDS = 12
 
 
 def profile(enable):
@@ -280,6 +281,14 @@ class Handle:
     def lse_correction(self, f1, f2, f3, dr, dv, dx):
         return self.check(lib().mpir_lse_correction(self.h, ptr(f1), ptr(f2), ptr(f3), ptr(dr), ptr(dv),
                                                     ptr(dx)), "mpir_lse_correction")
+
+    def larfb(self, V, T, C, trans=True, prec="fp32"):
+        """C <- (I - V X V^T) C on the tensor cores (FP32 tensors; V M x K
+        panel, T K x K with leading dimension 128, C M x N column-major)."""
+        M, K = V.shape
+        N = C.shape[1]
+        rc = lib().mpir_larfb(self.h, PREC[prec], M, N, K, ptr(V), ld(V), ptr(T), 1 if trans else 0, ptr(C), ld(C))
+        return self.check(rc, "mpir_larfb")
 
     def gls_correction(self, f1, f2, f3, dy, dz, dx):
         return self.check(lib().mpir_gls_correction(self.h, ptr(f1), ptr(f2), ptr(f3), ptr(dy), ptr(dz),
