@@ -70,6 +70,13 @@ template <typename T>
 int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int trans, T *x,
                          const DevScratch &sc, cudaStream_t s);
 
+// Same as apply_reflectors_vec with blocks of nbv reflectors whose
+// compact-WY factors are in Tw (nbv x nbv each, ld nbv): one thread-block
+// cluster, one cluster barrier per block (nbv in {16, 32, 128}).
+template <typename T>
+int apply_reflectors_vec_blk(const T *V, int ldv, int M, int K, const T *Tw, int nbv, int trans, T *x,
+                             cudaStream_t s);
+
 // Solve U x = b (trans = 0) or U^T x = b (trans = 1) in place, U upper
 // triangular n x n (ldu).  Zero diagonal -> bit 1 of *sc.status.
 template <typename T>

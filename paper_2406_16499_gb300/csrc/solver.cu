@@ -331,6 +331,16 @@ GemmPrec gemm_prec(int fact)
 
 #define RC(x) do { int _rc = (x); if (_rc) return _rc; } while (0)
 
+// Reflector-set application to one vector with the widest compact-WY
+// blocks the factorization kept: 128 (two-level FP32) or 16 (FP64).
+template <typename T>
+int vapply(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, int trans, T *x, const DevScratch &,
+           cudaStream_t s)
+{
+    if (sizeof(T) == 4) return apply_reflectors_vec_blk<T>(V, ldv, M, K, Tw128, OUTER_NB, trans, x, s);
+    return apply_reflectors_vec_blk<T>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
+}
+
 // T-vector combine: out[i] = alpha * a[ra ? n-1-i : i] + beta * b[rb ? n-1-i : i]
 template <typename T>
 __global__ void k_vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, int rb, T beta)
@@ -406,7 +416,7 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     double *g = w.scal + 8;
     pow2_normalizer(d, n, 1.0, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(d, w.tu, n, 1.0, 0, s, g);
-    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.tu, h->sc, s));
     // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
     vzero(w.tg, sizeof(T) * p, s);
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
@@ -417,7 +427,7 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s));
     vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s, g + 1);
     // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
-    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 0, w.tg, h->sc, s));
     vcopy<T, double>(w.tg, y, p, fs.s2, 1, s, g + 1);
     return cuda_check(h, "gls_initial");
 }
@@ -434,14 +444,14 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     double *g = w.scal + 8;
     pow2_normalizer(y, p, 1.0 / fs.s2, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(y, w.tw, p, 1.0 / fs.s2, 1, s, g);
-    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 1, w.tw, h->sc, s));
     // T~_L h~2 = w~[0:L]
     vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
     RC(trsv_upper<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s));
     // z' = Q [0_m; P_L h~2]
     vzero(w.tt, sizeof(T) * n, s);
     vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
-    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 0, w.tt, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, z, n, fs.s2 * fs.s2, 0, s, g + 1);
     return cuda_check(h, "gls_multipliers");
 }
@@ -460,10 +470,10 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     cudaStream_t s = h->stream;
     // step 1: u = Q^T f2'
     vcopy<double, T>(f2, w.tu, n, c2, 0, s);
-    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.tu, h->sc, s));
     // step 2: w~ = Z~^T (P_p f1') = P_p (Z f1')
     vcopy<double, T>(f1, w.tw, p, c1, 1, s);
-    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 1, w.tw, h->sc, s));
     // step 3: R^T h1 = f3'   (th[0:m] = h1)
     vcopy<double, T>(f3, w.th, m, c3, 0, s);
     RC(trsv_upper<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s));
@@ -490,12 +500,12 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s));
     vaxpy<T>(w.tt, dx, m, sW / sV / gamma, 0, s);
     // step 7: dy = Z^T g = P_p Z~ g~
-    RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, 0, w.tg, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 0, w.tg, h->sc, s));
     vaxpy<T>(w.tg, dy, p, 1.0 / gamma, 1, s);
     //         dz = -Q h,  h = [h1; P_L h~2]
     vcomb<T>(w.tt2, L, w.th + m, 1, T(1), nullptr, 0, T(0), s);
     cudaMemcpyAsync(w.th + m, w.tt2, sizeof(T) * L, cudaMemcpyDeviceToDevice, s);
-    RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, m, w.TwW, 0, w.th, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, w.th, h->sc, s));
     vaxpy<T>(w.th, dz, n, -sV / gamma, 0, s);
     return cuda_check(h, "gls_correction");
 }
@@ -663,7 +673,7 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     double *g = w.scal + 8;
     pow2_normalizer(b, m, fs.s1, d, p, fs.s2, g, s);
     vcopy<double, T>(b, w.tw, m, fs.s1, 0, s, g);
-    RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, 1, w.tw, h->sc, s));
     // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
     vcopy<double, T>(d, w.tb, p, fs.s2, 1, s, g);
     RC(trsv_upper<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s));
@@ -674,7 +684,7 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     RC(trsv_upper<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s));
     // x = Q^T y = P_n Q~ P_n y
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
-    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 0, w.tt, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, x, n, 1.0, 1, s, g + 1);
     return cuda_check(h, "lse_initial");
 }
@@ -696,7 +706,7 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     double *g = w.scal + 8;
     pow2_normalizer(w.f3, n, fs.s1, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s, g);
-    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.tu, h->sc, s));
     // R~ (P_p v') = u~[0:p]
     RC(trsv_upper<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s));
     vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s, g + 1);
@@ -716,10 +726,10 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     cudaStream_t s = h->stream;
     // step 1: u~ = Q~^T P_n f3' ;  u1 = P_q u~[p:n], u2 = P_p u~[0:p]
     vcopy<double, T>(f3, w.tu, n, c3, 1, s);
-    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.tu, h->sc, s));
     // step 2: w = Z^T f1'
     vcopy<double, T>(f1, w.tw, m, c1, 0, s);
-    RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, 1, w.tw, h->sc, s));
     // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
     if (p > 0) {
         vcopy<double, T>(f2, w.tb, p, c2, 1, s);
@@ -750,10 +760,10 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
         vaxpy<T>(w.tb, dv, p, sB / sA / gamma, 1, s);
     }
     // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
-    RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, 0, w.tq, h->sc, s));
+    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, 0, w.tq, h->sc, s));
     vaxpy<T>(w.tq, dr, m, 1.0 / gamma, 0, s);
     vcomb<T>(w.tt2, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
-    RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, p, w.TwB, 0, w.tt2, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, w.tt2, h->sc, s));
     vaxpy<T>(w.tt2, dx, n, sA / gamma, 1, s);
     return cuda_check(h, "lse_correction");
 }
@@ -1377,12 +1387,12 @@ static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
             // Q = P_n Q~^T P_n ; Q^T = P_n Q~ P_n
             const int n = w.n;
             vcopy<double, T>(vec, w.tt, n, 1.0, 1, s);
-            RC(apply_reflectors_vec<T>(w.Bt, w.ldBt, n, w.p, w.TwB, trans ? 0 : 1, w.tt, h->sc, s));
+            RC(vapply<T>(w.Bt, w.ldBt, n, w.p, w.TwB, w.Tw128B, trans ? 0 : 1, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, n, 1.0, 1, s);
         } else {
             const int m = w.m;
             vcopy<double, T>(vec, w.tt, m, 1.0, 0, s);
-            RC(apply_reflectors_vec<T>(w.At, w.ldAt, m, w.kA, w.TwA, trans, w.tt, h->sc, s));
+            RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, trans, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, m, 1.0, 0, s);
         }
     } else {
@@ -1390,13 +1400,13 @@ static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
         if (which == 0) {
             const int n = w.n;
             vcopy<double, T>(vec, w.tt, n, 1.0, 0, s);
-            RC(apply_reflectors_vec<T>(w.Wf, w.ldW, n, w.m, w.TwW, trans, w.tt, h->sc, s));
+            RC(vapply<T>(w.Wf, w.ldW, n, w.m, w.TwW, w.Tw128W, trans, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, n, 1.0, 0, s);
         } else {
             // Z = P_p Z~^T P_p ; Z^T = P_p Z~ P_p
             const int p = w.p;
             vcopy<double, T>(vec, w.tt, p, 1.0, 1, s);
-            RC(apply_reflectors_vec<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, trans ? 0 : 1, w.tt, h->sc, s));
+            RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, trans ? 0 : 1, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, p, 1.0, 1, s);
         }
     }

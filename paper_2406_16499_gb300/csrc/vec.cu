@@ -147,6 +147,250 @@ int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int tra
 }
 
 // ---------------------------------------------------------------------------
+// Cluster version of the reflector-set application, used whenever the
+// blocks' compact-WY factors are available at width NBV (128 for the
+// two-level FP32 factorization).  One thread-block cluster; CTA r owns rows
+// [r*slice, (r+1)*slice) of x in shared memory.  Per block of NBV
+// reflectors:
+//   1. each warp forms partial dots v_c^T x over the CTA's rows for its
+//      columns (coalesced column reads of V);
+//   2. cluster barrier; every CTA sums the partials of all CTAs from
+//      distributed shared memory in rank order (identical on every CTA);
+//   3. w' = X w with X = Tw^T (trans) or Tw, Tw staged in shared memory;
+//   4. x_i -= sum_c v_c(i) w'_c on the CTA's rows.
+// One cluster barrier per NBV reflectors (partials double-buffered).
+// ---------------------------------------------------------------------------
+constexpr int VEC_CL_THREADS = 512;
+
+template <typename T, int NBV>
+__global__ void __launch_bounds__(VEC_CL_THREADS, 1)
+k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restrict__ Tw, int trans,
+               T *__restrict__ x, int slice)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Ts = reinterpret_cast<T *>(smem_raw);          // NBV x NBV, X(i,k) at i + k*NBV
+    T *xs = Ts + NBV * NBV;                           // slice
+    __shared__ T pbuf[2][NBV];
+    __shared__ T wv[NBV];
+    __shared__ T wp[NBV];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NWARP = VEC_CL_THREADS / 32;
+    const int s0 = crank * slice;
+    const int s1 = min(s0 + slice, M);
+    for (int i = s0 + tid; i < s1; i += VEC_CL_THREADS) xs[i - s0] = x[i];
+    __syncthreads();
+    const int nblk = ceil_div(K, NBV);
+    for (int t = 0; t < nblk; t++) {
+        const int b = trans ? t : nblk - 1 - t;
+        const int j0 = b * NBV;
+        const int kb = min(NBV, K - j0);
+        const int par = t & 1;
+        // stage X (used after the barrier)
+        const T *Tb = Tw + (size_t)b * NBV * NBV;
+        for (int e = tid; e < NBV * NBV; e += VEC_CL_THREADS) {
+            const int i = e % NBV, k = e / NBV;
+            const T tv = Tb[i + (size_t)k * NBV];
+            if (trans) Ts[k + i * NBV] = tv; else Ts[i + k * NBV] = tv;
+        }
+        // 1. partial dots
+        for (int c = warp; c < NBV; c += NWARP) {
+            T acc = T(0);
+            if (c < kb) {
+                const int j = j0 + c;
+                const T *vc = V + (size_t)j * ldv;
+                for (int i = max(s0, j) + lane; i < s1; i += 32) {
+                    const T v = i == j ? T(1) : vc[i];
+                    acc = fma(v, xs[i - s0], acc);
+                }
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) pbuf[par][c] = acc;
+        }
+        cluster.sync();
+        // 2. cluster-wide sums
+        if (tid < NBV) {
+            T wsum = T(0);
+            for (int r = 0; r < cs; r++) wsum += *cluster.map_shared_rank(&pbuf[par][tid], r);
+            wv[tid] = wsum;
+        }
+        __syncthreads();
+        // 3. w' = X w
+        if (tid < NBV) {
+            T sacc = T(0);
+            for (int k = 0; k < kb; k++) sacc = fma(Ts[tid + k * NBV], wv[k], sacc);
+            wp[tid] = tid < kb ? sacc : T(0);
+        }
+        __syncthreads();
+        // 4. update the owned rows
+        for (int i = max(s0, j0) + tid; i < s1; i += VEC_CL_THREADS) {
+            T d = T(0);
+            const int cmax = min(kb, i - j0 + 1);
+            for (int c = 0; c < cmax; c++) {
+                const int j = j0 + c;
+                const T v = i == j ? T(1) : V[(size_t)j * ldv + i];
+                d = fma(v, wp[c], d);
+            }
+            xs[i - s0] -= d;
+        }
+        __syncthreads();
+    }
+    for (int i = s0 + tid; i < s1; i += VEC_CL_THREADS) x[i] = xs[i - s0];
+    cluster.sync();   // keep shared memory alive until every remote read is done
+}
+
+static int cluster_size_for(const void *kern, int threads, size_t smem, int want)
+{
+    if (want <= 1) return 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(want, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = want;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int maxc = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&maxc, kern, &cfg) != cudaSuccess) { cudaGetLastError(); maxc = 8; }
+    int c = 1;
+    while (c * 2 <= want && c * 2 <= maxc) c *= 2;
+    return c;
+}
+
+template <typename T, int NBV>
+static int launch_vec_apply_cl(const T *V, int ldv, int M, int K, const T *Tw, int trans, T *x, cudaStream_t s)
+{
+    auto kern = k_vec_apply_cl<T, NBV>;
+    int want = ceil_div(M, 256);
+    if (want > 16) want = 16;
+    static bool attr = false;
+    const size_t tsz = (size_t)NBV * NBV * sizeof(T);
+    if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(tsz + 64 * 1024));
+        attr = true;
+    }
+    int cs = cluster_size_for((const void *)kern, VEC_CL_THREADS, tsz + (size_t)ceil_div(M, want) * sizeof(T), want);
+    int slice = ceil_div(M, cs);
+    size_t smem = tsz + (size_t)slice * sizeof(T);
+    if (smem > tsz + 64 * 1024) return MPIR_UNSUPPORTED;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(VEC_CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ProfScope ps(K_VEC_APPLY, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, V, ldv, M, K, Tw, trans, x, slice);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+template <typename T>
+int apply_reflectors_vec_blk(const T *V, int ldv, int M, int K, const T *Tw, int nbv, int trans, T *x,
+                             cudaStream_t s)
+{
+    if (K <= 0 || M <= 0) return 0;
+    if (nbv == 128) return launch_vec_apply_cl<T, 128>(V, ldv, M, K, Tw, trans, x, s);
+    if (nbv == 32) return launch_vec_apply_cl<T, 32>(V, ldv, M, K, Tw, trans, x, s);
+    if (nbv == 16) return launch_vec_apply_cl<T, 16>(V, ldv, M, K, Tw, trans, x, s);
+    return MPIR_UNSUPPORTED;
+}
+
+// ---------------------------------------------------------------------------
+// Cluster triangular solve with an upper triangular U (n x n):
+//   trans = 0: U x = b  (32-row blocks from the bottom)
+//   trans = 1: U^T x = b (32-row blocks from the top)
+// CTA r owns rows [r*slice, (r+1)*slice) of x (slice a multiple of 32).  Per
+// diagonal block: its owner solves the 32 x 32 triangle in one warp and
+// publishes the values in its shared memory; cluster barrier; every CTA
+// reads them through distributed shared memory and updates its own
+// unsolved rows.  One cluster barrier per 32 rows.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(VEC_CL_THREADS, 1)
+k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
+          int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);
+    __shared__ T xb[2][32];
+    __shared__ T xl[32];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int s0 = crank * slice;
+    const int s1 = min(s0 + slice, n);
+    for (int i = s0 + tid; i < s1; i += VEC_CL_THREADS) xs[i - s0] = x[i];
+    __syncthreads();
+    const int nblk = ceil_div(n, 32);
+    for (int t = 0; t < nblk; t++) {
+        const int blk = trans ? t : nblk - 1 - t;
+        const int r0 = blk * 32;
+        const int bs = min(32, n - r0);
+        const int par = t & 1;
+        const int owner = r0 / slice;
+        if (crank == owner && warp == 0) {
+            T rhs = lane < bs ? xs[r0 + lane - s0] : T(0);
+            T xv = T(0);
+            if (!trans) {
+                for (int c = bs - 1; c >= 0; c--) {
+                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    T xc = __shfl_sync(0xffffffffu, rhs, c);
+                    if (dcc == T(0) && lane == 0) atomicOr(status, 2);
+                    xc = xc / dcc;
+                    if (lane == c) xv = xc;
+                    if (lane < c) rhs = fma(-U[idx2(r0 + lane, r0 + c, ldu)], xc, rhs);
+                }
+            } else {
+                for (int c = 0; c < bs; c++) {
+                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    T xc = __shfl_sync(0xffffffffu, rhs, c);
+                    if (dcc == T(0) && lane == 0) atomicOr(status, 2);
+                    xc = xc / dcc;
+                    if (lane == c) xv = xc;
+                    if (lane > c && lane < bs) rhs = fma(-U[idx2(r0 + c, r0 + lane, ldu)], xc, rhs);
+                }
+            }
+            if (lane < bs) xs[r0 + lane - s0] = xv;
+            xb[par][lane] = lane < bs ? xv : T(0);
+        }
+        cluster.sync();
+        if (tid < 32) xl[tid] = *cluster.map_shared_rank(&xb[par][tid], owner);
+        __syncthreads();
+        if (!trans) {
+            const int hi = min(s1, r0);
+            for (int i = s0 + tid; i < hi; i += VEC_CL_THREADS) {
+                T d = T(0);
+                for (int c = 0; c < bs; c++) d = fma(U[idx2(i, r0 + c, ldu)], xl[c], d);
+                xs[i - s0] -= d;
+            }
+        } else {
+            const int lo = max(s0, r0 + bs);
+            for (int i = lo + tid; i < s1; i += VEC_CL_THREADS) {
+                const T *ucol = U + idx2(r0, i, ldu);
+                T d = T(0);
+                for (int c = 0; c < bs; c++) d = fma(ucol[c], xl[c], d);
+                xs[i - s0] -= d;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = s0 + tid; i < s1; i += VEC_CL_THREADS) x[i] = xs[i - s0];
+    cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
 // Blocked triangular solve with an upper triangular U (n x n):
 //   trans = 0: U x = b  (blocks of 32 from the bottom)
 //   trans = 1: U^T x = b (blocks of 32 from the top)
@@ -229,9 +473,48 @@ k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__
 }
 
 template <typename T>
+static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
+{
+    auto kern = k_trsv_cl<T>;
+    const int nblk = ceil_div(n, 32);
+    int want = ceil_div(nblk, 8);            // 256 rows per CTA
+    if (want > 16) want = 16;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
+        attr = true;
+    }
+    int cs = cluster_size_for((const void *)kern, VEC_CL_THREADS, (size_t)ceil_div(nblk, want) * 32 * sizeof(T), want);
+    const int slice = ceil_div(nblk, cs) * 32;
+    cs = ceil_div(n, slice);
+    const size_t smem = (size_t)slice * sizeof(T);
+    if (smem > 128 * 1024) return -1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(VEC_CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ProfScope ps(K_TRSV, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, sc.status);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+template <typename T>
 int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
 {
     if (n <= 0) return 0;
+    {
+        const int rc = trsv_upper_cl<T>(U, ldu, n, trans, x, sc, s);
+        if (rc >= 0) return rc;          // -1: too large for one cluster, use the grid version
+    }
     auto kern = k_trsv_upper<T>;
     const int nblk = ceil_div(n, 32);
     int want = ceil_div(nblk, 4);          // 128 rows per block
@@ -495,6 +778,10 @@ template int apply_reflectors_vec<float>(const float *, int, int, int, const flo
                                          const DevScratch &, cudaStream_t);
 template int apply_reflectors_vec<double>(const double *, int, int, int, const double *, int, double *,
                                           const DevScratch &, cudaStream_t);
+template int apply_reflectors_vec_blk<float>(const float *, int, int, int, const float *, int, int, float *,
+                                             cudaStream_t);
+template int apply_reflectors_vec_blk<double>(const double *, int, int, int, const double *, int, int, double *,
+                                              cudaStream_t);
 template int trsv_upper<float>(const float *, int, int, int, float *, const DevScratch &, cudaStream_t);
 template int trsv_upper<double>(const double *, int, int, int, double *, const DevScratch &, cudaStream_t);
 template int gemv<float>(const float *, int, int, int, int, float, const float *, float, float *, int, int,
