@@ -99,6 +99,29 @@ __host__ __device__ __forceinline__ size_t idx2(int i, int j, int ld)
     return (size_t)j * (size_t)ld + (size_t)i;
 }
 
+// Largest power-of-two cluster size <= want that the device can schedule for
+// `kern` with this block size and dynamic shared memory.
+inline int cluster_size_for(const void *kern, int threads, size_t smem, int want)
+{
+    if (want <= 1) return 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(want, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = want;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int maxc = 0;
+    if (cudaOccupancyMaxPotentialClusterSize(&maxc, kern, &cfg) != cudaSuccess) { cudaGetLastError(); maxc = 8; }
+    int c = 1;
+    while (c * 2 <= want && c * 2 <= maxc) c *= 2;
+    return c;
+}
+
 template <typename T> struct Lim;
 template <> struct Lim<float> { static constexpr float eps = 5.9604645e-08f; };
 template <> struct Lim<double> { static constexpr double eps = 1.1102230246251565e-16; };

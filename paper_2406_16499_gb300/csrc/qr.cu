@@ -49,11 +49,12 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     const int L = M - j0;
     const int kpanel = min(ncols, L);
 
-    __shared__ T red_s[NW][32];
+    __shared__ T red_s[2][NW][32];
     __shared__ T xbuf[2][32];
+    __shared__ T gbuf[2][16][32];
     __shared__ T prow[2][NB];
-    __shared__ T coef_s[NB];
-    __shared__ T sc_s[2];
+    __shared__ T prow_l[2][NB];
+    __shared__ T coefw[NW][NB];
     __shared__ T G_s[NB][NB + 1];
     __shared__ T tau_s[NB];
     __shared__ T T_s[NB][NB + 1];
@@ -94,7 +95,7 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                     for (int c = 0; c < H; c++) acc[c] = fma(ak, a[q][h0 + c], acc[c]);
                 }
                 T wsum = warp_transpose_reduce<T, H>(acc);
-                if (lane < H) red_s[warp][h0 + lane] = wsum;
+                if (lane < H) red_s[par][warp][h0 + lane] = wsum;
             }
 #pragma unroll
             for (int q = 0; q < RPT; q++) {
@@ -104,46 +105,48 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                 }
             }
             __syncthreads();
+            // every warp forms the column totals and the coefficients itself
             T tot = T(0), pj = T(0);
-            if (warp == 0 && lane < NB) {
+            if (cs == 1) {
+                if (lane < NB) {
 #pragma unroll
-                for (int w = 0; w < NW; w++) tot += red_s[w][lane];
-                xbuf[par][lane] = tot;
+                    for (int w = 0; w < NW; w++) tot += red_s[par][w][lane];
+                    pj = prow[par][lane];
+                }
+            } else {
+                if (warp == 0 && lane < NB) {
+                    T t = T(0);
+#pragma unroll
+                    for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
+                    xbuf[par][lane] = t;
+                }
+                cluster.sync();
+                if (warp < cs && lane < NB) gbuf[par][warp][lane] = *cluster.map_shared_rank(&xbuf[par][lane], warp);
+                if (warp == NW - 1 && lane < NB) prow_l[par][lane] = *cluster.map_shared_rank(&prow[par][lane], 0);
+                __syncthreads();
+                if (lane < NB) {
+                    for (int r = 0; r < cs; r++) tot += gbuf[par][r][lane];
+                    pj = prow_l[par][lane];
+                }
             }
-            if (cs > 1) cluster.sync();
+            const T alpha = __shfl_sync(0xffffffffu, pj, kk);
+            const T sp = __shfl_sync(0xffffffffu, tot, kk);
+            T beta, tv, scale;
+            if (sp == T(0)) {
+                tv = T(0); beta = alpha; scale = T(1);
+            } else {
+                const T nrm = sqrt(alpha * alpha + sp);
+                beta = alpha >= T(0) ? -nrm : nrm;
+                tv = (beta - alpha) / beta;
+                scale = T(1) / (alpha - beta);
+            }
+            const T dot = pj + scale * tot;
+            if (lane < NB) coefw[warp][lane] = lane > kk ? tv * dot : T(0);
             if (warp == 0) {
-                if (lane < NB) {
-                    if (cs > 1) {
-                        T t = T(0);
-                        for (int r = 0; r < cs; r++) t += *cluster.map_shared_rank(&xbuf[par][lane], r);
-                        tot = t;
-                        pj = *cluster.map_shared_rank(&prow[par][lane], 0);
-                    } else {
-                        pj = prow[par][lane];
-                    }
-                }
-                const T alpha = __shfl_sync(0xffffffffu, pj, kk);
-                const T sp = __shfl_sync(0xffffffffu, tot, kk);
-                T beta, tv, scale;
-                if (sp == T(0)) {
-                    tv = T(0); beta = alpha; scale = T(1);
-                } else {
-                    const T nrm = sqrt(alpha * alpha + sp);
-                    beta = alpha >= T(0) ? -nrm : nrm;
-                    tv = (beta - alpha) / beta;
-                    scale = T(1) / (alpha - beta);
-                }
-                const T dot = pj + scale * tot;
-                if (lane < NB) {
-                    coef_s[lane] = lane > kk ? tv * dot : T(0);
-                    if (lane < kk) G_s[lane][kk] = dot;
-                }
-                if (lane == 0) { sc_s[0] = scale; sc_s[1] = beta; tau_s[kk] = tv; }
+                if (lane < kk) G_s[lane][kk] = dot;
+                if (lane == 0) tau_s[kk] = tv;
             }
-            __syncthreads();
-            const T scale = sc_s[0], beta = sc_s[1];
-            // columns c <= kk are untouched (their coefficient is zero), so
-            // only c > kk is visited; coefficients are broadcast smem reads
+            __syncwarp();
             // branch-free: f = v_i (scale * a(i,kk) below the pivot, 1 on the
             // pivot row, 0 above), a(i, c) -= coef_c * f for c > kk
 #pragma unroll
@@ -152,11 +155,12 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                 const T sk = a[q][kk] * scale;
                 const T f = below ? sk : (piv ? T(1) : T(0));
 #pragma unroll
-                for (int c = kk + 1; c < NB; c++) a[q][c] = fma(-coef_s[c], f, a[q][c]);
+                for (int c = kk + 1; c < NB; c++) a[q][c] = fma(-coefw[warp][c], f, a[q][c]);
                 a[q][kk] = below ? sk : (piv ? beta : a[q][kk]);
             }
         }
     }
+    __syncthreads();
 
     // write the factored panel back.  The base pointer is laundered so that
     // the compiler does not keep the 64 load addresses alive across the loop.
@@ -408,6 +412,101 @@ k_inner_update(const T *__restrict__ V, int ldv, int kb, int L, T *__restrict__ 
     }
 }
 
+// Fused inner update on one thread-block cluster: CTA r owns rows
+// [r*chunk, (r+1)*chunk); partial V^T C over its rows, a DSMEM sum over the
+// cluster (rank order, identical on every CTA), W = Tw^T S, then
+// C -= V W on its rows.  One launch and one cluster barrier per update.
+template <int NB>
+__global__ void __launch_bounds__(256, 1)
+k_inner_cl(const float *__restrict__ V, int ldv, int kb, int L, float *__restrict__ C, int ldc, int nc,
+           const float *__restrict__ Tw, int chunk)
+{
+    __shared__ float Vs[32][NB + 1];
+    __shared__ float Cs[32][INNER_MAXC + 1];      // C staging, later the reduced S = V^T C
+    __shared__ float pw[NB * INNER_MAXC];         // this CTA's partial, read remotely
+    __shared__ float Wt[NB][INNER_MAXC + 1];
+    __shared__ float Xs[NB][NB + 1];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int r0 = crank * chunk, r1 = min(r0 + chunk, L);
+    constexpr int CSTEP = 256 / NB;
+    constexpr int NOUT = (INNER_MAXC + CSTEP - 1) / CSTEP;
+    const int i = tid % NB, cb = tid / NB;
+    float acc[NOUT];
+#pragma unroll
+    for (int q = 0; q < NOUT; q++) acc[q] = 0.f;
+    for (int rr = r0; rr < r1; rr += 32) {
+        for (int e = tid; e < 32 * NB; e += 256) {
+            const int r = e % 32, c = e / 32, gr = rr + r;
+            float v = 0.f;
+            if (gr < r1 && c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f);
+            Vs[r][c] = v;
+        }
+        for (int e = tid; e < 32 * nc; e += 256) {
+            const int r = e % 32, c = e / 32, gr = rr + r;
+            Cs[r][c] = gr < r1 ? C[idx2(gr, c, ldc)] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < 32; r++) {
+            const float v = Vs[r][i];
+#pragma unroll
+            for (int q = 0; q < NOUT; q++) {
+                const int c = cb + CSTEP * q;
+                if (c < nc) acc[q] = fmaf(v, Cs[r][c], acc[q]);
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < NOUT; q++) {
+        const int c = cb + CSTEP * q;
+        if (c < nc) pw[i + c * NB] = acc[q];
+    }
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int a = e % NB, k = e / NB;
+        Xs[k][a] = Tw[a + k * NB];                // X = Tw^T
+    }
+    cluster.sync();
+    for (int e = tid; e < NB * nc; e += 256) {
+        float sum = 0.f;
+        for (int r = 0; r < cs; r++) sum += *cluster.map_shared_rank(&pw[e], r);
+        Cs[e % NB][e / NB] = sum;
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * nc; e += 256) {
+        const int a = e % NB, c = e / NB;
+        float sum = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < NB; k++) sum = fmaf(Xs[a][k], Cs[k][c], sum);
+        Wt[a][c] = sum;
+    }
+    __syncthreads();
+    const int lr = tid & 31, cg0 = tid >> 5;
+    for (int rr = r0; rr < r1; rr += 32) {
+        __syncthreads();
+        for (int e = tid; e < 32 * NB; e += 256) {
+            const int r = e % 32, c = e / 32, gr = rr + r;
+            float v = 0.f;
+            if (gr < r1 && c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f);
+            Vs[r][c] = v;
+        }
+        __syncthreads();
+        const int gr = rr + lr;
+        if (gr < r1) {
+            for (int c = cg0; c < nc; c += 8) {
+                float t = 0.f;
+#pragma unroll 8
+                for (int k = 0; k < NB; k++) t = fmaf(Vs[lr][k], Wt[k][c], t);
+                C[idx2(gr, c, ldc)] -= t;
+            }
+        }
+    }
+    cluster.sync();   // pw must outlive the remote reads
+}
+
 // ---------------------------------------------------------------------------
 // Outer (128-reflector) blocks, FP32 storage.
 //
@@ -469,8 +568,16 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
     for (int e = tid; e < 32 * OUTER_NB; e += 256) {
         const int i = e % OUTER_NB, c = e / OUTER_NB;
         float s = 0.f;
-        if (c0 + c < nc)
-            for (int z = 0; z < nsplit; z++) s += P[(size_t)z * pstride + (size_t)(c0 + c) * ldp + i];
+        if (c0 + c < nc) {
+            const float *pp = P + (size_t)(c0 + c) * ldp + i;
+            int z = 0;
+            for (; z + 4 <= nsplit; z += 4) {
+                const float a0 = pp[(size_t)z * pstride], a1 = pp[(size_t)(z + 1) * pstride];
+                const float a2 = pp[(size_t)(z + 2) * pstride], a3 = pp[(size_t)(z + 3) * pstride];
+                s += a0; s += a1; s += a2; s += a3;
+            }
+            for (; z < nsplit; z++) s += pp[(size_t)z * pstride];
+        }
         S[i + c * OUTER_NB] = s;
     }
     if (Tb) {
@@ -508,8 +615,9 @@ k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, f
     extern __shared__ float sm[];
     float *Ts = sm;                                  // 128 x 128 column-major
     float *Pm = sm + OUTER_NB * OUTER_NB;            // 96 x 32 scratch
+    float *Gs = Pm + 96 * 32;                        // G staged, 128 x 128
     const int tid = threadIdx.x;
-    for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) Ts[e] = 0.f;
+    for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) { Ts[e] = 0.f; Gs[e] = G[e]; }
     __syncthreads();
     const int nblk = ceil_div(nr, 32);
     for (int b = 0; b < nblk; b++)
@@ -524,7 +632,7 @@ k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, f
         for (int e = tid; e < h * 32; e += 256) {
             const int i = e % h, c = e / h;
             float s = 0.f;
-            for (int k = 0; k < 32; k++) s = fmaf(G[i + (h + k) * OUTER_NB], Ts[(h + k) + (h + c) * OUTER_NB], s);
+            for (int k = 0; k < 32; k++) s = fmaf(Gs[i + (h + k) * OUTER_NB], Ts[(h + k) + (h + c) * OUTER_NB], s);
             Pm[i + c * 96] = s;
         }
         __syncthreads();
@@ -585,6 +693,33 @@ static int launch_larfb(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+// Inner update of nc (<= 96) columns on one cluster (fused kernel).
+static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int L, float *C, int ldc, int nc,
+                           cudaStream_t s)
+{
+    auto kern = k_inner_cl<32>;
+    static bool attr = false;
+    if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); attr = true; }
+    int want = ceil_div(L, 256);
+    if (want > 16) want = 16;
+    const int cs = cluster_size_for((const void *)kern, 256, 0, want);
+    const int chunk = ceil_div(L, cs);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ProfScope ps(K_LARFB, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, V, ldv, kb, L, C, ldc, nc, Tw, chunk);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
 // Inner update of nc (<= 96) columns: three row-parallel kernels.
 template <typename T>
 static int inner_update(const T *V, int ldv, const T *Tw, int kb, int L, T *C, int ldc, int nc, T *P, T *W,
@@ -593,6 +728,8 @@ static int inner_update(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
     constexpr int NB = panel_nb<T>();
     if (nc <= 0 || L <= 0 || kb <= 0) return 0;
     if (nc > INNER_MAXC) return launch_larfb<T>(V, ldv, Tw, kb, L, C, ldc, nc, 1, s);
+    if (sizeof(T) == 4)
+        return inner_update_cl((const float *)V, ldv, (const float *)Tw, kb, L, (float *)C, ldc, nc, s);
     const int nch = ceil_div(L, INNER_ROWS);
     ProfScope ps(K_LARFB, s);
     k_inner_w<T, NB><<<nch, 256, 0, s>>>(V, ldv, kb, L, C, ldc, nc, P);
@@ -719,7 +856,7 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
                                                      w.G, OUTER_NB, 0);
     }
     {
-        const size_t smem = (size_t)(OUTER_NB * OUTER_NB + 96 * 32) * 4;
+        const size_t smem = (size_t)(2 * OUTER_NB * OUTER_NB + 96 * 32) * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_outer_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
         k_outer_T<<<1, 256, smem, s>>>(Tw32, w.G, nr, Tb);

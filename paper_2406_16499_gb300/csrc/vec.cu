@@ -195,15 +195,23 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
             const T tv = Tb[i + (size_t)k * NBV];
             if (trans) Ts[k + i * NBV] = tv; else Ts[i + k * NBV] = tv;
         }
-        // 1. partial dots
+        // 1. partial dots (rows unrolled by 4 for memory-level parallelism)
         for (int c = warp; c < NBV; c += NWARP) {
             T acc = T(0);
             if (c < kb) {
                 const int j = j0 + c;
                 const T *vc = V + (size_t)j * ldv;
-                for (int i = max(s0, j) + lane; i < s1; i += 32) {
-                    const T v = i == j ? T(1) : vc[i];
-                    acc = fma(v, xs[i - s0], acc);
+                const int ib = max(s0, j);
+                for (int i0 = ib; i0 < s1; i0 += 128) {
+                    T vv[4], xx[4];
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const int i = i0 + lane + 32 * u;
+                        vv[u] = i < s1 ? (i == j ? T(1) : vc[i]) : T(0);
+                        xx[u] = i < s1 ? xs[i - s0] : T(0);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 4; u++) acc = fma(vv[u], xx[u], acc);
                 }
             }
             acc = warp_sum(acc);
@@ -224,14 +232,19 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
             wp[tid] = tid < kb ? sacc : T(0);
         }
         __syncthreads();
-        // 4. update the owned rows
+        // 4. update the owned rows (wp[c] = 0 for c >= kb; 16 loads in flight)
         for (int i = max(s0, j0) + tid; i < s1; i += VEC_CL_THREADS) {
             T d = T(0);
             const int cmax = min(kb, i - j0 + 1);
-            for (int c = 0; c < cmax; c++) {
-                const int j = j0 + c;
-                const T v = i == j ? T(1) : V[(size_t)j * ldv + i];
-                d = fma(v, wp[c], d);
+            for (int c0 = 0; c0 < cmax; c0 += 16) {
+                T vv[16];
+#pragma unroll
+                for (int u = 0; u < 16; u++) {
+                    const int c = c0 + u, j = j0 + c;
+                    vv[u] = c < cmax ? (i == j ? T(1) : V[(size_t)j * ldv + i]) : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 16; u++) d = fma(vv[u], wp[(c0 + u) & (NBV - 1)], d);
             }
             xs[i - s0] -= d;
         }
@@ -239,27 +252,6 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
     }
     for (int i = s0 + tid; i < s1; i += VEC_CL_THREADS) x[i] = xs[i - s0];
     cluster.sync();   // keep shared memory alive until every remote read is done
-}
-
-static int cluster_size_for(const void *kern, int threads, size_t smem, int want)
-{
-    if (want <= 1) return 1;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(want, 1, 1);
-    cfg.blockDim = dim3(threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = want;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    int maxc = 0;
-    if (cudaOccupancyMaxPotentialClusterSize(&maxc, kern, &cfg) != cudaSuccess) { cudaGetLastError(); maxc = 8; }
-    int c = 1;
-    while (c * 2 <= want && c * 2 <= maxc) c *= 2;
-    return c;
 }
 
 template <typename T, int NBV>
@@ -326,6 +318,7 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
     T *xs = reinterpret_cast<T *>(smem_raw);
     __shared__ T xb[2][32];
     __shared__ T xl[32];
+    __shared__ T dg[32][33];       // the diagonal block, staged before the solve
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -341,25 +334,30 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
         const int par = t & 1;
         const int owner = r0 / slice;
         if (crank == owner && warp == 0) {
+            // stage the 32 x 32 diagonal block (all loads in flight at once)
+#pragma unroll
+            for (int c = 0; c < 32; c++)
+                dg[lane][c] = (c < bs && lane < bs) ? U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
+            __syncwarp();
             T rhs = lane < bs ? xs[r0 + lane - s0] : T(0);
             T xv = T(0);
             if (!trans) {
                 for (int c = bs - 1; c >= 0; c--) {
-                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    const T dcc = dg[c][c];
                     T xc = __shfl_sync(0xffffffffu, rhs, c);
                     if (dcc == T(0) && lane == 0) atomicOr(status, 2);
                     xc = xc / dcc;
                     if (lane == c) xv = xc;
-                    if (lane < c) rhs = fma(-U[idx2(r0 + lane, r0 + c, ldu)], xc, rhs);
+                    if (lane < c) rhs = fma(-dg[lane][c], xc, rhs);
                 }
             } else {
                 for (int c = 0; c < bs; c++) {
-                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    const T dcc = dg[c][c];
                     T xc = __shfl_sync(0xffffffffu, rhs, c);
                     if (dcc == T(0) && lane == 0) atomicOr(status, 2);
                     xc = xc / dcc;
                     if (lane == c) xv = xc;
-                    if (lane > c && lane < bs) rhs = fma(-U[idx2(r0 + c, r0 + lane, ldu)], xc, rhs);
+                    if (lane > c && lane < bs) rhs = fma(-dg[c][lane], xc, rhs);
                 }
             }
             if (lane < bs) xs[r0 + lane - s0] = xv;
@@ -368,11 +366,15 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
         cluster.sync();
         if (tid < 32) xl[tid] = *cluster.map_shared_rank(&xb[par][tid], owner);
         __syncthreads();
+        // xl[c] = 0 for c >= bs, so the 32-term loops below need no bound
         if (!trans) {
             const int hi = min(s1, r0);
             for (int i = s0 + tid; i < hi; i += VEC_CL_THREADS) {
+                const T *urow = U + idx2(i, r0, ldu);
                 T d = T(0);
-                for (int c = 0; c < bs; c++) d = fma(U[idx2(i, r0 + c, ldu)], xl[c], d);
+#pragma unroll
+                for (int c = 0; c < 32; c++)
+                    if (c < bs) d = fma(urow[(size_t)c * ldu], xl[c], d);
                 xs[i - s0] -= d;
             }
         } else {
@@ -380,7 +382,9 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
             for (int i = lo + tid; i < s1; i += VEC_CL_THREADS) {
                 const T *ucol = U + idx2(r0, i, ldu);
                 T d = T(0);
-                for (int c = 0; c < bs; c++) d = fma(ucol[c], xl[c], d);
+#pragma unroll
+                for (int c = 0; c < 32; c++)
+                    if (c < bs) d = fma(ucol[c], xl[c], d);
                 xs[i - s0] -= d;
             }
         }
