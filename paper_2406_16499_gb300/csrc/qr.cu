@@ -76,87 +76,100 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
             a[q][c] = (rr[q] >= 0 && c < ncols) ? col[rr[q]] : T(0);
     }
 
+    // Runtime column loop (a fully unrolled loop overflows the instruction
+    // cache); register-array indices stay compile-time through predication.
+#pragma unroll 1
+    for (int kk = 0; kk < kpanel; kk++) {
+        const int par = kk & 1;
+        // pivot-column value of each owned row (select chain, no dynamic index)
+        T akk[RPT];
 #pragma unroll
-    for (int kk = 0; kk < NB; kk++) {
-        if (kk < kpanel) {
-            const int par = kk & 1;
-            // the reduction runs in halves of H columns to bound the number
-            // of live accumulators (registers hold the panel itself)
-            constexpr int H = NB > 16 ? 16 : NB;
+        for (int q = 0; q < RPT; q++) {
+            T v = T(0);
 #pragma unroll
-            for (int h0 = 0; h0 < NB; h0 += H) {
-                T acc[H];
+            for (int c = 0; c < NB; c++) v = (c == kk) ? a[q][c] : v;
+            akk[q] = v;
+        }
+        // the reduction runs in halves of H columns to bound the number of
+        // live accumulators (registers hold the panel itself)
+        constexpr int H = NB > 16 ? 16 : NB;
 #pragma unroll
-                for (int c = 0; c < H; c++) acc[c] = T(0);
+        for (int h0 = 0; h0 < NB; h0 += H) {
+            T acc[H];
 #pragma unroll
-                for (int q = 0; q < RPT; q++) {
-                    const T ak = rr[q] > kk ? a[q][kk] : T(0);   // rows below the pivot
-#pragma unroll
-                    for (int c = 0; c < H; c++) acc[c] = fma(ak, a[q][h0 + c], acc[c]);
-                }
-                T wsum = warp_transpose_reduce<T, H>(acc);
-                if (lane < H) red_s[par][warp][h0 + lane] = wsum;
-            }
+            for (int c = 0; c < H; c++) acc[c] = T(0);
 #pragma unroll
             for (int q = 0; q < RPT; q++) {
-                if (rr[q] == kk) {
+                const T ak = rr[q] > kk ? akk[q] : T(0);   // rows below the pivot
 #pragma unroll
-                    for (int c = 0; c < NB; c++) prow[par][c] = a[q][c];
-                }
+                for (int c = 0; c < H; c++) acc[c] = fma(ak, a[q][h0 + c], acc[c]);
             }
+            T wsum = warp_transpose_reduce<T, H>(acc);
+            if (lane < H) red_s[par][warp][h0 + lane] = wsum;
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; q++) {
+            if (rr[q] == kk) {
+#pragma unroll
+                for (int c = 0; c < NB; c++) prow[par][c] = a[q][c];
+            }
+        }
+        __syncthreads();
+        // every warp forms the column totals and the coefficients itself
+        T tot = T(0), pj = T(0);
+        if (cs == 1) {
+            if (lane < NB) {
+#pragma unroll
+                for (int w = 0; w < NW; w++) tot += red_s[par][w][lane];
+                pj = prow[par][lane];
+            }
+        } else {
+            if (warp == 0 && lane < NB) {
+                T t = T(0);
+#pragma unroll
+                for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
+                xbuf[par][lane] = t;
+            }
+            cluster.sync();
+            if (warp < cs && lane < NB) gbuf[par][warp][lane] = *cluster.map_shared_rank(&xbuf[par][lane], warp);
+            if (warp == NW - 1 && lane < NB) prow_l[par][lane] = *cluster.map_shared_rank(&prow[par][lane], 0);
             __syncthreads();
-            // every warp forms the column totals and the coefficients itself
-            T tot = T(0), pj = T(0);
-            if (cs == 1) {
-                if (lane < NB) {
-#pragma unroll
-                    for (int w = 0; w < NW; w++) tot += red_s[par][w][lane];
-                    pj = prow[par][lane];
-                }
-            } else {
-                if (warp == 0 && lane < NB) {
-                    T t = T(0);
-#pragma unroll
-                    for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
-                    xbuf[par][lane] = t;
-                }
-                cluster.sync();
-                if (warp < cs && lane < NB) gbuf[par][warp][lane] = *cluster.map_shared_rank(&xbuf[par][lane], warp);
-                if (warp == NW - 1 && lane < NB) prow_l[par][lane] = *cluster.map_shared_rank(&prow[par][lane], 0);
-                __syncthreads();
-                if (lane < NB) {
-                    for (int r = 0; r < cs; r++) tot += gbuf[par][r][lane];
-                    pj = prow_l[par][lane];
-                }
+            if (lane < NB) {
+                for (int r = 0; r < cs; r++) tot += gbuf[par][r][lane];
+                pj = prow_l[par][lane];
             }
-            const T alpha = __shfl_sync(0xffffffffu, pj, kk);
-            const T sp = __shfl_sync(0xffffffffu, tot, kk);
-            T beta, tv, scale;
-            if (sp == T(0)) {
-                tv = T(0); beta = alpha; scale = T(1);
-            } else {
-                const T nrm = sqrt(alpha * alpha + sp);
-                beta = alpha >= T(0) ? -nrm : nrm;
-                tv = (beta - alpha) / beta;
-                scale = T(1) / (alpha - beta);
-            }
-            const T dot = pj + scale * tot;
-            if (lane < NB) coefw[warp][lane] = lane > kk ? tv * dot : T(0);
-            if (warp == 0) {
-                if (lane < kk) G_s[lane][kk] = dot;
-                if (lane == 0) tau_s[kk] = tv;
-            }
-            __syncwarp();
-            // branch-free: f = v_i (scale * a(i,kk) below the pivot, 1 on the
-            // pivot row, 0 above), a(i, c) -= coef_c * f for c > kk
+        }
+        const T alpha = __shfl_sync(0xffffffffu, pj, kk);
+        const T sp = __shfl_sync(0xffffffffu, tot, kk);
+        T beta, tv, scale;
+        if (sp == T(0)) {
+            tv = T(0); beta = alpha; scale = T(1);
+        } else {
+            const T nrm = sqrt(alpha * alpha + sp);
+            beta = alpha >= T(0) ? -nrm : nrm;
+            tv = (beta - alpha) / beta;
+            scale = T(1) / (alpha - beta);
+        }
+        const T dot = pj + scale * tot;
+        if (lane < NB) coefw[warp][lane] = lane > kk ? tv * dot : T(0);
+        if (warp == 0) {
+            if (lane < kk) G_s[lane][kk] = dot;
+            if (lane == 0) tau_s[kk] = tv;
+        }
+        __syncwarp();
+        // branch-free update: f = v_i (scale * a(i,kk) below the pivot, 1 on
+        // the pivot row, 0 above); a(i, c) -= coef_c * f (coef_c = 0 for
+        // c <= kk); the pivot column becomes v (or beta on the pivot row)
 #pragma unroll
-            for (int q = 0; q < RPT; q++) {
-                const bool below = rr[q] > kk, piv = rr[q] == kk;
-                const T sk = a[q][kk] * scale;
-                const T f = below ? sk : (piv ? T(1) : T(0));
+        for (int q = 0; q < RPT; q++) {
+            const bool below = rr[q] > kk, piv = rr[q] == kk;
+            const T sk = akk[q] * scale;
+            const T f = below ? sk : (piv ? T(1) : T(0));
+            const T newk = below ? sk : (piv ? beta : akk[q]);
 #pragma unroll
-                for (int c = kk + 1; c < NB; c++) a[q][c] = fma(-coefw[warp][c], f, a[q][c]);
-                a[q][kk] = below ? sk : (piv ? beta : a[q][kk]);
+            for (int c = 0; c < NB; c++) {
+                const T upd = fma(-coefw[warp][c], f, a[q][c]);
+                a[q][c] = (c == kk) ? newk : upd;
             }
         }
     }
