@@ -47,18 +47,14 @@ static std::vector<cudaEvent_t> g_ev;
 static std::vector<int> g_kind;
 static size_t g_nrec = 0;
 static bool g_open = false;
-constexpr size_t PROF_CAP = 1 << 16;
+constexpr size_t PROF_CAP = 1 << 14;
 
 void prof_begin(int kind, cudaStream_t s)
 {
     g_launches[kind]++;
-    if (!g_prof || g_nrec >= PROF_CAP) return;
-    if (g_ev.size() < 2 * (g_nrec + 1)) {
-        size_t old = g_ev.size();
-        g_ev.resize(old + 2048);
-        for (size_t i = old; i < g_ev.size(); i++) cudaEventCreate(&g_ev[i]);
-        g_kind.resize(g_ev.size() / 2);
-    }
+    // the event pool is created by mpir_profile(1); launches beyond it are
+    // counted but not timed (no resource is created on the launch path)
+    if (!g_prof || 2 * (g_nrec + 1) > g_ev.size()) return;
     cudaEventRecord(g_ev[2 * g_nrec], s);
     g_open = true;
 }
@@ -872,6 +868,12 @@ int mpir_profile(int enable)
     g_prof = enable != 0;
     g_nrec = 0;
     g_open = false;
+    if (g_prof && g_ev.size() < 2 * PROF_CAP) {
+        const size_t old = g_ev.size();
+        g_ev.resize(2 * PROF_CAP);
+        for (size_t i = old; i < g_ev.size(); i++) cudaEventCreate(&g_ev[i]);
+        g_kind.resize(PROF_CAP);
+    }
     return 0;
 }
 

@@ -46,6 +46,24 @@ def logspace_sigma(k, cond, top=1.0):
     return top * np.logspace(0.0, -np.log10(cond), k)
 
 
+def latm1_sigma(k, cond, mode=3):
+    """Singular values with condition number `cond` in the three xLATM1-style
+    patterns the paper's generator can produce (the paper does not say which
+    one it used): mode 1 one large value (1, 1/cond, ..., 1/cond), mode 2 one
+    small value (1, ..., 1, 1/cond), mode 3 geometric spacing."""
+    if k <= 1:
+        return np.ones(max(k, 0))
+    if mode == 1:
+        s = np.full(k, 1.0 / cond)
+        s[0] = 1.0
+        return s
+    if mode == 2:
+        s = np.ones(k)
+        s[-1] = 1.0 / cond
+        return s
+    return logspace_sigma(k, cond)
+
+
 def svd_matrix(g, rows, cols, sigma):
     """U diag(sigma) V^T, U rows x r, V cols x r, r = len(sigma)."""
     r = len(sigma)
@@ -56,10 +74,11 @@ def svd_matrix(g, rows, cols, sigma):
 
 # ------------------------------------------------------------------ LSE --
 
-def lse_paper(seed, m, n, p, kappa):
-    """[A^T, B^T] = W1 Sigma W2 with kappa_2([A; B]) = kappa (Sec. 6.2)."""
+def lse_paper(seed, m, n, p, kappa, mode=3):
+    """[A^T, B^T] = W1 Sigma W2 with kappa_2([A; B]) = kappa (Sec. 6.2);
+    `mode` selects the singular-value pattern (latm1_sigma)."""
     g = rng(seed)
-    sigma = logspace_sigma(n, kappa)
+    sigma = latm1_sigma(n, kappa, mode)
     AB = svd_matrix(g, m + p, n, sigma)
     A = np.asfortranarray(AB[:m])
     B = np.asfortranarray(AB[m:])
@@ -140,10 +159,10 @@ def gls_ar1(seed=20242623, n=4096, m=1024, cond_w=1e3, rho=0.9):
     return dict(W=W, V=V, d=d)
 
 
-def gls_paper(seed, n, m, p, kappa):
+def gls_paper(seed, n, m, p, kappa, mode=3):
     """[W, V] = W1 Sigma W2 with kappa_2([W, V]) = kappa (Sec. 6.3)."""
     g = rng(seed)
-    sigma = logspace_sigma(n, kappa)
+    sigma = latm1_sigma(n, kappa, mode)
     WV = svd_matrix(g, n, m + p, sigma)
     W = np.asfortranarray(WV[:, :m])
     V = np.asfortranarray(WV[:, m:])
