@@ -298,6 +298,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         if (ok) {
 #pragma unroll 1
             for (int c0 = 0; c0 < TC_BN; c0 += 32) {
+                // SUB: issue the 32 loads of C first (independent, coalesced
+                // across the warp), then read the accumulator and store
+                float cv[32];
+                if (EPI == TCE_SUB) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int col = n_tile * TC_BN + c0 + j;
+                        cv[j] = (row < args.M && col < args.N) ? args.out[(size_t)col * args.ldo + row] : 0.f;
+                    }
+                }
                 float v[32];
                 tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)c0, v);
                 if (row < args.M) {
@@ -305,12 +315,10 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     for (int j = 0; j < 32; j++) {
                         const int col = n_tile * TC_BN + c0 + j;
                         if (col < args.N) {
-                            if (EPI == TCE_STORE) {
+                            if (EPI == TCE_STORE)
                                 args.out[(size_t)z * args.split_stride + (size_t)col * args.ldo + row] = v[j];
-                            } else {
-                                float *c = args.out + (size_t)col * args.ldo + row;
-                                *c -= v[j];
-                            }
+                            else
+                                args.out[(size_t)col * args.ldo + row] = cv[j] - v[j];
                         }
                     }
                 }

@@ -79,8 +79,13 @@ int apply_reflectors_vec_blk(const T *V, int ldv, int M, int K, const T *Tw, int
 
 // Solve U x = b (trans = 0) or U^T x = b (trans = 1) in place, U upper
 // triangular n x n (ldu).  Zero diagonal -> bit 1 of *sc.status.
+// Dinv (optional): inverses of the 32 x 32 diagonal blocks of U from
+// invert_diag32 (the solve then forms each block by a 32-wide product).
 template <typename T>
-int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s);
+int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
+               const T *Dinv = nullptr);
+template <typename T>
+void invert_diag32(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s);
 
 // y <- beta y + alpha op(M) x, M rows x cols (ld); op = M (trans = 0) or M^T.
 // If upper_mask, entries M(i, j) with i > j + diag_off are treated as zero.

@@ -568,31 +568,17 @@ k_prep_v(const float *__restrict__ X, int ldx, int L, int nr, float *__restrict_
 }
 
 // W = op(Tb) * sum_z P[z] (128 x nc), op = Tb^T (trans), Tb, or identity
-// (Tb == NULL); optionally split into W = Wh + Wl.  One block per 32 columns.
+// (Tb == NULL); optionally split into W = Wh + Wl.  One block per 16 columns.
+constexpr int RW_COLS = 16;
 __global__ void __launch_bounds__(256)
 k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, const float *__restrict__ Tb,
            int trans, int nc, float *__restrict__ Wh, float *__restrict__ Wl, int ldw, int split)
 {
     extern __shared__ float sm[];
-    float *S = sm;                                   // [32 cols][128] (column-major 128 x 32)
-    float *Xs = sm + 32 * OUTER_NB;                  // 128 x 128 column-major (x(i,k) at i + 128 k)
+    float *S = sm;                                   // 128 x RW_COLS, column-major
+    float *Xs = sm + RW_COLS * OUTER_NB;             // 128 x 128 column-major (x(i,k) at i + 128 k)
     const int tid = threadIdx.x;
-    const int c0 = blockIdx.x * 32;
-    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
-        const int i = e % OUTER_NB, c = e / OUTER_NB;
-        float s = 0.f;
-        if (c0 + c < nc) {
-            const float *pp = P + (size_t)(c0 + c) * ldp + i;
-            int z = 0;
-            for (; z + 4 <= nsplit; z += 4) {
-                const float a0 = pp[(size_t)z * pstride], a1 = pp[(size_t)(z + 1) * pstride];
-                const float a2 = pp[(size_t)(z + 2) * pstride], a3 = pp[(size_t)(z + 3) * pstride];
-                s += a0; s += a1; s += a2; s += a3;
-            }
-            for (; z < nsplit; z++) s += pp[(size_t)z * pstride];
-        }
-        S[i + c * OUTER_NB] = s;
-    }
+    const int c0 = blockIdx.x * RW_COLS;
     if (Tb) {
         for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) {
             const int i = e % OUTER_NB, k = e / OUTER_NB;
@@ -600,13 +586,31 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
             if (trans) Xs[k + i * OUTER_NB] = t; else Xs[i + k * OUTER_NB] = t;
         }
     }
+    for (int e = tid; e < RW_COLS * OUTER_NB; e += 256) {
+        const int i = e % OUTER_NB, c = e / OUTER_NB;
+        float s = 0.f;
+        if (c0 + c < nc) {
+            const float *pp = P + (size_t)(c0 + c) * ldp + i;
+            int z = 0;
+            for (; z + 8 <= nsplit; z += 8) {
+                float a[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) a[u] = pp[(size_t)(z + u) * pstride];
+#pragma unroll
+                for (int u = 0; u < 8; u++) s += a[u];
+            }
+            for (; z < nsplit; z++) s += pp[(size_t)z * pstride];
+        }
+        S[i + c * OUTER_NB] = s;
+    }
     __syncthreads();
-    for (int e = tid; e < 32 * OUTER_NB; e += 256) {
+    for (int e = tid; e < RW_COLS * OUTER_NB; e += 256) {
         const int i = e % OUTER_NB, c = e / OUTER_NB;
         if (c0 + c >= nc) continue;
         float w;
         if (Tb) {
             float s = 0.f;
+#pragma unroll 8
             for (int k = 0; k < OUTER_NB; k++) s = fmaf(Xs[i + k * OUTER_NB], S[k + c * OUTER_NB], s);
             w = s;
         } else {
@@ -833,11 +837,11 @@ static int outer_apply(OuterWs &w, const float *Tb, int trans, int L, float *C, 
     if (rc) return rc;
     {
         ProfScope ps(K_LARFB_AUX, s);
-        const size_t smem = (size_t)(32 + OUTER_NB) * OUTER_NB * 4;
+        const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_reduce_w<<<ceil_div(Nc, 32), 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, Tb, trans, Nc, w.W, w.Wl,
-                                                        OUTER_NB, split);
+        k_reduce_w<<<ceil_div(Nc, RW_COLS), 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, Tb, trans, Nc, w.W,
+                                                             w.Wl, OUTER_NB, split);
     }
     // C -= V W  (M = L, N = Nc, K = 128)
     rc = gemm_tc(mode, 0, TCE_SUB, tVt, tVtl, tW, tWl, 0, 0, 0, 0, L, Nc, OUTER_NB, C, ldc, 0, 1, err, s);
@@ -853,7 +857,7 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     if (rc) return MPIR_UNSUPPORTED;
     const int ksteps = ceil_div(L, 32);
-    int nsplit = ksteps < 64 ? ksteps : 64;
+    int nsplit = ksteps < 24 ? ksteps : 24;
     if (nsplit < 1) nsplit = 1;
     const size_t pstride = (size_t)OUTER_NB * OUTER_NB;
     // G = V^T V with both operands pre-split (w.V holds only the TF32 part)
@@ -862,11 +866,11 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     if (rc) return rc;
     ProfScope ps(K_LARFB_AUX, s);
     {
-        const size_t smem = (size_t)(32 + OUTER_NB) * OUTER_NB * 4;
+        const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_reduce_w<<<OUTER_NB / 32, 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, nullptr, 0, OUTER_NB, w.G,
-                                                     w.G, OUTER_NB, 0);
+        k_reduce_w<<<OUTER_NB / RW_COLS, 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, nullptr, 0, OUTER_NB, w.G,
+                                                          w.G, OUTER_NB, 0);
     }
     {
         const size_t smem = (size_t)(2 * OUTER_NB * OUTER_NB + 96 * 32) * 4;

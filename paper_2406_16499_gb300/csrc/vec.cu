@@ -300,25 +300,73 @@ int apply_reflectors_vec_blk(const T *V, int ldv, int M, int K, const T *Tw, int
 }
 
 // ---------------------------------------------------------------------------
+// Inverses of the 32 x 32 diagonal blocks of an upper triangular N x N
+// matrix (one warp per block, lane j solves column j by back substitution;
+// a partial last block is padded with the identity).  Zero pivot -> bit 1 of
+// *status.  Used by the cluster triangular solve below; the inverse of a
+// leading principal part of a block is the leading part of its inverse, so
+// solves of any leading n <= N reuse them.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_invert_diag32(const T *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, int *__restrict__ status)
+{
+    __shared__ T Us[32][33];
+    __shared__ T Xs[32][33];
+    const int lane = threadIdx.x, blk = blockIdx.x, r0 = blk * 32;
+    for (int c = 0; c < 32; c++) {
+        T v;
+        if (r0 + lane < N && r0 + c < N) v = lane <= c ? U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
+        else v = lane == c ? T(1) : T(0);
+        Us[lane][c] = v;
+    }
+    __syncwarp();
+    const int j = lane;
+    for (int i = 31; i >= 0; i--) {
+        T val = T(0);
+        if (i <= j) {
+            T sum = i == j ? T(1) : T(0);
+            for (int k = i + 1; k <= j; k++) sum = fma(-Us[i][k], Xs[k][j], sum);
+            const T d = Us[i][i];
+            if (d == T(0)) atomicOr(status, 2);
+            val = sum / d;
+        }
+        Xs[i][j] = val;
+    }
+    __syncwarp();
+    for (int i = 0; i < 32; i++) Dinv[(size_t)blk * 1024 + i + 32 * j] = Xs[i][j];
+}
+
+template <typename T>
+void invert_diag32(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
+{
+    if (N <= 0) return;
+    ProfScope ps(K_TRSV, s);
+    k_invert_diag32<T><<<ceil_div(N, 32), 32, 0, s>>>(U, ldu, N, Dinv, status);
+}
+
+// ---------------------------------------------------------------------------
 // Cluster triangular solve with an upper triangular U (n x n):
 //   trans = 0: U x = b  (32-row blocks from the bottom)
 //   trans = 1: U^T x = b (32-row blocks from the top)
-// CTA r owns rows [r*slice, (r+1)*slice) of x (slice a multiple of 32).  Per
-// diagonal block: its owner solves the 32 x 32 triangle in one warp and
-// publishes the values in its shared memory; cluster barrier; every CTA
-// reads them through distributed shared memory and updates its own
-// unsolved rows.  One cluster barrier per 32 rows.
+// CTA r owns rows [r*slice, (r+1)*slice) of x (slice a multiple of 32, at
+// most 1024 = two rows per thread).  Per diagonal block: every thread first
+// issues the loads of the block column of U for its rows (independent of
+// x); the owner forms x_blk = D b_blk with the pre-inverted diagonal block
+// D (or by substitution when no inverses are given) and publishes it;
+// cluster barrier; every CTA reads x_blk through distributed shared memory
+// and updates its unsolved rows.  One cluster barrier per 32 rows.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(VEC_CL_THREADS, 1)
 k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
-          int *__restrict__ status)
+          const T *__restrict__ Dinv, int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
     __shared__ T xb[2][32];
     __shared__ T xl[32];
-    __shared__ T dg[32][33];       // the diagonal block, staged before the solve
+    __shared__ T dg[32][33];
     cg::cluster_group cluster = cg::this_cluster();
     const int crank = (int)cluster.block_rank();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -333,31 +381,56 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
         const int bs = min(32, n - r0);
         const int par = t & 1;
         const int owner = r0 / slice;
-        if (crank == owner && warp == 0) {
-            // stage the 32 x 32 diagonal block (all loads in flight at once)
+        // rows this thread updates after the barrier, and their U entries
+        const int lo = trans ? max(s0, r0 + bs) : s0;
+        const int hi = trans ? s1 : min(s1, r0);
+        constexpr int TROWS = sizeof(T) == 4 ? 2 : 1;    // rows prefetched per thread
+        const int ia = s0 + tid, ib = s0 + tid + VEC_CL_THREADS;
+        const bool va = ia >= lo && ia < hi, vb = TROWS > 1 && ib >= lo && ib < hi;
+        T ua[32], ub[TROWS > 1 ? 32 : 1];
+#pragma unroll
+        for (int c = 0; c < 32; c++)
+            ua[c] = (va && c < bs) ? (trans ? U[idx2(r0 + c, ia, ldu)] : U[idx2(ia, r0 + c, ldu)]) : T(0);
+        if (TROWS > 1) {
 #pragma unroll
             for (int c = 0; c < 32; c++)
-                dg[lane][c] = (c < bs && lane < bs) ? U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
-            __syncwarp();
+                ub[c % (TROWS > 1 ? 32 : 1)] =
+                    (vb && c < bs) ? (trans ? U[idx2(r0 + c, ib, ldu)] : U[idx2(ib, r0 + c, ldu)]) : T(0);
+        }
+        if (crank == owner && warp == 0) {
             T rhs = lane < bs ? xs[r0 + lane - s0] : T(0);
             T xv = T(0);
-            if (!trans) {
-                for (int c = bs - 1; c >= 0; c--) {
-                    const T dcc = dg[c][c];
-                    T xc = __shfl_sync(0xffffffffu, rhs, c);
-                    if (dcc == T(0) && lane == 0) atomicOr(status, 2);
-                    xc = xc / dcc;
-                    if (lane == c) xv = xc;
-                    if (lane < c) rhs = fma(-dg[lane][c], xc, rhs);
-                }
+            if (Dinv) {
+                const T *D = Dinv + (size_t)blk * 1024;
+                T drow[32];
+#pragma unroll
+                for (int k = 0; k < 32; k++) drow[k] = trans ? D[k + 32 * lane] : D[lane + 32 * k];
+#pragma unroll
+                for (int k = 0; k < 32; k++) xv = fma(drow[k], __shfl_sync(0xffffffffu, rhs, k), xv);
+                if (lane >= bs) xv = T(0);
             } else {
-                for (int c = 0; c < bs; c++) {
-                    const T dcc = dg[c][c];
-                    T xc = __shfl_sync(0xffffffffu, rhs, c);
-                    if (dcc == T(0) && lane == 0) atomicOr(status, 2);
-                    xc = xc / dcc;
-                    if (lane == c) xv = xc;
-                    if (lane > c && lane < bs) rhs = fma(-dg[c][lane], xc, rhs);
+#pragma unroll
+                for (int c = 0; c < 32; c++)
+                    dg[lane][c] = (c < bs && lane < bs) ? U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
+                __syncwarp();
+                if (!trans) {
+                    for (int c = bs - 1; c >= 0; c--) {
+                        const T dcc = dg[c][c];
+                        T xc = __shfl_sync(0xffffffffu, rhs, c);
+                        if (dcc == T(0) && lane == 0) atomicOr(status, 2);
+                        xc = xc / dcc;
+                        if (lane == c) xv = xc;
+                        if (lane < c) rhs = fma(-dg[lane][c], xc, rhs);
+                    }
+                } else {
+                    for (int c = 0; c < bs; c++) {
+                        const T dcc = dg[c][c];
+                        T xc = __shfl_sync(0xffffffffu, rhs, c);
+                        if (dcc == T(0) && lane == 0) atomicOr(status, 2);
+                        xc = xc / dcc;
+                        if (lane == c) xv = xc;
+                        if (lane > c && lane < bs) rhs = fma(-dg[c][lane], xc, rhs);
+                    }
                 }
             }
             if (lane < bs) xs[r0 + lane - s0] = xv;
@@ -366,27 +439,17 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
         cluster.sync();
         if (tid < 32) xl[tid] = *cluster.map_shared_rank(&xb[par][tid], owner);
         __syncthreads();
-        // xl[c] = 0 for c >= bs, so the 32-term loops below need no bound
-        if (!trans) {
-            const int hi = min(s1, r0);
-            for (int i = s0 + tid; i < hi; i += VEC_CL_THREADS) {
-                const T *urow = U + idx2(i, r0, ldu);
-                T d = T(0);
+        if (va) {
+            T d = T(0);
 #pragma unroll
-                for (int c = 0; c < 32; c++)
-                    if (c < bs) d = fma(urow[(size_t)c * ldu], xl[c], d);
-                xs[i - s0] -= d;
-            }
-        } else {
-            const int lo = max(s0, r0 + bs);
-            for (int i = lo + tid; i < s1; i += VEC_CL_THREADS) {
-                const T *ucol = U + idx2(r0, i, ldu);
-                T d = T(0);
+            for (int c = 0; c < 32; c++) d = fma(ua[c], xl[c], d);
+            xs[ia - s0] -= d;
+        }
+        if (TROWS > 1 && vb) {
+            T d = T(0);
 #pragma unroll
-                for (int c = 0; c < 32; c++)
-                    if (c < bs) d = fma(ucol[c], xl[c], d);
-                xs[i - s0] -= d;
-            }
+            for (int c = 0; c < 32; c++) d = fma(ub[c % (TROWS > 1 ? 32 : 1)], xl[c], d);
+            xs[ib - s0] -= d;
         }
         __syncthreads();
     }
@@ -477,7 +540,8 @@ k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__
 }
 
 template <typename T>
-static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
+static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
+                         const T *Dinv)
 {
     auto kern = k_trsv_cl<T>;
     const int nblk = ceil_div(n, 32);
@@ -493,7 +557,7 @@ static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevS
     const int slice = ceil_div(nblk, cs) * 32;
     cs = ceil_div(n, slice);
     const size_t smem = (size_t)slice * sizeof(T);
-    if (smem > 128 * 1024) return -1;
+    if (slice > (sizeof(T) == 4 ? 2 : 1) * VEC_CL_THREADS) return -1;   // rows a thread can prefetch
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(VEC_CL_THREADS, 1, 1);
@@ -507,16 +571,16 @@ static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevS
     cfg.attrs = at;
     cfg.numAttrs = 1;
     ProfScope ps(K_TRSV, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, sc.status);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv, sc.status);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
 template <typename T>
-int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
+int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s, const T *Dinv)
 {
     if (n <= 0) return 0;
     {
-        const int rc = trsv_upper_cl<T>(U, ldu, n, trans, x, sc, s);
+        const int rc = trsv_upper_cl<T>(U, ldu, n, trans, x, sc, s, Dinv);
         if (rc >= 0) return rc;          // -1: too large for one cluster, use the grid version
     }
     auto kern = k_trsv_upper<T>;
@@ -786,8 +850,12 @@ template int apply_reflectors_vec_blk<float>(const float *, int, int, int, const
                                              cudaStream_t);
 template int apply_reflectors_vec_blk<double>(const double *, int, int, int, const double *, int, int, double *,
                                               cudaStream_t);
-template int trsv_upper<float>(const float *, int, int, int, float *, const DevScratch &, cudaStream_t);
-template int trsv_upper<double>(const double *, int, int, int, double *, const DevScratch &, cudaStream_t);
+template int trsv_upper<float>(const float *, int, int, int, float *, const DevScratch &, cudaStream_t,
+                               const float *);
+template int trsv_upper<double>(const double *, int, int, int, double *, const DevScratch &, cudaStream_t,
+                                const double *);
+template void invert_diag32<float>(const float *, int, int, float *, int *, cudaStream_t);
+template void invert_diag32<double>(const double *, int, int, double *, int *, cudaStream_t);
 template int gemv<float>(const float *, int, int, int, int, float, const float *, float, float *, int, int,
                          cudaStream_t);
 template int gemv<double>(const double *, int, int, int, int, double, const double *, double, double *, int,
