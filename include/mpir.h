@@ -250,6 +250,31 @@ int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
 int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int ldv,
                const float *T, int trans, float *C, int ldc);
 
+/* GLS residual without any allocation.  The paper has no counterpart: this
+ * is an interface for callers that cannot call cudaMalloc -- code running
+ * while a CUDA graph is being captured (allocation is not allowed there),
+ * framework plug-ins whose host owns every device allocation through its own
+ * pool, and real-time loops that must not enter the driver's allocator.
+ * Same arithmetic and outputs as mpir_gls_residual (f1, f2, f3 as there;
+ * norms2: a DEVICE array of 6 doubles receiving the squared norms of f1, f2,
+ * f3, x, y, z, or NULL), enqueued on `stream` (a cudaStream_t), without a
+ * handle.  Its scratch is a fixed file-scope device array of 4 MiB
+ * (524288 doubles) that every GPU loading the library holds until the
+ * process exits; shapes whose partial sums exceed it
+ * (ceil(m/256)*n + ceil(n/256)*m + ceil(p/256)*n + ceil(n/256)*p + 1832
+ * doubles; e.g. n = m = p = 4096 needs 264k) return MPIR_UNSUPPORTED.
+ * The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and leaves
+ * its contents behind, so calls whose GPU work overlaps (two streams, two
+ * host threads) race and must be serialized by the caller.  Returns 0, a
+ * negative argument index, MPIR_UNSUPPORTED or MPIR_CUDA_ERROR. */
+int mpir_gls_residual_noalloc(int n, int m, int p, const double *W, int ldw,
+                              const double *V, int ldv, const double *d,
+                              const double *x, const double *y, const double *z,
+                              double *f1, double *f2, double *f3, double *norms2,
+                              void *stream);
+
 /* Library version string. */
 const char *mpir_version(void);
 

@@ -75,6 +75,7 @@ _SIG = {
     "mpir_lse_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_gls_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_larfb": ([_P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I], _I),
+    "mpir_gls_residual_noalloc": ([_I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
     "mpir_launch_count": ([_I], ctypes.c_longlong),
@@ -99,6 +100,19 @@ def profile_read():
 
 def launch_count(kind=-1):
     return int(lib().mpir_launch_count(kind))
+
+
+def gls_residual_noalloc(W, V, d, x, y, z, f1, f2, f3, norms2=None, stream=None):
+    """mpir_gls_residual_noalloc on CUDA tensors (no handle, no allocation
+    inside the library); norms2: optional CUDA tensor of 6 doubles."""
+    import torch
+    n, m = W.shape
+    p = V.shape[1]
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    return int(lib().mpir_gls_residual_noalloc(n, m, p, ptr(W), ld(W), ptr(V), ld(V), ptr(d), ptr(x), ptr(y),
+                                               ptr(z), ptr(f1), ptr(f2), ptr(f3), ptr(norms2),
+                                               ctypes.c_void_p(stream)))
 
 
 def library_path():
