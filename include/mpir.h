@@ -238,6 +238,29 @@ int mpir_lse_correction(mpir_handle h, const double *f1, const double *f2,
 int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
                         const double *f3, double *dy, double *dz, double *dx);
 
+/* GMRES-IR building blocks (Sec. 5.2 / 5.3) on the held factors: the
+ * scaled augmented operator and the block-diagonal split preconditioners,
+ * in FP64 arithmetic on FP64 vectors (factors read in their storage
+ * precision).  which: 0 -> F~(alpha, beta) u, 1 -> M_l u, 2 -> M_r u,
+ * 3 -> M_l F~ M_r u.
+ * LSE (needs m >= n): vectors of length m + p + n ordered [m; p; n],
+ *   F~ = [a I, 0, A; 0, 0, b B; A^T, b B^T, 0],
+ *   M_l = diag(a^-1/2 I, a^-1/2 b^-1 S R^-1, a^1/2 T1^-T Q),
+ *   M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-T S^T, a^1/2 Q^T T1^-1),
+ *   T1 the leading n x n of T, S its trailing p x p.
+ * GLS (needs n <= p): vectors of length p + n + m ordered [p; n; m],
+ *   F~ = [a I, V^T, 0; V, 0, b W; 0, b W^T, 0],
+ *   M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^T, a^-1/2 b^-1 S^T R^-T),
+ *   M_r = diag(a^-1/2 I, a^1/2 Q T2^-T, a^-1/2 b^-1 R^-1 S),
+ *   T = [0, T2], S the leading m x m of T2.
+ * A, B (W, V): the FP64 matrices that were factored.  alpha, beta > 0.
+ * in, out: device arrays, distinct.  Returns 0, a negative argument index,
+ * or MPIR_UNSUPPORTED (no matching factors held, or the shape condition). */
+int mpir_lse_bd_apply(mpir_handle h, const double *A, int lda, const double *B, int ldb,
+                      double alpha, double beta, int which, const double *in, double *out);
+int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, int ldv,
+                      double alpha, double beta, int which, const double *in, double *out);
+
 /* Stage 2-4 building block (xLARFB with a 128-reflector block on the
  * tensor cores): C <- (I - V X V^T) C with X = T^T (trans = 1) or T
  * (trans = 0).  V: the unit lower trapezoid of the M x K panel at V (ldv;
@@ -285,7 +308,8 @@ const char *mpir_version(void);
  * returns, per kind, the summed event time (ms) and the number of timed
  * launches.  Kinds: 0 panel_qr, 1 larfb, 2 vec_apply, 3 trsv, 4 gemv,
  * 5 dual_gemv_fp64, 6 resid_finalize, 7 convert, 8 norm, 9 elementwise,
- * 10 larfb_tc (tcgen05 GEMM), 11 larfb_aux (V / W preparation).
+ * 10 larfb_tc (tcgen05 GEMM), 11 larfb_aux (V / W preparation), 12 gmres
+ * (Arnoldi steps and cycle updates).
  * Not thread-safe; a profiling aid, off by default. */
 int mpir_profile(int enable);
 int mpir_profile_read(double *ms, long long *launches, int nkinds);

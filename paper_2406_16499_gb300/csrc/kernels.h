@@ -9,7 +9,7 @@ namespace mpir {
 // Kernel kinds for the launch counter and the optional per-kind timers.
 enum KernelKind {
     K_PANEL = 0, K_LARFB, K_VEC_APPLY, K_TRSV, K_GEMV, K_DUAL_GEMV, K_FINALIZE, K_CONVERT, K_NORM,
-    K_ELEMWISE, K_LARFB_TC, K_LARFB_AUX, K_NKINDS
+    K_ELEMWISE, K_LARFB_TC, K_LARFB_AUX, K_GMRES, K_NKINDS
 };
 // Called around every kernel launch: counts the launch and, when timing is
 // enabled (mpir_profile), records a CUDA event pair on the launch stream.
@@ -73,9 +73,15 @@ int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int tra
 // Same as apply_reflectors_vec with blocks of nbv reflectors whose
 // compact-WY factors are in Tw (nbv x nbv each, ld nbv): one thread-block
 // cluster, one cluster barrier per block (nbv in {16, 32, 128}).
-template <typename T>
-int apply_reflectors_vec_blk(const T *V, int ldv, int M, int K, const T *Tw, int nbv, int trans, T *x,
+template <typename TS, typename T>
+int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, int nbv, int trans, T *x,
                              cudaStream_t s);
+// Mixed precision (factors stored as TS, arithmetic and vectors in T).
+template <typename TS, typename T>
+int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s);
+template <typename TS, typename T>
+int gemv_mixed(const TS *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
+               int upper_mask, int diag_off, cudaStream_t s);
 
 // Solve U x = b (trans = 0) or U^T x = b (trans = 1) in place, U upper
 // triangular n x n (ldu).  Zero diagonal -> bit 1 of *sc.status.

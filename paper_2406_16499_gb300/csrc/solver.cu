@@ -32,6 +32,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "gmres.h"
 #include "kernels.h"
 #include "mpir.h"
 
@@ -71,7 +72,7 @@ void prof_end(int kind, cudaStream_t s)
 
 static const char *g_kind_names[K_NKINDS] = {"panel_qr", "larfb", "vec_apply", "trsv", "gemv",
                                              "dual_gemv_fp64", "resid_finalize", "convert", "norm",
-                                             "elementwise", "larfb_tc", "larfb_aux"};
+                                             "elementwise", "larfb_tc", "larfb_aux", "gmres"};
 
 #define MPIR_VERSION_STRING "libmpir 0.1 (sm_103a)"
 
@@ -337,8 +338,8 @@ template <typename T>
 int vapply(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, int trans, T *x, const DevScratch &,
            cudaStream_t s)
 {
-    if (sizeof(T) == 4) return apply_reflectors_vec_blk<T>(V, ldv, M, K, Tw128, OUTER_NB, trans, x, s);
-    return apply_reflectors_vec_blk<T>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
+    if (sizeof(T) == 4) return apply_reflectors_vec_blk<T, T>(V, ldv, M, K, Tw128, OUTER_NB, trans, x, s);
+    return apply_reflectors_vec_blk<T, T>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
 }
 
 // T-vector combine: out[i] = alpha * a[ra ? n-1-i : i] + beta * b[rb ? n-1-i : i]
@@ -563,21 +564,219 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b)
     return t;
 }
 
+
+// ============================================== GMRES-IR (Sec. 5) ==
+// Block-diagonal split preconditioners built from the held factors and
+// applied in FP64 arithmetic to FP64 vectors (the factors stay in their
+// storage precision), the scaled augmented operator F~(alpha, beta) on the
+// FP64 originals, and the outer loop that solves each correction system with
+// restarted GMRES instead of Alg. 1 / Alg. 3.
+//
+// Scaled factors.  The factors held are those of sA A, sB B (sW W, sV V), so
+// R = R'/sB, T = T'/sA for LSE (R = R'/sW, T = T'/sV for GLS); the scalars
+// below fold these ratios into the preconditioner's block scalings.
+
+// Scratch of the operator and of the GMRES engine.
+struct BDScratch {
+    GmresWs gw;
+    double *rhs, *t, *u, *gf, *w1, *w2, *w3;
+};
+
+size_t bd_bytes(int N, int R, int mx)
+{
+    size_t b = gmres_ws_bytes(N, R);
+    const size_t vn = ((size_t)N * sizeof(double) + 255) & ~(size_t)255;
+    const size_t vm = ((size_t)std::max(mx, 1) * sizeof(double) + 255) & ~(size_t)255;
+    return b + 4 * vn + 3 * vm;
+}
+
+BDScratch bd_layout(void *base, int N, int R, int mx)
+{
+    BDScratch b{};
+    b.gw = gmres_layout(base, N, R);
+    Carver c((char *)base + gmres_ws_bytes(N, R));
+    b.rhs = c.take<double>(N); b.t = c.take<double>(N); b.u = c.take<double>(N); b.gf = c.take<double>(N);
+    b.w1 = c.take<double>(std::max(mx, 1)); b.w2 = c.take<double>(std::max(mx, 1));
+    b.w3 = c.take<double>(std::max(mx, 1));
+    return b;
+}
+
+// Triangular solve and gemv in FP64 arithmetic on factors stored as T.
+template <typename T>
+int trsv_d(const T *U, int ldu, int n, int trans, double *x, const DevScratch &sc, cudaStream_t s)
+{
+    return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s);
+}
+template <typename T>
+int gemv_d(const T *M, int ld, int rows, int cols, int trans, double alpha, const double *x, double beta, double *y,
+           int upper_mask, int diag_off, cudaStream_t s)
+{
+    return gemv_mixed<T, double>(M, ld, rows, cols, trans, alpha, x, beta, y, upper_mask, diag_off, s);
+}
+
+// Reflector set applied in FP64 arithmetic to an FP64 vector.
+template <typename T>
+int vapply_d(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, int trans, double *x, cudaStream_t s)
+{
+    if (sizeof(T) == 4) return apply_reflectors_vec_blk<T, double>(V, ldv, M, K, Tw128, OUTER_NB, trans, x, s);
+    return apply_reflectors_vec_blk<T, double>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
+}
+
+// GLS (n <= p, Sec. 5.3):  F~ = [a I, V^T, 0; V, 0, b W; 0, b W^T, 0] on
+// u = [u1 (p); u2 (n); u3 (m)];  T = [0, T2] (T2 n x n), S = T2(1:m, 1:m),
+//   M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^T, a^-1/2 b^-1 S^T R^-T),
+//   M_r = diag(a^-1/2 I, a^1/2 Q T2^-T,  a^-1/2 b^-1 R^-1 S).
+// Reversed coordinates: T2 = P_n T~_n^T P_n (T~_n the leading n x n of the
+// factor of C~) and S = P_m T~_S^T P_m, T~_S = T~(L:n, L:n), L = n - m.
+template <typename T>
+struct GlsBDOp : LinOp {
+    mpir_ctx *h;
+    GlsWs<T> &w;
+    BDScratch &b;
+    const double *W, *V;
+    int ldw, ldv;
+    double al, be;
+    GlsBDOp(mpir_ctx *h_, GlsWs<T> &w_, BDScratch &b_, const double *W_, int ldw_, const double *V_, int ldv_,
+            double al_, double be_)
+        : h(h_), w(w_), b(b_), W(W_), V(V_), ldw(ldw_), ldv(ldv_), al(al_), be(be_) {}
+
+    const T *TS() const { return w.Ct + idx2(w.L, w.L, w.ldCt); }
+
+    int Mr(const double *t, double *u)
+    {
+        const int n = w.n, m = w.m, p = w.p;
+        const double sW = h->fs.s1, sV = h->fs.s2, sa = std::sqrt(al);
+        cudaStream_t s = h->stream;
+        vcomb<double>(u, p, t, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+        // a^1/2 Q T2^-T t2 = a^1/2 sV Q P_n T~_n'^-1 P_n t2
+        vcomb<double>(b.w1, n, t + p, 1, 1.0, nullptr, 0, 0.0, s);
+        RC(trsv_d<T>(w.Ct, w.ldCt, n, 0, b.w1, h->sc, s));
+        vcomb<double>(u + p, n, b.w1, 1, sa * sV, nullptr, 0, 0.0, s);
+        RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, u + p, s));
+        if (m > 0) {
+            // a^-1/2 b^-1 R^-1 S t3 = a^-1/2 b^-1 (sW/sV) R'^-1 P_m T~_S'^T P_m t3
+            vcomb<double>(b.w1, m, t + p + n, 1, 1.0, nullptr, 0, 0.0, s);
+            RC(gemv_d<T>(TS(), w.ldCt, m, m, 1, 1.0, b.w1, 0.0, b.w2, 1, 0, s));
+            vcomb<double>(u + p + n, m, b.w2, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
+            RC(trsv_d<T>(w.Wf, w.ldW, m, 0, u + p + n, h->sc, s));
+        }
+        return 0;
+    }
+
+    int Fmul(const double *u, double *g)
+    {
+        const int n = w.n, m = w.m, p = w.p;
+        cudaStream_t s = h->stream;
+        if (m > 0) dual_gemv(W, ldw, n, m, u + p + n, u + p, w.pWx, w.pWtz, s);
+        dual_gemv(V, ldv, n, p, u, u + p, w.pVy, w.pVtz, s);
+        combine_parts(g, p, al, u, 1.0, w.pVtz, w.pv.nrb, p, 0.0, nullptr, 0, 0, s);
+        combine_parts(g + p, n, 0.0, nullptr, 1.0, w.pVy, w.pv.ncb, n, be, m > 0 ? w.pWx : nullptr, w.pw.ncb, n,
+                      s);
+        if (m > 0) combine_parts(g + p + n, m, 0.0, nullptr, be, w.pWtz, w.pw.nrb, m, 0.0, nullptr, 0, 0, s);
+        return 0;
+    }
+
+    int Ml(const double *g, double *o)
+    {
+        const int n = w.n, m = w.m, p = w.p;
+        const double sW = h->fs.s1, sV = h->fs.s2, sa = std::sqrt(al);
+        cudaStream_t s = h->stream;
+        vcomb<double>(o, p, g, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+        // a^1/2 T2^-1 Q^T g2 = a^1/2 sV P_n T~_n'^-T P_n Q^T g2
+        vcomb<double>(b.w1, n, g + p, 0, 1.0, nullptr, 0, 0.0, s);
+        RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, b.w1, s));
+        vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
+        RC(trsv_d<T>(w.Ct, w.ldCt, n, 1, b.w2, h->sc, s));
+        vcomb<double>(o + p, n, b.w2, 1, sa * sV, nullptr, 0, 0.0, s);
+        if (m > 0) {
+            // a^-1/2 b^-1 S^T R^-T g3 = a^-1/2 b^-1 (sW/sV) P_m T~_S' P_m R'^-T g3
+            vcomb<double>(b.w1, m, g + p + n, 0, 1.0, nullptr, 0, 0.0, s);
+            RC(trsv_d<T>(w.Wf, w.ldW, m, 1, b.w1, h->sc, s));
+            vcomb<double>(b.w2, m, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
+            RC(gemv_d<T>(TS(), w.ldCt, m, m, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
+            vcomb<double>(o + p + n, m, b.w3, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
+        }
+        return 0;
+    }
+
+    int apply(const double *in, double *out) override
+    {
+        RC(Mr(in, b.u));
+        RC(Fmul(b.u, b.gf));
+        return Ml(b.gf, out);
+    }
+};
+
+// One GMRES-IR correction (GLS): solve M_l F~ M_r t = M_l [a^1/2 f1;
+// a^-1/2 f2; a^1/2 b f3], then [a^-1/2 dy; -a^1/2 dz; a^-1/2 b^-1 dx] = M_r t
+// and the updates are added to (y, z, x).
+template <typename T>
+int gls_gmres_correction(mpir_ctx *h, GlsWs<T> &w, BDScratch &b, const double *W, int ldw, const double *V,
+                         int ldv, double al, double be, double itol, int imax, double *y, double *z, double *x,
+                         int *inner)
+{
+    const int n = w.n, m = w.m, p = w.p;
+    cudaStream_t s = h->stream;
+    const double sa = std::sqrt(al);
+    GlsBDOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
+    vcomb<double>(b.t, p, w.f1, 0, sa, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + p, n, w.f2, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + p + n, m, w.f3, 0, sa * be, nullptr, 0, 0.0, s);
+    RC(op.Ml(b.t, b.rhs));
+    int k = 0;
+    double rel = 0.0;
+    RC(gmres_solve(op, b.rhs, b.t, b.gw, itol, imax, h->hbuf, s, &k, &rel));
+    *inner += k;
+    RC(op.Mr(b.t, b.u));
+    vaxpy<double>(b.u, y, p, sa, 0, s);
+    vaxpy<double>(b.u + p, z, n, -1.0 / sa, 0, s);
+    vaxpy<double>(b.u + p + n, x, m, sa * be, 0, s);
+    return cuda_check(h, "gls_gmres_correction");
+}
+
+double inner_tol_default(const mpir_opts &o, int fact)
+{
+    if (o.inner_tol > 0) return o.inner_tol;
+    return (fact == MPIR_BF16 || fact == MPIR_TF32) ? 1e-4 : 1e-8;
+}
+
+// alpha of F~ (Sec. 5; floored so that a consistent problem keeps it > 0)
+double bd_alpha(const mpir_opts &o, double lead, double fro, double other)
+{
+    if (o.alpha > 0) return o.alpha;
+    const double sqrt_u = std::ldexp(1.0, -26) * std::sqrt(0.5);   // sqrt(2^-53)
+    const double a = std::max(lead, sqrt_u * fro * other);
+    return (a > 0 && std::isfinite(a)) ? a : 1.0;
+}
+
 template <typename T>
 int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
                    const double *d, double *x, double *y, double *z_out, const mpir_opts &o, int fact,
                    mpir_info *info)
 {
     cudaStream_t s = h->stream;
+    const bool gm = o.refine == MPIR_GMRES;
+    size_t main_bytes = 0;
+    gls_layout<T>(nullptr, n, m, p, &main_bytes);
+    const int NG = p + n + m, mx = std::max(std::max(m, n), std::max(p, 1));
+    if (gm) {
+        if (n > p) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.3) needs n <= p");
+        if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
+        RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
+    }
     cudaEventRecord(h->ev[0], s);
     RC(gls_factor_impl<T>(h, n, m, p, W, ldw, V, ldv, fact));
     cudaEventRecord(h->ev[1], s);
     GlsWs<T> w = gls_layout<T>(h->ws, n, m, p, nullptr);
+    BDScratch bs{};
+    if (gm) bs = bd_layout((char *)h->ws + main_bytes, NG, o.restart, mx);
     double *z = z_out ? z_out : w.z;
     RC(gls_initial_impl<T>(h, d, x, y));
     int st = MPIR_OK;
-    int it = 0;
+    int it = 0, inner = 0;
     double ratio[3] = {0, 0, 0};
+    double al = 1.0;
+    float t_gm = 0;
     if (o.refine != MPIR_DIRECT) {
         RC(gls_multipliers_impl<T>(h, y, z));
         cudaEventRecord(h->ev[2], s);
@@ -604,12 +803,23 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
             else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
             // normalize the right-hand side of the scaled correction system
             // (f1, sV f2, sW/sV f3), not the raw blocks
+            if (gm) {
+                // Sec. 5.3: correction from GMRES on the preconditioned F~
+                if (it == 0) al = bd_alpha(o, nr[4], fV, nr[5]);
+                cudaEventRecord(h->ev[5], s);
+                RC(gls_gmres_correction<T>(h, w, bs, W, ldw, V, ldv, al, o.beta, inner_tol_default(o, fact),
+                                           o.inner_maxit, y, z, x, &inner));
+                cudaEventRecord(h->ev[6], s);
+                cudaEventSynchronize(h->ev[6]);
+                t_gm += ev_ms(h->ev[5], h->ev[6]);
+                continue;
+            }
             const double sW = h->fs.s1, sV = h->fs.s2;
             const double fmax = std::max(nr[0], std::max(nr[1] * sV, nr[2] * sW / sV));
             const double gamma = pow2_norm(fmax);
             RC(gls_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, y, z, x));
         }
-        if (info) { info->time_ms[2] = t_res; }
+        if (info) { info->time_ms[2] = t_res; info->time_ms[4] = t_gm; info->inner_iters = inner; }
     }
     RC(check_dev_flags(h));
     cudaEventRecord(h->ev[7], s);
@@ -794,21 +1004,146 @@ double dnorm_host(mpir_ctx *h, const double *dvec, int n, double *scratch)
     return std::sqrt(h->hbuf[1]);
 }
 
+
+// LSE (m >= n, Sec. 5.2):  F~ = [a I, 0, A; 0, 0, b B; A^T, b B^T, 0] on
+// u = [u1 (m); u2 (p); u3 (n)];  T1 = T(1:n, 1:n), S = T1(q+1:n, q+1:n),
+//   M_l = diag(a^-1/2 I, a^-1/2 b^-1 S R^-1, a^1/2 T1^-T Q),
+//   M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-T S^T, a^1/2 Q^T T1^-1).
+// Reversed coordinates: R = P_p R~^T P_p, Q = P_n Q~^T P_n; T is held as is.
+template <typename T>
+struct LseBDOp : LinOp {
+    mpir_ctx *h;
+    LseWs<T> &w;
+    BDScratch &b;
+    const double *A, *B;
+    int lda, ldb;
+    double al, be;
+    LseBDOp(mpir_ctx *h_, LseWs<T> &w_, BDScratch &b_, const double *A_, int lda_, const double *B_, int ldb_,
+            double al_, double be_)
+        : h(h_), w(w_), b(b_), A(A_), B(B_), lda(lda_), ldb(ldb_), al(al_), be(be_) {}
+
+    const T *TS() const { return w.At + idx2(w.q, w.q, w.ldAt); }
+
+    int Mr(const double *t, double *u)
+    {
+        const int m = w.m, n = w.n, p = w.p;
+        const double sA = h->fs.s1, sB = h->fs.s2, sa = std::sqrt(al);
+        cudaStream_t s = h->stream;
+        vcomb<double>(u, m, t, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+        if (p > 0) {
+            // a^-1/2 b^-1 R^-T S^T t2 = a^-1/2 b^-1 (sB/sA) P_p R~'^-1 P_p S'^T t2
+            RC(gemv_d<T>(TS(), w.ldAt, p, p, 1, 1.0, t + m, 0.0, b.w1, 1, 0, s));
+            vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
+            RC(trsv_d<T>(w.Bt, w.ldBt, p, 0, b.w2, h->sc, s));
+            vcomb<double>(u + m, p, b.w2, 1, sB / (sA * sa * be), nullptr, 0, 0.0, s);
+        }
+        // a^1/2 Q^T T1^-1 t3 = a^1/2 sA P_n Q~ P_n T1'^-1 t3
+        vcomb<double>(b.w1, n, t + m + p, 0, 1.0, nullptr, 0, 0.0, s);
+        RC(trsv_d<T>(w.At, w.ldAt, n, 0, b.w1, h->sc, s));
+        vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
+        RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, b.w2, s));
+        vcomb<double>(u + m + p, n, b.w2, 1, sa * sA, nullptr, 0, 0.0, s);
+        return 0;
+    }
+
+    int Fmul(const double *u, double *g)
+    {
+        const int m = w.m, n = w.n, p = w.p;
+        cudaStream_t s = h->stream;
+        dual_gemv(A, lda, m, n, u + m + p, u, w.pAx, w.pAtr, s);
+        if (p > 0) dual_gemv(B, ldb, p, n, u + m + p, u + m, w.pBx, w.pBtv, s);
+        combine_parts(g, m, al, u, 1.0, w.pAx, w.pa.ncb, m, 0.0, nullptr, 0, 0, s);
+        if (p > 0) combine_parts(g + m, p, 0.0, nullptr, be, w.pBx, w.pb.ncb, p, 0.0, nullptr, 0, 0, s);
+        combine_parts(g + m + p, n, 0.0, nullptr, 1.0, w.pAtr, w.pa.nrb, n, be, p > 0 ? w.pBtv : nullptr,
+                      w.pb.nrb, n, s);
+        return 0;
+    }
+
+    int Ml(const double *g, double *o)
+    {
+        const int m = w.m, n = w.n, p = w.p;
+        const double sA = h->fs.s1, sB = h->fs.s2, sa = std::sqrt(al);
+        cudaStream_t s = h->stream;
+        vcomb<double>(o, m, g, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+        if (p > 0) {
+            // a^-1/2 b^-1 S R^-1 g2 = a^-1/2 b^-1 (sB/sA) S' P_p R~'^-T P_p g2
+            vcomb<double>(b.w1, p, g + m, 1, 1.0, nullptr, 0, 0.0, s);
+            RC(trsv_d<T>(w.Bt, w.ldBt, p, 1, b.w1, h->sc, s));
+            vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
+            RC(gemv_d<T>(TS(), w.ldAt, p, p, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
+            vcomb<double>(o + m, p, b.w3, 0, sB / (sA * sa * be), nullptr, 0, 0.0, s);
+        }
+        // a^1/2 T1^-T Q g3 = a^1/2 sA T1'^-T P_n Q~^T P_n g3
+        vcomb<double>(b.w1, n, g + m + p, 1, 1.0, nullptr, 0, 0.0, s);
+        RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, b.w1, s));
+        vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
+        RC(trsv_d<T>(w.At, w.ldAt, n, 1, b.w2, h->sc, s));
+        vcomb<double>(o + m + p, n, b.w2, 0, sa * sA, nullptr, 0, 0.0, s);
+        return 0;
+    }
+
+    int apply(const double *in, double *out) override
+    {
+        RC(Mr(in, b.u));
+        RC(Fmul(b.u, b.gf));
+        return Ml(b.gf, out);
+    }
+};
+
+// One GMRES-IR correction (LSE): right-hand side [a^1/2 f1; a^1/2 b f2;
+// a^-1/2 f3], solution [a^-1/2 dr; -a^-1/2 b^-1 dv; a^1/2 dx] = M_r t.
+template <typename T>
+int lse_gmres_correction(mpir_ctx *h, LseWs<T> &w, BDScratch &b, const double *A, int lda, const double *B,
+                         int ldb, double al, double be, double itol, int imax, double *r, double *v, double *x,
+                         int *inner)
+{
+    const int m = w.m, n = w.n, p = w.p;
+    cudaStream_t s = h->stream;
+    const double sa = std::sqrt(al);
+    LseBDOp<T> op(h, w, b, A, lda, B, ldb, al, be);
+    vcomb<double>(b.t, m, w.f1, 0, sa, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + m, p, w.f2, 0, sa * be, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + m + p, n, w.f3, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+    RC(op.Ml(b.t, b.rhs));
+    int k = 0;
+    double rel = 0.0;
+    RC(gmres_solve(op, b.rhs, b.t, b.gw, itol, imax, h->hbuf, s, &k, &rel));
+    *inner += k;
+    RC(op.Mr(b.t, b.u));
+    vaxpy<double>(b.u, r, m, sa, 0, s);
+    vaxpy<double>(b.u + m, v, p, -sa * be, 0, s);
+    vaxpy<double>(b.u + m + p, x, n, 1.0 / sa, 0, s);
+    return cuda_check(h, "lse_gmres_correction");
+}
+
 template <typename T>
 int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
                    const double *b, const double *d, double *x, double *r_out, double *v_out,
                    const mpir_opts &o, int fact, mpir_info *info)
 {
     cudaStream_t s = h->stream;
+    const bool gm = o.refine == MPIR_GMRES;
+    size_t main_bytes = 0;
+    lse_layout<T>(nullptr, m, n, p, &main_bytes);
+    const int NG = m + p + n, mx = std::max(std::max(m, n), std::max(p, 1));
+    if (gm) {
+        if (m < n) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.2) needs m >= n");
+        if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
+        RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
+    }
     cudaEventRecord(h->ev[0], s);
     RC(lse_factor_impl<T>(h, m, n, p, A, lda, B, ldb, fact));
     cudaEventRecord(h->ev[1], s);
     LseWs<T> w = lse_layout<T>(h->ws, m, n, p, nullptr);
+    BDScratch bs{};
+    if (gm) bs = bd_layout((char *)h->ws + main_bytes, NG, o.restart, mx);
     double *r = r_out ? r_out : w.r;
     double *v = v_out ? v_out : w.v;
     RC(lse_initial_impl<T>(h, b, d, x));
-    int st = MPIR_OK, it = 0;
+    int st = MPIR_OK, it = 0, inner = 0;
     double ratio[3] = {0, 0, 0};
+    double al = 1.0;
+    float t_gm = 0;
     if (o.refine != MPIR_DIRECT || r_out || v_out) RC(lse_multipliers_impl<T>(h, A, lda, b, x, r, v));
     if (o.refine != MPIR_DIRECT) {
         const double nb = dnorm_host(h, b, m, w.part), nd = p > 0 ? dnorm_host(h, d, p, w.part) : 0.0;
@@ -835,11 +1170,22 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
             else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
             // normalize the right-hand side of the scaled correction system
             // (f1, sB/sA f2, sA f3), not the raw blocks
+            if (gm) {
+                // Sec. 5.2: correction from GMRES on the preconditioned F~
+                if (it == 0) al = bd_alpha(o, nr[4], fA, nr[3]);
+                cudaEventRecord(h->ev[5], s);
+                RC(lse_gmres_correction<T>(h, w, bs, A, lda, B, ldb, al, o.beta, inner_tol_default(o, fact),
+                                           o.inner_maxit, r, v, x, &inner));
+                cudaEventRecord(h->ev[6], s);
+                cudaEventSynchronize(h->ev[6]);
+                t_gm += ev_ms(h->ev[5], h->ev[6]);
+                continue;
+            }
             const double sA = h->fs.s1, sB = h->fs.s2;
             const double gamma = pow2_norm(std::max(nr[0], std::max(nr[1] * sB / sA, nr[2] * sA)));
             RC(lse_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, r, v, x));
         }
-        if (info) info->time_ms[2] = t_res;
+        if (info) { info->time_ms[2] = t_res; info->time_ms[4] = t_gm; info->inner_iters = inner; }
     }
     RC(check_dev_flags(h));
     cudaEventRecord(h->ev[7], s);
@@ -1006,6 +1352,8 @@ int mpir_lse_workspace_size(int m, int n, int p, const mpir_opts *opts, size_t *
     lse_layout<float>(nullptr, m, n, p, &b32);
     lse_layout<double>(nullptr, m, n, p, &b64);
     *bytes = (o.fact == MPIR_FP64 || o.escalate) ? std::max(b32, b64) : b32;
+    if (o.refine == MPIR_GMRES)
+        *bytes += bd_bytes(m + p + n, std::min(o.restart, GMRES_MAX_RESTART), std::max(std::max(m, n), std::max(p, 1)));
     return 0;
 }
 
@@ -1021,6 +1369,8 @@ int mpir_gls_workspace_size(int n, int m, int p, const mpir_opts *opts, size_t *
     gls_layout<float>(nullptr, n, m, p, &b32);
     gls_layout<double>(nullptr, n, m, p, &b64);
     *bytes = (o.fact == MPIR_FP64 || o.escalate) ? std::max(b32, b64) : b32;
+    if (o.refine == MPIR_GMRES)
+        *bytes += bd_bytes(p + n + m, std::min(o.restart, GMRES_MAX_RESTART), std::max(std::max(m, n), std::max(p, 1)));
     return 0;
 }
 
@@ -1435,6 +1785,96 @@ int mpir_apply_factor(mpir_handle h, int which, int trans, double *vec)
     if (!vec) return -4;
     int rc = is_fp64(h->fs.fact) ? apply_factor_impl<double>(h, which, trans, vec)
                                  : apply_factor_impl<float>(h, which, trans, vec);
+    if (rc) return rc;
+    return check_dev_flags(h);
+}
+
+} // extern "C"
+
+// --------------------------------------- GMRES-IR operator (step level) --
+template <typename Op>
+static int bd_dispatch(Op &op, int which, const double *in, double *out, BDScratch &b)
+{
+    switch (which) {
+    case 0: return op.Fmul(in, out);
+    case 1: return op.Ml(in, out);
+    case 2: return op.Mr(in, out);
+    default: return op.apply(in, out);
+    }
+}
+
+template <typename T>
+static int lse_bd_apply_impl(mpir_ctx *h, const double *A, int lda, const double *B, int ldb, double al,
+                             double be, int which, const double *in, double *out)
+{
+    const FactorState &fs = h->fs;
+    const int N = fs.m + fs.p + fs.n, mx = std::max(std::max(fs.m, fs.n), std::max(fs.p, 1));
+    RC(ensure_rws(h, bd_bytes(N, 1, mx)));
+    BDScratch b = bd_layout(h->rws, N, 1, mx);
+    LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+    LseBDOp<T> op(h, w, b, A, lda, B, ldb, al, be);
+    RC(bd_dispatch(op, which, in, out, b));
+    return cuda_check(h, "lse_bd_apply");
+}
+
+template <typename T>
+static int gls_bd_apply_impl(mpir_ctx *h, const double *W, int ldw, const double *V, int ldv, double al,
+                             double be, int which, const double *in, double *out)
+{
+    const FactorState &fs = h->fs;
+    const int N = fs.p + fs.n + fs.m, mx = std::max(std::max(fs.m, fs.n), std::max(fs.p, 1));
+    RC(ensure_rws(h, bd_bytes(N, 1, mx)));
+    BDScratch b = bd_layout(h->rws, N, 1, mx);
+    GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+    GlsBDOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
+    RC(bd_dispatch(op, which, in, out, b));
+    return cuda_check(h, "gls_bd_apply");
+}
+
+extern "C" {
+
+int mpir_lse_bd_apply(mpir_handle h, const double *A, int lda, const double *B, int ldb, double alpha,
+                      double beta, int which, const double *in, double *out)
+{
+    if (!h) return -1;
+    const FactorState &fs = h->fs;
+    if (fs.kind != Kind::LSE) return set_err(h, MPIR_UNSUPPORTED, "no LSE factors held");
+    if (fs.m < fs.n) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.2) needs m >= n");
+    if (!A) return -2;
+    if (lda < std::max(1, fs.m)) return -3;
+    if (fs.p > 0 && !B) return -4;
+    if (ldb < std::max(1, fs.p)) return -5;
+    if (!(alpha > 0) || !std::isfinite(alpha)) return -6;
+    if (!(beta > 0) || !std::isfinite(beta)) return -7;
+    if (which < 0 || which > 3) return -8;
+    if (!in) return -9;
+    if (!out || out == in) return -10;
+    clear_dev_flags(h);
+    int rc = is_fp64(fs.fact) ? lse_bd_apply_impl<double>(h, A, lda, B, ldb, alpha, beta, which, in, out)
+                              : lse_bd_apply_impl<float>(h, A, lda, B, ldb, alpha, beta, which, in, out);
+    if (rc) return rc;
+    return check_dev_flags(h);
+}
+
+int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, int ldv, double alpha,
+                      double beta, int which, const double *in, double *out)
+{
+    if (!h) return -1;
+    const FactorState &fs = h->fs;
+    if (fs.kind != Kind::GLS) return set_err(h, MPIR_UNSUPPORTED, "no GLS factors held");
+    if (fs.n > fs.p) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.3) needs n <= p");
+    if (fs.m > 0 && !W) return -2;
+    if (ldw < std::max(1, fs.n)) return -3;
+    if (!V) return -4;
+    if (ldv < std::max(1, fs.n)) return -5;
+    if (!(alpha > 0) || !std::isfinite(alpha)) return -6;
+    if (!(beta > 0) || !std::isfinite(beta)) return -7;
+    if (which < 0 || which > 3) return -8;
+    if (!in) return -9;
+    if (!out || out == in) return -10;
+    clear_dev_flags(h);
+    int rc = is_fp64(fs.fact) ? gls_bd_apply_impl<double>(h, W, ldw, V, ldv, alpha, beta, which, in, out)
+                              : gls_bd_apply_impl<float>(h, W, ldw, V, ldv, alpha, beta, which, in, out);
     if (rc) return rc;
     return check_dev_flags(h);
 }

@@ -162,9 +162,9 @@ int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int tra
 // ---------------------------------------------------------------------------
 constexpr int VEC_CL_THREADS = 512;
 
-template <typename T, int NBV>
+template <typename TS, typename T, int NBV>
 __global__ void __launch_bounds__(VEC_CL_THREADS, 1)
-k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restrict__ Tw, int trans,
+k_vec_apply_cl(const TS *__restrict__ V, int ldv, int M, int K, const TS *__restrict__ Tw, int trans,
                T *__restrict__ x, int slice)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -189,10 +189,10 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
         const int kb = min(NBV, K - j0);
         const int par = t & 1;
         // stage X (used after the barrier)
-        const T *Tb = Tw + (size_t)b * NBV * NBV;
+        const TS *Tb = Tw + (size_t)b * NBV * NBV;
         for (int e = tid; e < NBV * NBV; e += VEC_CL_THREADS) {
             const int i = e % NBV, k = e / NBV;
-            const T tv = Tb[i + (size_t)k * NBV];
+            const T tv = (T)Tb[i + (size_t)k * NBV];
             if (trans) Ts[k + i * NBV] = tv; else Ts[i + k * NBV] = tv;
         }
         // 1. partial dots (rows unrolled by 4 for memory-level parallelism)
@@ -200,14 +200,14 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
             T acc = T(0);
             if (c < kb) {
                 const int j = j0 + c;
-                const T *vc = V + (size_t)j * ldv;
+                const TS *vc = V + (size_t)j * ldv;
                 const int ib = max(s0, j);
                 for (int i0 = ib; i0 < s1; i0 += 128) {
                     T vv[4], xx[4];
 #pragma unroll
                     for (int u = 0; u < 4; u++) {
                         const int i = i0 + lane + 32 * u;
-                        vv[u] = i < s1 ? (i == j ? T(1) : vc[i]) : T(0);
+                        vv[u] = i < s1 ? (i == j ? T(1) : (T)vc[i]) : T(0);
                         xx[u] = i < s1 ? xs[i - s0] : T(0);
                     }
 #pragma unroll
@@ -241,7 +241,7 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
 #pragma unroll
                 for (int u = 0; u < 16; u++) {
                     const int c = c0 + u, j = j0 + c;
-                    vv[u] = c < cmax ? (i == j ? T(1) : V[(size_t)j * ldv + i]) : T(0);
+                    vv[u] = c < cmax ? (i == j ? T(1) : (T)V[(size_t)j * ldv + i]) : T(0);
                 }
 #pragma unroll
                 for (int u = 0; u < 16; u++) d = fma(vv[u], wp[(c0 + u) & (NBV - 1)], d);
@@ -254,10 +254,10 @@ k_vec_apply_cl(const T *__restrict__ V, int ldv, int M, int K, const T *__restri
     cluster.sync();   // keep shared memory alive until every remote read is done
 }
 
-template <typename T, int NBV>
-static int launch_vec_apply_cl(const T *V, int ldv, int M, int K, const T *Tw, int trans, T *x, cudaStream_t s)
+template <typename TS, typename T, int NBV>
+static int launch_vec_apply_cl(const TS *V, int ldv, int M, int K, const TS *Tw, int trans, T *x, cudaStream_t s)
 {
-    auto kern = k_vec_apply_cl<T, NBV>;
+    auto kern = k_vec_apply_cl<TS, T, NBV>;
     int want = ceil_div(M, 256);
     if (want > 16) want = 16;
     static bool attr = false;
@@ -288,14 +288,14 @@ static int launch_vec_apply_cl(const T *V, int ldv, int M, int K, const T *Tw, i
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
-template <typename T>
-int apply_reflectors_vec_blk(const T *V, int ldv, int M, int K, const T *Tw, int nbv, int trans, T *x,
+template <typename TS, typename T>
+int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, int nbv, int trans, T *x,
                              cudaStream_t s)
 {
     if (K <= 0 || M <= 0) return 0;
-    if (nbv == 128) return launch_vec_apply_cl<T, 128>(V, ldv, M, K, Tw, trans, x, s);
-    if (nbv == 32) return launch_vec_apply_cl<T, 32>(V, ldv, M, K, Tw, trans, x, s);
-    if (nbv == 16) return launch_vec_apply_cl<T, 16>(V, ldv, M, K, Tw, trans, x, s);
+    if (nbv == 128) return launch_vec_apply_cl<TS, T, 128>(V, ldv, M, K, Tw, trans, x, s);
+    if (nbv == 32) return launch_vec_apply_cl<TS, T, 32>(V, ldv, M, K, Tw, trans, x, s);
+    if (nbv == 16) return launch_vec_apply_cl<TS, T, 16>(V, ldv, M, K, Tw, trans, x, s);
     return MPIR_UNSUPPORTED;
 }
 
@@ -357,10 +357,10 @@ void invert_diag32(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_
 // cluster barrier; every CTA reads x_blk through distributed shared memory
 // and updates its unsolved rows.  One cluster barrier per 32 rows.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename TS, typename T>
 __global__ void __launch_bounds__(VEC_CL_THREADS, 1)
-k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
-          const T *__restrict__ Dinv, int *__restrict__ status)
+k_trsv_cl(const TS *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
+          const TS *__restrict__ Dinv, int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
@@ -390,28 +390,28 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
         T ua[32], ub[TROWS > 1 ? 32 : 1];
 #pragma unroll
         for (int c = 0; c < 32; c++)
-            ua[c] = (va && c < bs) ? (trans ? U[idx2(r0 + c, ia, ldu)] : U[idx2(ia, r0 + c, ldu)]) : T(0);
+            ua[c] = (va && c < bs) ? (T)(trans ? U[idx2(r0 + c, ia, ldu)] : U[idx2(ia, r0 + c, ldu)]) : T(0);
         if (TROWS > 1) {
 #pragma unroll
             for (int c = 0; c < 32; c++)
                 ub[c % (TROWS > 1 ? 32 : 1)] =
-                    (vb && c < bs) ? (trans ? U[idx2(r0 + c, ib, ldu)] : U[idx2(ib, r0 + c, ldu)]) : T(0);
+                    (vb && c < bs) ? (T)(trans ? U[idx2(r0 + c, ib, ldu)] : U[idx2(ib, r0 + c, ldu)]) : T(0);
         }
         if (crank == owner && warp == 0) {
             T rhs = lane < bs ? xs[r0 + lane - s0] : T(0);
             T xv = T(0);
             if (Dinv) {
-                const T *D = Dinv + (size_t)blk * 1024;
+                const TS *D = Dinv + (size_t)blk * 1024;
                 T drow[32];
 #pragma unroll
-                for (int k = 0; k < 32; k++) drow[k] = trans ? D[k + 32 * lane] : D[lane + 32 * k];
+                for (int k = 0; k < 32; k++) drow[k] = (T)(trans ? D[k + 32 * lane] : D[lane + 32 * k]);
 #pragma unroll
                 for (int k = 0; k < 32; k++) xv = fma(drow[k], __shfl_sync(0xffffffffu, rhs, k), xv);
                 if (lane >= bs) xv = T(0);
             } else {
 #pragma unroll
                 for (int c = 0; c < 32; c++)
-                    dg[lane][c] = (c < bs && lane < bs) ? U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
+                    dg[lane][c] = (c < bs && lane < bs) ? (T)U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
                 __syncwarp();
                 if (!trans) {
                     for (int c = bs - 1; c >= 0; c--) {
@@ -466,9 +466,9 @@ k_trsv_cl(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x,
 // and publishes the 32 values; grid barrier; every block subtracts the
 // block column's contribution from its own not-yet-solved rows.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename TS, typename T>
 __global__ void __launch_bounds__(256)
-k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
+k_trsv_upper(const TS *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
              T *__restrict__ xbuf, int *__restrict__ status, GridBarrier gb)
 {
     extern __shared__ unsigned char smem_raw[];
@@ -491,21 +491,21 @@ k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__
             T xv = T(0);
             if (!trans) {
                 for (int c = bs - 1; c >= 0; c--) {
-                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    const T dcc = (T)U[idx2(r0 + c, r0 + c, ldu)];
                     T xc = __shfl_sync(0xffffffffu, rhs, c);
                     if (dcc == T(0)) { if (lane == 0) atomicOr(status, 2); }
                     xc = xc / dcc;
                     if (lane == c) xv = xc;
-                    if (lane < c) rhs = fma(-U[idx2(r0 + lane, r0 + c, ldu)], xc, rhs);
+                    if (lane < c) rhs = fma(-(T)U[idx2(r0 + lane, r0 + c, ldu)], xc, rhs);
                 }
             } else {
                 for (int c = 0; c < bs; c++) {
-                    const T dcc = U[idx2(r0 + c, r0 + c, ldu)];
+                    const T dcc = (T)U[idx2(r0 + c, r0 + c, ldu)];
                     T xc = __shfl_sync(0xffffffffu, rhs, c);
                     if (dcc == T(0)) { if (lane == 0) atomicOr(status, 2); }
                     xc = xc / dcc;
                     if (lane == c) xv = xc;
-                    if (lane > c && lane < bs) rhs = fma(-U[idx2(r0 + c, r0 + lane, ldu)], xc, rhs);
+                    if (lane > c && lane < bs) rhs = fma(-(T)U[idx2(r0 + c, r0 + lane, ldu)], xc, rhs);
                 }
             }
             if (lane < bs) {
@@ -521,16 +521,16 @@ k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__
             const int hi = min(s1, r0);
             for (int i = s0 + tid; i < hi; i += 256) {
                 T d = T(0);
-                for (int c = 0; c < bs; c++) d = fma(U[idx2(i, r0 + c, ldu)], xb[c], d);
+                for (int c = 0; c < bs; c++) d = fma((T)U[idx2(i, r0 + c, ldu)], xb[c], d);
                 xs[i - s0] -= d;
             }
         } else {
             // rows i >= r0 + bs: x_i -= sum_c U(r0+c, i) xb_c
             const int lo = max(s0, r0 + bs);
             for (int i = lo + tid; i < s1; i += 256) {
-                const T *ucol = U + idx2(r0, i, ldu);
+                const TS *ucol = U + idx2(r0, i, ldu);
                 T d = T(0);
-                for (int c = 0; c < bs; c++) d = fma(ucol[c], xb[c], d);
+                for (int c = 0; c < bs; c++) d = fma((T)ucol[c], xb[c], d);
                 xs[i - s0] -= d;
             }
         }
@@ -539,11 +539,11 @@ k_trsv_upper(const T *__restrict__ U, int ldu, int n, int trans, T *__restrict__
     for (int i = s0 + tid; i < s1; i += 256) x[i] = xs[i - s0];
 }
 
-template <typename T>
-static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
-                         const T *Dinv)
+template <typename TS, typename T>
+static int trsv_upper_cl(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
+                         const TS *Dinv)
 {
-    auto kern = k_trsv_cl<T>;
+    auto kern = k_trsv_cl<TS, T>;
     const int nblk = ceil_div(n, 32);
     int want = ceil_div(nblk, 8);            // 256 rows per CTA
     if (want > 16) want = 16;
@@ -575,15 +575,16 @@ static int trsv_upper_cl(const T *U, int ldu, int n, int trans, T *x, const DevS
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
-template <typename T>
-int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s, const T *Dinv)
+template <typename TS, typename T>
+static int trsv_dispatch(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
+                         const TS *Dinv)
 {
     if (n <= 0) return 0;
     {
-        const int rc = trsv_upper_cl<T>(U, ldu, n, trans, x, sc, s, Dinv);
+        const int rc = trsv_upper_cl<TS, T>(U, ldu, n, trans, x, sc, s, Dinv);
         if (rc >= 0) return rc;          // -1: too large for one cluster, use the grid version
     }
-    auto kern = k_trsv_upper<T>;
+    auto kern = k_trsv_upper<TS, T>;
     const int nblk = ceil_div(n, 32);
     int want = ceil_div(nblk, 4);          // 128 rows per block
     int G = want;
@@ -612,14 +613,28 @@ int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+template <typename T>
+int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s, const T *Dinv)
+{
+    return trsv_dispatch<T, T>(U, ldu, n, trans, x, sc, s, Dinv);
+}
+
+// Mixed-precision solve: U stored as TS, arithmetic and x in T (FP32 factors
+// applied in FP64 by GMRES-IR).  Substitution on the stored diagonal blocks.
+template <typename TS, typename T>
+int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
+{
+    return trsv_dispatch<TS, T>(U, ldu, n, trans, x, sc, s, nullptr);
+}
+
 // ---------------------------------------------------------------------------
 // gemv.  trans = 0: 32 rows per block (lanes), 8 warps split the columns.
 //        trans = 1: one warp per output column.
 // upper_mask: M(i, j) treated as 0 when i > j + diag_off.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename TS, typename T>
 __global__ void __launch_bounds__(256)
-k_gemv_n(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
+k_gemv_n(const TS *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
          T beta, T *__restrict__ y, int upper_mask, int diag_off)
 {
     __shared__ T red[8][33];
@@ -630,7 +645,7 @@ k_gemv_n(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *
         int jlo = 0;
         if (upper_mask) jlo = max(0, i - diag_off);
         for (int j = warp; j < cols; j += 8)
-            if (j >= jlo) acc = fma(M[idx2(i, j, ld)], x[j], acc);
+            if (j >= jlo) acc = fma((T)M[idx2(i, j, ld)], x[j], acc);
     }
     red[warp][lane] = acc;
     __syncthreads();
@@ -641,9 +656,9 @@ k_gemv_n(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *
     }
 }
 
-template <typename T>
+template <typename TS, typename T>
 __global__ void __launch_bounds__(256)
-k_gemv_t(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
+k_gemv_t(const TS *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
          T beta, T *__restrict__ y, int upper_mask, int diag_off)
 {
     const int lane = threadIdx.x & 31;
@@ -651,27 +666,34 @@ k_gemv_t(const T *__restrict__ M, int ld, int rows, int cols, T alpha, const T *
     if (j >= cols) return;
     int ihi = rows;
     if (upper_mask) ihi = min(rows, j + diag_off + 1);
-    const T *col = M + idx2(0, j, ld);
+    const TS *col = M + idx2(0, j, ld);
     T acc = T(0);
-    for (int i = lane; i < ihi; i += 32) acc = fma(col[i], x[i], acc);
+    for (int i = lane; i < ihi; i += 32) acc = fma((T)col[i], x[i], acc);
     acc = warp_sum(acc);
     if (lane == 0) y[j] = (beta == T(0) ? T(0) : beta * y[j]) + alpha * acc;
+}
+
+template <typename TS, typename T>
+int gemv_mixed(const TS *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
+               int upper_mask, int diag_off, cudaStream_t s)
+{
+    if ((!trans && rows <= 0) || (trans && cols <= 0)) return 0;
+    ProfScope ps(K_GEMV, s);
+    if (!trans) {
+        k_gemv_n<TS, T><<<ceil_div(rows, 32), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
+                                                        diag_off);
+    } else {
+        k_gemv_t<TS, T><<<ceil_div(cols, 8), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
+                                                       diag_off);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
 template <typename T>
 int gemv(const T *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
          int upper_mask, int diag_off, cudaStream_t s)
 {
-    if ((!trans && rows <= 0) || (trans && cols <= 0)) return 0;
-    ProfScope ps(K_GEMV, s);
-    if (!trans) {
-        k_gemv_n<T><<<ceil_div(rows, 32), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
-                                                        diag_off);
-    } else {
-        k_gemv_t<T><<<ceil_div(cols, 8), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
-                                                       diag_off);
-    }
-    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+    return gemv_mixed<T, T>(M, ld, rows, cols, trans, alpha, x, beta, y, upper_mask, diag_off, s);
 }
 
 // ------------------------------------------------------------ elementwise --
@@ -846,10 +868,20 @@ template int apply_reflectors_vec<float>(const float *, int, int, int, const flo
                                          const DevScratch &, cudaStream_t);
 template int apply_reflectors_vec<double>(const double *, int, int, int, const double *, int, double *,
                                           const DevScratch &, cudaStream_t);
-template int apply_reflectors_vec_blk<float>(const float *, int, int, int, const float *, int, int, float *,
+template int apply_reflectors_vec_blk<float, float>(const float *, int, int, int, const float *, int, int, float *,
+                                                    cudaStream_t);
+template int apply_reflectors_vec_blk<double, double>(const double *, int, int, int, const double *, int, int,
+                                                      double *, cudaStream_t);
+template int apply_reflectors_vec_blk<float, double>(const float *, int, int, int, const float *, int, int,
+                                                     double *, cudaStream_t);
+template int trsv_upper_mixed<float, double>(const float *, int, int, int, double *, const DevScratch &,
                                              cudaStream_t);
-template int apply_reflectors_vec_blk<double>(const double *, int, int, int, const double *, int, int, double *,
+template int gemv_mixed<float, double>(const float *, int, int, int, int, double, const double *, double,
+                                       double *, int, int, cudaStream_t);
+template int trsv_upper_mixed<double, double>(const double *, int, int, int, double *, const DevScratch &,
                                               cudaStream_t);
+template int gemv_mixed<double, double>(const double *, int, int, int, int, double, const double *, double,
+                                        double *, int, int, cudaStream_t);
 template int trsv_upper<float>(const float *, int, int, int, float *, const DevScratch &, cudaStream_t,
                                const float *);
 template int trsv_upper<double>(const double *, int, int, int, double *, const DevScratch &, cudaStream_t,

@@ -75,6 +75,8 @@ _SIG = {
     "mpir_lse_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_gls_correction": ([_P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_larfb": ([_P, _I, _I, _I, _I, _P, _I, _P, _I, _P, _I], _I),
+    "mpir_lse_bd_apply": ([_P, _P, _I, _P, _I, ctypes.c_double, ctypes.c_double, _I, _P, _P], _I),
+    "mpir_gls_bd_apply": ([_P, _P, _I, _P, _I, ctypes.c_double, ctypes.c_double, _I, _P, _P], _I),
     "mpir_gls_residual_noalloc": ([_I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
@@ -82,7 +84,7 @@ _SIG = {
     "mpir_kernel_kind_name": ([_I], ctypes.c_char_p),
 }
 
-NKINDS = 12
+NKINDS = 13
 
 
 def profile(enable):
@@ -303,6 +305,21 @@ class Handle:
         N = C.shape[1]
         rc = lib().mpir_larfb(self.h, PREC[prec], M, N, K, ptr(V), ld(V), ptr(T), 1 if trans else 0, ptr(C), ld(C))
         return self.check(rc, "mpir_larfb")
+
+    BD_WHICH = {"F": 0, "Ml": 1, "Mr": 2, "op": 3}
+
+    def lse_bd_apply(self, A, B, alpha, beta, which, vin, vout):
+        """F~, M_l, M_r or M_l F~ M_r (Sec. 5.2) on [m; p; n] vectors."""
+        p = B.shape[0]
+        return self.check(lib().mpir_lse_bd_apply(self.h, ptr(A), ld(A), ptr(B), ld(B) if p else 1, float(alpha),
+                                                  float(beta), self.BD_WHICH[which], ptr(vin), ptr(vout)),
+                          "mpir_lse_bd_apply")
+
+    def gls_bd_apply(self, W, V, alpha, beta, which, vin, vout):
+        """F~, M_l, M_r or M_l F~ M_r (Sec. 5.3) on [p; n; m] vectors."""
+        return self.check(lib().mpir_gls_bd_apply(self.h, ptr(W), ld(W), ptr(V), ld(V), float(alpha), float(beta),
+                                                  self.BD_WHICH[which], ptr(vin), ptr(vout)),
+                          "mpir_gls_bd_apply")
 
     def gls_correction(self, f1, f2, f3, dy, dz, dx):
         return self.check(lib().mpir_gls_correction(self.h, ptr(f1), ptr(f2), ptr(f3), ptr(dy), ptr(dz),
