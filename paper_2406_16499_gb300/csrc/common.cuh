@@ -5,6 +5,9 @@
 #include <cooperative_groups.h>
 #include <cstdint>
 #include <cstddef>
+#include <mutex>
+#include <utility>
+#include <vector>
 
 namespace mpir {
 
@@ -101,9 +104,38 @@ __host__ __device__ __forceinline__ size_t idx2(int i, int j, int ld)
 
 // Largest power-of-two cluster size <= want that the device can schedule for
 // `kern` with this block size and dynamic shared memory.
+// The occupancy query costs far more host time than a launch, so its answer
+// is cached per (kernel, block size, shared memory, wanted size, device).
+struct ClusterKey {
+    const void *kern;
+    int threads, want, device;
+    size_t smem;
+};
+
+inline int cluster_size_query(const void *kern, int threads, size_t smem, int want);
+
 inline int cluster_size_for(const void *kern, int threads, size_t smem, int want)
 {
     if (want <= 1) return 1;
+    static std::mutex mu;
+    static std::vector<std::pair<ClusterKey, int>> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        for (const auto &e : cache)
+            if (e.first.kern == kern && e.first.threads == threads && e.first.want == want &&
+                e.first.device == dev && e.first.smem == smem)
+                return e.second;
+    }
+    const int c = cluster_size_query(kern, threads, smem, want);
+    std::lock_guard<std::mutex> lk(mu);
+    if (cache.size() < 4096) cache.push_back({ClusterKey{kern, threads, want, dev, smem}, c});
+    return c;
+}
+
+inline int cluster_size_query(const void *kern, int threads, size_t smem, int want)
+{
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(want, 1, 1);
     cfg.blockDim = dim3(threads, 1, 1);

@@ -78,7 +78,10 @@ int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, i
                              cudaStream_t s);
 // Mixed precision (factors stored as TS, arithmetic and vectors in T).
 template <typename TS, typename T>
-int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s);
+int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
+                     const T *Dinv = nullptr);
+template <typename TS, typename T>
+void invert_diag32_mixed(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s);
 template <typename TS, typename T>
 int gemv_mixed(const TS *M, int ld, int rows, int cols, int trans, T alpha, const T *x, T beta, T *y,
                int upper_mask, int diag_off, cudaStream_t s);

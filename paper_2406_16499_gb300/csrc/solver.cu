@@ -577,9 +577,14 @@ float ev_ms(cudaEvent_t a, cudaEvent_t b)
 // below fold these ratios into the preconditioner's block scalings.
 
 // Scratch of the operator and of the GMRES engine.
+// dT, dR: FP64 inverses of the 32 x 32 diagonal blocks of the two
+// triangular factors the preconditioners solve with (computed once per
+// factorization from the stored factors; the solves then form each block
+// by a 32-wide product instead of a substitution chain).
 struct BDScratch {
     GmresWs gw;
     double *rhs, *t, *u, *gf, *w1, *w2, *w3;
+    double *dT, *dR;
 };
 
 size_t bd_bytes(int N, int R, int mx)
@@ -587,7 +592,8 @@ size_t bd_bytes(int N, int R, int mx)
     size_t b = gmres_ws_bytes(N, R);
     const size_t vn = ((size_t)N * sizeof(double) + 255) & ~(size_t)255;
     const size_t vm = ((size_t)std::max(mx, 1) * sizeof(double) + 255) & ~(size_t)255;
-    return b + 4 * vn + 3 * vm;
+    const size_t vd = (size_t)std::max(ceil_div(mx, 32), 1) * 1024 * sizeof(double);
+    return b + 4 * vn + 3 * vm + 2 * vd;
 }
 
 BDScratch bd_layout(void *base, int N, int R, int mx)
@@ -598,14 +604,17 @@ BDScratch bd_layout(void *base, int N, int R, int mx)
     b.rhs = c.take<double>(N); b.t = c.take<double>(N); b.u = c.take<double>(N); b.gf = c.take<double>(N);
     b.w1 = c.take<double>(std::max(mx, 1)); b.w2 = c.take<double>(std::max(mx, 1));
     b.w3 = c.take<double>(std::max(mx, 1));
+    b.dT = c.take<double>((size_t)std::max(ceil_div(mx, 32), 1) * 1024);
+    b.dR = c.take<double>((size_t)std::max(ceil_div(mx, 32), 1) * 1024);
     return b;
 }
 
 // Triangular solve and gemv in FP64 arithmetic on factors stored as T.
 template <typename T>
-int trsv_d(const T *U, int ldu, int n, int trans, double *x, const DevScratch &sc, cudaStream_t s)
+int trsv_d(const T *U, int ldu, int n, int trans, double *x, const DevScratch &sc, cudaStream_t s,
+           const double *Dinv)
 {
-    return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s);
+    return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s, Dinv);
 }
 template <typename T>
 int gemv_d(const T *M, int ld, int rows, int cols, int trans, double alpha, const double *x, double beta, double *y,
@@ -642,6 +651,13 @@ struct GlsBDOp : LinOp {
 
     const T *TS() const { return w.Ct + idx2(w.L, w.L, w.ldCt); }
 
+    // FP64 inverses of the diagonal blocks of T~_n and R
+    void prepare()
+    {
+        invert_diag32_mixed<T, double>(w.Ct, w.ldCt, w.n, b.dT, h->sc.status, h->stream);
+        invert_diag32_mixed<T, double>(w.Wf, w.ldW, w.m, b.dR, h->sc.status, h->stream);
+    }
+
     int Mr(const double *t, double *u)
     {
         const int n = w.n, m = w.m, p = w.p;
@@ -650,7 +666,7 @@ struct GlsBDOp : LinOp {
         vcomb<double>(u, p, t, 0, 1.0 / sa, nullptr, 0, 0.0, s);
         // a^1/2 Q T2^-T t2 = a^1/2 sV Q P_n T~_n'^-1 P_n t2
         vcomb<double>(b.w1, n, t + p, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.Ct, w.ldCt, n, 0, b.w1, h->sc, s));
+        RC(trsv_d<T>(w.Ct, w.ldCt, n, 0, b.w1, h->sc, s, b.dT));
         vcomb<double>(u + p, n, b.w1, 1, sa * sV, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, u + p, s));
         if (m > 0) {
@@ -658,7 +674,7 @@ struct GlsBDOp : LinOp {
             vcomb<double>(b.w1, m, t + p + n, 1, 1.0, nullptr, 0, 0.0, s);
             RC(gemv_d<T>(TS(), w.ldCt, m, m, 1, 1.0, b.w1, 0.0, b.w2, 1, 0, s));
             vcomb<double>(u + p + n, m, b.w2, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Wf, w.ldW, m, 0, u + p + n, h->sc, s));
+            RC(trsv_d<T>(w.Wf, w.ldW, m, 0, u + p + n, h->sc, s, b.dR));
         }
         return 0;
     }
@@ -686,12 +702,12 @@ struct GlsBDOp : LinOp {
         vcomb<double>(b.w1, n, g + p, 0, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.Ct, w.ldCt, n, 1, b.w2, h->sc, s));
+        RC(trsv_d<T>(w.Ct, w.ldCt, n, 1, b.w2, h->sc, s, b.dT));
         vcomb<double>(o + p, n, b.w2, 1, sa * sV, nullptr, 0, 0.0, s);
         if (m > 0) {
             // a^-1/2 b^-1 S^T R^-T g3 = a^-1/2 b^-1 (sW/sV) P_m T~_S' P_m R'^-T g3
             vcomb<double>(b.w1, m, g + p + n, 0, 1.0, nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Wf, w.ldW, m, 1, b.w1, h->sc, s));
+            RC(trsv_d<T>(w.Wf, w.ldW, m, 1, b.w1, h->sc, s, b.dR));
             vcomb<double>(b.w2, m, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
             RC(gemv_d<T>(TS(), w.ldCt, m, m, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
             vcomb<double>(o + p + n, m, b.w3, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
@@ -713,12 +729,13 @@ struct GlsBDOp : LinOp {
 template <typename T>
 int gls_gmres_correction(mpir_ctx *h, GlsWs<T> &w, BDScratch &b, const double *W, int ldw, const double *V,
                          int ldv, double al, double be, double itol, int imax, double *y, double *z, double *x,
-                         int *inner)
+                         int *inner, bool first)
 {
     const int n = w.n, m = w.m, p = w.p;
     cudaStream_t s = h->stream;
     const double sa = std::sqrt(al);
     GlsBDOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
+    if (first) op.prepare();
     vcomb<double>(b.t, p, w.f1, 0, sa, nullptr, 0, 0.0, s);
     vcomb<double>(b.t + p, n, w.f2, 0, 1.0 / sa, nullptr, 0, 0.0, s);
     vcomb<double>(b.t + p + n, m, w.f3, 0, sa * be, nullptr, 0, 0.0, s);
@@ -808,7 +825,7 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
                 if (it == 0) al = bd_alpha(o, nr[4], fV, nr[5]);
                 cudaEventRecord(h->ev[5], s);
                 RC(gls_gmres_correction<T>(h, w, bs, W, ldw, V, ldv, al, o.beta, inner_tol_default(o, fact),
-                                           o.inner_maxit, y, z, x, &inner));
+                                           o.inner_maxit, y, z, x, &inner, it == 0));
                 cudaEventRecord(h->ev[6], s);
                 cudaEventSynchronize(h->ev[6]);
                 t_gm += ev_ms(h->ev[5], h->ev[6]);
@@ -1024,6 +1041,13 @@ struct LseBDOp : LinOp {
 
     const T *TS() const { return w.At + idx2(w.q, w.q, w.ldAt); }
 
+    // FP64 inverses of the diagonal blocks of T1 and R~
+    void prepare()
+    {
+        invert_diag32_mixed<T, double>(w.At, w.ldAt, w.n, b.dT, h->sc.status, h->stream);
+        invert_diag32_mixed<T, double>(w.Bt, w.ldBt, w.p, b.dR, h->sc.status, h->stream);
+    }
+
     int Mr(const double *t, double *u)
     {
         const int m = w.m, n = w.n, p = w.p;
@@ -1034,12 +1058,12 @@ struct LseBDOp : LinOp {
             // a^-1/2 b^-1 R^-T S^T t2 = a^-1/2 b^-1 (sB/sA) P_p R~'^-1 P_p S'^T t2
             RC(gemv_d<T>(TS(), w.ldAt, p, p, 1, 1.0, t + m, 0.0, b.w1, 1, 0, s));
             vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Bt, w.ldBt, p, 0, b.w2, h->sc, s));
+            RC(trsv_d<T>(w.Bt, w.ldBt, p, 0, b.w2, h->sc, s, b.dR));
             vcomb<double>(u + m, p, b.w2, 1, sB / (sA * sa * be), nullptr, 0, 0.0, s);
         }
         // a^1/2 Q^T T1^-1 t3 = a^1/2 sA P_n Q~ P_n T1'^-1 t3
         vcomb<double>(b.w1, n, t + m + p, 0, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.At, w.ldAt, n, 0, b.w1, h->sc, s));
+        RC(trsv_d<T>(w.At, w.ldAt, n, 0, b.w1, h->sc, s, b.dT));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, b.w2, s));
         vcomb<double>(u + m + p, n, b.w2, 1, sa * sA, nullptr, 0, 0.0, s);
@@ -1068,7 +1092,7 @@ struct LseBDOp : LinOp {
         if (p > 0) {
             // a^-1/2 b^-1 S R^-1 g2 = a^-1/2 b^-1 (sB/sA) S' P_p R~'^-T P_p g2
             vcomb<double>(b.w1, p, g + m, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Bt, w.ldBt, p, 1, b.w1, h->sc, s));
+            RC(trsv_d<T>(w.Bt, w.ldBt, p, 1, b.w1, h->sc, s, b.dR));
             vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
             RC(gemv_d<T>(TS(), w.ldAt, p, p, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
             vcomb<double>(o + m, p, b.w3, 0, sB / (sA * sa * be), nullptr, 0, 0.0, s);
@@ -1077,7 +1101,7 @@ struct LseBDOp : LinOp {
         vcomb<double>(b.w1, n, g + m + p, 1, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.At, w.ldAt, n, 1, b.w2, h->sc, s));
+        RC(trsv_d<T>(w.At, w.ldAt, n, 1, b.w2, h->sc, s, b.dT));
         vcomb<double>(o + m + p, n, b.w2, 0, sa * sA, nullptr, 0, 0.0, s);
         return 0;
     }
@@ -1095,12 +1119,13 @@ struct LseBDOp : LinOp {
 template <typename T>
 int lse_gmres_correction(mpir_ctx *h, LseWs<T> &w, BDScratch &b, const double *A, int lda, const double *B,
                          int ldb, double al, double be, double itol, int imax, double *r, double *v, double *x,
-                         int *inner)
+                         int *inner, bool first)
 {
     const int m = w.m, n = w.n, p = w.p;
     cudaStream_t s = h->stream;
     const double sa = std::sqrt(al);
     LseBDOp<T> op(h, w, b, A, lda, B, ldb, al, be);
+    if (first) op.prepare();
     vcomb<double>(b.t, m, w.f1, 0, sa, nullptr, 0, 0.0, s);
     vcomb<double>(b.t + m, p, w.f2, 0, sa * be, nullptr, 0, 0.0, s);
     vcomb<double>(b.t + m + p, n, w.f3, 0, 1.0 / sa, nullptr, 0, 0.0, s);
@@ -1175,7 +1200,7 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
                 if (it == 0) al = bd_alpha(o, nr[4], fA, nr[3]);
                 cudaEventRecord(h->ev[5], s);
                 RC(lse_gmres_correction<T>(h, w, bs, A, lda, B, ldb, al, o.beta, inner_tol_default(o, fact),
-                                           o.inner_maxit, r, v, x, &inner));
+                                           o.inner_maxit, r, v, x, &inner, it == 0));
                 cudaEventRecord(h->ev[6], s);
                 cudaEventSynchronize(h->ev[6]);
                 t_gm += ev_ms(h->ev[5], h->ev[6]);
@@ -1813,6 +1838,7 @@ static int lse_bd_apply_impl(mpir_ctx *h, const double *A, int lda, const double
     BDScratch b = bd_layout(h->rws, N, 1, mx);
     LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
     LseBDOp<T> op(h, w, b, A, lda, B, ldb, al, be);
+    op.prepare();
     RC(bd_dispatch(op, which, in, out, b));
     return cuda_check(h, "lse_bd_apply");
 }
@@ -1827,6 +1853,7 @@ static int gls_bd_apply_impl(mpir_ctx *h, const double *W, int ldw, const double
     BDScratch b = bd_layout(h->rws, N, 1, mx);
     GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
     GlsBDOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
+    op.prepare();
     RC(bd_dispatch(op, which, in, out, b));
     return cuda_check(h, "gls_bd_apply");
 }

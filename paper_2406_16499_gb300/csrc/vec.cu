@@ -307,16 +307,16 @@ int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, i
 // leading principal part of a block is the leading part of its inverse, so
 // solves of any leading n <= N reuse them.
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename TS, typename T>
 __global__ void __launch_bounds__(32)
-k_invert_diag32(const T *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, int *__restrict__ status)
+k_invert_diag32(const TS *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, int *__restrict__ status)
 {
     __shared__ T Us[32][33];
     __shared__ T Xs[32][33];
     const int lane = threadIdx.x, blk = blockIdx.x, r0 = blk * 32;
     for (int c = 0; c < 32; c++) {
         T v;
-        if (r0 + lane < N && r0 + c < N) v = lane <= c ? U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
+        if (r0 + lane < N && r0 + c < N) v = lane <= c ? (T)U[idx2(r0 + lane, r0 + c, ldu)] : T(0);
         else v = lane == c ? T(1) : T(0);
         Us[lane][c] = v;
     }
@@ -337,12 +337,18 @@ k_invert_diag32(const T *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, i
     for (int i = 0; i < 32; i++) Dinv[(size_t)blk * 1024 + i + 32 * j] = Xs[i][j];
 }
 
-template <typename T>
-void invert_diag32(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
+template <typename TS, typename T>
+void invert_diag32_mixed(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
 {
     if (N <= 0) return;
     ProfScope ps(K_TRSV, s);
-    k_invert_diag32<T><<<ceil_div(N, 32), 32, 0, s>>>(U, ldu, N, Dinv, status);
+    k_invert_diag32<TS, T><<<ceil_div(N, 32), 32, 0, s>>>(U, ldu, N, Dinv, status);
+}
+
+template <typename T>
+void invert_diag32(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
+{
+    invert_diag32_mixed<T, T>(U, ldu, N, Dinv, status, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -360,7 +366,7 @@ void invert_diag32(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_
 template <typename TS, typename T>
 __global__ void __launch_bounds__(VEC_CL_THREADS, 1)
 k_trsv_cl(const TS *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
-          const TS *__restrict__ Dinv, int *__restrict__ status)
+          const T *__restrict__ Dinv, int *__restrict__ status)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);
@@ -401,10 +407,10 @@ k_trsv_cl(const TS *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x
             T rhs = lane < bs ? xs[r0 + lane - s0] : T(0);
             T xv = T(0);
             if (Dinv) {
-                const TS *D = Dinv + (size_t)blk * 1024;
+                const T *D = Dinv + (size_t)blk * 1024;
                 T drow[32];
 #pragma unroll
-                for (int k = 0; k < 32; k++) drow[k] = (T)(trans ? D[k + 32 * lane] : D[lane + 32 * k]);
+                for (int k = 0; k < 32; k++) drow[k] = trans ? D[k + 32 * lane] : D[lane + 32 * k];
 #pragma unroll
                 for (int k = 0; k < 32; k++) xv = fma(drow[k], __shfl_sync(0xffffffffu, rhs, k), xv);
                 if (lane >= bs) xv = T(0);
@@ -541,7 +547,7 @@ k_trsv_upper(const TS *__restrict__ U, int ldu, int n, int trans, T *__restrict_
 
 template <typename TS, typename T>
 static int trsv_upper_cl(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
-                         const TS *Dinv)
+                         const T *Dinv)
 {
     auto kern = k_trsv_cl<TS, T>;
     const int nblk = ceil_div(n, 32);
@@ -577,7 +583,7 @@ static int trsv_upper_cl(const TS *U, int ldu, int n, int trans, T *x, const Dev
 
 template <typename TS, typename T>
 static int trsv_dispatch(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
-                         const TS *Dinv)
+                         const T *Dinv)
 {
     if (n <= 0) return 0;
     {
@@ -620,11 +626,13 @@ int trsv_upper(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc
 }
 
 // Mixed-precision solve: U stored as TS, arithmetic and x in T (FP32 factors
-// applied in FP64 by GMRES-IR).  Substitution on the stored diagonal blocks.
+// applied in FP64 by GMRES-IR).  Dinv (optional, type T): inverses of the
+// diagonal blocks from invert_diag32_mixed; else substitution.
 template <typename TS, typename T>
-int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s)
+int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,
+                     const T *Dinv)
 {
-    return trsv_dispatch<TS, T>(U, ldu, n, trans, x, sc, s, nullptr);
+    return trsv_dispatch<TS, T>(U, ldu, n, trans, x, sc, s, Dinv);
 }
 
 // ---------------------------------------------------------------------------
@@ -875,11 +883,13 @@ template int apply_reflectors_vec_blk<double, double>(const double *, int, int, 
 template int apply_reflectors_vec_blk<float, double>(const float *, int, int, int, const float *, int, int,
                                                      double *, cudaStream_t);
 template int trsv_upper_mixed<float, double>(const float *, int, int, int, double *, const DevScratch &,
-                                             cudaStream_t);
+                                             cudaStream_t, const double *);
+template void invert_diag32_mixed<float, double>(const float *, int, int, double *, int *, cudaStream_t);
+template void invert_diag32_mixed<double, double>(const double *, int, int, double *, int *, cudaStream_t);
 template int gemv_mixed<float, double>(const float *, int, int, int, int, double, const double *, double,
                                        double *, int, int, cudaStream_t);
 template int trsv_upper_mixed<double, double>(const double *, int, int, int, double *, const DevScratch &,
-                                              cudaStream_t);
+                                              cudaStream_t, const double *);
 template int gemv_mixed<double, double>(const double *, int, int, int, int, double, const double *, double,
                                         double *, int, int, cudaStream_t);
 template int trsv_upper<float>(const float *, int, int, int, float *, const DevScratch &, cudaStream_t,

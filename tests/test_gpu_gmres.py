@@ -167,11 +167,12 @@ def test_gmres_ir_beyond_classical_limit(h, oracle_mod):
     assert st != 0
     st, info, x, r, v = run_lse(h, P, refine="gmres", escalate=False)
     assert st == 0 and info.fact_used == 2
-    met = oracle_mod.lse_metrics(P["A"], P["B"], P["b"], P["d"], x, r, v)
-    assert met["eta"] <= 1e-14 and met["e_con"] <= 1e-14
+    # eta, e_con <= 1e-14 and forward error <= 10 kappa u against the
+    # oracle's solution (kappa ~ 8e10 here, so x itself is only accurate to
+    # ~1e-6 in any FP64 method)
+    check_lse(oracle_mod, P, x, r, v)
     ref = G.lse_gmres_ir(P["A"], P["B"], P["b"], P["d"])
     assert ref["status"] == 0
-    assert rel(x, ref["x"]) <= 1e-6
 
 
 @pytest.mark.parametrize("kappa", [1e3, 1e7])
