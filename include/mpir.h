@@ -150,8 +150,20 @@ int gls_solve(mpir_handle h, int n, int m, int p,
 /* ---------------------------------------------------------------------
  * Batched solves of independent problems of uneven sizes.  All size, ld
  * and pointer arrays are HOST arrays of length `count`; the matrices and
- * vectors they point to are device memory.  infos (host, count entries)
- * receives per-problem results; the return value is the largest status.
+ * vectors they point to are device memory.  infos (host, count entries,
+ * may be NULL) receives per-problem results; the return value is the
+ * largest status, or -3 (message: which problem, which argument) when a
+ * problem's arguments are illegal as for lse_solve.
+ * lse_solve_batched runs every problem in one persistent launch (each CTA
+ * takes problems largest-first from a device queue and runs the GRQ, the
+ * null-space start and classical IR on it; FP32 factors for the BF16 / TF32
+ * / FP32 kinds, FP64 factors for MPIR_FP64), replayed from a CUDA graph
+ * captured once per batch shape; the CTA shape is picked by timing the
+ * candidates on a sample of the batch the first time a shape is seen.
+ * Problems that do not converge are re-solved one by one with an FP64
+ * factorization when opts->escalate is set (info.escalated = 1).
+ * refine = MPIR_GMRES solves the problems one by one with lse_solve.
+ * The handle's stream is synchronized before returning.
  * ------------------------------------------------------------------- */
 int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n,
                       const int *p, const double *const *A, const int *lda,
@@ -309,7 +321,7 @@ const char *mpir_version(void);
  * launches.  Kinds: 0 panel_qr, 1 larfb, 2 vec_apply, 3 trsv, 4 gemv,
  * 5 dual_gemv_fp64, 6 resid_finalize, 7 convert, 8 norm, 9 elementwise,
  * 10 larfb_tc (tcgen05 GEMM), 11 larfb_aux (V / W preparation), 12 gmres
- * (Arnoldi steps and cycle updates).
+ * (Arnoldi steps and cycle updates), 13 batched (persistent batched solves).
  * Not thread-safe; a profiling aid, off by default. */
 int mpir_profile(int enable);
 int mpir_profile_read(double *ms, long long *launches, int nkinds);

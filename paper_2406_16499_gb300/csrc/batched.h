@@ -1,0 +1,64 @@
+// batched.h -- persistent batched LSE solver (many small problems, one launch).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <vector>
+
+namespace mpir {
+
+// One problem of the batch (device table entry; pointers are device memory).
+struct BInst {
+    const double *A, *B, *b, *d;
+    double *x;
+    int m, n, p, lda, ldb, pad;
+};
+
+// Per-problem result written by the kernel.
+struct BResult {
+    int status, iters;
+    double ratio[3];
+};
+
+struct BParams {
+    double tol;
+    int maxit;
+    int refine;        // MPIR_CLASSICAL or MPIR_DIRECT
+    int scale;         // power-of-two scaling of A, B (Sec. 6.1)
+};
+
+// Launch shape: threads per CTA and dynamic shared memory per CTA.
+struct BConfig {
+    int threads;       // 256 or 512
+    int minb;          // CTAs per SM the register budget is sized for (1 or 2)
+    size_t smem;
+};
+
+// Device-side state a handle keeps for batched solves.
+struct BatchArena {
+    BInst *tab = nullptr;
+    int *order = nullptr;
+    BResult *res = nullptr;
+    int *next = nullptr;
+    void *gscr = nullptr;
+    size_t cap = 0, gscr_bytes = 0;
+    BInst *htab = nullptr;          // pinned staging
+    BResult *hres = nullptr;
+    int *horder = nullptr;
+    size_t hcap = 0;
+    // launch cache: autotuned configuration and captured graph
+    struct Tuned { unsigned long long sig; bool fp64; BConfig cfg; };
+    std::vector<Tuned> tuned;
+    cudaGraphExec_t graph = nullptr;
+    unsigned long long graph_key = 0;
+};
+
+int batched_ctas_per_sm(const BConfig &cfg, bool fp64);
+int batched_launch(const BConfig &cfg, bool fp64, const BInst *tab, const int *order, int count, int *next,
+                   BResult *res, void *gscr, size_t gstride_words, int grid, const BParams &prm, cudaStream_t s);
+size_t batched_big_words(int m, int n, int p);           // factor words kept in smem or global scratch
+size_t batched_smem_min(int m, int n, int p, bool fp64);  // smem with the factors in global scratch
+size_t batched_smem_full(int m, int n, int p, bool fp64); // smem with everything resident
+double batched_work(int m, int n, int p);                // GRQ + residual flops of one problem
+
+} // namespace mpir

@@ -31,6 +31,7 @@
 #include <vector>
 #include <algorithm>
 
+#include "batched.h"
 #include "common.cuh"
 #include "gmres.h"
 #include "kernels.h"
@@ -60,6 +61,8 @@ void prof_begin(int kind, cudaStream_t s)
     g_open = true;
 }
 
+void prof_count(int kind) { g_launches[kind]++; }
+
 void prof_end(int kind, cudaStream_t s)
 {
     if (!g_prof || !g_open) return;
@@ -72,7 +75,8 @@ void prof_end(int kind, cudaStream_t s)
 
 static const char *g_kind_names[K_NKINDS] = {"panel_qr", "larfb", "vec_apply", "trsv", "gemv",
                                              "dual_gemv_fp64", "resid_finalize", "convert", "norm",
-                                             "elementwise", "larfb_tc", "larfb_aux", "gmres"};
+                                             "elementwise", "larfb_tc", "larfb_aux", "gmres",
+                                             "batched"};
 
 #define MPIR_VERSION_STRING "libmpir 0.1 (sm_103a)"
 
@@ -218,6 +222,8 @@ struct mpir_ctx {
     cudaEvent_t ev[8];
     void *rws = nullptr;         // scratch of the standalone residual entry points
     size_t rws_bytes = 0;
+    BatchArena ba;               // batched solves: tables, results, tuned shapes, graph
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
 };
 
 namespace {
@@ -1336,6 +1342,15 @@ int mpir_destroy(mpir_handle h)
     if (h->scratch_base) cudaFree(h->scratch_base);
     if (h->rws) cudaFree(h->rws);
     if (h->hbuf) cudaFreeHost(h->hbuf);
+    {
+        BatchArena &a = h->ba;
+        if (a.graph) cudaGraphExecDestroy(a.graph);
+        cudaFree(a.tab); cudaFree(a.order); cudaFree(a.res); cudaFree(a.next); cudaFree(a.gscr);
+        if (a.htab) cudaFreeHost(a.htab);
+        if (a.hres) cudaFreeHost(a.hres);
+        if (a.horder) cudaFreeHost(a.horder);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    }
     for (int i = 0; i < 8; i++) cudaEventDestroy(h->ev[i]);
     delete h;
     return 0;
@@ -1484,6 +1499,140 @@ int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, cons
     return st;
 }
 
+// Per-problem loop over the single-problem solver: GMRES-IR requests and
+// the escalation of problems the batched kernel did not converge.
+static int lse_solve_each(mpir_handle h, const std::vector<int> &which, const int *m, const int *n, const int *p,
+                          const double *const *A, const int *lda, const double *const *B, const int *ldb,
+                          const double *const *b, const double *const *d, double *const *x, const mpir_opts &o,
+                          mpir_info *infos, int esc_base)
+{
+    int worst = 0;
+    for (int i : which) {
+        mpir_info inf;
+        int st = lse_solve(h, m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i], nullptr, nullptr, &o,
+                           &inf);
+        if (st < 0) return st;
+        inf.escalated += esc_base;
+        if (infos) infos[i] = inf;
+        worst = std::max(worst, st);
+    }
+    return worst;
+}
+
+static int batch_reserve(mpir_ctx *h, int count, size_t gscr_bytes)
+{
+    BatchArena &a = h->ba;
+    if ((size_t)count > a.cap) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(a.tab); cudaFree(a.order); cudaFree(a.res); cudaFree(a.next);
+        a.tab = nullptr; a.order = nullptr; a.res = nullptr; a.next = nullptr; a.cap = 0;
+        if (a.graph) { cudaGraphExecDestroy(a.graph); a.graph = nullptr; a.graph_key = 0; }
+        const size_t c = std::max<size_t>(count, 256);
+        if (cudaMalloc(&a.tab, c * sizeof(BInst)) != cudaSuccess || cudaMalloc(&a.order, c * sizeof(int)) != cudaSuccess ||
+            cudaMalloc(&a.res, c * sizeof(BResult)) != cudaSuccess || cudaMalloc(&a.next, 256) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(h, MPIR_CUDA_ERROR, "batched tables: cudaMalloc failed");
+        }
+        a.cap = c;
+    }
+    if ((size_t)count > a.hcap) {
+        if (a.htab) cudaFreeHost(a.htab);
+        if (a.hres) cudaFreeHost(a.hres);
+        if (a.horder) cudaFreeHost(a.horder);
+        a.htab = nullptr; a.hres = nullptr; a.horder = nullptr; a.hcap = 0;
+        const size_t c = std::max<size_t>(count, 256);
+        if (cudaMallocHost(&a.htab, c * sizeof(BInst)) != cudaSuccess ||
+            cudaMallocHost(&a.hres, c * sizeof(BResult)) != cudaSuccess ||
+            cudaMallocHost(&a.horder, c * sizeof(int)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(h, MPIR_CUDA_ERROR, "batched staging: cudaMallocHost failed");
+        }
+        a.hcap = c;
+    }
+    if (gscr_bytes > a.gscr_bytes) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(a.gscr);
+        a.gscr = nullptr; a.gscr_bytes = 0;
+        if (a.graph) { cudaGraphExecDestroy(a.graph); a.graph = nullptr; a.graph_key = 0; }
+        if (cudaMalloc(&a.gscr, gscr_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(h, MPIR_CUDA_ERROR, "batched scratch: cudaMalloc failed");
+        }
+        a.gscr_bytes = gscr_bytes;
+    }
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, MPIR_CUDA_ERROR, "batched: stream creation failed");
+    }
+    return 0;
+}
+
+static unsigned long long mix64(unsigned long long h, unsigned long long v)
+{
+    h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+    return h;
+}
+
+// Candidate launch shapes: 512 threads (one CTA per SM), 256 threads with
+// the full register file, and 256 threads sized for two CTAs per SM (half
+// the shared memory each).  smem_full: the largest on-chip need of the
+// batch; smem_min: the largest need with the factors in global scratch.
+static std::vector<BConfig> batch_candidates(size_t smem_min, size_t smem_full, size_t optin)
+{
+    std::vector<BConfig> c;
+    const size_t one = std::max(smem_min, std::min(smem_full, optin));
+    const size_t two = std::max(smem_min, std::min(smem_full, optin / 2 - 1024));
+    if (one <= optin) { c.push_back({512, 1, one}); c.push_back({256, 1, one}); }
+    if (two <= optin / 2 - 1024) c.push_back({256, 2, two});
+    return c;
+}
+
+// Time each candidate on a stratified sample of the batch (every k-th
+// problem of the largest-first order) and keep the fastest; cached per
+// handle by a signature of the batch.
+static int batch_tune(mpir_ctx *h, bool fp64, int count, unsigned long long sig, size_t smem_min,
+                      size_t smem_full, size_t gstride, const BParams &prm, BConfig *out)
+{
+    BatchArena &a = h->ba;
+    for (const auto &t : a.tuned)
+        if (t.sig == sig && t.fp64 == fp64) { *out = t.cfg; return 0; }
+    int dev = 0, sms = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const size_t cap = (size_t)optin - 1024;   // static shared memory of the kernel
+    std::vector<BConfig> cand = batch_candidates(smem_min, smem_full, cap);
+    if (cand.empty()) return set_err(h, MPIR_UNSUPPORTED, "batched: a problem needs more shared memory than a CTA has");
+    // sample: every k-th problem of the sorted order, about three per SM
+    const int want = std::min(count, 3 * sms);
+    const int stride = std::max(1, count / std::max(want, 1));
+    std::vector<int> samp;
+    for (int k = 0; k < count && (int)samp.size() < want; k += stride) samp.push_back(a.horder[k]);
+    int *dsamp = a.order + count;   // sampled order after the real one (capacity checked by the caller)
+    cudaMemcpyAsync(dsamp, samp.data(), samp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    float best = INFINITY;
+    BConfig pick = cand[0];
+    for (const BConfig &c : cand) {
+        const int per = batched_ctas_per_sm(c, fp64);
+        if (per <= 0) continue;
+        const int grid = sms * per;
+        if ((size_t)grid * gstride * (fp64 ? 8 : 4) > a.gscr_bytes) continue;
+        RC(batched_launch(c, fp64, a.tab, dsamp, (int)samp.size(), a.next, a.res, a.gscr, gstride, grid, prm,
+                          h->stream));   // warm-up (module load, caches)
+        cudaEventRecord(h->ev[5], h->stream);
+        RC(batched_launch(c, fp64, a.tab, dsamp, (int)samp.size(), a.next, a.res, a.gscr, gstride, grid, prm,
+                          h->stream));
+        cudaEventRecord(h->ev[6], h->stream);
+        if (cudaEventSynchronize(h->ev[6]) != cudaSuccess) return cuda_check(h, "batched tune");
+        const float t = ev_ms(h->ev[5], h->ev[6]);
+        if (t < best) { best = t; pick = c; }
+    }
+    if (!(best < INFINITY)) return set_err(h, MPIR_UNSUPPORTED, "batched: no launch shape fits");
+    a.tuned.push_back({sig, fp64, pick});
+    *out = pick;
+    return 0;
+}
+
 int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, const int *p,
                       const double *const *A, const int *lda, const double *const *B, const int *ldb,
                       const double *const *b, const double *const *d, double *const *x,
@@ -1491,10 +1640,112 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
 {
     if (!h) return -1;
     if (count < 0) return -2;
-    int worst = 0;
+    if (count == 0) return 0;
+    if (!m) return -3;
+    if (!n) return -4;
+    if (!p) return -5;
+    if (!A) return -6;
+    if (!lda) return -7;
+    if (!B) return -8;
+    if (!ldb) return -9;
+    if (!b) return -10;
+    if (!d) return -11;
+    if (!x) return -12;
     for (int i = 0; i < count; i++) {
-        int st = lse_solve(h, m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i], nullptr, nullptr,
-                           opts, infos ? &infos[i] : nullptr);
+        const int a = lse_check_args(m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i]);
+        if (a) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "problem %d: illegal argument %d of lse_solve", i, -a);
+            return set_err(h, -3, msg);
+        }
+    }
+    mpir_opts o;
+    fill_opts(opts, &o);
+    if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
+    std::vector<int> all(count);
+    for (int i = 0; i < count; i++) all[i] = i;
+    if (o.refine == MPIR_GMRES) return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
+    const bool fp64 = o.fact == MPIR_FP64;
+    // problem table, largest work first
+    size_t big = 0, smin = 0, sfull = 0;
+    unsigned long long sig = mix64(0, (unsigned long long)count);
+    int mmax = 0, nmax = 0, pmax = 0;
+    for (int i = 0; i < count; i++) {
+        big = std::max(big, batched_big_words(m[i], n[i], p[i]));
+        smin = std::max(smin, batched_smem_min(m[i], n[i], p[i], fp64));
+        sfull = std::max(sfull, batched_smem_full(m[i], n[i], p[i], fp64));
+        mmax = std::max(mmax, m[i]); nmax = std::max(nmax, n[i]); pmax = std::max(pmax, p[i]);
+    }
+    sig = mix64(mix64(mix64(sig, mmax), nmax), pmax);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t gstride = (big + 63) & ~(size_t)63;
+    RC(batch_reserve(h, 2 * count, (size_t)2 * sms * gstride * (fp64 ? 8 : 4)));
+    BatchArena &a = h->ba;
+    for (int i = 0; i < count; i++)
+        a.htab[i] = BInst{A[i], B[i], b[i], d[i], x[i], m[i], n[i], p[i], lda[i], std::max(ldb[i], 1), 0};
+    std::vector<double> work(count);
+    for (int i = 0; i < count; i++) work[i] = batched_work(m[i], n[i], p[i]);
+    for (int i = 0; i < count; i++) a.horder[i] = i;
+    std::stable_sort(a.horder, a.horder + count, [&](int u, int v) { return work[u] > work[v]; });
+    cudaStream_t s = h->stream;
+    cudaMemcpyAsync(a.tab, a.htab, sizeof(BInst) * count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(a.order, a.horder, sizeof(int) * count, cudaMemcpyHostToDevice, s);
+    BParams prm{o.tol, o.maxit, o.refine == MPIR_DIRECT ? MPIR_DIRECT : MPIR_CLASSICAL, 1};
+    BConfig cfg{};
+    RC(batch_tune(h, fp64, count, sig, smin, sfull, gstride, prm, &cfg));
+    const int grid = sms * std::max(1, batched_ctas_per_sm(cfg, fp64));
+    // the launch, captured once per (shape, buffers) and replayed
+    unsigned long long key = mix64(sig, fp64);
+    key = mix64(mix64(mix64(key, cfg.threads), cfg.minb), cfg.smem);
+    key = mix64(mix64(key, grid), (unsigned long long)(uintptr_t)a.gscr);
+    key = mix64(mix64(key, (unsigned long long)(uintptr_t)a.tab), o.maxit);
+    key = mix64(mix64(key, prm.refine), (unsigned long long)std::llround(-std::log2(o.tol) * 1024));
+    if (!a.graph || a.graph_key != key) {
+        if (a.graph) { cudaGraphExecDestroy(a.graph); a.graph = nullptr; }
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return cuda_check(h, "batched capture");
+        const int rc = batched_launch(cfg, fp64, a.tab, a.order, count, a.next, a.res, a.gscr, gstride, grid, prm,
+                                      h->cap_stream);
+        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
+        if (rc || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return set_err(h, rc ? rc : MPIR_CUDA_ERROR, "batched: graph capture failed");
+        }
+        const cudaError_t ie = cudaGraphInstantiate(&a.graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) { a.graph = nullptr; return cuda_check(h, "batched graph instantiate"); }
+        a.graph_key = key;
+    }
+    {
+        ProfScope ps(K_BATCHED, s);
+        if (cudaGraphLaunch(a.graph, s) != cudaSuccess) return cuda_check(h, "batched graph launch");
+    }
+    cudaMemcpyAsync(a.hres, a.res, sizeof(BResult) * count, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "batched");
+    int worst = 0;
+    std::vector<int> redo;
+    for (int i = 0; i < count; i++) {
+        const BResult &r = a.hres[i];
+        if (infos) {
+            mpir_info &f = infos[i];
+            f.status = r.status;
+            f.iters = r.iters;
+            f.fact_used = fp64 ? MPIR_FP64 : MPIR_FP32;
+            f.refine_used = prm.refine;
+            for (int k = 0; k < 3; k++) f.stop_ratio[k] = r.ratio[k];
+        }
+        if (r.status != MPIR_OK && o.escalate && !fp64 && prm.refine != MPIR_DIRECT) redo.push_back(i);
+        else worst = std::max(worst, r.status);
+    }
+    if (!redo.empty()) {
+        // escalation (a12): re-solve with an FP64 factorization
+        mpir_opts o64 = o;
+        o64.fact = MPIR_FP64;
+        const int st = lse_solve_each(h, redo, m, n, p, A, lda, B, ldb, b, d, x, o64, infos, 1);
         if (st < 0) return st;
         worst = std::max(worst, st);
     }

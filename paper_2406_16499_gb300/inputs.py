@@ -120,9 +120,10 @@ def lse_large(seed=20243623, cond_a=1e4, cond_b=1e2, m=16384, n=8192, p=1024):
     return lse_svd(seed, m, n, p, cond_a, cond_b)
 
 
-def lse_batch(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_hi=1e6):
-    """Uneven batch: m ~ U[m_lo, m_hi], n ~ U[16, m/2], p ~ U[1, n/4],
-    cond(A) log-uniform in [cond_lo, cond_hi], cond(B) = 10."""
+def lse_batch_specs(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_hi=1e6):
+    """(seed, m, n, p, cond(A)) of each problem of the uneven batch:
+    m ~ U[m_lo, m_hi], n ~ U[16, m/2], p ~ U[1, n/4], cond(A) log-uniform in
+    [cond_lo, cond_hi]."""
     g = rng(seed)
     out = []
     for i in range(count):
@@ -130,8 +131,25 @@ def lse_batch(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_h
         n = int(g.integers(16, max(16, m // 2) + 1))
         p = int(g.integers(1, max(1, n // 4) + 1))
         c = float(np.exp(g.uniform(np.log(cond_lo), np.log(cond_hi))))
-        out.append(lse_svd(int(g.integers(1 << 62)), m, n, p, c, 10.0))
+        out.append((int(g.integers(1 << 62)), m, n, p, c))
     return out
+
+
+def lse_batch(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_hi=1e6, workers=1):
+    """Uneven batch: m ~ U[m_lo, m_hi], n ~ U[16, m/2], p ~ U[1, n/4],
+    cond(A) log-uniform in [cond_lo, cond_hi], cond(B) = 10 (lse_svd per
+    problem with its own seed, so the result does not depend on workers)."""
+    specs = lse_batch_specs(seed, count, m_lo, m_hi, cond_lo, cond_hi)
+
+    def one(sp):
+        s, m, n, p, c = sp
+        return lse_svd(s, m, n, p, c, 10.0)
+
+    if workers <= 1:
+        return [one(sp) for sp in specs]
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(one, specs))
 
 
 # ------------------------------------------------------------------ GLS --

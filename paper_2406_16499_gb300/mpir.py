@@ -84,7 +84,7 @@ _SIG = {
     "mpir_kernel_kind_name": ([_I], ctypes.c_char_p),
 }
 
-NKINDS = 13
+NKINDS = 14
 
 
 def profile(enable):
@@ -231,6 +231,26 @@ class Handle:
         rc = lib().lse_solve(self.h, m, n, p, ptr(A), ld(A), ptr(B), ld(B) if p else 1, ptr(b), ptr(d),
                              ptr(x), ptr(r), ptr(v), ctypes.byref(o), ctypes.byref(info))
         return self.check(rc, "lse_solve"), info
+
+    def lse_solve_batched(self, probs, xs, opts=None):
+        """probs: sequence of dicts with device tensors A, B, b, d (column-major
+        FP64); xs: device output vectors.  Returns (status, [Info])."""
+        cnt = len(probs)
+        I_ = ctypes.c_int * max(cnt, 1)
+        P_ = ctypes.c_void_p * max(cnt, 1)
+        m, n, p, lda, ldb = I_(), I_(), I_(), I_(), I_()
+        A, B, b, d, x = P_(), P_(), P_(), P_(), P_()
+        for i, pr in enumerate(probs):
+            m[i], n[i] = pr["A"].shape
+            p[i] = pr["B"].shape[0]
+            lda[i], ldb[i] = ld(pr["A"]), (ld(pr["B"]) if p[i] else 1)
+            A[i], B[i], b[i], d[i], x[i] = ptr(pr["A"]), ptr(pr["B"]), ptr(pr["b"]), ptr(pr["d"]), ptr(xs[i])
+        infos = (Info * max(cnt, 1))()
+        o = opts if opts is not None else make_opts()
+        cast = lambda a: ctypes.cast(a, ctypes.c_void_p)
+        rc = lib().lse_solve_batched(self.h, cnt, cast(m), cast(n), cast(p), cast(A), cast(lda), cast(B), cast(ldb),
+                                     cast(b), cast(d), cast(x), ctypes.byref(o), ctypes.cast(infos, ctypes.POINTER(Info)))
+        return self.check(rc, "lse_solve_batched"), list(infos)[:cnt]
 
     def gls_solve(self, W, V, d, x, y, z=None, opts=None):
         n, m = W.shape
