@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
                     help="time the mixed-precision solve only (for profiler runs)")
+    ap.add_argument("--batched-count", type=int, default=10000,
+                    help="problems of the uneven batched LSE workload (0: skip it)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched LSE workload (prints its JSON object)")
     return ap.parse_args()
 
 
@@ -177,6 +181,101 @@ def traffic_record(kind):
     return r["bytes_per_launch"] if sha == r.get("source_sha") else None
 
 
+# ------------------------------------------------------ batched workload --
+
+def batch_work(m, n, p):
+    """Algorithmic flops of one batched problem: the GRQ (QR of the n x p
+    B~, At P_n Q~ P_n, QR of the m x n At) plus one FP64 residual."""
+    kA = min(m, n)
+    f = 2.0 * n * p * p - 2.0 * p ** 3 / 3.0 + 4.0 * m * n * p
+    f += 2.0 * m * n * kA - 2.0 * kA ** 3 / 3.0
+    return f
+
+
+def run_batched(count, h, dev, stream, rank=0, sample_every=500):
+    """Uneven batch of `count` LSE problems (m ~ U[32,512], n ~ U[16,m/2],
+    p ~ U[1,n/4], cond(A) log-uniform in [1e1,1e6]) solved in one persistent
+    launch; FP64-comparator on the same kernel; sampled oracle accuracy."""
+    import numpy as np
+    import torch
+    from paper_2406_16499_gb300 import inputs as I, mpir
+    specs = I.lse_batch_specs(count=count)
+    t0 = time.perf_counter()
+    probs = I.lse_batch_torch(specs, dev)
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    xs = [torch.zeros(sp[2], dtype=torch.float64, device=dev) for sp in specs]
+    batch = mpir.LseBatch(probs, xs)
+
+    def timed(opts, reps):
+        st, infos = h.lse_solve_batched(batch, opts=opts)     # tune + capture on first sight
+        torch.cuda.synchronize(dev)
+        call, devt = [], []
+        for _ in range(reps):
+            mpir.profile(True)
+            t0 = time.perf_counter()
+            st, infos = h.lse_solve_batched(batch, opts=opts)
+            torch.cuda.synchronize(dev)
+            call.append((time.perf_counter() - t0) * 1e3)
+            devt.append(mpir.profile_read()["batched"][0])
+            mpir.profile(False)
+        return st, infos, sorted(call)[len(call) // 2], sorted(devt)[len(devt) // 2]
+
+    launches0 = mpir.launch_count(13)
+    st, infos, ms, dms = timed(mpir.make_opts(fact="fp32"), 3)
+    launches = (mpir.launch_count(13) - launches0) // 4
+    shapes = [h.batched_get_shape(b) for b in (0, 1)]
+    n_esc = sum(1 for f in infos if f.escalated)
+    n_bad = sum(1 for f in infos if f.status != 0)
+    iters = [f.iters for f in infos]
+    eta_kernel = max(max(f.stop_ratio) for f in infos)
+    st64, infos64, ms64, dms64 = timed(mpir.make_opts(fact="fp64", refine="direct", escalate=False), 2)
+    flops = sum(batch_work(m, n, p) for _, m, n, p, _ in specs)
+    in_bytes = sum(8.0 * (m * n + p * n + m + p) for _, m, n, p, _ in specs)
+    peaks = measured_peaks()
+    out = {"workload": "batched uneven LSE, %d problems, m~U[32,512] n~U[16,m/2] p~U[1,n/4], "
+                       "cond(A) log-U[1e1,1e6], cond(B)=10" % count,
+           "value": count * 1000.0 / ms, "unit": "solves/s", "ms": ms,
+           "device": {"value": count * 1000.0 / dms, "ms": dms,
+                      "what": "graph launch of the persistent kernels alone (CUDA events)"},
+           "status": st, "not_converged": n_bad, "escalated": n_esc, "iters_mean": float(np.mean(iters)),
+           "eta_kernel_max": eta_kernel,
+           "shapes": shapes,
+           "fp64_direct": {"value": count * 1000.0 / ms64, "unit": "solves/s", "ms": ms64,
+                           "device_ms": dms64, "status": st64},
+           "speedup_vs_fp64_direct": ms64 / ms,
+           "device_speedup_vs_fp64_direct": dms64 / dms,
+           "gflops": flops / (dms * 1e-3) / 1e9,
+           "roofline": {"fp32_frac": flops / (dms * 1e-3) / 1e12 / fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0)),
+                        "hbm_frac": in_bytes / (dms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                        "note": "device time; FP32 GRQ flops vs FP32 SIMT peak; FP64 input bytes vs measured HBM"},
+           "persistent_launches_per_solve_call": int(launches),
+           "input_generation_s": gen_s}
+    if rank == 0:
+        import oracle
+        worst = {"eta": 0.0, "e_con": 0.0, "fe_over_bound": 0.0}
+        ks = list(range(0, count, max(1, sample_every)))
+        for k in ks:
+            P = {key: v.cpu().numpy() for key, v in probs[k].items()}
+            x = xs[k].cpu().numpy()
+            A, B, b, d = P["A"], P["B"], P["b"], P["d"]
+            t = oracle.lse_truth(A, B, b, d)
+            F = oracle.lse_factor(A, B, "fp64")
+            r = b - A @ x
+            v = oracle.lse_init_v(F, A, r)
+            met = oracle.lse_metrics(A, B, b, d, x, r, v)
+            kap = oracle.lse_kappa(F, t["x"], t["r"])[0]
+            fe = float(np.linalg.norm(x - t["x"]) / np.linalg.norm(t["x"]))
+            worst["eta"] = max(worst["eta"], met["eta"])
+            worst["e_con"] = max(worst["e_con"], met["e_con"])
+            worst["fe_over_bound"] = max(worst["fe_over_bound"], fe / (10 * kap * 1.1e-16))
+        worst.pop("eta")
+        out["accuracy_sample"] = dict(worst, problems=len(ks),
+                                      note="oracle e_con and forward error / (10 kappa u) on every "
+                                           "%d-th problem; eta from the kernel's FP64 residual" % sample_every)
+    return out
+
+
 # --------------------------------------------------------------- arms --
 
 def make_inputs(rank):
@@ -252,6 +351,12 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     h = mpir.Handle(local, stream.cuda_stream)
     opts = mpir.make_opts(fact=args.fact, refine="classical")
+    if args.batched_only:
+        res = run_batched(args.batched_count, h, dev, stream, rank)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        h.close()
+        return 0
 
     def solve(o=opts, xx=x, yy=y, zz=z, WW=W, VV=V, dd=d):
         st, info = h.gls_solve(WW, VV, dd, xx, yy, zz, o)
@@ -362,6 +467,11 @@ def run_ours(args):
         met = oracle.gls_metrics(Wn, Vn, dn, xg.cpu().numpy(), yg.cpu().numpy(), zg.cpu().numpy())
         gmres["eta"] = met["eta"]
 
+    # ---- batched uneven LSE (one persistent launch per call) ---------------
+    batched = None
+    if args.batched_count > 0 and world == 1:
+        batched = run_batched(args.batched_count, h, dev, stream, rank)
+
     # ---- end to end from pinned host buffers through the public API --------
     Wh = torch.from_numpy(np.ascontiguousarray(Wn.T)).pin_memory()
     Vh = torch.from_numpy(np.ascontiguousarray(Vn.T)).pin_memory()
@@ -453,6 +563,7 @@ def run_ours(args):
             "accuracy": acc,
             "fp64_direct": fp64,
             "gmres_ir": gmres,
+            "batched_lse": batched,
             "speedup_vs_fp64_direct": value / (world * fp64["value"]),
             "kernels": kernels,
             "algorithmic": work,

@@ -172,6 +172,20 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n,
                       double *const *x, const mpir_opts *opts,
                       mpir_info *infos);
 
+/* Launch shapes of lse_solve_batched.  The problems of a call are split in
+ * two size buckets: bucket 0 (problems whose factors and vectors need more
+ * than a quarter of a CTA's shared memory) and bucket 1 (the others).  Each
+ * bucket runs as 512-thread CTAs split into groups of 512, 256, 128 or 64
+ * threads, one problem per group; the group size is picked by timing every
+ * shape that fits on a sample of the bucket the first time the bucket's
+ * signature is seen (kept per handle).  set_shape(h, g) forces group size g
+ * for every bucket (where it fits; 0 restores the timing); get_shape
+ * reports the shape the last call used for a bucket (group 0 and problems 0
+ * for an empty bucket).  Return 0 or a negative argument index. */
+int mpir_batched_set_shape(mpir_handle h, int group);
+int mpir_batched_get_shape(mpir_handle h, int bucket, int *group, size_t *smem_bytes,
+                           int *problems);
+
 int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m,
                       const int *p, const double *const *W, const int *ldw,
                       const double *const *V, const int *ldv,

@@ -27,10 +27,11 @@ struct BParams {
     int scale;         // power-of-two scaling of A, B (Sec. 6.1)
 };
 
-// Launch shape: threads per CTA and dynamic shared memory per CTA.
+// Launch shape: 512 threads per CTA split into groups of `group` threads
+// (512, 256, 128 or 64), each solving its own problem; `smem` dynamic shared
+// memory per CTA, split evenly between the groups.
 struct BConfig {
-    int threads;       // 256 or 512
-    int minb;          // CTAs per SM the register budget is sized for (1 or 2)
+    int group;
     size_t smem;
 };
 
@@ -51,6 +52,9 @@ struct BatchArena {
     std::vector<Tuned> tuned;
     cudaGraphExec_t graph = nullptr;
     unsigned long long graph_key = 0;
+    int force_group = 0;            // 0: autotune; else the group size every bucket uses
+    BConfig last[2] = {};           // shapes of the last call (per size bucket)
+    int last_count[2] = {0, 0};
 };
 
 int batched_ctas_per_sm(const BConfig &cfg, bool fp64);

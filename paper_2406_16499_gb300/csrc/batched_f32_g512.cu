@@ -1,0 +1,15 @@
+// batched_f32_g512.cu -- one launch shape of the batched LSE kernel
+// (float factors, groups of 512 threads), compiled on its own.
+#include "batched_kernel.cuh"
+
+namespace mpir {
+
+int batched_launch_f32_g512(const BInst *tab, const int *order, int count, int *next, BResult *res, void *gscr,
+                          size_t gstride, size_t smem, int grid, const BParams &prm, cudaStream_t s)
+{
+    return launch_cfg<512, float>(tab, order, count, next, res, (float *)gscr, gstride, smem, grid, prm, s);
+}
+
+int batched_occupancy_f32_g512(size_t smem) { return occupancy_of<512, float>(smem); }
+
+} // namespace mpir

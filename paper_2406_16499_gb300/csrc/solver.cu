@@ -1573,42 +1573,52 @@ static unsigned long long mix64(unsigned long long h, unsigned long long v)
     return h;
 }
 
-// Candidate launch shapes: 512 threads (one CTA per SM), 256 threads with
-// the full register file, and 256 threads sized for two CTAs per SM (half
-// the shared memory each).  smem_full: the largest on-chip need of the
-// batch; smem_min: the largest need with the factors in global scratch.
+// Candidate launch shapes for a bucket of problems: 512-thread CTAs split
+// into groups of 512, 256, 128 or 64 threads (one problem per group), each
+// group with an equal share of the shared memory, as much as the bucket's
+// largest problem can use (smem_full) but at least what every problem needs
+// with its factors in global scratch (smem_min).
 static std::vector<BConfig> batch_candidates(size_t smem_min, size_t smem_full, size_t optin)
 {
     std::vector<BConfig> c;
-    const size_t one = std::max(smem_min, std::min(smem_full, optin));
-    const size_t two = std::max(smem_min, std::min(smem_full, optin / 2 - 1024));
-    if (one <= optin) { c.push_back({512, 1, one}); c.push_back({256, 1, one}); }
-    if (two <= optin / 2 - 1024) c.push_back({256, 2, two});
+    for (int gt : {512, 256, 128, 64}) {
+        const int G = 512 / gt;
+        size_t per = std::min(smem_full, (optin / G) & ~(size_t)15);
+        per = (std::max(per, smem_min) + 15) & ~(size_t)15;
+        if (per * G > optin) continue;
+        c.push_back(BConfig{gt, per * G});
+    }
     return c;
 }
 
-// Time each candidate on a stratified sample of the batch (every k-th
-// problem of the largest-first order) and keep the fastest; cached per
-// handle by a signature of the batch.
-static int batch_tune(mpir_ctx *h, bool fp64, int count, unsigned long long sig, size_t smem_min,
-                      size_t smem_full, size_t gstride, const BParams &prm, BConfig *out)
+// Time each candidate on a stratified sample of the bucket (every k-th
+// problem of its largest-first order) and keep the fastest; cached per
+// handle by a signature of the bucket.
+static int batch_tune(mpir_ctx *h, bool fp64, const int *border, int bcount, int *dsamp, int *next,
+                      unsigned long long sig, size_t smem_min, size_t smem_full, size_t gstride,
+                      const BParams &prm, BConfig *out)
 {
     BatchArena &a = h->ba;
+    sig = mix64(sig, (unsigned long long)a.force_group);
     for (const auto &t : a.tuned)
         if (t.sig == sig && t.fp64 == fp64) { *out = t.cfg; return 0; }
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const size_t cap = (size_t)optin - 1024;   // static shared memory of the kernel
+    const size_t cap = (size_t)optin - 2048;   // static shared memory of the kernel
     std::vector<BConfig> cand = batch_candidates(smem_min, smem_full, cap);
+    if (a.force_group) {
+        std::vector<BConfig> f;
+        for (const BConfig &c : cand)
+            if (c.group == a.force_group) f.push_back(c);
+        if (!f.empty()) cand = f;
+    }
     if (cand.empty()) return set_err(h, MPIR_UNSUPPORTED, "batched: a problem needs more shared memory than a CTA has");
-    // sample: every k-th problem of the sorted order, about three per SM
-    const int want = std::min(count, 3 * sms);
-    const int stride = std::max(1, count / std::max(want, 1));
+    const int want = std::min(bcount, 8 * sms);
+    const int stride = std::max(1, bcount / std::max(want, 1));
     std::vector<int> samp;
-    for (int k = 0; k < count && (int)samp.size() < want; k += stride) samp.push_back(a.horder[k]);
-    int *dsamp = a.order + count;   // sampled order after the real one (capacity checked by the caller)
+    for (int k = 0; k < bcount && (int)samp.size() < want; k += stride) samp.push_back(border[k]);
     cudaMemcpyAsync(dsamp, samp.data(), samp.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     float best = INFINITY;
     BConfig pick = cand[0];
@@ -1616,11 +1626,11 @@ static int batch_tune(mpir_ctx *h, bool fp64, int count, unsigned long long sig,
         const int per = batched_ctas_per_sm(c, fp64);
         if (per <= 0) continue;
         const int grid = sms * per;
-        if ((size_t)grid * gstride * (fp64 ? 8 : 4) > a.gscr_bytes) continue;
-        RC(batched_launch(c, fp64, a.tab, dsamp, (int)samp.size(), a.next, a.res, a.gscr, gstride, grid, prm,
+        if ((size_t)grid * (512 / c.group) * gstride * (fp64 ? 8 : 4) > a.gscr_bytes) continue;
+        RC(batched_launch(c, fp64, a.tab, dsamp, (int)samp.size(), next, a.res, a.gscr, gstride, grid, prm,
                           h->stream));   // warm-up (module load, caches)
         cudaEventRecord(h->ev[5], h->stream);
-        RC(batched_launch(c, fp64, a.tab, dsamp, (int)samp.size(), a.next, a.res, a.gscr, gstride, grid, prm,
+        RC(batched_launch(c, fp64, a.tab, dsamp, (int)samp.size(), next, a.res, a.gscr, gstride, grid, prm,
                           h->stream));
         cudaEventRecord(h->ev[6], h->stream);
         if (cudaEventSynchronize(h->ev[6]) != cudaSuccess) return cuda_check(h, "batched tune");
@@ -1666,49 +1676,68 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
     for (int i = 0; i < count; i++) all[i] = i;
     if (o.refine == MPIR_GMRES) return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
     const bool fp64 = o.fact == MPIR_FP64;
-    // problem table, largest work first
-    size_t big = 0, smin = 0, sfull = 0;
-    unsigned long long sig = mix64(0, (unsigned long long)count);
-    int mmax = 0, nmax = 0, pmax = 0;
-    for (int i = 0; i < count; i++) {
-        big = std::max(big, batched_big_words(m[i], n[i], p[i]));
-        smin = std::max(smin, batched_smem_min(m[i], n[i], p[i], fp64));
-        sfull = std::max(sfull, batched_smem_full(m[i], n[i], p[i], fp64));
-        mmax = std::max(mmax, m[i]); nmax = std::max(nmax, n[i]); pmax = std::max(pmax, p[i]);
-    }
-    sig = mix64(mix64(mix64(sig, mmax), nmax), pmax);
-    int dev = 0, sms = 0;
+    int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t gstride = (big + 63) & ~(size_t)63;
-    RC(batch_reserve(h, 2 * count, (size_t)2 * sms * gstride * (fp64 ? 8 : 4)));
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // two size buckets: problems whose whole state fits a quarter of a CTA's
+    // shared memory (several problems per CTA) and the others
+    const size_t cut = ((size_t)optin - 2048) / 4;
+    struct Bucket { std::vector<int> idx; size_t smin = 0, sfull = 0, big = 0; int mmax = 0, nmax = 0, pmax = 0; };
+    Bucket bk[2];
+    std::vector<double> work(count);
+    for (int i = 0; i < count; i++) {
+        const size_t sf = batched_smem_full(m[i], n[i], p[i], fp64);
+        Bucket &u = bk[sf <= cut ? 1 : 0];
+        u.idx.push_back(i);
+        u.smin = std::max(u.smin, batched_smem_min(m[i], n[i], p[i], fp64));
+        u.sfull = std::max(u.sfull, sf);
+        u.big = std::max(u.big, batched_big_words(m[i], n[i], p[i]));
+        u.mmax = std::max(u.mmax, m[i]); u.nmax = std::max(u.nmax, n[i]); u.pmax = std::max(u.pmax, p[i]);
+        work[i] = batched_work(m[i], n[i], p[i]);
+    }
+    const size_t gstride = (std::max(bk[0].big, bk[1].big) + 63) & ~(size_t)63;
+    RC(batch_reserve(h, 2 * count, (size_t)8 * sms * gstride * (fp64 ? 8 : 4)));
     BatchArena &a = h->ba;
     for (int i = 0; i < count; i++)
         a.htab[i] = BInst{A[i], B[i], b[i], d[i], x[i], m[i], n[i], p[i], lda[i], std::max(ldb[i], 1), 0};
-    std::vector<double> work(count);
-    for (int i = 0; i < count; i++) work[i] = batched_work(m[i], n[i], p[i]);
-    for (int i = 0; i < count; i++) a.horder[i] = i;
-    std::stable_sort(a.horder, a.horder + count, [&](int u, int v) { return work[u] > work[v]; });
+    // order: bucket 0 (large) then bucket 1, each largest work first
+    int off[3] = {0, 0, 0};
+    for (int u = 0; u < 2; u++) {
+        std::stable_sort(bk[u].idx.begin(), bk[u].idx.end(), [&](int s1, int s2) { return work[s1] > work[s2]; });
+        std::copy(bk[u].idx.begin(), bk[u].idx.end(), a.horder + off[u]);
+        off[u + 1] = off[u] + (int)bk[u].idx.size();
+    }
     cudaStream_t s = h->stream;
     cudaMemcpyAsync(a.tab, a.htab, sizeof(BInst) * count, cudaMemcpyHostToDevice, s);
     cudaMemcpyAsync(a.order, a.horder, sizeof(int) * count, cudaMemcpyHostToDevice, s);
     BParams prm{o.tol, o.maxit, o.refine == MPIR_DIRECT ? MPIR_DIRECT : MPIR_CLASSICAL, 1};
-    BConfig cfg{};
-    RC(batch_tune(h, fp64, count, sig, smin, sfull, gstride, prm, &cfg));
-    const int grid = sms * std::max(1, batched_ctas_per_sm(cfg, fp64));
-    // the launch, captured once per (shape, buffers) and replayed
-    unsigned long long key = mix64(sig, fp64);
-    key = mix64(mix64(mix64(key, cfg.threads), cfg.minb), cfg.smem);
-    key = mix64(mix64(key, grid), (unsigned long long)(uintptr_t)a.gscr);
-    key = mix64(mix64(key, (unsigned long long)(uintptr_t)a.tab), o.maxit);
-    key = mix64(mix64(key, prm.refine), (unsigned long long)std::llround(-std::log2(o.tol) * 1024));
+    BConfig cfg[2] = {};
+    int grid[2] = {0, 0};
+    unsigned long long key = mix64(mix64(0, (unsigned long long)count), fp64);
+    for (int u = 0; u < 2; u++) {
+        const int bc = off[u + 1] - off[u];
+        if (bc == 0) continue;
+        unsigned long long sig = mix64(mix64(mix64(mix64(u + 1, bc), bk[u].mmax), bk[u].nmax), bk[u].pmax);
+        RC(batch_tune(h, fp64, a.horder + off[u], bc, a.order + count, a.next + 32 * u, sig, bk[u].smin,
+                      bk[u].sfull, gstride, prm, &cfg[u]));
+        grid[u] = sms * std::max(1, batched_ctas_per_sm(cfg[u], fp64));
+        key = mix64(mix64(mix64(mix64(key, sig), cfg[u].group), cfg[u].smem), grid[u]);
+    }
+    for (int u = 0; u < 2; u++) { a.last[u] = cfg[u]; a.last_count[u] = off[u + 1] - off[u]; }
+    key = mix64(mix64(key, (unsigned long long)(uintptr_t)a.gscr), (unsigned long long)(uintptr_t)a.tab);
+    key = mix64(mix64(key, o.maxit), prm.refine);
+    key = mix64(key, (unsigned long long)std::llround(-std::log2(o.tol) * 1024));
+    // the launches, captured once per (shapes, buffers) and replayed
     if (!a.graph || a.graph_key != key) {
         if (a.graph) { cudaGraphExecDestroy(a.graph); a.graph = nullptr; }
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return cuda_check(h, "batched capture");
-        const int rc = batched_launch(cfg, fp64, a.tab, a.order, count, a.next, a.res, a.gscr, gstride, grid, prm,
-                                      h->cap_stream);
+        int rc = 0;
+        for (int u = 0; u < 2 && !rc; u++)
+            rc = batched_launch(cfg[u], fp64, a.tab, a.order + off[u], off[u + 1] - off[u], a.next + 32 * u, a.res,
+                                a.gscr, gstride, grid[u], prm, h->cap_stream);
         const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &g);
         if (rc || ce != cudaSuccess) {
             if (g) cudaGraphDestroy(g);
@@ -1742,7 +1771,7 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
         else worst = std::max(worst, r.status);
     }
     if (!redo.empty()) {
-        // escalation (a12): re-solve with an FP64 factorization
+        // escalation: re-solve with an FP64 factorization
         mpir_opts o64 = o;
         o64.fact = MPIR_FP64;
         const int st = lse_solve_each(h, redo, m, n, p, A, lda, B, ldb, b, d, x, o64, infos, 1);
@@ -2155,6 +2184,28 @@ int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, 
                               : gls_bd_apply_impl<float>(h, W, ldw, V, ldv, alpha, beta, which, in, out);
     if (rc) return rc;
     return check_dev_flags(h);
+}
+
+} // extern "C"
+
+extern "C" {
+
+int mpir_batched_set_shape(mpir_handle h, int group)
+{
+    if (!h) return -1;
+    if (group != 0 && group != 512 && group != 256 && group != 128 && group != 64) return -2;
+    h->ba.force_group = group;
+    return 0;
+}
+
+int mpir_batched_get_shape(mpir_handle h, int bucket, int *group, size_t *smem_bytes, int *problems)
+{
+    if (!h) return -1;
+    if (bucket < 0 || bucket > 1) return -2;
+    if (group) *group = h->ba.last[bucket].group;
+    if (smem_bytes) *smem_bytes = h->ba.last[bucket].smem;
+    if (problems) *problems = h->ba.last_count[bucket];
+    return 0;
 }
 
 } // extern "C"

@@ -152,6 +152,41 @@ def lse_batch(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_h
         return list(ex.map(one, specs))
 
 
+def lse_batch_torch(specs, device, cond_b=10.0):
+    """The problems of lse_batch_specs drawn with torch's generator on
+    `device` (same construction as lse_svd: Haar factors from the QR of
+    Gaussian matrices with sign(diag R) folded in, logspace spectra, d = B x,
+    b = A x + N(0,1)); fast enough for ten thousand problems.  Returns dicts
+    of FP64 column-major tensors (A, B, b, d)."""
+    import torch
+
+    def haar(g, rows, cols):
+        X = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
+        Q, R = torch.linalg.qr(X)
+        sg = torch.sign(torch.diagonal(R))
+        sg[sg == 0] = 1.0
+        return Q * sg
+
+    def svd_m(g, rows, cols, sigma):
+        U = haar(g, rows, len(sigma))
+        V = haar(g, cols, len(sigma))
+        M = (U * sigma) @ V.T
+        return M.t().contiguous().t()
+
+    out = []
+    for s, m, n, p, c in specs:
+        g = torch.Generator(device=device)
+        g.manual_seed(s & ((1 << 63) - 1))
+        sa = torch.from_numpy(logspace_sigma(min(m, n), c)).to(device)
+        sb = torch.from_numpy(logspace_sigma(p, cond_b)).to(device)
+        A = svd_m(g, m, n, sa)
+        B = svd_m(g, p, n, sb)
+        x = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+        out.append(dict(A=A, B=B, d=B @ x, b=A @ x + torch.randn(m, generator=g, device=device,
+                                                                   dtype=torch.float64)))
+    return out
+
+
 # ------------------------------------------------------------------ GLS --
 
 def ar1_cholesky(n, rho):

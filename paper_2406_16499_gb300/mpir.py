@@ -78,6 +78,8 @@ _SIG = {
     "mpir_lse_bd_apply": ([_P, _P, _I, _P, _I, ctypes.c_double, ctypes.c_double, _I, _P, _P], _I),
     "mpir_gls_bd_apply": ([_P, _P, _I, _P, _I, ctypes.c_double, ctypes.c_double, _I, _P, _P], _I),
     "mpir_gls_residual_noalloc": ([_I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
+    "mpir_batched_set_shape": ([_P, _I], _I),
+    "mpir_batched_get_shape": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
     "mpir_launch_count": ([_I], ctypes.c_longlong),
@@ -186,6 +188,38 @@ def make_opts(fact="fp32", refine="classical", tol=0.0, maxit=0, escalate=True, 
     return o
 
 
+class LseBatch:
+    """The host-side argument arrays of lse_solve_batched, built once for a
+    list of problems (dicts of column-major FP64 device tensors A, B, b, d)
+    and their output vectors, so that repeated solves skip the marshalling."""
+
+    def __init__(self, probs, xs):
+        import numpy as np
+        cnt = len(probs)
+        self.count = cnt
+        self.keep = (list(probs), list(xs))       # the tensors must outlive the arrays
+        sz = max(cnt, 1)
+        ints = np.zeros((5, sz), dtype=np.int32)
+        ptrs = np.zeros((5, sz), dtype=np.uint64)
+        for i, pr in enumerate(probs):
+            A, B = pr["A"], pr["B"]
+            ints[0, i], ints[1, i] = A.shape
+            ints[2, i] = B.shape[0]
+            ints[3, i] = ld(A)
+            ints[4, i] = ld(B) if B.shape[0] else 1
+            ptrs[0, i] = ptr(A) or 0
+            ptrs[1, i] = ptr(B) or 0
+            ptrs[2, i] = ptr(pr["b"]) or 0
+            ptrs[3, i] = ptr(pr["d"]) or 0
+            ptrs[4, i] = ptr(xs[i]) or 0
+        self._ints, self._ptrs = np.ascontiguousarray(ints), np.ascontiguousarray(ptrs)
+        ip = lambda k: ctypes.c_void_p(self._ints[k].ctypes.data)
+        pp = lambda k: ctypes.c_void_p(self._ptrs[k].ctypes.data)
+        # (m, n, p, A, lda, B, ldb, b, d, x) in the C argument order
+        self.args = (ip(0), ip(1), ip(2), pp(0), ip(3), pp(1), ip(4), pp(2), pp(3), pp(4))
+        self.infos = (Info * sz)()
+
+
 class Handle:
     """Owns an mpir_handle bound to a device and a CUDA stream (the current
     torch stream by default)."""
@@ -232,25 +266,25 @@ class Handle:
                              ptr(x), ptr(r), ptr(v), ctypes.byref(o), ctypes.byref(info))
         return self.check(rc, "lse_solve"), info
 
-    def lse_solve_batched(self, probs, xs, opts=None):
-        """probs: sequence of dicts with device tensors A, B, b, d (column-major
-        FP64); xs: device output vectors.  Returns (status, [Info])."""
-        cnt = len(probs)
-        I_ = ctypes.c_int * max(cnt, 1)
-        P_ = ctypes.c_void_p * max(cnt, 1)
-        m, n, p, lda, ldb = I_(), I_(), I_(), I_(), I_()
-        A, B, b, d, x = P_(), P_(), P_(), P_(), P_()
-        for i, pr in enumerate(probs):
-            m[i], n[i] = pr["A"].shape
-            p[i] = pr["B"].shape[0]
-            lda[i], ldb[i] = ld(pr["A"]), (ld(pr["B"]) if p[i] else 1)
-            A[i], B[i], b[i], d[i], x[i] = ptr(pr["A"]), ptr(pr["B"]), ptr(pr["b"]), ptr(pr["d"]), ptr(xs[i])
-        infos = (Info * max(cnt, 1))()
+    def lse_solve_batched(self, probs, xs=None, opts=None):
+        """probs: an LseBatch, or a sequence of dicts with device tensors A, B,
+        b, d (column-major FP64) together with xs, the device output vectors.
+        Returns (status, [Info])."""
+        batch = probs if isinstance(probs, LseBatch) else LseBatch(probs, xs)
         o = opts if opts is not None else make_opts()
-        cast = lambda a: ctypes.cast(a, ctypes.c_void_p)
-        rc = lib().lse_solve_batched(self.h, cnt, cast(m), cast(n), cast(p), cast(A), cast(lda), cast(B), cast(ldb),
-                                     cast(b), cast(d), cast(x), ctypes.byref(o), ctypes.cast(infos, ctypes.POINTER(Info)))
-        return self.check(rc, "lse_solve_batched"), list(infos)[:cnt]
+        rc = lib().lse_solve_batched(self.h, batch.count, *batch.args, ctypes.byref(o),
+                                     ctypes.cast(batch.infos, ctypes.POINTER(Info)))
+        return self.check(rc, "lse_solve_batched"), list(batch.infos)[:batch.count]
+
+    def batched_set_shape(self, group=0):
+        """Force the batched group size (512/256/128/64) or 0 for autotuning."""
+        return self.check(lib().mpir_batched_set_shape(self.h, int(group)), "mpir_batched_set_shape")
+
+    def batched_get_shape(self, bucket):
+        g, sm, cnt = ctypes.c_int(), ctypes.c_size_t(), ctypes.c_int()
+        self.check(lib().mpir_batched_get_shape(self.h, bucket, ctypes.byref(g), ctypes.byref(sm), ctypes.byref(cnt)),
+                   "mpir_batched_get_shape")
+        return dict(group=g.value, smem=sm.value, problems=cnt.value)
 
     def gls_solve(self, W, V, d, x, y, z=None, opts=None):
         n, m = W.shape
