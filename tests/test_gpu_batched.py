@@ -155,3 +155,46 @@ def test_batched_rejects_bad_problem(h):
     probs[1] = bad
     with pytest.raises(mpir.MpirError, match="problem 1"):
         run_batch(h, probs)
+
+
+@pytest.mark.parametrize("group", [512, 256, 128, 64])
+def test_batched_every_launch_shape(h, oracle_mod, group):
+    """Every compiled launch shape (threads per problem) solves the batch;
+    shapes that cannot hold a problem fall back to the tuned ones."""
+    probs = I.lse_batch(seed=18, count=24, m_hi=200)
+    h.batched_set_shape(group)
+    try:
+        st, infos, xs = run_batch(h, probs)
+        used = [h.batched_get_shape(b) for b in (0, 1)]
+    finally:
+        h.batched_set_shape(0)
+    assert st == 0
+    assert any(u["group"] == group for u in used if u["problems"])
+    for P, x in zip(probs, xs):
+        check(oracle_mod, P, x)
+
+
+def test_batched_autotuner_near_best(h):
+    """The autotuned shape is within 30% of the fastest forced shape on the
+    same batch (device time of the graph launch)."""
+    import torch
+    from paper_2406_16499_gb300 import mpir
+    probs = I.lse_batch(seed=19, count=600)
+    dp = [to_dev(P) for P in probs]
+    xs = [zeros(P["A"].shape[1]) for P in probs]
+    batch = mpir.LseBatch(dp, xs)
+    times = {}
+    for g in (512, 256, 128, 64, 0):
+        h.batched_set_shape(g)
+        h.lse_solve_batched(batch)
+        best = float("inf")
+        for _ in range(3):
+            mpir.profile(True)
+            st, _ = h.lse_solve_batched(batch)
+            torch.cuda.synchronize()
+            best = min(best, mpir.profile_read()["batched"][0])
+            mpir.profile(False)
+        assert st == 0
+        times[g] = best
+    h.batched_set_shape(0)
+    assert times[0] <= 1.3 * min(times[g] for g in (512, 256, 128, 64)), times
