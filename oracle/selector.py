@@ -14,12 +14,16 @@ Features (16 per problem):
 for GLS (n, m, p, W, V, d) the roles are (n, m, p) -> (m, n, p) read as
 rows n of W, columns m, V n x p: 0 log n, 1 log m, 2 log(p + 1), 3 m/n,
 4 n/p, 7 log ||W||_F, 8 log ||V||_F, 9 log ||d||, 10 0, 11 log(||W||/||V||),
-12-14 kappa^ of W, V and [W, V].  Logs are natural, of max(x, 1e-300).
+12-14 kappa^ of W, V and [W, V].  Logs are natural, of x clamped to
+[1e-300, 1e300].
 
 kappa^(M) = sigma_max(B_k) / sigma_min(B_k) of the k x k bidiagonal of k
 steps of Golub-Kahan-Lanczos bidiagonalization of M started from a given
-vector (no reorthogonalization).  Its singular values interlace those of M,
-so kappa^ <= kappa_2(M), with equality once k >= the number of columns.
+vector, every new vector reorthogonalized against the previous ones (two
+classical Gram-Schmidt passes), k = min(16, rows, columns) of M; for a
+wide M the start vector is first mapped into range(M^T).  The Ritz values
+interlace the nonzero singular values, so kappa^ <= sigma_max / sigma_r
+(r = rank), with equality once k reaches the rank.
 
 MLP: 16 -> 64 -> 64 -> 6, ReLU, softmax, cross-entropy; weights are used
 as given (the GPU rounds them to bfloat16 before every forward; parity tests
@@ -33,28 +37,48 @@ TINY = 1e-300
 
 # ------------------------------------------------------------- features --
 
+BREAKDOWN = 64 * np.finfo(np.float64).eps / 2     # relative to the largest alpha / beta so far
+
+
 def gkl_bidiag(mv, rmv, s, k):
     """k steps of Golub-Kahan-Lanczos bidiagonalization: M V_k = U_k B_k with
     B_k upper bidiagonal (diag alpha, superdiag beta), v_1 = s / ||s||.
-    mv(x) = M x, rmv(y) = M^T y.  Stops early on a zero alpha or beta."""
+    mv(x) = M x, rmv(y) = M^T y; u and v are reorthogonalized against the
+    earlier ones (two classical Gram-Schmidt passes).  Stops early when an alpha or beta falls
+    to rounding level (below 64 u times the largest one so far): the Krylov
+    space is exhausted (e.g. k exceeds the rank) and further steps would
+    only add rounding noise."""
     v = s / np.linalg.norm(s)
     alphas, betas = [], []
     u_prev, beta = None, 0.0
+    big = 0.0
+    Us, Vs = [], [v]
     for j in range(k):
         u = mv(v) - (beta * u_prev if u_prev is not None else 0.0)
+        for _ in range(2):                     # reorthogonalize (two CGS passes)
+            if Us:
+                Um = np.column_stack(Us)
+                u = u - Um @ (Um.T @ u)
         a = np.linalg.norm(u)
-        if a == 0.0:
+        if not a > BREAKDOWN * max(big, a if j == 0 else big):
             break
+        big = max(big, a)
         u = u / a
         alphas.append(a)
+        Us.append(u)
         if j == k - 1:
             break
         w = rmv(u) - a * v
+        for _ in range(2):
+            Vm = np.column_stack(Vs)
+            w = w - Vm @ (Vm.T @ w)
         beta = np.linalg.norm(w)
-        if beta == 0.0:
+        if not beta > BREAKDOWN * big:
             break
+        big = max(big, beta)
         betas.append(beta)
         v = w / beta
+        Vs.append(v)
         u_prev = u
     kk = len(alphas)
     Bk = np.diag(alphas)
@@ -63,7 +87,13 @@ def gkl_bidiag(mv, rmv, s, k):
     return Bk
 
 
-def kappa_hat(mv, rmv, s, k=16):
+def kappa_hat(mv, rmv, s, k=16, wide=False):
+    """sigma_max / sigma_min of the GKL bidiagonal.  For a wide M (fewer rows
+    than columns) the start vector is first mapped into range(M^T)
+    (s <- M^T M s), so that the Ritz values interlace the nonzero singular
+    values instead of approaching the null space."""
+    if wide:
+        s = rmv(mv(s))
     Bk = gkl_bidiag(mv, rmv, s, k)
     if Bk.size == 0:
         return 1.0
@@ -72,7 +102,7 @@ def kappa_hat(mv, rmv, s, k=16):
 
 
 def _lg(x):
-    return float(np.log(max(float(x), TINY)))
+    return float(np.log(min(max(float(x), TINY), 1e300)))
 
 
 def lse_flops(m, n, p):
@@ -92,9 +122,9 @@ def lse_features(A, B, b, d, s, k=16):
     p = B.shape[0]
     fA, fB = np.linalg.norm(A), np.linalg.norm(B)
     AB = np.vstack([A, B])
-    kA = kappa_hat(lambda x: A @ x, lambda y: A.T @ y, s, k)
-    kB = kappa_hat(lambda x: B @ x, lambda y: B.T @ y, s, k) if p else 1.0
-    kAB = kappa_hat(lambda x: AB @ x, lambda y: AB.T @ y, s, k)
+    kA = kappa_hat(lambda x: A @ x, lambda y: A.T @ y, s, min(k, m, n), m < n)
+    kB = kappa_hat(lambda x: B @ x, lambda y: B.T @ y, s, min(k, p, n), p < n) if p else 1.0
+    kAB = kappa_hat(lambda x: AB @ x, lambda y: AB.T @ y, s, min(k, m + p, n), m + p < n)
     return np.array([_lg(m), _lg(n), np.log(p + 1.0), n / m, p / n, 0.0, 0.0, _lg(fA), _lg(fB),
                      _lg(np.linalg.norm(b)), _lg(np.linalg.norm(d)), _lg(fA) - _lg(fB),
                      _lg(kA), _lg(kB), _lg(kAB), _lg(lse_flops(m, n, p))])
@@ -108,9 +138,9 @@ def gls_features(W, V, d, s, k=16):
     p = V.shape[1]
     fW, fV = np.linalg.norm(W), np.linalg.norm(V)
     WV = np.hstack([W, V])
-    kW = kappa_hat(lambda x: W @ x, lambda y: W.T @ y, s[:m], k) if m else 1.0
-    kV = kappa_hat(lambda x: V @ x, lambda y: V.T @ y, s[m:], k)
-    kWV = kappa_hat(lambda x: WV @ x, lambda y: WV.T @ y, s, k)
+    kW = kappa_hat(lambda x: W @ x, lambda y: W.T @ y, s[:m], min(k, n, m), n < m) if m else 1.0
+    kV = kappa_hat(lambda x: V @ x, lambda y: V.T @ y, s[m:], min(k, n, p), n < p)
+    kWV = kappa_hat(lambda x: WV @ x, lambda y: WV.T @ y, s, min(k, n, m + p), n < m + p)
     return np.array([_lg(n), _lg(m), np.log(p + 1.0), m / n, n / p, 1.0, 0.0, _lg(fW), _lg(fV),
                      _lg(np.linalg.norm(d)), 0.0, _lg(fW) - _lg(fV),
                      _lg(kW), _lg(kV), _lg(kWV), _lg(gls_flops(n, m, p))])

@@ -61,14 +61,20 @@ def test_adam_first_step_is_signed_lr():
         assert np.allclose(old[k] - P[k], 1e-2 * G[k] / (np.abs(G[k]) + 1e-8), rtol=1e-12)
 
 
-@pytest.mark.parametrize("shape,cond", [((120, 40), 1e3), ((60, 30), 1e6), ((300, 200), 1e2)])
+@pytest.mark.parametrize("shape,cond", [((120, 40), 1e3), ((60, 30), 1e6), ((300, 200), 1e2), ((15, 60), 1e1),
+                                        ((40, 300), 1e4)])
 def test_kappa_hat_below_kappa(shape, cond):
+    """Interlacing: sigma_max / sigma_rank bounds the sketch (wide matrices
+    included, whose start vector is mapped into range(M^T))."""
     from paper_2406_16499_gb300 import inputs as I
     g = I.rng(11)
-    M = I.svd_matrix(g, shape[0], shape[1], I.logspace_sigma(shape[1], cond))
+    r = min(shape)
+    M = I.svd_matrix(g, shape[0], shape[1], I.logspace_sigma(r, cond))
     s = g.standard_normal(shape[1])
-    kh = S.kappa_hat(lambda x: M @ x, lambda y: M.T @ y, s, 16)
-    assert 1.0 <= kh <= cond * (1 + 1e-10)
+    kh = S.kappa_hat(lambda x: M @ x, lambda y: M.T @ y, s, min(16, r), shape[0] < shape[1])
+    assert 1.0 <= kh <= cond * (1 + 1e-8)
+    if r <= 16:
+        assert abs(kh / cond - 1) < 1e-6
 
 
 def test_kappa_hat_exact_for_few_columns():
