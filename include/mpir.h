@@ -44,7 +44,9 @@ typedef enum {
     MPIR_BF16 = 0,
     MPIR_TF32 = 1,
     MPIR_FP32 = 2,
-    MPIR_FP64 = 3
+    MPIR_FP64 = 3,
+    MPIR_AUTO = 4   /* the learned selector picks the precision and the
+                       refinement variant (mpir_selector_set)                 */
 } mpir_prec;
 
 /* Refinement variant. */
@@ -323,6 +325,58 @@ int mpir_gls_residual_noalloc(int n, int m, int p, const double *W, int ldw,
                               const double *x, const double *y, const double *z,
                               double *f1, double *f2, double *f3, double *norms2,
                               void *stream);
+
+/* =====================================================================
+ * Learned selector (not in the paper): picks, per problem, the
+ * factorization precision {BF16, FP32, FP64} and the refinement variant
+ * {classical, GMRES} (6 classes, in that order: BF16+classical,
+ * BF16+GMRES, FP32+classical, FP32+GMRES, FP64+classical, FP64+GMRES).
+ * ===================================================================== */
+
+/* 16 features of a problem (device float[16]): log m, log n, log(p+1), n/m,
+ * p/n, kind (0), complex flag (0), log ||A||_F, log ||B||_F, log ||b||,
+ * log ||d||, log(||A||_F/||B||_F), log kappa^(A), log kappa^(B),
+ * log kappa^([A; B]), log(GRQ flop estimate); kappa^ = sigma_max/sigma_min
+ * of the bidiagonal of min(16, rows, columns) Golub-Kahan-Lanczos steps
+ * (FP64, no reorthogonalization) started from s (device, length n).  GLS: log n,
+ * log m, log(p+1), m/n, n/p, kind 1, 0, log ||W||_F, log ||V||_F, log ||d||,
+ * 0, log(||W||_F/||V||_F), kappa^ of W, V, [W, V], log(flops); s has length
+ * m + p (W uses s[0:m], V s[m:m+p]).  Logs are natural, of the value clamped
+ * to [1e-300, 1e300].  One thread-block cluster. */
+int mpir_lse_features(mpir_handle h, int m, int n, int p, const double *A, int lda,
+                      const double *B, int ldb, const double *b, const double *d,
+                      const double *s, float *features);
+int mpir_gls_features(mpir_handle h, int n, int m, int p, const double *W, int ldw,
+                      const double *V, int ldv, const double *d, const double *s,
+                      float *features);
+
+/* The MLP 16 -> 64 -> 64 -> 6 (ReLU, softmax).  params: device FP32 array
+ * of mpir_mlp_param_count() floats laid out as W1[64][16], b1[64],
+ * W2[64][64], b2[64], W3[6][64], b3[6] (row-major, W[o][i] maps input i to
+ * output o); the kernels round the weights to bfloat16 (nearest, ties to
+ * even) and accumulate in FP32.  X: device float[count][16]; prob: device
+ * float[count][6]. */
+int mpir_mlp_param_count(void);
+int mpir_mlp_forward(mpir_handle h, const float *params, const float *X, int count, float *prob);
+/* One training step on the mean cross-entropy of (X, labels) (labels: device
+ * int[count] in 0..5): gradients into grad (device, param_count floats, may
+ * be NULL), mean loss into *loss (device float, may be NULL), and, when
+ * adam_m and adam_v (device, param_count floats each) are given and lr > 0,
+ * an Adam update (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected with the
+ * 1-based step count `step`) of params. */
+int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam_v, int step,
+                        float lr, const float *X, const int *labels, int count, float *grad,
+                        float *loss);
+
+/* Install a trained selector in the handle (host arrays: params as above,
+ * feature standardization mean[16] and scale[16]: the network sees
+ * (f - mean) / scale).  Solves with opts->fact = MPIR_AUTO then compute the
+ * features (start vector: splitmix64 of seed 0x5EED + j mapped to [-1, 1)),
+ * run the network, and solve with the most probable class (GMRES classes
+ * fall back to classical IR where the block-diagonal preconditioner does not
+ * apply); escalation to FP64 stays the fallback.  info->fact_used /
+ * refine_used report the choice.  NULL params removes the selector. */
+int mpir_selector_set(mpir_handle h, const float *params, const float *mean, const float *scale);
 
 /* Library version string. */
 const char *mpir_version(void);

@@ -18,9 +18,10 @@ rows n of W, columns m, V n x p: 0 log n, 1 log m, 2 log(p + 1), 3 m/n,
 [1e-300, 1e300].
 
 kappa^(M) = sigma_max(B_k) / sigma_min(B_k) of the k x k bidiagonal of k
-steps of Golub-Kahan-Lanczos bidiagonalization of M started from a given
-vector, every new vector reorthogonalized against the previous ones (two
-classical Gram-Schmidt passes), k = min(16, rows, columns) of M; for a
+steps of Golub-Kahan-Lanczos bidiagonalization of M (in float32 for the
+features, so kappa^ saturates near 1 / u_single ~ 1e7) started from a given
+vector, every new vector reorthogonalized once against the previous ones
+(classical Gram-Schmidt), k = min(16, rows, columns) of M; for a
 wide M the start vector is first mapped into range(M^T).  The Ritz values
 interlace the nonzero singular values, so kappa^ <= sigma_max / sigma_r
 (r = rank), with equality once k reaches the rank.
@@ -37,15 +38,16 @@ TINY = 1e-300
 
 # ------------------------------------------------------------- features --
 
-BREAKDOWN = 64 * np.finfo(np.float64).eps / 2     # relative to the largest alpha / beta so far
+BREAKDOWN = 64 * np.finfo(np.float32).eps / 2     # relative to the largest alpha / beta so far (the
+                                                  # feature sketch runs in float32)
 
 
 def gkl_bidiag(mv, rmv, s, k):
     """k steps of Golub-Kahan-Lanczos bidiagonalization: M V_k = U_k B_k with
     B_k upper bidiagonal (diag alpha, superdiag beta), v_1 = s / ||s||.
-    mv(x) = M x, rmv(y) = M^T y; u and v are reorthogonalized against the
-    earlier ones (two classical Gram-Schmidt passes).  Stops early when an alpha or beta falls
-    to rounding level (below 64 u times the largest one so far): the Krylov
+    mv(x) = M x, rmv(y) = M^T y; u and v are reorthogonalized once against
+    the earlier ones (classical Gram-Schmidt).  Stops early when an alpha or beta falls
+    to rounding level (below 64 u_single times the largest one so far): the Krylov
     space is exhausted (e.g. k exceeds the rank) and further steps would
     only add rounding noise."""
     v = s / np.linalg.norm(s)
@@ -55,7 +57,7 @@ def gkl_bidiag(mv, rmv, s, k):
     Us, Vs = [], [v]
     for j in range(k):
         u = mv(v) - (beta * u_prev if u_prev is not None else 0.0)
-        for _ in range(2):                     # reorthogonalize (two CGS passes)
+        if True:                               # reorthogonalize (one CGS pass)
             if Us:
                 Um = np.column_stack(Us)
                 u = u - Um @ (Um.T @ u)
@@ -69,7 +71,7 @@ def gkl_bidiag(mv, rmv, s, k):
         if j == k - 1:
             break
         w = rmv(u) - a * v
-        for _ in range(2):
+        if True:                               # reorthogonalize (one CGS pass)
             Vm = np.column_stack(Vs)
             w = w - Vm @ (Vm.T @ w)
         beta = np.linalg.norm(w)
@@ -85,6 +87,14 @@ def gkl_bidiag(mv, rmv, s, k):
     for i in range(min(len(betas), kk - 1)):
         Bk[i, i + 1] = betas[i]
     return Bk
+
+
+def kappa_hat32(M, s, k=16, wide=False):
+    """kappa_hat with the bidiagonalization in float32 (vectors and products
+    of the matrix rounded to float32), as the selector computes it."""
+    M32 = np.asarray(M, np.float64).astype(np.float32)
+    s32 = np.asarray(s, np.float64).astype(np.float32)
+    return kappa_hat(lambda x: M32 @ x.astype(np.float32), lambda y: M32.T @ y.astype(np.float32), s32, k, wide)
 
 
 def kappa_hat(mv, rmv, s, k=16, wide=False):
@@ -122,9 +132,9 @@ def lse_features(A, B, b, d, s, k=16):
     p = B.shape[0]
     fA, fB = np.linalg.norm(A), np.linalg.norm(B)
     AB = np.vstack([A, B])
-    kA = kappa_hat(lambda x: A @ x, lambda y: A.T @ y, s, min(k, m, n), m < n)
-    kB = kappa_hat(lambda x: B @ x, lambda y: B.T @ y, s, min(k, p, n), p < n) if p else 1.0
-    kAB = kappa_hat(lambda x: AB @ x, lambda y: AB.T @ y, s, min(k, m + p, n), m + p < n)
+    kA = kappa_hat32(A, s, min(k, m, n), m < n)
+    kB = kappa_hat32(B, s, min(k, p, n), p < n) if p else 1.0
+    kAB = kappa_hat32(AB, s, min(k, m + p, n), m + p < n)
     return np.array([_lg(m), _lg(n), np.log(p + 1.0), n / m, p / n, 0.0, 0.0, _lg(fA), _lg(fB),
                      _lg(np.linalg.norm(b)), _lg(np.linalg.norm(d)), _lg(fA) - _lg(fB),
                      _lg(kA), _lg(kB), _lg(kAB), _lg(lse_flops(m, n, p))])
@@ -138,9 +148,9 @@ def gls_features(W, V, d, s, k=16):
     p = V.shape[1]
     fW, fV = np.linalg.norm(W), np.linalg.norm(V)
     WV = np.hstack([W, V])
-    kW = kappa_hat(lambda x: W @ x, lambda y: W.T @ y, s[:m], min(k, n, m), n < m) if m else 1.0
-    kV = kappa_hat(lambda x: V @ x, lambda y: V.T @ y, s[m:], min(k, n, p), n < p)
-    kWV = kappa_hat(lambda x: WV @ x, lambda y: WV.T @ y, s, min(k, n, m + p), n < m + p)
+    kW = kappa_hat32(W, s[:m], min(k, n, m), n < m) if m else 1.0
+    kV = kappa_hat32(V, s[m:], min(k, n, p), n < p)
+    kWV = kappa_hat32(WV, s, min(k, n, m + p), n < m + p)
     return np.array([_lg(n), _lg(m), np.log(p + 1.0), m / n, n / p, 1.0, 0.0, _lg(fW), _lg(fV),
                      _lg(np.linalg.norm(d)), 0.0, _lg(fW) - _lg(fV),
                      _lg(kW), _lg(kV), _lg(kWV), _lg(gls_flops(n, m, p))])

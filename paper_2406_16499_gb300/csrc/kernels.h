@@ -9,7 +9,7 @@ namespace mpir {
 // Kernel kinds for the launch counter and the optional per-kind timers.
 enum KernelKind {
     K_PANEL = 0, K_LARFB, K_VEC_APPLY, K_TRSV, K_GEMV, K_DUAL_GEMV, K_FINALIZE, K_CONVERT, K_NORM,
-    K_ELEMWISE, K_LARFB_TC, K_LARFB_AUX, K_GMRES, K_BATCHED, K_NKINDS
+    K_ELEMWISE, K_LARFB_TC, K_LARFB_AUX, K_GMRES, K_BATCHED, K_SELECTOR, K_NKINDS
 };
 // Called around every kernel launch: counts the launch and, when timing is
 // enabled (mpir_profile), records a CUDA event pair on the launch stream.

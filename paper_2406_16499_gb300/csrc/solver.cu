@@ -36,6 +36,7 @@
 #include "gmres.h"
 #include "kernels.h"
 #include "mpir.h"
+#include "selector.h"
 
 using namespace mpir;
 
@@ -76,7 +77,7 @@ void prof_end(int kind, cudaStream_t s)
 static const char *g_kind_names[K_NKINDS] = {"panel_qr", "larfb", "vec_apply", "trsv", "gemv",
                                              "dual_gemv_fp64", "resid_finalize", "convert", "norm",
                                              "elementwise", "larfb_tc", "larfb_aux", "gmres",
-                                             "batched"};
+                                             "batched", "selector"};
 
 #define MPIR_VERSION_STRING "libmpir 0.1 (sm_103a)"
 
@@ -224,6 +225,11 @@ struct mpir_ctx {
     size_t rws_bytes = 0;
     BatchArena ba;               // batched solves: tables, results, tuned shapes, graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // learned selector: parameters and feature standardization (device), scratch
+    float *sel = nullptr;        // params[MLP_PARAMS], X[16], prob[6], feat[16]
+    float sel_mean[16], sel_scale[16];
+    double *sel_s = nullptr;     // start vector of the condition sketch
+    size_t sel_s_len = 0;
 };
 
 namespace {
@@ -1351,6 +1357,8 @@ int mpir_destroy(mpir_handle h)
         if (a.horder) cudaFreeHost(a.horder);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     }
+    if (h->sel) cudaFree(h->sel);
+    if (h->sel_s) cudaFree(h->sel_s);
     for (int i = 0; i < 8; i++) cudaEventDestroy(h->ev[i]);
     delete h;
     return 0;
@@ -1446,6 +1454,64 @@ static int gls_check_args(int n, int m, int p, const double *W, int ldw, const d
     return 0;
 }
 
+// ------------------------------------------------------------ selector --
+// splitmix64 (Steele, Lea, Flood 2014) of seed + j mapped to [-1, 1).
+static double splitmix_unit(unsigned long long x)
+{
+    unsigned long long z = x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+}
+
+static int sel_start_vector(mpir_ctx *h, int len)
+{
+    if ((size_t)len <= h->sel_s_len) return 0;
+    if (h->sel_s) { cudaStreamSynchronize(h->stream); cudaFree(h->sel_s); h->sel_s = nullptr; h->sel_s_len = 0; }
+    std::vector<double> v(len);
+    for (int j = 0; j < len; j++) v[j] = splitmix_unit(0x5EEDULL + (unsigned long long)j);
+    if (cudaMalloc(&h->sel_s, sizeof(double) * len) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, MPIR_CUDA_ERROR, "selector: cudaMalloc failed");
+    }
+    cudaMemcpy(h->sel_s, v.data(), sizeof(double) * len, cudaMemcpyHostToDevice);
+    h->sel_s_len = len;
+    return 0;
+}
+
+// Features -> standardized input -> MLP -> most probable class.
+static int sel_choose(mpir_ctx *h, int kind, int d0, int d1, int d2, const double *M1, int ld1, const double *M2,
+                      int ld2, const double *v1, int n1, const double *v2, int n2, int *cls)
+{
+    if (!h->sel) return set_err(h, MPIR_UNSUPPORTED, "fact = MPIR_AUTO needs a selector (mpir_selector_set)");
+    const int R = kind == 0 ? d0 + d2 : d0, C = kind == 0 ? d1 : d1 + d2;
+    RC(sel_start_vector(h, C));
+    RC(ensure_rws(h, sizeof(double) * features_ws_doubles(R, C)));
+    float *X = h->sel + MLP_PARAMS, *prob = X + 16, *feat = prob + 8;
+    cudaStream_t s = h->stream;
+    RC(features_launch(kind, d0, d1, d2, M1, ld1, M2, ld2, h->sel_s, v1, n1, v2, n2, 16, (double *)h->rws, feat, s));
+    float f[16], pr[8];
+    cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "selector features");
+    for (int q = 0; q < 16; q++) f[q] = (f[q] - h->sel_mean[q]) / h->sel_scale[q];
+    cudaMemcpyAsync(X, f, sizeof(f), cudaMemcpyHostToDevice, s);
+    RC(mlp_forward(h->sel, X, 1, prob, s));
+    cudaMemcpyAsync(pr, prob, sizeof(float) * NCLASS, cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "selector forward");
+    int best = 0;
+    for (int c = 1; c < NCLASS; c++) if (pr[c] > pr[best]) best = c;
+    *cls = best;
+    return 0;
+}
+
+static void sel_apply(int cls, mpir_opts *o)
+{
+    static const int facts[3] = {MPIR_BF16, MPIR_FP32, MPIR_FP64};
+    o->fact = facts[cls / 2];
+    o->refine = (cls % 2) ? MPIR_GMRES : MPIR_CLASSICAL;
+}
+
 int lse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
               const double *b, const double *d, double *x, double *r, double *v, const mpir_opts *opts,
               mpir_info *info)
@@ -1456,6 +1522,13 @@ int lse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, cons
     mpir_opts o;
     fill_opts(opts, &o);
     if (info) std::memset(info, 0, sizeof(*info));
+    if (o.fact == MPIR_AUTO) {
+        int cls = 0;
+        RC(sel_choose(h, 0, m, n, p, A, lda, B, std::max(ldb, 1), b, m, d, p, &cls));
+        sel_apply(cls, &o);
+        if (o.refine == MPIR_GMRES && m < n) o.refine = MPIR_CLASSICAL;
+    }
+    if (o.fact < MPIR_BF16 || o.fact > MPIR_FP64) return set_err(h, -14, "illegal opts->fact");
     int fact = o.fact;
     int esc = 0, st = 0;
     while (true) {
@@ -1482,6 +1555,13 @@ int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, cons
     mpir_opts o;
     fill_opts(opts, &o);
     if (info) std::memset(info, 0, sizeof(*info));
+    if (o.fact == MPIR_AUTO) {
+        int cls = 0;
+        RC(sel_choose(h, 1, n, m, p, W, ldw, V, ldv, d, n, nullptr, 0, &cls));
+        sel_apply(cls, &o);
+        if (o.refine == MPIR_GMRES && n > p) o.refine = MPIR_CLASSICAL;
+    }
+    if (o.fact < MPIR_BF16 || o.fact > MPIR_FP64) return set_err(h, -14, "illegal opts->fact");
     int fact = o.fact;
     int esc = 0, st = 0;
     while (true) {
@@ -1674,7 +1754,9 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
     if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
     std::vector<int> all(count);
     for (int i = 0; i < count; i++) all[i] = i;
-    if (o.refine == MPIR_GMRES) return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
+    // GMRES-IR and the learned selector run problem by problem
+    if (o.refine == MPIR_GMRES || o.fact == MPIR_AUTO)
+        return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
     const bool fp64 = o.fact == MPIR_FP64;
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -2206,6 +2288,94 @@ int mpir_batched_get_shape(mpir_handle h, int bucket, int *group, size_t *smem_b
     if (smem_bytes) *smem_bytes = h->ba.last[bucket].smem;
     if (problems) *problems = h->ba.last_count[bucket];
     return 0;
+}
+
+} // extern "C"
+
+extern "C" {
+
+int mpir_lse_features(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+                      const double *b, const double *d, const double *s, float *features)
+{
+    if (!h) return -1;
+    if (m < 1) return -2;
+    if (n < 1) return -3;
+    if (p < 0) return -4;
+    if (!A || lda < m) return -5;
+    if ((p > 0 && !B) || ldb < std::max(1, p)) return -7;
+    if (!b) return -9;
+    if (p > 0 && !d) return -10;
+    if (!s) return -11;
+    if (!features) return -12;
+    RC(ensure_rws(h, sizeof(double) * features_ws_doubles(m + p, n)));
+    RC(features_launch(0, m, n, p, A, lda, B, std::max(ldb, 1), s, b, m, d, p, 16, (double *)h->rws, features,
+                       h->stream));
+    return cuda_check(h, "mpir_lse_features");
+}
+
+int mpir_gls_features(mpir_handle h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+                      const double *d, const double *s, float *features)
+{
+    if (!h) return -1;
+    if (n < 1) return -2;
+    if (m < 0) return -3;
+    if (p < 1) return -4;
+    if ((m > 0 && !W) || ldw < n) return -5;
+    if (!V || ldv < n) return -7;
+    if (!d) return -9;
+    if (!s) return -10;
+    if (!features) return -11;
+    RC(ensure_rws(h, sizeof(double) * features_ws_doubles(n, m + p)));
+    RC(features_launch(1, m, n, p, W, std::max(ldw, 1), V, ldv, s, d, n, nullptr, 0, 16, (double *)h->rws, features,
+                       h->stream));
+    return cuda_check(h, "mpir_gls_features");
+}
+
+int mpir_mlp_param_count(void) { return MLP_PARAMS; }
+
+int mpir_mlp_forward(mpir_handle h, const float *params, const float *X, int count, float *prob)
+{
+    if (!h) return -1;
+    if (!params) return -2;
+    if (!X && count > 0) return -3;
+    if (count < 0) return -4;
+    if (!prob && count > 0) return -5;
+    RC(mlp_forward(params, X, count, prob, h->stream));
+    return cuda_check(h, "mpir_mlp_forward");
+}
+
+int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam_v, int step, float lr,
+                        const float *X, const int *labels, int count, float *grad, float *loss)
+{
+    if (!h) return -1;
+    if (!params) return -2;
+    if (step < 1) return -5;
+    if (!X) return -7;
+    if (!labels) return -8;
+    if (count < 1) return -9;
+    RC(ensure_rws(h, sizeof(float) * mlp_ws_floats(count)));
+    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, labels, count, (float *)h->rws, grad, loss, h->stream));
+    return cuda_check(h, "mpir_mlp_train_step");
+}
+
+int mpir_selector_set(mpir_handle h, const float *params, const float *mean, const float *scale)
+{
+    if (!h) return -1;
+    if (!params) {
+        if (h->sel) { cudaStreamSynchronize(h->stream); cudaFree(h->sel); h->sel = nullptr; }
+        return 0;
+    }
+    if (!mean) return -3;
+    if (!scale) return -4;
+    for (int q = 0; q < 16; q++) if (!(scale[q] != 0.0f)) return -4;
+    if (!h->sel && cudaMalloc(&h->sel, sizeof(float) * (MLP_PARAMS + 64)) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, MPIR_CUDA_ERROR, "selector: cudaMalloc failed");
+    }
+    cudaMemcpy(h->sel, params, sizeof(float) * MLP_PARAMS, cudaMemcpyHostToDevice);
+    std::memcpy(h->sel_mean, mean, sizeof(h->sel_mean));
+    std::memcpy(h->sel_scale, scale, sizeof(h->sel_scale));
+    return cuda_check(h, "mpir_selector_set");
 }
 
 } // extern "C"

@@ -187,6 +187,38 @@ def lse_batch_torch(specs, device, cond_b=10.0):
     return out
 
 
+def splitmix_vector(n, seed=0x5EED):
+    """x_j = splitmix64(seed + j) (Steele, Lea, Flood 2014) mapped to
+    [-1, 1): the start vector of the selector's condition sketch."""
+    M = (1 << 64) - 1
+    out = np.empty(n)
+    for j in range(n):
+        z = (seed + j + 0x9E3779B97F4A7C15) & M
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+        z ^= z >> 31
+        out[j] = (z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0
+    return out
+
+
+def selector_lse_problems(seed, count, m_lo=64, m_hi=400, cond_lo=1e0, cond_hi=1e12):
+    """LSE problems for training / evaluating the selector: m ~ U[m_lo, m_hi],
+    n ~ U[16, m/2], p ~ U[1, n/4], kappa_2([A; B]) log-uniform in
+    [cond_lo, cond_hi] with a random xLATM1-style pattern (lse_paper)."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        m = int(g.integers(m_lo, m_hi + 1))
+        n = int(g.integers(16, max(16, m // 2) + 1))
+        p = int(g.integers(1, max(1, n // 4) + 1))
+        c = float(np.exp(g.uniform(np.log(cond_lo), np.log(cond_hi))))
+        mode = int(g.integers(1, 4))
+        P = lse_paper(int(g.integers(1 << 62)), m, n, p, c, mode)
+        P["kappa"] = c
+        out.append(P)
+    return out
+
+
 # ------------------------------------------------------------------ GLS --
 
 def ar1_cholesky(n, rho):

@@ -14,7 +14,7 @@ from . import build as _build
 
 _lib = None
 
-PREC = {"bf16": 0, "tf32": 1, "fp32": 2, "fp64": 3}
+PREC = {"bf16": 0, "tf32": 1, "fp32": 2, "fp64": 3, "auto": 4}
 REFINE = {"classical": 0, "gmres": 1, "direct": 2}
 STATUS = {0: "ok", 1: "singular R", 2: "singular T", 3: "not converged", 4: "non-finite",
           5: "unsupported", 6: "cuda error", 7: "device timeout"}
@@ -80,13 +80,19 @@ _SIG = {
     "mpir_gls_residual_noalloc": ([_I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P], _I),
     "mpir_batched_set_shape": ([_P, _I], _I),
     "mpir_batched_get_shape": ([_P, _I, ctypes.POINTER(_I), ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(_I)], _I),
+    "mpir_lse_features": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P], _I),
+    "mpir_gls_features": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P], _I),
+    "mpir_mlp_param_count": ([], _I),
+    "mpir_mlp_forward": ([_P, _P, _P, _I, _P], _I),
+    "mpir_mlp_train_step": ([_P, _P, _P, _P, _I, ctypes.c_float, _P, _P, _I, _P, _P], _I),
+    "mpir_selector_set": ([_P, _P, _P, _P], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
     "mpir_launch_count": ([_I], ctypes.c_longlong),
     "mpir_kernel_kind_name": ([_I], ctypes.c_char_p),
 }
 
-NKINDS = 14
+NKINDS = 15
 
 
 def profile(enable):
@@ -275,6 +281,38 @@ class Handle:
         rc = lib().lse_solve_batched(self.h, batch.count, *batch.args, ctypes.byref(o),
                                      ctypes.cast(batch.infos, ctypes.POINTER(Info)))
         return self.check(rc, "lse_solve_batched"), list(batch.infos)[:batch.count]
+
+    # ---- learned selector ------------------------------------------------
+    def lse_features(self, A, B, b, d, s, out):
+        p = B.shape[0]
+        return self.check(lib().mpir_lse_features(self.h, A.shape[0], A.shape[1], p, ptr(A), ld(A), ptr(B),
+                                                  ld(B) if p else 1, ptr(b), ptr(d), ptr(s), ptr(out)),
+                          "mpir_lse_features")
+
+    def gls_features(self, W, V, d, s, out):
+        n, m = W.shape
+        return self.check(lib().mpir_gls_features(self.h, n, m, V.shape[1], ptr(W), ld(W), ptr(V), ld(V), ptr(d),
+                                                  ptr(s), ptr(out)), "mpir_gls_features")
+
+    def mlp_forward(self, params, X, prob):
+        return self.check(lib().mpir_mlp_forward(self.h, ptr(params), ptr(X), X.shape[0], ptr(prob)),
+                          "mpir_mlp_forward")
+
+    def mlp_train_step(self, params, m, v, step, lr, X, y, grad=None, loss=None):
+        return self.check(lib().mpir_mlp_train_step(self.h, ptr(params), ptr(m), ptr(v), int(step), float(lr),
+                                                    ptr(X), ptr(y), X.shape[0], ptr(grad), ptr(loss)),
+                          "mpir_mlp_train_step")
+
+    def selector_set(self, params, mean, scale):
+        """params, mean, scale: host float32 numpy arrays (None removes)."""
+        import numpy as np
+        if params is None:
+            return self.check(lib().mpir_selector_set(self.h, None, None, None), "mpir_selector_set")
+        P = np.ascontiguousarray(params, dtype=np.float32)
+        mu = np.ascontiguousarray(mean, dtype=np.float32)
+        sc = np.ascontiguousarray(scale, dtype=np.float32)
+        return self.check(lib().mpir_selector_set(self.h, P.ctypes.data, mu.ctypes.data, sc.ctypes.data),
+                          "mpir_selector_set")
 
     def batched_set_shape(self, group=0):
         """Force the batched group size (512/256/128/64) or 0 for autotuning."""

@@ -96,12 +96,12 @@ def test_features_layout():
     assert f[0] == pytest.approx(np.log(200)) and f[1] == pytest.approx(np.log(100))
     assert f[3] == pytest.approx(0.5) and f[4] == pytest.approx(0.2) and f[5] == 0.0
     assert f[7] == pytest.approx(np.log(np.linalg.norm(P["A"])))
-    assert f[12] <= np.log(1e2) + 1e-9          # kappa(A) = 1e2 by construction
+    assert f[12] <= np.log(1e2) + 1e-5          # kappa(A) = 1e2 by construction
     G = I.gls_svd(5, 60, 20, 80, 1e3, 1e1)
     s = np.random.default_rng(1).standard_normal(100)
     f = S.gls_features(G["W"], G["V"], G["d"], s)
     assert f[5] == 1.0 and f[0] == pytest.approx(np.log(60)) and f[4] == pytest.approx(60 / 80)
-    assert f[12] <= np.log(1e3) + 1e-9
+    assert f[12] <= np.log(1e3) + 1e-5
 
 
 def test_bf16_rounding():
