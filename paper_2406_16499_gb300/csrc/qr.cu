@@ -35,13 +35,12 @@ constexpr int PANEL_MAX_CLUSTER = 16;
 //     Tw^{-1} = triu(V^T V, 1) + diag(1 / tau)
 // by one back substitution per column (lane k solves column k).
 // ---------------------------------------------------------------------------
-template <typename T, int NB>
-__global__ void __launch_bounds__(PANEL_NT, 1)
+template <typename T, int NB, int NT, int RPT>
+__global__ void __launch_bounds__(NT, 1)
 k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
            T *__restrict__ tau, T *__restrict__ Tw)
 {
-    constexpr int NW = PANEL_NT / 32;
-    constexpr int RPT = PANEL_RPT;
+    constexpr int NW = NT / 32;
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -65,7 +64,7 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     T a[RPT][NB];
 #pragma unroll
     for (int q = 0; q < RPT; q++) {
-        int r = row_base + tid + q * PANEL_NT;
+        int r = row_base + tid + q * NT;
         rr[q] = r < row_end ? r : -1;
     }
 #pragma unroll
@@ -131,7 +130,7 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                 xbuf[par][lane] = t;
             }
             cluster.sync();
-            if (warp < cs && lane < NB) gbuf[par][warp][lane] = *cluster.map_shared_rank(&xbuf[par][lane], warp);
+            for (int r = warp; r < cs && lane < NB; r += NW) gbuf[par][r][lane] = *cluster.map_shared_rank(&xbuf[par][lane], r);
             if (warp == NW - 1 && lane < NB) prow_l[par][lane] = *cluster.map_shared_rank(&prow[par][lane], 0);
             __syncthreads();
             if (lane < NB) {
@@ -667,16 +666,16 @@ k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, f
 
 // ------------------------------------------------------------------ host --
 
-template <typename T>
-static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, cudaStream_t s)
+template <typename T, int NT, int RPT>
+static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, cudaStream_t s)
 {
     constexpr int NB = panel_nb<T>();
     const int L = M - j0;
-    int cs = ceil_div(L, PANEL_ROWS_PER_CTA);
+    int cs = ceil_div(L, NT * RPT);
     if (cs < 1) cs = 1;
     if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
     const int chunk = ceil_div(L, cs);
-    auto kern = k_panel_qr<T, NB>;
+    auto kern = k_panel_qr<T, NB, NT, RPT>;
     static bool attr_done = false;
     if (!attr_done) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -684,7 +683,7 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
-    cfg.blockDim = dim3(PANEL_NT, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
@@ -697,6 +696,115 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
     ProfScope ps(K_PANEL, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// Rows per CTA as small as the 16-CTA cluster limit allows: the panel's
+// column steps are latency and issue bound, so fewer rows per SM (more SMs)
+// shorten every step.
+template <typename T>
+static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, cudaStream_t s)
+{
+    const int L = M - j0;
+    if constexpr (sizeof(T) == 4) {
+        if (L <= 16 * 128) return launch_panel_shape<T, 128, 1>(A, lda, M, j0, ncols, tau, Tw, s);
+        if (L <= 16 * 256) return launch_panel_shape<T, 256, 1>(A, lda, M, j0, ncols, tau, Tw, s);
+        if (L <= 16 * 512) return launch_panel_shape<T, 512, 1>(A, lda, M, j0, ncols, tau, Tw, s);
+    }
+    return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, s);
+}
+
+// Inner update with the CTA's whole row chunk of V and C staged in shared
+// memory at once (every load issued up front instead of one 32-row tile per
+// round trip): partial S = V^T C, DSMEM sum over the cluster, W = Tw^T S,
+// C -= V W in shared memory, one coalesced write-back.  Leading dimension of
+// the staged chunk odd (rp) so that column-wise warp reads hit distinct banks.
+template <int NB>
+__global__ void __launch_bounds__(256, 1)
+k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restrict__ C, int ldc, int nc,
+             const float *__restrict__ Tw, int chunk, int rp)
+{
+    extern __shared__ __align__(16) float sm[];
+    float *Vc = sm;                          // rp x NB
+    float *Cc = Vc + (size_t)rp * NB;        // rp x nc
+    __shared__ float pw[NB * INNER_MAXC];    // this CTA's partial, read remotely
+    __shared__ float Sx[NB][INNER_MAXC + 1];
+    __shared__ float Wt[NB][INNER_MAXC + 1];
+    __shared__ float Xs[NB][NB + 1];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int r0 = crank * chunk, r1 = min(r0 + chunk, L), R = max(0, r1 - r0);
+    for (int e = tid; e < R * NB; e += 256) {
+        const int r = e % R, c = e / R, gr = r0 + r;
+        float v = 0.f;
+        if (c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f);
+        Vc[r + (size_t)c * rp] = v;
+    }
+    for (int e = tid; e < R * nc; e += 256) {
+        const int r = e % R, c = e / R;
+        Cc[r + (size_t)c * rp] = C[idx2(r0 + r, c, ldc)];
+    }
+    for (int e = tid; e < NB * NB; e += 256) {
+        const int a = e % NB, k = e / NB;
+        Xs[k][a] = Tw[a + k * NB];                // X = Tw^T
+    }
+    __syncthreads();
+    // partial S(i, c) = sum_r V(r, i) C(r, c): lane i, column group cb
+    constexpr int CSTEP = 256 / NB;
+    constexpr int NOUT = (INNER_MAXC + CSTEP - 1) / CSTEP;
+    const int i = tid % NB, cb = tid / NB;
+    float acc[NOUT];
+#pragma unroll
+    for (int q = 0; q < NOUT; q++) acc[q] = 0.f;
+    const float *vi = Vc + (size_t)i * rp;
+#pragma unroll 4
+    for (int r = 0; r < R; r++) {
+        const float v = vi[r];
+#pragma unroll
+        for (int q = 0; q < NOUT; q++) {
+            const int c = cb + CSTEP * q;
+            if (c < nc) acc[q] = fmaf(v, Cc[r + (size_t)c * rp], acc[q]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NOUT; q++) {
+        const int c = cb + CSTEP * q;
+        if (c < nc) pw[i + c * NB] = acc[q];
+    }
+    cluster.sync();
+    for (int e = tid; e < NB * nc; e += 256) {
+        float sum = 0.f;
+        for (int q = 0; q < cs; q++) sum += *cluster.map_shared_rank(&pw[e], q);
+        Sx[e % NB][e / NB] = sum;
+    }
+    __syncthreads();
+    for (int e = tid; e < NB * nc; e += 256) {
+        const int a = e % NB, c = e / NB;
+        float sum = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < NB; k++) sum = fmaf(Xs[a][k], Sx[k][c], sum);
+        Wt[a][c] = sum;
+    }
+    __syncthreads();
+    // C -= V W (thread per row of the chunk), then the write-back
+    for (int r = tid; r < R; r += 256) {
+        float vr[NB];
+#pragma unroll
+        for (int k = 0; k < NB; k++) vr[k] = Vc[r + (size_t)k * rp];
+        for (int c = 0; c < nc; c++) {
+            float t = 0.f;
+#pragma unroll
+            for (int k = 0; k < NB; k++) t = fmaf(vr[k], Wt[k][c], t);
+            Cc[r + (size_t)c * rp] -= t;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < R * nc; e += 256) {
+        const int r = e % R, c = e / R;
+        C[idx2(r0 + r, c, ldc)] = Cc[r + (size_t)c * rp];
+    }
+    cluster.sync();   // pw must outlive the remote reads
 }
 
 template <typename T>
@@ -714,6 +822,38 @@ static int launch_larfb(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
 static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int L, float *C, int ldc, int nc,
                            cudaStream_t s)
 {
+    {   // whole chunk in shared memory when it fits (16-CTA cluster)
+        auto kern = k_inner_cl_s<32>;
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+            attr = true;
+        }
+        const int want = std::max(1, std::min(16, ceil_div(L, 64)));
+        const int chunk0 = ceil_div(L, want);
+        const size_t smem0 = (size_t)((chunk0 | 1) * (32 + nc)) * sizeof(float);
+        const int cs = cluster_size_for((const void *)kern, 256, smem0, want);
+        const int chunk = ceil_div(L, cs), rp = chunk | 1;
+        const size_t smem = (size_t)rp * (32 + nc) * sizeof(float);
+        if (smem <= 160 * 1024) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(cs, 1, 1);
+            cfg.blockDim = dim3(256, 1, 1);
+            cfg.dynamicSmemBytes = smem;
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = cs;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            ProfScope ps(K_LARFB, s);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, kern, V, ldv, kb, L, C, ldc, nc, Tw, chunk, rp);
+            return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+        }
+    }
     auto kern = k_inner_cl<32>;
     static bool attr = false;
     if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); attr = true; }
