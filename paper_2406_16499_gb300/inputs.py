@@ -152,6 +152,36 @@ def lse_batch(seed=20244623, count=10000, m_lo=32, m_hi=512, cond_lo=1e1, cond_h
         return list(ex.map(one, specs))
 
 
+def lse_svd_torch(seed, m, n, p, cond_a, cond_b, device, noise=1.0):
+    """lse_svd's construction drawn with torch's generator on `device` (for
+    sizes whose Haar factors are slow to draw on the host): A = U diag(sigma)
+    V^T with logspace spectra, d = B x, b = A x + noise N(0,1).  FP64
+    column-major tensors (A, B, b, d, x_true)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & ((1 << 63) - 1))
+
+    def haar(rows, cols):
+        X = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
+        Q, R = torch.linalg.qr(X)
+        sg = torch.sign(torch.diagonal(R))
+        sg[sg == 0] = 1.0
+        return Q * sg
+
+    def svd_m(rows, cols, sigma):
+        U = haar(rows, len(sigma))
+        V = haar(cols, len(sigma))
+        return ((U * sigma) @ V.T).t().contiguous().t()
+
+    sa = torch.from_numpy(logspace_sigma(min(m, n), cond_a)).to(device)
+    sb = torch.from_numpy(logspace_sigma(p, cond_b)).to(device)
+    A = svd_m(m, n, sa)
+    B = svd_m(p, n, sb)
+    x = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    b = A @ x + noise * torch.randn(m, generator=g, device=device, dtype=torch.float64)
+    return dict(A=A, B=B, b=b, d=B @ x, x_true=x)
+
+
 def lse_batch_torch(specs, device, cond_b=10.0):
     """The problems of lse_batch_specs drawn with torch's generator on
     `device` (same construction as lse_svd: Haar factors from the QR of
