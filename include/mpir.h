@@ -389,7 +389,8 @@ const char *mpir_version(void);
  * launches.  Kinds: 0 panel_qr, 1 larfb, 2 vec_apply, 3 trsv, 4 gemv,
  * 5 dual_gemv_fp64, 6 resid_finalize, 7 convert, 8 norm, 9 elementwise,
  * 10 larfb_tc (tcgen05 GEMM), 11 larfb_aux (V / W preparation), 12 gmres
- * (Arnoldi steps and cycle updates), 13 batched (persistent batched solves).
+ * (Arnoldi steps and cycle updates), 13 batched (persistent batched solves),
+ * 14 selector (features and MLP kernels).
  * Not thread-safe; a profiling aid, off by default. */
 int mpir_profile(int enable);
 int mpir_profile_read(double *ms, long long *launches, int nkinds);
