@@ -47,11 +47,25 @@ struct DevScratch {          // small device scratch owned by the handle
 // factors go to Tw128 (128 x 128 per block) and whose trailing updates run
 // on the tensor cores (gemm_tc.cu) at `prec`.  lda must be a multiple of 4
 // (16-byte rows for TMA).  ws: geqrf_ws_bytes() of scratch.
+// tf (optional, FP32 storage only): also form the aggregated compact-WY
+// factor of all k reflectors, tf->Tf (k x k upper triangular, column-major,
+// ld tf->ldt >= k, a multiple of 4, 16-byte aligned):
+// H_0 ... H_{k-1} = I - V Tf V^T.  With tf->side set, that work runs on the
+// side stream (forked from s by tf->fork after each outer block, scratch
+// tf->ws2 of geqrf_ws_bytes(M, N)): the caller makes s wait for the side
+// stream before it reads Tf or reuses the scratch.
 // Returns 0, or MPIR_UNSUPPORTED / MPIR_CUDA_ERROR.
+struct TfullJob {
+    float *Tf;
+    int ldt;
+    cudaStream_t side;
+    cudaEvent_t fork, join;
+    void *ws2;
+};
 size_t geqrf_ws_bytes(int M, int N);
 template <typename T>
 int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, T *Tw128, GemmPrec prec, void *ws, int *err,
-          cudaStream_t s);
+          cudaStream_t s, const TfullJob *tf = nullptr);
 
 // C (M x Nc, ldc) <- Z^T C (trans = 1) or Z C (trans = 0) for the reflector
 // set left in (V, ldv, K reflectors, Tw, Tw128) by geqrf on an M-row matrix.
@@ -77,6 +91,14 @@ int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int tra
 template <typename TS, typename T>
 int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, int nbv, int trans, T *x,
                              cudaStream_t s);
+// x (length M) <- (I - V op(Tf) V^T) x with the aggregated factor Tf of all
+// K reflectors (geqrf's Tf, ld ldt): op = Tf^T (trans = 1, Z^T x) or Tf
+// (Z x).  Four or five full-GPU launches, no dependent per-block steps.
+// ws: wy_apply_ws_bytes(M, K) bytes (device, 256-byte aligned).
+size_t wy_apply_ws_bytes(int M, int K);
+template <typename TS, typename T>
+int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int trans, T *x, void *ws,
+                 cudaStream_t s);
 // Mixed precision (factors stored as TS, arithmetic and vectors in T).
 template <typename TS, typename T>
 int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,

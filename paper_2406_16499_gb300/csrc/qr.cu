@@ -1004,8 +1004,8 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     rc = gemm_tc(mode, 0, TCE_STORE, tV, tVl, tV, tVl, 0, 0, 0, 0, OUTER_NB, OUTER_NB, L, w.P, OUTER_NB,
                  pstride, nsplit, err, s);
     if (rc) return rc;
-    ProfScope ps(K_LARFB_AUX, s);
     {
+        ProfScope ps(K_LARFB_AUX, s);
         const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
@@ -1013,10 +1013,174 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
                                                           w.G, OUTER_NB, 0);
     }
     {
+        ProfScope ps(K_LARFB_AUX, s);
         const size_t smem = (size_t)(2 * OUTER_NB * OUTER_NB + 96 * 32) * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_outer_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
         k_outer_T<<<1, 256, smem, s>>>(Tw32, w.G, nr, Tb);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// ---------------------------------------------------------------------------
+// Aggregated compact-WY factor of the whole reflector set: Tf (K x K upper
+// triangular, column-major, ld ldt) with H_0 ... H_{K-1} = I - V Tf V^T, so
+// that a vector application is three matrix-vector products instead of one
+// dependent step per block.  Built block column by block column during the
+// two-level factorization: with V_1 the reflectors before outer block b
+// (columns 0..J0) and V_2 = V_b,
+//   (I - V_1 T_1 V_1^T)(I - V_2 T_2 V_2^T)
+//       = I - [V_1 V_2] [T_1, -T_1 (V_1^T V_2) T_2; 0, T_2] [V_1 V_2]^T
+// (Schreiber and Van Loan's aggregation of WY factors).  V_2 is zero above
+// row J0, so V_1^T V_2 only involves rows >= J0, where V_1 is the plain
+// stored part A(J0:, 0:J0).  X = (V_1^T V_2) T_2 comes from the tensor-core
+// product and the split-K reduction of the trailing update (its transpose,
+// 128 x J0, ld 128); T_12 = -T_1 X is the SIMT product below.
+// ---------------------------------------------------------------------------
+constexpr int TF_TI = 64;                         // rows of T_12 per tile
+constexpr int TF_KS = 32;                         // k per shared-memory stage
+constexpr int TF_TILE = TF_TI * OUTER_NB;
+
+// part[ti * nkc + kc] (64 x 128, column-major) = T(i0:i0+64, kc chunk) X(kc chunk, :)
+__global__ void __launch_bounds__(256)
+k_tfull_prod(const float *__restrict__ Tf, int ldt, const float *__restrict__ Xt, int J0, int KC, int nkc,
+             float *__restrict__ part)
+{
+    const int ti = blockIdx.x, kc = blockIdx.y;
+    const int i0 = ti * TF_TI;
+    const int k1 = min((kc + 1) * KC, J0);
+    if (k1 <= i0) return;                         // T(i, k) = 0 for k < i
+    const int k0 = max(kc * KC, i0);
+    __shared__ __align__(16) float Ts[TF_KS][TF_TI];       // Ts[kk][r] = T(i0 + r, k + kk)
+    __shared__ __align__(16) float Xs[TF_KS][OUTER_NB];    // Xs[kk][c] = X(k + kk, c)
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    float acc[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; r++)
+#pragma unroll
+        for (int c = 0; c < 8; c++) acc[r][c] = 0.f;
+    for (int k = k0; k < k1; k += TF_KS) {
+        for (int e = tid; e < TF_KS * TF_TI / 4; e += 256) {
+            const int kk = e / (TF_TI / 4), r4 = e % (TF_TI / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k + kk < k1) v = *reinterpret_cast<const float4 *>(Tf + (size_t)(k + kk) * ldt + i0 + 4 * r4);
+            *reinterpret_cast<float4 *>(&Ts[kk][4 * r4]) = v;
+        }
+        for (int e = tid; e < TF_KS * OUTER_NB / 4; e += 256) {
+            const int kk = e / (OUTER_NB / 4), c4 = e % (OUTER_NB / 4);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k + kk < k1) v = *reinterpret_cast<const float4 *>(Xt + (size_t)(k + kk) * OUTER_NB + 4 * c4);
+            *reinterpret_cast<float4 *>(&Xs[kk][4 * c4]) = v;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int kk = 0; kk < TF_KS; kk++) {
+            const float4 a = *reinterpret_cast<const float4 *>(&Ts[kk][4 * ty]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Xs[kk][4 * tx]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Xs[kk][64 + 4 * tx]);
+            const float av[4] = {a.x, a.y, a.z, a.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 4; r++)
+#pragma unroll
+                for (int c = 0; c < 8; c++) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    float *pp = part + ((size_t)ti * nkc + kc) * TF_TILE;
+#pragma unroll
+    for (int c = 0; c < 8; c++) {
+        const int col = c < 4 ? 4 * tx + c : 64 + 4 * tx + (c - 4);
+#pragma unroll
+        for (int r = 0; r < 4; r++) pp[(size_t)col * TF_TI + 4 * ty + r] = acc[r][c];
+    }
+}
+
+// Tf(i0 + r, J0 + c) = -sum over the valid chunks (fixed order); the diagonal
+// block Tf(J0:J0+nr, J0:J0+nr) = Tb (grid row blockIdx.x == J0 / 64 copies it).
+__global__ void __launch_bounds__(256)
+k_tfull_reduce(const float *__restrict__ part, int J0, int nr, int KC, int nkc, const float *__restrict__ Tb,
+               float *__restrict__ Tf, int ldt)
+{
+    const int ti = blockIdx.x, tid = threadIdx.x;
+    if (ti * TF_TI >= J0) {
+        if (blockIdx.y) return;
+        for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) {
+            const int i = e % OUTER_NB, c = e / OUTER_NB;
+            if (i < nr && c < nr) Tf[(size_t)(J0 + c) * ldt + J0 + i] = Tb[i + (size_t)c * OUTER_NB];
+        }
+        return;
+    }
+    // blockIdx.y: a group of 16 columns; loads batched 8 deep, summed in chunk order
+    const int i0 = ti * TF_TI, kc0 = i0 / KC;
+    const int e = blockIdx.y * 16 * TF_TI + tid * 4;          // 4 consecutive rows per thread
+    const int r = e % TF_TI, c = e / TF_TI;
+    if (c >= nr) return;
+    const float *pp = part + (size_t)ti * nkc * TF_TILE + (size_t)c * TF_TI + r;
+    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int kc = kc0; kc < nkc; kc += 8) {
+        float4 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+            v[u] = kc + u < nkc ? *reinterpret_cast<const float4 *>(pp + (size_t)(kc + u) * TF_TILE)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 8; u++) { sum.x += v[u].x; sum.y += v[u].y; sum.z += v[u].z; sum.w += v[u].w; }
+    }
+    float *out = Tf + (size_t)(J0 + c) * ldt + i0 + r;
+    out[0] = -sum.x; out[1] = -sum.y; out[2] = -sum.z; out[3] = -sum.w;
+}
+
+// Block column b of Tf (outer block at J0, nr reflectors, its prepared V in
+// w and its factor Tb).  A: the matrix being factored (lda), M rows.
+static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int nr, const float *Tb, float *Tf,
+                       int ldt, int mode, int *err, cudaStream_t s)
+{
+    const int L = M - J0;
+    int ntile = J0 / TF_TI, KC = 32, nkc = 0;
+    if (J0 > 0) {
+        const int split = mode == TCM_TF32X3;
+        CUtensorMap tV, tVl, tA;
+        int rc = tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
+        rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
+        rc |= tmap_colmajor(&tA, A + J0, L, J0, lda, OUTER_NB);
+        if (rc) return MPIR_UNSUPPORTED;
+        const int ntn = ceil_div(J0, OUTER_NB);
+        const int ksteps = ceil_div(L, 32);
+        int nsplit = ceil_div(2 * 152, ntn);
+        if (nsplit > PSPLIT_CAP / ntn) nsplit = PSPLIT_CAP / ntn;
+        if (nsplit > ksteps) nsplit = ksteps;
+        if (nsplit < 1) nsplit = 1;
+        if ((size_t)nsplit * OUTER_NB * ntn * OUTER_NB > w.pcap) nsplit = 1;
+        const size_t pstride = (size_t)OUTER_NB * ntn * OUTER_NB;
+        // P[z] = V_b^T A(J0:, 0:J0)   (128 x J0, split-K)
+        rc = gemm_tc(mode, split, TCE_STORE, tV, tVl, tA, tA, 0, 0, 0, 0, OUTER_NB, J0, L, w.P, OUTER_NB, pstride,
+                     nsplit, err, s);
+        if (rc) return rc;
+        {
+            ProfScope ps(K_LARFB_AUX, s);
+            const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
+            static bool attr = false;
+            if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+            // W = T_b^T sum P = X^T,  X = (V_1^T V_b) T_b
+            k_reduce_w<<<ceil_div(J0, RW_COLS), 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, Tb, 1, J0, w.W,
+                                                                 w.W, OUTER_NB, 0);
+        }
+        // chunking of k: about four tiles per SM, partials within w.P
+        int want = ceil_div(8 * 152, ntile);
+        const int cap = (int)(w.pcap / ((size_t)ntile * TF_TILE));
+        if (want > cap) want = cap;
+        if (want > J0 / TF_KS) want = J0 / TF_KS;
+        if (want < 1) want = 1;
+        KC = ceil_div(ceil_div(J0, want), TF_KS) * TF_KS;
+        nkc = ceil_div(J0, KC);
+        if ((size_t)ntile * nkc * TF_TILE > w.pcap) return MPIR_UNSUPPORTED;
+        ProfScope ps(K_LARFB_AUX, s);
+        k_tfull_prod<<<dim3(ntile, nkc), 256, 0, s>>>(Tf, ldt, w.W, J0, KC, nkc, w.P);
+    }
+    {
+        ProfScope ps(K_LARFB_AUX, s);
+        k_tfull_reduce<<<dim3(ntile + 1, OUTER_NB / 16), 256, 0, s>>>(w.P, J0, nr, KC, nkc, Tb, Tf, ldt);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
@@ -1045,7 +1209,7 @@ static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, cudaStream_t s
 
 template <>
 int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *, int *,
-                  cudaStream_t s)
+                  cudaStream_t s, const TfullJob *)
 {
     return geqrf_simt<double>(A, lda, M, N, tau, Tw, s);
 }
@@ -1055,13 +1219,23 @@ int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, dou
 // the tensor cores.
 template <>
 int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *Tw128, GemmPrec prec, void *ws,
-                 int *err, cudaStream_t s)
+                 int *err, cudaStream_t s, const TfullJob *tf)
 {
     constexpr int NB = 32;
     const int k = M < N ? M : N;
     if (lda % 4) return MPIR_UNSUPPORTED;
     OuterWs w = outer_layout(ws, M, N, nullptr);
     const int mode = tc_mode(prec);
+    // the aggregated factor is built on the side stream when there is one,
+    // from its own prepared copy of each finished outer block
+    const bool side = tf && tf->side && tf->side != s && tf->ws2;
+    cudaStream_t ss = side ? tf->side : s;
+    OuterWs w2 = side ? outer_layout(tf->ws2, M, N, nullptr) : w;
+    if (tf) {
+        if (tf->ldt < k || tf->ldt % 4 || ((uintptr_t)tf->Tf & 15)) return MPIR_UNSUPPORTED;
+        if (side) { cudaEventRecord(tf->fork, s); cudaStreamWaitEvent(ss, tf->fork, 0); }
+        cudaMemsetAsync(tf->Tf, 0, (size_t)tf->ldt * k * sizeof(float), ss);
+    }
     for (int J0 = 0; J0 < k; J0 += OUTER_NB) {
         const int ncolsO = N - J0 < OUTER_NB ? N - J0 : OUTER_NB;
         const int L = M - J0;
@@ -1085,6 +1259,15 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
         prep_v(A + idx2(J0, J0, lda), lda, L, nr, w, mode == TCM_TF32X3, s);
         int rc = outer_T(w, Tw + (size_t)(J0 / NB) * NB * NB, L, nr, Tb, mode, err, s);
         if (rc) return rc;
+        if (tf) {
+            if (side) {
+                cudaEventRecord(tf->fork, s);
+                cudaStreamWaitEvent(ss, tf->fork, 0);
+                prep_v(A + idx2(J0, J0, lda), lda, L, nr, w2, mode == TCM_TF32X3, ss);
+            }
+            rc = tfull_block(w2, A, lda, M, J0, nr, Tb, tf->Tf, tf->ldt, mode, err, ss);
+            if (rc) return rc;
+        }
         if (Nc > 0) {
             rc = outer_apply(w, Tb, 1, L, A + idx2(J0, J0 + ncolsO, lda), lda, Nc, mode, err, s);
             if (rc) return rc;

@@ -104,7 +104,11 @@ template <typename T> struct LseWs {
     int m, n, p, q, kA;
     int ldBt, ldX, ldAt;                 // padded to 32 (TMA rows of 128 bytes)
     T *Bt, *tauB, *TwB, *X, *At, *tauA, *TwA, *Tw128B, *Tw128A, *DinvB, *DinvA;
+    T *TfB, *TfA;                        // aggregated compact-WY factors (FP32 storage only)
+    int ldtB, ldtA;
     void *gws;                           // scratch of the two-level factorization
+    void *wy;                            // scratch of the aggregated vector applications
+    void *gws2;                          // side-stream scratch of the aggregated factors
     T *tu, *tw, *ty, *tq, *tb, *tt, *tt2;
     double *f1, *f2, *f3, *r, *v, *pAx, *pAtr, *pBx, *pBtv, *normpart, *norms2, *scal, *part;
     DualGemvPlan pa, pb;
@@ -114,7 +118,11 @@ template <typename T> struct GlsWs {
     int n, m, p, L, o, kC;
     int ldW, ldC, ldCt;                  // padded to 32 (TMA rows of 128 bytes)
     T *Wf, *tauW, *TwW, *Cf, *Ct, *tauC, *TwC, *Tw128W, *Tw128C, *DinvW, *DinvC;
+    T *TfW, *TfC;                        // aggregated compact-WY factors (FP32 storage only)
+    int ldtW, ldtC;
     void *gws;                           // scratch of the two-level factorization
+    void *wy;                            // scratch of the aggregated vector applications
+    void *gws2;                          // side-stream scratch of the aggregated factors
     T *tu, *tw, *th, *tg, *tt, *tt2;
     double *f1, *f2, *f3, *z, *pWx, *pWtz, *pVy, *pVtz, *normpart, *norms2, *scal, *part;
     DualGemvPlan pw, pv;
@@ -141,6 +149,13 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
     w.DinvA = c.take<T>((size_t)std::max(ceil_div(w.kA, 32), 1) * 1024);
     w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
                                            geqrf_ws_bytes(m, n)));
+    w.ldtB = rup32(std::max(p, 1)); w.ldtA = rup32(std::max(w.kA, 1));
+    if (sizeof(T) == 4) {
+        w.TfB = c.take<T>((size_t)w.ldtB * std::max(p, 1));
+        w.TfA = c.take<T>((size_t)w.ldtA * std::max(w.kA, 1));
+        w.wy = c.take<unsigned char>(std::max(wy_apply_ws_bytes(n, p), wy_apply_ws_bytes(m, w.kA)));
+        w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(m, n)));
+    }
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.ty = c.take<T>(mx); w.tq = c.take<T>(mx);
     w.tb = c.take<T>(mx); w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
     w.pa = dual_gemv_plan(m, n);
@@ -180,6 +195,13 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
     w.DinvC = c.take<T>((size_t)std::max(ceil_div(w.kC, 32), 1) * 1024);
     w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
                                            geqrf_ws_bytes(p, n)));
+    w.ldtW = rup32(std::max(m, 1)); w.ldtC = rup32(std::max(w.kC, 1));
+    if (sizeof(T) == 4) {
+        w.TfW = c.take<T>((size_t)w.ldtW * std::max(m, 1));
+        w.TfC = c.take<T>((size_t)w.ldtC * std::max(w.kC, 1));
+        w.wy = c.take<unsigned char>(std::max(wy_apply_ws_bytes(n, m), wy_apply_ws_bytes(p, w.kC)));
+        w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(p, n)));
+    }
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.th = c.take<T>(mx); w.tg = c.take<T>(mx);
     w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
     w.pw = dual_gemv_plan(n, m);
@@ -225,6 +247,9 @@ struct mpir_ctx {
     size_t rws_bytes = 0;
     BatchArena ba;               // batched solves: tables, results, tuned shapes, graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    cudaStream_t side = nullptr;         // aggregated compact-WY factors, built beside the factorization
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
+    TfullJob tfj{};
     // learned selector: parameters and feature standardization (device), scratch
     float *sel = nullptr;        // params[MLP_PARAMS], X[16], prob[6], feat[16]
     float sel_mean[16], sel_scale[16];
@@ -238,6 +263,37 @@ int set_err(mpir_ctx *h, int code, const char *msg)
 {
     if (h) h->err = msg ? msg : "";
     return code;
+}
+
+// Job description for geqrf's aggregated factor (FP32 storage only); the
+// side stream and its events are created on first use.
+template <typename T>
+const TfullJob *tfjob(mpir_ctx *h, T *Tf, int ldt, void *ws2)
+{
+    if (sizeof(T) != 4 || !Tf) return nullptr;
+    if (!h->side) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            h->side = nullptr;
+        }
+    }
+    h->tfj.Tf = reinterpret_cast<float *>(Tf);
+    h->tfj.ldt = ldt;
+    h->tfj.side = h->side;
+    h->tfj.fork = h->side_fork;
+    h->tfj.join = h->side_join;
+    h->tfj.ws2 = ws2;
+    return &h->tfj;
+}
+
+// The stream waits for everything queued on the side stream so far.
+void join_side(mpir_ctx *h, cudaStream_t s)
+{
+    if (!h->side) return;
+    cudaEventRecord(h->side_join, h->side);
+    cudaStreamWaitEvent(s, h->side_join, 0);
 }
 
 int cuda_check(mpir_ctx *h, const char *where)
@@ -254,7 +310,11 @@ int ensure_ws(mpir_ctx *h, size_t bytes)
 {
     if (h->ws_bytes >= bytes) return 0;
     if (h->ws && !h->ws_owned) return set_err(h, MPIR_UNSUPPORTED, "caller workspace too small");
-    if (h->ws) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0; }
+    if (h->ws) {
+        cudaStreamSynchronize(h->stream);
+        if (h->side) cudaStreamSynchronize(h->side);
+        cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0;
+    }
     if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "workspace cudaMalloc failed"); }
     h->ws_bytes = bytes;
     h->ws_owned = true;
@@ -347,9 +407,10 @@ GemmPrec gemm_prec(int fact)
 // Reflector-set application to one vector with the widest compact-WY
 // blocks the factorization kept: 128 (two-level FP32) or 16 (FP64).
 template <typename T>
-int vapply(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, int trans, T *x, const DevScratch &,
-           cudaStream_t s)
+int vapply(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, const T *Tf, int ldt, void *wy, int trans,
+           T *x, const DevScratch &, cudaStream_t s)
 {
+    if (sizeof(T) == 4 && Tf) return wy_apply_vec<T, T>(V, ldv, M, K, Tf, ldt, trans, x, wy, s);
     if (sizeof(T) == 4) return apply_reflectors_vec_blk<T, T>(V, ldv, M, K, Tw128, OUTER_NB, trans, x, s);
     return apply_reflectors_vec_blk<T, T>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
 }
@@ -391,6 +452,7 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     RC(ensure_ws(h, bytes));
     GlsWs<T> w = gls_layout<T>(h->ws, n, m, p, nullptr);
     cudaStream_t s = h->stream;
+    join_side(h, s);
     clear_dev_flags(h);
     absmax_sumsq(W, ldw, n, m, w.part, w.scal + 0, s);
     absmax_sumsq(V, ldv, n, p, w.part, w.scal + 2, s);
@@ -407,16 +469,17 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     const GemmPrec gp = gemm_prec(fact);
     // QR of W (Lemma 4.6, first factorization)
     mconvert<double, T>(W, ldw, w.Wf, w.ldW, n, m, 0, 0, 0, sW, s);
-    RC(geqrf<T>(w.Wf, w.ldW, n, m, w.tauW, w.TwW, w.Tw128W, gp, w.gws, h->sc.err, s));
+    RC(geqrf<T>(w.Wf, w.ldW, n, m, w.tauW, w.TwW, w.Tw128W, gp, w.gws, h->sc.err, s, tfjob(h, w.TfW, w.ldtW, w.gws2)));
     // C = Q^T V
     mconvert<double, T>(V, ldv, w.Cf, w.ldC, n, p, 0, 0, 0, sV, s);
     RC(apply_reflectors_left<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.Cf, w.ldC, p, gp, w.gws, h->sc.err, s));
     // RQ of C as QR of C~ = P_p C^T P_n
     mconvert<T, T>(w.Cf, w.ldC, w.Ct, w.ldCt, p, n, 1, 1, 1, 1.0, s);
-    RC(geqrf<T>(w.Ct, w.ldCt, p, n, w.tauC, w.TwC, w.Tw128C, gp, w.gws, h->sc.err, s));
+    RC(geqrf<T>(w.Ct, w.ldCt, p, n, w.tauC, w.TwC, w.Tw128C, gp, w.gws, h->sc.err, s, tfjob(h, w.TfC, w.ldtC, w.gws2)));
     // inverses of the 32 x 32 diagonal blocks of R and T~ for the solves
     invert_diag32<T>(w.Wf, w.ldW, m, w.DinvW, h->sc.status, s);
     invert_diag32<T>(w.Ct, w.ldCt, w.L, w.DinvC, h->sc.status, s);   // T~_L, the block that is solved
+    if (sizeof(T) == 4) join_side(h, s);
     return cuda_check(h, "gls_factor");
 }
 
@@ -432,7 +495,7 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     double *g = w.scal + 8;
     pow2_normalizer(d, n, 1.0, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(d, w.tu, n, 1.0, 0, s, g);
-    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 1, w.tu, h->sc, s));
     // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
     vzero(w.tg, sizeof(T) * p, s);
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
@@ -443,7 +506,7 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s, w.DinvW));
     vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s, g + 1);
     // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
-    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 0, w.tg, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
     vcopy<T, double>(w.tg, y, p, fs.s2, 1, s, g + 1);
     return cuda_check(h, "gls_initial");
 }
@@ -460,14 +523,14 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     double *g = w.scal + 8;
     pow2_normalizer(y, p, 1.0 / fs.s2, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(y, w.tw, p, 1.0 / fs.s2, 1, s, g);
-    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // T~_L h~2 = w~[0:L]
     vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
     RC(trsv_upper<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s, w.DinvC));
     // z' = Q [0_m; P_L h~2]
     vzero(w.tt, sizeof(T) * n, s);
     vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
-    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, w.tt, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, z, n, fs.s2 * fs.s2, 0, s, g + 1);
     return cuda_check(h, "gls_multipliers");
 }
@@ -486,10 +549,10 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     cudaStream_t s = h->stream;
     // step 1: u = Q^T f2'
     vcopy<double, T>(f2, w.tu, n, c2, 0, s);
-    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 1, w.tu, h->sc, s));
     // step 2: w~ = Z~^T (P_p f1') = P_p (Z f1')
     vcopy<double, T>(f1, w.tw, p, c1, 1, s);
-    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // step 3: R^T h1 = f3'   (th[0:m] = h1)
     vcopy<double, T>(f3, w.th, m, c3, 0, s);
     RC(trsv_upper<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s, w.DinvW));
@@ -516,12 +579,12 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s, w.DinvW));
     vaxpy<T>(w.tt, dx, m, sW / sV / gamma, 0, s);
     // step 7: dy = Z^T g = P_p Z~ g~
-    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, 0, w.tg, h->sc, s));
+    RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
     vaxpy<T>(w.tg, dy, p, 1.0 / gamma, 1, s);
     //         dz = -Q h,  h = [h1; P_L h~2]
     vcomb<T>(w.tt2, L, w.th + m, 1, T(1), nullptr, 0, T(0), s);
     cudaMemcpyAsync(w.th + m, w.tt2, sizeof(T) * L, cudaMemcpyDeviceToDevice, s);
-    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, w.th, h->sc, s));
+    RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 0, w.th, h->sc, s));
     vaxpy<T>(w.th, dz, n, -sV / gamma, 0, s);
     return cuda_check(h, "gls_correction");
 }
@@ -637,8 +700,10 @@ int gemv_d(const T *M, int ld, int rows, int cols, int trans, double alpha, cons
 
 // Reflector set applied in FP64 arithmetic to an FP64 vector.
 template <typename T>
-int vapply_d(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, int trans, double *x, cudaStream_t s)
+int vapply_d(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, const T *Tf, int ldt, void *wy,
+             int trans, double *x, cudaStream_t s)
 {
+    if (sizeof(T) == 4 && Tf) return wy_apply_vec<T, double>(V, ldv, M, K, Tf, ldt, trans, x, wy, s);
     if (sizeof(T) == 4) return apply_reflectors_vec_blk<T, double>(V, ldv, M, K, Tw128, OUTER_NB, trans, x, s);
     return apply_reflectors_vec_blk<T, double>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
 }
@@ -680,7 +745,7 @@ struct GlsBDOp : LinOp {
         vcomb<double>(b.w1, n, t + p, 1, 1.0, nullptr, 0, 0.0, s);
         RC(trsv_d<T>(w.Ct, w.ldCt, n, 0, b.w1, h->sc, s, b.dT));
         vcomb<double>(u + p, n, b.w1, 1, sa * sV, nullptr, 0, 0.0, s);
-        RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 0, u + p, s));
+        RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 0, u + p, s));
         if (m > 0) {
             // a^-1/2 b^-1 R^-1 S t3 = a^-1/2 b^-1 (sW/sV) R'^-1 P_m T~_S'^T P_m t3
             vcomb<double>(b.w1, m, t + p + n, 1, 1.0, nullptr, 0, 0.0, s);
@@ -712,7 +777,7 @@ struct GlsBDOp : LinOp {
         vcomb<double>(o, p, g, 0, 1.0 / sa, nullptr, 0, 0.0, s);
         // a^1/2 T2^-1 Q^T g2 = a^1/2 sV P_n T~_n'^-T P_n Q^T g2
         vcomb<double>(b.w1, n, g + p, 0, 1.0, nullptr, 0, 0.0, s);
-        RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, b.w1, s));
+        RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(trsv_d<T>(w.Ct, w.ldCt, n, 1, b.w2, h->sc, s, b.dT));
         vcomb<double>(o + p, n, b.w2, 1, sa * sV, nullptr, 0, 0.0, s);
@@ -876,6 +941,7 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     RC(ensure_ws(h, bytes));
     LseWs<T> w = lse_layout<T>(h->ws, m, n, p, nullptr);
     cudaStream_t s = h->stream;
+    join_side(h, s);
     clear_dev_flags(h);
     absmax_sumsq(A, lda, m, n, w.part, w.scal + 0, s);
     absmax_sumsq(B, ldb, p, n, w.part, w.scal + 2, s);
@@ -892,16 +958,17 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     const GemmPrec gp = gemm_prec(fact);
     // RQ of B as QR of B~ = P_n B^T P_p (Lemma 4.5, first factorization)
     mconvert<double, T>(B, ldb, w.Bt, w.ldBt, n, p, 1, 1, 1, sB, s);
-    RC(geqrf<T>(w.Bt, w.ldBt, n, p, w.tauB, w.TwB, w.Tw128B, gp, w.gws, h->sc.err, s));
+    RC(geqrf<T>(w.Bt, w.ldBt, n, p, w.tauB, w.TwB, w.Tw128B, gp, w.gws, h->sc.err, s, tfjob(h, w.TfB, w.ldtB, w.gws2)));
     // X = Q~^T P_n A^T = P_n (A Q^T)^T
     mconvert<double, T>(A, lda, w.X, w.ldX, n, m, 1, 1, 0, sA, s);
     RC(apply_reflectors_left<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.X, w.ldX, m, gp, w.gws, h->sc.err, s));
     // A Q^T = X^T P_n, then its QR  (A Q^T = Z T)
     mconvert<T, T>(w.X, w.ldX, w.At, w.ldAt, m, n, 1, 0, 1, 1.0, s);
-    RC(geqrf<T>(w.At, w.ldAt, m, n, w.tauA, w.TwA, w.Tw128A, gp, w.gws, h->sc.err, s));
+    RC(geqrf<T>(w.At, w.ldAt, m, n, w.tauA, w.TwA, w.Tw128A, gp, w.gws, h->sc.err, s, tfjob(h, w.TfA, w.ldtA, w.gws2)));
     // inverses of the 32 x 32 diagonal blocks of R~ and T for the solves
     invert_diag32<T>(w.Bt, w.ldBt, p, w.DinvB, h->sc.status, s);
     invert_diag32<T>(w.At, w.ldAt, w.q, w.DinvA, h->sc.status, s);   // T11, the block that is solved
+    if (sizeof(T) == 4) join_side(h, s);
     return cuda_check(h, "lse_factor");
 }
 
@@ -918,7 +985,7 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     double *g = w.scal + 8;
     pow2_normalizer(b, m, fs.s1, d, p, fs.s2, g, s);
     vcopy<double, T>(b, w.tw, m, fs.s1, 0, s, g);
-    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 1, w.tw, h->sc, s));
     // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
     vcopy<double, T>(d, w.tb, p, fs.s2, 1, s, g);
     RC(trsv_upper<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
@@ -929,7 +996,7 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     RC(trsv_upper<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
     // x = Q^T y = P_n Q~ P_n y
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
-    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, w.tt, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, x, n, 1.0, 1, s, g + 1);
     return cuda_check(h, "lse_initial");
 }
@@ -951,7 +1018,7 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     double *g = w.scal + 8;
     pow2_normalizer(w.f3, n, fs.s1, nullptr, 0, 0.0, g, s);
     vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s, g);
-    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, w.tu, h->sc, s));
     // R~ (P_p v') = u~[0:p]
     RC(trsv_upper<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s, w.DinvB));
     vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s, g + 1);
@@ -971,10 +1038,10 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     cudaStream_t s = h->stream;
     // step 1: u~ = Q~^T P_n f3' ;  u1 = P_q u~[p:n], u2 = P_p u~[0:p]
     vcopy<double, T>(f3, w.tu, n, c3, 1, s);
-    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.tu, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, w.tu, h->sc, s));
     // step 2: w = Z^T f1'
     vcopy<double, T>(f1, w.tw, m, c1, 0, s);
-    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, 1, w.tw, h->sc, s));
+    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 1, w.tw, h->sc, s));
     // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
     if (p > 0) {
         vcopy<double, T>(f2, w.tb, p, c2, 1, s);
@@ -1005,10 +1072,10 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
         vaxpy<T>(w.tb, dv, p, sB / sA / gamma, 1, s);
     }
     // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
-    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, 0, w.tq, h->sc, s));
+    RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 0, w.tq, h->sc, s));
     vaxpy<T>(w.tq, dr, m, 1.0 / gamma, 0, s);
     vcomb<T>(w.tt2, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
-    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, w.tt2, h->sc, s));
+    RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, w.tt2, h->sc, s));
     vaxpy<T>(w.tt2, dx, n, sA / gamma, 1, s);
     return cuda_check(h, "lse_correction");
 }
@@ -1077,7 +1144,7 @@ struct LseBDOp : LinOp {
         vcomb<double>(b.w1, n, t + m + p, 0, 1.0, nullptr, 0, 0.0, s);
         RC(trsv_d<T>(w.At, w.ldAt, n, 0, b.w1, h->sc, s, b.dT));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 0, b.w2, s));
+        RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, b.w2, s));
         vcomb<double>(u + m + p, n, b.w2, 1, sa * sA, nullptr, 0, 0.0, s);
         return 0;
     }
@@ -1111,7 +1178,7 @@ struct LseBDOp : LinOp {
         }
         // a^1/2 T1^-T Q g3 = a^1/2 sA T1'^-T P_n Q~^T P_n g3
         vcomb<double>(b.w1, n, g + m + p, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, b.w1, s));
+        RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(trsv_d<T>(w.At, w.ldAt, n, 1, b.w2, h->sc, s, b.dT));
         vcomb<double>(o + m + p, n, b.w2, 0, sa * sA, nullptr, 0, 0.0, s);
@@ -1344,6 +1411,7 @@ int mpir_destroy(mpir_handle h)
 {
     if (!h) return -1;
     cudaStreamSynchronize(h->stream);
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->ws && h->ws_owned) cudaFree(h->ws);
     if (h->scratch_base) cudaFree(h->scratch_base);
     if (h->rws) cudaFree(h->rws);
@@ -1356,6 +1424,12 @@ int mpir_destroy(mpir_handle h)
         if (a.hres) cudaFreeHost(a.hres);
         if (a.horder) cudaFreeHost(a.horder);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    }
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaStreamDestroy(h->side);
+        cudaEventDestroy(h->side_fork);
+        cudaEventDestroy(h->side_join);
     }
     if (h->sel) cudaFree(h->sel);
     if (h->sel_s) cudaFree(h->sel_s);
@@ -1375,6 +1449,7 @@ int mpir_set_workspace(mpir_handle h, void *ptr, size_t bytes)
 {
     if (!h) return -1;
     if (((uintptr_t)ptr & 255) != 0) return -2;
+    if (h->side) cudaStreamSynchronize(h->side);
     if (h->ws && h->ws_owned) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); }
     h->ws = ptr;
     h->ws_bytes = ptr ? bytes : 0;
@@ -2136,12 +2211,12 @@ static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
             // Q = P_n Q~^T P_n ; Q^T = P_n Q~ P_n
             const int n = w.n;
             vcopy<double, T>(vec, w.tt, n, 1.0, 1, s);
-            RC(vapply<T>(w.Bt, w.ldBt, n, w.p, w.TwB, w.Tw128B, trans ? 0 : 1, w.tt, h->sc, s));
+            RC(vapply<T>(w.Bt, w.ldBt, n, w.p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, trans ? 0 : 1, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, n, 1.0, 1, s);
         } else {
             const int m = w.m;
             vcopy<double, T>(vec, w.tt, m, 1.0, 0, s);
-            RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, trans, w.tt, h->sc, s));
+            RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, trans, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, m, 1.0, 0, s);
         }
     } else {
@@ -2149,13 +2224,13 @@ static int apply_factor_impl(mpir_ctx *h, int which, int trans, double *vec)
         if (which == 0) {
             const int n = w.n;
             vcopy<double, T>(vec, w.tt, n, 1.0, 0, s);
-            RC(vapply<T>(w.Wf, w.ldW, n, w.m, w.TwW, w.Tw128W, trans, w.tt, h->sc, s));
+            RC(vapply<T>(w.Wf, w.ldW, n, w.m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, trans, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, n, 1.0, 0, s);
         } else {
             // Z = P_p Z~^T P_p ; Z^T = P_p Z~ P_p
             const int p = w.p;
             vcopy<double, T>(vec, w.tt, p, 1.0, 1, s);
-            RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, trans ? 0 : 1, w.tt, h->sc, s));
+            RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, trans ? 0 : 1, w.tt, h->sc, s));
             vcopy<T, double>(w.tt, vec, p, 1.0, 1, s);
         }
     }

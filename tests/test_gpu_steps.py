@@ -156,6 +156,60 @@ def test_gqr_invariants(h, fact, tol, n, m, p):
     assert np.linalg.norm(Z.T @ Z - np.eye(p)) <= tol * 30 * p
 
 
+def _explicit_t(h, which, k):
+    """Columns of Q^T (or Z^T) through the transposed application."""
+    import torch
+    cols = []
+    for j in range(k):
+        e = torch.zeros(k, dtype=torch.float64, device="cuda")
+        e[j] = 1.0
+        h.apply_factor(which, True, e)
+        cols.append(host(e))
+    return np.column_stack(cols)
+
+
+def test_grq_gqr_many_blocks(h):
+    """Reflector sets of several 128-wide outer blocks (the FP32 path applies
+    them through the aggregated compact-WY factor): Lemma 4.5 / 4.6 still
+    hold, and the transposed application is the transpose of the forward one."""
+    tol = 3e-6
+    m, n, p = 700, 600, 300
+    P = I.lse_svd(3 * m + n + p, m, n, p, 1e2, 1e1)
+    A, B = P["A"], P["B"]
+    h.lse_factor(dev(A), dev(B), "fp32")
+    import torch
+    R = torch.zeros((p, p), dtype=torch.float64, device="cuda").t().contiguous().t()
+    T = torch.zeros((n, m), dtype=torch.float64, device="cuda").t()
+    h.get_RT(R, T)
+    R, T = host(R), host(T)
+    Q, Z = _explicit(h, "Q", n), _explicit(h, "Z", m)
+    RB = np.zeros((p, n))
+    RB[:, n - p:] = R
+    assert np.linalg.norm(B - RB @ Q) <= tol * 30 * np.linalg.norm(B)
+    assert np.linalg.norm(A - Z @ T @ Q) <= tol * 30 * np.linalg.norm(A)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= tol * 30 * n
+    assert np.linalg.norm(Z.T @ Z - np.eye(m)) <= tol * 30 * m
+    assert np.abs(_explicit_t(h, "Q", n) - Q.T).max() <= 1e-5
+    assert np.abs(_explicit_t(h, "Z", m) - Z.T).max() <= 1e-5
+    n, m, p = 900, 400, 800
+    G = I.gls_svd(n + 3 * m + p, n, m, p, 1e2, 1e1)
+    W, V = G["W"], G["V"]
+    h.gls_factor(dev(W), dev(V), "fp32")
+    R = torch.zeros((m, m), dtype=torch.float64, device="cuda").t()
+    T = torch.zeros((p, n), dtype=torch.float64, device="cuda").t()
+    h.get_RT(R, T)
+    R, T = host(R), host(T)
+    Q, Z = _explicit(h, "Q", n), _explicit(h, "Z", p)
+    RW = np.zeros((n, m))
+    RW[:m] = R
+    assert np.linalg.norm(W - Q @ RW) <= tol * 30 * np.linalg.norm(W)
+    assert np.linalg.norm(V - Q @ T @ Z) <= tol * 30 * np.linalg.norm(V)
+    assert np.linalg.norm(Q.T @ Q - np.eye(n)) <= tol * 30 * n
+    assert np.linalg.norm(Z.T @ Z - np.eye(p)) <= tol * 30 * p
+    assert np.abs(_explicit_t(h, "Q", n) - Q.T).max() <= 1e-5
+    assert np.abs(_explicit_t(h, "Z", p) - Z.T).max() <= 1e-5
+
+
 # ------------------------------------------------- initial solutions --
 
 @pytest.mark.parametrize("fact", ["fp32", "fp64"])
