@@ -99,6 +99,19 @@ size_t wy_apply_ws_bytes(int M, int K);
 template <typename TS, typename T>
 int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int trans, T *x, void *ws,
                  cudaStream_t s);
+// Triangular solves of FP32-stored factors of order n <= 8192 in 64-row
+// blocks (trsv64.cu): trsv64_ok(n, sizeof(storage)) says whether they apply;
+// invert_diag64 forms the inverses of the 64 x 64 diagonal blocks (4096
+// entries per block, column-major; zero pivot -> bit 1 of *status) that
+// trsv64 reads.  trsv64 returns -1 when it cannot run (the caller then uses
+// the 32-row solve by substitution).  dinv_elems(N): entries of an inverse
+// array for either block size.
+bool trsv64_ok(int n, size_t ts_bytes);
+size_t dinv_elems(int N);
+template <typename TS, typename T>
+void invert_diag64(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s);
+template <typename T>
+int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaStream_t s);
 // Mixed precision (factors stored as TS, arithmetic and vectors in T).
 template <typename TS, typename T>
 int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,

@@ -145,8 +145,8 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
     w.tauA = c.take<T>(std::max(w.kA, 1));
     w.TwA = c.take<T>((size_t)std::max(ceil_div(w.kA, NB), 1) * NB * NB);
     w.Tw128A = c.take<T>((size_t)std::max(ceil_div(w.kA, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
-    w.DinvB = c.take<T>((size_t)std::max(ceil_div(p, 32), 1) * 1024);
-    w.DinvA = c.take<T>((size_t)std::max(ceil_div(w.kA, 32), 1) * 1024);
+    w.DinvB = c.take<T>(dinv_elems(p));
+    w.DinvA = c.take<T>(dinv_elems(w.kA));
     w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
                                            geqrf_ws_bytes(m, n)));
     w.ldtB = rup32(std::max(p, 1)); w.ldtA = rup32(std::max(w.kA, 1));
@@ -191,8 +191,8 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
     w.tauC = c.take<T>(std::max(w.kC, 1));
     w.TwC = c.take<T>((size_t)std::max(ceil_div(w.kC, NB), 1) * NB * NB);
     w.Tw128C = c.take<T>((size_t)std::max(ceil_div(w.kC, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
-    w.DinvW = c.take<T>((size_t)std::max(ceil_div(m, 32), 1) * 1024);
-    w.DinvC = c.take<T>((size_t)std::max(ceil_div(w.kC, 32), 1) * 1024);
+    w.DinvW = c.take<T>(dinv_elems(m));
+    w.DinvC = c.take<T>(dinv_elems(w.kC));
     w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
                                            geqrf_ws_bytes(p, n)));
     w.ldtW = rup32(std::max(m, 1)); w.ldtC = rup32(std::max(w.kC, 1));
@@ -404,6 +404,29 @@ GemmPrec gemm_prec(int fact)
 
 #define RC(x) do { int _rc = (x); if (_rc) return _rc; } while (0)
 
+// Triangular solve with FP32 or FP64 factors: FP32 factors of order <= 8192
+// use 64-row diagonal blocks (inverses from inv_diag), others 32-row blocks.
+template <typename T>
+int tsolve(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s, const T *Dinv)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (trsv64_ok(n, sizeof(T))) {
+            const int rc = trsv64<T>(U, ldu, n, trans, x, Dinv, s);
+            if (rc >= 0) return rc;
+            return trsv_upper<T>(U, ldu, n, trans, x, sc, s, nullptr);
+        }
+    }
+    return trsv_upper<T>(U, ldu, n, trans, x, sc, s, Dinv);
+}
+template <typename T>
+void inv_diag(const T *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (trsv64_ok(N, sizeof(T))) { invert_diag64<T, T>(U, ldu, N, Dinv, status, s); return; }
+    }
+    invert_diag32<T>(U, ldu, N, Dinv, status, s);
+}
+
 // Reflector-set application to one vector with the widest compact-WY
 // blocks the factorization kept: 128 (two-level FP32) or 16 (FP64).
 template <typename T>
@@ -477,8 +500,8 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     mconvert<T, T>(w.Cf, w.ldC, w.Ct, w.ldCt, p, n, 1, 1, 1, 1.0, s);
     RC(geqrf<T>(w.Ct, w.ldCt, p, n, w.tauC, w.TwC, w.Tw128C, gp, w.gws, h->sc.err, s, tfjob(h, w.TfC, w.ldtC, w.gws2)));
     // inverses of the 32 x 32 diagonal blocks of R and T~ for the solves
-    invert_diag32<T>(w.Wf, w.ldW, m, w.DinvW, h->sc.status, s);
-    invert_diag32<T>(w.Ct, w.ldCt, w.L, w.DinvC, h->sc.status, s);   // T~_L, the block that is solved
+    inv_diag<T>(w.Wf, w.ldW, m, w.DinvW, h->sc.status, s);
+    inv_diag<T>(w.Ct, w.ldCt, w.L, w.DinvC, h->sc.status, s);   // T~_L, the block that is solved
     if (sizeof(T) == 4) join_side(h, s);
     return cuda_check(h, "gls_factor");
 }
@@ -499,11 +522,11 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
     vzero(w.tg, sizeof(T) * p, s);
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
-    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC));
     // R x = c1 - T12 s2,  P_m (T12 s2) = T~_12^T s~2
     RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 1, T(1), w.tg, T(0), w.tt, 0, 0, s));
     vcomb<T>(w.tt2, m, w.tu, 0, T(1), w.tt, 1, T(-1), s);
-    RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s, w.DinvW));
+    RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s, w.DinvW));
     vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s, g + 1);
     // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
@@ -526,7 +549,7 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // T~_L h~2 = w~[0:L]
     vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
-    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s, w.DinvC));
     // z' = Q [0_m; P_L h~2]
     vzero(w.tt, sizeof(T) * n, s);
     vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
@@ -555,17 +578,17 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // step 3: R^T h1 = f3'   (th[0:m] = h1)
     vcopy<double, T>(f3, w.th, m, c3, 0, s);
-    RC(trsv_upper<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s, w.DinvW));
+    RC(tsolve<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s, w.DinvW));
     // h~1 = P_m h1 (tt)
     vcomb<T>(w.tt, m, w.th, 1, T(1), nullptr, 0, T(0), s);
     // step 4: T22 g2 = u2  <=>  T~_L^T g~2 = P_L u2   (tg[0:L] = g~2)
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
-    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC));
     // step 5: T22^T h2 = w2 - g2 - T12^T h1  <=>  T~_L h~2 = w~2 - g~2 - T~_12 h~1
     RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 0, T(1), w.tt, T(0), w.tt2, 0, 0, s));
     vcomb<T>(w.th + m, L, w.tw, 0, T(1), w.tg, 0, T(-1), s);
     vcomb<T>(w.th + m, L, w.th + m, 0, T(1), w.tt2, 0, T(-1), s);
-    RC(trsv_upper<T>(w.Ct, w.ldCt, L, 0, w.th + m, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 0, w.th + m, h->sc, s, w.DinvC));
     // step 6: g1 = w1 - T11^T h1  <=>  g~1 = w~1 - T~_22 h~1   (tg[L:p])
     if (o > 0) {
         vcomb<T>(w.tg + L, o, w.tw + L, 0, T(1), nullptr, 0, T(0), s);
@@ -576,7 +599,7 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 1, T(1), w.tg, T(0), w.tt2, 0, 0, s));
     if (o > 0) RC(gemv<T>(w.Ct + idx2(L, L, w.ldCt), w.ldCt, o, m, 1, T(1), w.tg + L, T(1), w.tt2, 1, 0, s));
     vcomb<T>(w.tt, m, w.tu, 0, T(1), w.tt2, 1, T(-1), s);
-    RC(trsv_upper<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s, w.DinvW));
+    RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s, w.DinvW));
     vaxpy<T>(w.tt, dx, m, sW / sV / gamma, 0, s);
     // step 7: dy = Z^T g = P_p Z~ g~
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
@@ -667,7 +690,7 @@ size_t bd_bytes(int N, int R, int mx)
     size_t b = gmres_ws_bytes(N, R);
     const size_t vn = ((size_t)N * sizeof(double) + 255) & ~(size_t)255;
     const size_t vm = ((size_t)std::max(mx, 1) * sizeof(double) + 255) & ~(size_t)255;
-    const size_t vd = (size_t)std::max(ceil_div(mx, 32), 1) * 1024 * sizeof(double);
+    const size_t vd = dinv_elems(mx) * sizeof(double);
     return b + 4 * vn + 3 * vm + 2 * vd;
 }
 
@@ -679,17 +702,34 @@ BDScratch bd_layout(void *base, int N, int R, int mx)
     b.rhs = c.take<double>(N); b.t = c.take<double>(N); b.u = c.take<double>(N); b.gf = c.take<double>(N);
     b.w1 = c.take<double>(std::max(mx, 1)); b.w2 = c.take<double>(std::max(mx, 1));
     b.w3 = c.take<double>(std::max(mx, 1));
-    b.dT = c.take<double>((size_t)std::max(ceil_div(mx, 32), 1) * 1024);
-    b.dR = c.take<double>((size_t)std::max(ceil_div(mx, 32), 1) * 1024);
+    b.dT = c.take<double>(dinv_elems(mx));
+    b.dR = c.take<double>(dinv_elems(mx));
     return b;
 }
 
 // Triangular solve and gemv in FP64 arithmetic on factors stored as T.
+// FP32 factors of order <= 8192 use 64-row diagonal blocks (inverses from
+// inv_diag_d), others 32-row blocks.
 template <typename T>
 int trsv_d(const T *U, int ldu, int n, int trans, double *x, const DevScratch &sc, cudaStream_t s,
            const double *Dinv)
 {
+    if constexpr (sizeof(T) == 4) {
+        if (trsv64_ok(n, sizeof(T))) {
+            const int rc = trsv64<double>(U, ldu, n, trans, x, Dinv, s);
+            if (rc >= 0) return rc;
+            return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s, nullptr);
+        }
+    }
     return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s, Dinv);
+}
+template <typename T>
+void inv_diag_d(const T *U, int ldu, int N, double *Dinv, int *status, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (trsv64_ok(N, sizeof(T))) { invert_diag64<T, double>(U, ldu, N, Dinv, status, s); return; }
+    }
+    invert_diag32_mixed<T, double>(U, ldu, N, Dinv, status, s);
 }
 template <typename T>
 int gemv_d(const T *M, int ld, int rows, int cols, int trans, double alpha, const double *x, double beta, double *y,
@@ -731,8 +771,8 @@ struct GlsBDOp : LinOp {
     // FP64 inverses of the diagonal blocks of T~_n and R
     void prepare()
     {
-        invert_diag32_mixed<T, double>(w.Ct, w.ldCt, w.n, b.dT, h->sc.status, h->stream);
-        invert_diag32_mixed<T, double>(w.Wf, w.ldW, w.m, b.dR, h->sc.status, h->stream);
+        inv_diag_d<T>(w.Ct, w.ldCt, w.n, b.dT, h->sc.status, h->stream);
+        inv_diag_d<T>(w.Wf, w.ldW, w.m, b.dR, h->sc.status, h->stream);
     }
 
     int Mr(const double *t, double *u)
@@ -966,8 +1006,8 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     mconvert<T, T>(w.X, w.ldX, w.At, w.ldAt, m, n, 1, 0, 1, 1.0, s);
     RC(geqrf<T>(w.At, w.ldAt, m, n, w.tauA, w.TwA, w.Tw128A, gp, w.gws, h->sc.err, s, tfjob(h, w.TfA, w.ldtA, w.gws2)));
     // inverses of the 32 x 32 diagonal blocks of R~ and T for the solves
-    invert_diag32<T>(w.Bt, w.ldBt, p, w.DinvB, h->sc.status, s);
-    invert_diag32<T>(w.At, w.ldAt, w.q, w.DinvA, h->sc.status, s);   // T11, the block that is solved
+    inv_diag<T>(w.Bt, w.ldBt, p, w.DinvB, h->sc.status, s);
+    inv_diag<T>(w.At, w.ldAt, w.q, w.DinvA, h->sc.status, s);   // T11, the block that is solved
     if (sizeof(T) == 4) join_side(h, s);
     return cuda_check(h, "lse_factor");
 }
@@ -988,12 +1028,12 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 1, w.tw, h->sc, s));
     // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
     vcopy<double, T>(d, w.tb, p, fs.s2, 1, s, g);
-    RC(trsv_upper<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
+    RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
     // ty = [y1; y2], y2 = P_p y~2
     vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     vcomb<T>(w.ty, q, w.tw, 0, T(1), nullptr, 0, T(0), s);
     RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
-    RC(trsv_upper<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
+    RC(tsolve<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
     // x = Q^T y = P_n Q~ P_n y
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, w.tt, h->sc, s));
@@ -1020,7 +1060,7 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s, g);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, w.tu, h->sc, s));
     // R~ (P_p v') = u~[0:p]
-    RC(trsv_upper<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s, w.DinvB));
+    RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s, w.DinvB));
     vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s, g + 1);
     return cuda_check(h, "lse_multipliers");
 }
@@ -1045,17 +1085,17 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
     if (p > 0) {
         vcopy<double, T>(f2, w.tb, p, c2, 1, s);
-        RC(trsv_upper<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
+        RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
         vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     }
     // step 4: T11^T q1 = u1
     if (q > 0) {
         vcomb<T>(w.tq, q, w.tu + p, 1, T(1), nullptr, 0, T(0), s);
-        RC(trsv_upper<T>(w.At, w.ldAt, q, 1, w.tq, h->sc, s, w.DinvA));
+        RC(tsolve<T>(w.At, w.ldAt, q, 1, w.tq, h->sc, s, w.DinvA));
         // step 5: T11 y1 = w1 - q1 - T12 y2
         vcomb<T>(w.ty, q, w.tw, 0, T(1), w.tq, 0, T(-1), s);
         if (p > 0) RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
-        RC(trsv_upper<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
+        RC(tsolve<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
     }
     // step 6: q2 = w2 - T22 y2
     if (m - q > 0) {
@@ -1068,7 +1108,7 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
         if (q > 0) RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 1, T(1), w.tq, T(0), w.tt, 0, 0, s));
         if (m - q > 0) RC(gemv<T>(w.At + idx2(q, q, w.ldAt), w.ldAt, m - q, p, 1, T(1), w.tq + q, T(1), w.tt, 1, 0, s));
         vcomb<T>(w.tb, p, w.tt, 1, T(1), w.tu, 0, T(-1), s);
-        RC(trsv_upper<T>(w.Bt, w.ldBt, p, 0, w.tb, h->sc, s, w.DinvB));
+        RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tb, h->sc, s, w.DinvB));
         vaxpy<T>(w.tb, dv, p, sB / sA / gamma, 1, s);
     }
     // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
@@ -1123,8 +1163,8 @@ struct LseBDOp : LinOp {
     // FP64 inverses of the diagonal blocks of T1 and R~
     void prepare()
     {
-        invert_diag32_mixed<T, double>(w.At, w.ldAt, w.n, b.dT, h->sc.status, h->stream);
-        invert_diag32_mixed<T, double>(w.Bt, w.ldBt, w.p, b.dR, h->sc.status, h->stream);
+        inv_diag_d<T>(w.At, w.ldAt, w.n, b.dT, h->sc.status, h->stream);
+        inv_diag_d<T>(w.Bt, w.ldBt, w.p, b.dR, h->sc.status, h->stream);
     }
 
     int Mr(const double *t, double *u)

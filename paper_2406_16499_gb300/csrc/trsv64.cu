@@ -1,0 +1,238 @@
+// trsv64.cu -- the triangular solves of the correction solve (Alg. 3 / 4:
+// R, T22 and their transposes) for FP32-stored factors of order <= 8192,
+// in 64-row diagonal blocks whose inverses are formed once per
+// factorization.
+//
+// One thread-block cluster; CTA r owns rows [r*slice, (r+1)*slice) of x
+// (slice a multiple of 64, at most 512: one row per thread).  Per diagonal
+// block (from the bottom for U x = b, from the top for U^T x = b):
+//   1. every thread with an unsolved row loads its 64 entries of the block
+//      column of U (independent of x, in flight during the rest of the step);
+//      the CTA owning the next block loads that block's inverse;
+//   2. the owner forms x_blk = op(D) b_blk (two warps, D staged in shared
+//      memory one step earlier) and writes x_blk into every CTA's shared
+//      memory through distributed shared memory;
+//   3. one cluster barrier (release / acquire) makes x_blk visible;
+//   4. every thread subtracts its row's 64-term product.
+// One cluster barrier per 64 rows; no dependent global-memory read on the
+// critical path.
+#include "common.cuh"
+#include "kernels.h"
+#include "mpir.h"
+
+namespace mpir {
+
+constexpr int T64_THREADS = 512;
+constexpr int T64_MAXN = 16 * T64_THREADS;
+constexpr int T64_DS = 64 * 65;                  // one staged inverse, rows padded
+
+bool trsv64_ok(int n, size_t ts_bytes) { return ts_bytes == 4 && n > 0 && n <= T64_MAXN; }
+
+size_t dinv_elems(int N)
+{
+    const size_t a = (size_t)(ceil_div(N > 0 ? N : 1, 32)) * 1024;
+    const size_t b = (size_t)(ceil_div(N > 0 ? N : 1, 64)) * 4096;
+    return a > b ? a : b;
+}
+
+// Inverses of the 64 x 64 diagonal blocks of an upper triangular N x N U
+// (one CTA of 64 threads per block, thread j solves column j by back
+// substitution; a partial last block is padded with the identity).  Zero
+// pivot -> bit 1 of *status.  Dinv block b at Dinv + 4096 b, column-major.
+template <typename TS, typename T>
+__global__ void __launch_bounds__(64)
+k_invert_diag64(const TS *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, int *__restrict__ status)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Us = reinterpret_cast<T *>(smem_raw);     // [64][65]
+    T *Xs = Us + T64_DS;                         // [64][65]
+    const int j = threadIdx.x, blk = blockIdx.x, r0 = blk * 64;
+    for (int c = 0; c < 64; c++) {
+        T v;
+        if (r0 + j < N && r0 + c < N) v = j <= c ? (T)U[idx2(r0 + j, r0 + c, ldu)] : T(0);
+        else v = j == c ? T(1) : T(0);
+        Us[j * 65 + c] = v;
+    }
+    __syncthreads();
+    for (int i = 63; i >= 0; i--) {
+        T val = T(0);
+        if (i <= j) {
+            T sum = i == j ? T(1) : T(0);
+            for (int k = i + 1; k <= j; k++) sum = fma(-Us[i * 65 + k], Xs[k * 65 + j], sum);
+            const T d = Us[i * 65 + i];
+            if (d == T(0)) atomicOr(status, 2);
+            val = sum / d;
+        }
+        Xs[i * 65 + j] = val;
+    }
+    __syncthreads();
+    for (int i = 0; i < 64; i++) Dinv[(size_t)blk * 4096 + i + 64 * j] = Xs[i * 65 + j];
+}
+
+template <typename TS, typename T>
+void invert_diag64(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
+{
+    if (N <= 0) return;
+    const size_t smem = 2 * T64_DS * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_invert_diag64<TS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    ProfScope ps(K_TRSV, s);
+    k_invert_diag64<TS, T><<<ceil_div(N, 64), 64, smem, s>>>(U, ldu, N, Dinv, status);
+}
+
+template <typename T>
+__device__ __forceinline__ void t64_load_d(const T *__restrict__ Dinv, int blk, int tid, T (&d)[8])
+{
+    const T *D = Dinv + (size_t)blk * 4096;
+#pragma unroll
+    for (int u = 0; u < 8; u++) d[u] = D[tid + u * T64_THREADS];
+}
+
+// Stage op(D) row-major (padded): Ds[r * 65 + c] = op(D)(r, c), op = D or D^T.
+template <typename T>
+__device__ __forceinline__ void t64_store_d(T *Ds, int trans, int tid, const T (&d)[8])
+{
+#pragma unroll
+    for (int u = 0; u < 8; u++) {
+        const int e = tid + u * T64_THREADS;     // D(r, c) at r + 64 c
+        const int r = e & 63, c = e >> 6;
+        if (trans) Ds[c * 65 + r] = d[u]; else Ds[r * 65 + c] = d[u];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(T64_THREADS, 1)
+k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
+         const T *__restrict__ Dinv)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *xs = reinterpret_cast<T *>(smem_raw);                 // slice
+    T *Ds = xs + slice;                                      // [2][64 * 65]
+    __shared__ T xin[2][64];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x;
+    const int s0 = crank * slice;
+    const int s1 = min(s0 + slice, n);
+    const int i = s0 + tid;                                  // this thread's row
+    for (int r = s0 + tid; r < s1; r += T64_THREADS) xs[r - s0] = x[r];
+    const int nblk = ceil_div(n, 64);
+    {
+        const int b0 = trans ? 0 : nblk - 1;
+        if (crank == (b0 * 64) / slice) {
+            T d[8];
+            t64_load_d(Dinv, b0, tid, d);
+            t64_store_d(Ds, trans, tid, d);
+        }
+    }
+    __syncthreads();
+    for (int t = 0; t < nblk; t++) {
+        const int blk = trans ? t : nblk - 1 - t;
+        const int r0 = blk * 64;
+        const int bs = min(64, n - r0);
+        const int par = t & 1;
+        const int owner = r0 / slice;
+        // 1. this row's entries of the block column (rows still unsolved)
+        const int lo = trans ? max(s0, r0 + bs) : s0;
+        const int hi = trans ? s1 : min(s1, r0);
+        const bool va = i >= lo && i < hi;
+        float u[64];
+        if (trans) {
+            // U(r0 + c, i): 64 consecutive entries of column i (16-byte aligned
+            // when bs = 64: r0, ldu multiples of 4)
+            const float *col = U + (size_t)i * ldu + r0;
+            if (va && bs == 64) {
+#pragma unroll
+                for (int q = 0; q < 16; q++) {
+                    const float4 v = *reinterpret_cast<const float4 *>(col + 4 * q);
+                    u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < 64; c++) u[c] = (va && c < bs) ? col[c] : 0.f;
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < 64; c++) u[c] = (va && c < bs) ? U[idx2(i, r0 + c, ldu)] : 0.f;
+        }
+        // next block's inverse, loaded by its owner
+        const int nb = t + 1 < nblk ? (trans ? t + 1 : nblk - 2 - t) : -1;
+        const bool stage = nb >= 0 && crank == (nb * 64) / slice;
+        T dn[8];
+        if (stage) t64_load_d(Dinv, nb, tid, dn);
+        // 2. the owner forms x_blk and publishes it to every CTA
+        if (crank == owner && tid < 64) {
+            const T *Dr = Ds + par * T64_DS + tid * 65;
+            T acc = T(0);
+#pragma unroll 16
+            for (int k = 0; k < 64; k++) acc = fma(Dr[k], k < bs ? xs[r0 + k - s0] : T(0), acc);
+            const T xv = tid < bs ? acc : T(0);
+            for (int r = 0; r < cs; r++) *cluster.map_shared_rank(&xin[par][tid], r) = xv;
+        }
+        // 3. x_blk visible everywhere
+        cluster.sync();
+        // 4. update the unsolved rows; the owner stores its block
+        if (va) {
+            T dsum = T(0);
+#pragma unroll
+            for (int c = 0; c < 64; c++) dsum = fma((T)u[c], xin[par][c], dsum);
+            xs[i - s0] -= dsum;
+        }
+        if (crank == owner && tid < bs) xs[r0 + tid - s0] = xin[par][tid];
+        if (stage) t64_store_d(Ds + (par ^ 1) * T64_DS, trans, tid, dn);
+        __syncthreads();
+    }
+    for (int r = s0 + tid; r < s1; r += T64_THREADS) x[r] = xs[r - s0];
+    cluster.sync();   // no CTA leaves while others may still write into it
+}
+
+template <typename T>
+int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaStream_t s)
+{
+    if (n <= 0) return 0;
+    if (n > T64_MAXN || ldu % 4 || ((uintptr_t)U & 15)) return -1;
+    auto kern = k_trsv64<T>;
+    const int nblk = ceil_div(n, 64);
+    int want = ceil_div(nblk, 4);                          // 256 rows per CTA
+    if (want > 16) want = 16;
+    const size_t dsz = 2 * T64_DS * sizeof(T);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(dsz + T64_THREADS * sizeof(T)));
+        attr = true;
+    }
+    int cs = cluster_size_for((const void *)kern, T64_THREADS, dsz + (size_t)ceil_div(nblk, want) * 64 * sizeof(T),
+                              want);
+    const int slice = ceil_div(nblk, cs) * 64;
+    if (slice > T64_THREADS) return -1;
+    cs = ceil_div(n, slice);
+    const size_t smem = dsz + (size_t)slice * sizeof(T);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(T64_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    ProfScope ps(K_TRSV, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+template void invert_diag64<float, float>(const float *, int, int, float *, int *, cudaStream_t);
+template void invert_diag64<float, double>(const float *, int, int, double *, int *, cudaStream_t);
+template int trsv64<float>(const float *, int, int, int, float *, const float *, cudaStream_t);
+template int trsv64<double>(const float *, int, int, int, double *, const double *, cudaStream_t);
+
+} // namespace mpir
