@@ -35,10 +35,52 @@ constexpr int PANEL_MAX_CLUSTER = 16;
 //     Tw^{-1} = triu(V^T V, 1) + diag(1 / tau)
 // by one back substitution per column (lane k solves column k).
 // ---------------------------------------------------------------------------
+// Cluster message passing of the panel: every CTA pushes its column message
+// into every CTA's shared memory with st.async, which signals the
+// receiver's mbarrier (complete_tx); the receiver announces the bytes it
+// expects one column ahead, so no message can arrive before its count.
+constexpr uint32_t PANEL_WAIT_LIMIT = 1u << 22;
+
+__device__ __forceinline__ uint32_t pq_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t pq_mapa(uint32_t addr, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void pq_st_async(uint32_t raddr, float4 v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(raddr), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ void pq_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait on the phase of parity `parity`; false on timeout.
+__device__ __forceinline__ bool pq_wait(uint32_t bar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < PANEL_WAIT_LIMIT; it++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <typename T, int NB, int NT, int RPT>
 __global__ void __launch_bounds__(NT, 1)
 k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
-           T *__restrict__ tau, T *__restrict__ Tw)
+           T *__restrict__ tau, T *__restrict__ Tw, int *__restrict__ err)
 {
     constexpr int NW = NT / 32;
     cg::cluster_group cluster = cg::this_cluster();
@@ -48,11 +90,16 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     const int L = M - j0;
     const int kpanel = min(ncols, L);
 
+    // column message of a CTA: its partial sums (NB) and its part of the
+    // pivot row (NB; nonzero on rank 0 only), 16-byte vectors
+    constexpr int MSG = 2 * NB;
+    constexpr int NV = MSG * (int)sizeof(T) / 16;
+    static_assert(MSG * sizeof(T) % 16 == 0, "message of whole 16-byte vectors");
     __shared__ T red_s[2][NW][32];
-    __shared__ T xbuf[2][32];
-    __shared__ T gbuf[2][16][32];
+    __shared__ __align__(16) T xbuf[2][MSG];
+    __shared__ __align__(16) T gbuf[2][16][MSG];
+    __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ T prow[2][NB];
-    __shared__ T prow_l[2][NB];
     __shared__ T coefw[NW][NB];
     __shared__ T G_s[NB][NB + 1];
     __shared__ T tau_s[NB];
@@ -60,6 +107,17 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
 
     const int row_base = crank * chunk;
     const int row_end = min(row_base + chunk, L);
+    const uint32_t msg_bytes = (uint32_t)(cs * MSG * sizeof(T));
+    bool timed_out = false;
+    if (cs > 1) {
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[0])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[1])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            pq_expect_tx(pq_smem(&mbar[0]), msg_bytes);        // column 0
+        }
+        cluster.sync();                                         // barriers ready before any message
+    }
     int rr[RPT];
     T a[RPT][NB];
 #pragma unroll
@@ -113,6 +171,9 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                 for (int c = 0; c < NB; c++) prow[par][c] = a[q][c];
             }
         }
+        // the next column's message count is announced before this column's
+        // messages leave (no CTA can send column kk+1 before it has ours)
+        if (cs > 1 && tid == 0 && kk + 1 < kpanel) pq_expect_tx(pq_smem(&mbar[par ^ 1]), msg_bytes);
         __syncthreads();
         // every warp forms the column totals and the coefficients itself
         T tot = T(0), pj = T(0);
@@ -123,19 +184,31 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                 pj = prow[par][lane];
             }
         } else {
-            if (warp == 0 && lane < NB) {
-                T t = T(0);
+            if (warp == 0) {
+                if (lane < NB) {
+                    T t = T(0);
 #pragma unroll
-                for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
-                xbuf[par][lane] = t;
+                    for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
+                    xbuf[par][lane] = t;
+                    xbuf[par][NB + lane] = crank == 0 ? prow[par][lane] : T(0);
+                }
+                __syncwarp();
+                const uint32_t src = pq_smem(&gbuf[par][crank][0]);
+                const uint32_t bar = pq_smem(&mbar[par]);
+                for (int e = lane; e < cs * NV; e += 32) {
+                    const int r = e / NV, q = e % NV;
+                    const float4 v = reinterpret_cast<const float4 *>(&xbuf[par][0])[q];
+                    pq_st_async(pq_mapa(src + 16 * q, r), v, pq_mapa(bar, r));
+                }
             }
-            cluster.sync();
-            for (int r = warp; r < cs && lane < NB; r += NW) gbuf[par][r][lane] = *cluster.map_shared_rank(&xbuf[par][lane], r);
-            if (warp == NW - 1 && lane < NB) prow_l[par][lane] = *cluster.map_shared_rank(&prow[par][lane], 0);
-            __syncthreads();
+            // after a timeout the remaining columns skip their waits (the
+            // error flag reports the panel; the kernel still ends promptly)
+            if (!timed_out && !pq_wait(pq_smem(&mbar[par]), (uint32_t)(kk >> 1) & 1u)) timed_out = true;
             if (lane < NB) {
-                for (int r = 0; r < cs; r++) tot += gbuf[par][r][lane];
-                pj = prow_l[par][lane];
+                for (int r = 0; r < cs; r++) {
+                    tot += gbuf[par][r][lane];
+                    pj += gbuf[par][r][NB + lane];
+                }
             }
         }
         const T alpha = __shfl_sync(0xffffffffu, pj, kk);
@@ -209,7 +282,8 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
             for (int i = 0; i < NB; i++) Tw[i + (size_t)k * NB] = T_s[i][k];
         }
     }
-    if (cs > 1) cluster.sync();   // keep shared memory alive for remote readers
+    if (timed_out) atomicOr(err, 8);
+    if (cs > 1) cluster.sync();   // no CTA leaves while messages to it may be in flight
 }
 
 // ---------------------------------------------------------------------------
@@ -667,7 +741,7 @@ k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, f
 // ------------------------------------------------------------------ host --
 
 template <typename T, int NT, int RPT>
-static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, cudaStream_t s)
+static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, int *err, cudaStream_t s)
 {
     constexpr int NB = panel_nb<T>();
     const int L = M - j0;
@@ -694,7 +768,7 @@ static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     ProfScope ps(K_PANEL, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw, err);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
@@ -702,15 +776,15 @@ static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T
 // column steps are latency and issue bound, so fewer rows per SM (more SMs)
 // shorten every step.
 template <typename T>
-static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, cudaStream_t s)
+static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, int *err, cudaStream_t s)
 {
     const int L = M - j0;
     if constexpr (sizeof(T) == 4) {
-        if (L <= 16 * 128) return launch_panel_shape<T, 128, 1>(A, lda, M, j0, ncols, tau, Tw, s);
-        if (L <= 16 * 256) return launch_panel_shape<T, 256, 1>(A, lda, M, j0, ncols, tau, Tw, s);
-        if (L <= 16 * 512) return launch_panel_shape<T, 512, 1>(A, lda, M, j0, ncols, tau, Tw, s);
+        if (L <= 16 * 128) return launch_panel_shape<T, 128, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        if (L <= 16 * 256) return launch_panel_shape<T, 256, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        if (L <= 16 * 512) return launch_panel_shape<T, 512, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
     }
-    return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, s);
+    return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, s);
 }
 
 // Inner update with the CTA's whole row chunk of V and C staged in shared
@@ -1186,7 +1260,7 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
 }
 
 template <typename T>
-static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, cudaStream_t s)
+static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cudaStream_t s)
 {
     constexpr int NB = panel_nb<T>();
     const int k = M < N ? M : N;
@@ -1194,7 +1268,7 @@ static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, cudaStream_t s
         const int ncols = N - j0 < NB ? N - j0 : NB;
         const int L = M - j0;
         T *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
-        int rc = launch_panel<T>(A, lda, M, j0, ncols, tau, Twb, s);
+        int rc = launch_panel<T>(A, lda, M, j0, ncols, tau, Twb, err, s);
         if (rc) return rc;
         const int kb = ncols < L ? ncols : L;
         const int Nc = N - j0 - ncols;
@@ -1208,10 +1282,10 @@ static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, cudaStream_t s
 }
 
 template <>
-int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *, int *,
+int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *, int *err,
                   cudaStream_t s, const TfullJob *)
 {
-    return geqrf_simt<double>(A, lda, M, N, tau, Tw, s);
+    return geqrf_simt<double>(A, lda, M, N, tau, Tw, err, s);
 }
 
 // Two-level QR, FP32 storage: 32-wide register panels inside 128-wide
@@ -1244,7 +1318,7 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
             const int ncols = J0 + ncolsO - j0 < NB ? J0 + ncolsO - j0 : NB;
             const int Li = M - j0;
             float *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
-            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, s);
+            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, err, s);
             if (rc) return rc;
             const int kb = ncols < Li ? ncols : Li;
             const int nc = J0 + ncolsO - j0 - ncols;

@@ -381,6 +381,7 @@ int check_dev_flags(mpir_ctx *h)
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return cuda_check(h, "sync");
     if (flags[0] & DEV_ERR_BARRIER_TIMEOUT) return set_err(h, MPIR_DEVICE_TIMEOUT, "device barrier timed out");
     if (flags[0] & 4) return set_err(h, MPIR_DEVICE_TIMEOUT, "tensor-core pipeline wait timed out");
+    if (flags[0] & 8) return set_err(h, MPIR_DEVICE_TIMEOUT, "panel message wait timed out");
     if (flags[1] & 1) return set_err(h, MPIR_SINGULAR_R, "R has a zero diagonal entry");
     if (flags[1] & 2) return set_err(h, MPIR_SINGULAR_T, "triangular factor has a zero diagonal entry");
     return 0;
