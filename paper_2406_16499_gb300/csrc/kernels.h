@@ -55,13 +55,23 @@ struct DevScratch {          // small device scratch owned by the handle
 // tf->ws2 of geqrf_ws_bytes(M, N)): the caller makes s wait for the side
 // stream before it reads Tf or reuses the scratch.
 // Returns 0, or MPIR_UNSUPPORTED / MPIR_CUDA_ERROR.
+//
+// Look-ahead (FP32 storage, tf->crit set and ws of geqrf_la_ws_bytes): the
+// panels, the inner updates and the update of the next outer block's
+// columns run on tf->crit (a high-priority stream forked from s); the rest
+// of each trailing update runs on s, overlapped with the next block's
+// panels (events tf->la_a / tf->la_b order the two).  geqrf returns with s
+// joined to tf->crit.
 struct TfullJob {
     float *Tf;
     int ldt;
     cudaStream_t side;
     cudaEvent_t fork, join;
     void *ws2;
+    cudaStream_t crit;
+    cudaEvent_t la_a, la_b;
 };
+size_t geqrf_la_ws_bytes(int M, int N);
 size_t geqrf_ws_bytes(int M, int N);
 template <typename T>
 int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, T *Tw128, GemmPrec prec, void *ws, int *err,

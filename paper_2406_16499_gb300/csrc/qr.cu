@@ -1009,6 +1009,9 @@ size_t geqrf_ws_bytes(int M, int N)
     return b;
 }
 
+// two block-parity copies for the critical path + one for the wide updates
+size_t geqrf_la_ws_bytes(int M, int N) { return 3 * geqrf_ws_bytes(M, N); }
+
 static int tc_mode(GemmPrec p) { return p == GemmPrec::FP32 ? TCM_TF32X3 : TCM_TF32; }
 
 // Prepares V (and splits) for the outer block whose panel sits at X (ldx),
@@ -1298,19 +1301,28 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
     constexpr int NB = 32;
     const int k = M < N ? M : N;
     if (lda % 4) return MPIR_UNSUPPORTED;
-    OuterWs w = outer_layout(ws, M, N, nullptr);
     const int mode = tc_mode(prec);
+    // look-ahead: critical path on tf->crit, wide trailing updates on s
+    const bool la = tf && tf->crit && tf->crit != s && tf->la_a && tf->la_b;
+    const size_t one = geqrf_ws_bytes(M, N);
+    OuterWs wv[2] = {outer_layout(ws, M, N, nullptr),
+                     outer_layout(la ? (char *)ws + one : ws, M, N, nullptr)};
+    OuterWs wu = la ? outer_layout((char *)ws + 2 * one, M, N, nullptr) : wv[0];
+    cudaStream_t cs = la ? tf->crit : s;
+    if (la) { cudaEventRecord(tf->la_a, s); cudaStreamWaitEvent(cs, tf->la_a, 0); }
     // the aggregated factor is built on the side stream when there is one,
     // from its own prepared copy of each finished outer block
-    const bool side = tf && tf->side && tf->side != s && tf->ws2;
-    cudaStream_t ss = side ? tf->side : s;
-    OuterWs w2 = side ? outer_layout(tf->ws2, M, N, nullptr) : w;
-    if (tf) {
+    const bool side = tf && tf->side && tf->side != s && tf->side != cs && tf->ws2;
+    cudaStream_t ss = side ? tf->side : cs;
+    OuterWs w2 = side ? outer_layout(tf->ws2, M, N, nullptr) : wv[0];
+    if (tf && tf->Tf) {
         if (tf->ldt < k || tf->ldt % 4 || ((uintptr_t)tf->Tf & 15)) return MPIR_UNSUPPORTED;
-        if (side) { cudaEventRecord(tf->fork, s); cudaStreamWaitEvent(ss, tf->fork, 0); }
+        if (side) { cudaEventRecord(tf->fork, cs); cudaStreamWaitEvent(ss, tf->fork, 0); }
         cudaMemsetAsync(tf->Tf, 0, (size_t)tf->ldt * k * sizeof(float), ss);
     }
-    for (int J0 = 0; J0 < k; J0 += OUTER_NB) {
+    bool wide_pending = false;
+    for (int J0 = 0, b = 0; J0 < k; J0 += OUTER_NB, b++) {
+        OuterWs &w = wv[b & 1];
         const int ncolsO = N - J0 < OUTER_NB ? N - J0 : OUTER_NB;
         const int L = M - J0;
         const int nr = ncolsO < L ? ncolsO : L;
@@ -1318,34 +1330,53 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
             const int ncols = J0 + ncolsO - j0 < NB ? J0 + ncolsO - j0 : NB;
             const int Li = M - j0;
             float *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
-            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, err, s);
+            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, err, cs);
             if (rc) return rc;
             const int kb = ncols < Li ? ncols : Li;
             const int nc = J0 + ncolsO - j0 - ncols;
             if (nc > 0) {
                 rc = inner_update<float>(A + idx2(j0, j0, lda), lda, Twb, kb, Li, A + idx2(j0, j0 + ncols, lda), lda,
-                                         nc, w.innerP, w.innerW, s);
+                                         nc, w.innerP, w.innerW, cs);
                 if (rc) return rc;
             }
         }
         const int Nc = N - J0 - ncolsO;
         float *Tb = Tw128 + (size_t)(J0 / OUTER_NB) * OUTER_NB * OUTER_NB;
-        prep_v(A + idx2(J0, J0, lda), lda, L, nr, w, mode == TCM_TF32X3, s);
-        int rc = outer_T(w, Tw + (size_t)(J0 / NB) * NB * NB, L, nr, Tb, mode, err, s);
+        prep_v(A + idx2(J0, J0, lda), lda, L, nr, w, mode == TCM_TF32X3, cs);
+        int rc = outer_T(w, Tw + (size_t)(J0 / NB) * NB * NB, L, nr, Tb, mode, err, cs);
         if (rc) return rc;
-        if (tf) {
+        if (tf && tf->Tf) {
             if (side) {
-                cudaEventRecord(tf->fork, s);
+                cudaEventRecord(tf->fork, cs);
                 cudaStreamWaitEvent(ss, tf->fork, 0);
                 prep_v(A + idx2(J0, J0, lda), lda, L, nr, w2, mode == TCM_TF32X3, ss);
             }
-            rc = tfull_block(w2, A, lda, M, J0, nr, Tb, tf->Tf, tf->ldt, mode, err, ss);
+            rc = tfull_block(side ? w2 : w, A, lda, M, J0, nr, Tb, tf->Tf, tf->ldt, mode, err, ss);
             if (rc) return rc;
         }
         if (Nc > 0) {
-            rc = outer_apply(w, Tb, 1, L, A + idx2(J0, J0 + ncolsO, lda), lda, Nc, mode, err, s);
+            // the next block's columns first (critical path), after the
+            // previous wide update has finished with them
+            const int n1 = la ? (Nc < OUTER_NB ? Nc : OUTER_NB) : Nc;
+            if (wide_pending) { cudaStreamWaitEvent(cs, tf->la_b, 0); wide_pending = false; }
+            rc = outer_apply(w, Tb, 1, L, A + idx2(J0, J0 + ncolsO, lda), lda, n1, mode, err, cs);
             if (rc) return rc;
+            if (la && Nc > n1) {
+                cudaEventRecord(tf->la_a, cs);
+                cudaStreamWaitEvent(s, tf->la_a, 0);
+                OuterWs wt = wu;
+                wt.V = w.V; wt.Vl = w.Vl; wt.Vt = w.Vt; wt.Vtl = w.Vtl; wt.ldv = w.ldv;
+                rc = outer_apply(wt, Tb, 1, L, A + idx2(J0, J0 + ncolsO + n1, lda), lda, Nc - n1, mode, err, s);
+                if (rc) return rc;
+                cudaEventRecord(tf->la_b, s);
+                wide_pending = true;
+            }
         }
+    }
+    if (la) {
+        if (wide_pending) cudaStreamWaitEvent(cs, tf->la_b, 0);
+        cudaEventRecord(tf->la_a, cs);
+        cudaStreamWaitEvent(s, tf->la_a, 0);
     }
     return 0;
 }

@@ -147,8 +147,12 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
     w.Tw128A = c.take<T>((size_t)std::max(ceil_div(w.kA, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
     w.DinvB = c.take<T>(dinv_elems(p));
     w.DinvA = c.take<T>(dinv_elems(w.kA));
-    w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
-                                           geqrf_ws_bytes(m, n)));
+    if (sizeof(T) == 4)   // look-ahead factorizations of B~ and A Q^T, the apply to A
+        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_la_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
+                                               geqrf_la_ws_bytes(m, n)));
+    else
+        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
+                                               geqrf_ws_bytes(m, n)));
     w.ldtB = rup32(std::max(p, 1)); w.ldtA = rup32(std::max(w.kA, 1));
     if (sizeof(T) == 4) {
         w.TfB = c.take<T>((size_t)w.ldtB * std::max(p, 1));
@@ -193,8 +197,12 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
     w.Tw128C = c.take<T>((size_t)std::max(ceil_div(w.kC, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
     w.DinvW = c.take<T>(dinv_elems(m));
     w.DinvC = c.take<T>(dinv_elems(w.kC));
-    w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
-                                           geqrf_ws_bytes(p, n)));
+    if (sizeof(T) == 4)   // look-ahead factorizations of W and C~, the apply to V
+        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_la_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
+                                               geqrf_la_ws_bytes(p, n)));
+    else
+        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
+                                               geqrf_ws_bytes(p, n)));
     w.ldtW = rup32(std::max(m, 1)); w.ldtC = rup32(std::max(w.kC, 1));
     if (sizeof(T) == 4) {
         w.TfW = c.take<T>((size_t)w.ldtW * std::max(m, 1));
@@ -249,6 +257,8 @@ struct mpir_ctx {
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaStream_t side = nullptr;         // aggregated compact-WY factors, built beside the factorization
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
+    cudaStream_t crit = nullptr;         // high-priority stream of the factorization's critical path
+    cudaEvent_t la_a = nullptr, la_b = nullptr;
     TfullJob tfj{};
     // learned selector: parameters and feature standardization (device), scratch
     float *sel = nullptr;        // params[MLP_PARAMS], X[16], prob[6], feat[16]
@@ -279,21 +289,40 @@ const TfullJob *tfjob(mpir_ctx *h, T *Tf, int ldt, void *ws2)
             h->side = nullptr;
         }
     }
+    if (!h->crit) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&h->crit, cudaStreamNonBlocking, hi) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->la_a, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->la_b, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            h->crit = nullptr;
+        }
+    }
     h->tfj.Tf = reinterpret_cast<float *>(Tf);
     h->tfj.ldt = ldt;
     h->tfj.side = h->side;
     h->tfj.fork = h->side_fork;
     h->tfj.join = h->side_join;
     h->tfj.ws2 = ws2;
+    h->tfj.crit = h->crit;
+    h->tfj.la_a = h->la_a;
+    h->tfj.la_b = h->la_b;
     return &h->tfj;
 }
 
-// The stream waits for everything queued on the side stream so far.
+// The stream waits for everything queued on the side and critical-path
+// streams so far.
 void join_side(mpir_ctx *h, cudaStream_t s)
 {
-    if (!h->side) return;
-    cudaEventRecord(h->side_join, h->side);
-    cudaStreamWaitEvent(s, h->side_join, 0);
+    if (h->side) {
+        cudaEventRecord(h->side_join, h->side);
+        cudaStreamWaitEvent(s, h->side_join, 0);
+    }
+    if (h->crit) {
+        cudaEventRecord(h->la_a, h->crit);
+        cudaStreamWaitEvent(s, h->la_a, 0);
+    }
 }
 
 int cuda_check(mpir_ctx *h, const char *where)
@@ -313,6 +342,7 @@ int ensure_ws(mpir_ctx *h, size_t bytes)
     if (h->ws) {
         cudaStreamSynchronize(h->stream);
         if (h->side) cudaStreamSynchronize(h->side);
+        if (h->crit) cudaStreamSynchronize(h->crit);
         cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0;
     }
     if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "workspace cudaMalloc failed"); }
@@ -1453,6 +1483,7 @@ int mpir_destroy(mpir_handle h)
     if (!h) return -1;
     cudaStreamSynchronize(h->stream);
     if (h->side) cudaStreamSynchronize(h->side);
+    if (h->crit) cudaStreamSynchronize(h->crit);
     if (h->ws && h->ws_owned) cudaFree(h->ws);
     if (h->scratch_base) cudaFree(h->scratch_base);
     if (h->rws) cudaFree(h->rws);
@@ -1471,6 +1502,12 @@ int mpir_destroy(mpir_handle h)
         cudaStreamDestroy(h->side);
         cudaEventDestroy(h->side_fork);
         cudaEventDestroy(h->side_join);
+    }
+    if (h->crit) {
+        cudaStreamSynchronize(h->crit);
+        cudaStreamDestroy(h->crit);
+        cudaEventDestroy(h->la_a);
+        cudaEventDestroy(h->la_b);
     }
     if (h->sel) cudaFree(h->sel);
     if (h->sel_s) cudaFree(h->sel_s);
@@ -1491,6 +1528,7 @@ int mpir_set_workspace(mpir_handle h, void *ptr, size_t bytes)
     if (!h) return -1;
     if (((uintptr_t)ptr & 255) != 0) return -2;
     if (h->side) cudaStreamSynchronize(h->side);
+    if (h->crit) cudaStreamSynchronize(h->crit);
     if (h->ws && h->ws_owned) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); }
     h->ws = ptr;
     h->ws_bytes = ptr ? bytes : 0;
