@@ -77,6 +77,21 @@ __device__ __forceinline__ bool pq_wait(uint32_t bar, uint32_t parity)
     return false;
 }
 
+// v[k] for a warp-uniform k by a log-depth select tree (N a power of two):
+// N - 1 selects, dependency depth log2(N), compile-time register indices.
+template <typename T, int N>
+__device__ __forceinline__ T pq_select(const T (&v)[N], int k)
+{
+    T t[N];
+#pragma unroll
+    for (int c = 0; c < N; c++) t[c] = v[c];
+#pragma unroll
+    for (int w = 1; w < N; w *= 2)
+#pragma unroll
+        for (int c = 0; c < N; c += 2 * w) t[c] = (k & w) ? t[c + w] : t[c];
+    return t[0];
+}
+
 template <typename T, int NB, int NT, int RPT>
 __global__ void __launch_bounds__(NT, 1)
 k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
@@ -96,11 +111,11 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     constexpr int NV = MSG * (int)sizeof(T) / 16;
     static_assert(MSG * sizeof(T) % 16 == 0, "message of whole 16-byte vectors");
     __shared__ T red_s[2][NW][32];
-    __shared__ __align__(16) T xbuf[2][MSG];
+    __shared__ __align__(16) T xbuf[NW][MSG];               // each warp's copy of the message
     __shared__ __align__(16) T gbuf[2][16][MSG];
     __shared__ __align__(8) unsigned long long mbar[2];
     __shared__ T prow[2][NB];
-    __shared__ T coefw[NW][NB];
+    __shared__ __align__(16) T coefw[NW][NB];
     __shared__ T G_s[NB][NB + 1];
     __shared__ T tau_s[NB];
     __shared__ T T_s[NB][NB + 1];
@@ -138,15 +153,10 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
 #pragma unroll 1
     for (int kk = 0; kk < kpanel; kk++) {
         const int par = kk & 1;
-        // pivot-column value of each owned row (select chain, no dynamic index)
+        // pivot-column value of each owned row (select tree, no dynamic index)
         T akk[RPT];
 #pragma unroll
-        for (int q = 0; q < RPT; q++) {
-            T v = T(0);
-#pragma unroll
-            for (int c = 0; c < NB; c++) v = (c == kk) ? a[q][c] : v;
-            akk[q] = v;
-        }
+        for (int q = 0; q < RPT; q++) akk[q] = pq_select<T, NB>(a[q], kk);
         // the reduction runs in halves of H columns to bound the number of
         // live accumulators (registers hold the panel itself)
         constexpr int H = NB > 16 ? 16 : NB;
@@ -184,31 +194,37 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
                 pj = prow[par][lane];
             }
         } else {
-            if (warp == 0) {
-                if (lane < NB) {
-                    T t = T(0);
+            // every warp forms the CTA's message and sends it to its share
+            // of the destinations (ranks warp, warp + NW, ...)
+            if (lane < NB) {
+                T t = T(0);
 #pragma unroll
-                    for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
-                    xbuf[par][lane] = t;
-                    xbuf[par][NB + lane] = crank == 0 ? prow[par][lane] : T(0);
-                }
-                __syncwarp();
-                const uint32_t src = pq_smem(&gbuf[par][crank][0]);
+                for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
+                xbuf[warp][lane] = t;
+                xbuf[warp][NB + lane] = crank == 0 ? prow[par][lane] : T(0);
+            }
+            __syncwarp();
+            if (lane < NV) {
+                const float4 v = reinterpret_cast<const float4 *>(&xbuf[warp][0])[lane];
+                const uint32_t dst = pq_smem(&gbuf[par][crank][0]) + 16 * lane;
                 const uint32_t bar = pq_smem(&mbar[par]);
-                for (int e = lane; e < cs * NV; e += 32) {
-                    const int r = e / NV, q = e % NV;
-                    const float4 v = reinterpret_cast<const float4 *>(&xbuf[par][0])[q];
-                    pq_st_async(pq_mapa(src + 16 * q, r), v, pq_mapa(bar, r));
-                }
+                for (int r = warp; r < cs; r += NW) pq_st_async(pq_mapa(dst, r), v, pq_mapa(bar, r));
             }
             // after a timeout the remaining columns skip their waits (the
             // error flag reports the panel; the kernel still ends promptly)
             if (!timed_out && !pq_wait(pq_smem(&mbar[par]), (uint32_t)(kk >> 1) & 1u)) timed_out = true;
             if (lane < NB) {
-                for (int r = 0; r < cs; r++) {
+                T t2 = T(0), p2 = T(0);
+                int r = 0;
+                for (; r + 1 < cs; r += 2) {
                     tot += gbuf[par][r][lane];
+                    t2 += gbuf[par][r + 1][lane];
                     pj += gbuf[par][r][NB + lane];
+                    p2 += gbuf[par][r + 1][NB + lane];
                 }
+                if (r < cs) { tot += gbuf[par][r][lane]; pj += gbuf[par][r][NB + lane]; }
+                tot += t2;
+                pj += p2;
             }
         }
         const T alpha = __shfl_sync(0xffffffffu, pj, kk);
@@ -232,6 +248,8 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
         // branch-free update: f = v_i (scale * a(i,kk) below the pivot, 1 on
         // the pivot row, 0 above); a(i, c) -= coef_c * f (coef_c = 0 for
         // c <= kk); the pivot column becomes v (or beta on the pivot row)
+        // groups of 8 columns wholly left of the pivot are untouched (warp-
+        // uniform branch)
 #pragma unroll
         for (int q = 0; q < RPT; q++) {
             const bool below = rr[q] > kk, piv = rr[q] == kk;
@@ -239,9 +257,14 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
             const T f = below ? sk : (piv ? T(1) : T(0));
             const T newk = below ? sk : (piv ? beta : akk[q]);
 #pragma unroll
-            for (int c = 0; c < NB; c++) {
-                const T upd = fma(-coefw[warp][c], f, a[q][c]);
-                a[q][c] = (c == kk) ? newk : upd;
+            for (int g = 0; g < NB; g += 8) {
+                if (g + 7 >= kk) {
+#pragma unroll
+                    for (int c = g; c < g + 8; c++) {
+                        const T upd = fma(-coefw[warp][c], f, a[q][c]);
+                        a[q][c] = (c == kk) ? newk : upd;
+                    }
+                }
             }
         }
     }
