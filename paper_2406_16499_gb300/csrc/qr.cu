@@ -811,95 +811,129 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
 }
 
 // Inner update with the CTA's whole row chunk of V and C staged in shared
-// memory at once (every load issued up front instead of one 32-row tile per
-// round trip): partial S = V^T C, DSMEM sum over the cluster, W = Tw^T S,
-// C -= V W in shared memory, one coalesced write-back.  Leading dimension of
-// the staged chunk odd (rp) so that column-wise warp reads hit distinct banks.
+// memory at once: partial S = V^T C, DSMEM sum over the cluster,
+// W = Tw^T S, C -= V W in shared memory, one coalesced write-back.
+// V is staged row-major (rows of 36 floats: 16-byte vectors, distinct banks
+// per quarter warp), C column-major with an odd leading dimension rp.  The
+// products are register-blocked: S in 4 x 4 tiles per thread (one vector
+// load of V and four loads of C per 16 FMAs), the update one row per thread
+// with W^T rows read as broadcast vectors.
+constexpr int IV_LD = 36;
+
 template <int NB>
 __global__ void __launch_bounds__(256, 1)
 k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restrict__ C, int ldc, int nc,
              const float *__restrict__ Tw, int chunk, int rp)
 {
+    static_assert(NB == 32, "32-wide panels");
     extern __shared__ __align__(16) float sm[];
-    float *Vc = sm;                          // rp x NB
-    float *Cc = Vc + (size_t)rp * NB;        // rp x nc
-    __shared__ float pw[NB * INNER_MAXC];    // this CTA's partial, read remotely
-    __shared__ float Sx[NB][INNER_MAXC + 1];
-    __shared__ float Wt[NB][INNER_MAXC + 1];
-    __shared__ float Xs[NB][NB + 1];
+    float *Vc = sm;                                    // chunk x IV_LD, row-major
+    float *Cc = Vc + (size_t)chunk * IV_LD;            // nc x rp, column-major
+    __shared__ __align__(16) float pw[INNER_MAXC * NB];     // this CTA's partial S, [c][i]
+    __shared__ __align__(16) float Sx[INNER_MAXC * NB];     // cluster sum, [c][i]
+    __shared__ __align__(16) float Wc[INNER_MAXC * IV_LD];  // W^T rows: Wc[c][k] = W(k, c)
+    __shared__ float Xs[NB][NB + 1];                        // Xs[a][k] = Tw(k, a)
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
     const int tid = threadIdx.x;
     const int r0 = crank * chunk, r1 = min(r0 + chunk, L), R = max(0, r1 - r0);
-    for (int e = tid; e < R * NB; e += 256) {
-        const int r = e % R, c = e / R, gr = r0 + r;
-        float v = 0.f;
-        if (c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f);
-        Vc[r + (size_t)c * rp] = v;
-    }
-    for (int e = tid; e < R * nc; e += 256) {
-        const int r = e % R, c = e / R;
-        Cc[r + (size_t)c * rp] = C[idx2(r0 + r, c, ldc)];
+    // staging: rows over threads, columns unrolled (no index division)
+    for (int r = tid; r < R; r += 256) {
+        const int gr = r0 + r;
+#pragma unroll 8
+        for (int c = 0; c < NB; c++) {
+            float v = 0.f;
+            if (c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f);
+            Vc[(size_t)r * IV_LD + c] = v;
+        }
+#pragma unroll 8
+        for (int c = 0; c < nc; c++) Cc[r + (size_t)c * rp] = C[idx2(gr, c, ldc)];
     }
     for (int e = tid; e < NB * NB; e += 256) {
-        const int a = e % NB, k = e / NB;
-        Xs[k][a] = Tw[a + k * NB];                // X = Tw^T
+        const int k = e & (NB - 1), a = e / NB;
+        Xs[a][k] = Tw[k + a * NB];
     }
     __syncthreads();
-    // partial S(i, c) = sum_r V(r, i) C(r, c): lane i, column group cb
-    constexpr int CSTEP = 256 / NB;
-    constexpr int NOUT = (INNER_MAXC + CSTEP - 1) / CSTEP;
-    const int i = tid % NB, cb = tid / NB;
-    float acc[NOUT];
+    // partial S: thread (ti, tc) owns S(4ti..4ti+3, 4tc..4tc+3)
+    {
+        const int ti = tid & 7, tc = tid >> 3;
+        const int i0 = 4 * ti, c0 = 4 * tc;
+        if (c0 < nc) {
+            float acc[4][4];
 #pragma unroll
-    for (int q = 0; q < NOUT; q++) acc[q] = 0.f;
-    const float *vi = Vc + (size_t)i * rp;
+            for (int a = 0; a < 4; a++)
+#pragma unroll
+                for (int b = 0; b < 4; b++) acc[a][b] = 0.f;
+            const float *cp[4];
+#pragma unroll
+            for (int b = 0; b < 4; b++) cp[b] = Cc + (size_t)min(c0 + b, nc - 1) * rp;
 #pragma unroll 4
-    for (int r = 0; r < R; r++) {
-        const float v = vi[r];
+            for (int r = 0; r < R; r++) {
+                const float4 v = *reinterpret_cast<const float4 *>(Vc + (size_t)r * IV_LD + i0);
+                float cv[4];
 #pragma unroll
-        for (int q = 0; q < NOUT; q++) {
-            const int c = cb + CSTEP * q;
-            if (c < nc) acc[q] = fmaf(v, Cc[r + (size_t)c * rp], acc[q]);
+                for (int b = 0; b < 4; b++) cv[b] = cp[b][r];
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    acc[0][b] = fmaf(v.x, cv[b], acc[0][b]);
+                    acc[1][b] = fmaf(v.y, cv[b], acc[1][b]);
+                    acc[2][b] = fmaf(v.z, cv[b], acc[2][b]);
+                    acc[3][b] = fmaf(v.w, cv[b], acc[3][b]);
+                }
+            }
+#pragma unroll
+            for (int b = 0; b < 4; b++)
+                if (c0 + b < nc)
+                    *reinterpret_cast<float4 *>(&pw[(c0 + b) * NB + i0]) =
+                        make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
         }
     }
-#pragma unroll
-    for (int q = 0; q < NOUT; q++) {
-        const int c = cb + CSTEP * q;
-        if (c < nc) pw[i + c * NB] = acc[q];
-    }
     cluster.sync();
-    for (int e = tid; e < NB * nc; e += 256) {
-        float sum = 0.f;
-        for (int q = 0; q < cs; q++) sum += *cluster.map_shared_rank(&pw[e], q);
-        Sx[e % NB][e / NB] = sum;
+    // cluster sum, 16-byte remote loads in rank order
+    for (int e = tid; e < nc * (NB / 4); e += 256) {
+        float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < cs; q++) {
+            const float4 v = reinterpret_cast<const float4 *>(cluster.map_shared_rank(pw, q))[e];
+            sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+        }
+        reinterpret_cast<float4 *>(Sx)[e] = sum;
     }
     __syncthreads();
+    // W(a, c) = sum_k Tw(k, a) S(k, c)
     for (int e = tid; e < NB * nc; e += 256) {
-        const int a = e % NB, c = e / NB;
+        const int a = e & (NB - 1), c = e / NB;
         float sum = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < NB; k++) sum = fmaf(Xs[a][k], Sx[k][c], sum);
-        Wt[a][c] = sum;
+        for (int k = 0; k < NB; k++) sum = fmaf(Xs[a][k], Sx[c * NB + k], sum);
+        Wc[c * IV_LD + a] = sum;
     }
     __syncthreads();
-    // C -= V W (thread per row of the chunk), then the write-back
+    // C -= V W, one row per thread
     for (int r = tid; r < R; r += 256) {
         float vr[NB];
 #pragma unroll
-        for (int k = 0; k < NB; k++) vr[k] = Vc[r + (size_t)k * rp];
+        for (int q = 0; q < NB / 4; q++) {
+            const float4 v = *reinterpret_cast<const float4 *>(Vc + (size_t)r * IV_LD + 4 * q);
+            vr[4 * q] = v.x; vr[4 * q + 1] = v.y; vr[4 * q + 2] = v.z; vr[4 * q + 3] = v.w;
+        }
         for (int c = 0; c < nc; c++) {
             float t = 0.f;
 #pragma unroll
-            for (int k = 0; k < NB; k++) t = fmaf(vr[k], Wt[k][c], t);
+            for (int q = 0; q < NB / 4; q++) {
+                const float4 w = *reinterpret_cast<const float4 *>(&Wc[c * IV_LD + 4 * q]);
+                t = fmaf(vr[4 * q], w.x, t);
+                t = fmaf(vr[4 * q + 1], w.y, t);
+                t = fmaf(vr[4 * q + 2], w.z, t);
+                t = fmaf(vr[4 * q + 3], w.w, t);
+            }
             Cc[r + (size_t)c * rp] -= t;
         }
     }
     __syncthreads();
-    for (int e = tid; e < R * nc; e += 256) {
-        const int r = e % R, c = e / R;
-        C[idx2(r0 + r, c, ldc)] = Cc[r + (size_t)c * rp];
+    for (int r = tid; r < R; r += 256) {
+#pragma unroll 8
+        for (int c = 0; c < nc; c++) C[idx2(r0 + r, c, ldc)] = Cc[r + (size_t)c * rp];
     }
     cluster.sync();   // pw must outlive the remote reads
 }
@@ -929,10 +963,10 @@ static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int
         }
         const int want = std::max(1, std::min(16, ceil_div(L, 64)));
         const int chunk0 = ceil_div(L, want);
-        const size_t smem0 = (size_t)((chunk0 | 1) * (32 + nc)) * sizeof(float);
+        const size_t smem0 = ((size_t)chunk0 * IV_LD + (size_t)(chunk0 | 1) * nc) * sizeof(float);
         const int cs = cluster_size_for((const void *)kern, 256, smem0, want);
         const int chunk = ceil_div(L, cs), rp = chunk | 1;
-        const size_t smem = (size_t)rp * (32 + nc) * sizeof(float);
+        const size_t smem = ((size_t)chunk * IV_LD + (size_t)rp * nc) * sizeof(float);
         if (smem <= 160 * 1024) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(cs, 1, 1);
