@@ -810,15 +810,18 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
     return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, s);
 }
 
-// Inner update with the CTA's whole row chunk of V and C staged in shared
-// memory at once: partial S = V^T C, DSMEM sum over the cluster,
-// W = Tw^T S, C -= V W in shared memory, one coalesced write-back.
-// V is staged row-major (rows of 36 floats: 16-byte vectors, distinct banks
-// per quarter warp), C column-major with an odd leading dimension rp.  The
-// products are register-blocked: S in 4 x 4 tiles per thread (one vector
-// load of V and four loads of C per 16 FMAs), the update one row per thread
-// with W^T rows read as broadcast vectors.
+// Inner update with the CTA's whole row chunk of V and of a 32-column group
+// of C staged in shared memory: partial S = V^T C, DSMEM sum over the
+// cluster, W = Tw^T S, C -= V W in shared memory, one coalesced write-back.
+// Column groups are independent (grid y, one cluster each), so an update of
+// nc columns spans ceil(nc / 32) clusters.  V is staged row-major (rows of
+// 36 floats: 16-byte vectors, distinct banks per quarter warp), C
+// column-major with an odd leading dimension rp.  S is register-blocked in
+// 4 x 4 tiles over four row groups (one vector load of V and four loads of C
+// per 16 FMAs), summed over the groups in shared memory; the update is one
+// row per thread with W^T rows read as broadcast vectors.
 constexpr int IV_LD = 36;
+constexpr int IC = 32;                             // columns per cluster
 
 template <int NB>
 __global__ void __launch_bounds__(256, 1)
@@ -828,15 +831,19 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
     static_assert(NB == 32, "32-wide panels");
     extern __shared__ __align__(16) float sm[];
     float *Vc = sm;                                    // chunk x IV_LD, row-major
-    float *Cc = Vc + (size_t)chunk * IV_LD;            // nc x rp, column-major
-    __shared__ __align__(16) float pw[INNER_MAXC * NB];     // this CTA's partial S, [c][i]
-    __shared__ __align__(16) float Sx[INNER_MAXC * NB];     // cluster sum, [c][i]
-    __shared__ __align__(16) float Wc[INNER_MAXC * IV_LD];  // W^T rows: Wc[c][k] = W(k, c)
-    __shared__ float Xs[NB][NB + 1];                        // Xs[a][k] = Tw(k, a)
+    float *Cc = Vc + (size_t)chunk * IV_LD;            // IC x rp, column-major
+    __shared__ __align__(16) float pg[4][IC * NB];     // row-group partials, [c][i]
+    __shared__ __align__(16) float pw[IC * NB];        // this CTA's partial S, read remotely
+    __shared__ __align__(16) float Sx[IC * NB];        // cluster sum
+    __shared__ __align__(16) float Wc[IC * IV_LD];     // W^T rows: Wc[c][k] = W(k, c)
+    __shared__ float Xs[NB][NB + 1];                   // Xs[a][k] = Tw(k, a)
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
     const int tid = threadIdx.x;
+    const int cg0 = blockIdx.y * IC;
+    const int ncl = min(IC, nc - cg0);                 // columns of this group
+    C += (size_t)cg0 * ldc;
     const int r0 = crank * chunk, r1 = min(r0 + chunk, L), R = max(0, r1 - r0);
     // staging: rows over threads, columns unrolled (no index division)
     for (int r = tid; r < R; r += 256) {
@@ -848,50 +855,50 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
             Vc[(size_t)r * IV_LD + c] = v;
         }
 #pragma unroll 8
-        for (int c = 0; c < nc; c++) Cc[r + (size_t)c * rp] = C[idx2(gr, c, ldc)];
+        for (int c = 0; c < IC; c++)
+            Cc[r + (size_t)c * rp] = c < ncl ? C[idx2(gr, c, ldc)] : 0.f;
     }
     for (int e = tid; e < NB * NB; e += 256) {
         const int k = e & (NB - 1), a = e / NB;
         Xs[a][k] = Tw[k + a * NB];
     }
     __syncthreads();
-    // partial S: thread (ti, tc) owns S(4ti..4ti+3, 4tc..4tc+3)
+    // partial S: thread (rg, ti, tc) owns S(4ti.., 4tc..) over row group rg
     {
-        const int ti = tid & 7, tc = tid >> 3;
+        const int rg = tid >> 6, ti = tid & 7, tc = (tid >> 3) & 7;
         const int i0 = 4 * ti, c0 = 4 * tc;
-        if (c0 < nc) {
-            float acc[4][4];
+        const int ra = (R * rg) >> 2, rb = (R * (rg + 1)) >> 2;
+        float acc[4][4];
 #pragma unroll
-            for (int a = 0; a < 4; a++)
+        for (int a = 0; a < 4; a++)
 #pragma unroll
-                for (int b = 0; b < 4; b++) acc[a][b] = 0.f;
-            const float *cp[4];
-#pragma unroll
-            for (int b = 0; b < 4; b++) cp[b] = Cc + (size_t)min(c0 + b, nc - 1) * rp;
+            for (int b = 0; b < 4; b++) acc[a][b] = 0.f;
+        const float *cp = Cc + (size_t)c0 * rp;
 #pragma unroll 4
-            for (int r = 0; r < R; r++) {
-                const float4 v = *reinterpret_cast<const float4 *>(Vc + (size_t)r * IV_LD + i0);
-                float cv[4];
+        for (int r = ra; r < rb; r++) {
+            const float4 v = *reinterpret_cast<const float4 *>(Vc + (size_t)r * IV_LD + i0);
+            float cv[4];
 #pragma unroll
-                for (int b = 0; b < 4; b++) cv[b] = cp[b][r];
+            for (int b = 0; b < 4; b++) cv[b] = cp[(size_t)b * rp + r];
 #pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    acc[0][b] = fmaf(v.x, cv[b], acc[0][b]);
-                    acc[1][b] = fmaf(v.y, cv[b], acc[1][b]);
-                    acc[2][b] = fmaf(v.z, cv[b], acc[2][b]);
-                    acc[3][b] = fmaf(v.w, cv[b], acc[3][b]);
-                }
+            for (int b = 0; b < 4; b++) {
+                acc[0][b] = fmaf(v.x, cv[b], acc[0][b]);
+                acc[1][b] = fmaf(v.y, cv[b], acc[1][b]);
+                acc[2][b] = fmaf(v.z, cv[b], acc[2][b]);
+                acc[3][b] = fmaf(v.w, cv[b], acc[3][b]);
             }
-#pragma unroll
-            for (int b = 0; b < 4; b++)
-                if (c0 + b < nc)
-                    *reinterpret_cast<float4 *>(&pw[(c0 + b) * NB + i0]) =
-                        make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
         }
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+            *reinterpret_cast<float4 *>(&pg[rg][(c0 + b) * NB + i0]) =
+                make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
     }
+    __syncthreads();
+    for (int e = tid; e < IC * NB; e += 256) pw[e] = (pg[0][e] + pg[1][e]) + (pg[2][e] + pg[3][e]);
     cluster.sync();
     // cluster sum, 16-byte remote loads in rank order
-    for (int e = tid; e < nc * (NB / 4); e += 256) {
+    {
+        const int e = tid;                              // IC * NB / 4 == 256 vectors
         float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
         for (int q = 0; q < cs; q++) {
             const float4 v = reinterpret_cast<const float4 *>(cluster.map_shared_rank(pw, q))[e];
@@ -901,7 +908,7 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
     }
     __syncthreads();
     // W(a, c) = sum_k Tw(k, a) S(k, c)
-    for (int e = tid; e < NB * nc; e += 256) {
+    for (int e = tid; e < NB * IC; e += 256) {
         const int a = e & (NB - 1), c = e / NB;
         float sum = 0.f;
 #pragma unroll 8
@@ -909,7 +916,7 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
         Wc[c * IV_LD + a] = sum;
     }
     __syncthreads();
-    // C -= V W, one row per thread
+    // C -= V W, one row per thread (two accumulators per column)
     for (int r = tid; r < R; r += 256) {
         float vr[NB];
 #pragma unroll
@@ -917,23 +924,29 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
             const float4 v = *reinterpret_cast<const float4 *>(Vc + (size_t)r * IV_LD + 4 * q);
             vr[4 * q] = v.x; vr[4 * q + 1] = v.y; vr[4 * q + 2] = v.z; vr[4 * q + 3] = v.w;
         }
-        for (int c = 0; c < nc; c++) {
-            float t = 0.f;
+#pragma unroll 2
+        for (int c = 0; c < ncl; c++) {
+            float t0 = 0.f, t1 = 0.f;
 #pragma unroll
-            for (int q = 0; q < NB / 4; q++) {
-                const float4 w = *reinterpret_cast<const float4 *>(&Wc[c * IV_LD + 4 * q]);
-                t = fmaf(vr[4 * q], w.x, t);
-                t = fmaf(vr[4 * q + 1], w.y, t);
-                t = fmaf(vr[4 * q + 2], w.z, t);
-                t = fmaf(vr[4 * q + 3], w.w, t);
+            for (int q = 0; q < NB / 4; q += 2) {
+                const float4 w0 = *reinterpret_cast<const float4 *>(&Wc[c * IV_LD + 4 * q]);
+                const float4 w1 = *reinterpret_cast<const float4 *>(&Wc[c * IV_LD + 4 * q + 4]);
+                t0 = fmaf(vr[4 * q], w0.x, t0);
+                t0 = fmaf(vr[4 * q + 1], w0.y, t0);
+                t0 = fmaf(vr[4 * q + 2], w0.z, t0);
+                t0 = fmaf(vr[4 * q + 3], w0.w, t0);
+                t1 = fmaf(vr[4 * q + 4], w1.x, t1);
+                t1 = fmaf(vr[4 * q + 5], w1.y, t1);
+                t1 = fmaf(vr[4 * q + 6], w1.z, t1);
+                t1 = fmaf(vr[4 * q + 7], w1.w, t1);
             }
-            Cc[r + (size_t)c * rp] -= t;
+            Cc[r + (size_t)c * rp] -= t0 + t1;
         }
     }
     __syncthreads();
     for (int r = tid; r < R; r += 256) {
 #pragma unroll 8
-        for (int c = 0; c < nc; c++) C[idx2(r0 + r, c, ldc)] = Cc[r + (size_t)c * rp];
+        for (int c = 0; c < ncl; c++) C[idx2(r0 + r, c, ldc)] = Cc[r + (size_t)c * rp];
     }
     cluster.sync();   // pw must outlive the remote reads
 }
@@ -963,13 +976,13 @@ static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int
         }
         const int want = std::max(1, std::min(16, ceil_div(L, 64)));
         const int chunk0 = ceil_div(L, want);
-        const size_t smem0 = ((size_t)chunk0 * IV_LD + (size_t)(chunk0 | 1) * nc) * sizeof(float);
+        const size_t smem0 = ((size_t)chunk0 * IV_LD + (size_t)(chunk0 | 1) * IC) * sizeof(float);
         const int cs = cluster_size_for((const void *)kern, 256, smem0, want);
         const int chunk = ceil_div(L, cs), rp = chunk | 1;
-        const size_t smem = ((size_t)chunk * IV_LD + (size_t)rp * nc) * sizeof(float);
+        const size_t smem = ((size_t)chunk * IV_LD + (size_t)rp * IC) * sizeof(float);
         if (smem <= 160 * 1024) {
             cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(cs, 1, 1);
+            cfg.gridDim = dim3(cs, ceil_div(nc, IC), 1);
             cfg.blockDim = dim3(256, 1, 1);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = s;
