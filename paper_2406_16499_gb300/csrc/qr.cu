@@ -719,10 +719,29 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
     }
 }
 
+// out[e] = sum_z P[z * pstride + e] in split order, one element per thread.
+__global__ void __launch_bounds__(256)
+k_sum_splits(const float *__restrict__ P, int nsplit, size_t pstride, int n, float *__restrict__ out)
+{
+    const int e = blockIdx.x * 256 + threadIdx.x;
+    if (e >= n) return;
+    float v[8];
+    float sum = 0.f;
+    int z = 0;
+    for (; z + 8 <= nsplit; z += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) v[u] = P[(size_t)(z + u) * pstride + e];
+#pragma unroll
+        for (int u = 0; u < 8; u++) sum += v[u];
+    }
+    for (; z < nsplit; z++) sum += P[(size_t)z * pstride + e];
+    out[e] = sum;
+}
+
 // Compact-WY factor of an outer block from its four 32-wide inner factors
 // and the Gram matrix G = V^T V (Tw^{-1} = triu(G, 1) + diag(1/tau)):
 //   T(0:32j, 32j:32j+32) = -T(0:32j, 0:32j) G(0:32j, 32j:32j+32) T_j.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, float *__restrict__ Tb)
 {
     extern __shared__ float sm[];
@@ -735,26 +754,44 @@ k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, f
     const int nblk = ceil_div(nr, 32);
     for (int b = 0; b < nblk; b++)
         for (int e = tid; e < 32 * 32; e += 256) {
-            const int i = e % 32, k = e / 32;
-            Ts[(32 * b + i) + (32 * b + k) * OUTER_NB] = Tw32[(size_t)b * 1024 + i + k * 32];
+            const int ii = e & 31, k = e >> 5;
+            Ts[(32 * b + ii) + (32 * b + k) * OUTER_NB] = Tw32[(size_t)b * 1024 + ii + k * 32];
         }
     __syncthreads();
+    // thread (row i = tid % 128, 16-column half ch = tid / 128): 16
+    // independent accumulators per product, no index division
+    const int i = tid & (OUTER_NB - 1), ch = tid >> 7;
     for (int j = 1; j < nblk; j++) {
         const int h = 32 * j;
         // Pm = G(0:h, h:h+32) * T_j
-        for (int e = tid; e < h * 32; e += 256) {
-            const int i = e % h, c = e / h;
-            float s = 0.f;
-            for (int k = 0; k < 32; k++) s = fmaf(Gs[i + (h + k) * OUTER_NB], Ts[(h + k) + (h + c) * OUTER_NB], s);
-            Pm[i + c * 96] = s;
+        if (i < h) {
+            float acc[16];
+#pragma unroll
+            for (int c = 0; c < 16; c++) acc[c] = 0.f;
+#pragma unroll 4
+            for (int k = 0; k < 32; k++) {
+                const float g = Gs[i + (h + k) * OUTER_NB];
+#pragma unroll
+                for (int c = 0; c < 16; c++)
+                    acc[c] = fmaf(g, Ts[(h + k) + (h + 16 * ch + c) * OUTER_NB], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 16; c++) Pm[i + (16 * ch + c) * 96] = acc[c];
         }
         __syncthreads();
         // T(0:h, h:h+32) = -T(0:h, 0:h) * Pm   (T upper triangular)
-        for (int e = tid; e < h * 32; e += 256) {
-            const int i = e % h, c = e / h;
-            float s = 0.f;
-            for (int k = i; k < h; k++) s = fmaf(Ts[i + k * OUTER_NB], Pm[k + c * 96], s);
-            Ts[i + (h + c) * OUTER_NB] = -s;
+        if (i < h) {
+            float acc[16];
+#pragma unroll
+            for (int c = 0; c < 16; c++) acc[c] = 0.f;
+#pragma unroll 4
+            for (int k = i; k < h; k++) {
+                const float t = Ts[i + k * OUTER_NB];
+#pragma unroll
+                for (int c = 0; c < 16; c++) acc[c] = fmaf(t, Pm[k + (16 * ch + c) * 96], acc[c]);
+            }
+#pragma unroll
+            for (int c = 0; c < 16; c++) Ts[i + (h + 16 * ch + c) * OUTER_NB] = -acc[c];
         }
         __syncthreads();
     }
@@ -1153,11 +1190,7 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     if (rc) return rc;
     {
         ProfScope ps(K_LARFB_AUX, s);
-        const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
-        static bool attr = false;
-        if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_reduce_w<<<OUTER_NB / RW_COLS, 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, nullptr, 0, OUTER_NB, w.G,
-                                                          w.G, OUTER_NB, 0);
+        k_sum_splits<<<OUTER_NB * OUTER_NB / 256, 256, 0, s>>>(w.P, nsplit, pstride, OUTER_NB * OUTER_NB, w.G);
     }
     {
         ProfScope ps(K_LARFB_AUX, s);
