@@ -665,7 +665,7 @@ k_prep_v(const float *__restrict__ X, int ldx, int L, int nr, float *__restrict_
 
 // W = op(Tb) * sum_z P[z] (128 x nc), op = Tb^T (trans), Tb, or identity
 // (Tb == NULL); optionally split into W = Wh + Wl.  One block per 16 columns.
-constexpr int RW_COLS = 16;
+template <int RW_COLS>
 __global__ void __launch_bounds__(256)
 k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, const float *__restrict__ Tb,
            int trans, int nc, float *__restrict__ Wh, float *__restrict__ Wl, int ldw, int split)
@@ -716,6 +716,26 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
         if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(w)); h = __uint_as_float(u); }
         Wh[(size_t)(c0 + c) * ldw + i] = h;
         if (split) Wl[(size_t)(c0 + c) * ldw + i] = w - h;
+    }
+}
+
+// W = op(Tb) sum_z P[z] (or the plain sum when Tb is null) over nc columns:
+// 16 columns per CTA, 4 when that would leave the grid small.
+static void reduce_w(const float *P, int nsplit, size_t pstride, const float *Tb, int trans, int nc, float *Wh,
+                     float *Wl, int ldw, int split, cudaStream_t s)
+{
+    if (nc >= 16 * 64) {
+        const size_t smem = (size_t)(16 + OUTER_NB) * OUTER_NB * 4;
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_reduce_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_reduce_w<16><<<ceil_div(nc, 16), 256, smem, s>>>(P, nsplit, pstride, OUTER_NB, Tb, trans, nc, Wh, Wl, ldw,
+                                                          split);
+    } else {
+        const size_t smem = (size_t)(4 + OUTER_NB) * OUTER_NB * 4;
+        static bool attr = false;
+        if (!attr) { cudaFuncSetAttribute(k_reduce_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        k_reduce_w<4><<<ceil_div(nc, 4), 256, smem, s>>>(P, nsplit, pstride, OUTER_NB, Tb, trans, nc, Wh, Wl, ldw,
+                                                        split);
     }
 }
 
@@ -1161,11 +1181,7 @@ static int outer_apply(OuterWs &w, const float *Tb, int trans, int L, float *C, 
     if (rc) return rc;
     {
         ProfScope ps(K_LARFB_AUX, s);
-        const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
-        static bool attr = false;
-        if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_reduce_w<<<ceil_div(Nc, RW_COLS), 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, Tb, trans, Nc, w.W,
-                                                             w.Wl, OUTER_NB, split);
+        reduce_w(w.P, nsplit, pstride, Tb, trans, Nc, w.W, w.Wl, OUTER_NB, split, s);
     }
     // C -= V W  (M = L, N = Nc, K = 128)
     rc = gemm_tc(mode, 0, TCE_SUB, tVt, tVtl, tW, tWl, 0, 0, 0, 0, L, Nc, OUTER_NB, C, ldc, 0, 1, err, s);
@@ -1339,12 +1355,8 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
         if (rc) return rc;
         {
             ProfScope ps(K_LARFB_AUX, s);
-            const size_t smem = (size_t)(RW_COLS + OUTER_NB) * OUTER_NB * 4;
-            static bool attr = false;
-            if (!attr) { cudaFuncSetAttribute(k_reduce_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
             // W = T_b^T sum P = X^T,  X = (V_1^T V_b) T_b
-            k_reduce_w<<<ceil_div(J0, RW_COLS), 256, smem, s>>>(w.P, nsplit, pstride, OUTER_NB, Tb, 1, J0, w.W,
-                                                                 w.W, OUTER_NB, 0);
+            reduce_w(w.P, nsplit, pstride, Tb, 1, J0, w.W, w.W, OUTER_NB, 0, s);
         }
         // chunking of k: about four tiles per SM, partials within w.P
         int want = ceil_div(8 * 152, ntile);
