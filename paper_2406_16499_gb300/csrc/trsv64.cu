@@ -111,7 +111,7 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *xs = reinterpret_cast<T *>(smem_raw);                 // slice
     T *Ds = xs + slice;                                      // [2][64 * 65]
-    __shared__ T xin[2][64];
+    __shared__ __align__(16) T xin[2][64];
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -173,14 +173,33 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
             const T xv = tid < bs ? acc : T(0);
             for (int r = 0; r < cs; r++) *cluster.map_shared_rank(&xin[par][tid], r) = xv;
         }
-        // 3. x_blk visible everywhere
-        cluster.sync();
-        // 4. update the unsolved rows; the owner stores its block
+        // 3. x_blk visible everywhere: only the owner's stores need release
+        // ordering; every CTA acquires
+        if (crank == owner) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        else asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        // 4. update the unsolved rows (x_blk read as 16-byte vectors); the
+        // owner stores its block
         if (va) {
-            T dsum = T(0);
+            T d0 = T(0), d1 = T(0);
+            if constexpr (sizeof(T) == 4) {
 #pragma unroll
-            for (int c = 0; c < 64; c++) dsum = fma((T)u[c], xin[par][c], dsum);
-            xs[i - s0] -= dsum;
+                for (int q = 0; q < 16; q++) {
+                    const float4 xv = reinterpret_cast<const float4 *>(&xin[par][0])[q];
+                    d0 = fma((T)u[4 * q], (T)xv.x, d0);
+                    d1 = fma((T)u[4 * q + 1], (T)xv.y, d1);
+                    d0 = fma((T)u[4 * q + 2], (T)xv.z, d0);
+                    d1 = fma((T)u[4 * q + 3], (T)xv.w, d1);
+                }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 32; q++) {
+                    const double2 xv = reinterpret_cast<const double2 *>(&xin[par][0])[q];
+                    d0 = fma((T)u[2 * q], (T)xv.x, d0);
+                    d1 = fma((T)u[2 * q + 1], (T)xv.y, d1);
+                }
+            }
+            xs[i - s0] -= d0 + d1;
         }
         if (crank == owner && tid < bs) xs[r0 + tid - s0] = xin[par][tid];
         if (stage) t64_store_d(Ds + (par ^ 1) * T64_DS, trans, tid, dn);
@@ -197,8 +216,7 @@ int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaS
     if (n > T64_MAXN || ldu % 4 || ((uintptr_t)U & 15)) return -1;
     auto kern = k_trsv64<T>;
     const int nblk = ceil_div(n, 64);
-    int want = ceil_div(nblk, 4);                          // 256 rows per CTA
-    if (want > 16) want = 16;
+    int want = nblk < 16 ? nblk : 16;                      // as many CTAs as the cluster allows
     const size_t dsz = 2 * T64_DS * sizeof(T);
     static bool attr = false;
     if (!attr) {
