@@ -39,7 +39,6 @@ constexpr int PANEL_MAX_CLUSTER = 16;
 // into every CTA's shared memory with st.async, which signals the
 // receiver's mbarrier (complete_tx); the receiver announces the bytes it
 // expects one column ahead, so no message can arrive before its count.
-constexpr uint32_t PANEL_WAIT_LIMIT = 1u << 22;
 
 __device__ __forceinline__ uint32_t pq_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -61,13 +60,15 @@ __device__ __forceinline__ void pq_expect_tx(uint32_t bar, uint32_t bytes)
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait on the phase of parity `parity`; false on timeout.
+// Bounded wait on the phase of parity `parity`; false on timeout.  Polls
+// with test_wait (no suspension of the waiting warp between polls).
+constexpr uint32_t PANEL_POLL_LIMIT = 1u << 26;
 __device__ __forceinline__ bool pq_wait(uint32_t bar, uint32_t parity)
 {
-    for (uint32_t it = 0; it < PANEL_WAIT_LIMIT; it++) {
+    for (uint32_t it = 0; it < PANEL_POLL_LIMIT; it++) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done)
                      : "r"(bar), "r"(parity)
@@ -307,6 +308,200 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     }
     if (timed_out) atomicOr(err, 8);
     if (cs > 1) cluster.sync();   // no CTA leaves while messages to it may be in flight
+}
+
+// ---------------------------------------------------------------------------
+// FP32 panel with two threads per row (k_panel_qr's algorithm, same column
+// message protocol): lane pair (2r, 2r+1) of a warp holds row r's columns
+// 0..15 and 16..31.  Every per-column chain (pivot select, products, the
+// warp reduction, the update) is half as long, and a CTA has twice the warps
+// to hide latency.  The warp reduction exchanges only between lanes of the
+// same half (xor 16, 8, 4, 2), leaving lane l with the warp total of column
+// 16 (l & 1) + (l >> 1).  NT threads hold NT / 2 rows.
+// ---------------------------------------------------------------------------
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk, float *__restrict__ tau,
+            float *__restrict__ Tw, int *__restrict__ err)
+{
+    constexpr int NB = 32, HB = 16;
+    constexpr int NW = NT / 32;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int h = lane & 1;                              // this thread's half of the row
+    const int L = M - j0;
+    const int kpanel = min(ncols, L);
+    constexpr int MSG = 2 * NB;
+    constexpr int NV = MSG * (int)sizeof(float) / 16;
+    __shared__ float red_s[2][NW][32];
+    __shared__ __align__(16) float xbuf[NW][MSG];
+    __shared__ __align__(16) float gbuf[2][16][MSG];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ float prow[2][NB];
+    __shared__ __align__(16) float coefw[NW][NB];
+    __shared__ float G_s[NB][NB + 1];
+    __shared__ float tau_s[NB];
+    __shared__ float T_s[NB][NB + 1];
+
+    const int row_base = crank * chunk;
+    const int row_end = min(row_base + chunk, L);
+    const uint32_t msg_bytes = (uint32_t)(cs * MSG * sizeof(float));
+    bool timed_out = false;
+    if (cs > 1) {
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[0])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[1])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            pq_expect_tx(pq_smem(&mbar[0]), msg_bytes);
+        }
+        cluster.sync();
+    }
+    const int r = row_base + warp * 16 + (lane >> 1);
+    const int rr = r < row_end ? r : -1;
+    float a[HB];
+#pragma unroll
+    for (int c = 0; c < HB; c++) {
+        const int cc = HB * h + c;
+        a[c] = (rr >= 0 && cc < ncols) ? A[idx2(j0 + rr, j0 + cc, lda)] : 0.f;
+    }
+    const int col_of_lane = HB * h + (lane >> 1);        // column total this lane ends with
+
+#pragma unroll 1
+    for (int kk = 0; kk < kpanel; kk++) {
+        const int par = kk & 1;
+        // pivot value of the row: select in the half that holds column kk,
+        // exchanged within the lane pair
+        const float vsel = pq_select<float, HB>(a, kk & (HB - 1));
+        const float vother = __shfl_xor_sync(0xffffffffu, vsel, 1);
+        const float akk = (h == (kk >> 4)) ? vsel : vother;
+        float acc[HB];
+        {
+            const float ak = rr > kk ? akk : 0.f;        // rows below the pivot
+#pragma unroll
+            for (int c = 0; c < HB; c++) acc[c] = ak * a[c];
+        }
+        // transpose-reduce over the 16 lanes of the same half
+#pragma unroll
+        for (int sft = HB / 2; sft >= 1; sft >>= 1) {
+            const int m = 2 * sft;
+            const bool upper = (lane & m) != 0;
+#pragma unroll
+            for (int i = 0; i < sft; i++) {
+                const float send = upper ? acc[i] : acc[i + sft];
+                const float keep = upper ? acc[i + sft] : acc[i];
+                acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+            }
+        }
+        red_s[par][warp][col_of_lane] = acc[0];
+        if (rr == kk) {
+#pragma unroll
+            for (int c = 0; c < HB; c++) prow[par][HB * h + c] = a[c];
+        }
+        if (cs > 1 && tid == 0 && kk + 1 < kpanel) pq_expect_tx(pq_smem(&mbar[par ^ 1]), msg_bytes);
+        __syncthreads();
+        float tot = 0.f, pj = 0.f;
+        if (cs == 1) {
+#pragma unroll
+            for (int w = 0; w < NW; w++) tot += red_s[par][w][lane];
+            pj = prow[par][lane];
+        } else {
+            {
+                float t = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
+                xbuf[warp][lane] = t;
+                xbuf[warp][NB + lane] = crank == 0 ? prow[par][lane] : 0.f;
+            }
+            __syncwarp();
+            if (lane < NV) {
+                const float4 v = reinterpret_cast<const float4 *>(&xbuf[warp][0])[lane];
+                const uint32_t dst = pq_smem(&gbuf[par][crank][0]) + 16 * lane;
+                const uint32_t bar = pq_smem(&mbar[par]);
+                for (int q = warp; q < cs; q += NW) pq_st_async(pq_mapa(dst, q), v, pq_mapa(bar, q));
+            }
+            if (!timed_out && !pq_wait(pq_smem(&mbar[par]), (uint32_t)(kk >> 1) & 1u)) timed_out = true;
+            float t2 = 0.f, p2 = 0.f;
+            int q = 0;
+            for (; q + 1 < cs; q += 2) {
+                tot += gbuf[par][q][lane];
+                t2 += gbuf[par][q + 1][lane];
+                pj += gbuf[par][q][NB + lane];
+                p2 += gbuf[par][q + 1][NB + lane];
+            }
+            if (q < cs) { tot += gbuf[par][q][lane]; pj += gbuf[par][q][NB + lane]; }
+            tot += t2;
+            pj += p2;
+        }
+        const float alpha = __shfl_sync(0xffffffffu, pj, kk);
+        const float sp = __shfl_sync(0xffffffffu, tot, kk);
+        float beta, tv, scale;
+        if (sp == 0.f) {
+            tv = 0.f; beta = alpha; scale = 1.f;
+        } else {
+            const float nrm = sqrtf(alpha * alpha + sp);
+            beta = alpha >= 0.f ? -nrm : nrm;
+            tv = (beta - alpha) / beta;
+            scale = 1.f / (alpha - beta);
+        }
+        const float dot = pj + scale * tot;
+        coefw[warp][lane] = lane > kk ? tv * dot : 0.f;
+        if (warp == 0) {
+            if (lane < kk) G_s[lane][kk] = dot;
+            if (lane == 0) tau_s[kk] = tv;
+        }
+        __syncwarp();
+        {
+            const bool below = rr > kk, piv = rr == kk;
+            const float sk = akk * scale;
+            const float f = below ? sk : (piv ? 1.f : 0.f);
+            const float newk = below ? sk : (piv ? beta : akk);
+            const int kloc = kk - HB * h;                 // pivot index in this half (may be out of range)
+#pragma unroll
+            for (int q = 0; q < HB / 4; q++) {
+                const float4 cw = *reinterpret_cast<const float4 *>(&coefw[warp][HB * h + 4 * q]);
+                const float cv[4] = {cw.x, cw.y, cw.z, cw.w};
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const int c = 4 * q + u;
+                    const float upd = fmaf(-cv[u], f, a[c]);
+                    a[c] = (c == kloc) ? newk : upd;
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    float *Aw = A;
+    asm volatile("" : "+l"(Aw));
+    if (rr >= 0) {
+#pragma unroll
+        for (int c = 0; c < HB; c++) {
+            const int cc = HB * h + c;
+            if (cc < ncols) Aw[idx2(j0 + rr, j0 + cc, lda)] = a[c];
+        }
+    }
+    if (crank == 0 && warp == 0) {
+        if (lane < kpanel) tau[j0 + lane] = tau_s[lane];
+        const int k = lane;
+        for (int i = NB - 1; i >= 0; i--) {
+            float val = 0.f;
+            if (k < kpanel && i <= k) {
+                if (i == k) {
+                    val = tau_s[k];
+                } else {
+                    float sum = 0.f;
+                    for (int c = i + 1; c <= k; c++) sum = fmaf(G_s[i][c], T_s[c][k], sum);
+                    val = -tau_s[i] * sum;
+                }
+            }
+            T_s[i][k] = val;
+        }
+        for (int i = 0; i < NB; i++) Tw[i + (size_t)k * NB] = T_s[i][k];
+    }
+    if (timed_out) atomicOr(err, 8);
+    if (cs > 1) cluster.sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -852,14 +1047,49 @@ static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+template <int NT>
+static int launch_panel2(float *A, int lda, int M, int j0, int ncols, float *tau, float *Tw, int *err, cudaStream_t s)
+{
+    const int L = M - j0;
+    int cs = ceil_div(L, NT / 2);
+    if (cs < 1) cs = 1;
+    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
+    const int chunk = ceil_div(L, cs);
+    auto kern = k_panel_qr2<NT>;
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        attr_done = true;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ProfScope ps(K_PANEL, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw, err);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
 // Rows per CTA as small as the 16-CTA cluster limit allows: the panel's
 // column steps are latency and issue bound, so fewer rows per SM (more SMs)
-// shorten every step.
+// shorten every step.  FP32 panels of up to 4096 rows hold two threads per
+// row.
 template <typename T>
 static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, int *err, cudaStream_t s)
 {
     const int L = M - j0;
     if constexpr (sizeof(T) == 4) {
+        if (L <= 16 * 64) return launch_panel2<128>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        if (L <= 16 * 128) return launch_panel2<256>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        if (L <= 16 * 256) return launch_panel2<512>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 128) return launch_panel_shape<T, 128, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 256) return launch_panel_shape<T, 256, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 512) return launch_panel_shape<T, 512, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
