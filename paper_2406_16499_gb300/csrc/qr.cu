@@ -93,6 +93,31 @@ __device__ __forceinline__ T pq_select(const T (&v)[N], int k)
     return t[0];
 }
 
+// Compact-WY factor of a panel from its Gram entries (one warp, lane k
+// forms column k):  Tw = (triu(G, 1) + diag(1 / tau))^{-1}, i.e.
+//   T(k, k) = tau_k,  T(i, k) = -tau_i sum_{c > i} G(i, c) T(c, k)  (i < k).
+// Column k lives in registers (t[c] = 0 for c > k) and the recurrence is
+// fully unrolled, so the only serial chain is one product per row; the G
+// entries are warp-broadcast shared-memory reads.
+template <typename T, int NB, int LDG>
+__device__ __forceinline__ void panel_T_from_gram(const T (*G_s)[LDG], const T *tau_s, int kpanel, T *Tw)
+{
+    const int k = threadIdx.x & 31;
+    T t[NB];
+#pragma unroll
+    for (int i = NB - 1; i >= 0; i--) {
+        T sum = T(0);
+#pragma unroll
+        for (int c = i + 1; c < NB; c++) sum = fma(G_s[i][c], t[c], sum);
+        const T ti = i == k ? tau_s[i] : -tau_s[i] * sum;
+        t[i] = (i <= k && k < kpanel) ? ti : T(0);
+    }
+    if (k < NB) {
+#pragma unroll
+        for (int i = 0; i < NB; i++) Tw[i + (size_t)k * NB] = t[i];
+    }
+}
+
 template <typename T, int NB, int NT, int RPT>
 __global__ void __launch_bounds__(NT, 1)
 k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
@@ -119,12 +144,13 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     __shared__ __align__(16) T coefw[NW][NB];
     __shared__ T G_s[NB][NB + 1];
     __shared__ T tau_s[NB];
-    __shared__ T T_s[NB][NB + 1];
 
     const int row_base = crank * chunk;
     const int row_end = min(row_base + chunk, L);
     const uint32_t msg_bytes = (uint32_t)(cs * MSG * sizeof(T));
     bool timed_out = false;
+    // Gram entries beyond the panel stay zero (the T recurrence reads them)
+    for (int e = tid; e < NB * (NB + 1); e += NT) (&G_s[0][0])[e] = T(0);
     if (cs > 1) {
         if (tid == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[0])) : "memory");
@@ -287,24 +313,7 @@ k_panel_qr(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
 
     if (crank == 0 && warp == 0) {
         if (lane < kpanel) tau[j0 + lane] = tau_s[lane];
-        // Tw = (triu(G, 1) + diag(1/tau))^{-1}, column `lane` by back substitution.
-        const int k = lane;
-        if (k < NB) {
-            for (int i = NB - 1; i >= 0; i--) {
-                T val = T(0);
-                if (k < kpanel && i <= k) {
-                    if (i == k) {
-                        val = tau_s[k];
-                    } else {
-                        T s = T(0);
-                        for (int c = i + 1; c <= k; c++) s = fma(G_s[i][c], T_s[c][k], s);
-                        val = -tau_s[i] * s;
-                    }
-                }
-                T_s[i][k] = val;
-            }
-            for (int i = 0; i < NB; i++) Tw[i + (size_t)k * NB] = T_s[i][k];
-        }
+        panel_T_from_gram<T, NB, NB + 1>(G_s, tau_s, kpanel, Tw);
     }
     if (timed_out) atomicOr(err, 8);
     if (cs > 1) cluster.sync();   // no CTA leaves while messages to it may be in flight
@@ -343,12 +352,12 @@ k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     __shared__ __align__(16) float coefw[NW][NB];
     __shared__ float G_s[NB][NB + 1];
     __shared__ float tau_s[NB];
-    __shared__ float T_s[NB][NB + 1];
 
     const int row_base = crank * chunk;
     const int row_end = min(row_base + chunk, L);
     const uint32_t msg_bytes = (uint32_t)(cs * MSG * sizeof(float));
     bool timed_out = false;
+    for (int e = tid; e < NB * (NB + 1); e += NT) (&G_s[0][0])[e] = 0.f;
     if (cs > 1) {
         if (tid == 0) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[0])) : "memory");
@@ -484,21 +493,7 @@ k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     }
     if (crank == 0 && warp == 0) {
         if (lane < kpanel) tau[j0 + lane] = tau_s[lane];
-        const int k = lane;
-        for (int i = NB - 1; i >= 0; i--) {
-            float val = 0.f;
-            if (k < kpanel && i <= k) {
-                if (i == k) {
-                    val = tau_s[k];
-                } else {
-                    float sum = 0.f;
-                    for (int c = i + 1; c <= k; c++) sum = fmaf(G_s[i][c], T_s[c][k], sum);
-                    val = -tau_s[i] * sum;
-                }
-            }
-            T_s[i][k] = val;
-        }
-        for (int i = 0; i < NB; i++) Tw[i + (size_t)k * NB] = T_s[i][k];
+        panel_T_from_gram<float, NB, NB + 1>(G_s, tau_s, kpanel, Tw);
     }
     if (timed_out) atomicOr(err, 8);
     if (cs > 1) cluster.sync();
