@@ -367,6 +367,10 @@ k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
         }
         cluster.sync();
     }
+    // programmatic dependent launch: everything above overlaps the previous
+    // kernel's tail; its results are read only after this wait
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const int r = row_base + warp * 16 + (lane >> 1);
     const int rr = r < row_end ? r : -1;
     float a[HB];
@@ -1061,13 +1065,15 @@ static int launch_panel2(float *A, int lda, int M, int j0, int ncols, float *tau
     cfg.blockDim = dim3(NT, 1, 1);
     cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // waits in-kernel
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     ProfScope ps(K_PANEL, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw, err);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
@@ -1127,6 +1133,8 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
     const int ncl = min(IC, nc - cg0);                 // columns of this group
     C += (size_t)cg0 * ldc;
     const int r0 = crank * chunk, r1 = min(r0 + chunk, L), R = max(0, r1 - r0);
+    asm volatile("griddepcontrol.wait;" ::: "memory");             // previous kernel's results
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     // staging: rows over threads, columns unrolled (no index division)
     for (int r = tid; r < R; r += 256) {
         const int gr = r0 + r;
@@ -1268,13 +1276,15 @@ static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int
             cfg.blockDim = dim3(256, 1, 1);
             cfg.dynamicSmemBytes = smem;
             cfg.stream = s;
-            cudaLaunchAttribute at[1];
+            cudaLaunchAttribute at[2];
             at[0].id = cudaLaunchAttributeClusterDimension;
             at[0].val.clusterDim.x = cs;
             at[0].val.clusterDim.y = 1;
             at[0].val.clusterDim.z = 1;
+            at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // waits in-kernel
+            at[1].val.programmaticStreamSerializationAllowed = 1;
             cfg.attrs = at;
-            cfg.numAttrs = 1;
+            cfg.numAttrs = 2;
             ProfScope ps(K_LARFB, s);
             cudaError_t e = cudaLaunchKernelEx(&cfg, kern, V, ldv, kb, L, C, ldc, nc, Tw, chunk, rp);
             return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
