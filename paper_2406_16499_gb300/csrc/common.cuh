@@ -94,6 +94,33 @@ __device__ __forceinline__ T warp_transpose_reduce(T (&v)[V])
     return r;
 }
 
+// -------------------------------------------- programmatic dependent launch --
+// A kernel launched with pdl_launch (or the ProgrammaticStreamSerialization
+// attribute) may start while the previous kernel on its stream is still
+// running: it must call pdl_wait() before touching anything that kernel
+// writes (pdl_wait returns once the previous grid has completed and its
+// memory is visible).  pdl_trigger() lets the next such kernel begin
+// launching; both are no-ops for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t pdl_launch(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
 // ------------------------------------------------------------- helpers --
 
 __host__ __device__ __forceinline__ int ceil_div(int a, int b) { return (a + b - 1) / b; }

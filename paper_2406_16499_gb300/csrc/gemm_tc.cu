@@ -200,6 +200,9 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         abort_s = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // (no-op under an ordinary launch) the previous kernel's outputs are read
+    // only after this wait; no tensor memory is held while waiting
+    pdl_wait();
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_s)),
                      "r"((uint32_t)TC_BN)
@@ -395,6 +398,7 @@ static int launch_tc(const CUtensorMap &A, const CUtensorMap &A2, const CUtensor
         attr = true;
     }
     ProfScope ps(K_LARFB_TC, s);
+    // ordinary launch: a waiting grid of this size would hold every SM
     kern<<<dim3(ntn, ntm, nsplit), TC_THREADS, smem, s>>>(A, A2, B, B2, args);
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }

@@ -369,8 +369,8 @@ k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
     }
     // programmatic dependent launch: everything above overlaps the previous
     // kernel's tail; its results are read only after this wait
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();
+    pdl_trigger();
     const int r = row_base + warp * 16 + (lane >> 1);
     const int rr = r < row_end ? r : -1;
     float a[HB];
@@ -823,6 +823,8 @@ __global__ void __launch_bounds__(256)
 k_prep_v(const float *__restrict__ X, int ldx, int L, int nr, float *__restrict__ Vh, float *__restrict__ Vl,
          int ldv, float *__restrict__ Vth, float *__restrict__ Vtl, int split)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ float tile[32][OUTER_NB + 1];
     const int r0 = blockIdx.x * 32;
     const int tid = threadIdx.x;
@@ -864,6 +866,8 @@ __global__ void __launch_bounds__(256)
 k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, const float *__restrict__ Tb,
            int trans, int nc, float *__restrict__ Wh, float *__restrict__ Wl, int ldw, int split)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float sm[];
     float *S = sm;                                   // 128 x RW_COLS, column-major
     float *Xs = sm + RW_COLS * OUTER_NB;             // 128 x 128 column-major (x(i,k) at i + 128 k)
@@ -922,14 +926,14 @@ static void reduce_w(const float *P, int nsplit, size_t pstride, const float *Tb
         const size_t smem = (size_t)(16 + OUTER_NB) * OUTER_NB * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_reduce_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_reduce_w<16><<<ceil_div(nc, 16), 256, smem, s>>>(P, nsplit, pstride, OUTER_NB, Tb, trans, nc, Wh, Wl, ldw,
-                                                          split);
+        pdl_launch(k_reduce_w<16>, dim3(ceil_div(nc, 16)), dim3(256), smem, s, P, nsplit, pstride, (int)OUTER_NB, Tb, trans,
+                   nc, Wh, Wl, ldw, split);
     } else {
         const size_t smem = (size_t)(4 + OUTER_NB) * OUTER_NB * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_reduce_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_reduce_w<4><<<ceil_div(nc, 4), 256, smem, s>>>(P, nsplit, pstride, OUTER_NB, Tb, trans, nc, Wh, Wl, ldw,
-                                                        split);
+        pdl_launch(k_reduce_w<4>, dim3(ceil_div(nc, 4)), dim3(256), smem, s, P, nsplit, pstride, (int)OUTER_NB, Tb, trans,
+                   nc, Wh, Wl, ldw, split);
     }
 }
 
@@ -937,6 +941,8 @@ static void reduce_w(const float *P, int nsplit, size_t pstride, const float *Tb
 __global__ void __launch_bounds__(256)
 k_sum_splits(const float *__restrict__ P, int nsplit, size_t pstride, int n, float *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int e = blockIdx.x * 256 + threadIdx.x;
     if (e >= n) return;
     float v[8];
@@ -958,6 +964,8 @@ k_sum_splits(const float *__restrict__ P, int nsplit, size_t pstride, int n, flo
 __global__ void __launch_bounds__(256, 1)
 k_outer_T(const float *__restrict__ Tw32, const float *__restrict__ G, int nr, float *__restrict__ Tb)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ float sm[];
     float *Ts = sm;                                  // 128 x 128 column-major
     float *Pm = sm + OUTER_NB * OUTER_NB;            // 96 x 32 scratch
@@ -1133,8 +1141,8 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
     const int ncl = min(IC, nc - cg0);                 // columns of this group
     C += (size_t)cg0 * ldc;
     const int r0 = crank * chunk, r1 = min(r0 + chunk, L), R = max(0, r1 - r0);
-    asm volatile("griddepcontrol.wait;" ::: "memory");             // previous kernel's results
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    pdl_wait();                                         // previous kernel's results
+    pdl_trigger();
     // staging: rows over threads, columns unrolled (no index division)
     for (int r = tid; r < R; r += 256) {
         const int gr = r0 + r;
@@ -1381,7 +1389,7 @@ static int tc_mode(GemmPrec p) { return p == GemmPrec::FP32 ? TCM_TF32X3 : TCM_T
 static void prep_v(const float *X, int ldx, int L, int nr, OuterWs &w, int split, cudaStream_t s)
 {
     ProfScope ps(K_LARFB_AUX, s);
-    k_prep_v<<<ceil_div(w.ldv, 32), 256, 0, s>>>(X, ldx, L, nr, w.V, w.Vl, w.ldv, w.Vt, w.Vtl, split);
+    pdl_launch(k_prep_v, dim3(ceil_div(w.ldv, 32)), dim3(256), 0, s, X, ldx, L, nr, w.V, w.Vl, w.ldv, w.Vt, w.Vtl, split);
 }
 
 // C (L x Nc, ldc) <- (I - V X V^T) C for the prepared outer block, X = Tb^T
@@ -1441,14 +1449,15 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     if (rc) return rc;
     {
         ProfScope ps(K_LARFB_AUX, s);
-        k_sum_splits<<<OUTER_NB * OUTER_NB / 256, 256, 0, s>>>(w.P, nsplit, pstride, OUTER_NB * OUTER_NB, w.G);
+        pdl_launch(k_sum_splits, dim3(OUTER_NB * OUTER_NB / 256), dim3(256), 0, s, (const float *)w.P, nsplit, pstride,
+                   (int)(OUTER_NB * OUTER_NB), w.G);
     }
     {
         ProfScope ps(K_LARFB_AUX, s);
         const size_t smem = (size_t)(2 * OUTER_NB * OUTER_NB + 96 * 32) * 4;
         static bool attr = false;
         if (!attr) { cudaFuncSetAttribute(k_outer_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
-        k_outer_T<<<1, 256, smem, s>>>(Tw32, w.G, nr, Tb);
+        pdl_launch(k_outer_T, dim3(1), dim3(256), smem, s, Tw32, (const float *)w.G, nr, Tb);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
@@ -1477,6 +1486,8 @@ __global__ void __launch_bounds__(256)
 k_tfull_prod(const float *__restrict__ Tf, int ldt, const float *__restrict__ Xt, int J0, int KC, int nkc,
              float *__restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     const int ti = blockIdx.x, kc = blockIdx.y;
     const int i0 = ti * TF_TI;
     const int k1 = min((kc + 1) * KC, J0);
@@ -1533,6 +1544,8 @@ __global__ void __launch_bounds__(256)
 k_tfull_reduce(const float *__restrict__ part, int J0, int nr, int KC, int nkc, const float *__restrict__ Tb,
                float *__restrict__ Tf, int ldt)
 {
+    pdl_wait();
+    pdl_trigger();
     const int ti = blockIdx.x, tid = threadIdx.x;
     if (ti * TF_TI >= J0) {
         if (blockIdx.y) return;

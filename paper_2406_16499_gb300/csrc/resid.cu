@@ -30,6 +30,8 @@ __global__ void __launch_bounds__(256)
 k_dual_gemv(const double *__restrict__ A, int lda, int rows, int cols, const double *__restrict__ x,
             const double *__restrict__ r, double *__restrict__ pAx, double *__restrict__ pAtr)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double red[8][RB + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int rb = blockIdx.x, cb = blockIdx.y;
@@ -82,7 +84,7 @@ void dual_gemv(const double *A, int lda, int rows, int cols, const double *x, co
     if (rows <= 0 || cols <= 0) return;
     dim3 grid(ceil_div(rows, RB), ceil_div(cols, CB));
     ProfScope ps(K_DUAL_GEMV, s);
-    k_dual_gemv<<<grid, 256, 0, s>>>(A, lda, rows, cols, x, r, part_Ax, part_Atr);
+    pdl_launch(k_dual_gemv, grid, dim3(256), 0, s, A, lda, rows, cols, x, r, part_Ax, part_Atr);
 }
 
 // ------------------------------------------------------------------ finalize --
@@ -105,6 +107,8 @@ k_resid_finalize(int n0, int n1, int n2, int n3, int n4, int n5,
                  double *__restrict__ f1, double *__restrict__ f2, double *__restrict__ f3,
                  double *__restrict__ normpart)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double red[8][6];
     double sq[6] = {0, 0, 0, 0, 0, 0};
     const int total = n0 + n1 + n2 + n3 + n4 + n5;
@@ -156,6 +160,8 @@ k_resid_finalize(int n0, int n1, int n2, int n3, int n4, int n5,
 
 __global__ void k_norm_final(const double *__restrict__ normpart, int nb, double *__restrict__ norms2)
 {
+    pdl_wait();
+    pdl_trigger();
     if (threadIdx.x < 6) {
         double s = 0.0;
         for (int b = 0; b < nb; b++) s += normpart[(size_t)b * 6 + threadIdx.x];
@@ -178,9 +184,9 @@ void lse_resid_finalize(int m, int n, int p, const double *b, const double *d, c
     const int total = m + p + n + n + m + p;
     const int nb = finalize_blocks(total);
     ProfScope ps(K_FINALIZE, s);
-    k_resid_finalize<0><<<nb, 256, 0, s>>>(m, p, n, n, m, p, b, d, x, r, v, pAx, ncbA, pAtr, nrbA, pBx, ncbB,
+    pdl_launch(k_resid_finalize<0>, dim3(nb), dim3(256), 0, s, m, p, n, n, m, p, b, d, x, r, v, pAx, ncbA, pAtr, nrbA, pBx, ncbB,
                                            pBtv, nrbB, f1, f2, f3, normpart);
-    k_norm_final<<<1, 32, 0, s>>>(normpart, nb, norms2);
+    pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
 }
 
 void gls_resid_finalize(int n, int m, int p, const double *d, const double *x, const double *y,
@@ -191,9 +197,9 @@ void gls_resid_finalize(int n, int m, int p, const double *d, const double *x, c
     const int total = p + n + m + m + p + n;
     const int nb = finalize_blocks(total);
     ProfScope ps(K_FINALIZE, s);
-    k_resid_finalize<1><<<nb, 256, 0, s>>>(p, n, m, m, p, n, d, nullptr, x, y, z, pWx, ncbW, pWtz, nrbW, pVy,
+    pdl_launch(k_resid_finalize<1>, dim3(nb), dim3(256), 0, s, p, n, m, m, p, n, d, nullptr, x, y, z, pWx, ncbW, pWtz, nrbW, pVy,
                                            ncbV, pVtz, nrbV, f1, f2, f3, normpart);
-    k_norm_final<<<1, 32, 0, s>>>(normpart, nb, norms2);
+    pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
 }
 
 } // namespace mpir

@@ -473,6 +473,8 @@ int vapply(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, const
 template <typename T>
 __global__ void k_vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, int rb, T beta)
 {
+    pdl_wait();
+    pdl_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         T v = alpha * a[ra ? n - 1 - i : i];
@@ -485,7 +487,7 @@ void vcomb(T *out, int n, const T *a, int ra, T alpha, const T *b, int rb, T bet
 {
     if (n <= 0) return;
     ProfScope ps(K_ELEMWISE, s);
-    k_vcomb<T><<<ceil_div(n, 256), 256, 0, s>>>(out, n, a, ra, alpha, b, rb, beta);
+    pdl_launch(k_vcomb<T>, dim3(ceil_div(n, 256)), dim3(256), 0, s, out, n, a, ra, alpha, b, rb, beta);
 }
 
 __global__ void k_mask_lower(double *M, int ld, int rows, int cols, int off)

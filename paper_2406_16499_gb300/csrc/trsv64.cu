@@ -119,6 +119,8 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
     const int s0 = crank * slice;
     const int s1 = min(s0 + slice, n);
     const int i = s0 + tid;                                  // this thread's row
+    pdl_wait();                                              // x and Dinv come from earlier kernels
+    pdl_trigger();
     for (int r = s0 + tid; r < s1; r += T64_THREADS) xs[r - s0] = x[r];
     const int nblk = ceil_div(n, 64);
     {
@@ -236,13 +238,15 @@ int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaS
     cfg.blockDim = dim3(T64_THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = cs;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // waits in-kernel
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     ProfScope ps(K_TRSV, s);
     cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;

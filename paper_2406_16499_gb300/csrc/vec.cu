@@ -645,6 +645,8 @@ __global__ void __launch_bounds__(256)
 k_gemv_n(const TS *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
          T beta, T *__restrict__ y, int upper_mask, int diag_off)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ T red[8][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int i = blockIdx.x * 32 + lane;
@@ -669,6 +671,8 @@ __global__ void __launch_bounds__(256)
 k_gemv_t(const TS *__restrict__ M, int ld, int rows, int cols, T alpha, const T *__restrict__ x,
          T beta, T *__restrict__ y, int upper_mask, int diag_off)
 {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (j >= cols) return;
@@ -688,10 +692,10 @@ int gemv_mixed(const TS *M, int ld, int rows, int cols, int trans, T alpha, cons
     if ((!trans && rows <= 0) || (trans && cols <= 0)) return 0;
     ProfScope ps(K_GEMV, s);
     if (!trans) {
-        k_gemv_n<TS, T><<<ceil_div(rows, 32), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
+        pdl_launch(k_gemv_n<TS, T>, dim3(ceil_div(rows, 32)), dim3(256), 0, s, M, ld, rows, cols, alpha, x, beta, y, upper_mask,
                                                         diag_off);
     } else {
-        k_gemv_t<TS, T><<<ceil_div(cols, 8), 256, 0, s>>>(M, ld, rows, cols, alpha, x, beta, y, upper_mask,
+        pdl_launch(k_gemv_t<TS, T>, dim3(ceil_div(cols, 8)), dim3(256), 0, s, M, ld, rows, cols, alpha, x, beta, y, upper_mask,
                                                        diag_off);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
@@ -710,6 +714,8 @@ template <typename Ts, typename Td>
 __global__ void k_vcopy(const Ts *__restrict__ src, Td *__restrict__ dst, int n, double scale, int rev,
                         const double *__restrict__ dscale)
 {
+    pdl_wait();
+    pdl_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     const double g = dscale ? scale * dscale[0] : scale;
     if (i < n) dst[i] = (Td)(g * (double)src[rev ? n - 1 - i : i]);
@@ -719,6 +725,8 @@ __global__ void __launch_bounds__(256)
 k_pow2_normalizer(const double *__restrict__ u, int nu, double a1, const double *__restrict__ w, int nw,
                   double a2, double *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double red[8];
     double mx = 0.0;
     for (int i = threadIdx.x; i < nu; i += 256) mx = fmax(mx, fabs(a1 * u[i]));
@@ -739,12 +747,14 @@ void pow2_normalizer(const double *u, int nu, double a1, const double *w, int nw
                      cudaStream_t s)
 {
     ProfScope ps(K_NORM, s);
-    k_pow2_normalizer<<<1, 256, 0, s>>>(u, nu, a1, w, nw, a2, out);
+    pdl_launch(k_pow2_normalizer, dim3(1), dim3(256), 0, s, u, nu, a1, w, nw, a2, out);
 }
 
 template <typename Ts>
 __global__ void k_vaxpy(const Ts *__restrict__ src, double *__restrict__ dst, int n, double scale, int rev)
 {
+    pdl_wait();
+    pdl_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) dst[i] += scale * (double)src[rev ? n - 1 - i : i];
 }
@@ -754,7 +764,7 @@ void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s,
 {
     if (n <= 0) return;
     ProfScope ps(K_ELEMWISE, s);
-    k_vcopy<Ts, Td><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev, dscale);
+    pdl_launch(k_vcopy<Ts, Td>, dim3(ceil_div(n, 256)), dim3(256), 0, s, src, dst, n, scale, rev, dscale);
 }
 
 template <typename Ts>
@@ -762,7 +772,7 @@ void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_
 {
     if (n <= 0) return;
     ProfScope ps(K_ELEMWISE, s);
-    k_vaxpy<Ts><<<ceil_div(n, 256), 256, 0, s>>>(src, dst, n, scale, rev);
+    pdl_launch(k_vaxpy<Ts>, dim3(ceil_div(n, 256)), dim3(256), 0, s, src, dst, n, scale, rev);
 }
 
 void vzero(void *dst, size_t bytes, cudaStream_t s)

@@ -37,6 +37,8 @@ template <typename TS, typename T, int MODE>
 __global__ void __launch_bounds__(256)
 k_wy_coldot(const TS *__restrict__ A, int lda, int ncol, int len, const T *__restrict__ v, T *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * 8 + (threadIdx.x >> 5);
     if (j >= ncol) return;
@@ -69,6 +71,8 @@ template <typename TS, typename T, int MODE>
 __global__ void __launch_bounds__(WY_RT)
 k_wy_rowprod(const TS *__restrict__ A, int lda, int nrow, int ncol, const T *__restrict__ w, T *__restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i0 = blockIdx.x * WY_RT, c0 = blockIdx.y * WY_CC;
     if (!wy_chunk_valid<MODE>(i0, c0, nrow, ncol)) return;
     __shared__ T ws[WY_CC];
@@ -98,6 +102,8 @@ template <typename T, int MODE>
 __global__ void __launch_bounds__(256)
 k_wy_final(const T *__restrict__ part, int nrow, int ncol, T *__restrict__ x)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * 256 + threadIdx.x;
     if (i >= nrow) return;
     const int i0 = (i / WY_RT) * WY_RT;
@@ -132,26 +138,26 @@ int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int 
     const int nch = ceil_div(K, WY_CC);
     {
         ProfScope ps(K_VEC_APPLY, s);
-        k_wy_coldot<TS, T, 0><<<ceil_div(K, 8), 256, 0, s>>>(V, ldv, K, M, x, y);
+        pdl_launch(k_wy_coldot<TS, T, 0>, dim3(ceil_div(K, 8)), dim3(256), 0, s, V, ldv, K, M, x, y);
     }
     if (trans) {
         ProfScope ps(K_VEC_APPLY, s);
-        k_wy_coldot<TS, T, 1><<<ceil_div(K, 8), 256, 0, s>>>(Tf, ldt, K, K, y, wp);
+        pdl_launch(k_wy_coldot<TS, T, 1>, dim3(ceil_div(K, 8)), dim3(256), 0, s, Tf, ldt, K, K, y, wp);
     } else {
         {
             ProfScope ps(K_VEC_APPLY, s);
-            k_wy_rowprod<TS, T, 1><<<dim3(ceil_div(K, WY_RT), nch), WY_RT, 0, s>>>(Tf, ldt, K, K, y, part);
+            pdl_launch(k_wy_rowprod<TS, T, 1>, dim3(ceil_div(K, WY_RT), nch), dim3(WY_RT), 0, s, Tf, ldt, K, K, y, part);
         }
         ProfScope ps(K_VEC_APPLY, s);
-        k_wy_final<T, 1><<<ceil_div(K, 256), 256, 0, s>>>(part, K, K, wp);
+        pdl_launch(k_wy_final<T, 1>, dim3(ceil_div(K, 256)), dim3(256), 0, s, part, K, K, wp);
     }
     {
         ProfScope ps(K_VEC_APPLY, s);
-        k_wy_rowprod<TS, T, 0><<<dim3(ceil_div(M, WY_RT), nch), WY_RT, 0, s>>>(V, ldv, M, K, wp, part);
+        pdl_launch(k_wy_rowprod<TS, T, 0>, dim3(ceil_div(M, WY_RT), nch), dim3(WY_RT), 0, s, V, ldv, M, K, wp, part);
     }
     {
         ProfScope ps(K_VEC_APPLY, s);
-        k_wy_final<T, 0><<<ceil_div(M, 256), 256, 0, s>>>(part, M, K, x);
+        pdl_launch(k_wy_final<T, 0>, dim3(ceil_div(M, 256)), dim3(256), 0, s, part, M, K, x);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
