@@ -1146,15 +1146,15 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
     // staging: rows over threads, columns unrolled (no index division)
     for (int r = tid; r < R; r += 256) {
         const int gr = r0 + r;
-#pragma unroll 8
-        for (int c = 0; c < NB; c++) {
-            float v = 0.f;
-            if (c < kb) v = gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f);
-            Vc[(size_t)r * IV_LD + c] = v;
-        }
-#pragma unroll 8
-        for (int c = 0; c < IC; c++)
-            Cc[r + (size_t)c * rp] = c < ncl ? C[idx2(gr, c, ldc)] : 0.f;
+        float v[NB], cv[IC];
+#pragma unroll
+        for (int c = 0; c < NB; c++) v[c] = (c < kb && gr > c) ? V[idx2(gr, c, ldv)] : 0.f;
+#pragma unroll
+        for (int c = 0; c < IC; c++) cv[c] = c < ncl ? C[idx2(gr, c, ldc)] : 0.f;
+#pragma unroll
+        for (int c = 0; c < NB; c++) Vc[(size_t)r * IV_LD + c] = (c < kb && gr == c) ? 1.f : v[c];
+#pragma unroll
+        for (int c = 0; c < IC; c++) Cc[r + (size_t)c * rp] = cv[c];
     }
     for (int e = tid; e < NB * NB; e += 256) {
         const int k = e & (NB - 1), a = e / NB;
@@ -1194,14 +1194,18 @@ k_inner_cl_s(const float *__restrict__ V, int ldv, int kb, int L, float *__restr
     __syncthreads();
     for (int e = tid; e < IC * NB; e += 256) pw[e] = (pg[0][e] + pg[1][e]) + (pg[2][e] + pg[3][e]);
     cluster.sync();
-    // cluster sum, 16-byte remote loads in rank order
+    // cluster sum, 16-byte remote loads in rank order (all issued before the
+    // first add: cs <= 16)
     {
         const int e = tid;                              // IC * NB / 4 == 256 vectors
+        float4 v[16];
+#pragma unroll
+        for (int q = 0; q < 16; q++)
+            v[q] = q < cs ? reinterpret_cast<const float4 *>(cluster.map_shared_rank(pw, q))[e]
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-        for (int q = 0; q < cs; q++) {
-            const float4 v = reinterpret_cast<const float4 *>(cluster.map_shared_rank(pw, q))[e];
-            sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
-        }
+#pragma unroll
+        for (int q = 0; q < 16; q++) { sum.x += v[q].x; sum.y += v[q].y; sum.z += v[q].z; sum.w += v[q].w; }
         reinterpret_cast<float4 *>(Sx)[e] = sum;
     }
     __syncthreads();
