@@ -121,7 +121,7 @@ size_t dinv_elems(int N);
 template <typename TS, typename T>
 void invert_diag64(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s);
 template <typename T>
-int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaStream_t s);
+int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *err, cudaStream_t s);
 // Mixed precision (factors stored as TS, arithmetic and vectors in T).
 template <typename TS, typename T>
 int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,

@@ -412,6 +412,7 @@ int check_dev_flags(mpir_ctx *h)
     if (flags[0] & DEV_ERR_BARRIER_TIMEOUT) return set_err(h, MPIR_DEVICE_TIMEOUT, "device barrier timed out");
     if (flags[0] & 4) return set_err(h, MPIR_DEVICE_TIMEOUT, "tensor-core pipeline wait timed out");
     if (flags[0] & 8) return set_err(h, MPIR_DEVICE_TIMEOUT, "panel message wait timed out");
+    if (flags[0] & 16) return set_err(h, MPIR_DEVICE_TIMEOUT, "triangular solve message wait timed out");
     if (flags[1] & 1) return set_err(h, MPIR_SINGULAR_R, "R has a zero diagonal entry");
     if (flags[1] & 2) return set_err(h, MPIR_SINGULAR_T, "triangular factor has a zero diagonal entry");
     return 0;
@@ -442,7 +443,7 @@ int tsolve(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cu
 {
     if constexpr (sizeof(T) == 4) {
         if (trsv64_ok(n, sizeof(T))) {
-            const int rc = trsv64<T>(U, ldu, n, trans, x, Dinv, s);
+            const int rc = trsv64<T>(U, ldu, n, trans, x, Dinv, sc.err, s);
             if (rc >= 0) return rc;
             return trsv_upper<T>(U, ldu, n, trans, x, sc, s, nullptr);
         }
@@ -749,7 +750,7 @@ int trsv_d(const T *U, int ldu, int n, int trans, double *x, const DevScratch &s
 {
     if constexpr (sizeof(T) == 4) {
         if (trsv64_ok(n, sizeof(T))) {
-            const int rc = trsv64<double>(U, ldu, n, trans, x, Dinv, s);
+            const int rc = trsv64<double>(U, ldu, n, trans, x, Dinv, sc.err, s);
             if (rc >= 0) return rc;
             return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s, nullptr);
         }

@@ -10,12 +10,13 @@
 //      column of U (independent of x, in flight during the rest of the step);
 //      the CTA owning the next block loads that block's inverse;
 //   2. the owner forms x_blk = op(D) b_blk (two warps, D staged in shared
-//      memory one step earlier) and writes x_blk into every CTA's shared
-//      memory through distributed shared memory;
-//   3. one cluster barrier (release / acquire) makes x_blk visible;
+//      memory one step earlier) and sends x_blk into every CTA's shared
+//      memory with st.async (one message slot and one mbarrier per step);
+//   3. every CTA waits for that step's message on its own mbarrier;
 //   4. every thread subtracts its row's 64-term product.
-// One cluster barrier per 64 rows; no dependent global-memory read on the
-// critical path.
+// No cluster-wide barrier per step: the chain from one block's owner to the
+// next is one distributed-shared-memory hop, and no dependent global-memory
+// read sits on it.
 #include "common.cuh"
 #include "kernels.h"
 #include "mpir.h"
@@ -103,15 +104,62 @@ __device__ __forceinline__ void t64_store_d(T *Ds, int trans, int tid, const T (
     }
 }
 
+constexpr uint32_t T64_POLL_LIMIT = 1u << 26;
+
+__device__ __forceinline__ uint32_t t64_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint32_t t64_mapa(uint32_t addr, int rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void t64_st_async(uint32_t raddr, float v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
+                 ::"r"(raddr), "r"(__float_as_uint(v)), "r"(rbar) : "memory");
+}
+
+__device__ __forceinline__ void t64_st_async(uint32_t raddr, double v, uint32_t rbar)
+{
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
+                 ::"r"(raddr), "l"(__double_as_longlong(v)), "r"(rbar) : "memory");
+}
+
+// Bounded poll of phase 0 of a step's mbarrier; false on timeout.
+__device__ __forceinline__ bool t64_wait(uint32_t bar)
+{
+    for (uint32_t it = 0; it < T64_POLL_LIMIT; it++) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done)
+                     : "r"(bar)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Message passing instead of a cluster barrier per step: the owner of block
+// t sends x_t with st.async into slot t of every CTA, which signals that
+// CTA's mbarrier t (one slot and one barrier per step, so a fast owner never
+// overwrites a slot a slower CTA still reads).  Every CTA waits only for the
+// x block it needs next; the chain from one owner to the next is one
+// distributed-shared-memory hop.
 template <typename T>
 __global__ void __launch_bounds__(T64_THREADS, 1)
 k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
-         const T *__restrict__ Dinv)
+         const T *__restrict__ Dinv, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *xs = reinterpret_cast<T *>(smem_raw);                 // slice
-    T *Ds = xs + slice;                                      // [2][64 * 65]
-    __shared__ __align__(16) T xin[2][64];
+    const int nblk = ceil_div(n, 64);
+    unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smem_raw);     // [nblk]
+    T *xin = reinterpret_cast<T *>(smem_raw + 8 * ((nblk + 1) & ~1));            // [nblk][64]
+    T *Ds = xin + (size_t)nblk * 64;                                             // [2][64 * 65]
+    T *xs = Ds + 2 * T64_DS;                                                     // slice
     cg::cluster_group cluster = cg::this_cluster();
     const int cs = (int)cluster.num_blocks();
     const int crank = (int)cluster.block_rank();
@@ -119,10 +167,17 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
     const int s0 = crank * slice;
     const int s1 = min(s0 + slice, n);
     const int i = s0 + tid;                                  // this thread's row
+    for (int t = tid; t < nblk; t += T64_THREADS) {
+        const uint32_t b = t64_smem(&mbar[t]);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"((uint32_t)(64 * sizeof(T)))
+                     : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    cluster.sync();                                          // every barrier armed before any message
     pdl_wait();                                              // x and Dinv come from earlier kernels
     pdl_trigger();
     for (int r = s0 + tid; r < s1; r += T64_THREADS) xs[r - s0] = x[r];
-    const int nblk = ceil_div(n, 64);
     {
         const int b0 = trans ? 0 : nblk - 1;
         if (crank == (b0 * 64) / slice) {
@@ -132,12 +187,14 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
         }
     }
     __syncthreads();
+    bool timed_out = false;
     for (int t = 0; t < nblk; t++) {
         const int blk = trans ? t : nblk - 1 - t;
         const int r0 = blk * 64;
         const int bs = min(64, n - r0);
         const int par = t & 1;
         const int owner = r0 / slice;
+        T *xt = xin + (size_t)t * 64;
         // 1. this row's entries of the block column (rows still unsolved)
         const int lo = trans ? max(s0, r0 + bs) : s0;
         const int hi = trans ? s1 : min(s1, r0);
@@ -166,28 +223,27 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
         const bool stage = nb >= 0 && crank == (nb * 64) / slice;
         T dn[8];
         if (stage) t64_load_d(Dinv, nb, tid, dn);
-        // 2. the owner forms x_blk and publishes it to every CTA
+        // 2. the owner forms x_t and sends it to every CTA (itself included)
         if (crank == owner && tid < 64) {
             const T *Dr = Ds + par * T64_DS + tid * 65;
             T acc = T(0);
 #pragma unroll 16
             for (int k = 0; k < 64; k++) acc = fma(Dr[k], k < bs ? xs[r0 + k - s0] : T(0), acc);
             const T xv = tid < bs ? acc : T(0);
-            for (int r = 0; r < cs; r++) *cluster.map_shared_rank(&xin[par][tid], r) = xv;
+            const uint32_t dst = t64_smem(&xt[tid]), bar = t64_smem(&mbar[t]);
+            for (int r = 0; r < cs; r++) t64_st_async(t64_mapa(dst, r), xv, t64_mapa(bar, r));
         }
-        // 3. x_blk visible everywhere: only the owner's stores need release
-        // ordering; every CTA acquires
-        if (crank == owner) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-        else asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-        // 4. update the unsolved rows (x_blk read as 16-byte vectors); the
+        // 3. wait for x_t (after a timeout the remaining steps skip their
+        // waits; the error flag reports it)
+        if (!timed_out && !t64_wait(t64_smem(&mbar[t]))) timed_out = true;
+        // 4. update the unsolved rows (x_t read as 16-byte vectors); the
         // owner stores its block
         if (va) {
             T d0 = T(0), d1 = T(0);
             if constexpr (sizeof(T) == 4) {
 #pragma unroll
                 for (int q = 0; q < 16; q++) {
-                    const float4 xv = reinterpret_cast<const float4 *>(&xin[par][0])[q];
+                    const float4 xv = reinterpret_cast<const float4 *>(xt)[q];
                     d0 = fma((T)u[4 * q], (T)xv.x, d0);
                     d1 = fma((T)u[4 * q + 1], (T)xv.y, d1);
                     d0 = fma((T)u[4 * q + 2], (T)xv.z, d0);
@@ -196,43 +252,45 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
             } else {
 #pragma unroll
                 for (int q = 0; q < 32; q++) {
-                    const double2 xv = reinterpret_cast<const double2 *>(&xin[par][0])[q];
+                    const double2 xv = reinterpret_cast<const double2 *>(xt)[q];
                     d0 = fma((T)u[2 * q], (T)xv.x, d0);
                     d1 = fma((T)u[2 * q + 1], (T)xv.y, d1);
                 }
             }
             xs[i - s0] -= d0 + d1;
         }
-        if (crank == owner && tid < bs) xs[r0 + tid - s0] = xin[par][tid];
+        if (crank == owner && tid < bs) xs[r0 + tid - s0] = xt[tid];
         if (stage) t64_store_d(Ds + (par ^ 1) * T64_DS, trans, tid, dn);
         __syncthreads();
     }
     for (int r = s0 + tid; r < s1; r += T64_THREADS) x[r] = xs[r - s0];
-    cluster.sync();   // no CTA leaves while others may still write into it
+    if (timed_out && tid == 0) atomicOr(err, 16);
+    cluster.sync();   // no CTA leaves while messages to it may be in flight
 }
 
 template <typename T>
-int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaStream_t s)
+int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *err, cudaStream_t s)
 {
     if (n <= 0) return 0;
     if (n > T64_MAXN || ldu % 4 || ((uintptr_t)U & 15)) return -1;
     auto kern = k_trsv64<T>;
     const int nblk = ceil_div(n, 64);
     int want = nblk < 16 ? nblk : 16;                      // as many CTAs as the cluster allows
-    const size_t dsz = 2 * T64_DS * sizeof(T);
+    // barriers, one message slot per step, two staged inverses, the owned rows
+    const size_t fixed = 8 * (size_t)((nblk + 1) & ~1) + (size_t)nblk * 64 * sizeof(T) + 2 * T64_DS * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(dsz + T64_THREADS * sizeof(T)));
+                             (int)(8 * 128 + 128 * 64 * sizeof(T) + 2 * T64_DS * sizeof(T) + T64_THREADS * sizeof(T)));
         attr = true;
     }
-    int cs = cluster_size_for((const void *)kern, T64_THREADS, dsz + (size_t)ceil_div(nblk, want) * 64 * sizeof(T),
+    int cs = cluster_size_for((const void *)kern, T64_THREADS, fixed + (size_t)ceil_div(nblk, want) * 64 * sizeof(T),
                               want);
     const int slice = ceil_div(nblk, cs) * 64;
     if (slice > T64_THREADS) return -1;
     cs = ceil_div(n, slice);
-    const size_t smem = dsz + (size_t)slice * sizeof(T);
+    const size_t smem = fixed + (size_t)slice * sizeof(T);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(T64_THREADS, 1, 1);
@@ -248,13 +306,13 @@ int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, cudaS
     cfg.attrs = at;
     cfg.numAttrs = 2;
     ProfScope ps(K_TRSV, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv, err);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
 template void invert_diag64<float, float>(const float *, int, int, float *, int *, cudaStream_t);
 template void invert_diag64<float, double>(const float *, int, int, double *, int *, cudaStream_t);
-template int trsv64<float>(const float *, int, int, int, float *, const float *, cudaStream_t);
-template int trsv64<double>(const float *, int, int, int, double *, const double *, cudaStream_t);
+template int trsv64<float>(const float *, int, int, int, float *, const float *, int *, cudaStream_t);
+template int trsv64<double>(const float *, int, int, int, double *, const double *, int *, cudaStream_t);
 
 } // namespace mpir
