@@ -374,8 +374,11 @@ int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam
  * features (start vector: splitmix64 of seed 0x5EED + j mapped to [-1, 1)),
  * run the network, and solve with the most probable class (GMRES classes
  * fall back to classical IR where the block-diagonal preconditioner does not
- * apply); escalation to FP64 stays the fallback.  info->fact_used /
- * refine_used report the choice.  NULL params removes the selector. */
+ * apply); escalation to FP64 stays the fallback.  The FP32 factorization
+ * runs on the handle's stream while the features and the network run on a
+ * stream of their own; it is kept when an FP32 class is chosen and
+ * discarded otherwise.  info->fact_used / refine_used report the choice.
+ * NULL params removes the selector. */
 int mpir_selector_set(mpir_handle h, const float *params, const float *mean, const float *scale);
 
 /* Library version string. */

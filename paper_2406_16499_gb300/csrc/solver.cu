@@ -265,6 +265,9 @@ struct mpir_ctx {
     float sel_mean[16], sel_scale[16];
     double *sel_s = nullptr;     // start vector of the condition sketch
     size_t sel_s_len = 0;
+    cudaStream_t sel_stream = nullptr;   // features + MLP, beside the speculative FP32 factorization
+    cudaEvent_t sel_ev = nullptr;
+    float *sel_host = nullptr;   // pinned: features (16) and class probabilities (8)
 };
 
 namespace {
@@ -920,7 +923,7 @@ double bd_alpha(const mpir_opts &o, double lead, double fro, double other)
 template <typename T>
 int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
                    const double *d, double *x, double *y, double *z_out, const mpir_opts &o, int fact,
-                   mpir_info *info)
+                   mpir_info *info, bool factored = false)
 {
     cudaStream_t s = h->stream;
     const bool gm = o.refine == MPIR_GMRES;
@@ -932,9 +935,11 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
         if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
         RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
     }
-    cudaEventRecord(h->ev[0], s);
-    RC(gls_factor_impl<T>(h, n, m, p, W, ldw, V, ldv, fact));
-    cudaEventRecord(h->ev[1], s);
+    if (!factored) {              // else factored (and timed) by the caller
+        cudaEventRecord(h->ev[0], s);
+        RC(gls_factor_impl<T>(h, n, m, p, W, ldw, V, ldv, fact));
+        cudaEventRecord(h->ev[1], s);
+    }
     GlsWs<T> w = gls_layout<T>(h->ws, n, m, p, nullptr);
     BDScratch bs{};
     if (gm) bs = bd_layout((char *)h->ws + main_bytes, NG, o.restart, mx);
@@ -1297,7 +1302,7 @@ int lse_gmres_correction(mpir_ctx *h, LseWs<T> &w, BDScratch &b, const double *A
 template <typename T>
 int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
                    const double *b, const double *d, double *x, double *r_out, double *v_out,
-                   const mpir_opts &o, int fact, mpir_info *info)
+                   const mpir_opts &o, int fact, mpir_info *info, bool factored = false)
 {
     cudaStream_t s = h->stream;
     const bool gm = o.refine == MPIR_GMRES;
@@ -1309,9 +1314,11 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
         if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
         RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
     }
-    cudaEventRecord(h->ev[0], s);
-    RC(lse_factor_impl<T>(h, m, n, p, A, lda, B, ldb, fact));
-    cudaEventRecord(h->ev[1], s);
+    if (!factored) {              // else factored (and timed) by the caller
+        cudaEventRecord(h->ev[0], s);
+        RC(lse_factor_impl<T>(h, m, n, p, A, lda, B, ldb, fact));
+        cudaEventRecord(h->ev[1], s);
+    }
     LseWs<T> w = lse_layout<T>(h->ws, m, n, p, nullptr);
     BDScratch bs{};
     if (gm) bs = bd_layout((char *)h->ws + main_bytes, NG, o.restart, mx);
@@ -1512,6 +1519,12 @@ int mpir_destroy(mpir_handle h)
         cudaEventDestroy(h->la_a);
         cudaEventDestroy(h->la_b);
     }
+    if (h->sel_stream) {
+        cudaStreamSynchronize(h->sel_stream);
+        cudaStreamDestroy(h->sel_stream);
+        cudaEventDestroy(h->sel_ev);
+    }
+    if (h->sel_host) cudaFreeHost(h->sel_host);
     if (h->sel) cudaFree(h->sel);
     if (h->sel_s) cudaFree(h->sel_s);
     for (int i = 0; i < 8; i++) cudaEventDestroy(h->ev[i]);
@@ -1637,27 +1650,51 @@ static int sel_start_vector(mpir_ctx *h, int len)
     return 0;
 }
 
-// Features -> standardized input -> MLP -> most probable class.
-static int sel_choose(mpir_ctx *h, int kind, int d0, int d1, int d2, const double *M1, int ld1, const double *M2,
-                      int ld2, const double *v1, int n1, const double *v2, int n2, int *cls)
+// Features -> standardized input -> MLP -> most probable class, on the
+// selector's own stream: sel_begin enqueues the features (and their copy to
+// pinned host memory) and returns at once, so the caller can put the
+// likeliest path (the FP32 factorization) on the GPU meanwhile; sel_end
+// waits for the features, runs the MLP and returns the class.
+static int sel_begin(mpir_ctx *h, int kind, int d0, int d1, int d2, const double *M1, int ld1, const double *M2,
+                     int ld2, const double *v1, int n1, const double *v2, int n2)
 {
     if (!h->sel) return set_err(h, MPIR_UNSUPPORTED, "fact = MPIR_AUTO needs a selector (mpir_selector_set)");
     const int R = kind == 0 ? d0 + d2 : d0, C = kind == 0 ? d1 : d1 + d2;
     RC(sel_start_vector(h, C));
     RC(ensure_rws(h, sizeof(double) * features_ws_doubles(R, C)));
-    float *X = h->sel + MLP_PARAMS, *prob = X + 16, *feat = prob + 8;
-    cudaStream_t s = h->stream;
-    RC(features_launch(kind, d0, d1, d2, M1, ld1, M2, ld2, h->sel_s, v1, n1, v2, n2, 16, (double *)h->rws, feat, s));
-    float f[16], pr[8];
-    cudaMemcpyAsync(f, feat, sizeof(f), cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "selector features");
-    for (int q = 0; q < 16; q++) f[q] = (f[q] - h->sel_mean[q]) / h->sel_scale[q];
-    cudaMemcpyAsync(X, f, sizeof(f), cudaMemcpyHostToDevice, s);
-    RC(mlp_forward(h->sel, X, 1, prob, s));
-    cudaMemcpyAsync(pr, prob, sizeof(float) * NCLASS, cudaMemcpyDeviceToHost, s);
-    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "selector forward");
+    if (!h->sel_stream) {
+        if (cudaStreamCreateWithFlags(&h->sel_stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->sel_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaMallocHost(&h->sel_host, 32 * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_err(h, MPIR_CUDA_ERROR, "selector: stream or pinned buffer");
+        }
+    }
+    // the selector stream starts where the caller's stream is (inputs ready)
+    cudaEventRecord(h->sel_ev, h->stream);
+    cudaStreamWaitEvent(h->sel_stream, h->sel_ev, 0);
+    float *feat = h->sel + MLP_PARAMS + 16 + 8;
+    cudaStream_t ss = h->sel_stream;
+    RC(features_launch(kind, d0, d1, d2, M1, ld1, M2, ld2, h->sel_s, v1, n1, v2, n2, 16, (double *)h->rws, feat, ss));
+    cudaMemcpyAsync(h->sel_host, feat, 16 * sizeof(float), cudaMemcpyDeviceToHost, ss);
+    cudaEventRecord(h->sel_ev, ss);
+    return 0;
+}
+
+static int sel_end(mpir_ctx *h, int *cls)
+{
+    float *X = h->sel + MLP_PARAMS, *prob = X + 16;
+    cudaStream_t ss = h->sel_stream;
+    if (cudaEventSynchronize(h->sel_ev) != cudaSuccess) return cuda_check(h, "selector features");
+    float f[16];
+    for (int q = 0; q < 16; q++) f[q] = (h->sel_host[q] - h->sel_mean[q]) / h->sel_scale[q];
+    std::memcpy(h->sel_host + 16, f, 16 * sizeof(float));
+    cudaMemcpyAsync(X, h->sel_host + 16, sizeof(f), cudaMemcpyHostToDevice, ss);
+    RC(mlp_forward(h->sel, X, 1, prob, ss));
+    cudaMemcpyAsync(h->sel_host, prob, sizeof(float) * NCLASS, cudaMemcpyDeviceToHost, ss);
+    if (cudaStreamSynchronize(ss) != cudaSuccess) return cuda_check(h, "selector forward");
     int best = 0;
-    for (int c = 1; c < NCLASS; c++) if (pr[c] > pr[best]) best = c;
+    for (int c = 1; c < NCLASS; c++) if (h->sel_host[c] > h->sel_host[best]) best = c;
     *cls = best;
     return 0;
 }
@@ -1679,18 +1716,31 @@ int lse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, cons
     mpir_opts o;
     fill_opts(opts, &o);
     if (info) std::memset(info, 0, sizeof(*info));
+    bool factored = false;
     if (o.fact == MPIR_AUTO) {
+        // the FP32 factors are computed while the selector decides; they are
+        // kept when it picks an FP32 class
+        size_t mb = 0;
+        lse_layout<float>(nullptr, m, n, p, &mb);
+        const int NG = m + p + n, mx = std::max(std::max(m, n), std::max(p, 1));
+        RC(ensure_ws(h, mb + (m >= n ? bd_bytes(NG, std::min(o.restart, GMRES_MAX_RESTART), mx) : 0)));
+        RC(sel_begin(h, 0, m, n, p, A, lda, B, std::max(ldb, 1), b, m, d, p));
+        cudaEventRecord(h->ev[0], h->stream);
+        RC(lse_factor_impl<float>(h, m, n, p, A, lda, B, ldb, MPIR_FP32));
+        cudaEventRecord(h->ev[1], h->stream);
         int cls = 0;
-        RC(sel_choose(h, 0, m, n, p, A, lda, B, std::max(ldb, 1), b, m, d, p, &cls));
+        RC(sel_end(h, &cls));
         sel_apply(cls, &o);
         if (o.refine == MPIR_GMRES && m < n) o.refine = MPIR_CLASSICAL;
+        factored = o.fact == MPIR_FP32;
     }
     if (o.fact < MPIR_BF16 || o.fact > MPIR_FP64) return set_err(h, -14, "illegal opts->fact");
     int fact = o.fact;
     int esc = 0, st = 0;
     while (true) {
         st = is_fp64(fact) ? lse_solve_once<double>(h, m, n, p, A, lda, B, ldb, b, d, x, r, v, o, fact, info)
-                           : lse_solve_once<float>(h, m, n, p, A, lda, B, ldb, b, d, x, r, v, o, fact, info);
+                           : lse_solve_once<float>(h, m, n, p, A, lda, B, ldb, b, d, x, r, v, o, fact, info,
+                                                   factored && esc == 0);
         if (st == MPIR_OK || st < 0 || st == MPIR_CUDA_ERROR || st == MPIR_UNSUPPORTED ||
             st == MPIR_DEVICE_TIMEOUT || !o.escalate || o.refine == MPIR_DIRECT)
             break;
@@ -1712,18 +1762,29 @@ int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, cons
     mpir_opts o;
     fill_opts(opts, &o);
     if (info) std::memset(info, 0, sizeof(*info));
+    bool factored = false;
     if (o.fact == MPIR_AUTO) {
+        size_t mb = 0;
+        gls_layout<float>(nullptr, n, m, p, &mb);
+        const int NG = p + n + m, mx = std::max(std::max(m, n), std::max(p, 1));
+        RC(ensure_ws(h, mb + (n <= p ? bd_bytes(NG, std::min(o.restart, GMRES_MAX_RESTART), mx) : 0)));
+        RC(sel_begin(h, 1, n, m, p, W, ldw, V, ldv, d, n, nullptr, 0));
+        cudaEventRecord(h->ev[0], h->stream);
+        RC(gls_factor_impl<float>(h, n, m, p, W, ldw, V, ldv, MPIR_FP32));
+        cudaEventRecord(h->ev[1], h->stream);
         int cls = 0;
-        RC(sel_choose(h, 1, n, m, p, W, ldw, V, ldv, d, n, nullptr, 0, &cls));
+        RC(sel_end(h, &cls));
         sel_apply(cls, &o);
         if (o.refine == MPIR_GMRES && n > p) o.refine = MPIR_CLASSICAL;
+        factored = o.fact == MPIR_FP32;
     }
     if (o.fact < MPIR_BF16 || o.fact > MPIR_FP64) return set_err(h, -14, "illegal opts->fact");
     int fact = o.fact;
     int esc = 0, st = 0;
     while (true) {
         st = is_fp64(fact) ? gls_solve_once<double>(h, n, m, p, W, ldw, V, ldv, d, x, y, z, o, fact, info)
-                           : gls_solve_once<float>(h, n, m, p, W, ldw, V, ldv, d, x, y, z, o, fact, info);
+                           : gls_solve_once<float>(h, n, m, p, W, ldw, V, ldv, d, x, y, z, o, fact, info,
+                                                   factored && esc == 0);
         if (st == MPIR_OK || st < 0 || st == MPIR_CUDA_ERROR || st == MPIR_UNSUPPORTED ||
             st == MPIR_DEVICE_TIMEOUT || !o.escalate || o.refine == MPIR_DIRECT)
             break;

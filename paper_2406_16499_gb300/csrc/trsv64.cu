@@ -38,7 +38,8 @@ size_t dinv_elems(int N)
 
 // Inverses of the 64 x 64 diagonal blocks of an upper triangular N x N U
 // (one CTA of 64 threads per block, thread j solves column j by back
-// substitution; a partial last block is padded with the identity).  Zero
+// substitution in registers; a partial last block is padded with the
+// identity).  Zero
 // pivot -> bit 1 of *status.  Dinv block b at Dinv + 4096 b, column-major.
 template <typename TS, typename T>
 __global__ void __launch_bounds__(64)
@@ -46,7 +47,6 @@ k_invert_diag64(const TS *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, 
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *Us = reinterpret_cast<T *>(smem_raw);     // [64][65]
-    T *Xs = Us + T64_DS;                         // [64][65]
     const int j = threadIdx.x, blk = blockIdx.x, r0 = blk * 64;
     for (int c = 0; c < 64; c++) {
         T v;
@@ -55,26 +55,29 @@ k_invert_diag64(const TS *__restrict__ U, int ldu, int N, T *__restrict__ Dinv, 
         Us[j * 65 + c] = v;
     }
     __syncthreads();
+    // column j in registers, recurrence fully unrolled (x[k] = 0 for k > j, so
+    // the full-length sums are exact); U entries are warp-broadcast reads
+    T xr[64];
+    bool zero_pivot = false;
+#pragma unroll
     for (int i = 63; i >= 0; i--) {
-        T val = T(0);
-        if (i <= j) {
-            T sum = i == j ? T(1) : T(0);
-            for (int k = i + 1; k <= j; k++) sum = fma(-Us[i * 65 + k], Xs[k * 65 + j], sum);
-            const T d = Us[i * 65 + i];
-            if (d == T(0)) atomicOr(status, 2);
-            val = sum / d;
-        }
-        Xs[i * 65 + j] = val;
+        T sum = i == j ? T(1) : T(0);
+#pragma unroll
+        for (int k = i + 1; k < 64; k++) sum = fma(-Us[i * 65 + k], xr[k], sum);
+        const T d = Us[i * 65 + i];
+        zero_pivot |= d == T(0);
+        xr[i] = i <= j ? sum / d : T(0);
     }
-    __syncthreads();
-    for (int i = 0; i < 64; i++) Dinv[(size_t)blk * 4096 + i + 64 * j] = Xs[i * 65 + j];
+    if (zero_pivot && j == 0) atomicOr(status, 2);
+#pragma unroll
+    for (int i = 0; i < 64; i++) Dinv[(size_t)blk * 4096 + i + 64 * j] = xr[i];
 }
 
 template <typename TS, typename T>
 void invert_diag64(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s)
 {
     if (N <= 0) return;
-    const size_t smem = 2 * T64_DS * sizeof(T);
+    const size_t smem = T64_DS * sizeof(T);
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_invert_diag64<TS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
