@@ -107,7 +107,7 @@ __device__ __forceinline__ void t64_store_d(T *Ds, int trans, int tid, const T (
     }
 }
 
-constexpr uint32_t T64_POLL_LIMIT = 1u << 26;
+constexpr uint32_t T64_POLL_LIMIT = 1u << 24;
 
 __device__ __forceinline__ uint32_t t64_smem(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -130,13 +130,15 @@ __device__ __forceinline__ void t64_st_async(uint32_t raddr, double v, uint32_t 
                  ::"r"(raddr), "l"(__double_as_longlong(v)), "r"(rbar) : "memory");
 }
 
-// Bounded poll of phase 0 of a step's mbarrier; false on timeout.
+// Bounded wait on phase 0 of a step's mbarrier; false on timeout.  try_wait
+// parks the warp between polls, so waiting warps do not crowd the shared-
+// memory pipe that the owner's products and messages use.
 __device__ __forceinline__ bool t64_wait(uint32_t bar)
 {
     for (uint32_t it = 0; it < T64_POLL_LIMIT; it++) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done)
                      : "r"(bar)
