@@ -154,7 +154,11 @@ __device__ __forceinline__ bool t64_wait(uint32_t bar)
 // overwrites a slot a slower CTA still reads).  Every CTA waits only for the
 // x block it needs next; the chain from one owner to the next is one
 // distributed-shared-memory hop.
-template <typename T>
+// TPR threads per row (2 when a CTA owns at most 256 rows): each holds 64 /
+// TPR entries of the row's block column and the partial products meet by a
+// lane-pair shuffle, so every per-row chain (and the FP64 work of the FP64
+// variant) is spread over twice the warps.
+template <typename T, int TPR>
 __global__ void __launch_bounds__(T64_THREADS, 1)
 k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
          const T *__restrict__ Dinv, int *__restrict__ err)
@@ -171,7 +175,9 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
     const int tid = threadIdx.x;
     const int s0 = crank * slice;
     const int s1 = min(s0 + slice, n);
-    const int i = s0 + tid;                                  // this thread's row
+    constexpr int CW = 64 / TPR;                             // block-column entries per thread
+    const int i = s0 + tid / TPR;                            // this thread's row
+    const int c0 = (tid % TPR) * CW;                         // its first column in the block
     for (int t = tid; t < nblk; t += T64_THREADS) {
         const uint32_t b = t64_smem(&mbar[t]);
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(b) : "memory");
@@ -204,24 +210,24 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
         const int lo = trans ? max(s0, r0 + bs) : s0;
         const int hi = trans ? s1 : min(s1, r0);
         const bool va = i >= lo && i < hi;
-        float u[64];
+        float u[CW];
         if (trans) {
-            // U(r0 + c, i): 64 consecutive entries of column i (16-byte aligned
-            // when bs = 64: r0, ldu multiples of 4)
-            const float *col = U + (size_t)i * ldu + r0;
+            // U(r0 + c0 + c, i): consecutive entries of column i (16-byte
+            // aligned when bs = 64: r0, c0, ldu multiples of 4)
+            const float *col = U + (size_t)i * ldu + r0 + c0;
             if (va && bs == 64) {
 #pragma unroll
-                for (int q = 0; q < 16; q++) {
+                for (int q = 0; q < CW / 4; q++) {
                     const float4 v = *reinterpret_cast<const float4 *>(col + 4 * q);
                     u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
                 }
             } else {
 #pragma unroll
-                for (int c = 0; c < 64; c++) u[c] = (va && c < bs) ? col[c] : 0.f;
+                for (int c = 0; c < CW; c++) u[c] = (va && c0 + c < bs) ? col[c] : 0.f;
             }
         } else {
 #pragma unroll
-            for (int c = 0; c < 64; c++) u[c] = (va && c < bs) ? U[idx2(i, r0 + c, ldu)] : 0.f;
+            for (int c = 0; c < CW; c++) u[c] = (va && c0 + c < bs) ? U[idx2(i, r0 + c0 + c, ldu)] : 0.f;
         }
         // next block's inverse, loaded by its owner
         const int nb = t + 1 < nblk ? (trans ? t + 1 : nblk - 2 - t) : -1;
@@ -229,40 +235,49 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
         T dn[8];
         if (stage) t64_load_d(Dinv, nb, tid, dn);
         // 2. the owner forms x_t and sends it to every CTA (itself included)
-        if (crank == owner && tid < 64) {
-            const T *Dr = Ds + par * T64_DS + tid * 65;
+        if (crank == owner && tid < 64 * TPR) {
+            const int row = tid / TPR, k0 = (tid % TPR) * CW;
+            const T *Dr = Ds + par * T64_DS + row * 65 + k0;
+            const T *xb = xs + r0 - s0 + k0;
             T acc = T(0);
 #pragma unroll 16
-            for (int k = 0; k < 64; k++) acc = fma(Dr[k], k < bs ? xs[r0 + k - s0] : T(0), acc);
-            const T xv = tid < bs ? acc : T(0);
-            const uint32_t dst = t64_smem(&xt[tid]), bar = t64_smem(&mbar[t]);
-            for (int r = 0; r < cs; r++) t64_st_async(t64_mapa(dst, r), xv, t64_mapa(bar, r));
+            for (int k = 0; k < CW; k++) acc = fma(Dr[k], k0 + k < bs ? xb[k] : T(0), acc);
+            if (TPR == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            if (tid % TPR == 0) {
+                const T xv = row < bs ? acc : T(0);
+                const uint32_t dst = t64_smem(&xt[row]), bar = t64_smem(&mbar[t]);
+                for (int r = 0; r < cs; r++) t64_st_async(t64_mapa(dst, r), xv, t64_mapa(bar, r));
+            }
         }
         // 3. wait for x_t (after a timeout the remaining steps skip their
         // waits; the error flag reports it)
         if (!timed_out && !t64_wait(t64_smem(&mbar[t]))) timed_out = true;
         // 4. update the unsolved rows (x_t read as 16-byte vectors); the
         // owner stores its block
-        if (va) {
+        {
             T d0 = T(0), d1 = T(0);
-            if constexpr (sizeof(T) == 4) {
+            if (va) {
+                if constexpr (sizeof(T) == 4) {
 #pragma unroll
-                for (int q = 0; q < 16; q++) {
-                    const float4 xv = reinterpret_cast<const float4 *>(xt)[q];
-                    d0 = fma((T)u[4 * q], (T)xv.x, d0);
-                    d1 = fma((T)u[4 * q + 1], (T)xv.y, d1);
-                    d0 = fma((T)u[4 * q + 2], (T)xv.z, d0);
-                    d1 = fma((T)u[4 * q + 3], (T)xv.w, d1);
-                }
-            } else {
+                    for (int q = 0; q < CW / 4; q++) {
+                        const float4 xv = reinterpret_cast<const float4 *>(xt + c0)[q];
+                        d0 = fma((T)u[4 * q], (T)xv.x, d0);
+                        d1 = fma((T)u[4 * q + 1], (T)xv.y, d1);
+                        d0 = fma((T)u[4 * q + 2], (T)xv.z, d0);
+                        d1 = fma((T)u[4 * q + 3], (T)xv.w, d1);
+                    }
+                } else {
 #pragma unroll
-                for (int q = 0; q < 32; q++) {
-                    const double2 xv = reinterpret_cast<const double2 *>(xt)[q];
-                    d0 = fma((T)u[2 * q], (T)xv.x, d0);
-                    d1 = fma((T)u[2 * q + 1], (T)xv.y, d1);
+                    for (int q = 0; q < CW / 2; q++) {
+                        const double2 xv = reinterpret_cast<const double2 *>(xt + c0)[q];
+                        d0 = fma((T)u[2 * q], (T)xv.x, d0);
+                        d1 = fma((T)u[2 * q + 1], (T)xv.y, d1);
+                    }
                 }
             }
-            xs[i - s0] -= d0 + d1;
+            T dsum = d0 + d1;
+            if (TPR == 2) dsum += __shfl_xor_sync(0xffffffffu, dsum, 1);
+            if (va && tid % TPR == 0) xs[i - s0] -= dsum;
         }
         if (crank == owner && tid < bs) xs[r0 + tid - s0] = xt[tid];
         if (stage) t64_store_d(Ds + (par ^ 1) * T64_DS, trans, tid, dn);
@@ -278,23 +293,27 @@ int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *
 {
     if (n <= 0) return 0;
     if (n > T64_MAXN || ldu % 4 || ((uintptr_t)U & 15)) return -1;
-    auto kern = k_trsv64<T>;
     const int nblk = ceil_div(n, 64);
     int want = nblk < 16 ? nblk : 16;                      // as many CTAs as the cluster allows
     // barriers, one message slot per step, two staged inverses, the owned rows
     const size_t fixed = 8 * (size_t)((nblk + 1) & ~1) + (size_t)nblk * 64 * sizeof(T) + 2 * T64_DS * sizeof(T);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(8 * 128 + 128 * 64 * sizeof(T) + 2 * T64_DS * sizeof(T) + T64_THREADS * sizeof(T)));
+        for (auto kk : {k_trsv64<T, 1>, k_trsv64<T, 2>}) {
+            cudaFuncSetAttribute(kk, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(8 * 128 + 128 * 64 * sizeof(T) + 2 * T64_DS * sizeof(T) + T64_THREADS * sizeof(T)));
+        }
         attr = true;
     }
-    int cs = cluster_size_for((const void *)kern, T64_THREADS, fixed + (size_t)ceil_div(nblk, want) * 64 * sizeof(T),
-                              want);
+    int cs = cluster_size_for((const void *)k_trsv64<T, 1>, T64_THREADS,
+                              fixed + (size_t)ceil_div(nblk, want) * 64 * sizeof(T), want);
     const int slice = ceil_div(nblk, cs) * 64;
     if (slice > T64_THREADS) return -1;
     cs = ceil_div(n, slice);
+    // two threads per row when a CTA owns at most 256 rows (same block size
+    // and shared memory, so the cluster size above holds for both)
+    auto kern = slice <= T64_THREADS / 2 ? k_trsv64<T, 2> : k_trsv64<T, 1>;
     const size_t smem = fixed + (size_t)slice * sizeof(T);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
