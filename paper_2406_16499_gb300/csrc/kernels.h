@@ -73,9 +73,11 @@ struct TfullJob {
 };
 size_t geqrf_la_ws_bytes(int M, int N);
 size_t geqrf_ws_bytes(int M, int N);
+// kmax >= 0 stops after min(M, N, kmax) reflectors; the remaining columns
+// are still updated (so [W | V] with kmax = m leaves R over Q^T V).
 template <typename T>
 int geqrf(T *A, int lda, int M, int N, T *tau, T *Tw, T *Tw128, GemmPrec prec, void *ws, int *err,
-          cudaStream_t s, const TfullJob *tf = nullptr);
+          cudaStream_t s, const TfullJob *tf = nullptr, int kmax = -1);
 
 // C (M x Nc, ldc) <- Z^T C (trans = 1) or Z C (trans = 0) for the reflector
 // set left in (V, ldv, K reflectors, Tw, Tw128) by geqrf on an M-row matrix.

@@ -1630,12 +1630,13 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
 }
 
 template <typename T>
-static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cudaStream_t s)
+static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cudaStream_t s, int kmax)
 {
     constexpr int NB = panel_nb<T>();
-    const int k = M < N ? M : N;
+    int k = M < N ? M : N;
+    if (kmax >= 0 && kmax < k) k = kmax;
     for (int j0 = 0; j0 < k; j0 += NB) {
-        const int ncols = N - j0 < NB ? N - j0 : NB;
+        const int ncols = k - j0 < NB ? k - j0 : NB;
         const int L = M - j0;
         T *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
         int rc = launch_panel<T>(A, lda, M, j0, ncols, tau, Twb, err, s);
@@ -1653,9 +1654,9 @@ static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cuda
 
 template <>
 int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *, int *err,
-                  cudaStream_t s, const TfullJob *)
+                  cudaStream_t s, const TfullJob *, int kmax)
 {
-    return geqrf_simt<double>(A, lda, M, N, tau, Tw, err, s);
+    return geqrf_simt<double>(A, lda, M, N, tau, Tw, err, s, kmax);
 }
 
 // Two-level QR, FP32 storage: 32-wide register panels inside 128-wide
@@ -1663,10 +1664,11 @@ int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, dou
 // the tensor cores.
 template <>
 int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *Tw128, GemmPrec prec, void *ws,
-                 int *err, cudaStream_t s, const TfullJob *tf)
+                 int *err, cudaStream_t s, const TfullJob *tf, int kmax)
 {
     constexpr int NB = 32;
-    const int k = M < N ? M : N;
+    int k = M < N ? M : N;
+    if (kmax >= 0 && kmax < k) k = kmax;
     if (lda % 4) return MPIR_UNSUPPORTED;
     const int mode = tc_mode(prec);
     // look-ahead: critical path on tf->crit, wide trailing updates on s
@@ -1690,7 +1692,7 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
     bool wide_pending = false;
     for (int J0 = 0, b = 0; J0 < k; J0 += OUTER_NB, b++) {
         OuterWs &w = wv[b & 1];
-        const int ncolsO = N - J0 < OUTER_NB ? N - J0 : OUTER_NB;
+        const int ncolsO = k - J0 < OUTER_NB ? k - J0 : OUTER_NB;
         const int L = M - J0;
         const int nr = ncolsO < L ? ncolsO : L;
         for (int j0 = J0; j0 < J0 + nr; j0 += NB) {

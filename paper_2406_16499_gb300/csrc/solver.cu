@@ -136,29 +136,28 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
     w.m = m; w.n = n; w.p = p; w.q = n - p; w.kA = std::min(m, n);
     const int mx = std::max(std::max(m, n), std::max(p, 1));
     w.ldBt = rup32(std::max(n, 1)); w.ldX = rup32(std::max(n, 1)); w.ldAt = rup32(std::max(m, 1));
-    w.Bt = c.take<T>((size_t)w.ldBt * std::max(p, 1));
+    // B~ and X side by side: one factorization call leaves R~ over Q~^T X
+    w.Bt = c.take<T>((size_t)w.ldBt * std::max(p + m, 1));
+    w.X = w.Bt + (size_t)w.ldBt * p;
     w.tauB = c.take<T>(std::max(p, 1));
     w.TwB = c.take<T>((size_t)std::max(ceil_div(p, NB), 1) * NB * NB);
     w.Tw128B = c.take<T>((size_t)std::max(ceil_div(p, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
-    w.X = c.take<T>((size_t)w.ldX * std::max(m, 1));
     w.At = c.take<T>((size_t)w.ldAt * n);
     w.tauA = c.take<T>(std::max(w.kA, 1));
     w.TwA = c.take<T>((size_t)std::max(ceil_div(w.kA, NB), 1) * NB * NB);
     w.Tw128A = c.take<T>((size_t)std::max(ceil_div(w.kA, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
     w.DinvB = c.take<T>(dinv_elems(p));
     w.DinvA = c.take<T>(dinv_elems(w.kA));
-    if (sizeof(T) == 4)   // look-ahead factorizations of B~ and A Q^T, the apply to A
-        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_la_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
-                                               geqrf_la_ws_bytes(m, n)));
+    if (sizeof(T) == 4)   // look-ahead factorizations of [B~ X] and A Q^T
+        w.gws = c.take<unsigned char>(std::max(geqrf_la_ws_bytes(n, p + m), geqrf_la_ws_bytes(m, n)));
     else
-        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(n, m)),
-                                               geqrf_ws_bytes(m, n)));
+        w.gws = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, p + m), geqrf_ws_bytes(m, n)));
     w.ldtB = rup32(std::max(p, 1)); w.ldtA = rup32(std::max(w.kA, 1));
     if (sizeof(T) == 4) {
         w.TfB = c.take<T>((size_t)w.ldtB * std::max(p, 1));
         w.TfA = c.take<T>((size_t)w.ldtA * std::max(w.kA, 1));
         w.wy = c.take<unsigned char>(std::max(wy_apply_ws_bytes(n, p), wy_apply_ws_bytes(m, w.kA)));
-        w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, p), geqrf_ws_bytes(m, n)));
+        w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, p + m), geqrf_ws_bytes(m, n)));
     }
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.ty = c.take<T>(mx); w.tq = c.take<T>(mx);
     w.tb = c.take<T>(mx); w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
@@ -186,29 +185,28 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
     w.n = n; w.m = m; w.p = p; w.L = n - m; w.o = p - n + m; w.kC = std::min(n, p);
     const int mx = std::max(std::max(m, n), std::max(p, 1));
     w.ldW = rup32(n); w.ldC = rup32(n); w.ldCt = rup32(std::max(p, 1));
-    w.Wf = c.take<T>((size_t)w.ldW * std::max(m, 1));
+    // W and C side by side: one factorization call leaves R over Q^T V
+    w.Wf = c.take<T>((size_t)w.ldW * std::max(m + p, 1));
+    w.Cf = w.Wf + (size_t)w.ldW * m;
     w.tauW = c.take<T>(std::max(m, 1));
     w.TwW = c.take<T>((size_t)std::max(ceil_div(m, NB), 1) * NB * NB);
     w.Tw128W = c.take<T>((size_t)std::max(ceil_div(m, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
-    w.Cf = c.take<T>((size_t)w.ldC * std::max(p, 1));
     w.Ct = c.take<T>((size_t)w.ldCt * n);
     w.tauC = c.take<T>(std::max(w.kC, 1));
     w.TwC = c.take<T>((size_t)std::max(ceil_div(w.kC, NB), 1) * NB * NB);
     w.Tw128C = c.take<T>((size_t)std::max(ceil_div(w.kC, OUTER_NB), 1) * OUTER_NB * OUTER_NB);
     w.DinvW = c.take<T>(dinv_elems(m));
     w.DinvC = c.take<T>(dinv_elems(w.kC));
-    if (sizeof(T) == 4)   // look-ahead factorizations of W and C~, the apply to V
-        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_la_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
-                                               geqrf_la_ws_bytes(p, n)));
+    if (sizeof(T) == 4)   // look-ahead factorizations of [W V] and C~
+        w.gws = c.take<unsigned char>(std::max(geqrf_la_ws_bytes(n, m + p), geqrf_la_ws_bytes(p, n)));
     else
-        w.gws = c.take<unsigned char>(std::max(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(n, p)),
-                                               geqrf_ws_bytes(p, n)));
+        w.gws = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, m + p), geqrf_ws_bytes(p, n)));
     w.ldtW = rup32(std::max(m, 1)); w.ldtC = rup32(std::max(w.kC, 1));
     if (sizeof(T) == 4) {
         w.TfW = c.take<T>((size_t)w.ldtW * std::max(m, 1));
         w.TfC = c.take<T>((size_t)w.ldtC * std::max(w.kC, 1));
         w.wy = c.take<unsigned char>(std::max(wy_apply_ws_bytes(n, m), wy_apply_ws_bytes(p, w.kC)));
-        w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, m), geqrf_ws_bytes(p, n)));
+        w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, m + p), geqrf_ws_bytes(p, n)));
     }
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.th = c.take<T>(mx); w.tg = c.take<T>(mx);
     w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
@@ -527,12 +525,12 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     h->fs.fro1 = std::sqrt(h->hbuf[1]);
     h->fs.fro2 = std::sqrt(h->hbuf[3]);
     const GemmPrec gp = gemm_prec(fact);
-    // QR of W (Lemma 4.6, first factorization)
+    // QR of W (Lemma 4.6, first factorization) with C = Q^T V formed by the
+    // same trailing updates: [W V] factored through its first m columns
     mconvert<double, T>(W, ldw, w.Wf, w.ldW, n, m, 0, 0, 0, sW, s);
-    RC(geqrf<T>(w.Wf, w.ldW, n, m, w.tauW, w.TwW, w.Tw128W, gp, w.gws, h->sc.err, s, tfjob(h, w.TfW, w.ldtW, w.gws2)));
-    // C = Q^T V
     mconvert<double, T>(V, ldv, w.Cf, w.ldC, n, p, 0, 0, 0, sV, s);
-    RC(apply_reflectors_left<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, 1, w.Cf, w.ldC, p, gp, w.gws, h->sc.err, s));
+    RC(geqrf<T>(w.Wf, w.ldW, n, m + p, w.tauW, w.TwW, w.Tw128W, gp, w.gws, h->sc.err, s,
+                tfjob(h, w.TfW, w.ldtW, w.gws2), m));
     // RQ of C as QR of C~ = P_p C^T P_n
     mconvert<T, T>(w.Cf, w.ldC, w.Ct, w.ldCt, p, n, 1, 1, 1, 1.0, s);
     RC(geqrf<T>(w.Ct, w.ldCt, p, n, w.tauC, w.TwC, w.Tw128C, gp, w.gws, h->sc.err, s, tfjob(h, w.TfC, w.ldtC, w.gws2)));
@@ -1035,12 +1033,13 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     h->fs.fro1 = std::sqrt(h->hbuf[1]);
     h->fs.fro2 = std::sqrt(h->hbuf[3]);
     const GemmPrec gp = gemm_prec(fact);
-    // RQ of B as QR of B~ = P_n B^T P_p (Lemma 4.5, first factorization)
+    // RQ of B as QR of B~ = P_n B^T P_p (Lemma 4.5, first factorization),
+    // with X = Q~^T P_n A^T = P_n (A Q^T)^T formed by the same trailing
+    // updates: [B~ X] factored through its first p columns
     mconvert<double, T>(B, ldb, w.Bt, w.ldBt, n, p, 1, 1, 1, sB, s);
-    RC(geqrf<T>(w.Bt, w.ldBt, n, p, w.tauB, w.TwB, w.Tw128B, gp, w.gws, h->sc.err, s, tfjob(h, w.TfB, w.ldtB, w.gws2)));
-    // X = Q~^T P_n A^T = P_n (A Q^T)^T
     mconvert<double, T>(A, lda, w.X, w.ldX, n, m, 1, 1, 0, sA, s);
-    RC(apply_reflectors_left<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, 1, w.X, w.ldX, m, gp, w.gws, h->sc.err, s));
+    RC(geqrf<T>(w.Bt, w.ldBt, n, p + m, w.tauB, w.TwB, w.Tw128B, gp, w.gws, h->sc.err, s,
+                tfjob(h, w.TfB, w.ldtB, w.gws2), p));
     // A Q^T = X^T P_n, then its QR  (A Q^T = Z T)
     mconvert<T, T>(w.X, w.ldX, w.At, w.ldAt, m, n, 1, 0, 1, 1.0, s);
     RC(geqrf<T>(w.At, w.ldAt, m, n, w.tauA, w.TwA, w.Tw128A, gp, w.gws, h->sc.err, s, tfjob(h, w.TfA, w.ldtA, w.gws2)));
