@@ -280,10 +280,11 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 #pragma unroll 4
                 for (int e = et; e < TC_TILE_B / 16; e += NCONV) {
                     float4 v = hi[e], h, l;
-                    h.x = tf32_round(v.x); l.x = v.x - h.x;
-                    h.y = tf32_round(v.y); l.y = v.y - h.y;
-                    h.z = tf32_round(v.z); l.z = v.z - h.z;
-                    h.w = tf32_round(v.w); l.w = v.w - h.w;
+                    // low parts rounded to nearest TF32 (the MMA would truncate them)
+                    h.x = tf32_round(v.x); l.x = tf32_round(v.x - h.x);
+                    h.y = tf32_round(v.y); l.y = tf32_round(v.y - h.y);
+                    h.z = tf32_round(v.z); l.z = tf32_round(v.z - h.z);
+                    h.w = tf32_round(v.w); l.w = tf32_round(v.w - h.w);
                     hi[e] = h;
                     lo[e] = l;
                 }

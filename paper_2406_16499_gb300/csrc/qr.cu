@@ -813,6 +813,16 @@ k_inner_cl(const float *__restrict__ V, int ldv, int kb, int L, float *__restric
 // ---------------------------------------------------------------------------
 // Outer (128-reflector) blocks, FP32 storage.
 //
+// Nearest TF32 value (the tensor cores read only a TF32 operand's top 19 bits;
+// rounding the low part of a hi/lo split, instead of letting the hardware
+// truncate it, halves the split's representation error to 2^-22 |a|).
+__device__ __forceinline__ float tf32_rn(float x)
+{
+    uint32_t u;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(x));
+    return __uint_as_float(u);
+}
+
 // k_prep_v: the unit lower trapezoid V of an outer block (rows j0.., columns
 // j0..j0+nr) in the layouts the tensor-core GEMMs read:
 //   V, Vlo   L x 128 column-major (ld ldv)  -- A operand of W = V^T C
@@ -843,7 +853,7 @@ k_prep_v(const float *__restrict__ X, int ldx, int L, int nr, float *__restrict_
             float h = v;
             if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v)); h = __uint_as_float(u); }
             Vh[idx2(gr, c, ldv)] = h;
-            if (split) Vl[idx2(gr, c, ldv)] = v - h;
+            if (split) Vl[idx2(gr, c, ldv)] = tf32_rn(v - h);
         }
     }
     // Vt / Vtlo: 128 x L, coalesced along the 128 columns of V
@@ -854,7 +864,7 @@ k_prep_v(const float *__restrict__ X, int ldx, int L, int nr, float *__restrict_
             float h = v;
             if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v)); h = __uint_as_float(u); }
             Vth[idx2(c, gr, OUTER_NB)] = h;
-            if (split) Vtl[idx2(c, gr, OUTER_NB)] = v - h;
+            if (split) Vtl[idx2(c, gr, OUTER_NB)] = tf32_rn(v - h);
         }
     }
 }
@@ -913,7 +923,7 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
         float h = w;
         if (split) { uint32_t u; asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(w)); h = __uint_as_float(u); }
         Wh[(size_t)(c0 + c) * ldw + i] = h;
-        if (split) Wl[(size_t)(c0 + c) * ldw + i] = w - h;
+        if (split) Wl[(size_t)(c0 + c) * ldw + i] = tf32_rn(w - h);
     }
 }
 
