@@ -20,6 +20,11 @@
  *    unless the refinement loop needs a host decision (the classical loop
  *    reads a 4-byte convergence flag back once per iteration).  The info
  *    struct is a HOST pointer and is complete when the call returns.
+ *    Internally a factorization also uses streams the handle owns (a
+ *    high-priority stream for the critical path, a side stream for the
+ *    aggregated compact-WY factors, one for the selector); before a call
+ *    returns, all of its work is ordered before the handle's stream's
+ *    subsequent work, so the caller sees one stream.
  *  - Return codes follow LAPACK's info: 0 success; -i argument i illegal
  *    (checked on the host before anything is launched); positive values
  *    are MPIR_* status codes below.
