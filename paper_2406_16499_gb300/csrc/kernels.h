@@ -70,6 +70,8 @@ struct TfullJob {
     void *ws2;
     cudaStream_t crit;
     cudaEvent_t la_a, la_b;
+    cudaStream_t aux;            // outer-block factor, beside the next columns' V^T C
+    cudaEvent_t ax_a, ax_b;
 };
 size_t geqrf_la_ws_bytes(int M, int N);
 size_t geqrf_ws_bytes(int M, int N);

@@ -1355,10 +1355,11 @@ static int inner_update(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
 
 // Scratch of the two-level factorization (FP32 path).
 struct OuterWs {
-    float *V, *Vl, *Vt, *Vtl, *P, *W, *Wl, *G, *innerP, *innerW;
+    float *V, *Vl, *Vt, *Vtl, *P, *W, *Wl, *G, *GP, *innerP, *innerW;
     int ldv;
     size_t pcap;
 };
+constexpr int GSPLIT = 24;               // split-K of the outer block's Gram matrix
 
 static constexpr int PSPLIT_CAP = 320;   // (column tiles x K splits) of W = V^T C
 
@@ -1380,6 +1381,7 @@ static OuterWs outer_layout(void *base, int M, int N, size_t *bytes)
     w.W = take((size_t)OUTER_NB * ncp);
     w.Wl = take((size_t)OUTER_NB * ncp);
     w.G = take((size_t)OUTER_NB * OUTER_NB);
+    w.GP = take((size_t)OUTER_NB * OUTER_NB * GSPLIT);
     w.innerP = take((size_t)ceil_div(M > 0 ? M : 1, INNER_ROWS) * 32 * INNER_MAXC * 2);
     w.innerW = take((size_t)32 * INNER_MAXC * 2);
     if (bytes) *bytes = (size_t)((off + 1023) & ~(uintptr_t)1023);
@@ -1406,23 +1408,24 @@ static void prep_v(const float *X, int ldx, int L, int nr, OuterWs &w, int split
     pdl_launch(k_prep_v, dim3(ceil_div(w.ldv, 32)), dim3(256), 0, s, X, ldx, L, nr, w.V, w.Vl, w.ldv, w.Vt, w.Vtl, split);
 }
 
-// C (L x Nc, ldc) <- (I - V X V^T) C for the prepared outer block, X = Tb^T
-// (trans) or Tb, on the tensor cores:  P = V^T C (split-K),  W = X sum P,
-// C -= V W.
-static int outer_apply(OuterWs &w, const float *Tb, int trans, int L, float *C, int ldc, int Nc, int mode,
-                       int *err, cudaStream_t s)
+struct OuterPlan {
+    int nsplit;
+    size_t pstride;
+};
+
+// Phase 1 of an outer update: P = V^T C (split-K partials), which does not
+// need the block's T factor.
+static int outer_apply_p1(OuterWs &w, int L, float *C, int ldc, int Nc, int mode, int *err, cudaStream_t s,
+                          OuterPlan *pl)
 {
+    pl->nsplit = 0;
     if (Nc <= 0 || L <= 0) return 0;
     const int split = mode == TCM_TF32X3;
-    CUtensorMap tV, tVl, tC, tVt, tVtl, tW, tWl;
+    CUtensorMap tV, tVl, tC;
     int rc = 0;
     rc |= tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     rc |= tmap_colmajor(&tC, C, L, Nc, ldc, OUTER_NB);
-    rc |= tmap_colmajor(&tVt, w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
-    rc |= tmap_colmajor(&tVtl, split ? w.Vtl : w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
-    rc |= tmap_colmajor(&tW, w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
-    rc |= tmap_colmajor(&tWl, split ? w.Wl : w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
     if (rc) return MPIR_UNSUPPORTED;
     const int ntn = ceil_div(Nc, OUTER_NB);
     const int ksteps = ceil_div(L, 32);
@@ -1435,14 +1438,43 @@ static int outer_apply(OuterWs &w, const float *Tb, int trans, int L, float *C, 
     // P[z] = V^T C  (M = 128 rows of V^T, N = Nc, K = L)
     rc = gemm_tc(mode, split, TCE_STORE, tV, tVl, tC, tC, 0, 0, 0, 0, OUTER_NB, Nc, L, w.P, OUTER_NB, pstride,
                  nsplit, err, s);
-    if (rc) return rc;
+    pl->nsplit = nsplit;
+    pl->pstride = pstride;
+    return rc;
+}
+
+// Phase 2: W = op(Tb) sum P, C -= V W.
+static int outer_apply_p2(OuterWs &w, const float *Tb, int trans, int L, float *C, int ldc, int Nc, int mode,
+                          const OuterPlan &pl, int *err, cudaStream_t s)
+{
+    if (Nc <= 0 || L <= 0) return 0;
+    const int split = mode == TCM_TF32X3;
+    CUtensorMap tVt, tVtl, tW, tWl;
+    int rc = 0;
+    rc |= tmap_colmajor(&tVt, w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
+    rc |= tmap_colmajor(&tVtl, split ? w.Vtl : w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
+    rc |= tmap_colmajor(&tW, w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
+    rc |= tmap_colmajor(&tWl, split ? w.Wl : w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
+    if (rc) return MPIR_UNSUPPORTED;
     {
         ProfScope ps(K_LARFB_AUX, s);
-        reduce_w(w.P, nsplit, pstride, Tb, trans, Nc, w.W, w.Wl, OUTER_NB, split, s);
+        reduce_w(w.P, pl.nsplit, pl.pstride, Tb, trans, Nc, w.W, w.Wl, OUTER_NB, split, s);
     }
     // C -= V W  (M = L, N = Nc, K = 128)
     rc = gemm_tc(mode, 0, TCE_SUB, tVt, tVtl, tW, tWl, 0, 0, 0, 0, L, Nc, OUTER_NB, C, ldc, 0, 1, err, s);
     return rc ? rc : (cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR);
+}
+
+// C (L x Nc, ldc) <- (I - V X V^T) C for the prepared outer block, X = Tb^T
+// (trans) or Tb, on the tensor cores:  P = V^T C (split-K),  W = X sum P,
+// C -= V W.
+static int outer_apply(OuterWs &w, const float *Tb, int trans, int L, float *C, int ldc, int Nc, int mode,
+                       int *err, cudaStream_t s)
+{
+    OuterPlan pl{};
+    int rc = outer_apply_p1(w, L, C, ldc, Nc, mode, err, s, &pl);
+    if (rc) return rc;
+    return outer_apply_p2(w, Tb, trans, L, C, ldc, Nc, mode, pl, err, s);
 }
 
 // G = V^T V of the prepared block, then the outer compact-WY factor Tb.
@@ -1454,16 +1486,18 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     if (rc) return MPIR_UNSUPPORTED;
     const int ksteps = ceil_div(L, 32);
-    int nsplit = ksteps < 24 ? ksteps : 24;
+    int nsplit = ksteps < GSPLIT ? ksteps : GSPLIT;
     if (nsplit < 1) nsplit = 1;
     const size_t pstride = (size_t)OUTER_NB * OUTER_NB;
-    // G = V^T V with both operands pre-split (w.V holds only the TF32 part)
-    rc = gemm_tc(mode, 0, TCE_STORE, tV, tVl, tV, tVl, 0, 0, 0, 0, OUTER_NB, OUTER_NB, L, w.P, OUTER_NB,
+    // G = V^T V with both operands pre-split (w.V holds only the TF32 part);
+    // its own partial buffer, so that it can run beside the next columns'
+    // V^T C
+    rc = gemm_tc(mode, 0, TCE_STORE, tV, tVl, tV, tVl, 0, 0, 0, 0, OUTER_NB, OUTER_NB, L, w.GP, OUTER_NB,
                  pstride, nsplit, err, s);
     if (rc) return rc;
     {
         ProfScope ps(K_LARFB_AUX, s);
-        pdl_launch(k_sum_splits, dim3(OUTER_NB * OUTER_NB / 256), dim3(256), 0, s, (const float *)w.P, nsplit, pstride,
+        pdl_launch(k_sum_splits, dim3(OUTER_NB * OUTER_NB / 256), dim3(256), 0, s, (const float *)w.GP, nsplit, pstride,
                    (int)(OUTER_NB * OUTER_NB), w.G);
     }
     {
@@ -1683,6 +1717,7 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
     const int mode = tc_mode(prec);
     // look-ahead: critical path on tf->crit, wide trailing updates on s
     const bool la = tf && tf->crit && tf->crit != s && tf->la_a && tf->la_b;
+    const bool ax = la && tf->aux && tf->ax_a && tf->ax_b;
     const size_t one = geqrf_ws_bytes(M, N);
     OuterWs wv[2] = {outer_layout(ws, M, N, nullptr),
                      outer_layout(la ? (char *)ws + one : ws, M, N, nullptr)};
@@ -1720,10 +1755,26 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
             }
         }
         const int Nc = N - J0 - ncolsO;
+        const int n1 = la ? (Nc < OUTER_NB ? Nc : OUTER_NB) : Nc;    // columns updated on the critical path
         float *Tb = Tw128 + (size_t)(J0 / OUTER_NB) * OUTER_NB * OUTER_NB;
         prep_v(A + idx2(J0, J0, lda), lda, L, nr, w, mode == TCM_TF32X3, cs);
-        int rc = outer_T(w, Tw + (size_t)(J0 / NB) * NB * NB, L, nr, Tb, mode, err, cs);
+        // the block's factor (Gram matrix and T) on the auxiliary stream while
+        // the critical path forms V^T C for the next columns, which needs no T
+        int rc = 0;
+        OuterPlan pl{};
+        cudaStream_t ts = ax ? tf->aux : cs;
+        if (ax) { cudaEventRecord(tf->ax_a, cs); cudaStreamWaitEvent(ts, tf->ax_a, 0); }
+        rc = outer_T(w, Tw + (size_t)(J0 / NB) * NB * NB, L, nr, Tb, mode, err, ts);
         if (rc) return rc;
+        if (ax) cudaEventRecord(tf->ax_b, ts);
+        if (Nc > 0) {
+            // the next block's columns (after the previous wide update has
+            // finished with them)
+            if (wide_pending) { cudaStreamWaitEvent(cs, tf->la_b, 0); wide_pending = false; }
+            rc = outer_apply_p1(w, L, A + idx2(J0, J0 + ncolsO, lda), lda, n1, mode, err, cs, &pl);
+            if (rc) return rc;
+        }
+        if (ax) cudaStreamWaitEvent(cs, tf->ax_b, 0);                 // T of this block ready
         if (tf && tf->Tf) {
             if (side) {
                 cudaEventRecord(tf->fork, cs);
@@ -1734,11 +1785,7 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
             if (rc) return rc;
         }
         if (Nc > 0) {
-            // the next block's columns first (critical path), after the
-            // previous wide update has finished with them
-            const int n1 = la ? (Nc < OUTER_NB ? Nc : OUTER_NB) : Nc;
-            if (wide_pending) { cudaStreamWaitEvent(cs, tf->la_b, 0); wide_pending = false; }
-            rc = outer_apply(w, Tb, 1, L, A + idx2(J0, J0 + ncolsO, lda), lda, n1, mode, err, cs);
+            rc = outer_apply_p2(w, Tb, 1, L, A + idx2(J0, J0 + ncolsO, lda), lda, n1, mode, pl, err, cs);
             if (rc) return rc;
             if (la && Nc > n1) {
                 cudaEventRecord(tf->la_a, cs);

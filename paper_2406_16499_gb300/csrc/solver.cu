@@ -257,6 +257,8 @@ struct mpir_ctx {
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaStream_t crit = nullptr;         // high-priority stream of the factorization's critical path
     cudaEvent_t la_a = nullptr, la_b = nullptr;
+    cudaStream_t aux = nullptr;          // outer-block factors beside the critical path
+    cudaEvent_t ax_a = nullptr, ax_b = nullptr;
     TfullJob tfj{};
     // learned selector: parameters and feature standardization (device), scratch
     float *sel = nullptr;        // params[MLP_PARAMS], X[16], prob[6], feat[16]
@@ -299,6 +301,13 @@ const TfullJob *tfjob(mpir_ctx *h, T *Tf, int ldt, void *ws2)
             cudaGetLastError();
             h->crit = nullptr;
         }
+        if (h->crit &&
+            (cudaStreamCreateWithPriority(&h->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->ax_a, cudaEventDisableTiming) != cudaSuccess ||
+             cudaEventCreateWithFlags(&h->ax_b, cudaEventDisableTiming) != cudaSuccess)) {
+            cudaGetLastError();
+            h->aux = nullptr;
+        }
     }
     h->tfj.Tf = reinterpret_cast<float *>(Tf);
     h->tfj.ldt = ldt;
@@ -309,6 +318,9 @@ const TfullJob *tfjob(mpir_ctx *h, T *Tf, int ldt, void *ws2)
     h->tfj.crit = h->crit;
     h->tfj.la_a = h->la_a;
     h->tfj.la_b = h->la_b;
+    h->tfj.aux = h->aux;
+    h->tfj.ax_a = h->ax_a;
+    h->tfj.ax_b = h->ax_b;
     return &h->tfj;
 }
 
@@ -323,6 +335,10 @@ void join_side(mpir_ctx *h, cudaStream_t s)
     if (h->crit) {
         cudaEventRecord(h->la_a, h->crit);
         cudaStreamWaitEvent(s, h->la_a, 0);
+    }
+    if (h->aux) {
+        cudaEventRecord(h->ax_a, h->aux);
+        cudaStreamWaitEvent(s, h->ax_a, 0);
     }
 }
 
@@ -344,6 +360,8 @@ int ensure_ws(mpir_ctx *h, size_t bytes)
         cudaStreamSynchronize(h->stream);
         if (h->side) cudaStreamSynchronize(h->side);
         if (h->crit) cudaStreamSynchronize(h->crit);
+    if (h->aux) cudaStreamSynchronize(h->aux);
+        if (h->aux) cudaStreamSynchronize(h->aux);
         cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0;
     }
     if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "workspace cudaMalloc failed"); }
@@ -1493,6 +1511,7 @@ int mpir_destroy(mpir_handle h)
     cudaStreamSynchronize(h->stream);
     if (h->side) cudaStreamSynchronize(h->side);
     if (h->crit) cudaStreamSynchronize(h->crit);
+    if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->ws && h->ws_owned) cudaFree(h->ws);
     if (h->scratch_base) cudaFree(h->scratch_base);
     if (h->rws) cudaFree(h->rws);
@@ -1517,6 +1536,12 @@ int mpir_destroy(mpir_handle h)
         cudaStreamDestroy(h->crit);
         cudaEventDestroy(h->la_a);
         cudaEventDestroy(h->la_b);
+    }
+    if (h->aux) {
+        cudaStreamSynchronize(h->aux);
+        cudaStreamDestroy(h->aux);
+        cudaEventDestroy(h->ax_a);
+        cudaEventDestroy(h->ax_b);
     }
     if (h->sel_stream) {
         cudaStreamSynchronize(h->sel_stream);
@@ -1544,6 +1569,7 @@ int mpir_set_workspace(mpir_handle h, void *ptr, size_t bytes)
     if (((uintptr_t)ptr & 255) != 0) return -2;
     if (h->side) cudaStreamSynchronize(h->side);
     if (h->crit) cudaStreamSynchronize(h->crit);
+    if (h->aux) cudaStreamSynchronize(h->aux);
     if (h->ws && h->ws_owned) { cudaStreamSynchronize(h->stream); cudaFree(h->ws); }
     h->ws = ptr;
     h->ws_bytes = ptr ? bytes : 0;
