@@ -1,6 +1,8 @@
-// qr.cu -- blocked Householder QR on GB300: cluster panel kernel + fused
-// trailing update.  The generalized factorizations of the paper (GRQ for
-// LSE, GQR for GLS, Lemma 4.5 / 4.6) are built from this one QR: an RQ
+// qr.cu -- blocked Householder QR on GB300: cluster panel kernels with
+// st.async column messages, cluster inner updates, tensor-core outer
+// updates with look-ahead, and the aggregated compact-WY factor of the whole
+// reflector set.  The generalized factorizations of the paper (GRQ for LSE,
+// GQR for GLS, Lemma 4.5 / 4.6) are built from this one QR: an RQ
 // factorization of C is a QR factorization of the reversed transpose of C
 // (the host driver forms that copy), so every reflector is a column of a
 // column-major matrix and every access below is coalesced.
@@ -1705,7 +1707,10 @@ int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, dou
 
 // Two-level QR, FP32 storage: 32-wide register panels inside 128-wide
 // outer blocks; inner updates row-parallel SIMT, outer trailing updates on
-// the tensor cores.
+// the tensor cores.  Streams (when tf provides them): panels, inner updates
+// and the next block's columns on tf->crit; each block's factor (Gram
+// matrix, T) on tf->aux beside the next columns' V^T C; the rest of the
+// trailing update on s; the aggregated factor Tf on tf->side.
 template <>
 int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *Tw128, GemmPrec prec, void *ws,
                  int *err, cudaStream_t s, const TfullJob *tf, int kmax)
