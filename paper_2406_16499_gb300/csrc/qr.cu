@@ -1111,8 +1111,6 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
         if (L <= 16 * 64) return launch_panel2<128>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 128) return launch_panel2<256>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 256) return launch_panel2<512>(A, lda, M, j0, ncols, tau, Tw, err, s);
-        if (L <= 16 * 128) return launch_panel_shape<T, 128, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
-        if (L <= 16 * 256) return launch_panel_shape<T, 256, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 512) return launch_panel_shape<T, 512, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
     }
     return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, s);
