@@ -4,7 +4,7 @@
 // as three passes that each span the whole GPU and read their matrix once:
 //     y  = V^T x         column dots, one warp per reflector;
 //     w' = op(Tf) y      column dots (Tf^T) or row products (Tf);
-//     x -= V w'          row products over 128-column chunks, then a sum of
+//     x -= V w'          row products over 64-column chunks, then a sum of
 //                        the chunk partials in a fixed order (deterministic).
 // This is the vector side of every correction solve (Sec. 3, Alg. 3 / 4:
 // the orthogonal factors of the generalized factorizations applied to the
@@ -17,7 +17,7 @@
 namespace mpir {
 
 constexpr int WY_RT = 256;     // rows per tile of the row products (one per thread)
-constexpr int WY_CC = 128;     // columns per chunk of the row products
+constexpr int WY_CC = 64;      // columns per chunk of the row products
 constexpr int WY_U = 16;       // independent loads in flight per thread
 
 // Whether tile (rows from i0) x chunk (columns from c0) of the row products
