@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 #include <cooperative_groups.h>
+#include <atomic>
 #include <cstdint>
 #include <cstddef>
 #include <mutex>
@@ -12,6 +13,29 @@
 namespace mpir {
 
 namespace cg = cooperative_groups;
+
+// Function attributes (dynamic shared-memory limit, non-portable cluster
+// size) belong to the device that is current when they are set.  A launcher
+// keeps one of these per kernel and passes it the set-up: it runs the first
+// time each device (0..63; every time on higher ordinals) launches, from any
+// host thread; running it twice is harmless.
+class PerDeviceOnce {
+  public:
+    template <typename F>
+    void operator()(F &&fn)
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); dev = 0; }
+        if (dev < 0 || dev >= 64) { fn(); return; }
+        const unsigned long long bit = 1ull << dev;
+        if (done_.load(std::memory_order_acquire) & bit) return;
+        fn();
+        done_.fetch_or(bit, std::memory_order_acq_rel);
+    }
+
+  private:
+    std::atomic<unsigned long long> done_{0};
+};
 
 // Device-side error word (bit flags) written by kernels that give up a
 // bounded wait; the host reads it after synchronising.

@@ -393,11 +393,8 @@ static int launch_tc(const CUtensorMap &A, const CUtensorMap &A2, const CUtensor
     constexpr int NBUF = MODE == TCM_TF32X3 ? 2 : 1;
     const size_t smem = (size_t)STAGES * (NA * TC_TILE_A + NBUF * TC_TILE_B) + 1024;
     auto kern = k_gemm_tc<MODE, BSPLIT, EPI, STAGES>;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
     ProfScope ps(K_LARFB_TC, s);
     // ordinary launch: a waiting grid of this size would hold every SM
     kern<<<dim3(ntn, ntm, nsplit), TC_THREADS, smem, s>>>(A, A2, B, B2, args);

@@ -156,12 +156,11 @@ k_arnoldi_cgs2(double *__restrict__ Vb, size_t ldv, int N, int j, int R, double 
 static int arnoldi_step(GmresWs &w, int j, cudaStream_t s)
 {
     auto kern = k_arnoldi_cgs2;
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([&] {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        attr = true;
-    }
+    });
     int want = ceil_div(w.N, 1024);
     if (want > 16) want = 16;
     if (want < 1) want = 1;

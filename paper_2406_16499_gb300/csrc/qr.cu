@@ -936,14 +936,14 @@ static void reduce_w(const float *P, int nsplit, size_t pstride, const float *Tb
 {
     if (nc >= 16 * 64) {
         const size_t smem = (size_t)(16 + OUTER_NB) * OUTER_NB * 4;
-        static bool attr = false;
-        if (!attr) { cudaFuncSetAttribute(k_reduce_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        static PerDeviceOnce once;
+        once([&] { cudaFuncSetAttribute(k_reduce_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
         pdl_launch(k_reduce_w<16>, dim3(ceil_div(nc, 16)), dim3(256), smem, s, P, nsplit, pstride, (int)OUTER_NB, Tb, trans,
                    nc, Wh, Wl, ldw, split);
     } else {
         const size_t smem = (size_t)(4 + OUTER_NB) * OUTER_NB * 4;
-        static bool attr = false;
-        if (!attr) { cudaFuncSetAttribute(k_reduce_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        static PerDeviceOnce once;
+        once([&] { cudaFuncSetAttribute(k_reduce_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
         pdl_launch(k_reduce_w<4>, dim3(ceil_div(nc, 4)), dim3(256), smem, s, P, nsplit, pstride, (int)OUTER_NB, Tb, trans,
                    nc, Wh, Wl, ldw, split);
     }
@@ -1044,11 +1044,8 @@ static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T
     if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
     const int chunk = ceil_div(L, cs);
     auto kern = k_panel_qr<T, NB, NT, RPT>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        attr_done = true;
-    }
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); });
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);
@@ -1075,11 +1072,8 @@ static int launch_panel2(float *A, int lda, int M, int j0, int ncols, float *tau
     if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
     const int chunk = ceil_div(L, cs);
     auto kern = k_panel_qr2<NT>;
-    static bool attr_done = false;
-    if (!attr_done) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        attr_done = true;
-    }
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); });
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(NT, 1, 1);
@@ -1280,12 +1274,11 @@ static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int
 {
     {   // whole chunk in shared memory when it fits (16-CTA cluster)
         auto kern = k_inner_cl_s<32>;
-        static bool attr = false;
-        if (!attr) {
+        static PerDeviceOnce once;
+        once([&] {
             cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-            attr = true;
-        }
+        });
         const int want = std::max(1, std::min(16, ceil_div(L, 64)));
         const int chunk0 = ceil_div(L, want);
         const size_t smem0 = ((size_t)chunk0 * IV_LD + (size_t)(chunk0 | 1) * IC) * sizeof(float);
@@ -1313,8 +1306,8 @@ static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int
         }
     }
     auto kern = k_inner_cl<32>;
-    static bool attr = false;
-    if (!attr) { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); attr = true; }
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); });
     int want = ceil_div(L, 256);
     if (want > 16) want = 16;
     const int cs = cluster_size_for((const void *)kern, 256, 0, want);
@@ -1503,8 +1496,8 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     {
         ProfScope ps(K_LARFB_AUX, s);
         const size_t smem = (size_t)(2 * OUTER_NB * OUTER_NB + 96 * 32) * 4;
-        static bool attr = false;
-        if (!attr) { cudaFuncSetAttribute(k_outer_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); attr = true; }
+        static PerDeviceOnce once;
+        once([&] { cudaFuncSetAttribute(k_outer_T, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
         pdl_launch(k_outer_T, dim3(1), dim3(256), smem, s, Tw32, (const float *)w.G, nr, Tb);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;

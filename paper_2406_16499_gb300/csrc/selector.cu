@@ -540,18 +540,13 @@ int features_launch(int kind, int m, int n, int p, const double *A, int lda, con
     if (kind == 0) { V.R = m + p; V.C = n; } else { V.R = n; V.C = m + p; }
     if (k < 1 || k > FT_KMAX) return MPIR_UNSUPPORTED;
     auto kern = k_features;
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([&] {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        attr = true;
-    }
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+    });
     const size_t smem = (size_t)3 * V.C * sizeof(float);
     if (smem > 160 * 1024) return MPIR_UNSUPPORTED;
-    static size_t smem_set = 0;
-    if (smem > smem_set) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
-        smem_set = 160 * 1024;
-    }
     // one CTA while the block fits comfortably (cluster barriers cost more
     // than the arithmetic of small problems), up to 16 for large ones
     const double elems = (double)V.R * V.C;

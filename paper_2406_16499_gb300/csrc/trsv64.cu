@@ -78,11 +78,8 @@ void invert_diag64(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream
 {
     if (N <= 0) return;
     const size_t smem = T64_DS * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_invert_diag64<TS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(k_invert_diag64<TS, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
     ProfScope ps(K_TRSV, s);
     k_invert_diag64<TS, T><<<ceil_div(N, 64), 64, smem, s>>>(U, ldu, N, Dinv, status);
 }
@@ -297,15 +294,14 @@ int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *
     int want = nblk < 16 ? nblk : 16;                      // as many CTAs as the cluster allows
     // barriers, one message slot per step, two staged inverses, the owned rows
     const size_t fixed = 8 * (size_t)((nblk + 1) & ~1) + (size_t)nblk * 64 * sizeof(T) + 2 * T64_DS * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([&] {
         for (auto kk : {k_trsv64<T, 1>, k_trsv64<T, 2>}) {
             cudaFuncSetAttribute(kk, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             cudaFuncSetAttribute(kk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(8 * 128 + 128 * 64 * sizeof(T) + 2 * T64_DS * sizeof(T) + T64_THREADS * sizeof(T)));
         }
-        attr = true;
-    }
+    });
     int cs = cluster_size_for((const void *)k_trsv64<T, 1>, T64_THREADS,
                               fixed + (size_t)ceil_div(nblk, want) * 64 * sizeof(T), want);
     const int slice = ceil_div(nblk, cs) * 64;

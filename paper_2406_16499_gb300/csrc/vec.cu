@@ -260,13 +260,12 @@ static int launch_vec_apply_cl(const TS *V, int ldv, int M, int K, const TS *Tw,
     auto kern = k_vec_apply_cl<TS, T, NBV>;
     int want = ceil_div(M, 256);
     if (want > 16) want = 16;
-    static bool attr = false;
     const size_t tsz = (size_t)NBV * NBV * sizeof(T);
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([&] {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(tsz + 64 * 1024));
-        attr = true;
-    }
+    });
     int cs = cluster_size_for((const void *)kern, VEC_CL_THREADS, tsz + (size_t)ceil_div(M, want) * sizeof(T), want);
     int slice = ceil_div(M, cs);
     size_t smem = tsz + (size_t)slice * sizeof(T);
@@ -553,12 +552,11 @@ static int trsv_upper_cl(const TS *U, int ldu, int n, int trans, T *x, const Dev
     const int nblk = ceil_div(n, 32);
     int want = ceil_div(nblk, 8);            // 256 rows per CTA
     if (want > 16) want = 16;
-    static bool attr = false;
-    if (!attr) {
+    static PerDeviceOnce once;
+    once([&] {
         cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024);
-        attr = true;
-    }
+    });
     int cs = cluster_size_for((const void *)kern, VEC_CL_THREADS, (size_t)ceil_div(nblk, want) * 32 * sizeof(T), want);
     const int slice = ceil_div(nblk, cs) * 32;
     cs = ceil_div(n, slice);
