@@ -399,7 +399,8 @@ const char *mpir_version(void);
  * 10 larfb_tc (tcgen05 GEMM), 11 larfb_aux (V / W preparation), 12 gmres
  * (Arnoldi steps and cycle updates), 13 batched (persistent batched solves),
  * 14 selector (features and MLP kernels).
- * Not thread-safe; a profiling aid, off by default. */
+ * Launch counting is safe from any thread; the timing mode is a
+ * single-threaded profiling aid, off by default. */
 int mpir_profile(int enable);
 int mpir_profile_read(double *ms, long long *launches, int nkinds);
 long long mpir_launch_count(int kind);          /* kind < 0: all kinds */

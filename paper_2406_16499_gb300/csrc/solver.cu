@@ -27,6 +27,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
+#include <atomic>
 #include <string>
 #include <vector>
 #include <algorithm>
@@ -41,10 +42,11 @@
 using namespace mpir;
 
 // ----------------------------------------------------- launch profiling --
-// Process-wide: a launch counter per kernel kind, and (when enabled) a pool
+// Process-wide: a launch counter per kernel kind (atomic: launches may come
+// from several host threads), and (when enabled, single-threaded use) a pool
 // of CUDA event pairs recorded around every launch on its own stream.
 namespace mpir {
-static long long g_launches[K_NKINDS];
+static std::atomic<long long> g_launches[K_NKINDS];
 static bool g_prof = false;
 static std::vector<cudaEvent_t> g_ev;
 static std::vector<int> g_kind;
@@ -54,7 +56,7 @@ constexpr size_t PROF_CAP = 1 << 14;
 
 void prof_begin(int kind, cudaStream_t s)
 {
-    g_launches[kind]++;
+    g_launches[kind].fetch_add(1, std::memory_order_relaxed);
     // the event pool is created by mpir_profile(1); launches beyond it are
     // counted but not timed (no resource is created on the launch path)
     if (!g_prof || 2 * (g_nrec + 1) > g_ev.size()) return;
@@ -62,7 +64,7 @@ void prof_begin(int kind, cudaStream_t s)
     g_open = true;
 }
 
-void prof_count(int kind) { g_launches[kind]++; }
+void prof_count(int kind) { g_launches[kind].fetch_add(1, std::memory_order_relaxed); }
 
 void prof_end(int kind, cudaStream_t s)
 {
@@ -1453,10 +1455,10 @@ long long mpir_launch_count(int kind)
 {
     if (kind < 0) {
         long long t = 0;
-        for (int k = 0; k < K_NKINDS; k++) t += g_launches[k];
+        for (int k = 0; k < K_NKINDS; k++) t += g_launches[k].load(std::memory_order_relaxed);
         return t;
     }
-    return kind < K_NKINDS ? g_launches[kind] : 0;
+    return kind < K_NKINDS ? g_launches[kind].load(std::memory_order_relaxed) : 0;
 }
 
 const char *mpir_kernel_kind_name(int kind)
