@@ -109,7 +109,9 @@ void mpir_default_opts(mpir_opts *opts);
 
 /* Create a handle bound to device `device` (the current device if < 0) and
  * CUDA stream `stream` (a cudaStream_t, NULL = legacy default stream).
- * Returns 0 or MPIR_CUDA_ERROR. */
+ * Returns 0 or MPIR_CUDA_ERROR.  Creation and destruction leave the caller's
+ * current device as it was; every other call on a handle must be made with
+ * the handle's device current (the convention of CUDA library handles). */
 int mpir_create(mpir_handle *handle, int device, void *stream);
 int mpir_destroy(mpir_handle handle);
 int mpir_set_stream(mpir_handle handle, void *stream);

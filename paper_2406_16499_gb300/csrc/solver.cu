@@ -86,6 +86,28 @@ static const char *g_kind_names[K_NKINDS] = {"panel_qr", "larfb", "vec_apply", "
 // ------------------------------------------------------------------ ctx --
 
 namespace {
+// Makes `dev` the current device for the scope and gives the caller's
+// current device back at its end (creation and destruction only: every other
+// call on a handle is made with the handle's device current).
+struct DeviceScope {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceScope(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+        if (dev >= 0 && dev != prev && cudaSetDevice(dev) != cudaSuccess) { cudaGetLastError(); ok = false; }
+    }
+    ~DeviceScope()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
+} // namespace
+
+namespace {
 
 enum class Kind { NONE, LSE, GLS };
 
@@ -1486,10 +1508,11 @@ int mpir_create(mpir_handle *handle, int device, void *stream)
 {
     if (!handle) return -1;
     *handle = nullptr;
+    if (device < 0 && cudaGetDevice(&device) != cudaSuccess) { cudaGetLastError(); return MPIR_CUDA_ERROR; }
+    DeviceScope ds(device);
+    if (!ds.ok) return MPIR_CUDA_ERROR;
     mpir_ctx *h = new mpir_ctx();
-    if (device < 0) cudaGetDevice(&device);
     h->device = device;
-    if (cudaSetDevice(device) != cudaSuccess) { delete h; return MPIR_CUDA_ERROR; }
     h->stream = (cudaStream_t)stream;
     const size_t part_bytes = 1 << 20;
     if (cudaMalloc(&h->scratch_base, 4096 + part_bytes) != cudaSuccess) { delete h; cudaGetLastError(); return MPIR_CUDA_ERROR; }
@@ -1510,6 +1533,7 @@ int mpir_create(mpir_handle *handle, int device, void *stream)
 int mpir_destroy(mpir_handle h)
 {
     if (!h) return -1;
+    DeviceScope ds(h->device);
     cudaStreamSynchronize(h->stream);
     if (h->side) cudaStreamSynchronize(h->side);
     if (h->crit) cudaStreamSynchronize(h->crit);
