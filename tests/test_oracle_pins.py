@@ -117,6 +117,29 @@ def test_gls_identity_v_is_least_squares(oracle_mod):
     assert rel(t["z"], t["y"]) < 1e-12
 
 
+@pytest.mark.parametrize("m,n,p", [(9, 15, 6), (20, 21, 1), (1, 8, 7)])
+def test_lse_square_stack_is_a_linear_solve(oracle_mod, m, n, p):
+    """n = m + p: [A; B] is square and nonsingular (the rank conditions of
+    the problem statement, Sec. 1), so the LSE solution solves [A; B] x =
+    [b; d] and the least-squares residual r = b - A x vanishes."""
+    P = I.lse_svd(300 + m + n, m, n, p, 1e2, 1e1)
+    t = oracle_mod.lse_truth(P["A"], P["B"], P["b"], P["d"])
+    x = np.linalg.solve(np.vstack([P["A"], P["B"]]), np.concatenate([P["b"], P["d"]]))
+    kap = np.linalg.cond(np.vstack([P["A"], P["B"]]))
+    assert rel(t["x"], x) < 50 * kap * U
+    assert np.linalg.norm(t["r"]) < 50 * kap * U * np.linalg.norm(P["b"])
+
+
+def test_lse_square_b_fixes_x(oracle_mod):
+    """p = n: B x = d alone determines x (B nonsingular), whatever A and b
+    are; r is then the plain residual b - A x."""
+    P = I.lse_svd(41, 30, 12, 12, 1e3, 1e2)
+    t = oracle_mod.lse_truth(P["A"], P["B"], P["b"], P["d"])
+    x = np.linalg.solve(P["B"], P["d"])
+    assert rel(t["x"], x) < 50 * 1e2 * U
+    assert rel(t["r"], P["b"] - P["A"] @ x) < 1e-12
+
+
 # ----------------------------------------------------- exact brute force --
 
 @pytest.mark.parametrize("m,n,p", [(5, 4, 2), (4, 4, 1), (3, 4, 1), (4, 3, 3), (6, 3, 1)])
