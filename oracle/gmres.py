@@ -2,11 +2,13 @@
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
-Restates the paper's GMRES-IR for LSE (m >= n) and GLS (n <= p):
+Restates the paper's GMRES-IR for LSE and GLS:
 * the scaled augmented matrices F~(alpha, beta) and the scaled correction
   unknowns / right-hand sides (eq. lse-limit-notation, eq. gls-limit-notation);
 * the block-diagonal split preconditioners M_l, M_r built from the
-  low-precision factors (eq. lse-bdpre-mlarge, eq. gls-bdpre-plarge);
+  low-precision factors: LSE m >= n (eq. lse-bdpre-mlarge) and n > m
+  (eq. lse-bdpre-nlarge), GLS n <= p (eq. gls-bdpre-plarge) and n > p
+  (eq. gls-bdpre-nlarge);
 * restarted GMRES in FP64 with modified Gram-Schmidt Arnoldi and Givens
   rotations (Sec. 6.1: GMRES runs entirely in double precision);
 * the outer refinement loop of Alg. 2 / Alg. 4 with the correction system
@@ -32,16 +34,20 @@ class LseBD:
     """F~ = [a I 0 A; 0 0 b B; A^T b B^T 0] and the split preconditioner
     M_l = diag(a^-1/2 I, a^-1/2 b^-1 S R^-1, a^1/2 T1^-T Q),
     M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-T S^T, a^1/2 Q^T T1^-1),
-    S = T1(n-p+1:n, n-p+1:n), T1 the leading n x n of T (m >= n)."""
+    S = T1(n-p+1:n, n-p+1:n).  T1 is the leading n x n block of T when
+    m >= n (eq. lse-bdpre-mlarge); when n > m, T = [T^_1, T^_2] is m x n and
+    T1 is the paper's U = [T^_1 T^_2; 0 I_{n-m}], whose trailing p x p block
+    is its Y (eq. lse-bdpre-nlarge)."""
 
     def __init__(self, F, A, B, alpha, beta):
         m, n, p = F["m"], F["n"], F["p"]
-        if m < n:
-            raise ValueError("the m >= n preconditioner needs m >= n")
         R, T = R_T(F)
         self.F, self.A, self.B = F, np.asarray(A), np.asarray(B)
         self.m, self.n, self.p = m, n, p
-        self.T1 = T[:n, :n]
+        if m >= n:
+            self.T1 = T[:n, :n]
+        else:
+            self.T1 = np.vstack([T[:m, :n], np.hstack([np.zeros((n - m, m)), np.eye(n - m)])])
         self.S = self.T1[n - p:, n - p:]
         self.R = R
         self.a, self.b = alpha, beta
@@ -84,16 +90,21 @@ class GlsBD:
     """F~ = [a I V^T 0; V 0 b W; 0 b W^T 0] and the split preconditioner
     M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^T, a^-1/2 b^-1 S^T R^-T),
     M_r = diag(a^-1/2 I, a^1/2 Q T2^-T, a^-1/2 b^-1 R^-1 S),
-    T = [0, T2] (n <= p), S = T2(1:m, 1:m)."""
+    S = T2(1:m, 1:m).  When n <= p, T = [0, T2] (eq. gls-bdpre-plarge); when
+    n > p, T = [T^_1; T^_2] is n x p and T2 is the paper's
+    U = [I_{n-p} T^_1; 0 T^_2], whose leading m x m block is its Y
+    (eq. gls-bdpre-nlarge)."""
 
     def __init__(self, F, W, V, alpha, beta):
         n, m, p = F["n"], F["m"], F["p"]
-        if n > p:
-            raise ValueError("the n <= p preconditioner needs n <= p")
         R, T = R_T(F)
         self.F, self.W, self.V = F, np.asarray(W), np.asarray(V)
         self.n, self.m, self.p = n, m, p
-        self.T2 = T[:, p - n:]
+        if n <= p:
+            self.T2 = T[:, p - n:]
+        else:
+            self.T2 = np.vstack([np.hstack([np.eye(n - p), T[:n - p, :p]]),
+                                 np.hstack([np.zeros((p, n - p)), T[n - p:, :p]])])
         self.S = self.T2[:m, :m]
         self.R = R
         self.a, self.b = alpha, beta
@@ -187,7 +198,7 @@ def gmres(op, rhs, tol=1e-8, restart=30, maxit=300):
 
 def lse_gmres_ir(A, B, b, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_tol=1e-8,
                  inner_maxit=300, beta=1.0):
-    """LSE GMRES-IR with the block-diagonal split preconditioner (m >= n)."""
+    """LSE GMRES-IR with the block-diagonal split preconditioner."""
     A, B = np.asarray(A, dtype=np.float64), np.asarray(B, dtype=np.float64)
     b, d = np.asarray(b, dtype=np.float64), np.asarray(d, dtype=np.float64)
     F = lse_factor(A, B, fact)
@@ -221,7 +232,7 @@ def lse_gmres_ir(A, B, b, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner
 
 def gls_gmres_ir(W, V, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_tol=1e-8,
                  inner_maxit=300, beta=1.0):
-    """GLS GMRES-IR with the block-diagonal split preconditioner (n <= p)."""
+    """GLS GMRES-IR with the block-diagonal split preconditioner."""
     W, V = np.asarray(W, dtype=np.float64), np.asarray(V, dtype=np.float64)
     d = np.asarray(d, dtype=np.float64)
     F = gls_factor(W, V, fact)

@@ -6,6 +6,8 @@ its reported behaviour.
   multiplicities m-n, n-p, p (LSE) and p-n, n-m, m (GLS) (Sec. 5.2, App. C);
   its 2-norm condition number is below C = 1 + 2 lambda3/lambda2 ~ 9.0984.
   This pins F~, both preconditioners and their scalings at any alpha, beta.
+* For the wide shapes (LSE n > m, GLS n > p) the same product equals the
+  block matrices the paper gives for those preconditioners.
 * GMRES with full restart solves small systems exactly (numpy solve).
 * Table 4 / Table 5: with u_f = single, GMRES-IR reaches FP64-level accuracy
   where classical IR does not (kappa = 1e9, one small singular value).
@@ -58,6 +60,62 @@ def test_gls_preconditioned_spectrum(oracle_mod, n, m, p, a, b):
     want = np.sort(np.concatenate([np.repeat(cubic, m), np.repeat(gold_r, n - m), np.ones(p - n)]))
     assert np.allclose(ev, want, atol=1e-8)
     assert np.linalg.cond(M) <= 9.0985
+
+
+@pytest.mark.parametrize("m,n,p,a,b", [(8, 12, 6, 0.7, 1.3), (10, 14, 4, 1.0, 1.0), (5, 9, 9, 2.0, 0.5)])
+def test_lse_wide_preconditioned_matrix(oracle_mod, m, n, p, a, b):
+    """n > m (eq. lse-bdpre-nlarge): with exact (FP64) factors M_l F~ M_r is
+    [I_m 0 Zb; 0 0 Ib; Zb^T Ib^T 0], Zb = [Z, 0] (m x n), Ib = [0, I_p]
+    (Sec. 5.2), and its 2-norm condition number stays below C = 9.0984."""
+    from oracle import gmres as G
+    P = I.lse_svd(m * n + p + 7, m, n, p, 1e3, 1e1)
+    F = oracle_mod.lse_factor(P["A"], P["B"], "fp64")
+    bd = G.LseBD(F, P["A"], P["B"], a, b)
+    M = _dense(lambda t: bd.Ml(bd.Fmul(bd.Mr(t))), m + n + p)
+    Zb = np.hstack([oracle_mod.explicit(F, "Z"), np.zeros((m, n - m))])
+    Ib = np.hstack([np.zeros((p, n - p)), np.eye(p)])
+    X = np.zeros((m + p + n, m + p + n))
+    X[:m, :m] = np.eye(m)
+    X[:m, m + p:], X[m + p:, :m] = Zb, Zb.T
+    X[m:m + p, m + p:], X[m + p:, m:m + p] = Ib, Ib.T
+    assert np.abs(M - X).max() < 1e-10
+    assert np.linalg.cond(M) <= 9.0985
+
+
+@pytest.mark.parametrize("n,m,p,a,b", [(12, 4, 8, 0.6, 1.7), (10, 6, 5, 1.0, 1.0), (9, 3, 6, 3.0, 0.25)])
+def test_gls_wide_preconditioned_matrix(oracle_mod, n, m, p, a, b):
+    """n > p (eq. gls-bdpre-nlarge): with exact factors M_l F~ M_r is
+    [I_p Zc^T 0; Zc 0 Ic; 0 Ic^T 0], Zc = [0; Z] (n x p), Ic = [I_m; 0]
+    (Sec. 5.3), condition number below C."""
+    from oracle import gmres as G
+    G_ = I.gls_svd(n * m + p + 7, n, m, p, 1e3, 1e1)
+    F = oracle_mod.gls_factor(G_["W"], G_["V"], "fp64")
+    bd = G.GlsBD(F, G_["W"], G_["V"], a, b)
+    M = _dense(lambda t: bd.Ml(bd.Fmul(bd.Mr(t))), m + n + p)
+    Zc = np.vstack([np.zeros((n - p, p)), oracle_mod.explicit(F, "Z")])
+    Ic = np.vstack([np.eye(m), np.zeros((n - m, m))])
+    X = np.zeros((p + n + m, p + n + m))
+    X[:p, :p] = np.eye(p)
+    X[:p, p:p + n], X[p:p + n, :p] = Zc.T, Zc
+    X[p:p + n, p + n:], X[p + n:, p:p + n] = Ic, Ic.T
+    assert np.abs(M - X).max() < 1e-10
+    assert np.linalg.cond(M) <= 9.0985
+
+
+@pytest.mark.parametrize("kappa", [1e3, 1e6])
+def test_gmres_ir_wide_shapes_converge(oracle_mod, kappa):
+    """GMRES-IR with the wide-shape preconditioners (LSE n > m, GLS n > p)
+    reaches FP64-level accuracy with u_f = single while u_f kappa(A)
+    kappa(B) stays below one (the condition of Sec. 5.2 / 5.3)."""
+    from oracle import gmres as G
+    P = I.lse_paper(401, 40, 64, 32, kappa)
+    out = G.lse_gmres_ir(P["A"], P["B"], P["b"], P["d"])
+    met = oracle_mod.lse_metrics(P["A"], P["B"], P["b"], P["d"], out["x"], out["r"], out["v"])
+    assert out["status"] == 0 and met["eta"] < 1e-14 and met["e_con"] < 1e-14
+    Gp = I.gls_paper(501, 48, 16, 40, kappa)
+    out = G.gls_gmres_ir(Gp["W"], Gp["V"], Gp["d"])
+    met = oracle_mod.gls_metrics(Gp["W"], Gp["V"], Gp["d"], out["x"], out["y"], out["z"])
+    assert out["status"] == 0 and met["eta"] < 1e-14
 
 
 def test_gmres_full_restart_is_exact():
