@@ -78,7 +78,7 @@ def job_value(world, ms_per_step):
 # --------------------------------------------------------------- clocks --
 
 class ClockSampler:
-    """nvidia-smi sampling every 200 ms during the timed region."""
+    """nvidia-smi sampling every 50 ms while the benchmark loads the GPU."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -87,16 +87,26 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.path = None
+        self.out = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
+            self.out = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
-        except Exception:
+                 "-lms", "50"], stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:                       # no nvidia-smi: no clock record
             self.proc = None
+            return
+        # wait (at most 3 s) for the first sample, so that sampling covers
+        # the work that follows
+        t0 = time.time()
+        while self.proc.poll() is None and time.time() - t0 < 3.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
@@ -105,8 +115,10 @@ class ClockSampler:
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
-        except Exception:
+        except subprocess.TimeoutExpired:
             self.proc.kill()
+            self.proc.wait()
+        self.out.close()
         rows = []
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
@@ -175,8 +187,9 @@ def fp32_simt_peak(sm_mhz):
 
 def measured_peaks():
     try:
-        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
                 "sm_max_mhz": 2070.0, "_fallback": True}
 
@@ -185,16 +198,18 @@ def traffic_record(kind):
     """Per-launch DRAM traffic of `kind` from the committed ncu summary, if
     it was taken on the current source of the kernel (else None)."""
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-    except Exception:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None
     r = rec.get(kind)
     if not r:
         return None
     src = os.path.join(ROOT, "paper_2406_16499_gb300", "csrc", r["source"])
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    except Exception:
+        with open(src, "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
         return None
     return r["bytes_per_launch"] if sha == r.get("source_sha") else None
 
@@ -387,12 +402,14 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    # the clock sampler runs from before the warm-up (the GPU is loaded from
+    # then on) to the end of the timed steps
+    clocks = ClockSampler(local)
+    clocks.start()
     for _ in range(max(args.warmup, 3)):
         solve()
     barrier()
     launches0 = mpir.launch_count()
-    clocks = ClockSampler(local)
-    clocks.start()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     total_ms = 0.0
@@ -546,7 +563,10 @@ def run_ours(args):
         achieved = alg / (dom_ms * 1e-3) / 1e9
     roof.update({"kernel": dom_name, "achieved": achieved, "peak": peak, "frac": achieved / peak,
                  "launches_per_step": dom_cnt / kp, "ms_per_step": dom_ms / kp,
-                 "traffic": traffic_record(dom_name), "peak_source": "MEASURED_PEAKS.json/unit counts"})
+                 "traffic": traffic_record(dom_name),
+                 "peak_source": ("fallback peaks (MEASURED_PEAKS.json absent)" if peaks.get("_fallback")
+                                 else "MEASURED_PEAKS.json" if roof["bound"] == "hbm"
+                                 else "unit counts at the measured maximum SM clock (MEASURED_PEAKS.json)")})
     kernels = {k: {"ms_per_step": v[0] / kp, "launches_per_step": v[1] / kp} for k, v in prof.items() if v[1]}
 
     # ---- CPU oracle on the host cores (bounded sample, rank 0, N = 1) ----
