@@ -122,6 +122,18 @@ def test_gls_ar1_reduced(h, oracle_mod):
     check_gls(oracle_mod, G, x, y, z)
 
 
+def test_gls_ar1_full_size_classical(h, oracle_mod):
+    """The benchmarked workload itself (n = p = 4096, m = 1024, the same
+    seed and the same FP32 GQR + FP64 classical IR launch path): eq.
+    gls-stop ratios and the constraint residual from the oracle's
+    double-double residual, FP32 factors without escalation."""
+    G = I.gls_ar1()
+    st, info, x, y, z = run_gls(h, G, escalate=False)
+    assert st == 0 and info.escalated == 0 and info.fact_used == 2
+    met = oracle_mod.gls_metrics(G["W"], G["V"], G["d"], x, y, z)
+    assert met["eta"] <= 1e-14 and met["e_con"] <= 1e-14
+
+
 def test_fp64_direct_matches_oracle(h, oracle_mod):
     """The fixed-precision FP64 path (GQR + Paige, no refinement) is the
     comparator the mixed-precision solve is timed against."""
