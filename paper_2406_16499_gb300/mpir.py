@@ -151,12 +151,23 @@ def exported_symbols():
     return list(_SIG.keys())
 
 
-def ptr(t):
-    """Device pointer of a tensor (None or an empty tensor -> NULL)."""
+_CTYPE = {"f64": "torch.float64", "f32": "torch.float32", "i32": "torch.int32"}
+
+
+def ptr(t, ctype="f64"):
+    """Device pointer of a CUDA tensor whose element type matches the C
+    argument (ctype 'f64' for double*, 'f32' for float*, 'i32' for int*);
+    None or an empty tensor -> NULL, an int is taken as a raw address.  A
+    host tensor or another element type raises: the kernels would read past
+    the end of the buffer."""
     if t is None:
         return None
     if isinstance(t, int):
         return t
+    if not t.is_cuda:
+        raise MpirError("expected a CUDA tensor, got one on %s" % t.device)
+    if str(t.dtype) != _CTYPE[ctype]:
+        raise MpirError("expected %s elements for this argument, got %s" % (_CTYPE[ctype], t.dtype))
     if t.numel() == 0:
         return None
     return t.data_ptr()
@@ -286,21 +297,23 @@ class Handle:
     def lse_features(self, A, B, b, d, s, out):
         p = B.shape[0]
         return self.check(lib().mpir_lse_features(self.h, A.shape[0], A.shape[1], p, ptr(A), ld(A), ptr(B),
-                                                  ld(B) if p else 1, ptr(b), ptr(d), ptr(s), ptr(out)),
+                                                  ld(B) if p else 1, ptr(b), ptr(d), ptr(s), ptr(out, "f32")),
                           "mpir_lse_features")
 
     def gls_features(self, W, V, d, s, out):
         n, m = W.shape
         return self.check(lib().mpir_gls_features(self.h, n, m, V.shape[1], ptr(W), ld(W), ptr(V), ld(V), ptr(d),
-                                                  ptr(s), ptr(out)), "mpir_gls_features")
+                                                  ptr(s), ptr(out, "f32")), "mpir_gls_features")
 
     def mlp_forward(self, params, X, prob):
-        return self.check(lib().mpir_mlp_forward(self.h, ptr(params), ptr(X), X.shape[0], ptr(prob)),
+        return self.check(lib().mpir_mlp_forward(self.h, ptr(params, "f32"), ptr(X, "f32"), X.shape[0],
+                                                 ptr(prob, "f32")),
                           "mpir_mlp_forward")
 
     def mlp_train_step(self, params, m, v, step, lr, X, y, grad=None, loss=None):
-        return self.check(lib().mpir_mlp_train_step(self.h, ptr(params), ptr(m), ptr(v), int(step), float(lr),
-                                                    ptr(X), ptr(y), X.shape[0], ptr(grad), ptr(loss)),
+        return self.check(lib().mpir_mlp_train_step(self.h, ptr(params, "f32"), ptr(m, "f32"), ptr(v, "f32"),
+                                                    int(step), float(lr), ptr(X, "f32"), ptr(y, "i32"), X.shape[0],
+                                                    ptr(grad, "f32"), ptr(loss, "f32")),
                           "mpir_mlp_train_step")
 
     def selector_set(self, params, mean, scale):
@@ -395,7 +408,8 @@ class Handle:
         panel, T K x K with leading dimension 128, C M x N column-major)."""
         M, K = V.shape
         N = C.shape[1]
-        rc = lib().mpir_larfb(self.h, PREC[prec], M, N, K, ptr(V), ld(V), ptr(T), 1 if trans else 0, ptr(C), ld(C))
+        rc = lib().mpir_larfb(self.h, PREC[prec], M, N, K, ptr(V, "f32"), ld(V), ptr(T, "f32"), 1 if trans else 0,
+                              ptr(C, "f32"), ld(C))
         return self.check(rc, "mpir_larfb")
 
     BD_WHICH = {"F": 0, "Ml": 1, "Mr": 2, "op": 3}

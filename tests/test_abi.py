@@ -65,3 +65,34 @@ def test_workspace_queries_and_argument_checks(libmpir):
 def test_library_is_sm103a_only():
     from paper_2406_16499_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_checks_device_and_element_type():
+    """The binding hands the C ABI raw device pointers: a host tensor, or one
+    whose element type is not the C argument's, is refused before any call
+    (a float32 buffer read as doubles would be read past its end)."""
+    torch = pytest.importorskip("torch")
+    from paper_2406_16499_gb300 import mpir
+
+    class OnDevice:                        # stands in for a CUDA tensor
+        is_cuda, device = True, "cuda:0"
+
+        def __init__(self, dtype, n=4):
+            self.dtype, self.n = dtype, n
+
+        def numel(self):
+            return self.n
+
+        def data_ptr(self):
+            return 0x1000
+
+    with pytest.raises(mpir.MpirError):
+        mpir.ptr(torch.zeros(4, dtype=torch.float64))            # host memory
+    with pytest.raises(mpir.MpirError):
+        mpir.ptr(OnDevice(torch.float32))                        # double* argument
+    with pytest.raises(mpir.MpirError):
+        mpir.ptr(OnDevice(torch.int64), "i32")                   # int* labels
+    assert mpir.ptr(OnDevice(torch.float64)) == 0x1000
+    assert mpir.ptr(OnDevice(torch.float32), "f32") == 0x1000
+    assert mpir.ptr(OnDevice(torch.float64, 0)) is None          # empty -> NULL
+    assert mpir.ptr(None) is None
