@@ -21,6 +21,10 @@ follows:
 * ``lse_kappa`` / ``gls_kappa``        -- condition numbers for the
   forward-error tolerance (power iteration on FP64 factors)
 
+``oracle/gmres.py`` restates GMRES-IR (Sec. 5), ``oracle/selector.py`` the
+selector, and ``oracle/zoracle.py`` the complex problems (Sec. 1 defines both
+over C) with dense numpy factors.
+
 All pins that tie these functions to the paper and to independent
 mathematics are in ``tests/test_oracle_*.py``.
 """

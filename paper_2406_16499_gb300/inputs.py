@@ -14,13 +14,16 @@ Constructions
 * ``lse_paper`` / ``gls_paper``: [A^T, B^T] = W1 Sigma W2 (resp. [W, V]) with a
   prescribed kappa_2, logarithmically spaced singular values (the paper uses
   xLATM1; the spacing mode is not stated, geometric spacing is used here).
+* ``zlse_svd`` / ``zgls_svd``: the complex analogues (the paper defines both
+  problems over C; Haar unitary factors from the QR of a complex Gaussian
+  matrix with the phases of diag(R) folded into Q).
 * ``lse_small`` (m=200, n=100, p=20), ``gls_ar1`` (W 4096x1024 with cond 1e3,
   V the Cholesky factor of an AR(1) covariance, rho=0.9), ``lse_large``
   (m=16384, n=8192, p=1024), ``lse_batch`` (uneven batch): the workloads the
   benchmark and the parity tests use.
 
-Every generator takes an integer seed and returns float64 arrays in
-column-major (Fortran) order.
+Every generator takes an integer seed and returns float64 (complex128 for
+the z-prefixed ones) arrays in column-major (Fortran) order.
 """
 import numpy as np
 
@@ -292,5 +295,54 @@ def gls_svd(seed, n, m, p, cond_w, cond_v):
     V = svd_matrix(g, n, p, logspace_sigma(min(n, p), cond_v))
     x = g.standard_normal(m)
     y = g.standard_normal(p)
+    d = W @ x + V @ y
+    return dict(W=W, V=V, d=d)
+
+
+# ---------------------------------------------------------------- complex --
+
+def zhaar(g, rows, cols=None):
+    """rows x cols matrix with orthonormal columns, Haar-distributed over C
+    (QR of a complex Gaussian matrix, the phases of diag(R) folded into Q)."""
+    cols = rows if cols is None else cols
+    X = (g.standard_normal((rows, cols)) + 1j * g.standard_normal((rows, cols))) / np.sqrt(2.0)
+    Q, R = np.linalg.qr(X)
+    dg = np.diag(R)
+    ph = np.where(np.abs(dg) > 0, dg / np.where(np.abs(dg) > 0, np.abs(dg), 1.0), 1.0)
+    return Q * ph
+
+
+def zsvd_matrix(g, rows, cols, sigma):
+    """U diag(sigma) V^H with Haar unitary U (rows x r), V (cols x r)."""
+    r = len(sigma)
+    U = zhaar(g, rows, r)
+    V = zhaar(g, cols, r)
+    return np.asfortranarray((U * sigma) @ V.conj().T)
+
+
+def zgauss(g, k):
+    return (g.standard_normal(k) + 1j * g.standard_normal(k)) / np.sqrt(2.0)
+
+
+def zlse_svd(seed, m, n, p, cond_a, cond_b, noise=1.0):
+    """Complex LSE: A = U diag(logspace) V^H with cond(A) = cond_a, B
+    likewise with cond_b; d = B x_true, b = A x_true + noise * CN(0,1)."""
+    g = rng(seed)
+    A = zsvd_matrix(g, m, n, logspace_sigma(min(m, n), cond_a))
+    B = (zsvd_matrix(g, p, n, logspace_sigma(p, cond_b)) if p > 0
+         else np.zeros((0, n), dtype=np.complex128, order="F"))
+    x = zgauss(g, n)
+    d = B @ x
+    b = A @ x + noise * zgauss(g, m)
+    return dict(A=A, B=np.asfortranarray(B), b=b, d=d, x_true=x)
+
+
+def zgls_svd(seed, n, m, p, cond_w, cond_v):
+    """Complex GLS: W n x m with cond_w, V n x p with cond_v, d = W x + V y."""
+    g = rng(seed)
+    W = zsvd_matrix(g, n, m, logspace_sigma(m, cond_w))
+    V = zsvd_matrix(g, n, p, logspace_sigma(min(n, p), cond_v))
+    x = zgauss(g, m)
+    y = zgauss(g, p)
     d = W @ x + V @ y
     return dict(W=W, V=V, d=d)
