@@ -118,7 +118,10 @@ int mpir_set_stream(mpir_handle handle, void *stream);
 
 /* Caller-provided device workspace (e.g. a framework allocation).  The
  * handle then never calls cudaMalloc for the workspace.  bytes must be at
- * least what the *_workspace_size queries return; ptr 256-byte aligned. */
+ * least what the *_workspace_size queries return; ptr 256-byte aligned.
+ * Factors held from an earlier mpir_*_factor are dropped (the step-level
+ * calls then return MPIR_UNSUPPORTED until the next factorization); the same
+ * holds after a call that grows the handle's own workspace. */
 int mpir_set_workspace(mpir_handle handle, void *ptr, size_t bytes);
 
 /* Workspace a solve of the given shape needs (bytes). */
@@ -304,7 +307,8 @@ int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, 
  * C: M x N (ldc a multiple of 4, C 16-byte aligned).  All FP32 device
  * arrays, K <= 128.  prec: MPIR_FP32 (three TF32 products, FP32-class) or
  * MPIR_TF32 (one TF32 product).  Returns 0, a negative argument index, or
- * MPIR_UNSUPPORTED. */
+ * MPIR_UNSUPPORTED.  Uses the handle's workspace as scratch: factors held
+ * from an earlier mpir_*_factor are dropped. */
 int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int ldv,
                const float *T, int trans, float *C, int ldc);
 

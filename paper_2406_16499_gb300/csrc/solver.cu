@@ -384,10 +384,10 @@ int ensure_ws(mpir_ctx *h, size_t bytes)
         cudaStreamSynchronize(h->stream);
         if (h->side) cudaStreamSynchronize(h->side);
         if (h->crit) cudaStreamSynchronize(h->crit);
-    if (h->aux) cudaStreamSynchronize(h->aux);
         if (h->aux) cudaStreamSynchronize(h->aux);
         cudaFree(h->ws); h->ws = nullptr; h->ws_bytes = 0;
     }
+    h->fs.kind = Kind::NONE;             // factors held in the old buffer are gone
     if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "workspace cudaMalloc failed"); }
     h->ws_bytes = bytes;
     h->ws_owned = true;
@@ -1600,6 +1600,7 @@ int mpir_set_workspace(mpir_handle h, void *ptr, size_t bytes)
     h->ws = ptr;
     h->ws_bytes = ptr ? bytes : 0;
     h->ws_owned = false;
+    h->fs.kind = Kind::NONE;             // held factors lived in the previous workspace
     return 0;
 }
 
@@ -2165,6 +2166,7 @@ int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int
     if (!C && M * N > 0) return -10;
     if (ldc < std::max(1, M) || ldc % 4) return -11;
     RC(ensure_ws(h, geqrf_ws_bytes(M, N)));
+    h->fs.kind = Kind::NONE;             // the workspace holding any factors is used as scratch
     clear_dev_flags(h);
     RC(larfb_tc(V, ldv, M, K, T, trans, C, ldc, N, gemm_prec(prec), h->ws, h->sc.err, h->stream));
     RC(cuda_check(h, "mpir_larfb"));
