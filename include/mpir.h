@@ -114,6 +114,8 @@ void mpir_default_opts(mpir_opts *opts);
  * the handle's device current (the convention of CUDA library handles). */
 int mpir_create(mpir_handle *handle, int device, void *stream);
 int mpir_destroy(mpir_handle handle);
+/* Later calls run on `stream`; it first waits for the work already queued
+ * on the handle's previous stream (and the handle's internal streams). */
 int mpir_set_stream(mpir_handle handle, void *stream);
 
 /* Caller-provided device workspace (e.g. a framework allocation).  The

@@ -273,6 +273,7 @@ struct mpir_ctx {
     std::string err;
     FactorState fs;
     cudaEvent_t ev[8];
+    cudaEvent_t sw_ev = nullptr;         // orders a stream switch after queued work
     void *rws = nullptr;         // scratch of the standalone residual entry points
     size_t rws_bytes = 0;
     BatchArena ba;               // batched solves: tables, results, tuned shapes, graph
@@ -1525,6 +1526,7 @@ int mpir_create(mpir_handle *handle, int device, void *stream)
     h->sc.part_bytes = part_bytes;
     if (cudaMallocHost(&h->hbuf, 64 * sizeof(double)) != cudaSuccess) { cudaFree(h->scratch_base); delete h; cudaGetLastError(); return MPIR_CUDA_ERROR; }
     for (int i = 0; i < 8; i++) cudaEventCreate(&h->ev[i]);
+    cudaEventCreateWithFlags(&h->sw_ev, cudaEventDisableTiming);
     cudaDeviceSynchronize();
     *handle = h;
     return 0;
@@ -1578,6 +1580,7 @@ int mpir_destroy(mpir_handle h)
     if (h->sel) cudaFree(h->sel);
     if (h->sel_s) cudaFree(h->sel_s);
     for (int i = 0; i < 8; i++) cudaEventDestroy(h->ev[i]);
+    if (h->sw_ev) cudaEventDestroy(h->sw_ev);
     delete h;
     return 0;
 }
@@ -1585,7 +1588,15 @@ int mpir_destroy(mpir_handle h)
 int mpir_set_stream(mpir_handle h, void *stream)
 {
     if (!h) return -1;
-    h->stream = (cudaStream_t)stream;
+    const cudaStream_t ns = (cudaStream_t)stream;
+    if (ns != h->stream && h->sw_ev) {
+        // work queued on the old stream, and on the internal streams joined
+        // into it, finishes before the new stream touches the handle's buffers
+        join_side(h, h->stream);
+        cudaEventRecord(h->sw_ev, h->stream);
+        cudaStreamWaitEvent(ns, h->sw_ev, 0);
+    }
+    h->stream = ns;
     return 0;
 }
 
