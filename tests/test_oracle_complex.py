@@ -231,3 +231,20 @@ def test_complex_refinement_fails_beyond_the_single_precision_limit():
     P = I.zlse_svd(111, 60, 30, 6, 1e10, 1e1)
     out = Z.zlse_solve(P["A"], P["B"], P["b"], P["d"], fact="fp32", maxit=15)
     assert out["status"] != 0
+
+
+def test_complex_generators_realise_the_requested_spectra():
+    """zhaar gives orthonormal columns over C, zsvd_matrix the requested
+    singular values, the problem generators consistent right-hand sides, and
+    a seed always the same arrays."""
+    g = I.rng(5)
+    Q = I.zhaar(g, 30, 12)
+    assert np.iscomplexobj(Q) and np.abs(Q.conj().T @ Q - np.eye(12)).max() < 1e-13
+    sig = I.logspace_sigma(12, 1e4)
+    M = I.zsvd_matrix(g, 30, 12, sig)
+    assert np.allclose(np.linalg.svd(M, compute_uv=False), sig, rtol=1e-10)
+    P = I.zlse_svd(4, 20, 10, 3, 1e2, 1e1)
+    assert np.linalg.norm(P["B"] @ P["x_true"] - P["d"]) < 1e-13 * np.linalg.norm(P["d"])
+    G = I.zgls_svd(6, 15, 5, 18, 1e2, 1e1)
+    assert np.iscomplexobj(G["W"]) and np.iscomplexobj(G["d"])
+    assert np.array_equal(I.zlse_svd(4, 20, 10, 3, 1e2, 1e1)["A"], P["A"])
