@@ -1,0 +1,41 @@
+"""The benchmark's algorithmic work counts (the numerator of its roofline)
+against the textbook Householder flop counts.
+
+QR of an M x N matrix (M >= N): 2 M N^2 - 2 N^3 / 3 flops; applying its N
+reflectors to K columns: 4 M N K - 2 N^2 K.  The GQR of the n = p = 4096,
+m = 1024 GLS workload is then 7.87e9 (QR of W) + 6.01e10 (Q^T V) + 9.16e10
+(RQ of the n x p C) = 1.60e11 flops; the blocked compact-WY form adds the
+small triangular products of each panel (a few per cent).
+"""
+import os
+import sys
+
+import pytest
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+import bench  # noqa: E402
+
+
+def qr_flops(M, N):
+    return 2.0 * M * N * N - 2.0 * N ** 3 / 3.0
+
+
+@pytest.mark.parametrize("M,N", [(4096, 1024), (4096, 4096), (2000, 300)])
+def test_blocked_qr_count_matches_householder(M, N):
+    pf, lf = bench.qr_work(M, N)
+    assert pf > 0 and lf > 0
+    assert abs((pf + lf) / qr_flops(M, N) - 1) < 0.03
+
+
+def test_gls_workload_count_matches_the_gqr():
+    n, m, p = 4096, 1024, 4096
+    w = bench.gls_work(n, m, p)
+    textbook = qr_flops(n, m) + (4.0 * n * m * p - 2.0 * m * m * p) + qr_flops(p, n)
+    assert abs(textbook / 1.60e11 - 1) < 0.005
+    assert abs(w["factor_flops"] / textbook - 1) < 0.03
+    assert w["panel_flops"] < 0.02 * w["factor_flops"]        # the panels are ~1 % of the work
+    assert w["resid_bytes"] == 8.0 * (n * m + n * p)            # one FP64 read of W and V
+
+
+def test_fp32_simt_peak_from_unit_counts():
+    assert bench.fp32_simt_peak(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
