@@ -22,9 +22,12 @@ def qr_flops(M, N):
 
 @pytest.mark.parametrize("M,N", [(4096, 1024), (4096, 4096), (2000, 300)])
 def test_blocked_qr_count_matches_householder(M, N):
+    """At least the unblocked count, and above it by the compact-WY overhead,
+    which is of order nb / N (nb = 32 reflectors per panel)."""
     pf, lf = bench.qr_work(M, N)
     assert pf > 0 and lf > 0
-    assert abs((pf + lf) / qr_flops(M, N) - 1) < 0.03
+    excess = (pf + lf) / qr_flops(M, N) - 1
+    assert 0 <= excess <= 4 * 32 / N
 
 
 def test_gls_workload_count_matches_the_gqr():
