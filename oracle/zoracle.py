@@ -29,6 +29,9 @@ as library primitives, one Householder reflector at a time.
                                (eq. aug-LSE / aug-GLS) solved in complex128 and
                                refined with extended-precision residuals
 * ``zlse_metrics`` / ``zgls_metrics`` -- stop ratios and err-1 (Tables 4, 5)
+* ``ZLseBD`` / ``ZGlsBD`` / ``zgmres`` / ``zlse_gmres_ir`` / ``zgls_gmres_ir``
+                            -- GMRES-IR (Sec. 5) with the block-diagonal split
+                               preconditioners, conjugate transposes throughout
 
 Factors are computed in complex64 (fact='fp32') or complex128 ('fp64').
 Pins: tests/test_oracle_complex.py.
@@ -355,3 +358,190 @@ def zgls_metrics(W, V, d, x, y, z):
     den = np.linalg.norm(W) * np.linalg.norm(x) + np.linalg.norm(V) * np.linalg.norm(y) + np.linalg.norm(d)
     e_con = float(np.linalg.norm(np.asarray(f[1], np.complex128))) / (den or 1.0)
     return dict(eta=max(ratios), ratios=ratios, e_con=e_con)
+
+
+# ------------------------------------------------------------ GMRES-IR --
+# Sec. 5 over C: the scaled augmented matrices F~(alpha, beta), the
+# block-diagonal split preconditioners with conjugate transposes
+# (eq. lse-bdpre-mlarge, m >= n; eq. gls-bdpre-plarge, n <= p), restarted
+# GMRES in complex128, and the outer refinement loop.
+
+class ZLseBD:
+    """F~ = [a I 0 A; 0 0 b B; A^H b B^H 0],
+    M_l = diag(a^-1/2 I, a^-1/2 b^-1 Y R^-1, a^1/2 T1^-H Q),
+    M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-H Y^H, a^1/2 Q^H T1^-1),
+    T1 the leading n x n block of T, Y = T1(n-p+1:n, n-p+1:n) (m >= n)."""
+
+    def __init__(self, F, A, B, alpha, beta):
+        m, n, p = F["m"], F["n"], F["p"]
+        if m < n:
+            raise ValueError("eq. lse-bdpre-mlarge needs m >= n")
+        self.m, self.n, self.p = m, n, p
+        self.A, self.B = np.asarray(A, np.complex128), np.asarray(B, np.complex128)
+        self.Q = np.asarray(F["Q"], np.complex128)
+        self.R = np.asarray(F["R"], np.complex128)
+        self.T1 = np.asarray(F["T"], np.complex128)[:n, :n]
+        self.Y = self.T1[n - p:, n - p:]
+        self.a, self.b = alpha, beta
+
+    def split(self, u):
+        return u[:self.m], u[self.m:self.m + self.p], u[self.m + self.p:]
+
+    def Fmul(self, u):
+        u1, u2, u3 = self.split(u)
+        return np.concatenate([self.a * u1 + self.A @ u3, self.b * (self.B @ u3),
+                               _h(self.A) @ u1 + self.b * (_h(self.B) @ u2)])
+
+    def Ml(self, u):
+        u1, u2, u3 = self.split(u)
+        a, b = self.a, self.b
+        o2 = self.Y @ solve_triangular(self.R, u2) if self.p else u2
+        o3 = solve_triangular(_h(self.T1), self.Q @ u3, lower=True)
+        return np.concatenate([a ** -0.5 * u1, a ** -0.5 / b * o2, a ** 0.5 * o3])
+
+    def Mr(self, t):
+        t1, t2, t3 = self.split(t)
+        a, b = self.a, self.b
+        o2 = solve_triangular(_h(self.R), _h(self.Y) @ t2, lower=True) if self.p else t2
+        o3 = _h(self.Q) @ solve_triangular(self.T1, t3)
+        return np.concatenate([a ** -0.5 * t1, a ** -0.5 / b * o2, a ** 0.5 * o3])
+
+
+class ZGlsBD:
+    """F~ = [a I V^H 0; V 0 b W; 0 b W^H 0],
+    M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^H, a^-1/2 b^-1 S^H R^-H),
+    M_r = diag(a^-1/2 I, a^1/2 Q T2^-H, a^-1/2 b^-1 R^-1 S),
+    T = [0, T2] (n <= p), S = T2(1:m, 1:m)."""
+
+    def __init__(self, F, W, V, alpha, beta):
+        n, m, p = F["n"], F["m"], F["p"]
+        if n > p:
+            raise ValueError("eq. gls-bdpre-plarge needs n <= p")
+        self.n, self.m, self.p = n, m, p
+        self.W, self.V = np.asarray(W, np.complex128), np.asarray(V, np.complex128)
+        self.Q = np.asarray(F["Q"], np.complex128)
+        self.R = np.asarray(F["R"], np.complex128)
+        self.T2 = np.asarray(F["T"], np.complex128)[:, p - n:]
+        self.S = self.T2[:m, :m]
+        self.a, self.b = alpha, beta
+
+    def split(self, u):
+        return u[:self.p], u[self.p:self.p + self.n], u[self.p + self.n:]
+
+    def Fmul(self, u):
+        u1, u2, u3 = self.split(u)
+        return np.concatenate([self.a * u1 + _h(self.V) @ u2, self.V @ u1 + self.b * (self.W @ u3),
+                               self.b * (_h(self.W) @ u2)])
+
+    def Ml(self, u):
+        u1, u2, u3 = self.split(u)
+        a, b = self.a, self.b
+        o2 = solve_triangular(self.T2, _h(self.Q) @ u2)
+        o3 = _h(self.S) @ solve_triangular(_h(self.R), u3, lower=True) if self.m else u3
+        return np.concatenate([a ** -0.5 * u1, a ** 0.5 * o2, a ** -0.5 / b * o3])
+
+    def Mr(self, t):
+        t1, t2, t3 = self.split(t)
+        a, b = self.a, self.b
+        o2 = self.Q @ solve_triangular(_h(self.T2), t2, lower=True)
+        o3 = solve_triangular(self.R, self.S @ t3) if self.m else t3
+        return np.concatenate([a ** -0.5 * t1, a ** 0.5 * o2, a ** -0.5 / b * o3])
+
+
+def zgmres(op, rhs, tol=1e-8, restart=30, maxit=300):
+    """Restarted GMRES(restart) in complex128 from x0 = 0: modified
+    Gram-Schmidt Arnoldi with Hermitian inner products; the small
+    least-squares problem min ||beta e1 - H y|| by a library solve.
+    Returns (x, iterations, relative residual)."""
+    rhs = np.asarray(rhs, np.complex128)
+    nb = np.linalg.norm(rhs)
+    x = np.zeros_like(rhs)
+    if nb == 0:
+        return x, 0, 0.0
+    total, rel = 0, 1.0
+    r = rhs.copy()
+    while total < maxit:
+        beta0 = np.linalg.norm(r)
+        if beta0 <= tol * nb:
+            break
+        Vb = [r / beta0]
+        H = np.zeros((restart + 1, restart), np.complex128)
+        e1 = np.zeros(restart + 1, np.complex128)
+        e1[0] = beta0
+        y = np.zeros(0, np.complex128)
+        for j in range(restart):
+            w = op(Vb[j])
+            total += 1
+            for i in range(j + 1):
+                H[i, j] = np.vdot(Vb[i], w)
+                w = w - H[i, j] * Vb[i]
+            H[j + 1, j] = np.linalg.norm(w)
+            Vb.append(w / H[j + 1, j] if H[j + 1, j] != 0 else w)
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], e1[:j + 2], rcond=None)[0]
+            res = np.linalg.norm(e1[:j + 2] - H[:j + 2, :j + 1] @ y)
+            if res <= tol * nb or total >= maxit:
+                break
+        x = x + np.column_stack(Vb[:len(y)]) @ y
+        r = rhs - op(x)
+        rel = np.linalg.norm(r) / nb
+        if rel <= tol:
+            break
+    return x, total, rel
+
+
+def zlse_gmres_ir(A, B, b, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_tol=1e-8, inner_maxit=300,
+                  beta=1.0):
+    """Complex LSE GMRES-IR (m >= n), the readings of the real oracle:
+    alpha = max(||r0||, sqrt(u) ||A||_F ||x0||), beta = 1."""
+    A, B = np.asarray(A, np.complex128), np.asarray(B, np.complex128)
+    b, d = np.asarray(b, np.complex128), np.asarray(d, np.complex128)
+    F = zlse_factor(A, B, fact)
+    x = zlse_nullspace(F, b, d)
+    r = b - A @ x
+    v = zlse_init_v(F, A, r)
+    u = np.finfo(np.float64).eps / 2
+    alpha = max(np.linalg.norm(r), np.sqrt(u) * np.linalg.norm(A) * np.linalg.norm(x)) or 1.0
+    P = ZLseBD(F, A, B, alpha, beta)
+    op = lambda t: P.Ml(P.Fmul(P.Mr(t)))
+    status, inner, ratios, it = 3, 0, [np.inf] * 3, 0
+    a, bb = alpha, beta
+    for it in range(maxit):
+        f = zlse_residual(A, B, b, d, x, r, v)
+        ratios = _lse_ratios(A, B, b, d, x, r, v, f)
+        if max(ratios) <= tol:
+            status = 0
+            break
+        rhs = np.concatenate([a ** 0.5 * f[0], a ** 0.5 * bb * f[1], a ** -0.5 * f[2]])
+        t, k, _ = zgmres(op, P.Ml(rhs), inner_tol, restart, inner_maxit)
+        inner += k
+        d1, d2, d3 = P.split(P.Mr(t))
+        r, v, x = r + a ** 0.5 * d1, v - a ** 0.5 * bb * d2, x + a ** -0.5 * d3
+    return dict(x=x, r=r, v=v, status=status, iters=it, inner_iters=inner, ratios=ratios, alpha=alpha)
+
+
+def zgls_gmres_ir(W, V, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_tol=1e-8, inner_maxit=300,
+                  beta=1.0):
+    """Complex GLS GMRES-IR (n <= p): alpha = max(||y0||, sqrt(u) ||V||_F ||z0||)."""
+    W, V = np.asarray(W, np.complex128), np.asarray(V, np.complex128)
+    d = np.asarray(d, np.complex128)
+    F = zgls_factor(W, V, fact)
+    x, y = zgls_paige(F, d)
+    z = zgls_init_z(F, y)
+    u = np.finfo(np.float64).eps / 2
+    alpha = max(np.linalg.norm(y), np.sqrt(u) * np.linalg.norm(V) * np.linalg.norm(z)) or 1.0
+    P = ZGlsBD(F, W, V, alpha, beta)
+    op = lambda t: P.Ml(P.Fmul(P.Mr(t)))
+    status, inner, ratios, it = 3, 0, [np.inf] * 3, 0
+    a, bb = alpha, beta
+    for it in range(maxit):
+        f = zgls_residual(W, V, d, x, y, z)
+        ratios = _gls_ratios(W, V, d, x, y, z, f)
+        if max(ratios) <= tol:
+            status = 0
+            break
+        rhs = np.concatenate([a ** 0.5 * f[0], a ** -0.5 * f[1], a ** 0.5 * bb * f[2]])
+        t, k, _ = zgmres(op, P.Ml(rhs), inner_tol, restart, inner_maxit)
+        inner += k
+        d1, d2, d3 = P.split(P.Mr(t))
+        y, z, x = y + a ** 0.5 * d1, z - a ** -0.5 * d2, x + a ** 0.5 * bb * d3
+    return dict(x=x, y=y, z=z, status=status, iters=it, inner_iters=inner, ratios=ratios, alpha=alpha)

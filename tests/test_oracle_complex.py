@@ -248,3 +248,66 @@ def test_complex_generators_realise_the_requested_spectra():
     G = I.zgls_svd(6, 15, 5, 18, 1e2, 1e1)
     assert np.iscomplexobj(G["W"]) and np.iscomplexobj(G["d"])
     assert np.array_equal(I.zlse_svd(4, 20, 10, 3, 1e2, 1e1)["A"], P["A"])
+
+
+# ----------------------------------------------------- GMRES-IR over C --
+
+def _dense(op, N):
+    return np.column_stack([op(e) for e in np.eye(N, dtype=np.complex128)])
+
+
+def _bd_roots():
+    return np.sort(np.roots([1, -1, -2, 1]).real), np.array([(1 - 5 ** 0.5) / 2, (1 + 5 ** 0.5) / 2])
+
+
+@pytest.mark.parametrize("m,n,p,a,b", [(14, 9, 4, 0.7, 1.3), (12, 12, 5, 1.0, 1.0)])
+def test_complex_lse_preconditioned_matrix_spectrum(m, n, p, a, b):
+    """Sec. 5.2 over C: with exact factors M_l F~ M_r is Hermitian with the
+    eigenvalues 1, (1 +- sqrt 5)/2 and the roots of x^3 - x^2 - 2x + 1
+    (multiplicities m-n, n-p, p), so kappa_2 < 9.0985."""
+    from oracle import zoracle as Z
+    P = I.zlse_svd(121 + m, m, n, p, 1e3, 1e1)
+    bd = Z.ZLseBD(Z.zlse_factor(P["A"], P["B"], "fp64"), P["A"], P["B"], a, b)
+    M = _dense(lambda t: bd.Ml(bd.Fmul(bd.Mr(t))), m + n + p)
+    assert np.abs(M - M.conj().T).max() < 1e-12
+    cubic, gold = _bd_roots()
+    want = np.sort(np.concatenate([np.repeat(cubic, p), np.repeat(gold, n - p), np.ones(m - n)]))
+    assert np.abs(np.sort(np.linalg.eigvalsh(M)) - want).max() < 1e-10
+    assert np.linalg.cond(M) <= 9.0985
+
+
+@pytest.mark.parametrize("n,m,p,a,b", [(9, 3, 12, 0.6, 1.7), (10, 4, 10, 1.0, 1.0)])
+def test_complex_gls_preconditioned_matrix_spectrum(n, m, p, a, b):
+    """Sec. 5.3 over C: multiplicities m, n-m, p-n."""
+    from oracle import zoracle as Z
+    G = I.zgls_svd(131 + n, n, m, p, 1e3, 1e1)
+    bd = Z.ZGlsBD(Z.zgls_factor(G["W"], G["V"], "fp64"), G["W"], G["V"], a, b)
+    M = _dense(lambda t: bd.Ml(bd.Fmul(bd.Mr(t))), m + n + p)
+    cubic, gold = _bd_roots()
+    want = np.sort(np.concatenate([np.repeat(cubic, m), np.repeat(gold, n - m), np.ones(p - n)]))
+    assert np.abs(np.sort(np.linalg.eigvalsh(M)) - want).max() < 1e-10
+
+
+def test_complex_gmres_full_restart_is_exact():
+    from oracle import zoracle as Z
+    g = np.random.default_rng(8)
+    K = g.standard_normal((30, 30)) + 1j * g.standard_normal((30, 30)) + 8 * np.eye(30)
+    rhs = g.standard_normal(30) + 1j * g.standard_normal(30)
+    x, k, rel_ = Z.zgmres(lambda v: K @ v, rhs, tol=1e-13, restart=30, maxit=30)
+    assert rel_ < 1e-12 and rel(x, np.linalg.solve(K, rhs)) < 1e-10
+
+
+def test_complex_gmres_ir_beyond_the_classical_limit():
+    """Table 4 over C: at kappa = 1e9 classical IR with complex64 factors
+    does not converge, GMRES-IR with the split preconditioner does."""
+    from oracle import zoracle as Z
+    P = I.zlse_svd(5, 120, 40, 6, 1e9, 1e1)
+    A, B, b, d = P["A"], P["B"], P["b"], P["d"]
+    assert Z.zlse_solve(A, B, b, d, maxit=15)["status"] != 0
+    out = Z.zlse_gmres_ir(A, B, b, d)
+    met = Z.zlse_metrics(A, B, b, d, out["x"], out["r"], out["v"])
+    assert out["status"] == 0 and met["eta"] < 1e-14
+    G = I.zgls_svd(6, 40, 10, 48, 1e3, 1e1)
+    out = Z.zgls_gmres_ir(G["W"], G["V"], G["d"])
+    met = Z.zgls_metrics(G["W"], G["V"], G["d"], out["x"], out["y"], out["z"])
+    assert out["status"] == 0 and met["eta"] < 1e-14
