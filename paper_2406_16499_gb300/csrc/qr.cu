@@ -15,7 +15,6 @@ namespace mpir {
 
 constexpr int PANEL_NT = 512;
 constexpr int PANEL_RPT = 2;                      // rows held per thread
-constexpr int PANEL_ROWS_PER_CTA = PANEL_NT * PANEL_RPT;
 constexpr int PANEL_MAX_CLUSTER = 16;
 
 // ---------------------------------------------------------------------------
