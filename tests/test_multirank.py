@@ -75,3 +75,17 @@ def test_reference_arm_nonzero_rank_exits_without_work():
                         "--warmup", "1"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_each_rank_draws_its_own_problem(monkeypatch):
+    """Replicas: every rank solves an independent problem of the same shape
+    (seed offset by rank), so the job's throughput counts N distinct solves."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2406_16499_gb300 import inputs as I
+    monkeypatch.setattr(bench, "N_", 64)
+    monkeypatch.setattr(bench, "M_", 16)
+    g0, g1 = bench.make_inputs(0), bench.make_inputs(1)
+    assert g0["W"].shape == g1["W"].shape == (64, 16) and g0["V"].shape == (64, 64)
+    assert not (g0["W"] == g1["W"]).all()
+    assert (bench.make_inputs(1)["d"] == g1["d"]).all()
