@@ -82,7 +82,6 @@ def test_each_rank_draws_its_own_problem(monkeypatch):
     (seed offset by rank), so the job's throughput counts N distinct solves."""
     sys.path.insert(0, ROOT)
     import bench
-    from paper_2406_16499_gb300 import inputs as I
     monkeypatch.setattr(bench, "N_", 64)
     monkeypatch.setattr(bench, "M_", 16)
     g0, g1 = bench.make_inputs(0), bench.make_inputs(1)
