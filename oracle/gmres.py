@@ -8,7 +8,8 @@ Restates the paper's GMRES-IR for LSE and GLS:
 * the block-diagonal split preconditioners M_l, M_r built from the
   low-precision factors: LSE m >= n (eq. lse-bdpre-mlarge) and n > m
   (eq. lse-bdpre-nlarge), GLS n <= p (eq. gls-bdpre-plarge) and n > p
-  (eq. gls-bdpre-nlarge);
+  (eq. gls-bdpre-nlarge); and the left preconditioners of Sec. 5.1
+  (eq. lse-leftpre, eq. gls-leftpre), applied through Alg. 1 / Alg. 3;
 * restarted GMRES in FP64 with modified Gram-Schmidt Arnoldi and Givens
   rotations (Sec. 6.1: GMRES runs entirely in double precision);
 * the outer refinement loop of Alg. 2 / Alg. 4 with the correction system
@@ -24,8 +25,8 @@ factors are applied with the oracle's reflector routines.
 import numpy as np
 from scipy.linalg import solve_triangular
 
-from . import (R_T, apply, gls_factor, gls_init_z, gls_paige, gls_residual, lse_factor, lse_init_v,
-               lse_nullspace, lse_residual)
+from . import (R_T, apply, gls_correction, gls_factor, gls_init_z, gls_paige, gls_residual, lse_correction,
+               lse_factor, lse_init_v, lse_nullspace, lse_residual)
 
 U64 = np.finfo(np.float64).eps / 2
 
@@ -143,6 +144,49 @@ class GlsBD:
         return a ** 0.5 * d1, -(a ** -0.5) * d2, a ** 0.5 * b * d3
 
 
+class LseLeft(LseBD):
+    """The left preconditioner of Sec. 5.1 (eq. lse-leftpre): M ~ F~^{-1},
+    applied, as the paper does, by the correction solver on the factors.
+    F~ u = g is the correction system of Alg. 1 with f = (g1, g2 / b, a g3):
+    (dr, dv, dx) -> u = (dr / a, -dv / (a b), dx).  M_r = I."""
+
+    def __init__(self, F, A, B, alpha, beta):
+        m, n, p = F["m"], F["n"], F["p"]
+        self.F, self.A, self.B = F, np.asarray(A), np.asarray(B)
+        self.m, self.n, self.p = m, n, p
+        self.a, self.b = alpha, beta
+
+    def Ml(self, g):
+        g1, g2, g3 = self.split(g)
+        a, b = self.a, self.b
+        dr, dv, dx = lse_correction(self.F, g1, g2 / b, a * g3)
+        return np.concatenate([dr / a, -dv / (a * b), dx])
+
+    def Mr(self, t):
+        return t
+
+
+class GlsLeft(GlsBD):
+    """The left preconditioner of Sec. 5.1 (eq. gls-leftpre), applied by
+    Alg. 3: F~ u = g is the correction system with f = (g1, a g2, g3 / b):
+    (dy, dz, dx) -> u = (dy / a, -dz, dx / (a b)).  M_r = I."""
+
+    def __init__(self, F, W, V, alpha, beta):
+        n, m, p = F["n"], F["m"], F["p"]
+        self.F, self.W, self.V = F, np.asarray(W), np.asarray(V)
+        self.n, self.m, self.p = n, m, p
+        self.a, self.b = alpha, beta
+
+    def Ml(self, g):
+        g1, g2, g3 = self.split(g)
+        a, b = self.a, self.b
+        dy, dz, dx = gls_correction(self.F, g1, a * g2, g3 / b)
+        return np.concatenate([dy / a, -dz, dx / (a * b)])
+
+    def Mr(self, t):
+        return t
+
+
 def gmres(op, rhs, tol=1e-8, restart=30, maxit=300):
     """Restarted GMRES(restart) from x0 = 0, modified Gram-Schmidt Arnoldi,
     Givens rotations; stops when ||rhs - op(x)|| <= tol ||rhs||.
@@ -197,8 +241,9 @@ def gmres(op, rhs, tol=1e-8, restart=30, maxit=300):
 
 
 def lse_gmres_ir(A, B, b, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_tol=1e-8,
-                 inner_maxit=300, beta=1.0):
-    """LSE GMRES-IR with the block-diagonal split preconditioner."""
+                 inner_maxit=300, beta=1.0, precond="bd"):
+    """LSE GMRES-IR with the block-diagonal split preconditioner (precond
+    'bd') or the left preconditioner of Sec. 5.1 ('left')."""
     A, B = np.asarray(A, dtype=np.float64), np.asarray(B, dtype=np.float64)
     b, d = np.asarray(b, dtype=np.float64), np.asarray(d, dtype=np.float64)
     F = lse_factor(A, B, fact)
@@ -208,7 +253,7 @@ def lse_gmres_ir(A, B, b, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner
     nA, nB = np.linalg.norm(A), np.linalg.norm(B)
     alpha = max(np.linalg.norm(r), np.sqrt(U64) * nA * np.linalg.norm(x))
     alpha = alpha if alpha > 0 else 1.0
-    P = LseBD(F, A, B, alpha, beta)
+    P = (LseLeft if precond == "left" else LseBD)(F, A, B, alpha, beta)
     op = lambda t: P.Ml(P.Fmul(P.Mr(t)))
     status, inner, ratios = 3, 0, [0.0, 0.0, 0.0]
     it = 0
@@ -231,8 +276,9 @@ def lse_gmres_ir(A, B, b, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner
 
 
 def gls_gmres_ir(W, V, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_tol=1e-8,
-                 inner_maxit=300, beta=1.0):
-    """GLS GMRES-IR with the block-diagonal split preconditioner."""
+                 inner_maxit=300, beta=1.0, precond="bd"):
+    """GLS GMRES-IR with the block-diagonal split preconditioner (precond
+    'bd') or the left preconditioner of Sec. 5.1 ('left')."""
     W, V = np.asarray(W, dtype=np.float64), np.asarray(V, dtype=np.float64)
     d = np.asarray(d, dtype=np.float64)
     F = gls_factor(W, V, fact)
@@ -241,7 +287,7 @@ def gls_gmres_ir(W, V, d, fact="fp32", tol=2e-15, maxit=40, restart=30, inner_to
     nW, nV = np.linalg.norm(W), np.linalg.norm(V)
     alpha = max(np.linalg.norm(y), np.sqrt(U64) * nV * np.linalg.norm(z))
     alpha = alpha if alpha > 0 else 1.0
-    P = GlsBD(F, W, V, alpha, beta)
+    P = (GlsLeft if precond == "left" else GlsBD)(F, W, V, alpha, beta)
     op = lambda t: P.Ml(P.Fmul(P.Mr(t)))
     status, inner, ratios = 3, 0, [0.0, 0.0, 0.0]
     it = 0
