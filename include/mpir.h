@@ -42,9 +42,11 @@
 extern "C" {
 #endif
 
-/* Factorization precision u_f (Sec. 3; the panel is always FP32 for the
- * three low-precision kinds, the trailing-update GEMM operands are rounded
- * to the named type).  MPIR_FP64 is the fixed-precision FP64 path. */
+/* Factorization precision u_f (Sec. 3).  The panel is FP32 for the three
+ * low-precision kinds; the tensor-core trailing updates use three TF32
+ * products (MPIR_FP32, FP32-accurate) or one (MPIR_TF32; MPIR_BF16 runs the
+ * same single TF32 product in this build).  MPIR_FP64 is the
+ * fixed-precision FP64 path. */
 typedef enum {
     MPIR_BF16 = 0,
     MPIR_TF32 = 1,
