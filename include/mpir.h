@@ -202,6 +202,10 @@ int mpir_batched_set_shape(mpir_handle h, int group);
 int mpir_batched_get_shape(mpir_handle h, int bucket, int *group, size_t *smem_bytes,
                            int *problems);
 
+/* GLS analogue of lse_solve_batched (arrays of device pointers and sizes,
+ * per-problem infos, worst status returned).  This build solves the problems
+ * one after the other with gls_solve on the handle's stream; the persistent
+ * batched kernel covers LSE only. */
 int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m,
                       const int *p, const double *const *W, const int *ldw,
                       const double *const *V, const int *ldv,
