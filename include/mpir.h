@@ -45,7 +45,7 @@ extern "C" {
 /* Factorization precision u_f (Sec. 3).  The panel is FP32 for the three
  * low-precision kinds; the tensor-core trailing updates use three TF32
  * products (MPIR_FP32, FP32-accurate) or one (MPIR_TF32; MPIR_BF16 runs the
- * same single TF32 product in this build).  MPIR_FP64 is the
+ * same single TF32 product: there is no bfloat16 tensor-core path).  MPIR_FP64 is the
  * fixed-precision FP64 path. */
 typedef enum {
     MPIR_BF16 = 0,
@@ -71,7 +71,7 @@ enum {
     MPIR_SINGULAR_T = 2,      /* T11 (LSE) / T22 (GLS) has a zero diagonal       */
     MPIR_NOT_CONVERGED = 3,   /* maxit reached without meeting the stop test     */
     MPIR_NONFINITE = 4,       /* non-finite residual or input                    */
-    MPIR_UNSUPPORTED = 5,     /* size or option outside what this build handles  */
+    MPIR_UNSUPPORTED = 5,     /* size or option outside what the library handles */
     MPIR_CUDA_ERROR = 6,      /* a CUDA call failed (message: mpir_last_error)   */
     MPIR_DEVICE_TIMEOUT = 7   /* a bounded device-side wait gave up              */
 };
@@ -203,8 +203,8 @@ int mpir_batched_get_shape(mpir_handle h, int bucket, int *group, size_t *smem_b
                            int *problems);
 
 /* GLS analogue of lse_solve_batched (arrays of device pointers and sizes,
- * per-problem infos, worst status returned).  This build solves the problems
- * one after the other with gls_solve on the handle's stream; the persistent
+ * per-problem infos, worst status returned).  The problems are solved one
+ * after the other with gls_solve on the handle's stream; the persistent
  * batched kernel covers LSE only. */
 int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m,
                       const int *p, const double *const *W, const int *ldw,
