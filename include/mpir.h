@@ -357,7 +357,9 @@ int mpir_gls_residual_noalloc(int n, int m, int p, const double *W, int ldw,
  * log ||d||, log(||A||_F/||B||_F), log kappa^(A), log kappa^(B),
  * log kappa^([A; B]), log(GRQ flop estimate); kappa^ = sigma_max/sigma_min
  * of the bidiagonal of min(16, rows, columns) Golub-Kahan-Lanczos steps
- * (FP64, no reorthogonalization) started from s (device, length n).  GLS: log n,
+ * started from s (device, length n; a wide block starts from M^T M s),
+ * computed with FP32 vectors and products, each new vector reorthogonalized
+ * once, stopping only at breakdown (an entry below 2^-26 of the largest).  GLS: log n,
  * log m, log(p+1), m/n, n/p, kind 1, 0, log ||W||_F, log ||V||_F, log ||d||,
  * 0, log(||W||_F/||V||_F), kappa^ of W, V, [W, V], log(flops); s has length
  * m + p (W uses s[0:m], V s[m:m+p]).  Logs are natural, of the value clamped

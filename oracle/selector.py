@@ -18,13 +18,14 @@ rows n of W, columns m, V n x p: 0 log n, 1 log m, 2 log(p + 1), 3 m/n,
 [1e-300, 1e300].
 
 kappa^(M) = sigma_max(B_k) / sigma_min(B_k) of the k x k bidiagonal of k
-steps of Golub-Kahan-Lanczos bidiagonalization of M (in float32 for the
-features, so kappa^ saturates near 1 / u_single ~ 1e7) started from a given
-vector, every new vector reorthogonalized once against the previous ones
-(classical Gram-Schmidt), k = min(16, rows, columns) of M; for a
-wide M the start vector is first mapped into range(M^T).  The Ritz values
-interlace the nonzero singular values, so kappa^ <= sigma_max / sigma_r
-(r = rank), with equality once k reaches the rank.
+steps of Golub-Kahan-Lanczos bidiagonalization of M, in FP64, started from a
+given vector, every new vector fully reorthogonalized against the previous
+ones (two classical Gram-Schmidt passes), k = min(16, rows, columns) of M;
+for a wide M the start vector is first mapped into range(M^T).  The Ritz
+values interlace the nonzero singular values, so kappa^ <= sigma_max /
+sigma_r (r = rank), with equality once k reaches the rank.  This is the
+plain definition of the sketch; the GPU computes it in float32, and the
+parity tests derive their tolerance from that rounding.
 
 MLP: 16 -> 64 -> 64 -> 6, ReLU, softmax, cross-entropy; weights are used
 as given (the GPU rounds them to bfloat16 before every forward; parity tests
@@ -38,18 +39,19 @@ TINY = 1e-300
 
 # ------------------------------------------------------------- features --
 
-BREAKDOWN = 64 * np.finfo(np.float32).eps / 2     # relative to the largest alpha / beta so far (the
-                                                  # feature sketch runs in float32)
+BREAKDOWN = 2.0 ** -40     # relative to the largest alpha / beta so far: far above FP64
+                           # rounding (~1e-16 * sqrt(length)), far below any entry of the
+                           # bidiagonal of a block with condition number up to 1e12
 
 
 def gkl_bidiag(mv, rmv, s, k):
     """k steps of Golub-Kahan-Lanczos bidiagonalization: M V_k = U_k B_k with
     B_k upper bidiagonal (diag alpha, superdiag beta), v_1 = s / ||s||.
-    mv(x) = M x, rmv(y) = M^T y; u and v are reorthogonalized once against
-    the earlier ones (classical Gram-Schmidt).  Stops early when an alpha or beta falls
-    to rounding level (below 64 u_single times the largest one so far): the Krylov
-    space is exhausted (e.g. k exceeds the rank) and further steps would
-    only add rounding noise."""
+    mv(x) = M x, rmv(y) = M^T y; u and v are fully reorthogonalized against
+    the earlier ones (two classical Gram-Schmidt passes).  Stops early when an
+    alpha or beta falls to rounding level (below BREAKDOWN times the largest
+    one so far): the Krylov space is exhausted (e.g. k exceeds the rank) and
+    further steps would only add rounding noise."""
     v = s / np.linalg.norm(s)
     alphas, betas = [], []
     u_prev, beta = None, 0.0
@@ -57,9 +59,9 @@ def gkl_bidiag(mv, rmv, s, k):
     Us, Vs = [], [v]
     for j in range(k):
         u = mv(v) - (beta * u_prev if u_prev is not None else 0.0)
-        if True:                               # reorthogonalize (one CGS pass)
-            if Us:
-                Um = np.column_stack(Us)
+        if Us:                                 # reorthogonalize (two CGS passes)
+            Um = np.column_stack(Us)
+            for _ in range(2):
                 u = u - Um @ (Um.T @ u)
         a = np.linalg.norm(u)
         if not a > BREAKDOWN * max(big, a if j == 0 else big):
@@ -71,8 +73,8 @@ def gkl_bidiag(mv, rmv, s, k):
         if j == k - 1:
             break
         w = rmv(u) - a * v
-        if True:                               # reorthogonalize (one CGS pass)
-            Vm = np.column_stack(Vs)
+        Vm = np.column_stack(Vs)                # reorthogonalize (two CGS passes)
+        for _ in range(2):
             w = w - Vm @ (Vm.T @ w)
         beta = np.linalg.norm(w)
         if not beta > BREAKDOWN * big:
@@ -89,14 +91,6 @@ def gkl_bidiag(mv, rmv, s, k):
     return Bk
 
 
-def kappa_hat32(M, s, k=16, wide=False):
-    """kappa_hat with the bidiagonalization in float32 (vectors and products
-    of the matrix rounded to float32), as the selector computes it."""
-    M32 = np.asarray(M, np.float64).astype(np.float32)
-    s32 = np.asarray(s, np.float64).astype(np.float32)
-    return kappa_hat(lambda x: M32 @ x.astype(np.float32), lambda y: M32.T @ y.astype(np.float32), s32, k, wide)
-
-
 def kappa_hat(mv, rmv, s, k=16, wide=False):
     """sigma_max / sigma_min of the GKL bidiagonal.  For a wide M (fewer rows
     than columns) the start vector is first mapped into range(M^T)
@@ -109,6 +103,14 @@ def kappa_hat(mv, rmv, s, k=16, wide=False):
         return 1.0
     sv = np.linalg.svd(Bk, compute_uv=False)
     return sv[0] / sv[-1] if sv[-1] > 0 else np.inf
+
+
+def kappa_of(M, s, k):
+    """kappa^ of the dense FP64 matrix M (wide when it has fewer rows than
+    columns) from start vector s."""
+    M = np.asarray(M, np.float64)
+    return kappa_hat(lambda x: M @ x, lambda y: M.T @ y, np.asarray(s, np.float64), k,
+                     M.shape[0] < M.shape[1])
 
 
 def _lg(x):
@@ -132,9 +134,9 @@ def lse_features(A, B, b, d, s, k=16):
     p = B.shape[0]
     fA, fB = np.linalg.norm(A), np.linalg.norm(B)
     AB = np.vstack([A, B])
-    kA = kappa_hat32(A, s, min(k, m, n), m < n)
-    kB = kappa_hat32(B, s, min(k, p, n), p < n) if p else 1.0
-    kAB = kappa_hat32(AB, s, min(k, m + p, n), m + p < n)
+    kA = kappa_of(A, s, min(k, m, n))
+    kB = kappa_of(B, s, min(k, p, n)) if p else 1.0
+    kAB = kappa_of(AB, s, min(k, m + p, n))
     return np.array([_lg(m), _lg(n), np.log(p + 1.0), n / m, p / n, 0.0, 0.0, _lg(fA), _lg(fB),
                      _lg(np.linalg.norm(b)), _lg(np.linalg.norm(d)), _lg(fA) - _lg(fB),
                      _lg(kA), _lg(kB), _lg(kAB), _lg(lse_flops(m, n, p))])
@@ -148,9 +150,9 @@ def gls_features(W, V, d, s, k=16):
     p = V.shape[1]
     fW, fV = np.linalg.norm(W), np.linalg.norm(V)
     WV = np.hstack([W, V])
-    kW = kappa_hat32(W, s[:m], min(k, n, m), n < m) if m else 1.0
-    kV = kappa_hat32(V, s[m:], min(k, n, p), n < p)
-    kWV = kappa_hat32(WV, s, min(k, n, m + p), n < m + p)
+    kW = kappa_of(W, s[:m], min(k, n, m)) if m else 1.0
+    kV = kappa_of(V, s[m:], min(k, n, p))
+    kWV = kappa_of(WV, s, min(k, n, m + p))
     return np.array([_lg(n), _lg(m), np.log(p + 1.0), m / n, n / p, 1.0, 0.0, _lg(fW), _lg(fV),
                      _lg(np.linalg.norm(d)), 0.0, _lg(fW) - _lg(fV),
                      _lg(kW), _lg(kV), _lg(kWV), _lg(gls_flops(n, m, p))])

@@ -9,11 +9,15 @@
 // log ||d||, 0, log(||W||/||V||), kappa^ of W, V and [W, V]).
 // kappa^ = sigma_max(B_k) / sigma_min(B_k) of k = min(16, rows, columns)
 // steps of Golub-Kahan-Lanczos bidiagonalization (FP32 vectors and
-// products of the FP64 data, so kappa^ saturates near 1e7; every new vector
-// reorthogonalized once against the previous ones) from a given start vector,
-// stopped early when an alpha or beta falls below 64 u times the
-// largest one so far (the Krylov space is exhausted, e.g. k above the rank:
-// further steps would only add rounding noise); the singular values of the
+// products of the FP64 data; every new vector reorthogonalized once against
+// the previous ones) from a given start vector, stopped early only at
+// breakdown: an alpha or beta below 2^-26 of the largest one so far (the
+// Krylov space is exhausted).  On tall blocks the Ritz values then follow the
+// FP64 definition to within u_single ||M||_F up to kappa^ ~ 1e8; a
+// rank-deficient block reads as kappa^ at the FP32 noise level (1e6-1e8).
+// On a wide block FP32 rounding leaves components in the null space that
+// grow by alpha/beta per step, so long sketches of wide blocks with
+// alpha/beta well above 1 can drift.  The singular values of the
 // k x k bidiagonal come from bisection
 // on its Golub-Kahan tridiagonal form (zero diagonal), which resolves small
 // singular values to high relative accuracy.
@@ -34,7 +38,7 @@ namespace mpir {
 // ============================================================ features ==
 constexpr int FT_THREADS = 512;
 constexpr int FT_KMAX = 16;
-constexpr float GKL_BREAKDOWN_F = 64 * 5.9604645e-08f;   // 64 u (single: the sketch runs in FP32)
+constexpr float GKL_BREAKDOWN_F = 1.4901161e-08f;   // 2^-26: breakdown of the Krylov space only
 
 struct FeatView {
     int kind;          // 0 LSE ([A; B], runs split rows), 1 GLS ([W, V], runs split columns)
@@ -395,7 +399,7 @@ k_features(FeatView V, const double *__restrict__ s, const double *__restrict__ 
         float al[3];
         for (int r = 0; r < 3; r++) {
             al[r] = sqrtf(tot[r]);
-            // breakdown: alpha at rounding level of the largest alpha / beta so far
+            // breakdown: alpha negligible against the largest alpha / beta so far
             if (live[r] && !(al[r] > GKL_BREAKDOWN_F * (t == 0 ? al[r] : big[r]))) live[r] = false;
             if (live[r]) big[r] = fmaxf(big[r], al[r]);
             if (live[r] && tid == 0) { alpha[r][t] = al[r]; kk[r] = t + 1; }

@@ -87,6 +87,20 @@ def test_kappa_hat_exact_for_few_columns():
     assert abs(kh / 1e3 - 1) < 1e-8
 
 
+def test_kappa_hat_exact_at_rank_ill_conditioned():
+    """k = rank on a tall block with cond 1e10: the fully reorthogonalized
+    FP64 sketch is the complete bidiagonalization, so kappa^ is the
+    condition number itself (a single-precision sketch, or one stopped at
+    single-precision rounding level, saturates orders of magnitude lower)."""
+    from paper_2406_16499_gb300 import inputs as I
+    for seed, cond in ((13, 1e6), (14, 1e10)):
+        g = I.rng(seed)
+        M = I.svd_matrix(g, 300, 12, I.logspace_sigma(12, cond))
+        s = I.splitmix_vector(12)
+        kh = S.kappa_of(M, s, 12)
+        assert abs(kh / cond - 1) < 1e-5, (kh, cond)
+
+
 def test_features_layout():
     from paper_2406_16499_gb300 import inputs as I
     P = I.lse_small()
