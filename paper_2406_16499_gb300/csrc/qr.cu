@@ -1267,9 +1267,162 @@ static int launch_larfb(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+// Row-chunked inner update for panels too tall for one cluster's shared
+// memory (FP32): the rows are split into IT_ROWS-row chunks and the columns
+// into 32-column groups, one CTA per (chunk, group) in each of three
+// kernels chained by programmatic dependent launch:
+//   k_itall_part   P[g][q] = V_q^T C_{q,g}                     (32 x 32)
+//   k_itall_red    W_g = Tw^T sum_q P[g][q]   (fixed summation order)
+//   k_itall_apply  C_{q,g} -= V_q W_g
+// V is the unit lower trapezoid stored in the panel's columns (kb <= 32).
+constexpr int IT_ROWS = 256;
+
+__device__ __forceinline__ float itall_v(const float *__restrict__ V, int ldv, int kb, int gr, int c)
+{
+    return c < kb ? (gr > c ? V[idx2(gr, c, ldv)] : (gr == c ? 1.f : 0.f)) : 0.f;
+}
+
+__global__ void __launch_bounds__(256)
+k_itall_part(const float *__restrict__ V, int ldv, int kb, int L, const float *__restrict__ C, int ldc, int nc,
+             float *__restrict__ P, int nch)
+{
+    extern __shared__ __align__(16) float sm[];
+    float *Vc = sm;                                    // IT_ROWS x IV_LD, row-major
+    float *Cc = Vc + IT_ROWS * IV_LD;                  // IC x (IT_ROWS + 1), column-major
+    constexpr int RP = IT_ROWS + 1;
+    __shared__ __align__(16) float pg[4][IC * 32];
+    const int tid = threadIdx.x;
+    const int q = blockIdx.x, g = blockIdx.y;
+    const int cg0 = g * IC, ncl = min(IC, nc - cg0);
+    const int r0 = q * IT_ROWS, R = min(IT_ROWS, L - r0);
+    pdl_wait();
+    pdl_trigger();
+    for (int r = tid; r < IT_ROWS; r += 256) {
+        const int gr = r0 + r;
+        const bool in = r < R;
+#pragma unroll
+        for (int c = 0; c < 32; c++) Vc[r * IV_LD + c] = in ? itall_v(V, ldv, kb, gr, c) : 0.f;
+#pragma unroll
+        for (int c = 0; c < IC; c++) Cc[r + c * RP] = (in && c < ncl) ? C[idx2(gr, cg0 + c, ldc)] : 0.f;
+    }
+    __syncthreads();
+    const int rg = tid >> 6, ti = tid & 7, tc = (tid >> 3) & 7;
+    const int i0 = 4 * ti, c0 = 4 * tc;
+    const int ra = rg * (IT_ROWS / 4), rb = ra + IT_ROWS / 4;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; a++)
+#pragma unroll
+        for (int b = 0; b < 4; b++) acc[a][b] = 0.f;
+    const float *cp = Cc + c0 * RP;
+#pragma unroll 4
+    for (int r = ra; r < rb; r++) {
+        const float4 v = *reinterpret_cast<const float4 *>(Vc + r * IV_LD + i0);
+        float cv[4];
+#pragma unroll
+        for (int b = 0; b < 4; b++) cv[b] = cp[b * RP + r];
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            acc[0][b] = fmaf(v.x, cv[b], acc[0][b]);
+            acc[1][b] = fmaf(v.y, cv[b], acc[1][b]);
+            acc[2][b] = fmaf(v.z, cv[b], acc[2][b]);
+            acc[3][b] = fmaf(v.w, cv[b], acc[3][b]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+        *reinterpret_cast<float4 *>(&pg[rg][(c0 + b) * 32 + i0]) =
+            make_float4(acc[0][b], acc[1][b], acc[2][b], acc[3][b]);
+    __syncthreads();
+    float *Pq = P + ((size_t)g * nch + q) * (IC * 32);
+    for (int e = tid; e < IC * 32; e += 256) Pq[e] = (pg[0][e] + pg[1][e]) + (pg[2][e] + pg[3][e]);
+}
+
+__global__ void __launch_bounds__(1024)
+k_itall_red(const float *__restrict__ P, int nch, const float *__restrict__ Tw, float *__restrict__ W)
+{
+    __shared__ float S[IC * 32];                       // S(k, c) at k + 32 c
+    __shared__ float X[32][33];                        // X[a][k] = Tw(k, a)
+    const int e = threadIdx.x, g = blockIdx.x;
+    pdl_wait();
+    pdl_trigger();
+    X[e >> 5][e & 31] = Tw[(e & 31) + (e >> 5) * 32];
+    const float *Pg = P + (size_t)g * nch * (IC * 32) + e;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    int q = 0;
+    for (; q + 4 <= nch; q += 4) {
+        a0 += Pg[(size_t)q * (IC * 32)];
+        a1 += Pg[(size_t)(q + 1) * (IC * 32)];
+        a2 += Pg[(size_t)(q + 2) * (IC * 32)];
+        a3 += Pg[(size_t)(q + 3) * (IC * 32)];
+    }
+    for (; q < nch; q++) a0 += Pg[(size_t)q * (IC * 32)];
+    S[e] = (a0 + a1) + (a2 + a3);
+    __syncthreads();
+    const int a = e & 31, c = e >> 5;                  // W(a, c) = sum_k Tw(k, a) S(k, c)
+    float t = 0.f;
+#pragma unroll 8
+    for (int k = 0; k < 32; k++) t = fmaf(X[a][k], S[k + 32 * c], t);
+    W[(size_t)g * (IC * 32) + a + 32 * c] = t;
+}
+
+__global__ void __launch_bounds__(256)
+k_itall_apply(const float *__restrict__ V, int ldv, int kb, int L, float *__restrict__ C, int ldc, int nc,
+              const float *__restrict__ W)
+{
+    __shared__ __align__(16) float Wc[IC * IV_LD];     // Wc[c][k] = W(k, c)
+    const int tid = threadIdx.x;
+    const int q = blockIdx.x, g = blockIdx.y;
+    const int cg0 = g * IC, ncl = min(IC, nc - cg0);
+    const int gr = q * IT_ROWS + tid;
+    pdl_wait();
+    pdl_trigger();
+    for (int e = tid; e < IC * 32; e += 256) Wc[(e >> 5) * IV_LD + (e & 31)] = W[(size_t)g * (IC * 32) + e];
+    float vr[32];
+#pragma unroll
+    for (int k = 0; k < 32; k++) vr[k] = gr < L ? itall_v(V, ldv, kb, gr, k) : 0.f;
+    __syncthreads();
+    if (gr >= L) return;
+    float *Cr = C + gr + (size_t)cg0 * ldc;
+#pragma unroll 2
+    for (int c = 0; c < ncl; c++) {
+        float t0 = 0.f, t1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; k += 8) {
+            const float4 w0 = *reinterpret_cast<const float4 *>(&Wc[c * IV_LD + k]);
+            const float4 w1 = *reinterpret_cast<const float4 *>(&Wc[c * IV_LD + k + 4]);
+            t0 = fmaf(vr[k], w0.x, t0);
+            t0 = fmaf(vr[k + 1], w0.y, t0);
+            t0 = fmaf(vr[k + 2], w0.z, t0);
+            t0 = fmaf(vr[k + 3], w0.w, t0);
+            t1 = fmaf(vr[k + 4], w1.x, t1);
+            t1 = fmaf(vr[k + 5], w1.y, t1);
+            t1 = fmaf(vr[k + 6], w1.z, t1);
+            t1 = fmaf(vr[k + 7], w1.w, t1);
+        }
+        Cr[(size_t)c * ldc] -= t0 + t1;
+    }
+}
+
+static int inner_update_tall(const float *V, int ldv, const float *Tw, int kb, int L, float *C, int ldc, int nc,
+                             float *P, float *W, cudaStream_t s)
+{
+    const int nch = ceil_div(L, IT_ROWS), ngrp = ceil_div(nc, IC);
+    const size_t smem = ((size_t)IT_ROWS * IV_LD + (size_t)(IT_ROWS + 1) * IC) * sizeof(float);
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(k_itall_part, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
+    ProfScope ps(K_LARFB, s);
+    cudaError_t e = pdl_launch(k_itall_part, dim3(nch, ngrp), dim3(256), smem, s, V, ldv, kb, L, (const float *)C,
+                               ldc, nc, P, nch);
+    if (e == cudaSuccess) e = pdl_launch(k_itall_red, dim3(ngrp), dim3(1024), 0, s, (const float *)P, nch, Tw, W);
+    if (e == cudaSuccess)
+        e = pdl_launch(k_itall_apply, dim3(nch, ngrp), dim3(256), 0, s, V, ldv, kb, L, C, ldc, nc, (const float *)W);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
 // Inner update of nc (<= 96) columns on one cluster (fused kernel).
 static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int L, float *C, int ldc, int nc,
-                           cudaStream_t s)
+                           float *P, float *W, cudaStream_t s)
 {
     {   // whole chunk in shared memory when it fits (16-CTA cluster)
         auto kern = k_inner_cl_s<32>;
@@ -1304,6 +1457,7 @@ static int inner_update_cl(const float *V, int ldv, const float *Tw, int kb, int
             return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
         }
     }
+    if (P && W) return inner_update_tall(V, ldv, Tw, kb, L, C, ldc, nc, P, W, s);
     auto kern = k_inner_cl<32>;
     static PerDeviceOnce once;
     once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); });
@@ -1336,7 +1490,8 @@ static int inner_update(const T *V, int ldv, const T *Tw, int kb, int L, T *C, i
     if (nc <= 0 || L <= 0 || kb <= 0) return 0;
     if (nc > INNER_MAXC) return launch_larfb<T>(V, ldv, Tw, kb, L, C, ldc, nc, 1, s);
     if (sizeof(T) == 4)
-        return inner_update_cl((const float *)V, ldv, (const float *)Tw, kb, L, (float *)C, ldc, nc, s);
+        return inner_update_cl((const float *)V, ldv, (const float *)Tw, kb, L, (float *)C, ldc, nc, (float *)P,
+                               (float *)W, s);
     const int nch = ceil_div(L, INNER_ROWS);
     ProfScope ps(K_LARFB, s);
     k_inner_w<T, NB><<<nch, 256, 0, s>>>(V, ldv, kb, L, C, ldc, nc, P);

@@ -210,6 +210,43 @@ def test_grq_gqr_many_blocks(h):
     assert np.abs(_explicit_t(h, "Z", p) - Z.T).max() <= 1e-5
 
 
+def test_grq_invariants_tall(h):
+    """Panels taller than one cluster's shared memory (m = 12288 rows, the
+    row-chunked inner updates): Lemma 4.5 through products with random
+    vectors, B x ~ [0 R] Q x and A x ~ Z T Q x with backward errors
+    O(u_f) ||.||_F ||x||, and Q^T Q x = x, Z^T Z y = y."""
+    import torch
+    tol = 3e-6
+    m, n, p = 12288, 384, 64
+    T = I.lse_svd_torch(31, m, n, p, 1e2, 1e1, "cuda")
+    A, B = T["A"], T["B"]
+    h.lse_factor(A, B, "fp32")
+    R = torch.zeros((p, p), dtype=torch.float64, device="cuda").t().contiguous().t()
+    Tm = torch.zeros((n, m), dtype=torch.float64, device="cuda").t()
+    h.get_RT(R, Tm)
+    assert torch.allclose(Tm, torch.triu(Tm)) and torch.allclose(R, torch.triu(R))
+    nA, nB = float(torch.linalg.norm(A)), float(torch.linalg.norm(B))
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    for _ in range(4):
+        x = torch.randn(n, dtype=torch.float64, device="cuda", generator=g)
+        nx = float(torch.linalg.norm(x))
+        qx = x.clone()
+        h.apply_factor("Q", False, qx)
+        assert float(torch.linalg.norm(B @ x - R @ qx[n - p:])) <= tol * 30 * nB * nx
+        ztqx = Tm @ qx
+        h.apply_factor("Z", False, ztqx)
+        assert float(torch.linalg.norm(A @ x - ztqx)) <= tol * 30 * nA * nx
+        back = qx.clone()
+        h.apply_factor("Q", True, back)
+        assert float(torch.linalg.norm(back - x)) <= tol * 30 * np.sqrt(n) * nx
+        y = torch.randn(m, dtype=torch.float64, device="cuda", generator=g)
+        zy = y.clone()
+        h.apply_factor("Z", False, zy)
+        h.apply_factor("Z", True, zy)
+        assert float(torch.linalg.norm(zy - y)) <= tol * 30 * np.sqrt(m) * float(torch.linalg.norm(y))
+
+
 # ------------------------------------------------- initial solutions --
 
 @pytest.mark.parametrize("fact", ["fp32", "fp64"])
