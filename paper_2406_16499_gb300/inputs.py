@@ -185,6 +185,60 @@ def lse_svd_torch(seed, m, n, p, cond_a, cond_b, device, noise=1.0):
     return dict(A=A, B=B, b=b, d=B @ x, x_true=x)
 
 
+def lse_known_torch(seed, m, n, p, cond_a, cond_b, device, resid=1e-3):
+    """LSE with a known solution (the known-solution construction of the
+    KKT system eq. aug-LSE), drawn with torch's generator on `device`:
+    A = U_A diag(sigma) V_A^T (m >= n, logspace spectrum, cond_a),
+    B = U_B diag(sigma_B) V_B^T (cond_b), x* ~ N(0,1), and
+      r* = U_A Sigma^-1 V_A^T B^T v* + (I - U_A U_A^T) w,
+    so that A^T r* = B^T v*; b = A x* + r*, d = B x*.  Then (x*, r*, v*) is
+    the solution.  v* and w are scaled so that each part of r* has norm
+    resid/2 * sigma_min(A) ||x*||: the rounding of the stored A perturbs the
+    multiplier equation by ~u ||A|| ||r*||, which moves x by far less than
+    kappa u.  Also returns kappa_up, an upper bound of the forward-error
+    condition number kappa_N (1 + kappa_N ||r|| / (sigma_max(T11) ||x||)):
+    kappa_N = kappa_2(A restricted to null(B)) <= cond_a (the singular
+    values of A N with orthonormal N lie in [sigma_min(A), sigma_max(A)]),
+    so kappa_up = cond_a (1 + cond_a ||r*|| / (sigma_max(A) ||x*||)).
+    FP64 column-major tensors."""
+    import torch
+    assert m >= n
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & ((1 << 63) - 1))
+    f64 = dict(generator=g, device=device, dtype=torch.float64)
+
+    def haar(rows, cols):
+        X = torch.randn(rows, cols, **f64)
+        Q, R = torch.linalg.qr(X)
+        sg = torch.sign(torch.diagonal(R))
+        sg[sg == 0] = 1.0
+        return Q * sg
+
+    sa = torch.from_numpy(logspace_sigma(n, cond_a)).to(device)
+    sb = torch.from_numpy(logspace_sigma(p, cond_b)).to(device)
+    UA, VA = haar(m, n), haar(n, n)
+    UB, VB = haar(p, p), haar(n, p)
+    A = ((UA * sa) @ VA.T).t().contiguous().t()
+    B = ((UB * sb) @ VB.T).t().contiguous().t()
+    x = torch.randn(n, **f64)
+    nx = torch.linalg.norm(x)
+    tau = 0.5 * resid * float(sa[-1]) * float(nx)
+    gv = torch.randn(p, **f64)
+    r1 = UA @ ((VA.T @ (B.T @ gv)) / sa)
+    s1 = tau / float(torch.linalg.norm(r1))
+    v = gv * s1
+    r1 = r1 * s1
+    w = torch.randn(m, **f64)
+    r2 = w - UA @ (UA.T @ w)
+    r2 = r2 * (tau / float(torch.linalg.norm(r2)))
+    r = r1 + r2
+    b = A @ x + r
+    d = B @ x
+    kup = cond_a * (1.0 + cond_a * float(torch.linalg.norm(r)) / (float(sa[0]) * float(nx)))
+    del UA, VA, UB, VB
+    return dict(A=A, B=B, b=b, d=d, x_true=x, r_true=r, v_true=v, kappa_up=kup)
+
+
 def lse_batch_torch(specs, device, cond_b=10.0):
     """The problems of lse_batch_specs drawn with torch's generator on
     `device` (same construction as lse_svd: Haar factors from the QR of

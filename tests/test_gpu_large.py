@@ -1,9 +1,15 @@
 """The large LSE workload (m = 16384, n = 8192, p = 1024; cond(A) in 1e1,
-1e4, 1e8, cond(B) = 1e2) at full size.  The oracle's factorization is too
-slow at this size, so the checks are the size-independent properties the
-FP64-level bar is defined by, evaluated by the oracle's double-double
-residual: eq. lse-stop ratios (eta) and the constraint residual
-||Bx-d|| / (||B|| ||x|| + ||d||), both <= 1e-14."""
+1e4, 1e8, cond(B) = 1e2) at full size, in the launch configuration the
+benchmark times.  The oracle's factorization is too slow at this size, so
+the right-hand sides come from the known-solution construction
+(inputs.lse_known_torch): (x*, r*, v*) solve the KKT system exactly, and
+kappa_up bounds the forward-error condition number.  The bar:
+  * eq. lse-stop ratios (eta) and ||Bx-d|| / (||B|| ||x|| + ||d||) <= 1e-14,
+    from the oracle's double-double residual;
+  * forward error ||x - x*|| / ||x*|| <= 10 kappa_up 1.1e-16.
+cond(A) = 1e8 is beyond what FP32 factors can refine (u_f kappa > 1, and
+u_f kappa(A) kappa(B) > 1 for the block-diagonal preconditioner): the solve
+escalates to an FP64 factorization, which meets the bar."""
 import numpy as np
 import pytest
 
@@ -12,6 +18,9 @@ from paper_2406_16499_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 M, N, P = 16384, 8192, 1024
+SEED = 20243623
+
+_cache = {}
 
 
 @pytest.fixture(scope="module")
@@ -23,22 +32,38 @@ def h():
     hd = mpir.Handle()
     yield hd
     hd.close()
+    _cache.clear()
 
 
-@pytest.mark.parametrize("cond,fact,refine", [(1e1, "fp32", "classical"), (1e4, "tf32", "classical"),
-                                              (1e8, "fp32", "gmres")])
+def problem(cond):
+    if cond not in _cache:
+        _cache.clear()
+        T = I.lse_known_torch(SEED + int(np.log10(cond)), M, N, P, cond, 1e2, "cuda")
+        host = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in T.items()}
+        _cache[cond] = (T, host)
+    return _cache[cond]
+
+
+@pytest.mark.parametrize("cond,fact,refine", [(1e1, "fp32", "classical"), (1e1, "tf32", "classical"),
+                                              (1e4, "fp32", "classical"), (1e4, "fp32", "gmres"),
+                                              (1e8, "fp32", "classical")])
 def test_lse_large_full_size(h, oracle_mod, cond, fact, refine):
     import torch
     from paper_2406_16499_gb300 import mpir
-    T = I.lse_svd_torch(20243623 + int(np.log10(cond)), M, N, P, cond, 1e2, "cuda")
+    T, Hs = problem(cond)
     x = torch.zeros(N, dtype=torch.float64, device="cuda")
     r = torch.zeros(M, dtype=torch.float64, device="cuda")
     v = torch.zeros(P, dtype=torch.float64, device="cuda")
     st, info = h.lse_solve(T["A"], T["B"], T["b"], T["d"], x, r, v, mpir.make_opts(fact=fact, refine=refine))
     assert st == 0, (st, info.as_dict())
-    A = T["A"].cpu().numpy()
-    B = T["B"].cpu().numpy()
-    met = oracle_mod.lse_metrics(A, B, T["b"].cpu().numpy(), T["d"].cpu().numpy(), x.cpu().numpy(),
-                                 r.cpu().numpy(), v.cpu().numpy())
-    print(cond, fact, refine, info.as_dict()["iters"], info.as_dict()["escalated"], met["eta"], met["e_con"])
+    xh = x.cpu().numpy()
+    met = oracle_mod.lse_metrics(Hs["A"], Hs["B"], Hs["b"], Hs["d"], xh, r.cpu().numpy(), v.cpu().numpy())
+    fe = float(np.linalg.norm(xh - Hs["x_true"]) / np.linalg.norm(Hs["x_true"]))
+    bound = 10 * Hs["kappa_up"] * 1.1e-16
+    d = info.as_dict()
+    print("cond %.0e %s/%s iters %d escalated %d fact_used %d eta %.2e e_con %.2e fwd %.2e bound %.2e"
+          % (cond, fact, refine, d["iters"], d["escalated"], d["fact_used"], met["eta"], met["e_con"], fe, bound))
     assert met["eta"] <= 1e-14 and met["e_con"] <= 1e-14, met
+    assert fe <= bound, (fe, bound)
+    if cond <= 1e4 and refine == "classical" and fact == "fp32":
+        assert d["escalated"] == 0

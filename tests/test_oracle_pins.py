@@ -482,3 +482,23 @@ def test_input_generators_spectra():
     a = I.lse_small(9)["A"]
     b = I.lse_small(9)["A"]
     assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("cond", [1e2, 1e6])
+def test_known_solution_construction(oracle_mod, cond):
+    """The known-solution LSE construction used at full size: the oracle's
+    FP64 solution equals (x*, r*) to within the forward-error bound, and
+    kappa_up bounds the oracle's condition number (reading C13) from above."""
+    torch = pytest.importorskip("torch")
+    T = I.lse_known_torch(5, 90, 40, 7, cond, 1e1, "cpu")
+    A, B, b, d = (T[k].numpy() for k in ("A", "B", "b", "d"))
+    xs, rs = T["x_true"].numpy(), T["r_true"].numpy()
+    t = oracle_mod.lse_truth(A, B, b, d)
+    F = oracle_mod.lse_factor(A, B, "fp64")
+    kap = oracle_mod.lse_kappa(F, t["x"], t["r"])[0]
+    assert kap <= T["kappa_up"] * (1 + 1e-6), (kap, T["kappa_up"])
+    fe = np.linalg.norm(t["x"] - xs) / np.linalg.norm(xs)
+    assert fe <= 10 * T["kappa_up"] * 1.1e-16, (fe, T["kappa_up"])
+    assert np.linalg.norm(t["r"] - rs) <= 1e-6 * np.linalg.norm(rs)
+    # the multiplier equation of the construction
+    assert np.linalg.norm(A.T @ rs - B.T @ T["v_true"].numpy()) <= 1e-12 * np.linalg.norm(A) * np.linalg.norm(rs)
