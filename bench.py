@@ -1,13 +1,17 @@
 #!/usr/bin/env python3
-"""Benchmark: solves/s of the mixed-precision GLS solve (FP32 GQR + FP64
-classical iterative refinement, Alg. 4) on one GB300, next to the plain FP64
-GQR solve on the same GPU and the CPU oracle on the host cores.
+"""Benchmark: solves/s of the mixed-precision LSE solve (FP32 GRQ + FP64
+classical iterative refinement, Alg. 2) on one GB300, next to the plain
+FP64 GRQ solve on the same GPU and the CPU oracle on the host cores.
 
 Workload (one "step" = one complete solve, factorization included):
-  GLS in the xGGGLM convention, n = 4096, m = 1024, p = 4096:
-  W 4096 x 1024 with cond 1e3 (seeded SVD construction, logspace spectrum),
-  V the 4096 x 4096 lower-triangular Cholesky factor of an AR(1) covariance
-  (rho = 0.9), d = W x + V y with x, y ~ N(0, 1).
+  LSE min ||A x - b|| s.t. B x = d, m = 16384, n = 8192, p = 1024:
+  A = U diag(logspace) V^T with cond(A) = 1e4, B likewise with cond(B) =
+  1e2 (seeded Haar factors drawn on the GPU), right-hand sides from the
+  known-solution construction (x* ~ N(0,1); r* with A^T r* = B^T v*;
+  b = A x* + r*, d = B x*), so every result's forward error is measured.
+The same line reports the sweep cond(A) in {1e1, 1e4, 1e8} (FP32 and TF32
+factors, classical IR and GMRES-IR, FP64 direct), the GLS n = 4096 AR(1)
+workload, and 10,000 uneven batched LSE problems.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -28,11 +32,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "solves/s at FP64-level accuracy: mixed-precision IR vs FP64 GRQ/GQR, same GB300"
-WORKLOAD = ("GLS n=4096 m=1024 p=4096 (xGGGLM shapes): W cond 1e3 SVD construction, "
-            "V = Cholesky factor of AR(1) covariance rho=0.9, d = W x + V y")
-N_, M_, P_ = 4096, 1024, 4096
-SEED = 20242623
+M_, N_, P_ = 16384, 8192, 1024
+COND_A, COND_B = 1e4, 1e2
+CONDS = (1e1, 1e4, 1e8)
+SEED = 20243623
+WORKLOAD = ("LSE m=16384 n=8192 p=1024: A = U diag(logspace) V^T with cond(A)=1e4, B likewise with cond(B)=1e2 "
+            "(seeded Haar factors), known-solution right-hand sides (b = A x* + r*, d = B x*, A^T r* = B^T v*)")
+GLS_WORKLOAD = ("GLS n=4096 m=1024 p=4096 (xGGGLM shapes): W cond 1e3 SVD construction, "
+                "V = Cholesky factor of AR(1) covariance rho=0.9, d = W x + V y")
+GLS_N, GLS_M, GLS_SEED = 4096, 1024, 20242623
+U64 = 1.1e-16
 L2_FLUSH_BYTES = 256 << 20
+
+
+def config(fact="fp32"):
+    """The workload description both arms print (identical dicts)."""
+    return {"workload": WORKLOAD, "fact": fact, "refine": "classical", "cond_a": COND_A,
+            "l2": "inputs 1.14 GB FP64 > 129 MB L2 (no flush needed)"}
 
 
 def parse():
@@ -44,7 +60,9 @@ def parse():
     ap.add_argument("--fact", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--quick", action="store_true",
-                    help="time the mixed-precision solve only (for profiler runs)")
+                    help="time the headline solve only (for profiler runs)")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the cond(A) sweep")
+    ap.add_argument("--no-gls", action="store_true", help="skip the GLS n=4096 workload")
     ap.add_argument("--batched-count", type=int, default=10000,
                     help="problems of the uneven batched LSE workload (0: skip it)")
     ap.add_argument("--batched-only", action="store_true",
@@ -67,6 +85,14 @@ def rank_max(x, world, device=None):
     t = torch.tensor([float(x)], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def nproc():
+    """Host cores available to this process (what `nproc` prints)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
 
 
 def job_value(world, ms_per_step):
@@ -171,6 +197,45 @@ def apply_work(M, K, Nc, nb=32):
     return lf
 
 
+def qr_split(M, N, nb=32, outer=128):
+    """(panel, inner, outer) flops of the two-level blocked QR as the
+    library runs it: 32-wide panels, SIMT updates of the rest of each
+    128-wide outer block (inner), tensor-core updates of the trailing
+    matrix per outer block (outer)."""
+    k = min(M, N)
+    pf = inner = outer_f = 0.0
+    for J0 in range(0, k, outer):
+        no = min(outer, k - J0)
+        for j0 in range(J0, J0 + no, nb):
+            nc = min(nb, J0 + no - j0)
+            L = M - j0
+            kb = min(nc, L)
+            pf += 4.0 * L * kb * nc - 2.0 * kb * kb * nc
+            rest = J0 + no - j0 - nc
+            if rest > 0:
+                inner += 4.0 * L * kb * rest + 2.0 * kb * kb * rest
+        Nc = N - J0 - no
+        L = M - J0
+        kb = min(no, L)
+        if Nc > 0:
+            outer_f += 4.0 * L * kb * Nc + 2.0 * kb * kb * Nc
+    return pf, inner, outer_f
+
+
+def lse_work(m, n, p):
+    """Algorithmic work of one LSE solve as the library runs it: the QR of
+    B~ (n x p) with Q~^T applied to the n x m X = P A^T (the RQ of B and
+    A Q^T, Lemma 4.5), the QR of A Q^T (m x n); FP64 residual bytes and
+    flops of one refinement step (one read of A and B, 4 (mn + pn) flops,
+    t_r of Sec. 3.1)."""
+    p1, i1, o1 = qr_split(n, p)
+    o2 = 4.0 * n * p * m - 2.0 * p * p * m
+    p3, i3, o3 = qr_split(m, n)
+    return dict(panel_flops=p1 + p3, inner_flops=i1 + i3, tc_flops=o1 + o2 + o3,
+                factor_flops=p1 + i1 + o1 + o2 + p3 + i3 + o3,
+                resid_bytes=8.0 * (m * n + p * n), resid_flops=4.0 * (m * n + p * n))
+
+
 def gls_work(n, m, p, nb=32):
     p1, l1 = qr_work(n, m, nb)
     l2 = apply_work(n, m, p, nb)
@@ -180,9 +245,18 @@ def gls_work(n, m, p, nb=32):
                 resid_bytes=8.0 * (n * m + n * p), resid_flops=4.0 * (m * n + n * p))
 
 
-def fp32_simt_peak(sm_mhz):
-    """152 SMs x 128 FP32 lanes x 2 flop/FMA at the given SM clock (TFLOP/s)."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_simt_peak(sm_mhz, sms=152):
+    """SMs x 128 FP32 lanes x 2 flop/FMA at the given SM clock (TFLOP/s);
+    the SM count is read from the device at run time."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def tf32_peak(peaks, sustained=True):
+    """Dense TF32 tensor peak: the measured BF16 cuBLAS figure (sustained:
+    for a kernel timed inside a long step) times the nominal TF32 / BF16
+    ratio 1.1 / 2.25."""
+    bf = peaks.get("bf16_tflops_sustained" if sustained else "bf16_tflops") or peaks["bf16_tflops"]
+    return bf * 1.1 / 2.25
 
 
 def measured_peaks():
@@ -266,6 +340,7 @@ def run_batched(count, h, dev, stream, rank=0, sample_every=500):
     flops = sum(batch_work(m, n, p) for _, m, n, p, _ in specs)
     in_bytes = sum(8.0 * (m * n + p * n + m + p) for _, m, n, p, _ in specs)
     peaks = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out = {"workload": "batched uneven LSE, %d problems, m~U[32,512] n~U[16,m/2] p~U[1,n/4], "
                        "cond(A) log-U[1e1,1e6], cond(B)=10" % count,
            "value": count * 1000.0 / ms, "unit": "solves/s", "ms": ms,
@@ -279,7 +354,7 @@ def run_batched(count, h, dev, stream, rank=0, sample_every=500):
            "speedup_vs_fp64_direct": ms64 / ms,
            "device_speedup_vs_fp64_direct": dms64 / dms,
            "gflops": flops / (dms * 1e-3) / 1e9,
-           "roofline": {"fp32_frac": flops / (dms * 1e-3) / 1e12 / fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0)),
+           "roofline": {"fp32_frac": flops / (dms * 1e-3) / 1e12 / fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0), sms),
                         "hbm_frac": in_bytes / (dms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                         "note": "device time; FP32 GRQ flops vs FP32 SIMT peak; FP64 input bytes vs measured HBM"},
            "persistent_launches_per_solve_call": int(launches),
@@ -311,9 +386,42 @@ def run_batched(count, h, dev, stream, rank=0, sample_every=500):
 
 # --------------------------------------------------------------- arms --
 
-def make_inputs(rank):
+def cond_seed(cond, rank=0):
+    import math
+    return SEED + int(round(math.log10(cond))) + 1000 * rank
+
+
+def make_inputs(rank, device="cuda", cond=COND_A):
+    """The rank's LSE problem (replicas: every rank its own seed)."""
     from paper_2406_16499_gb300 import inputs as I
-    return I.gls_ar1(seed=SEED + 1000 * rank, n=N_, m=M_)
+    return I.lse_known_torch(cond_seed(cond, rank), M_, N_, P_, cond, COND_B, device)
+
+
+def make_gls_inputs(rank):
+    from paper_2406_16499_gb300 import inputs as I
+    return I.gls_ar1(seed=GLS_SEED + 1000 * rank, n=GLS_N, m=GLS_M)
+
+
+def host_problem(T):
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in T.items()}
+
+
+def oracle_accuracy(Hs, x, r, v):
+    """eta, e_con (oracle, double-double residual) and the forward error
+    against the known solution with its bound 10 kappa_up u."""
+    import numpy as np
+    import oracle
+    met = oracle.lse_metrics(Hs["A"], Hs["B"], Hs["b"], Hs["d"], x, r, v)
+    fe = float(np.linalg.norm(x - Hs["x_true"]) / np.linalg.norm(Hs["x_true"]))
+    bound = 10 * Hs["kappa_up"] * U64
+    return {"eta": met["eta"], "e_con": met["e_con"], "fwd": fe, "kappa_up": Hs["kappa_up"],
+            "fwd_over_bound": fe / bound,
+            "fp64_level": bool(met["eta"] <= 1e-14 and met["e_con"] <= 1e-14 and fe <= bound)}
+
+
+def oracle_cpu_solve(Hs, fact="fp32"):
+    import oracle
+    return oracle.lse_solve(Hs["A"], Hs["B"], Hs["b"], Hs["d"], fact=fact)
 
 
 def run_reference(args):
@@ -321,39 +429,186 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    G = make_inputs(0)
-    W, V, d = G["W"], G["V"], G["d"]
+    import numpy as np
+    import torch
+    T = make_inputs(0, "cpu")
+    Hs = host_problem(T)
+    del T
     oracle.lib()
     t0 = time.perf_counter()
-    out = oracle.gls_solve(W, V, d, fact="fp32")          # warm sample, also sizes the run
+    out = oracle_cpu_solve(Hs)                          # warm sample, also sizes the run
     t_first = time.perf_counter() - t0
     budget = 150.0
     warm = max(0, min(args.warmup - 1, int(budget / max(t_first, 1e-3)) // 4))
     for _ in range(warm):
-        oracle.gls_solve(W, V, d, fact="fp32")
+        oracle_cpu_solve(Hs)
     steps = max(1, min(args.steps, int(budget / max(t_first, 1e-3))))
     times = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        out = oracle.gls_solve(W, V, d, fact="fp32")
+        out = oracle_cpu_solve(Hs)
         times.append(time.perf_counter() - t0)
     ms = 1000.0 * sum(times) / len(times)
-    met = oracle.gls_metrics(W, V, d, out["x"], out["y"], out["z"])
+    acc = oracle_accuracy(Hs, out["x"], out["r"], out["v"])
     value = 1000.0 / ms
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
         "steps": steps, "warmup": 1 + warm, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "fact": "fp32", "refine": "classical",
-                   "parallelism": "replicas (rank 0 only for the CPU oracle)"},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
-                         "sample": "%d full solve(s) of the workload by the CPU oracle (Alg. 4: unblocked "
-                                   "FP32 GQR + FP64 classical IR, OpenMP)" % steps},
+        "config": config("fp32"),
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": nproc(), "kind": "oracle",
+                         "threads": oracle.num_threads(),
+                         "sample": "%d full solve(s) of the workload by the CPU oracle (Alg. 2: unblocked "
+                                   "FP32 GRQ + FP64 classical IR, OpenMP)" % steps},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "accuracy": {"eta": met["eta"], "e_con": met["e_con"], "iters": out["iters"], "status": out["status"]},
+        "accuracy": dict(acc, iters=out["iters"], status=out["status"]),
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def timed_solve(h, T, opts, stream, reps, x, r, v):
+    """Median device time (CUDA events on the launch stream) of `reps`
+    solves after one untimed one; returns (ms, status, info)."""
+    import torch
+    h.lse_solve(T["A"], T["B"], T["b"], T["d"], x, r, v, opts)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    ts, st, info = [], 0, None
+    for _ in range(reps):
+        e0.record(stream)
+        st, info = h.lse_solve(T["A"], T["B"], T["b"], T["d"], x, r, v, opts)
+        e1.record(stream)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sorted(ts)[len(ts) // 2], st, info
+
+
+def run_sweep(h, stream, rank, T_head, Hs_head):
+    """cond(A) in {1e1, 1e4, 1e8}: FP32 / TF32 factors with classical IR,
+    FP32 with GMRES-IR, and the FP64 direct solve; every result's accuracy
+    from the oracle's double-double residual and the known solution."""
+    import torch
+    from paper_2406_16499_gb300 import mpir
+    out = {}
+    x = torch.zeros(N_, dtype=torch.float64, device="cuda")
+    r = torch.zeros(M_, dtype=torch.float64, device="cuda")
+    v = torch.zeros(P_, dtype=torch.float64, device="cuda")
+    variants = [("fp32_classical", dict(fact="fp32", refine="classical"), 3),
+                ("tf32_classical", dict(fact="tf32", refine="classical", escalate=False), 3),
+                ("fp32_gmres", dict(fact="fp32", refine="gmres", escalate=False), 2),
+                ("fp64_direct", dict(fact="fp64", refine="direct"), 1)]
+    for cond in CONDS:
+        if cond == COND_A:
+            T, Hs = T_head, Hs_head
+        else:
+            T = make_inputs(rank, "cuda", cond)
+            Hs = host_problem(T) if rank == 0 else None
+        res = {}
+        for name, kw, reps in variants:
+            if name == "fp32_gmres" and cond >= 1e8:
+                res[name] = {"skipped": "u_f kappa(A) kappa(B) > 1: the block-diagonal preconditioner "
+                                        "does not apply (GMRES stalls; 6.3 s measured)"}
+                continue
+            ms, st, info = timed_solve(h, T, mpir.make_opts(**kw), stream, reps, x, r, v)
+            d = info.as_dict()
+            e = {"ms": ms, "status": st, "iters": d["iters"], "inner_iters": d["inner_iters"],
+                 "escalated": d["escalated"], "fact_used": d["fact_used"]}
+            if rank == 0:
+                e.update(oracle_accuracy(Hs, x.cpu().numpy(), r.cpu().numpy(), v.cpu().numpy()))
+            res[name] = e
+        out["%.0e" % cond] = res
+        if cond != COND_A:
+            del T, Hs
+            torch.cuda.empty_cache()
+    return out
+
+
+def run_gls(h, dev, stream, rank, steps):
+    """The GLS n = 4096 AR(1) workload: FP32 GQR + FP64 classical IR vs the
+    FP64 GQR direct solve, accuracy against the oracle's solution."""
+    import numpy as np
+    import torch
+    from paper_2406_16499_gb300 import mpir
+    G = make_gls_inputs(rank)
+    Wn, Vn, dn = G["W"], G["V"], G["d"]
+    n, m = Wn.shape
+    p = Vn.shape[1]
+
+    def to_dev(a):
+        return torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
+
+    W, V, d = to_dev(Wn), to_dev(Vn), torch.from_numpy(dn.copy()).to(dev)
+    x = torch.zeros(m, dtype=torch.float64, device=dev)
+    y = torch.zeros(p, dtype=torch.float64, device=dev)
+    z = torch.zeros(n, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(o, k):
+        h.gls_solve(W, V, d, x, y, z, o)
+        torch.cuda.synchronize()
+        ts, info = [], None
+        for _ in range(k):
+            flush.zero_()
+            e0.record(stream)
+            st, info = h.gls_solve(W, V, d, x, y, z, o)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2], st, info
+
+    out = {"workload": GLS_WORKLOAD, "l2": "inputs 168 MB > L2; 256 MB L2 flush before every timed step"}
+    ms, st, info = timed(mpir.make_opts(fact="fp32", refine="classical"), steps)
+    out["fp32_classical"] = {"ms": ms, "value": 1000.0 / ms, "unit": "solves/s", "status": st,
+                             "iters": info.iters}
+    if rank == 0:
+        import oracle
+        t = oracle.gls_truth(Wn, Vn, dn)
+        F = oracle.gls_factor(Wn, Vn, "fp64")
+        kap = oracle.gls_kappa(F, t["x"], t["y"])[0]
+        met = oracle.gls_metrics(Wn, Vn, dn, x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy())
+        fe = float(np.linalg.norm(x.cpu().numpy() - t["x"]) / np.linalg.norm(t["x"]))
+        out["fp32_classical"].update(eta=met["eta"], e_con=met["e_con"], fwd=fe, kappa=kap,
+                                     fwd_over_bound=fe / (10 * kap * U64))
+    ms, st, info = timed(mpir.make_opts(fact="fp32", refine="gmres", escalate=False), 2)
+    out["fp32_gmres"] = {"ms": ms, "status": st, "iters": info.iters, "inner_iters": info.inner_iters}
+    ms64, st, info = timed(mpir.make_opts(fact="fp64", refine="direct"), 2)
+    out["fp64_direct"] = {"ms": ms64, "value": 1000.0 / ms64, "status": st}
+    out["speedup_vs_fp64_direct"] = ms64 / out["fp32_classical"]["ms"]
+    return out
+
+
+def pick_roofline(prof, kp, work, iters, peaks, sms, clk):
+    """Roofline of the kernel kind with the largest device time per solve
+    (achieved = the algorithmic work of its launches / their summed CUDA-event
+    time)."""
+    cand = {k: v for k, v in prof.items() if v[1]}
+    name, (ms, cnt) = max(cand.items(), key=lambda kv: kv[1][0])
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sec = ms * 1e-3
+    if name == "larfb_tc":
+        alg = work["tc_flops"] * kp
+        roof = {"bound": "tensor", "unit": "TFLOP/s", "peak": tf32_peak(peaks, sustained=True),
+                "peak_note": "TF32 dense = measured sustained BF16 cuBLAS x 1.1/2.25 (of measured); the "
+                             "FP32-class update issues three TF32 products per algorithmic product",
+                "achieved": alg / sec / 1e12}
+    elif name in ("panel_qr", "larfb"):
+        alg = (work["panel_flops"] if name == "panel_qr" else work["inner_flops"]) * kp
+        roof = {"bound": "alu", "unit": "TFLOP/s", "peak": fp32_simt_peak(sm_max, sms),
+                "peak_note": "FP32 SIMT: %d SMs x 128 lanes x 2 x max SM clock" % sms,
+                "achieved": alg / sec / 1e12}
+    else:
+        alg = work["resid_bytes"] * kp * max(iters, 1)
+        roof = {"bound": "hbm", "unit": "GB/s", "peak": peaks["hbm_gbs"], "peak_note": "measured HBM copy",
+                "achieved": alg / sec / 1e9}
+    roof.update({"kernel": name, "frac": roof["achieved"] / roof["peak"], "launches_per_step": cnt / kp,
+                 "ms_per_step": ms / kp, "traffic": traffic_record(name),
+                 "peak_source": "fallback peaks (MEASURED_PEAKS.json absent)" if peaks.get("_fallback")
+                 else "MEASURED_PEAKS.json"})
+    return roof
 
 
 def run_ours(args):
@@ -368,22 +623,8 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-
-    G = make_inputs(rank)
-    Wn, Vn, dn = G["W"], G["V"], G["d"]
-    n, m = Wn.shape
-    p = Vn.shape[1]
-
-    def to_dev(a):
-        return torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
-
-    W, V, d = to_dev(Wn), to_dev(Vn), torch.from_numpy(dn.copy()).to(dev)
-    x = torch.zeros(m, dtype=torch.float64, device=dev)
-    y = torch.zeros(p, dtype=torch.float64, device=dev)
-    z = torch.zeros(n, dtype=torch.float64, device=dev)
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     h = mpir.Handle(local, stream.cuda_stream)
-    opts = mpir.make_opts(fact=args.fact, refine="classical")
     if args.batched_only:
         res = run_batched(args.batched_count, h, dev, stream, rank)
         if rank == 0:
@@ -391,10 +632,17 @@ def run_ours(args):
         h.close()
         return 0
 
-    def solve(o=opts, xx=x, yy=y, zz=z, WW=W, VV=V, dd=d):
-        st, info = h.gls_solve(WW, VV, dd, xx, yy, zz, o)
+    T = make_inputs(rank, dev)
+    A, B, b, d = T["A"], T["B"], T["b"], T["d"]
+    x = torch.zeros(N_, dtype=torch.float64, device=dev)
+    r = torch.zeros(M_, dtype=torch.float64, device=dev)
+    v = torch.zeros(P_, dtype=torch.float64, device=dev)
+    opts = mpir.make_opts(fact=args.fact, refine="classical")
+
+    def solve(o=opts, AA=A, BB=B, bb=b, dd=d):
+        st, info = h.lse_solve(AA, BB, bb, dd, x, r, v, o)
         if st != 0:
-            raise RuntimeError("gls_solve status %d: %s" % (st, h.last_error()))
+            raise RuntimeError("lse_solve status %d: %s" % (st, h.last_error()))
         return info
 
     def barrier():
@@ -402,8 +650,6 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    # the clock sampler runs from before the warm-up (the GPU is loaded from
-    # then on) to the end of the timed steps
     clocks = ClockSampler(local)
     clocks.start()
     for _ in range(max(args.warmup, 3)):
@@ -415,7 +661,6 @@ def run_ours(args):
     total_ms = 0.0
     info = None
     for _ in range(args.steps):
-        flush.zero_()
         e0.record(stream)
         info = solve()
         e1.record(stream)
@@ -438,156 +683,109 @@ def run_ours(args):
     mpir.profile(True)
     kp = max(2, min(args.steps, 4))
     for _ in range(kp):
-        flush.zero_()
         solve()
     torch.cuda.synchronize(dev)
     prof = mpir.profile_read()
     mpir.profile(False)
 
-    # ---- accuracy of the last solution (oracle, double-double residual) --
+    # ---- accuracy of the last solution: oracle residual, known solution --
+    Hs = host_problem(T) if rank == 0 else None
     acc = {}
     if rank == 0:
-        import oracle
-        met = oracle.gls_metrics(Wn, Vn, dn, x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy())
-        acc = {"eta": met["eta"], "e_con": met["e_con"], "iters": info.iters,
-               "stop_ratio": list(info.stop_ratio), "fact_used": info.fact_used, "escalated": info.escalated}
-
-    # ---- FP64 GQR direct solve on the same GPU (the fixed-precision path) --
-    o64 = mpir.make_opts(fact="fp64", refine="direct")
-    x64 = torch.zeros_like(x)
-    y64 = torch.zeros_like(y)
-    solve(o64, x64, y64)
-    torch.cuda.synchronize(dev)
-    k64 = 3
-    t64 = 0.0
-    for _ in range(k64):
-        flush.zero_()
-        e0.record(stream)
-        solve(o64, x64, y64)
-        e1.record(stream)
-        e1.synchronize()
-        t64 += e0.elapsed_time(e1)
-    ms64 = t64 / k64
-    fp64 = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_step": ms64,
-            "what": "FP64 GQR + Paige's method, no refinement, same kernels at FP64"}
-    if rank == 0:
-        import oracle
-        met = oracle.gls_metrics(Wn, Vn, dn, x64.cpu().numpy(), y64.cpu().numpy(),
-                                 np.zeros(n))
-        fp64["e_con"] = met["e_con"]
-
-    # ---- GMRES-IR (Sec. 5.3) on the same workload and FP32 factors ---------
-    og = mpir.make_opts(fact=args.fact, refine="gmres", escalate=False)
-    xg, yg, zg = torch.zeros_like(x), torch.zeros_like(y), torch.zeros_like(z)
-    solve(og, xg, yg, zg)
-    torch.cuda.synchronize(dev)
-    kg, tg, infog = 2, 0.0, None
-    for _ in range(kg):
-        flush.zero_()
-        e0.record(stream)
-        infog = solve(og, xg, yg, zg)
-        e1.record(stream)
-        e1.synchronize()
-        tg += e0.elapsed_time(e1)
-    msg = tg / kg
-    gmres = {"value": 1000.0 / msg, "unit": "solves/s", "ms_per_step": msg, "iters": infog.iters,
-             "inner_iters": infog.inner_iters, "gmres_ms": infog.time_ms[4],
-             "what": "GMRES-IR, block-diagonal split preconditioner, FP64 GMRES(30)"}
-    if rank == 0:
-        import oracle
-        met = oracle.gls_metrics(Wn, Vn, dn, xg.cpu().numpy(), yg.cpu().numpy(), zg.cpu().numpy())
-        gmres["eta"] = met["eta"]
-
-    # ---- batched uneven LSE (one persistent launch per call) ---------------
-    batched = None
-    if args.batched_count > 0 and world == 1:
-        batched = run_batched(args.batched_count, h, dev, stream, rank)
+        acc = oracle_accuracy(Hs, x.cpu().numpy(), r.cpu().numpy(), v.cpu().numpy())
+        acc.update(iters=info.iters, stop_ratio=list(info.stop_ratio), fact_used=info.fact_used,
+                   escalated=info.escalated)
 
     # ---- end to end from pinned host buffers through the public API --------
-    Wh = torch.from_numpy(np.ascontiguousarray(Wn.T)).pin_memory()
-    Vh = torch.from_numpy(np.ascontiguousarray(Vn.T)).pin_memory()
-    dh = torch.from_numpy(dn.copy()).pin_memory()
-    xh = torch.empty(m, dtype=torch.float64).pin_memory()
-    yh = torch.empty(p, dtype=torch.float64).pin_memory()
-    Wd = torch.empty((m, n), dtype=torch.float64, device=dev)
-    Vd = torch.empty((p, n), dtype=torch.float64, device=dev)
-    dd_ = torch.empty(n, dtype=torch.float64, device=dev)
-    h2d = (Wh.numel() + Vh.numel() + dh.numel()) * 8
-    d2h = (m + p) * 8
+    Ah = torch.empty((N_, M_), dtype=torch.float64).pin_memory()
+    Ah.copy_(A.t())
+    Bh = torch.empty((N_, P_), dtype=torch.float64).pin_memory()
+    Bh.copy_(B.t())
+    bh = b.cpu().pin_memory()
+    dh = d.cpu().pin_memory()
+    xh = torch.empty(N_, dtype=torch.float64).pin_memory()
+    Ad = torch.empty((N_, M_), dtype=torch.float64, device=dev)
+    Bd = torch.empty((N_, P_), dtype=torch.float64, device=dev)
+    bd = torch.empty(M_, dtype=torch.float64, device=dev)
+    ddv = torch.empty(P_, dtype=torch.float64, device=dev)
+    h2d = (Ah.numel() + Bh.numel() + bh.numel() + dh.numel()) * 8
+    d2h = N_ * 8
 
     def e2e_step():
-        Wd.copy_(Wh, non_blocking=True)
-        Vd.copy_(Vh, non_blocking=True)
-        dd_.copy_(dh, non_blocking=True)
-        solve(opts, x, y, z, Wd.t(), Vd.t(), dd_)
+        Ad.copy_(Ah, non_blocking=True)
+        Bd.copy_(Bh, non_blocking=True)
+        bd.copy_(bh, non_blocking=True)
+        ddv.copy_(dh, non_blocking=True)
+        solve(opts, Ad.t(), Bd.t(), bd, ddv)
         xh.copy_(x, non_blocking=True)
-        yh.copy_(y, non_blocking=True)
 
     e2e_step()
     torch.cuda.synchronize(dev)
     te = 0.0
-    ke = args.steps
+    ke = max(2, min(args.steps, 5))
     for _ in range(ke):
-        flush.zero_()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         e2e_step()
         torch.cuda.synchronize(dev)
         te += time.perf_counter() - t0
     e2e_ms = rank_max(1000.0 * te / ke, world, dev)
+    del Ah, Bh, Ad, Bd
+    torch.cuda.empty_cache()
+
+    # ---- cond(A) sweep: FP32 / TF32 / GMRES-IR / FP64 direct -------------
+    sweep = None if args.no_sweep else run_sweep(h, stream, rank, T, Hs)
+    fp64 = None
+    if sweep:
+        f = sweep["%.0e" % COND_A]["fp64_direct"]
+        fp64 = dict(f, value=1000.0 / f["ms"], unit="solves/s",
+                    what="FP64 GRQ + null-space method, no refinement, same kernels at FP64")
+
+    # ---- the GLS n = 4096 workload and the batched uneven LSE -------------
+    gls = None if args.no_gls else run_gls(h, dev, stream, rank, max(3, min(args.steps, 10)))
+    batched = None
+    if args.batched_count > 0 and world == 1:
+        batched = run_batched(args.batched_count, h, dev, stream, rank)
 
     # ---- roofline of the dominant kernel --------------------------------
-    work = gls_work(n, m, p)
+    work = lse_work(M_, N_, P_)
     peaks = measured_peaks()
-    # candidates run on the critical path only: larfb_tc / larfb_aux also
-    # launch on the side streams (aggregated factors, look-ahead updates),
-    # where their event times overlap the critical path and each other
-    crit = {k: v for k, v in prof.items() if k not in ("larfb_tc", "larfb_aux") and v[1]}
-    dom = max(crit.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_cnt) = dom
-    sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    if dom_name == "larfb":
-        alg = work["larfb_flops"] * kp
-        peak = fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0))
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_note": "FP32 SIMT: 152 SMs x 128 lanes x 2 x max SM clock"}
-        achieved = alg / (dom_ms * 1e-3) / 1e12
-    elif dom_name == "panel_qr":
-        alg = work["panel_flops"] * kp
-        peak = fp32_simt_peak(peaks.get("sm_max_mhz", 2070.0))
-        roof = {"bound": "alu", "unit": "TFLOP/s", "peak_note": "FP32 SIMT at max SM clock"}
-        achieved = alg / (dom_ms * 1e-3) / 1e12
-    else:
-        alg = work["resid_bytes"] * kp * (info.iters if info else 1)
-        peak = peaks["hbm_gbs"]
-        roof = {"bound": "hbm", "unit": "GB/s", "peak_note": "measured HBM copy bandwidth"}
-        achieved = alg / (dom_ms * 1e-3) / 1e9
-    roof.update({"kernel": dom_name, "achieved": achieved, "peak": peak, "frac": achieved / peak,
-                 "launches_per_step": dom_cnt / kp, "ms_per_step": dom_ms / kp,
-                 "traffic": traffic_record(dom_name),
-                 "peak_source": ("fallback peaks (MEASURED_PEAKS.json absent)" if peaks.get("_fallback")
-                                 else "MEASURED_PEAKS.json" if roof["bound"] == "hbm"
-                                 else "unit counts at the measured maximum SM clock (MEASURED_PEAKS.json)")})
+    roof = pick_roofline(prof, kp, work, info.iters if info else 1, peaks, sms, clk)
     kernels = {k: {"ms_per_step": v[0] / kp, "launches_per_step": v[1] / kp} for k, v in prof.items() if v[1]}
+    tc = prof.get("larfb_tc", (0.0, 0))
+    tensor = None
+    if tc[1]:
+        tensor = {"kernel": "k_gemm_tc (tcgen05, TMA, TMEM)", "algorithmic_tflops": work["tc_flops"] * kp /
+                  (tc[0] * 1e-3) / 1e12, "peak": tf32_peak(peaks, True),
+                  "note": "algorithmic trailing-update flops / summed event time of the tensor-core GEMM "
+                          "launches; the FP32-class update runs three TF32 products per product"}
+        tensor["frac"] = tensor["algorithmic_tflops"] / tensor["peak"]
+    dg = prof.get("dual_gemv_fp64", (0.0, 0))
+    resid = None
+    if dg[1]:
+        nres = dg[1] / 2.0                     # two launches (A and B blocks) per residual
+        resid = {"kernel": "k_dual_gemv (FP64 residual)", "gbs": work["resid_bytes"] * nres / (dg[0] * 1e-3) / 1e9,
+                 "peak": peaks["hbm_gbs"]}
+        resid["frac"] = resid["gbs"] / resid["peak"]
 
-    # ---- CPU oracle on the host cores (bounded sample, rank 0, N = 1) ----
+    # ---- CPU oracle on the host cores (rank 0, N = 1) ---------------------
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         t0 = time.perf_counter()
-        oracle.gls_solve(Wn, Vn, dn, fact="fp32")
-        tc = time.perf_counter() - t0
-        cpu = {"value": 1.0 / tc, "unit": "solves/s", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": "1 full solve of the workload (Alg. 4: unblocked FP32 GQR + FP64 IR, OpenMP), "
-                         "%.1f s" % tc}
+        oracle_cpu_solve(Hs)
+        tc_ = time.perf_counter() - t0
+        cpu = {"value": 1.0 / tc_, "unit": "solves/s", "cores": nproc(), "threads": oracle.num_threads(),
+               "kind": "oracle",
+               "sample": "1 full solve of the workload (Alg. 2: unblocked FP32 GRQ + FP64 IR, OpenMP), "
+                         "%.1f s" % tc_}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "fact": args.fact, "refine": "classical",
-                       "parallelism": "replicas" if world > 1 else "single GPU",
-                       "l2": "inputs 168 MB > L2; 256 MB L2 flush before every timed step"},
+            "config": config(args.fact),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": job_value(world, e2e_ms), "unit": "solves/s", "ms_per_step": e2e_ms,
@@ -596,11 +794,15 @@ def run_ours(args):
             "clocks": clk,
             "accuracy": acc,
             "fp64_direct": fp64,
-            "gmres_ir": gmres,
+            "speedup_vs_fp64_direct": (fp64["ms"] / ms) if fp64 else None,
+            "sweep": sweep,
+            "gls_ar1": gls,
             "batched_lse": batched,
-            "speedup_vs_fp64_direct": value / (world * fp64["value"]),
+            "tensor_core_update": tensor,
+            "fp64_residual": resid,
             "kernels": kernels,
             "algorithmic": work,
+            "parallelism": "replicas" if world > 1 else "single GPU",
         }
         print(json.dumps(line), flush=True)
     h.close()

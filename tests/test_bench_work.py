@@ -42,3 +42,24 @@ def test_gls_workload_count_matches_the_gqr():
 
 def test_fp32_simt_peak_from_unit_counts():
     assert bench.fp32_simt_peak(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+
+
+def test_lse_workload_count_matches_the_grq():
+    """LSE m = 16384, n = 8192, p = 1024: QR of the n x p B~ (1.65e10), its
+    reflectors applied to the m columns of X (5.15e11), QR of the m x n
+    A Q^T (1.83e12): 2.37e12 flops; the split into panel, inner (SIMT) and
+    tensor-core parts sums to the total."""
+    m, n, p = 16384, 8192, 1024
+    w = bench.lse_work(m, n, p)
+    textbook = qr_flops(n, p) + (4.0 * n * p * m - 2.0 * p * p * m) + qr_flops(m, n)
+    assert abs(textbook / 2.37e12 - 1) < 0.005
+    assert abs(w["factor_flops"] / textbook - 1) < 0.03
+    assert w["panel_flops"] + w["inner_flops"] + w["tc_flops"] == pytest.approx(w["factor_flops"])
+    assert w["tc_flops"] > 0.9 * w["factor_flops"]
+    assert w["resid_bytes"] == 8.0 * (m * n + p * n)
+
+
+def test_tf32_peak_from_measured_bf16():
+    peaks = {"bf16_tflops": 1920.0, "bf16_tflops_sustained": 1697.3}
+    assert bench.tf32_peak(peaks, sustained=False) == pytest.approx(1920.0 * 1.1 / 2.25)
+    assert bench.tf32_peak(peaks, sustained=True) == pytest.approx(1697.3 * 1.1 / 2.25)

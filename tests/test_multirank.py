@@ -80,11 +80,14 @@ def test_reference_arm_nonzero_rank_exits_without_work():
 def test_each_rank_draws_its_own_problem(monkeypatch):
     """Replicas: every rank solves an independent problem of the same shape
     (seed offset by rank), so the job's throughput counts N distinct solves."""
+    pytest.importorskip("torch")
     sys.path.insert(0, ROOT)
     import bench
-    monkeypatch.setattr(bench, "N_", 64)
-    monkeypatch.setattr(bench, "M_", 16)
-    g0, g1 = bench.make_inputs(0), bench.make_inputs(1)
-    assert g0["W"].shape == g1["W"].shape == (64, 16) and g0["V"].shape == (64, 64)
-    assert not (g0["W"] == g1["W"]).all()
-    assert (bench.make_inputs(1)["d"] == g1["d"]).all()
+    monkeypatch.setattr(bench, "M_", 64)
+    monkeypatch.setattr(bench, "N_", 32)
+    monkeypatch.setattr(bench, "P_", 4)
+    g0, g1 = bench.make_inputs(0, "cpu"), bench.make_inputs(1, "cpu")
+    assert g0["A"].shape == g1["A"].shape == (64, 32) and g0["B"].shape == (4, 32)
+    assert not (g0["A"] == g1["A"]).all()
+    assert (bench.make_inputs(1, "cpu")["d"] == g1["d"]).all()
+    assert bench.config("fp32") == bench.config("fp32") and bench.config()["workload"] == bench.WORKLOAD
