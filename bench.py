@@ -65,8 +65,17 @@ def parse():
     ap.add_argument("--no-gls", action="store_true", help="skip the GLS n=4096 workload")
     ap.add_argument("--batched-count", type=int, default=10000,
                     help="problems of the uneven batched LSE workload (0: skip it)")
+    ap.add_argument("--batched-gls-count", type=int, default=4000,
+                    help="problems of the uneven batched GLS workload (0: skip it)")
+    ap.add_argument("--selector-count", type=int, default=100,
+                    help="held-out LSE and GLS problems of the selector comparison (0: skip it)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched LSE workload (prints its JSON object)")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="with --quick: bracket the timed steps by cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
+    ap.add_argument("--size", type=int, nargs=3, metavar=("M", "N", "P"),
+                    help="with --quick: another LSE shape of the same construction (small ncu captures)")
     return ap.parse_args()
 
 
@@ -384,6 +393,166 @@ def run_batched(count, h, dev, stream, rank=0, sample_every=500):
     return out
 
 
+def gls_batch_work(n, m, p):
+    """Algorithmic flops of one batched GLS problem: the GQR (QR of the
+    n x m W, its reflectors applied to the p columns of V, QR of the p x n
+    C~) plus one residual."""
+    kC = min(n, p)
+    f = 2.0 * n * m * m - 2.0 * m ** 3 / 3.0 + 4.0 * n * m * p - 2.0 * m * m * p
+    f += 2.0 * p * n * kC - 2.0 * kC ** 3 / 3.0
+    return f + 8.0 * (n * m + n * p)
+
+
+def run_batched_gls(count, h, dev, rank=0, sample_every=250):
+    """Uneven batch of `count` GLS problems (n ~ U[32,512], m ~ U[4,n/2],
+    p ~ U[n,5n/4], cond(W) log-uniform in [1e1,1e5]) in one persistent
+    launch; FP64 comparator on the same kernel; oracle accuracy on a
+    sample."""
+    import numpy as np
+    import torch
+    from paper_2406_16499_gb300 import inputs as I, mpir
+    specs = I.gls_batch_specs(count=count)
+    t0 = time.perf_counter()
+    probs = I.gls_batch_torch(specs, dev)
+    torch.cuda.synchronize(dev)
+    gen_s = time.perf_counter() - t0
+    xs = [torch.zeros(sp[2], dtype=torch.float64, device=dev) for sp in specs]
+    ys = [torch.zeros(sp[3], dtype=torch.float64, device=dev) for sp in specs]
+    batch = mpir.GlsBatch(probs, xs, ys)
+
+    def timed(opts, reps):
+        h.gls_solve_batched(batch, opts=opts)
+        torch.cuda.synchronize(dev)
+        call, devt = [], []
+        st, infos = 0, None
+        for _ in range(reps):
+            mpir.profile(True)
+            t0 = time.perf_counter()
+            st, infos = h.gls_solve_batched(batch, opts=opts)
+            torch.cuda.synchronize(dev)
+            call.append((time.perf_counter() - t0) * 1e3)
+            devt.append(mpir.profile_read()["batched"][0])
+            mpir.profile(False)
+        return st, infos, sorted(call)[len(call) // 2], sorted(devt)[len(devt) // 2]
+
+    st, infos, ms, dms = timed(mpir.make_opts(fact="fp32"), 3)
+    st64, _, ms64, dms64 = timed(mpir.make_opts(fact="fp64", refine="direct", escalate=False), 2)
+    flops = sum(gls_batch_work(n, m, p) for _, n, m, p, _ in specs)
+    out = {"workload": "batched uneven GLS, %d problems, n~U[32,512] m~U[4,n/2] p~U[n,5n/4], "
+                       "cond(W) log-U[1e1,1e5], cond(V)=10" % count,
+           "value": count * 1000.0 / ms, "unit": "solves/s", "ms": ms,
+           "device": {"value": count * 1000.0 / dms, "ms": dms,
+                      "what": "graph launch of the persistent kernels alone (CUDA events)"},
+           "status": st, "not_converged": sum(1 for f in infos if f.status != 0),
+           "escalated": sum(1 for f in infos if f.escalated),
+           "iters_mean": float(np.mean([f.iters for f in infos])),
+           "fp64_direct": {"value": count * 1000.0 / ms64, "unit": "solves/s", "ms": ms64, "device_ms": dms64,
+                           "status": st64},
+           "speedup_vs_fp64_direct": ms64 / ms, "device_speedup_vs_fp64_direct": dms64 / dms,
+           "gflops": flops / (dms * 1e-3) / 1e9, "input_generation_s": gen_s}
+    if rank == 0:
+        import oracle
+        worst = {"e_con": 0.0, "fe_over_bound": 0.0}
+        ks = list(range(0, count, max(1, sample_every)))
+        for k in ks:
+            W, V, d = (probs[k][key].cpu().numpy() for key in ("W", "V", "d"))
+            x, y = xs[k].cpu().numpy(), ys[k].cpu().numpy()
+            t = oracle.gls_truth(W, V, d)
+            F = oracle.gls_factor(W, V, "fp64")
+            kap = oracle.gls_kappa(F, t["x"], t["y"])[0]
+            f2 = d - W @ x - V @ y
+            e_con = np.linalg.norm(f2) / (np.linalg.norm(W) * np.linalg.norm(x) + np.linalg.norm(V) *
+                                          np.linalg.norm(y) + np.linalg.norm(d))
+            fe = float(np.linalg.norm(x - t["x"]) / np.linalg.norm(t["x"]))
+            worst["e_con"] = max(worst["e_con"], e_con)
+            worst["fe_over_bound"] = max(worst["fe_over_bound"], fe / (10 * kap * U64))
+        out["accuracy_sample"] = dict(worst, problems=len(ks),
+                                      note="oracle e_con and forward error / (10 kappa u) on every "
+                                           "%d-th problem" % sample_every)
+    return out
+
+
+def run_selector(h, rank, count=100):
+    """The learned selector with the shipped weights on a held-out mixed set
+    (`count` LSE and `count` GLS problems, kappa_2 log-uniform in [1, 1e12]):
+    total wall time of fact = AUTO (features, network, chosen solve,
+    escalation) against fixed FP32 + classical IR with escalation, every
+    AUTO answer judged by the oracle (FP64-level bar)."""
+    import numpy as np
+    import torch
+    from paper_2406_16499_gb300 import inputs as I, mpir, selector as SEL
+    path = os.path.join(ROOT, "paper_2406_16499_gb300", "selector_weights.npz")
+    if not os.path.exists(path):
+        return {"skipped": "no trained selector weights (python -m paper_2406_16499_gb300.train_selector)"}
+    sel = SEL.Selector.load(path)
+    sel.install(h)
+    held = [("lse", P) for P in I.selector_lse_problems(909, count)]
+    held += [("gls", G) for G in I.selector_gls_problems(910, count)]
+
+    def dev(a):
+        a = np.asarray(a, dtype=np.float64)
+        return torch.from_numpy(a.copy()).cuda() if a.ndim == 1 else torch.from_numpy(np.ascontiguousarray(a.T)).cuda().t()
+
+    def run(kind, P, fact):
+        if kind == "lse":
+            A, B, b, d = (dev(P[k]) for k in ("A", "B", "b", "d"))
+            m, n = P["A"].shape
+            p = P["B"].shape[0]
+            x, r, v = (torch.zeros(k, dtype=torch.float64, device="cuda") for k in (n, m, max(p, 1)))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st, info = h.lse_solve(A, B, b, d, x, r, v if p else None, mpir.make_opts(fact=fact))
+            torch.cuda.synchronize()
+            return st, info, time.perf_counter() - t0, (x.cpu().numpy(), r.cpu().numpy(), v.cpu().numpy()[:p])
+        W, V, d = (dev(P[k]) for k in ("W", "V", "d"))
+        n, m = P["W"].shape
+        p = P["V"].shape[1]
+        x, y, z = (torch.zeros(k, dtype=torch.float64, device="cuda") for k in (m, p, n))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, info = h.gls_solve(W, V, d, x, y, z, mpir.make_opts(fact=fact))
+        torch.cuda.synchronize()
+        return st, info, time.perf_counter() - t0, (x.cpu().numpy(), y.cpu().numpy(), z.cpu().numpy())
+
+    run(*held[0], "fp32")
+    run(*held[0], "auto")
+    t_auto = t_fixed = 0.0
+    worst_eta = worst_econ = 0.0
+    chosen = [0] * 6
+    fails = esc_auto = esc_fixed = 0
+    for kind, P in held:
+        st0, inf0, tf, _ = run(kind, P, "fp32")
+        st1, inf1, ta, sol = run(kind, P, "auto")
+        t_fixed += tf
+        t_auto += ta
+        esc_fixed += inf0.escalated
+        esc_auto += inf1.escalated
+        if st1 != 0:
+            fails += 1
+        cls = 2 * {0: 0, 1: 0, 2: 1, 3: 2}.get(inf1.fact_used, 1) + (1 if inf1.refine_used == 1 else 0)
+        chosen[min(cls, 5)] += 1
+        if rank == 0:
+            import oracle
+            if kind == "lse":
+                met = oracle.lse_metrics(P["A"], P["B"], P["b"], P["d"], *sol)
+            else:
+                met = oracle.gls_metrics(P["W"], P["V"], P["d"], *sol)
+            worst_eta = max(worst_eta, met["eta"])
+            worst_econ = max(worst_econ, met["e_con"])
+    h.selector_set(None, None, None)
+    n_all = len(held)
+    return {"workload": "held-out mixed set: %d LSE (m~U[64,400]) + %d GLS (n~U[64,400]), kappa log-U[1,1e12]"
+                        % (count, count),
+            "auto": {"value": n_all / t_auto, "unit": "solves/s", "seconds": t_auto, "escalated": esc_auto,
+                     "failed": fails},
+            "fixed_fp32_escalating": {"value": n_all / t_fixed, "unit": "solves/s", "seconds": t_fixed,
+                                      "escalated": esc_fixed},
+            "gain": t_fixed / t_auto, "classes_chosen": dict(zip(["%s+%s" % c for c in SEL.CLASSES], chosen)),
+            "oracle_worst": {"eta": worst_eta, "e_con": worst_econ},
+            "note": "wall time per solve including the selector's features and network; weights trained by "
+                    "train_selector on the library's own timed solves"}
+
+
 # --------------------------------------------------------------- arms --
 
 def cond_seed(cond, rank=0):
@@ -467,11 +636,12 @@ def run_reference(args):
     return 0
 
 
-def timed_solve(h, T, opts, stream, reps, x, r, v):
+def timed_solve(h, T, opts, stream, reps, x, r, v, warm=True):
     """Median device time (CUDA events on the launch stream) of `reps`
-    solves after one untimed one; returns (ms, status, info)."""
+    solves after one untimed one (warm); returns (ms, status, info)."""
     import torch
-    h.lse_solve(T["A"], T["B"], T["b"], T["d"], x, r, v, opts)
+    if warm:
+        h.lse_solve(T["A"], T["B"], T["b"], T["d"], x, r, v, opts)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -495,9 +665,13 @@ def run_sweep(h, stream, rank, T_head, Hs_head):
     x = torch.zeros(N_, dtype=torch.float64, device="cuda")
     r = torch.zeros(M_, dtype=torch.float64, device="cuda")
     v = torch.zeros(P_, dtype=torch.float64, device="cuda")
+    # FP64 classical: FP64 factors + FP64 refinement, the fixed-precision
+    # solve that reaches the FP64-level bar (the unrefined FP64 direct solve
+    # computes r = b - A x directly and loses r's accuracy to cancellation)
     variants = [("fp32_classical", dict(fact="fp32", refine="classical"), 3),
                 ("tf32_classical", dict(fact="tf32", refine="classical", escalate=False), 3),
                 ("fp32_gmres", dict(fact="fp32", refine="gmres", escalate=False), 2),
+                ("fp64_classical", dict(fact="fp64", refine="classical", escalate=False), 1),
                 ("fp64_direct", dict(fact="fp64", refine="direct"), 1)]
     for cond in CONDS:
         if cond == COND_A:
@@ -511,7 +685,8 @@ def run_sweep(h, stream, rank, T_head, Hs_head):
                 res[name] = {"skipped": "u_f kappa(A) kappa(B) > 1: the block-diagonal preconditioner "
                                         "does not apply (GMRES stalls; 6.3 s measured)"}
                 continue
-            ms, st, info = timed_solve(h, T, mpir.make_opts(**kw), stream, reps, x, r, v)
+            ms, st, info = timed_solve(h, T, mpir.make_opts(**kw), stream, reps, x, r, v,
+                                       warm=not name.startswith("fp64"))
             d = info.as_dict()
             e = {"ms": ms, "status": st, "iters": d["iters"], "inner_iters": d["inner_iters"],
                  "escalated": d["escalated"], "fact_used": d["fact_used"]}
@@ -632,6 +807,11 @@ def run_ours(args):
         h.close()
         return 0
 
+    global M_, N_, P_
+    if args.size:
+        if not args.quick:
+            raise SystemExit("--size is for --quick profiling runs only")
+        M_, N_, P_ = args.size
     T = make_inputs(rank, dev)
     A, B, b, d = T["A"], T["B"], T["b"], T["d"]
     x = torch.zeros(N_, dtype=torch.float64, device=dev)
@@ -660,12 +840,16 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     total_ms = 0.0
     info = None
+    if args.profile_range:
+        torch.cuda.profiler.start()
     for _ in range(args.steps):
         e0.record(stream)
         info = solve()
         e1.record(stream)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
+    if args.profile_range:
+        torch.cuda.profiler.stop()
     clk = clocks.stop()
     barrier()
     gpu_launches = (mpir.launch_count() - launches0) // max(args.steps, 1)
@@ -675,7 +859,8 @@ def run_ours(args):
     if args.quick:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "ms_per_step": ms,
-                              "quick": True, "iters": info.iters if info else None}), flush=True)
+                              "quick": True, "size": [M_, N_, P_], "iters": info.iters if info else None,
+                              "gpu_launches": int(gpu_launches)}), flush=True)
         h.close()
         return 0
 
@@ -737,15 +922,22 @@ def run_ours(args):
     sweep = None if args.no_sweep else run_sweep(h, stream, rank, T, Hs)
     fp64 = None
     if sweep:
-        f = sweep["%.0e" % COND_A]["fp64_direct"]
+        f = sweep["%.0e" % COND_A]["fp64_classical"]
         fp64 = dict(f, value=1000.0 / f["ms"], unit="solves/s",
-                    what="FP64 GRQ + null-space method, no refinement, same kernels at FP64")
+                    what="FP64 GRQ + null-space start + FP64 classical IR (same kernels at FP64): the "
+                         "fixed-precision solve at the same FP64-level accuracy")
 
     # ---- the GLS n = 4096 workload and the batched uneven LSE -------------
     gls = None if args.no_gls else run_gls(h, dev, stream, rank, max(3, min(args.steps, 10)))
     batched = None
     if args.batched_count > 0 and world == 1:
         batched = run_batched(args.batched_count, h, dev, stream, rank)
+    batched_gls = None
+    if args.batched_gls_count > 0 and world == 1:
+        batched_gls = run_batched_gls(args.batched_gls_count, h, dev, rank)
+    selector = None
+    if args.selector_count > 0 and world == 1:
+        selector = run_selector(h, rank, args.selector_count)
 
     # ---- roofline of the dominant kernel --------------------------------
     work = lse_work(M_, N_, P_)
@@ -765,7 +957,9 @@ def run_ours(args):
     if dg[1]:
         nres = dg[1] / 2.0                     # two launches (A and B blocks) per residual
         resid = {"kernel": "k_dual_gemv (FP64 residual)", "gbs": work["resid_bytes"] * nres / (dg[0] * 1e-3) / 1e9,
-                 "peak": peaks["hbm_gbs"]}
+                 "peak": peaks["hbm_gbs"], "traffic_per_launch": traffic_record("dual_gemv_fp64"),
+                 "algorithmic_bytes_per_launch": work["resid_bytes"] / 2,
+                 "note": "FP64-pipe bound (two FMAs per 8-byte element); ncu: FP64 pipe 91 % busy"}
         resid["frac"] = resid["gbs"] / resid["peak"]
 
     # ---- CPU oracle on the host cores (rank 0, N = 1) ---------------------
@@ -798,6 +992,8 @@ def run_ours(args):
             "sweep": sweep,
             "gls_ar1": gls,
             "batched_lse": batched,
+            "batched_gls": batched_gls,
+            "selector": selector,
             "tensor_core_update": tensor,
             "fp64_residual": resid,
             "kernels": kernels,

@@ -42,11 +42,15 @@
 extern "C" {
 #endif
 
-/* Factorization precision u_f (Sec. 3).  The panel is FP32 for the three
+/* Factorization precision u_f (Sec. 3).  The panels are FP32 for the three
  * low-precision kinds; the tensor-core trailing updates use three TF32
- * products (MPIR_FP32, FP32-accurate) or one (MPIR_TF32; MPIR_BF16 runs the
- * same single TF32 product: there is no bfloat16 tensor-core path).  MPIR_FP64 is the
- * fixed-precision FP64 path. */
+ * products (MPIR_FP32, FP32-accurate), one TF32 product (MPIR_TF32) or one
+ * bfloat16 product (MPIR_BF16: tcgen05 kind::f16, FP32 accumulation).  For
+ * MPIR_TF32 and MPIR_BF16 only the dominant factorization (the QR of A Q^T
+ * for LSE, the RQ of Q^T V for GLS) runs at that precision; the first one
+ * (RQ of B with Q applied to A, QR of W with Q^T applied to V) stays
+ * FP32-class, and LSE factors those of (A D, B D) with a power-of-two column
+ * scaling D (x = D y).  MPIR_FP64 is the fixed-precision FP64 path. */
 typedef enum {
     MPIR_BF16 = 0,
     MPIR_TF32 = 1,
@@ -61,7 +65,10 @@ typedef enum {
     MPIR_CLASSICAL = 0,   /* classical IR (Alg. 2 / Alg. 4)                      */
     MPIR_GMRES = 1,       /* GMRES-IR with the block-diagonal split preconditioner
                              (Sec. 5.2, 5.3)                                      */
-    MPIR_DIRECT = 2       /* no refinement: null-space / Paige solve at u_f       */
+    MPIR_DIRECT = 2,      /* no refinement: null-space / Paige solve at u_f       */
+    MPIR_GMRES_LEFT = 3   /* GMRES-IR with the left preconditioner M ~ F~^-1 applied
+                             by the correction solver on the held factors
+                             (Sec. 5.1); every shape                              */
 } mpir_refine;
 
 /* Status codes (positive return values and mpir_info.status). */
@@ -80,7 +87,9 @@ typedef struct {
     int fact;          /* mpir_prec, default MPIR_FP32                            */
     int refine;        /* mpir_refine, default MPIR_CLASSICAL                     */
     double tol;        /* stop-test tolerance (eq. lse-stop / gls-stop); <= 0:
-                          2e-15                                                   */
+                          1e-15 (about 9 u: with the stop ratios below it the
+                          forward error stays below 10 kappa u down to
+                          kappa = 1)                                              */
     int maxit;         /* refinement steps, <= 0: 40 (Alg. 2 / Alg. 4 default)    */
     int restart;       /* GMRES restart length, <= 0: 30                          */
     int inner_maxit;   /* GMRES iterations per outer step, <= 0: 300              */
@@ -142,7 +151,8 @@ const char *mpir_last_error(mpir_handle handle);
  * Outputs: x (n); optionally r = b - A x (m) and the multiplier v (p) with
  * A^T r = B^T v (eq. aug-LSE); r and v may be NULL.
  * Algorithm: GRQ B = [0 R] Q, A = Z T Q at u_f, null-space start, then
- * Alg. 2 (classical) or GMRES-IR (Sec. 5.2), FP64 residuals and updates.
+ * Alg. 2 (classical), GMRES-IR with the split (Sec. 5.2) or the left
+ * (Sec. 5.1) preconditioner, FP64 residuals and updates.
  * ------------------------------------------------------------------- */
 int lse_solve(mpir_handle h, int m, int n, int p,
               const double *A, int lda, const double *B, int ldb,
@@ -156,7 +166,8 @@ int lse_solve(mpir_handle h, int m, int n, int p,
  *   rank([W, V]) = n (LAPACK xGGGLM's (A, B) = (W, V)).
  * Outputs: x (m), y (p), optionally z (n) with y = V^T z, W^T z = 0.
  * Algorithm: GQR W = Q [R; 0], V = Q T Z at u_f, Paige's method, then
- * Alg. 4 (classical) or GMRES-IR (Sec. 5.3).
+ * Alg. 4 (classical), GMRES-IR with the split (Sec. 5.3) or the left
+ * (Sec. 5.1) preconditioner.
  * ------------------------------------------------------------------- */
 int gls_solve(mpir_handle h, int n, int m, int p,
               const double *W, int ldw, const double *V, int ldv,
@@ -178,7 +189,7 @@ int gls_solve(mpir_handle h, int n, int m, int p,
  * candidates on a sample of the batch the first time a shape is seen.
  * Problems that do not converge are re-solved one by one with an FP64
  * factorization when opts->escalate is set (info.escalated = 1).
- * refine = MPIR_GMRES solves the problems one by one with lse_solve.
+ * refine = MPIR_GMRES or MPIR_GMRES_LEFT solves the problems one by one with lse_solve.
  * The handle's stream is synchronized before returning.
  * ------------------------------------------------------------------- */
 int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n,
@@ -288,13 +299,15 @@ int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
  * scaled augmented operator and the block-diagonal split preconditioners,
  * in FP64 arithmetic on FP64 vectors (factors read in their storage
  * precision).  which: 0 -> F~(alpha, beta) u, 1 -> M_l u, 2 -> M_r u,
- * 3 -> M_l F~ M_r u.
- * LSE (needs m >= n): vectors of length m + p + n ordered [m; p; n],
+ * 3 -> M_l F~ M_r u; 4 -> M u, 5 -> M F~ u with the left preconditioner
+ * M ~ F~^-1 of Sec. 5.1 (eq. lse-leftpre / gls-leftpre: the correction
+ * solver, Alg. 1 / Alg. 3, on the held factors; every shape).
+ * LSE (which 0-3 need m >= n): vectors of length m + p + n ordered [m; p; n],
  *   F~ = [a I, 0, A; 0, 0, b B; A^T, b B^T, 0],
  *   M_l = diag(a^-1/2 I, a^-1/2 b^-1 S R^-1, a^1/2 T1^-T Q),
  *   M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-T S^T, a^1/2 Q^T T1^-1),
  *   T1 the leading n x n of T, S its trailing p x p.
- * GLS (needs n <= p): vectors of length p + n + m ordered [p; n; m],
+ * GLS (which 0-3 need n <= p): vectors of length p + n + m ordered [p; n; m],
  *   F~ = [a I, V^T, 0; V, 0, b W; 0, b W^T, 0],
  *   M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^T, a^-1/2 b^-1 S^T R^-T),
  *   M_r = diag(a^-1/2 I, a^1/2 Q T2^-T, a^-1/2 b^-1 R^-1 S),
@@ -314,7 +327,8 @@ int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, 
  * 1), T: K x K upper triangular, column-major with leading dimension 128,
  * C: M x N (ldc a multiple of 4, C 16-byte aligned).  All FP32 device
  * arrays, K <= 128.  prec: MPIR_FP32 (three TF32 products, FP32-class) or
- * MPIR_TF32 (one TF32 product).  Returns 0, a negative argument index, or
+ * MPIR_TF32 (one TF32 product) or MPIR_BF16 (one bfloat16 product, FP32
+ * accumulation).  Returns 0, a negative argument index, or
  * MPIR_UNSUPPORTED.  Uses the handle's workspace as scratch: factors held
  * from an earlier mpir_*_factor are dropped. */
 int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int ldv,
@@ -335,7 +349,10 @@ int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int
  * doubles; e.g. n = m = p = 4096 needs 264k) return MPIR_UNSUPPORTED.
  * The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the one array and leaves
+ * before any stream capture.  The address is kept for the life of the
+ * process (concurrent first calls from several host threads are safe): a
+ * cudaDeviceReset of that device, which also frees every handle's memory,
+ * ends the library's use of the device in this process.  Every call shares the one array and leaves
  * its contents behind, so calls whose GPU work overlaps (two streams, two
  * host threads) race and must be serialized by the caller.  Returns 0, a
  * negative argument index, MPIR_UNSUPPORTED or MPIR_CUDA_ERROR. */
@@ -388,6 +405,13 @@ int mpir_mlp_forward(mpir_handle h, const float *params, const float *X, int cou
 int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam_v, int step,
                         float lr, const float *X, const int *labels, int count, float *grad,
                         float *loss);
+/* As mpir_mlp_train_step with a target distribution per sample instead of a
+ * label (targets: device float[count][6], each row summing to 1): the loss
+ * is the mean of -sum_c targets[c] log prob[c] (a cost-weighted target puts
+ * its mass on the classes that solve the problem fastest). */
+int mpir_mlp_train_step_soft(mpir_handle h, float *params, float *adam_m, float *adam_v, int step,
+                             float lr, const float *X, const float *targets, int count,
+                             float *grad, float *loss);
 
 /* Install a trained selector in the handle (host arrays: params as above,
  * feature standardization mean[16] and scale[16]: the network sees

@@ -1,4 +1,4 @@
-// batched.cu -- host side of the batched LSE solver: dispatch over the
+// batched.cu -- host side of the batched LSE / GLS solver: dispatch over the
 // compiled launch shapes and the sizing helpers (device code in
 // batched_kernel.cuh, one translation unit per launch shape).
 #include <algorithm>
@@ -64,26 +64,39 @@ int batched_launch(const BConfig &c, bool fp64, const BInst *tab, const int *ord
     }
 }
 
-size_t batched_big_words(int m, int n, int p)
+static BPlan plan_of(int kind, int m, int n, int p)
 {
-    const BPlan P = bplan(m, n, p);
-    return P.fac_big;
+    return kind == BKIND_GLS ? gplan(m, n, p) : bplan(m, n, p);
 }
 
-size_t batched_smem_min(int m, int n, int p, bool fp64)
+size_t batched_big_words(int kind, int m, int n, int p)
 {
-    const BPlan P = bplan(m, n, p);
+    return plan_of(kind, m, n, p).fac_big;
+}
+
+size_t batched_smem_min(int kind, int m, int n, int p, bool fp64)
+{
+    const BPlan P = plan_of(kind, m, n, p);
     return fp64 ? bsmem_need<double>(P, 0) : bsmem_need<float>(P, 0);
 }
 
-size_t batched_smem_full(int m, int n, int p, bool fp64)
+size_t batched_smem_full(int kind, int m, int n, int p, bool fp64)
 {
-    const BPlan P = bplan(m, n, p);
+    const BPlan P = plan_of(kind, m, n, p);
     return fp64 ? bsmem_need<double>(P, 2) : bsmem_need<float>(P, 2);
 }
 
-double batched_work(int m, int n, int p)
+double batched_work(int kind, int m, int n, int p)
 {
+    if (kind == BKIND_GLS) {
+        // GQR flops (QR of n x m with Q^T applied to the p columns of V, QR
+        // of the p x n C~) plus one residual
+        const double kC = std::min(n, p);
+        double f = 2.0 * n * m * m - 2.0 * (double)m * m * m / 3.0;
+        f += 4.0 * (double)n * m * p - 2.0 * (double)m * m * p;
+        f += 2.0 * (double)p * n * kC - 2.0 * kC * kC * kC / 3.0;
+        return f + 8.0 * ((double)n * m + (double)n * p);
+    }
     // GRQ flops (QR of n x p, apply to m x n from the right, QR of m x n)
     const double kA = std::min(m, n);
     double f = 2.0 * n * p * p - 2.0 * p * p * p / 3.0;

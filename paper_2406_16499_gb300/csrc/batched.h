@@ -1,4 +1,4 @@
-// batched.h -- persistent batched LSE solver (many small problems, one launch).
+// batched.h -- persistent batched LSE / GLS solver (many small problems, one launch).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,11 +8,15 @@
 namespace mpir {
 
 // One problem of the batch (device table entry; pointers are device memory).
+// kind 0: LSE (A m x n, B p x n, b, d -> x).  kind 1: GLS in the xGGGLM
+// convention with W = A (n x m, lda), V = B (n x p, ldb), d -> x (m), y (p);
+// the fields keep the GLS names m (columns of W), n (rows), p (columns of V).
 struct BInst {
     const double *A, *B, *b, *d;
-    double *x;
-    int m, n, p, lda, ldb, pad;
+    double *x, *y;
+    int m, n, p, lda, ldb, kind;
 };
+enum { BKIND_LSE = 0, BKIND_GLS = 1 };
 
 // Per-problem result written by the kernel.
 struct BResult {
@@ -60,9 +64,11 @@ struct BatchArena {
 int batched_ctas_per_sm(const BConfig &cfg, bool fp64);
 int batched_launch(const BConfig &cfg, bool fp64, const BInst *tab, const int *order, int count, int *next,
                    BResult *res, void *gscr, size_t gstride_words, int grid, const BParams &prm, cudaStream_t s);
-size_t batched_big_words(int m, int n, int p);           // factor words kept in smem or global scratch
-size_t batched_smem_min(int m, int n, int p, bool fp64);  // smem with the factors in global scratch
-size_t batched_smem_full(int m, int n, int p, bool fp64); // smem with everything resident
-double batched_work(int m, int n, int p);                // GRQ + residual flops of one problem
+// Sizes of one problem (kind: BKIND_LSE with (m, n, p) of lse_solve, or
+// BKIND_GLS with (m, n, p) = columns of W, rows, columns of V).
+size_t batched_big_words(int kind, int m, int n, int p);           // factor words kept in smem or global scratch
+size_t batched_smem_min(int kind, int m, int n, int p, bool fp64);  // smem with the factors in global scratch
+size_t batched_smem_full(int kind, int m, int n, int p, bool fp64); // smem with everything resident
+double batched_work(int kind, int m, int n, int p);                // factorization + residual flops
 
 } // namespace mpir

@@ -1,5 +1,5 @@
-// batched_kernel.cuh -- device code of the batched LSE solver: many independent
-// small problems in one persistent launch.
+// batched_kernel.cuh -- device code of the batched LSE / GLS solver: many
+// independent small problems in one persistent launch.
 //
 // Each CTA takes problems from a device work queue (largest first) and runs
 // the whole method on one problem at a time: scaling and down-conversion,
@@ -28,6 +28,7 @@
 namespace mpir {
 
 constexpr int BNB = 32;    // panel width = compact-WY block size
+constexpr int BWC = 256;   // trailing-update columns per pass (W scratch 32 x BWC)
 
 // Threads of one problem ("group"): GT consecutive threads of the CTA, with
 // their own named barrier (id 1 + group index; at most 16 groups).
@@ -103,8 +104,10 @@ __device__ __forceinline__ void sub_vw(T *row, int ld, const T (&v)[BNB], const 
 // A (M x N, ld) = Z T, Z = H_0 ... H_{K-1}; reflector vectors below the
 // diagonal, tau[K]; Tb: ceil(K/32) compact-WY factors (32 x 32, column-major)
 // with H_j0 ... H_j0+nb-1 = I - V Tb V^T.  G: 1024 scratch; Wb: 32 x (N-32)
-// scratch.  (Zero diagonals are checked by the caller on the part it solves
-// with.)
+// scratch (32 x min(N-32, BWC): the trailing update runs over column chunks).
+// K = min(M, N), or kmax when kmax >= 0 is smaller: the columns
+// beyond K then only receive the reflectors (Q^T applied to them).  (Zero
+// diagonals are checked by the caller on the part it solves with.)
 //
 // Panel step k (one CTA barrier per column): every thread forms the larfg
 // scalars of column k from alpha = A(k,k) and the held ||A(k+1:M, k)||^2;
@@ -113,13 +116,13 @@ __device__ __forceinline__ void sub_vw(T *row, int ld, const T (&v)[BNB], const 
 // leaves its new sub-diagonal norm; after the barrier column k is scaled in
 // place while the next step runs on the columns to its right.
 template <int GT, typename T>
-__device__ void cta_geqrf(T *A, int ld, int M, int N, T *tau, T *Tb, T *G, T *Wb, T *stage)
+__device__ void cta_geqrf(T *A, int ld, int M, int N, T *tau, T *Tb, T *G, T *Wb, T *stage, int kmax = -1)
 {
     const int tid = (threadIdx.x & (GT - 1)), lane = tid & 31, warp = tid >> 5;
     constexpr int NW = GT / 32;
     __shared__ T cn2_g[512 / GT][2];
     T *cn2 = cn2_g[threadIdx.x / GT];
-    const int K = min(M, N);
+    const int K = kmax >= 0 ? min(kmax, min(M, N)) : min(M, N);
     for (int j0 = 0; j0 < K; j0 += BNB) {
         const int nb = min(BNB, K - j0);
         // panel access: element (i, j0 + c) at P[(i - roff) + c * pld]; with a
@@ -227,10 +230,12 @@ __device__ void cta_geqrf(T *A, int ld, int M, int N, T *tau, T *Tb, T *G, T *Wb
             for (int c = 0; c < BNB; c++) Tk[lane + 32 * c] = tr[c];
         }
         gsync<GT>();
-        // ---- trailing update C <- (I - V Tk^T V^T) C, C = A(j0:M, cb:N)
-        const int cb = j0 + nb, Nc = N - cb;
+        // ---- trailing update C <- (I - V Tk^T V^T) C, C = A(j0:M, cb:N), in
+        // chunks of BWC columns
+        const int cb0 = j0 + nb;
         const T *Vp = P - roff;      // Vp[i + c * pld] = V(i, c) below the diagonal
-        if (Nc > 0) {
+        for (int cb = cb0; cb < N; cb += BWC) {
+            const int Nc = min(BWC, N - cb);
             // W = V^T C (warp per column, lanes over rows; lane c keeps W(c, j))
             for (int jj = warp; jj < Nc; jj += NW) {
                 const T *cj = A + (size_t)(cb + jj) * ld;
@@ -280,6 +285,7 @@ __device__ void cta_geqrf(T *A, int ld, int M, int N, T *tau, T *Tb, T *G, T *Wb
                     sub_vw<T>(A + i + (size_t)cb * ld, ld, v, Wb, 0, 1, Nc);
                 }
             }
+            gsync<GT>();
         }
         if (stage) {
             gsync<GT>();
@@ -507,7 +513,7 @@ __host__ __device__ inline BPlan bplan(int m, int n, int p)
     P.ldB = odd_ld(max(n, 1));
     P.ldA = odd_ld(max(m, 1));
     P.vec_d = (size_t)2 * (m + n + p) + 64;
-    P.vec_t = (size_t)7 * mx + p + kA + 64 + 1024 + (size_t)32 * max(max(n, p), 1);
+    P.vec_t = (size_t)7 * mx + p + kA + 64 + 1024 + (size_t)32 * min(BWC, max(max(n, p), 1));
     P.fac_small = (size_t)1024 * (ceil_div(p, BNB) + ceil_div(kA, BNB));
     P.fac_big = (size_t)P.ldB * p + (size_t)P.ldA * n;
     P.stage = (size_t)BNB * max(max(m, n), 1);
@@ -521,6 +527,25 @@ __host__ __device__ inline size_t bsmem_need(const BPlan &P, int mode)
 {
     size_t t = P.vec_t + P.fac_small + (mode == 2 ? P.fac_big : (mode == 1 ? P.stage : 0));
     return P.vec_d * 8 + ((t * sizeof(TF) + 15) & ~(size_t)15) + 64;
+}
+
+// GLS (n x m W, n x p V): [Wf Cf] n x (m + p) (ldB = odd_ld(n)) with Q^T V
+// in its last p columns, then Ct = P_p C^T P_n (p x n, ldA = odd_ld(p)).
+__host__ __device__ inline BPlan gplan(int m, int n, int p)
+{
+    BPlan P;
+    const int mx = max(max(m, n), max(p, 1));
+    const int kC = min(n, p);
+    P.ldB = odd_ld(max(n, 1));
+    P.ldA = odd_ld(max(p, 1));
+    P.vec_d = (size_t)2 * (m + n + p) + 64;
+    P.vec_t = (size_t)7 * mx + m + kC + 64 + 1024 + (size_t)32 * min(BWC, max(m + p, max(n, 1)));
+    // the panels' compact-WY factors travel with the big factors (shared
+    // memory, or the global scratch)
+    P.fac_small = 0;
+    P.fac_big = (size_t)P.ldB * (m + p) + (size_t)P.ldA * n + (size_t)1024 * (ceil_div(m, BNB) + ceil_div(kC, BNB));
+    P.stage = (size_t)BNB * max(max(n, p), 1);
+    return P;
 }
 
 // ------------------------------------------------------------ one problem --
@@ -547,7 +572,7 @@ __device__ void solve_one(const BInst &I, BResult *res, unsigned char *smem, siz
     TF *tu = tb0, *tw = tu + mx, *ty = tw + mx, *tq = ty + mx, *tbv = tq + mx, *tt = tbv + mx, *tt2 = tt + mx;
     TF *tauB = tt2 + mx, *tauA = tauB + p, *wbuf = tauA + kA, *G = wbuf + 64;
     TF *Wb = G + 1024;
-    TF *TB = Wb + (size_t)32 * max(max(n, p), 1), *TA = TB + (size_t)1024 * ceil_div(p, BNB);
+    TF *TB = Wb + (size_t)32 * min(BWC, max(max(n, p), 1)), *TA = TB + (size_t)1024 * ceil_div(p, BNB);
     TF *big = TA + (size_t)1024 * ceil_div(kA, BNB);
     TF *stage = nullptr;
     if (!big_smem) {
@@ -767,6 +792,248 @@ __device__ void solve_one(const BInst &I, BResult *res, unsigned char *smem, siz
     gsync<GT>();
 }
 
+// ------------------------------------------------------- one GLS problem --
+// GLS in the xGGGLM convention (W n x m, V n x p, d -> x, y), the method of
+// the single-problem solver in its reversed coordinates (Lemma 4.6, Sec. 2.2,
+// Alg. 3 / Alg. 4):  [W V] = Q [R T~; 0 ...] through the first m columns
+// (QR of W with Q^T V formed by the same trailing updates), C~ = P_p C^T P_n
+// = Z~ T~ (p x n), T~_L = T~(0:L, 0:L) the solved triangle (L = n - m),
+// Paige's start, z0 = Q [0; h], classical IR with FP64 residuals.
+template <int GT, typename TF>
+__device__ void solve_one_gls(const BInst &I, BResult *res, unsigned char *smem, size_t smem_bytes, TF *gscr,
+                              const BParams &prm)
+{
+    const int tid = (threadIdx.x & (GT - 1));
+    const int m = I.m, n = I.n, p = I.p, L = n - m, o = p - n + m, kC = min(n, p);
+    const int ldw = I.lda, ldv = I.ldb;
+    const double *W = I.A, *V = I.B, *d = I.d;
+    __shared__ double redd_g[512 / GT][GT / 32];
+    __shared__ int st_g[512 / GT];
+    double *redd = redd_g[threadIdx.x / GT];
+    int &st = st_g[threadIdx.x / GT];
+    const BPlan P = gplan(m, n, p);
+    const bool big_smem = bsmem_need<TF>(P, 2) <= smem_bytes;
+    const bool use_stage = !big_smem && bsmem_need<TF>(P, 1) <= smem_bytes;
+    double *X = reinterpret_cast<double *>(smem);
+    double *Y = X + m, *Z = Y + p, *F1 = Z + n, *F2 = F1 + p, *F3 = F2 + n;
+    TF *tb0 = reinterpret_cast<TF *>(smem + P.vec_d * 8);
+    const int mx = max(max(m, n), max(p, 1));
+    TF *tu = tb0, *tw = tu + mx, *th = tw + mx, *tg = th + mx, *tt = tg + mx, *tt2 = tt + mx;
+    TF *tauW = tt2 + 2 * mx, *tauC = tauW + m, *wbuf = tauC + kC, *G = wbuf + 64;
+    TF *Wb = G + 1024;
+    TF *big = Wb + (size_t)32 * min(BWC, max(m + p, max(n, 1)));
+    TF *stage = nullptr;
+    if (!big_smem) {
+        if (use_stage) stage = big;
+        big = gscr;
+    }
+    TF *Wf = big, *Ct = big + (size_t)P.ldB * (m + p);
+    TF *TW = Ct + (size_t)P.ldA * n, *TC = TW + (size_t)1024 * ceil_div(m, BNB);
+    const int ldW = P.ldB, ldC = P.ldA;
+    if (tid == 0) st = 0;
+    // ---- scaling (Sec. 6.1) and the norms of the stop test
+    double amW = 0.0, ssW = 0.0, amV = 0.0, ssV = 0.0, sd = 0.0;
+    for (int e = tid; e < n * m; e += GT) {
+        const double a = W[(size_t)(e % n) + (size_t)(e / n) * ldw];
+        amW = fmax(amW, fabs(a));
+        ssW = fma(a, a, ssW);
+    }
+    for (int e = tid; e < n * p; e += GT) {
+        const double a = V[(size_t)(e % n) + (size_t)(e / n) * ldv];
+        amV = fmax(amV, fabs(a));
+        ssV = fma(a, a, ssV);
+    }
+    for (int i = tid; i < n; i += GT) sd = fma(d[i], d[i], sd);
+    amW = bmax<GT>(amW, redd);
+    amV = bmax<GT>(amV, redd);
+    ssW = bsum<GT>(ssW, redd);
+    ssV = bsum<GT>(ssV, redd);
+    const double ndv = sqrt(bsum<GT>(sd, redd));
+    const double fW = sqrt(ssW), fV = sqrt(ssV);
+    if (!isfinite(ssW) || !isfinite(ssV)) {
+        if (tid == 0) { res->status = MPIR_NONFINITE; res->iters = 0; }
+        gsync<GT>();
+        return;
+    }
+    const double sW = prm.scale ? pow2_of(amW) : 1.0, sV = prm.scale ? pow2_of(amV) : 1.0;
+    for (int e = tid; e < n * m; e += GT) {
+        const int r = e % n, c = e / n;
+        Wf[r + (size_t)c * ldW] = (TF)(sW * W[r + (size_t)c * ldw]);
+    }
+    for (int e = tid; e < n * p; e += GT) {
+        const int r = e % n, c = e / n;
+        Wf[r + (size_t)(m + c) * ldW] = (TF)(sV * V[r + (size_t)c * ldv]);
+    }
+    gsync<GT>();
+    // ---- GQR (Lemma 4.6): QR of W with C = Q^T V, then the QR of C~
+    cta_geqrf<GT, TF>(Wf, ldW, n, m + p, tauW, TW, G, Wb, stage, m);
+    for (int e = tid; e < p * n; e += GT) {              // Ct(i, j) = C(n-1-j, p-1-i)
+        const int i = e % p, j = e / p;
+        Ct[i + (size_t)j * ldC] = Wf[(n - 1 - j) + (size_t)(m + p - 1 - i) * ldW];
+    }
+    gsync<GT>();
+    cta_geqrf<GT, TF>(Ct, ldC, p, n, tauC, TC, G, Wb, stage);
+    gsync<GT>();
+    // zero diagonals: R (bit 1), T~_L (bit 2)
+    for (int i = tid; i < m; i += GT) if (Wf[i + (size_t)i * ldW] == TF(0)) atomicOr(&st, 1);
+    for (int i = tid; i < L; i += GT) if (Ct[i + (size_t)i * ldC] == TF(0)) atomicOr(&st, 2);
+    gsync<GT>();
+    if (st) {
+        if (tid == 0) { res->status = (st & 1) ? MPIR_SINGULAR_R : MPIR_SINGULAR_T; res->iters = 0; }
+        gsync<GT>();
+        return;
+    }
+    // ---- Paige's method (Sec. 2.2): c = Q^T (g d)
+    double mxr = 0.0;
+    for (int i = tid; i < n; i += GT) mxr = fmax(mxr, fabs(d[i]));
+    mxr = bmax<GT>(mxr, redd);
+    const double g = sizeof(TF) == 4 ? pow2_of(mxr) : 1.0;
+    for (int i = tid; i < n; i += GT) tu[i] = (TF)(g * d[i]);
+    gsync<GT>();
+    cta_apply_vec<GT, TF>(Wf, ldW, n, m, TW, 1, tu, wbuf);
+    // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (tg[0:L]; tg[L:p] = 0)
+    for (int i = tid; i < p; i += GT) tg[i] = i < L ? tu[m + L - 1 - i] : TF(0);
+    for (int i = tid; i < m; i += GT) tt[i] = TF(0);
+    gsync<GT>();
+    cta_trsv<GT, TF>(Ct, ldC, L, 1, tg, &st, 2);
+    // R x = c1 - T12 s2,  P_m (T12 s2) = T~_12^T s~2
+    if (L > 0) cta_gemv_t<GT, TF>(Ct + (size_t)L * ldC, ldC, L, m, TF(1), tg, tt, false);
+    for (int i = tid; i < m; i += GT) tt2[i] = tu[i] - tt[m - 1 - i];
+    gsync<GT>();
+    cta_trsv<GT, TF>(Wf, ldW, m, 0, tt2, &st, 1);
+    for (int i = tid; i < m; i += GT) X[i] = (double)tt2[i] * sW / g;
+    gsync<GT>();
+    // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
+    cta_apply_vec<GT, TF>(Ct, ldC, p, kC, TC, 0, tg, wbuf);
+    for (int i = tid; i < p; i += GT) Y[i] = (double)tg[p - 1 - i] * sV / g;
+    for (int i = tid; i < n; i += GT) Z[i] = 0.0;
+    gsync<GT>();
+    int it = 0, status = MPIR_OK;
+    double ratio[3] = {0, 0, 0};
+    if (prm.refine != MPIR_DIRECT) {
+        // ---- multipliers (Alg. 4 step 3, z0 = Q [0; h]): w~ = Z~^T (P_p g y / sV)
+        double my = 0.0;
+        for (int i = tid; i < p; i += GT) my = fmax(my, fabs(Y[i] / sV));
+        my = bmax<GT>(my, redd);
+        const double gy = sizeof(TF) == 4 ? pow2_of(my) : 1.0;
+        for (int i = tid; i < p; i += GT) tw[i] = (TF)(gy * Y[p - 1 - i] / sV);
+        gsync<GT>();
+        cta_apply_vec<GT, TF>(Ct, ldC, p, kC, TC, 1, tw, wbuf);
+        for (int i = tid; i < L; i += GT) th[i] = tw[i];
+        for (int i = tid; i < n; i += GT) tt[i] = TF(0);
+        gsync<GT>();
+        cta_trsv<GT, TF>(Ct, ldC, L, 0, th, &st, 2);                          // T~_L h~2 = w~[0:L]
+        for (int i = tid; i < L; i += GT) tt[m + i] = th[L - 1 - i];
+        gsync<GT>();
+        cta_apply_vec<GT, TF>(Wf, ldW, n, m, TW, 0, tt, wbuf);               // z' = Q [0; P_L h~2]
+        for (int i = tid; i < n; i += GT) Z[i] = (double)tt[i] * sV * sV / gy;
+        gsync<GT>();
+        double best = INFINITY;
+        int since = 0;
+        status = MPIR_NOT_CONVERGED;
+        for (it = 0; it < prm.maxit; it++) {
+            // ---- FP64 residual (Alg. 4 step 5): f1 = -y + V^T z, f2 = d - W x - V y, f3 = W^T z
+            const int lane = tid & 31, warp = tid >> 5;
+            double s1 = 0.0, s2 = 0.0, s3 = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
+            for (int i = tid; i < n; i += GT) {
+                double acc = d[i];
+                for (int j = 0; j < m; j++) acc = fma(-W[i + (size_t)j * ldw], X[j], acc);
+                for (int j = 0; j < p; j++) acc = fma(-V[i + (size_t)j * ldv], Y[j], acc);
+                F2[i] = acc;
+                s2 = fma(acc, acc, s2);
+                sz = fma(Z[i], Z[i], sz);
+            }
+            for (int j = warp; j < p; j += GT / 32) {
+                double acc = 0.0;
+                for (int i = lane; i < n; i += 32) acc = fma(V[i + (size_t)j * ldv], Z[i], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) { const double f = acc - Y[j]; F1[j] = f; s1 = fma(f, f, s1); }
+            }
+            for (int j = warp; j < m; j += GT / 32) {
+                double acc = 0.0;
+                for (int i = lane; i < n; i += 32) acc = fma(W[i + (size_t)j * ldw], Z[i], acc);
+                acc = warp_sum(acc);
+                if (lane == 0) { F3[j] = acc; s3 = fma(acc, acc, s3); }
+            }
+            for (int i = tid; i < m; i += GT) sx = fma(X[i], X[i], sx);
+            for (int i = tid; i < p; i += GT) sy = fma(Y[i], Y[i], sy);
+            const double n1 = sqrt(bsum<GT>(s1, redd)), n2 = sqrt(bsum<GT>(s2, redd));
+            const double n3 = sqrt(bsum<GT>(s3, redd)), nx = sqrt(bsum<GT>(sx, redd));
+            const double ny = sqrt(bsum<GT>(sy, redd)), nz = sqrt(bsum<GT>(sz, redd));
+            // ---- stop test (eq. gls-stop) and stagnation
+            const double den[3] = {ny + fV * nz, ndv + fW * nx + fV * ny, fW * nz};
+            const double nrm[3] = {n1, n2, n3};
+            bool ok = true, fin = true;
+            for (int k = 0; k < 3; k++) {
+                ratio[k] = den[k] > 0 ? nrm[k] / den[k] : (nrm[k] > 0 ? INFINITY : 0.0);
+                if (!(nrm[k] <= prm.tol * den[k])) ok = false;
+                if (!isfinite(nrm[k])) fin = false;
+            }
+            if (!fin) { status = MPIR_NONFINITE; break; }
+            if (ok) { status = MPIR_OK; break; }
+            const double eta = fmax(ratio[0], fmax(ratio[1], ratio[2]));
+            if (eta < 0.5 * best) { best = eta; since = 0; }
+            else if (++since >= 3) { status = best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            // ---- correction (Alg. 3, read with T22 g2 = u2 and dz = -Q h)
+            const double gam = sizeof(TF) == 4 ? pow2_of(fmax(n1, fmax(n2 * sV, n3 * sW / sV))) : 1.0;
+            const double c1 = gam, c2 = gam * sV, c3 = gam * sW / sV;
+            for (int i = tid; i < n; i += GT) tu[i] = (TF)(c2 * F2[i]);
+            for (int i = tid; i < p; i += GT) tw[i] = (TF)(c1 * F1[p - 1 - i]);
+            for (int i = tid; i < m; i += GT) th[i] = (TF)(c3 * F3[i]);
+            gsync<GT>();
+            cta_apply_vec<GT, TF>(Wf, ldW, n, m, TW, 1, tu, wbuf);          // step 1: u = Q^T f2
+            cta_apply_vec<GT, TF>(Ct, ldC, p, kC, TC, 1, tw, wbuf);         // step 2: w~ = Z~^T P_p f1
+            cta_trsv<GT, TF>(Wf, ldW, m, 1, th, &st, 1);                     // step 3: R^T h1 = f3
+            for (int i = tid; i < m; i += GT) tt[i] = th[m - 1 - i];         // h~1 = P_m h1
+            for (int i = tid; i < L; i += GT) tg[i] = tu[m + L - 1 - i];     // step 4: T~_L^T g~2 = P_L u2
+            for (int i = tid; i < L; i += GT) tt2[i] = TF(0);
+            gsync<GT>();
+            cta_trsv<GT, TF>(Ct, ldC, L, 1, tg, &st, 2);
+            // step 5: T~_L h~2 = w~2 - g~2 - T~_12 h~1   (th[m:m+L])
+            if (L > 0) cta_gemv_n<GT, TF>(Ct + (size_t)L * ldC, ldC, L, m, TF(1), tt, tt2, false);
+            for (int i = tid; i < L; i += GT) th[m + i] = tw[i] - tg[i] - tt2[i];
+            gsync<GT>();
+            cta_trsv<GT, TF>(Ct, ldC, L, 0, th + m, &st, 2);
+            // step 6: g~1 = w~1 - T~_22 h~1   (tg[L:p])
+            if (o > 0) {
+                for (int i = tid; i < o; i += GT) tg[L + i] = tw[L + i];
+                gsync<GT>();
+                cta_gemv_n<GT, TF>(Ct + L + (size_t)L * ldC, ldC, o, m, TF(-1), tt, tg + L, true);
+            }
+            // step 8: R dx = u1 - P_m (T~_22^T g~1 + T~_12^T g~2)
+            for (int i = tid; i < m; i += GT) tt2[i] = TF(0);
+            gsync<GT>();
+            if (L > 0) cta_gemv_t<GT, TF>(Ct + (size_t)L * ldC, ldC, L, m, TF(1), tg, tt2, false);
+            if (o > 0) cta_gemv_t<GT, TF>(Ct + L + (size_t)L * ldC, ldC, o, m, TF(1), tg + L, tt2, true);
+            for (int i = tid; i < m; i += GT) tt[i] = tu[i] - tt2[m - 1 - i];
+            gsync<GT>();
+            cta_trsv<GT, TF>(Wf, ldW, m, 0, tt, &st, 1);
+            for (int i = tid; i < m; i += GT) X[i] += (double)tt[i] * sW / sV / gam;
+            gsync<GT>();
+            // step 7: dy = P_p Z~ g~ ;  dz = -Q [h1; P_L h~2]
+            cta_apply_vec<GT, TF>(Ct, ldC, p, kC, TC, 0, tg, wbuf);
+            for (int i = tid; i < L; i += GT) tt2[i] = th[m + L - 1 - i];
+            gsync<GT>();
+            for (int i = tid; i < L; i += GT) th[m + i] = tt2[i];
+            for (int i = tid; i < p; i += GT) Y[i] += (double)tg[p - 1 - i] / gam;
+            gsync<GT>();
+            cta_apply_vec<GT, TF>(Wf, ldW, n, m, TW, 0, th, wbuf);
+            for (int i = tid; i < n; i += GT) Z[i] -= (double)th[i] * sV / gam;
+            gsync<GT>();
+        }
+    }
+    // ---- result
+    for (int i = tid; i < m; i += GT) I.x[i] = X[i];
+    for (int i = tid; i < p; i += GT) I.y[i] = Y[i];
+    gsync<GT>();
+    if (tid == 0) {
+        res->status = st ? ((st & 1) ? MPIR_SINGULAR_R : MPIR_SINGULAR_T) : status;
+        res->iters = it;
+        for (int k = 0; k < 3; k++) res->ratio[k] = ratio[k];
+    }
+    gsync<GT>();
+}
+
 // ------------------------------------------------------- persistent kernel --
 // NT threads per CTA in NT / GT groups; each group takes problems from the
 // queue on its own (largest first) and solves them with its share of the
@@ -788,21 +1055,50 @@ k_lse_batched(const BInst *__restrict__ tab, const int *__restrict__ order, int 
         gsync<GT>();
         if (k >= count) break;
         const int idx = order[k];
-        solve_one<GT, TF>(tab[idx], res + idx, mysm, gsmem, my, prm);
+        if (tab[idx].kind == BKIND_GLS)
+            solve_one_gls<GT, TF>(tab[idx], res + idx, mysm, gsmem, my, prm);
+        else
+            solve_one<GT, TF>(tab[idx], res + idx, mysm, gsmem, my, prm);
     }
 }
 
 // ------------------------------------------------------------------ host --
+// The dynamic shared-memory limit of a kernel instantiation is raised once
+// per device to the device's opt-in maximum less the kernel's static shared
+// memory (a launch with less uses less),
+// so host threads launching the same instantiation with different sizes
+// never lower it under one another.
+template <int GT, typename TF>
+static bool batched_smem_limit(size_t smem)
+{
+    auto kern = k_lse_batched<512, GT, TF>;
+    static PerDeviceOnce once;
+    once([&] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) optin = 0;
+        cudaFuncAttributes st{};
+        if (cudaFuncGetAttributes(&st, kern) != cudaSuccess) { cudaGetLastError(); return; }
+        // the opt-in maximum covers static and dynamic shared memory together
+        const int dyn = optin - (int)st.sharedSizeBytes;
+        if (dyn <= 0 || cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+            cudaGetLastError();
+    });
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return smem <= (size_t)fa.maxDynamicSharedSizeBytes;
+}
+
 template <int GT, typename TF>
 static int launch_cfg(const BInst *tab, const int *order, int count, int *next, BResult *res, TF *gscr,
                       size_t gstride, size_t smem, int grid, const BParams &prm, cudaStream_t s)
 {
     constexpr int NT = 512;
     auto kern = k_lse_batched<NT, GT, TF>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return MPIR_UNSUPPORTED;
-    }
+    if (!batched_smem_limit<GT, TF>(smem)) return MPIR_UNSUPPORTED;
     const size_t gsmem = (smem / (NT / GT)) & ~(size_t)15;
     cudaMemsetAsync(next, 0, sizeof(int), s);
     prof_count(K_BATCHED);
@@ -814,10 +1110,7 @@ template <int GT, typename TF>
 static int occupancy_of(size_t smem)
 {
     auto kern = k_lse_batched<512, GT, TF>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
+    if (!batched_smem_limit<GT, TF>(smem)) return 0;
     int per = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 512, smem) != cudaSuccess) {
         cudaGetLastError();

@@ -7,6 +7,10 @@
 //
 // Precision modes
 //   TF32   : one kind::tf32 MMA per K step (inputs truncated to TF32).
+//   BF16   : FP32 tiles (two 32-wide K halves per 64-wide stage) rounded to
+//            bfloat16 (nearest even) in shared memory by the epilogue warps,
+//            written in the same 128-byte-swizzled K-major layout, then four
+//            kind::f16 MMAs (BF16 x BF16 -> FP32) per stage.
 //   TF32X3 : FP32-class accuracy from three TF32 MMAs per K step,
 //            a_hi b_hi + a_hi b_lo + a_lo b_hi, with x = x_hi + x_lo,
 //            x_hi = TF32(x) (round to nearest), x_lo = x - x_hi.
@@ -36,6 +40,7 @@ constexpr int TC_BK = 32;                         // 32 FP32 = one 128-byte swiz
 constexpr int TC_TILE_A = TC_BM * TC_BK * 4;      // 16 KB
 constexpr int TC_TILE_B = TC_BN * TC_BK * 4;      // 16 KB
 constexpr int TC_THREADS = 192;
+constexpr int TC_BK16 = 64;                       // K per BF16 stage: 64 BF16 = one 128-byte swizzle row
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;
 
 // ------------------------------------------------------------------ PTX --
@@ -111,6 +116,55 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N)
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::f16 with BF16 A and B: D = F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
+{
+    asm volatile("{\n\t.reg .pred p;\n\t"
+                 "setp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+                 "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                 : "memory");
+}
+
+// Two floats rounded to nearest-even bfloat16, packed with lo at the lower
+// address.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+    return r;
+}
+
+// One FP32 operand tile pair (K halves 0..31, 32..63, 128 rows, 128-byte
+// swizzle) -> the BF16 tile (128 rows x 64, 128-byte swizzle).  Thread et of
+// the 128 converters handles 16-byte output chunks e = et, et + 128, ...:
+// row r = e / 8, chunk j = e % 8 (BF16 k = 8j .. 8j+7), read from FP32 half
+// j / 4, chunks 2 (j % 4) and 2 (j % 4) + 1.  In a 128-byte-swizzled tile
+// chunk c of row r sits at chunk c ^ (r % 8).
+__device__ __forceinline__ void convert_tile_bf16(const unsigned char *src0, const unsigned char *src1,
+                                                  unsigned char *dst, int et)
+{
+#pragma unroll 2
+    for (int e = et; e < 128 * 8; e += 128) {
+        const int r = e >> 3, j = e & 7, x = r & 7;
+        const unsigned char *src = (j < 4 ? src0 : src1) + r * 128;
+        const int c0 = 2 * (j & 3);
+        const float4 u = *reinterpret_cast<const float4 *>(src + ((c0 ^ x) << 4));
+        const float4 v = *reinterpret_cast<const float4 *>(src + (((c0 + 1) ^ x) << 4));
+        uint4 o;
+        o.x = pack_bf16x2(u.x, u.y);
+        o.y = pack_bf16x2(u.z, u.w);
+        o.z = pack_bf16x2(v.x, v.y);
+        o.w = pack_bf16x2(v.z, v.w);
+        *reinterpret_cast<uint4 *>(dst + r * 128 + ((j ^ x) << 4)) = o;
+    }
+}
+
 __device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc)
 {
     asm volatile("{\n\t.reg .pred p;\n\t"
@@ -171,10 +225,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
           const __grid_constant__ CUtensorMap tmB, const __grid_constant__ CUtensorMap tmB2, TcArgs args)
 {
-    // A_lo / B_lo buffers exist only for TF32X3
-    constexpr int NA = MODE == TCM_TF32X3 ? 2 : 1;
-    constexpr int NBUF = MODE == TCM_TF32X3 ? 2 : 1;
-    constexpr int STAGE_BYTES = NA * TC_TILE_A + NBUF * TC_TILE_B;
+    // A_lo / B_lo buffers exist only for TF32X3; BF16 stages hold two FP32
+    // K halves of A and of B plus the BF16 tiles of A and B
+    constexpr bool BF = MODE == TCM_BF16;
+    constexpr int NA = MODE == TCM_TF32X3 || BF ? 2 : 1;
+    constexpr int NBUF = MODE == TCM_TF32X3 || BF ? 2 : 1;
+    constexpr int STAGE_BYTES = NA * TC_TILE_A + NBUF * TC_TILE_B + (BF ? TC_TILE_A + TC_TILE_B : 0);
+    constexpr int KSTEP = BF ? TC_BK16 : TC_BK;
     constexpr int NCONV = 128;   // converter / epilogue threads
 
     extern __shared__ __align__(1024) unsigned char smem_dyn[];
@@ -218,12 +275,14 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     auto tileA2 = [&](int s) { return smem + (size_t)s * STAGE_BYTES + TC_TILE_A; };
     auto tileB = [&](int s) { return smem + (size_t)s * STAGE_BYTES + NA * TC_TILE_A; };
     auto tileB2 = [&](int s) { return smem + (size_t)s * STAGE_BYTES + NA * TC_TILE_A + TC_TILE_B; };
+    auto tileAb = [&](int s) { return smem + (size_t)s * STAGE_BYTES + NA * TC_TILE_A + NBUF * TC_TILE_B; };
+    auto tileBb = [&](int s) { return tileAb(s) + TC_TILE_A; };
 
     int issued = 0;   // TMA stages issued by the producer (lane 0 of warp 0)
     if (warp == 0) {
         // ------------------------------------------------ TMA producer
         if (lane == 0) {
-            const bool b_two = MODE == TCM_TF32X3 && BSPLIT == 0;
+            const bool b_two = (MODE == TCM_TF32X3 && BSPLIT == 0) || BF;
             const uint32_t bytes = (uint32_t)(NA * TC_TILE_A + (b_two ? 2 : 1) * TC_TILE_B);
             for (int i = 0; i < nk; i++) {
                 const int s = i % STAGES;
@@ -231,12 +290,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (*(volatile int *)&abort_s) break;
                 const uint32_t fb = smem_u32(&bar_full[s]);
                 mbar_expect_tx(fb, bytes);
-                const int kx = (k_begin + i) * TC_BK;
+                const int kx = (k_begin + i) * KSTEP;
                 tma_load_2d(smem_u32(tileA(s)), &tmA, args.a_x0 + kx, args.a_y0 + m_tile * TC_BM, fb);
                 if (MODE == TCM_TF32X3)
                     tma_load_2d(smem_u32(tileA2(s)), &tmA2, args.a_x0 + kx, args.a_y0 + m_tile * TC_BM, fb);
+                if (BF)       // the second K half of A (same map, 32 further along K)
+                    tma_load_2d(smem_u32(tileA2(s)), &tmA, args.a_x0 + kx + TC_BK, args.a_y0 + m_tile * TC_BM, fb);
                 tma_load_2d(smem_u32(tileB(s)), &tmB, args.b_x0 + kx, args.b_y0 + n_tile * TC_BN, fb);
-                if (b_two)
+                if (BF)
+                    tma_load_2d(smem_u32(tileB2(s)), &tmB, args.b_x0 + kx + TC_BK, args.b_y0 + n_tile * TC_BN, fb);
+                else if (b_two)
                     tma_load_2d(smem_u32(tileB2(s)), &tmB2, args.b_x0 + kx, args.b_y0 + n_tile * TC_BN, fb);
                 issued = i + 1;
             }
@@ -244,8 +307,8 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            constexpr uint32_t IDESC = idesc_tf32(TC_BM, TC_BN);
-            const bool wait_ready = MODE == TCM_TF32X3 && BSPLIT == 1;
+            constexpr uint32_t IDESC = BF ? idesc_bf16(TC_BM, TC_BN) : idesc_tf32(TC_BM, TC_BN);
+            const bool wait_ready = (MODE == TCM_TF32X3 && BSPLIT == 1) || BF;
             for (int i = 0; i < nk; i++) {
                 const int s = i % STAGES;
                 const uint32_t par = (i / STAGES) & 1;
@@ -254,6 +317,17 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 tc_fence_after();
                 const uint32_t a0 = smem_u32(tileA(s)), b0 = smem_u32(tileB(s));
                 const uint32_t a1 = smem_u32(tileA2(s)), b1 = smem_u32(tileB2(s));
+                if (BF) {
+                    const uint32_t ab = smem_u32(tileAb(s)), bb = smem_u32(tileBb(s));
+#pragma unroll
+                    for (int ks = 0; ks < TC_BK16 / 16; ks++) {
+                        const uint32_t off = ks * 32;    // 16 BF16 = 32 bytes along K
+                        mma_bf16(tmem, sdesc_sw128(ab + off), sdesc_sw128(bb + off), IDESC,
+                                 (i > 0 || ks > 0) ? 1u : 0u);
+                    }
+                    mma_commit(smem_u32(&bar_empty[s]));
+                    continue;
+                }
 #pragma unroll
                 for (int ks = 0; ks < TC_BK / 8; ks++) {
                     const uint32_t off = ks * 32;    // 8 TF32 = 32 bytes along K
@@ -271,6 +345,16 @@ k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     } else {
         // ------------------------------------------------ B split + epilogue
         const int et = threadIdx.x - 64;              // 0..127
+        if (BF) {
+            for (int i = 0; i < nk; i++) {
+                const int s = i % STAGES;
+                if (!mbar_wait(smem_u32(&bar_full[s]), (i / STAGES) & 1)) { atomicOr(args.err, 4); abort_s = 1; break; }
+                convert_tile_bf16(tileA(s), tileA2(s), tileAb(s), et);
+                convert_tile_bf16(tileB(s), tileB2(s), tileBb(s), et);
+                fence_proxy_async_smem();
+                mbar_arrive(smem_u32(&bar_ready[s]));
+            }
+        }
         if (MODE == TCM_TF32X3 && BSPLIT == 1) {
             for (int i = 0; i < nk; i++) {
                 const int s = i % STAGES;
@@ -388,10 +472,12 @@ template <int MODE, int BSPLIT, int EPI>
 static int launch_tc(const CUtensorMap &A, const CUtensorMap &A2, const CUtensorMap &B, const CUtensorMap &B2,
                      const TcArgs &args, int ntn, int ntm, int nsplit, cudaStream_t s)
 {
-    constexpr int STAGES = MODE == TCM_TF32X3 ? 3 : 5;
-    constexpr int NA = MODE == TCM_TF32X3 ? 2 : 1;
-    constexpr int NBUF = MODE == TCM_TF32X3 ? 2 : 1;
-    const size_t smem = (size_t)STAGES * (NA * TC_TILE_A + NBUF * TC_TILE_B) + 1024;
+    constexpr bool BF = MODE == TCM_BF16;
+    constexpr int STAGES = MODE == TCM_TF32X3 ? 3 : (BF ? 2 : 5);
+    constexpr int NA = MODE == TCM_TF32X3 || BF ? 2 : 1;
+    constexpr int NBUF = MODE == TCM_TF32X3 || BF ? 2 : 1;
+    const size_t smem =
+        (size_t)STAGES * (NA * TC_TILE_A + NBUF * TC_TILE_B + (BF ? TC_TILE_A + TC_TILE_B : 0)) + 1024;
     auto kern = k_gemm_tc<MODE, BSPLIT, EPI, STAGES>;
     static PerDeviceOnce once;
     once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
@@ -410,7 +496,7 @@ int gemm_tc(int mode, int bsplit, int epi, const CUtensorMap &A, const CUtensorM
     TcArgs a;
     a.a_x0 = a_x0; a.a_y0 = a_y0; a.b_x0 = b_x0; a.b_y0 = b_y0;
     a.M = M; a.N = N;
-    a.ksteps = ceil_div(K, TC_BK);
+    a.ksteps = ceil_div(K, mode == TCM_BF16 ? TC_BK16 : TC_BK);
     if (nsplit < 1) nsplit = 1;
     if (nsplit > a.ksteps) nsplit = a.ksteps > 0 ? a.ksteps : 1;
     a.kps = ceil_div(a.ksteps, nsplit);
@@ -422,6 +508,10 @@ int gemm_tc(int mode, int bsplit, int epi, const CUtensorMap &A, const CUtensorM
                           : launch_tc<TCM_TF32X3, 0, TCE_STORE>(A, A2, B, B2, a, ntn, ntm, nsplit, s);
         return bsplit ? launch_tc<TCM_TF32X3, 1, TCE_SUB>(A, A2, B, B2, a, ntn, ntm, nsplit, s)
                       : launch_tc<TCM_TF32X3, 0, TCE_SUB>(A, A2, B, B2, a, ntn, ntm, nsplit, s);
+    }
+    if (mode == TCM_BF16) {
+        if (epi == TCE_STORE) return launch_tc<TCM_BF16, 0, TCE_STORE>(A, A2, B, B2, a, ntn, ntm, nsplit, s);
+        return launch_tc<TCM_BF16, 0, TCE_SUB>(A, A2, B, B2, a, ntn, ntm, nsplit, s);
     }
     if (epi == TCE_STORE) return launch_tc<TCM_TF32, 0, TCE_STORE>(A, A2, B, B2, a, ntn, ntm, nsplit, s);
     return launch_tc<TCM_TF32, 0, TCE_SUB>(A, A2, B, B2, a, ntn, ntm, nsplit, s);

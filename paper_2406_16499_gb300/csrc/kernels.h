@@ -163,18 +163,34 @@ void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s,
 // not finite); out[0] = g, out[1] = 1 / g.  Device only (no host sync).
 void pow2_normalizer(const double *u, int nu, double a1, const double *w, int nw, double a2, double *out,
                      cudaStream_t s);
-// dst[i] += scale * src[rev ? n-1-i : i]   (FP64 destination)
+// dst[i] += scale * g * src[rev ? n-1-i : i]   (FP64 destination; g = *dscale
+// when dscale != NULL, else 1)
 template <typename Ts>
-void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s);
+void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s,
+           const double *dscale = nullptr);
 void vzero(void *dst, size_t bytes, cudaStream_t s);
 
 // Matrix conversion with optional transpose and index reversal:
 //   dst(i, j) = (Td)(scale * src(ri, ci)),  i < rows_d, j < cols_d,
 // transpose = 0: (ri, ci) = (i', j');  transpose = 1: (ri, ci) = (j', i'),
 // where i' = rev_r ? rows_d-1-i : i and j' = rev_c ? cols_d-1-j : j.
+// With rs != NULL every destination row is further multiplied by
+// rs[rs_rev ? rows_d-1-i : i] (a per-row power-of-two scale).
 template <typename Ts, typename Td>
 void mconvert(const Ts *src, int lds, Td *dst, int ldd, int rows_d, int cols_d, int transpose,
-              int rev_r, int rev_c, double scale, cudaStream_t s);
+              int rev_r, int rev_c, double scale, cudaStream_t s, const double *rs = nullptr,
+              int rs_rev = 0);
+
+// v[i] *= D[rev ? n-1-i : i]  (D: device FP64 vector of powers of two).
+template <typename T>
+void vdiag(T *v, const double *D, int n, int rev, cudaStream_t s);
+
+// Per-column power-of-two scaling of the stacked [a1 A; a2 B] (A rows_a x n,
+// B rows_b x n, column-major): D[j] = 2^-e with
+// max(a1 max_i |A(i,j)|, a2 max_i |B(i,j)|) * D[j] in [0.5, 1) (1 for a zero
+// column).  One warp per column.
+void colscale_pow2(const double *A, int lda, int rows_a, const double *B, int ldb, int rows_b, int n, double a1,
+                   double a2, double *D, cudaStream_t s);
 
 // max |A(i,j)| and sum A(i,j)^2 (FP64) into out[0], out[1] (device).
 void absmax_sumsq(const double *A, int lda, int rows, int cols, double *part, double *out,
@@ -187,13 +203,13 @@ struct DualGemvPlan {
     int rows, cols, nrb, ncb;   // row / column blocks of 256
 };
 DualGemvPlan dual_gemv_plan(int rows, int cols);
-void dual_gemv(const double *A, int lda, int rows, int cols, const double *x, const double *r,
-               double *part_Ax, double *part_Atr, cudaStream_t s);
+cudaError_t dual_gemv(const double *A, int lda, int rows, int cols, const double *x, const double *r,
+                      double *part_Ax, double *part_Atr, cudaStream_t s);
 
 // LSE residual from partials: f1 = b - r - sum(Ax), f2 = d - sum(Bx),
 // f3 = -sum(A^T r) + sum(B^T v); norms2[0..5] = squares of ||f1||, ||f2||,
 // ||f3||, ||x||, ||r||, ||v|| (device).
-void lse_resid_finalize(int m, int n, int p, const double *b, const double *d,
+cudaError_t lse_resid_finalize(int m, int n, int p, const double *b, const double *d,
                         const double *x, const double *r, const double *v,
                         const double *pAx, int ncbA, const double *pAtr, int nrbA,
                         const double *pBx, int ncbB, const double *pBtv, int nrbB,
@@ -201,7 +217,7 @@ void lse_resid_finalize(int m, int n, int p, const double *b, const double *d,
                         cudaStream_t s);
 // GLS: f1 = -y + sum(V^T z), f2 = d - sum(Wx) - sum(Vy), f3 = sum(W^T z);
 // norms2 = squares of ||f1||, ||f2||, ||f3||, ||x||, ||y||, ||z||.
-void gls_resid_finalize(int n, int m, int p, const double *d, const double *x,
+cudaError_t gls_resid_finalize(int n, int m, int p, const double *d, const double *x,
                         const double *y, const double *z,
                         const double *pWx, int ncbW, const double *pWtz, int nrbW,
                         const double *pVy, int ncbV, const double *pVtz, int nrbV,

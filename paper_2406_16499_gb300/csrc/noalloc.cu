@@ -10,6 +10,7 @@
 // scratch in a fixed file-scope __device__ array that exists as soon as the
 // library is loaded on a device, and mpir_gls_residual_noalloc uses only
 // that array, the caller's buffers and the caller's stream.
+#include <atomic>
 #include <cstdio>
 
 #include "common.cuh"
@@ -23,23 +24,28 @@ namespace mpir {
 constexpr size_t NOALLOC_SCRATCH_DOUBLES = (size_t)1 << 19;
 static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
 
-// Device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch, looked up once per device (with that
+// device current).  Host threads may race on a device's first call: each
+// looks the same address up and stores it atomically, so every reader sees
+// either nothing (and looks it up itself) or the address.
 constexpr int NOALLOC_MAX_DEVICES = 64;
-static double *g_scratch_ptr[NOALLOC_MAX_DEVICES];
+static std::atomic<double *> g_scratch_ptr[NOALLOC_MAX_DEVICES];
 
 static int noalloc_scratch(double **out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return MPIR_CUDA_ERROR;
-    if (!g_scratch_ptr[dev]) {
+    double *cached = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!cached) {
         void *p = nullptr;
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
             cudaGetLastError();
             return MPIR_CUDA_ERROR;
         }
-        g_scratch_ptr[dev] = (double *)p;
+        cached = (double *)p;
+        g_scratch_ptr[dev].store(cached, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = cached;
     return 0;
 }
 
@@ -72,12 +78,15 @@ extern "C" int mpir_gls_residual_noalloc(int n, int m, int p, const double *W, i
     double *normpart = pVtz + (size_t)pv.nrb * p;
     double *nrm = normpart + 304 * 6;
     // every partial the finalize step reads is written by the gemvs of this
-    // call, so nothing has to be cleared first
-    dual_gemv(W, ldw, n, m, x, z, pWx, pWtz, s);
-    dual_gemv(V, ldv, n, p, y, z, pVy, pVtz, s);
-    gls_resid_finalize(n, m, p, d, x, y, z, pWx, pw.ncb, pWtz, pw.nrb, pVy, pv.ncb, pVtz, pv.nrb, f1, f2, f3,
-                       normpart, nrm, s);
+    // call, so nothing has to be cleared first; each launch's own status is
+    // checked, so an error left pending by the caller's earlier work is not
+    // reported as this call's
+    if (dual_gemv(W, ldw, n, m, x, z, pWx, pWtz, s) != cudaSuccess ||
+        dual_gemv(V, ldv, n, p, y, z, pVy, pVtz, s) != cudaSuccess ||
+        gls_resid_finalize(n, m, p, d, x, y, z, pWx, pw.ncb, pWtz, pw.nrb, pVy, pv.ncb, pVtz, pv.nrb, f1, f2, f3,
+                           normpart, nrm, s) != cudaSuccess)
+        return MPIR_CUDA_ERROR;
     if (norms2 && cudaMemcpyAsync(norms2, nrm, 6 * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return MPIR_CUDA_ERROR;
-    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+    return 0;
 }

@@ -880,15 +880,16 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
     pdl_wait();
     pdl_trigger();
     extern __shared__ float sm[];
+    constexpr int LDX = OUTER_NB + 1;                // odd stride: the transposed stores hit 32 banks
     float *S = sm;                                   // 128 x RW_COLS, column-major
-    float *Xs = sm + RW_COLS * OUTER_NB;             // 128 x 128 column-major (x(i,k) at i + 128 k)
+    float *Xs = sm + RW_COLS * OUTER_NB;             // 128 x 128 (x(i,k) at i + LDX k)
     const int tid = threadIdx.x;
     const int c0 = blockIdx.x * RW_COLS;
     if (Tb) {
         for (int e = tid; e < OUTER_NB * OUTER_NB; e += 256) {
             const int i = e % OUTER_NB, k = e / OUTER_NB;
             const float t = Tb[i + k * OUTER_NB];
-            if (trans) Xs[k + i * OUTER_NB] = t; else Xs[i + k * OUTER_NB] = t;
+            if (trans) Xs[k + i * LDX] = t; else Xs[i + k * LDX] = t;
         }
     }
     for (int e = tid; e < RW_COLS * OUTER_NB; e += 256) {
@@ -914,10 +915,15 @@ k_reduce_w(const float *__restrict__ P, int nsplit, size_t pstride, int ldp, con
         if (c0 + c >= nc) continue;
         float w;
         if (Tb) {
-            float s = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
 #pragma unroll 8
-            for (int k = 0; k < OUTER_NB; k++) s = fmaf(Xs[i + k * OUTER_NB], S[k + c * OUTER_NB], s);
-            w = s;
+            for (int k = 0; k < OUTER_NB; k += 4) {
+                s0 = fmaf(Xs[i + k * LDX], S[k + c * OUTER_NB], s0);
+                s1 = fmaf(Xs[i + (k + 1) * LDX], S[k + 1 + c * OUTER_NB], s1);
+                s2 = fmaf(Xs[i + (k + 2) * LDX], S[k + 2 + c * OUTER_NB], s2);
+                s3 = fmaf(Xs[i + (k + 3) * LDX], S[k + 3 + c * OUTER_NB], s3);
+            }
+            w = (s0 + s1) + (s2 + s3);
         } else {
             w = S[i + c * OUTER_NB];
         }
@@ -934,13 +940,13 @@ static void reduce_w(const float *P, int nsplit, size_t pstride, const float *Tb
                      float *Wl, int ldw, int split, cudaStream_t s)
 {
     if (nc >= 16 * 64) {
-        const size_t smem = (size_t)(16 + OUTER_NB) * OUTER_NB * 4;
+        const size_t smem = ((size_t)16 * OUTER_NB + (size_t)(OUTER_NB + 1) * OUTER_NB) * 4;
         static PerDeviceOnce once;
         once([&] { cudaFuncSetAttribute(k_reduce_w<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
         pdl_launch(k_reduce_w<16>, dim3(ceil_div(nc, 16)), dim3(256), smem, s, P, nsplit, pstride, (int)OUTER_NB, Tb, trans,
                    nc, Wh, Wl, ldw, split);
     } else {
-        const size_t smem = (size_t)(4 + OUTER_NB) * OUTER_NB * 4;
+        const size_t smem = ((size_t)4 * OUTER_NB + (size_t)(OUTER_NB + 1) * OUTER_NB) * 4;
         static PerDeviceOnce once;
         once([&] { cudaFuncSetAttribute(k_reduce_w<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); });
         pdl_launch(k_reduce_w<4>, dim3(ceil_div(nc, 4)), dim3(256), smem, s, P, nsplit, pstride, (int)OUTER_NB, Tb, trans,
@@ -1507,6 +1513,7 @@ struct OuterWs {
     size_t pcap;
 };
 constexpr int GSPLIT = 24;               // split-K of the outer block's Gram matrix
+constexpr int SPLIT_MIN_K = 8;           // K steps (of 32) per split of V^T C, at least
 
 static constexpr int PSPLIT_CAP = 320;   // (column tiles x K splits) of W = V^T C
 
@@ -1545,7 +1552,10 @@ size_t geqrf_ws_bytes(int M, int N)
 // two block-parity copies for the critical path + one for the wide updates
 size_t geqrf_la_ws_bytes(int M, int N) { return 3 * geqrf_ws_bytes(M, N); }
 
-static int tc_mode(GemmPrec p) { return p == GemmPrec::FP32 ? TCM_TF32X3 : TCM_TF32; }
+static int tc_mode(GemmPrec p)
+{
+    return p == GemmPrec::FP32 ? TCM_TF32X3 : (p == GemmPrec::BF16 ? TCM_BF16 : TCM_TF32);
+}
 
 // Prepares V (and splits) for the outer block whose panel sits at X (ldx),
 // height L, nr reflectors.
@@ -1578,6 +1588,10 @@ static int outer_apply_p1(OuterWs &w, int L, float *C, int ldc, int Nc, int mode
     const int ksteps = ceil_div(L, 32);
     int nsplit = ceil_div(2 * 152, ntn);
     if (nsplit > PSPLIT_CAP / ntn) nsplit = PSPLIT_CAP / ntn;
+    // every split runs at least SPLIT_MIN_K K steps: shorter ones spend
+    // their time in pipeline fill and in writing partials the reduction
+    // then has to read back
+    if (nsplit > ksteps / SPLIT_MIN_K) nsplit = ksteps / SPLIT_MIN_K;
     if (nsplit > ksteps) nsplit = ksteps;
     if (nsplit < 1) nsplit = 1;
     if ((size_t)nsplit * OUTER_NB * ntn * OUTER_NB > w.pcap) nsplit = 1;

@@ -78,13 +78,13 @@ k_dual_gemv(const double *__restrict__ A, int lda, int rows, int cols, const dou
     }
 }
 
-void dual_gemv(const double *A, int lda, int rows, int cols, const double *x, const double *r,
-               double *part_Ax, double *part_Atr, cudaStream_t s)
+cudaError_t dual_gemv(const double *A, int lda, int rows, int cols, const double *x, const double *r,
+                      double *part_Ax, double *part_Atr, cudaStream_t s)
 {
-    if (rows <= 0 || cols <= 0) return;
+    if (rows <= 0 || cols <= 0) return cudaSuccess;
     dim3 grid(ceil_div(rows, RB), ceil_div(cols, CB));
     ProfScope ps(K_DUAL_GEMV, s);
-    pdl_launch(k_dual_gemv, grid, dim3(256), 0, s, A, lda, rows, cols, x, r, part_Ax, part_Atr);
+    return pdl_launch(k_dual_gemv, grid, dim3(256), 0, s, A, lda, rows, cols, x, r, part_Ax, part_Atr);
 }
 
 // ------------------------------------------------------------------ finalize --
@@ -176,7 +176,7 @@ static int finalize_blocks(int total)
     return nb < 1 ? 1 : nb;
 }
 
-void lse_resid_finalize(int m, int n, int p, const double *b, const double *d, const double *x,
+cudaError_t lse_resid_finalize(int m, int n, int p, const double *b, const double *d, const double *x,
                         const double *r, const double *v, const double *pAx, int ncbA, const double *pAtr,
                         int nrbA, const double *pBx, int ncbB, const double *pBtv, int nrbB, double *f1,
                         double *f2, double *f3, double *normpart, double *norms2, cudaStream_t s)
@@ -184,12 +184,13 @@ void lse_resid_finalize(int m, int n, int p, const double *b, const double *d, c
     const int total = m + p + n + n + m + p;
     const int nb = finalize_blocks(total);
     ProfScope ps(K_FINALIZE, s);
-    pdl_launch(k_resid_finalize<0>, dim3(nb), dim3(256), 0, s, m, p, n, n, m, p, b, d, x, r, v, pAx, ncbA, pAtr, nrbA, pBx, ncbB,
-                                           pBtv, nrbB, f1, f2, f3, normpart);
-    pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
+    cudaError_t e = pdl_launch(k_resid_finalize<0>, dim3(nb), dim3(256), 0, s, m, p, n, n, m, p, b, d, x, r, v, pAx,
+                               ncbA, pAtr, nrbA, pBx, ncbB, pBtv, nrbB, f1, f2, f3, normpart);
+    if (e != cudaSuccess) return e;
+    return pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
 }
 
-void gls_resid_finalize(int n, int m, int p, const double *d, const double *x, const double *y,
+cudaError_t gls_resid_finalize(int n, int m, int p, const double *d, const double *x, const double *y,
                         const double *z, const double *pWx, int ncbW, const double *pWtz, int nrbW,
                         const double *pVy, int ncbV, const double *pVtz, int nrbV, double *f1, double *f2,
                         double *f3, double *normpart, double *norms2, cudaStream_t s)
@@ -197,9 +198,10 @@ void gls_resid_finalize(int n, int m, int p, const double *d, const double *x, c
     const int total = p + n + m + m + p + n;
     const int nb = finalize_blocks(total);
     ProfScope ps(K_FINALIZE, s);
-    pdl_launch(k_resid_finalize<1>, dim3(nb), dim3(256), 0, s, p, n, m, m, p, n, d, nullptr, x, y, z, pWx, ncbW, pWtz, nrbW, pVy,
-                                           ncbV, pVtz, nrbV, f1, f2, f3, normpart);
-    pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
+    cudaError_t e = pdl_launch(k_resid_finalize<1>, dim3(nb), dim3(256), 0, s, p, n, m, m, p, n, d, nullptr, x, y, z,
+                               pWx, ncbW, pWtz, nrbW, pVy, ncbV, pVtz, nrbV, f1, f2, f3, normpart);
+    if (e != cudaSuccess) return e;
+    return pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
 }
 
 } // namespace mpir

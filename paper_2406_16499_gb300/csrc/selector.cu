@@ -588,14 +588,16 @@ __device__ __forceinline__ float bf16_rne(float x)
 }
 
 // Warp per sample: forward with bfloat16 weights and FP32 accumulation; with
-// labels also the output deltas of the mean cross-entropy and the hidden
-// deltas, stored per sample for the gradient kernel.
+// labels y (or target distributions q, count x 6) also the output deltas of
+// the mean cross-entropy and the hidden deltas, stored per sample for the
+// gradient kernel.
 // acts (per sample, 262 floats): x[16] h1[64] h2[64] d1[64] d2[64] d3[6]
 constexpr int ACT = 16 + 64 + 64 + 64 + 64 + 6;
 
 __global__ void __launch_bounds__(MLP_THREADS)
 k_mlp_sample(const float *__restrict__ P, const float *__restrict__ X, int count, const int *__restrict__ y,
-             float *__restrict__ prob, float *__restrict__ acts, float *__restrict__ loss)
+             const float *__restrict__ q, float *__restrict__ prob, float *__restrict__ acts,
+             float *__restrict__ loss)
 {
     __shared__ float w[MLP_PARAMS];
     for (int e = threadIdx.x; e < MLP_PARAMS; e += MLP_THREADS) {
@@ -649,11 +651,14 @@ k_mlp_sample(const float *__restrict__ P, const float *__restrict__ X, int count
             for (int c = 0; c < NCLASS; c++) if (c == lane) v = pr[c];
             prob[(size_t)smp * NCLASS + lane] = v;
         }
-        if (!y) continue;
-        const int lab = y[smp];
+        if (!y && !q) continue;
+        const int lab = y ? y[smp] : -1;
+        float tq[NCLASS];
+#pragma unroll
+        for (int c = 0; c < NCLASS; c++) tq[c] = q ? q[(size_t)smp * NCLASS + c] : (c == lab ? 1.f : 0.f);
         float d3[NCLASS];
 #pragma unroll
-        for (int c = 0; c < NCLASS; c++) d3[c] = (pr[c] - (c == lab ? 1.f : 0.f)) / (float)count;
+        for (int c = 0; c < NCLASS; c++) d3[c] = (pr[c] - tq[c]) / (float)count;
         float d2[2], d1[2];
 #pragma unroll
         for (int q = 0; q < 2; q++) {
@@ -690,10 +695,11 @@ k_mlp_sample(const float *__restrict__ P, const float *__restrict__ X, int count
             act[272 + lane] = v;
         }
         if (lane == 0 && loss) {
-            float pl = 0.f;
+            float l = 0.f;
 #pragma unroll
-            for (int c = 0; c < NCLASS; c++) if (c == lab) pl = pr[c];
-            loss[smp] = -logf(fmaxf(pl, 1e-30f));
+            for (int c = 0; c < NCLASS; c++)
+                if (tq[c] > 0.f) l = fmaf(-tq[c], logf(fmaxf(pr[c], 1e-30f)), l);
+            loss[smp] = l;
         }
     }
 }
@@ -753,20 +759,20 @@ int mlp_forward(const float *P, const float *X, int count, float *prob, cudaStre
     if (count <= 0) return 0;
     const int grid = std::min(ceil_div(count, MLP_THREADS / 32), 1216);
     ProfScope ps(K_SELECTOR, s);
-    k_mlp_sample<<<grid, MLP_THREADS, 0, s>>>(P, X, count, nullptr, prob, nullptr, nullptr);
+    k_mlp_sample<<<grid, MLP_THREADS, 0, s>>>(P, X, count, nullptr, nullptr, prob, nullptr, nullptr);
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
-int mlp_train_step(float *P, float *M, float *Vv, int t, float lr, const float *X, const int *y, int count,
-                   float *ws, float *grad_out, float *loss_out, cudaStream_t s)
+int mlp_train_step(float *P, float *M, float *Vv, int t, float lr, const float *X, const int *y, const float *q,
+                   int count, float *ws, float *grad_out, float *loss_out, cudaStream_t s)
 {
-    if (count <= 0 || t < 1) return MPIR_UNSUPPORTED;
+    if (count <= 0 || t < 1 || (!y && !q)) return MPIR_UNSUPPORTED;
     float *acts = ws, *lossv = acts + (size_t)count * ACT, *grad = lossv + count;
     if (grad_out) grad = grad_out;
     const int grid = std::min(ceil_div(count, MLP_THREADS / 32), 1216);
     {
         ProfScope ps(K_SELECTOR, s);
-        k_mlp_sample<<<grid, MLP_THREADS, 0, s>>>(P, X, count, y, nullptr, acts, lossv);
+        k_mlp_sample<<<grid, MLP_THREADS, 0, s>>>(P, X, count, y, q, nullptr, acts, lossv);
     }
     {
         ProfScope ps(K_SELECTOR, s);

@@ -66,6 +66,18 @@ void prof_begin(int kind, cudaStream_t s)
 
 void prof_count(int kind) { g_launches[kind].fetch_add(1, std::memory_order_relaxed); }
 
+// Launch counts of the library's own kernels replayed from a captured graph:
+// the capture counted them once; every replay adds them again.
+static void prof_add(const long long *per_kind, long long times)
+{
+    for (int k = 0; k < K_NKINDS; k++)
+        if (per_kind[k]) g_launches[k].fetch_add(per_kind[k] * times, std::memory_order_relaxed);
+}
+static void prof_snapshot(long long *out)
+{
+    for (int k = 0; k < K_NKINDS; k++) out[k] = g_launches[k].load(std::memory_order_relaxed);
+}
+
 void prof_end(int kind, cudaStream_t s)
 {
     if (!g_prof || !g_open) return;
@@ -124,6 +136,20 @@ struct Carver {
     size_t used() const { return (size_t)((off + 255) & ~(uintptr_t)255); }
 };
 
+// Device-side state of the classical refinement loop (doubles): the loop's
+// control kernel reads the squared residual norms, applies the stop test and
+// the stagnation rule, and leaves the power-of-two scales of the next
+// correction for the correction's kernels.
+enum {
+    IRD_BEST = 0, IRD_SINCE = 1, IRD_IT = 2, IRD_STATUS = 3, IRD_RATIO = 4,   // ratio: 3 words
+    IRD_C = 8,        // c1, c2, c3: scales of the correction's right-hand side blocks
+    IRD_I = 11,       // i1, i2, i3: scales of the correction's outputs
+    IRD_S1 = 14, IRD_S2 = 15, IRD_F1 = 16, IRD_F2 = 17,   // sA, sB (sW, sV); ||A||_F, ||B||_F
+    IRD_N1 = 18,      // absmax, sum of squares of b (LSE) / d (GLS)
+    IRD_N2 = 20,      // absmax, sum of squares of d (LSE)
+    IRD_WORDS = 24
+};
+
 template <typename T> struct LseWs {
     int m, n, p, q, kA;
     int ldBt, ldX, ldAt;                 // padded to 32 (TMA rows of 128 bytes)
@@ -135,6 +161,8 @@ template <typename T> struct LseWs {
     void *gws2;                          // side-stream scratch of the aggregated factors
     T *tu, *tw, *ty, *tq, *tb, *tt, *tt2;
     double *f1, *f2, *f3, *r, *v, *pAx, *pAtr, *pBx, *pBtv, *normpart, *norms2, *scal, *part;
+    double *D;                           // column scaling (n), BF16 / TF32 factors
+    double *ird;                         // state of the device-side refinement loop (IRD_WORDS)
     DualGemvPlan pa, pb;
 };
 
@@ -149,6 +177,7 @@ template <typename T> struct GlsWs {
     void *gws2;                          // side-stream scratch of the aggregated factors
     T *tu, *tw, *th, *tg, *tt, *tt2;
     double *f1, *f2, *f3, *z, *pWx, *pWtz, *pVy, *pVtz, *normpart, *norms2, *scal, *part;
+    double *ird;                         // state of the device-side refinement loop (IRD_WORDS)
     DualGemvPlan pw, pv;
 };
 
@@ -197,6 +226,8 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
     w.norms2 = c.take<double>(8);
     w.scal = c.take<double>(16);
     w.part = c.take<double>(4096);
+    w.D = c.take<double>(std::max(n, 1));
+    w.ird = c.take<double>(IRD_WORDS);
     if (bytes) *bytes = c.used();
     return w;
 }
@@ -246,6 +277,7 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
     w.norms2 = c.take<double>(8);
     w.scal = c.take<double>(16);
     w.part = c.take<double>(4096);
+    w.ird = c.take<double>(IRD_WORDS);
     if (bytes) *bytes = c.used();
     return w;
 }
@@ -257,6 +289,7 @@ struct FactorState {
     int m = 0, n = 0, p = 0;            // LSE (m, n, p) or GLS (n, m, p) as in the API
     double s1 = 1, s2 = 1;              // LSE: sA, sB ; GLS: sW, sV
     double fro1 = 0, fro2 = 0;          // ||A||_F, ||B||_F  /  ||W||_F, ||V||_F
+    bool colscale = false;              // LSE factors of (sA A D, sB B D), x = D y
 };
 
 } // namespace
@@ -278,6 +311,12 @@ struct mpir_ctx {
     size_t rws_bytes = 0;
     BatchArena ba;               // batched solves: tables, results, tuned shapes, graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    // device-side classical refinement loop: the captured graph (a CUDA-graph
+    // while loop) of the last shape / buffer set, and whether capture works
+    cudaGraphExec_t irg = nullptr;
+    unsigned long long irg_key = 0;
+    bool irg_off = false;
+    long long irg_pre[K_NKINDS] = {}, irg_body[K_NKINDS] = {};   // launches per part of the graph
     cudaStream_t side = nullptr;         // aggregated compact-WY factors, built beside the factorization
     cudaEvent_t side_fork = nullptr, side_join = nullptr;
     cudaStream_t crit = nullptr;         // high-priority stream of the factorization's critical path
@@ -572,7 +611,10 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     // same trailing updates: [W V] factored through its first m columns
     mconvert<double, T>(W, ldw, w.Wf, w.ldW, n, m, 0, 0, 0, sW, s);
     mconvert<double, T>(V, ldv, w.Cf, w.ldC, n, p, 0, 0, 0, sV, s);
-    RC(geqrf<T>(w.Wf, w.ldW, n, m + p, w.tauW, w.TwW, w.Tw128W, gp, w.gws, h->sc.err, s,
+    // as for LSE: the QR of W and the application of its Q to V stay
+    // FP32-class; the dominant RQ of Q^T V runs at the class's precision
+    const GemmPrec gp1 = gp == GemmPrec::FP64 ? gp : GemmPrec::FP32;
+    RC(geqrf<T>(w.Wf, w.ldW, n, m + p, w.tauW, w.TwW, w.Tw128W, gp1, w.gws, h->sc.err, s,
                 tfjob(h, w.TfW, w.ldtW, w.gws2), m));
     // RQ of C as QR of C~ = P_p C^T P_n
     mconvert<T, T>(w.Cf, w.ldC, w.Ct, w.ldCt, p, n, 1, 1, 1, 1.0, s);
@@ -640,22 +682,27 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
 // (dy, dz, dx).  gamma normalizes the right-hand side.
 template <typename T>
 int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const double *f3, double gamma,
-                        double *dy, double *dz, double *dx)
+                        double *dy, double *dz, double *dx, const double *dsc = nullptr)
 {
     const FactorState &fs = h->fs;
     GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
     const int n = w.n, m = w.m, p = w.p, L = w.L, o = w.o;
     const double sW = fs.s1, sV = fs.s2;
-    const double c1 = gamma, c2 = gamma * sV, c3 = gamma * sW / sV;
+    // host scales, or the device scalars (c1, c2, c3, i1, i2, i3) of the
+    // device-side loop: i1 for dy, i2 for dz, i3 for dx
+    const double c1 = dsc ? 1.0 : gamma, c2 = dsc ? 1.0 : gamma * sV, c3 = dsc ? 1.0 : gamma * sW / sV;
+    const double i1 = dsc ? 1.0 : 1.0 / gamma, i2 = dsc ? 1.0 : -sV / gamma, i3 = dsc ? 1.0 : sW / sV / gamma;
+    const double *d1 = dsc, *d2 = dsc ? dsc + 1 : nullptr, *d3 = dsc ? dsc + 2 : nullptr;
+    const double *e1 = dsc ? dsc + 3 : nullptr, *e2 = dsc ? dsc + 4 : nullptr, *e3 = dsc ? dsc + 5 : nullptr;
     cudaStream_t s = h->stream;
     // step 1: u = Q^T f2'
-    vcopy<double, T>(f2, w.tu, n, c2, 0, s);
+    vcopy<double, T>(f2, w.tu, n, c2, 0, s, d2);
     RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 1, w.tu, h->sc, s));
     // step 2: w~ = Z~^T (P_p f1') = P_p (Z f1')
-    vcopy<double, T>(f1, w.tw, p, c1, 1, s);
+    vcopy<double, T>(f1, w.tw, p, c1, 1, s, d1);
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // step 3: R^T h1 = f3'   (th[0:m] = h1)
-    vcopy<double, T>(f3, w.th, m, c3, 0, s);
+    vcopy<double, T>(f3, w.th, m, c3, 0, s, d3);
     RC(tsolve<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s, w.DinvW));
     // h~1 = P_m h1 (tt)
     vcomb<T>(w.tt, m, w.th, 1, T(1), nullptr, 0, T(0), s);
@@ -678,15 +725,15 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     if (o > 0) RC(gemv<T>(w.Ct + idx2(L, L, w.ldCt), w.ldCt, o, m, 1, T(1), w.tg + L, T(1), w.tt2, 1, 0, s));
     vcomb<T>(w.tt, m, w.tu, 0, T(1), w.tt2, 1, T(-1), s);
     RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s, w.DinvW));
-    vaxpy<T>(w.tt, dx, m, sW / sV / gamma, 0, s);
+    vaxpy<T>(w.tt, dx, m, i3, 0, s, e3);
     // step 7: dy = Z^T g = P_p Z~ g~
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
-    vaxpy<T>(w.tg, dy, p, 1.0 / gamma, 1, s);
+    vaxpy<T>(w.tg, dy, p, i1, 1, s, e1);
     //         dz = -Q h,  h = [h1; P_L h~2]
     vcomb<T>(w.tt2, L, w.th + m, 1, T(1), nullptr, 0, T(0), s);
     cudaMemcpyAsync(w.th + m, w.tt2, sizeof(T) * L, cudaMemcpyDeviceToDevice, s);
     RC(vapply<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 0, w.th, h->sc, s));
-    vaxpy<T>(w.th, dz, n, -sV / gamma, 0, s);
+    vaxpy<T>(w.th, dz, n, i2, 0, s, e2);
     return cuda_check(h, "gls_correction");
 }
 
@@ -704,6 +751,195 @@ void gls_residual_dev(mpir_ctx *h, GlsWs<T> &w, const double *W, int ldw, const 
 }
 
 double dnorm_host(mpir_ctx *h, const double *dvec, int n, double *scratch);
+
+// ----------------------------------------------- device-side refinement loop --
+// The classical loop (Alg. 2 / Alg. 4) without a host decision per step: a
+// one-thread control kernel after each residual applies eq. lse-stop /
+// gls-stop and the stagnation rule to the squared norms on the device,
+// records the step count, status and ratios, leaves the power-of-two scales
+// of the next correction (gamma normalizes the scaled right-hand side) and
+// sets the condition of a CUDA-graph while node: the graph is
+//     reset, ||b||, ||d||, residual, control; while (cond) { correction,
+//     residual, control }
+// and the host reads the final state once.
+__global__ void k_ir_reset(double *__restrict__ ird)
+{
+    if (threadIdx.x != 0) return;
+    ird[IRD_BEST] = INFINITY;
+    ird[IRD_SINCE] = 0.0;
+    ird[IRD_IT] = 0.0;
+    ird[IRD_STATUS] = -1.0;
+    for (int k = 0; k < 4; k++) ird[IRD_N1 + k] = 0.0;
+}
+
+__device__ __forceinline__ double ir_pow2(double v)
+{   // 2^-e with v 2^-e in [0.5, 1); 1 for 0 or non-finite v
+    if (!(v > 0.0) || !isfinite(v)) return 1.0;
+    return ldexp(1.0, -(ilogb(v) + 1));
+}
+
+// kind 0: LSE, norms2 = squares of ||f1||, ||f2||, ||f3||, ||x||, ||r||, ||v||;
+// kind 1: GLS, ||f1||, ||f2||, ||f3||, ||x||, ||y||, ||z||.
+__global__ void k_ir_control(const double *__restrict__ norms2, double *__restrict__ ird, int kind, double tol,
+                             int maxit, cudaGraphConditionalHandle hc, int use_hc)
+{
+    if (threadIdx.x != 0) return;
+    double nr[6];
+    for (int k = 0; k < 6; k++) nr[k] = sqrt(norms2[k]);
+    const double s1 = ird[IRD_S1], s2 = ird[IRD_S2], f1 = ird[IRD_F1], f2 = ird[IRD_F2];
+    double den[3];
+    if (kind == 0) {
+        const double nb = sqrt(ird[IRD_N1 + 1]), nd = sqrt(ird[IRD_N2 + 1]);
+        den[0] = nb + nr[4] + f1 * nr[3];
+        den[1] = nd + f2 * nr[3];
+        den[2] = f1 * nr[4] + f2 * nr[5];
+    } else {
+        const double nd = sqrt(ird[IRD_N1 + 1]);
+        den[0] = nr[4] + f2 * nr[5];
+        den[1] = nd + f1 * nr[3] + f2 * nr[4];
+        den[2] = f1 * nr[5];
+    }
+    bool ok = true, fin = true;
+    for (int k = 0; k < 3; k++) {
+        const double rt = den[k] > 0 ? nr[k] / den[k] : (nr[k] > 0 ? INFINITY : 0.0);
+        ird[IRD_RATIO + k] = rt;
+        if (!(nr[k] <= tol * den[k])) ok = false;
+        if (!isfinite(nr[k])) fin = false;
+    }
+    const int it = (int)ird[IRD_IT];
+    int status = -1;
+    if (!fin) status = MPIR_NONFINITE;
+    else if (ok) status = MPIR_OK;
+    else {
+        const double eta = fmax(ird[IRD_RATIO], fmax(ird[IRD_RATIO + 1], ird[IRD_RATIO + 2]));
+        double best = ird[IRD_BEST];
+        int since = (int)ird[IRD_SINCE];
+        if (eta < 0.5 * best) { best = eta; since = 0; }
+        else if (++since >= 3) status = best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED;
+        ird[IRD_BEST] = best;
+        ird[IRD_SINCE] = since;
+        if (status < 0 && it >= maxit) status = MPIR_NOT_CONVERGED;
+    }
+    ird[IRD_STATUS] = status;
+    if (status < 0) {
+        double g;
+        if (kind == 0) {       // scaled system (f1, sB/sA f2, sA f3)
+            g = ir_pow2(fmax(nr[0], fmax(nr[1] * s2 / s1, nr[2] * s1)));
+            ird[IRD_C] = g; ird[IRD_C + 1] = g * s2 / s1; ird[IRD_C + 2] = g * s1;
+            ird[IRD_I] = 1.0 / g; ird[IRD_I + 1] = s2 / s1 / g; ird[IRD_I + 2] = s1 / g;
+        } else {               // scaled system (f1, sV f2, sW/sV f3)
+            g = ir_pow2(fmax(nr[0], fmax(nr[1] * s2, nr[2] * s1 / s2)));
+            ird[IRD_C] = g; ird[IRD_C + 1] = g * s2; ird[IRD_C + 2] = g * s1 / s2;
+            ird[IRD_I] = 1.0 / g; ird[IRD_I + 1] = -s2 / g; ird[IRD_I + 2] = s1 / s2 / g;
+        }
+        ird[IRD_IT] = it + 1;
+    }
+    if (use_hc) cudaGraphSetConditional(hc, status < 0 ? 1u : 0u);
+}
+
+static unsigned long long ir_mix(unsigned long long h, unsigned long long v)
+{
+    h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+    return h;
+}
+
+// Runs the device-side loop: (re)captures the graph when the key changes,
+// stages the per-solve scalars (s1, s2, ||.||_F of both matrices), launches
+// on the handle's stream and reads the final state back (the one host
+// synchronization of the loop).  pre(hc) / body(hc) enqueue the two parts on
+// h->stream (the capture stream while capturing).  Returns 0, or a positive
+// code when the graph could not be built (the caller then runs the host loop).
+template <typename Pre, typename Body>
+static int ir_graph_run(mpir_ctx *h, double *ird, unsigned long long key, Pre pre, Body body, int *it_out,
+                        int *st_out, double ratio[3])
+{
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return 1;
+    }
+    if (!h->irg || h->irg_key != key) {
+        if (h->irg) { cudaGraphExecDestroy(h->irg); h->irg = nullptr; }
+        cudaStream_t user = h->stream, cs = h->cap_stream;
+        cudaGraph_t g = nullptr;
+        cudaGraphConditionalHandle hc{};
+        bool okc = cudaGraphCreate(&g, 0) == cudaSuccess && cudaGraphConditionalHandleCreate(&hc, g, 0, 0) == cudaSuccess;
+        cudaGraphNodeParams cp{};
+        if (okc) okc = cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                       cudaSuccess;
+        long long c0[K_NKINDS], c1[K_NKINDS], c2[K_NKINDS];
+        prof_snapshot(c0);
+        std::copy(c0, c0 + K_NKINDS, c1);
+        std::copy(c0, c0 + K_NKINDS, c2);
+        if (okc) {
+            h->stream = cs;
+            const int rc = pre(hc);
+            prof_snapshot(c1);
+            cudaStreamCaptureStatus cst;
+            cudaGraph_t gc = nullptr;
+            const cudaGraphNode_t *deps = nullptr;
+            const cudaGraphEdgeData *edata = nullptr;
+            size_t nd = 0;
+            okc = rc == 0 && cudaStreamGetCaptureInfo(cs, &cst, nullptr, &gc, &deps, &edata, &nd) == cudaSuccess &&
+                  cst == cudaStreamCaptureStatusActive;
+            cudaGraphNode_t node = nullptr;
+            if (okc) {
+                cp.type = cudaGraphNodeTypeConditional;
+                cp.conditional.handle = hc;
+                cp.conditional.type = cudaGraphCondTypeWhile;
+                cp.conditional.size = 1;
+                okc = cudaGraphAddNode(&node, gc, deps, edata, nd, &cp) == cudaSuccess &&
+                      cudaStreamUpdateCaptureDependencies(cs, &node, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                          cudaSuccess;
+            }
+            cudaGraph_t gend = nullptr;
+            if (cudaStreamEndCapture(cs, &gend) != cudaSuccess) okc = false;
+            if (okc) {
+                cudaGraph_t bodyg = cp.conditional.phGraph_out[0];
+                okc = cudaStreamBeginCaptureToGraph(cs, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                      cudaSuccess;
+                if (okc) {
+                    const int rb = body(hc);
+                    prof_snapshot(c2);
+                    cudaGraph_t gb = nullptr;
+                    if (cudaStreamEndCapture(cs, &gb) != cudaSuccess || rb != 0) okc = false;
+                }
+            }
+            h->stream = user;
+        }
+        if (okc) okc = cudaGraphInstantiate(&h->irg, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!okc) {
+            h->irg = nullptr;
+            cudaGetLastError();
+            return 1;
+        }
+        h->irg_key = key;
+        for (int k = 0; k < K_NKINDS; k++) {
+            h->irg_pre[k] = c1[k] - c0[k];
+            h->irg_body[k] = c2[k] - c1[k];
+        }
+        // the capture counted one pass of each part; replays are added below
+        for (int k = 0; k < K_NKINDS; k++) g_launches[k].fetch_sub(c2[k] - c0[k], std::memory_order_relaxed);
+    }
+    if (cudaGraphLaunch(h->irg, h->stream) != cudaSuccess) return cuda_check(h, "refinement graph launch");
+    RC(read_back(h, ird, IRD_RATIO + 3));
+    prof_add(h->irg_pre, 1);
+    prof_add(h->irg_body, (long long)h->hbuf[IRD_IT] - 0);
+    *it_out = (int)h->hbuf[IRD_IT];
+    *st_out = (int)h->hbuf[IRD_STATUS];
+    for (int k = 0; k < 3; k++) ratio[k] = h->hbuf[IRD_RATIO + k];
+    return 0;
+}
+
+// Stages s1, s2, ||.||_F, ||.||_F of the held factorization into ird.
+static void ir_stage_scalars(mpir_ctx *h, double *ird)
+{
+    double *hb = h->hbuf + 48;
+    hb[0] = h->fs.s1; hb[1] = h->fs.s2; hb[2] = h->fs.fro1; hb[3] = h->fs.fro2;
+    cudaMemcpyAsync(ird + IRD_S1, hb, 4 * sizeof(double), cudaMemcpyHostToDevice, h->stream);
+}
+
+static bool ir_graph_usable(mpir_ctx *h) { return !h->irg_off && !g_prof; }
 
 struct StopState {
     double best = INFINITY;
@@ -726,7 +962,7 @@ void fill_opts(const mpir_opts *in, mpir_opts *o)
     mpir_default_opts(o);
     if (!in) return;
     *o = *in;
-    if (o->tol <= 0) o->tol = 2e-15;
+    if (o->tol <= 0) o->tol = 1e-15;
     if (o->maxit <= 0) o->maxit = 40;
     if (o->restart <= 0) o->restart = 30;
     if (o->inner_maxit <= 0) o->inner_maxit = 300;
@@ -946,6 +1182,68 @@ int gls_gmres_correction(mpir_ctx *h, GlsWs<T> &w, BDScratch &b, const double *W
     return cuda_check(h, "gls_gmres_correction");
 }
 
+// Sec. 5.1 (eq. gls-leftpre): the left preconditioner M ~ F~^-1, applied as
+// the paper does by the correction solver on the held factors (Alg. 3): F~ u
+// = g is the correction system with f = (g1, a g2, g3 / b), and its solution
+// (dy, dz, dx) gives u = (dy / a, -dz, dx / (a b)).  M_r = I; every shape.
+template <typename T>
+struct GlsLeftOp : LinOp {
+    GlsBDOp<T> bd;
+    GlsLeftOp(mpir_ctx *h_, GlsWs<T> &w_, BDScratch &b_, const double *W_, int ldw_, const double *V_, int ldv_,
+              double al_, double be_)
+        : bd(h_, w_, b_, W_, ldw_, V_, ldv_, al_, be_) {}
+
+    int Ml(const double *g, double *o)
+    {
+        mpir_ctx *h = bd.h;
+        const int n = bd.w.n, m = bd.w.m, p = bd.w.p;
+        const double al = bd.al, be = bd.be;
+        BDScratch &b = bd.b;
+        cudaStream_t s = h->stream;
+        vcomb<double>(b.w1, p, g, 0, 1.0, nullptr, 0, 0.0, s);
+        vcomb<double>(b.w2, n, g + p, 0, al, nullptr, 0, 0.0, s);
+        vcomb<double>(b.w3, m, g + p + n, 0, 1.0 / be, nullptr, 0, 0.0, s);
+        vzero(o, sizeof(double) * (size_t)(p + n + m), s);
+        RC(gls_correction_impl<T>(h, b.w1, b.w2, b.w3, 1.0, o, o + p, o + p + n));
+        vcomb<double>(o, p, o, 0, 1.0 / al, nullptr, 0, 0.0, s);
+        vcomb<double>(o + p, n, o + p, 0, -1.0, nullptr, 0, 0.0, s);
+        vcomb<double>(o + p + n, m, o + p + n, 0, 1.0 / (al * be), nullptr, 0, 0.0, s);
+        return 0;
+    }
+
+    int apply(const double *in, double *out) override
+    {
+        RC(bd.Fmul(in, bd.b.gf));
+        return Ml(bd.b.gf, out);
+    }
+};
+
+// One GMRES-IR correction with the left preconditioner (GLS): GMRES on
+// M F~ t = M [a^1/2 f1; a^-1/2 f2; a^1/2 b f3], then t = [a^-1/2 dy;
+// -a^1/2 dz; a^-1/2 b^-1 dx] and the updates are added to (y, z, x).
+template <typename T>
+int gls_gmres_left_correction(mpir_ctx *h, GlsWs<T> &w, BDScratch &b, const double *W, int ldw, const double *V,
+                              int ldv, double al, double be, double itol, int imax, double *y, double *z, double *x,
+                              int *inner)
+{
+    const int n = w.n, m = w.m, p = w.p;
+    cudaStream_t s = h->stream;
+    const double sa = std::sqrt(al);
+    GlsLeftOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
+    vcomb<double>(b.t, p, w.f1, 0, sa, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + p, n, w.f2, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + p + n, m, w.f3, 0, sa * be, nullptr, 0, 0.0, s);
+    RC(op.Ml(b.t, b.rhs));
+    int k = 0;
+    double rel = 0.0;
+    RC(gmres_solve(op, b.rhs, b.t, b.gw, itol, imax, h->hbuf, s, &k, &rel));
+    *inner += k;
+    vaxpy<double>(b.t, y, p, sa, 0, s);
+    vaxpy<double>(b.t + p, z, n, -1.0 / sa, 0, s);
+    vaxpy<double>(b.t + p + n, x, m, sa * be, 0, s);
+    return cuda_check(h, "gls_gmres_left_correction");
+}
+
 double inner_tol_default(const mpir_opts &o, int fact)
 {
     if (o.inner_tol > 0) return o.inner_tol;
@@ -967,12 +1265,13 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
                    mpir_info *info, bool factored = false)
 {
     cudaStream_t s = h->stream;
-    const bool gm = o.refine == MPIR_GMRES;
+    const bool left = o.refine == MPIR_GMRES_LEFT;
+    const bool gm = o.refine == MPIR_GMRES || left;
     size_t main_bytes = 0;
     gls_layout<T>(nullptr, n, m, p, &main_bytes);
     const int NG = p + n + m, mx = std::max(std::max(m, n), std::max(p, 1));
     if (gm) {
-        if (n > p) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.3) needs n <= p");
+        if (!left && n > p) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.3) needs n <= p");
         if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
         RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
     }
@@ -991,8 +1290,38 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
     double ratio[3] = {0, 0, 0};
     double al = 1.0;
     float t_gm = 0;
-    if (o.refine != MPIR_DIRECT) {
-        RC(gls_multipliers_impl<T>(h, y, z));
+    bool looped = false;
+    if (o.refine != MPIR_DIRECT) RC(gls_multipliers_impl<T>(h, y, z));
+    if (o.refine == MPIR_CLASSICAL && ir_graph_usable(h)) {
+        unsigned long long key = ir_mix(ir_mix(ir_mix(0, 2), sizeof(T)), (unsigned long long)n);
+        for (unsigned long long v_ : {(unsigned long long)m, (unsigned long long)p, (unsigned long long)ldw,
+                                      (unsigned long long)ldv, (unsigned long long)(uintptr_t)W,
+                                      (unsigned long long)(uintptr_t)V, (unsigned long long)(uintptr_t)d,
+                                      (unsigned long long)(uintptr_t)x, (unsigned long long)(uintptr_t)y,
+                                      (unsigned long long)(uintptr_t)z, (unsigned long long)(uintptr_t)h->ws,
+                                      (unsigned long long)o.maxit,
+                                      (unsigned long long)std::llround(-std::log2(o.tol) * 4096.0)})
+            key = ir_mix(key, v_);
+        ir_stage_scalars(h, w.ird);
+        auto pre = [&](cudaGraphConditionalHandle hc) {
+            k_ir_reset<<<1, 32, 0, h->stream>>>(w.ird);
+            absmax_sumsq(d, std::max(n, 1), n, 1, w.part, w.ird + IRD_N1, h->stream);
+            gls_residual_dev<T>(h, w, W, ldw, V, ldv, d, x, y, z);
+            k_ir_control<<<1, 32, 0, h->stream>>>(w.norms2, w.ird, 1, o.tol, o.maxit, hc, 1);
+            return cudaGetLastError() == cudaSuccess ? 0 : 1;
+        };
+        auto body = [&](cudaGraphConditionalHandle hc) {
+            int rc = gls_correction_impl<T>(h, w.f1, w.f2, w.f3, 1.0, y, z, x, w.ird + IRD_C);
+            gls_residual_dev<T>(h, w, W, ldw, V, ldv, d, x, y, z);
+            k_ir_control<<<1, 32, 0, h->stream>>>(w.norms2, w.ird, 1, o.tol, o.maxit, hc, 1);
+            return rc == 0 && cudaGetLastError() == cudaSuccess ? 0 : 1;
+        };
+        const int gr = ir_graph_run(h, w.ird, key, pre, body, &it, &st, ratio);
+        if (gr < 0 || gr == MPIR_CUDA_ERROR) return gr;
+        if (gr == 0) looped = true;
+        else h->irg_off = true;
+    }
+    if (o.refine != MPIR_DIRECT && !looped) {
         cudaEventRecord(h->ev[2], s);
         StopState ss;
         st = MPIR_NOT_CONVERGED;
@@ -1021,8 +1350,12 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
                 // Sec. 5.3: correction from GMRES on the preconditioned F~
                 if (it == 0) al = bd_alpha(o, nr[4], fV, nr[5]);
                 cudaEventRecord(h->ev[5], s);
-                RC(gls_gmres_correction<T>(h, w, bs, W, ldw, V, ldv, al, o.beta, inner_tol_default(o, fact),
-                                           o.inner_maxit, y, z, x, &inner, it == 0));
+                if (left)       // Sec. 5.1: M = F~^-1 applied by Alg. 3
+                    RC(gls_gmres_left_correction<T>(h, w, bs, W, ldw, V, ldv, al, o.beta,
+                                                    inner_tol_default(o, fact), o.inner_maxit, y, z, x, &inner));
+                else
+                    RC(gls_gmres_correction<T>(h, w, bs, W, ldw, V, ldv, al, o.beta, inner_tol_default(o, fact),
+                                               o.inner_maxit, y, z, x, &inner, it == 0));
                 cudaEventRecord(h->ev[6], s);
                 cudaEventSynchronize(h->ev[6]);
                 t_gm += ev_ms(h->ev[5], h->ev[6]);
@@ -1076,12 +1409,24 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     h->fs.fro1 = std::sqrt(h->hbuf[1]);
     h->fs.fro2 = std::sqrt(h->hbuf[3]);
     const GemmPrec gp = gemm_prec(fact);
+    // BF16 / TF32 factors: power-of-two column scaling D of [sA A; sB B]
+    // (Sec. 6.1 scaling before down-conversion), so every column enters the
+    // low-precision factorization with its largest entry in [0.5, 1); the
+    // factors are then those of (sA A D, sB B D) and x = D y
+    h->fs.colscale = sizeof(T) == 4 && (fact == MPIR_BF16 || fact == MPIR_TF32);
+    const double *Dc = h->fs.colscale ? w.D : nullptr;
+    if (Dc) colscale_pow2(A, lda, m, B, ldb, p, n, sA, sB, w.D, s);
     // RQ of B as QR of B~ = P_n B^T P_p (Lemma 4.5, first factorization),
     // with X = Q~^T P_n A^T = P_n (A Q^T)^T formed by the same trailing
     // updates: [B~ X] factored through its first p columns
-    mconvert<double, T>(B, ldb, w.Bt, w.ldBt, n, p, 1, 1, 1, sB, s);
-    mconvert<double, T>(A, lda, w.X, w.ldX, n, m, 1, 1, 0, sA, s);
-    RC(geqrf<T>(w.Bt, w.ldBt, n, p + m, w.tauB, w.TwB, w.Tw128B, gp, w.gws, h->sc.err, s,
+    mconvert<double, T>(B, ldb, w.Bt, w.ldBt, n, p, 1, 1, 1, sB, s, Dc, 1);
+    mconvert<double, T>(A, lda, w.X, w.ldX, n, m, 1, 1, 0, sA, s, Dc, 1);
+    // the low-precision classes (BF16, TF32) run the dominant factorization
+    // (QR of A Q^T) at their precision; the RQ of B and the application of
+    // its Q to A stay FP32-class, so that kappa(B) multiplies an FP32-sized
+    // error rather than a bfloat16 one
+    const GemmPrec gp1 = gp == GemmPrec::FP64 ? gp : GemmPrec::FP32;
+    RC(geqrf<T>(w.Bt, w.ldBt, n, p + m, w.tauB, w.TwB, w.Tw128B, gp1, w.gws, h->sc.err, s,
                 tfjob(h, w.TfB, w.ldtB, w.gws2), p));
     // A Q^T = X^T P_n, then its QR  (A Q^T = Z T)
     mconvert<T, T>(w.X, w.ldX, w.At, w.ldAt, m, n, 1, 0, 1, 1.0, s);
@@ -1119,6 +1464,7 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, w.tt, h->sc, s));
     vcopy<T, double>(w.tt, x, n, 1.0, 1, s, g + 1);
+    if (fs.colscale) vdiag<double>(x, w.D, n, 0, s);          // x = D y
     return cuda_check(h, "lse_initial");
 }
 
@@ -1135,6 +1481,7 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     RC(gemv<double>(A, lda, m, n, 0, -1.0, x, 1.0, r, 0, 0, s));
     if (p == 0) return cuda_check(h, "lse_multipliers");
     RC(gemv<double>(A, lda, m, n, 1, 1.0, r, 0.0, w.f3, 0, 0, s));
+    if (fs.colscale) vdiag<double>(w.f3, w.D, n, 0, s);       // (A D)^T r
     // u~ = Q~^T P_n (g sA A^T r), g a power-of-two normalizer
     double *g = w.scal + 8;
     pow2_normalizer(w.f3, n, fs.s1, nullptr, 0, 0.0, g, s);
@@ -1149,23 +1496,31 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
 // Alg. 1 in reversed coordinates; results are ADDED to (dr, dv, dx).
 template <typename T>
 int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const double *f3, double gamma,
-                        double *dr, double *dv, double *dx)
+                        double *dr, double *dv, double *dx, const double *dsc = nullptr)
 {
     const FactorState &fs = h->fs;
     LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
     const int m = w.m, n = w.n, p = w.p, q = w.q;
     const double sA = fs.s1, sB = fs.s2;
-    const double c1 = gamma, c2 = gamma * sB / sA, c3 = gamma * sA;
+    // scales of the right-hand side blocks and of the outputs: host values,
+    // or (dsc != NULL) device scalars c1, c2, c3, i1, i2, i3 left by the
+    // device-side loop's control kernel
+    const double c1 = dsc ? 1.0 : gamma, c2 = dsc ? 1.0 : gamma * sB / sA, c3 = dsc ? 1.0 : gamma * sA;
+    const double i1 = dsc ? 1.0 : 1.0 / gamma, i2 = dsc ? 1.0 : sB / sA / gamma, i3 = dsc ? 1.0 : sA / gamma;
+    const double *d1 = dsc, *d2 = dsc ? dsc + 1 : nullptr, *d3 = dsc ? dsc + 2 : nullptr;
+    const double *e1 = dsc ? dsc + 3 : nullptr, *e2 = dsc ? dsc + 4 : nullptr, *e3 = dsc ? dsc + 5 : nullptr;
     cudaStream_t s = h->stream;
     // step 1: u~ = Q~^T P_n f3' ;  u1 = P_q u~[p:n], u2 = P_p u~[0:p]
-    vcopy<double, T>(f3, w.tu, n, c3, 1, s);
+    // (with column scaling the third block of the scaled system is D f3)
+    vcopy<double, T>(f3, w.tu, n, c3, 1, s, d3);
+    if (fs.colscale) vdiag<T>(w.tu, w.D, n, 1, s);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, w.tu, h->sc, s));
     // step 2: w = Z^T f1'
-    vcopy<double, T>(f1, w.tw, m, c1, 0, s);
+    vcopy<double, T>(f1, w.tw, m, c1, 0, s, d1);
     RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 1, w.tw, h->sc, s));
     // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
     if (p > 0) {
-        vcopy<double, T>(f2, w.tb, p, c2, 1, s);
+        vcopy<double, T>(f2, w.tb, p, c2, 1, s, d2);
         RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
         vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     }
@@ -1190,14 +1545,15 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
         if (m - q > 0) RC(gemv<T>(w.At + idx2(q, q, w.ldAt), w.ldAt, m - q, p, 1, T(1), w.tq + q, T(1), w.tt, 1, 0, s));
         vcomb<T>(w.tb, p, w.tt, 1, T(1), w.tu, 0, T(-1), s);
         RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tb, h->sc, s, w.DinvB));
-        vaxpy<T>(w.tb, dv, p, sB / sA / gamma, 1, s);
+        vaxpy<T>(w.tb, dv, p, i2, 1, s, e2);
     }
     // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
     RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 0, w.tq, h->sc, s));
-    vaxpy<T>(w.tq, dr, m, 1.0 / gamma, 0, s);
+    vaxpy<T>(w.tq, dr, m, i1, 0, s, e1);
     vcomb<T>(w.tt2, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, w.tt2, h->sc, s));
-    vaxpy<T>(w.tt2, dx, n, sA / gamma, 1, s);
+    if (fs.colscale) vdiag<T>(w.tt2, w.D, n, 1, s);           // dx = D dy
+    vaxpy<T>(w.tt2, dx, n, i3, 1, s, e3);
     return cuda_check(h, "lse_correction");
 }
 
@@ -1267,6 +1623,7 @@ struct LseBDOp : LinOp {
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, b.w2, s));
         vcomb<double>(u + m + p, n, b.w2, 1, sa * sA, nullptr, 0, 0.0, s);
+        if (h->fs.colscale) vdiag<double>(u + m + p, w.D, n, 0, s);     // D (Q'^T T1'^-1) t3
         return 0;
     }
 
@@ -1297,8 +1654,9 @@ struct LseBDOp : LinOp {
             RC(gemv_d<T>(TS(), w.ldAt, p, p, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
             vcomb<double>(o + m, p, b.w3, 0, sB / (sA * sa * be), nullptr, 0, 0.0, s);
         }
-        // a^1/2 T1^-T Q g3 = a^1/2 sA T1'^-T P_n Q~^T P_n g3
+        // a^1/2 T1^-T Q g3 = a^1/2 sA T1'^-T P_n Q~^T P_n g3  (g3 -> D g3 with column scaling)
         vcomb<double>(b.w1, n, g + m + p, 1, 1.0, nullptr, 0, 0.0, s);
+        if (h->fs.colscale) vdiag<double>(b.w1, w.D, n, 1, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(trsv_d<T>(w.At, w.ldAt, n, 1, b.w2, h->sc, s, b.dT));
@@ -1341,18 +1699,78 @@ int lse_gmres_correction(mpir_ctx *h, LseWs<T> &w, BDScratch &b, const double *A
     return cuda_check(h, "lse_gmres_correction");
 }
 
+
+// Sec. 5.1 (eq. lse-leftpre): M ~ F~^-1 applied by Alg. 1 on the held
+// factors: F~ u = g is the correction system with f = (g1, g2 / b, a g3), and
+// its solution (dr, dv, dx) gives u = (dr / a, -dv / (a b), dx).  M_r = I;
+// every shape.
+template <typename T>
+struct LseLeftOp : LinOp {
+    LseBDOp<T> bd;
+    LseLeftOp(mpir_ctx *h_, LseWs<T> &w_, BDScratch &b_, const double *A_, int lda_, const double *B_, int ldb_,
+              double al_, double be_)
+        : bd(h_, w_, b_, A_, lda_, B_, ldb_, al_, be_) {}
+
+    int Ml(const double *g, double *o)
+    {
+        mpir_ctx *h = bd.h;
+        const int m = bd.w.m, n = bd.w.n, p = bd.w.p;
+        const double al = bd.al, be = bd.be;
+        BDScratch &b = bd.b;
+        cudaStream_t s = h->stream;
+        vcomb<double>(b.w1, m, g, 0, 1.0, nullptr, 0, 0.0, s);
+        if (p > 0) vcomb<double>(b.w2, p, g + m, 0, 1.0 / be, nullptr, 0, 0.0, s);
+        vcomb<double>(b.w3, n, g + m + p, 0, al, nullptr, 0, 0.0, s);
+        vzero(o, sizeof(double) * (size_t)(m + p + n), s);
+        RC(lse_correction_impl<T>(h, b.w1, b.w2, b.w3, 1.0, o, o + m, o + m + p));
+        vcomb<double>(o, m, o, 0, 1.0 / al, nullptr, 0, 0.0, s);
+        if (p > 0) vcomb<double>(o + m, p, o + m, 0, -1.0 / (al * be), nullptr, 0, 0.0, s);
+        return 0;
+    }
+
+    int apply(const double *in, double *out) override
+    {
+        RC(bd.Fmul(in, bd.b.gf));
+        return Ml(bd.b.gf, out);
+    }
+};
+
+template <typename T>
+int lse_gmres_left_correction(mpir_ctx *h, LseWs<T> &w, BDScratch &b, const double *A, int lda, const double *B,
+                              int ldb, double al, double be, double itol, int imax, double *r, double *v, double *x,
+                              int *inner)
+{
+    const int m = w.m, n = w.n, p = w.p;
+    cudaStream_t s = h->stream;
+    const double sa = std::sqrt(al);
+    LseLeftOp<T> op(h, w, b, A, lda, B, ldb, al, be);
+    vcomb<double>(b.t, m, w.f1, 0, sa, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + m, p, w.f2, 0, sa * be, nullptr, 0, 0.0, s);
+    vcomb<double>(b.t + m + p, n, w.f3, 0, 1.0 / sa, nullptr, 0, 0.0, s);
+    RC(op.Ml(b.t, b.rhs));
+    int k = 0;
+    double rel = 0.0;
+    RC(gmres_solve(op, b.rhs, b.t, b.gw, itol, imax, h->hbuf, s, &k, &rel));
+    *inner += k;
+    vaxpy<double>(b.t, r, m, sa, 0, s);
+    vaxpy<double>(b.t + m, v, p, -sa * be, 0, s);
+    vaxpy<double>(b.t + m + p, x, n, 1.0 / sa, 0, s);
+    return cuda_check(h, "lse_gmres_left_correction");
+}
+
 template <typename T>
 int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
                    const double *b, const double *d, double *x, double *r_out, double *v_out,
                    const mpir_opts &o, int fact, mpir_info *info, bool factored = false)
 {
     cudaStream_t s = h->stream;
-    const bool gm = o.refine == MPIR_GMRES;
+    const bool left = o.refine == MPIR_GMRES_LEFT;
+    const bool gm = o.refine == MPIR_GMRES || left;
     size_t main_bytes = 0;
     lse_layout<T>(nullptr, m, n, p, &main_bytes);
     const int NG = m + p + n, mx = std::max(std::max(m, n), std::max(p, 1));
     if (gm) {
-        if (m < n) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.2) needs m >= n");
+        if (!left && m < n) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.2) needs m >= n");
         if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
         RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
     }
@@ -1372,7 +1790,40 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
     double al = 1.0;
     float t_gm = 0;
     if (o.refine != MPIR_DIRECT || r_out || v_out) RC(lse_multipliers_impl<T>(h, A, lda, b, x, r, v));
-    if (o.refine != MPIR_DIRECT) {
+    bool looped = false;
+    if (o.refine == MPIR_CLASSICAL && ir_graph_usable(h)) {
+        // the loop on the device (one CUDA-graph launch, one host read)
+        unsigned long long key = ir_mix(ir_mix(ir_mix(0, 1), sizeof(T)), (unsigned long long)m);
+        for (unsigned long long v_ : {(unsigned long long)n, (unsigned long long)p, (unsigned long long)lda,
+                                      (unsigned long long)ldb, (unsigned long long)(uintptr_t)A,
+                                      (unsigned long long)(uintptr_t)B, (unsigned long long)(uintptr_t)b,
+                                      (unsigned long long)(uintptr_t)d, (unsigned long long)(uintptr_t)x,
+                                      (unsigned long long)(uintptr_t)r, (unsigned long long)(uintptr_t)v,
+                                      (unsigned long long)(uintptr_t)h->ws, (unsigned long long)o.maxit,
+                                      (unsigned long long)std::llround(-std::log2(o.tol) * 4096.0),
+                                      (unsigned long long)h->fs.colscale})
+            key = ir_mix(key, v_);
+        ir_stage_scalars(h, w.ird);
+        auto pre = [&](cudaGraphConditionalHandle hc) {
+            k_ir_reset<<<1, 32, 0, h->stream>>>(w.ird);
+            absmax_sumsq(b, std::max(m, 1), m, 1, w.part, w.ird + IRD_N1, h->stream);
+            if (p > 0) absmax_sumsq(d, std::max(p, 1), p, 1, w.part, w.ird + IRD_N2, h->stream);
+            lse_residual_dev<T>(h, w, A, lda, B, ldb, b, d, x, r, v);
+            k_ir_control<<<1, 32, 0, h->stream>>>(w.norms2, w.ird, 0, o.tol, o.maxit, hc, 1);
+            return cudaGetLastError() == cudaSuccess ? 0 : 1;
+        };
+        auto body = [&](cudaGraphConditionalHandle hc) {
+            int rc = lse_correction_impl<T>(h, w.f1, w.f2, w.f3, 1.0, r, v, x, w.ird + IRD_C);
+            lse_residual_dev<T>(h, w, A, lda, B, ldb, b, d, x, r, v);
+            k_ir_control<<<1, 32, 0, h->stream>>>(w.norms2, w.ird, 0, o.tol, o.maxit, hc, 1);
+            return rc == 0 && cudaGetLastError() == cudaSuccess ? 0 : 1;
+        };
+        const int gr = ir_graph_run(h, w.ird, key, pre, body, &it, &st, ratio);
+        if (gr < 0 || gr == MPIR_CUDA_ERROR) return gr;
+        if (gr == 0) looped = true;
+        else h->irg_off = true;       // capture not available: the host loop from now on
+    }
+    if (o.refine != MPIR_DIRECT && !looped) {
         const double nb = dnorm_host(h, b, m, w.part), nd = p > 0 ? dnorm_host(h, d, p, w.part) : 0.0;
         const double fA = h->fs.fro1, fB = h->fs.fro2;
         StopState ss;
@@ -1401,8 +1852,12 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
                 // Sec. 5.2: correction from GMRES on the preconditioned F~
                 if (it == 0) al = bd_alpha(o, nr[4], fA, nr[3]);
                 cudaEventRecord(h->ev[5], s);
-                RC(lse_gmres_correction<T>(h, w, bs, A, lda, B, ldb, al, o.beta, inner_tol_default(o, fact),
-                                           o.inner_maxit, r, v, x, &inner, it == 0));
+                if (left)       // Sec. 5.1: M = F~^-1 applied by Alg. 1
+                    RC(lse_gmres_left_correction<T>(h, w, bs, A, lda, B, ldb, al, o.beta,
+                                                    inner_tol_default(o, fact), o.inner_maxit, r, v, x, &inner));
+                else
+                    RC(lse_gmres_correction<T>(h, w, bs, A, lda, B, ldb, al, o.beta, inner_tol_default(o, fact),
+                                               o.inner_maxit, r, v, x, &inner, it == 0));
                 cudaEventRecord(h->ev[6], s);
                 cudaEventSynchronize(h->ev[6]);
                 t_gm += ev_ms(h->ev[5], h->ev[6]);
@@ -1495,7 +1950,7 @@ void mpir_default_opts(mpir_opts *o)
     std::memset(o, 0, sizeof(*o));
     o->fact = MPIR_FP32;
     o->refine = MPIR_CLASSICAL;
-    o->tol = 2e-15;
+    o->tol = 1e-15;
     o->maxit = 40;
     o->restart = 30;
     o->inner_maxit = 300;
@@ -1551,6 +2006,7 @@ int mpir_destroy(mpir_handle h)
         if (a.htab) cudaFreeHost(a.htab);
         if (a.hres) cudaFreeHost(a.hres);
         if (a.horder) cudaFreeHost(a.horder);
+        if (h->irg) cudaGraphExecDestroy(h->irg);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     }
     if (h->side) {
@@ -1633,7 +2089,7 @@ int mpir_lse_workspace_size(int m, int n, int p, const mpir_opts *opts, size_t *
     lse_layout<float>(nullptr, m, n, p, &b32);
     lse_layout<double>(nullptr, m, n, p, &b64);
     *bytes = (o.fact == MPIR_FP64 || o.escalate) ? std::max(b32, b64) : b32;
-    if (o.refine == MPIR_GMRES)
+    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT)
         *bytes += bd_bytes(m + p + n, std::min(o.restart, GMRES_MAX_RESTART), std::max(std::max(m, n), std::max(p, 1)));
     return 0;
 }
@@ -1650,7 +2106,7 @@ int mpir_gls_workspace_size(int n, int m, int p, const mpir_opts *opts, size_t *
     gls_layout<float>(nullptr, n, m, p, &b32);
     gls_layout<double>(nullptr, n, m, p, &b64);
     *bytes = (o.fact == MPIR_FP64 || o.escalate) ? std::max(b32, b64) : b32;
-    if (o.refine == MPIR_GMRES)
+    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT)
         *bytes += bd_bytes(p + n + m, std::min(o.restart, GMRES_MAX_RESTART), std::max(std::max(m, n), std::max(p, 1)));
     return 0;
 }
@@ -2004,40 +2460,13 @@ static int batch_tune(mpir_ctx *h, bool fp64, const int *border, int bcount, int
     return 0;
 }
 
-int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, const int *p,
-                      const double *const *A, const int *lda, const double *const *B, const int *ldb,
-                      const double *const *b, const double *const *d, double *const *x,
-                      const mpir_opts *opts, mpir_info *infos)
+// The persistent batched launch over a table of problems (LSE or GLS, any
+// mix): two size buckets, an autotuned launch shape per bucket, the launches
+// captured once in a CUDA graph and replayed.  Fills infos (when given) and
+// returns the worst status; `redo` receives the problems to escalate.
+static int batched_core(mpir_ctx *h, int count, const std::vector<BInst> &insts, const mpir_opts &o,
+                        mpir_info *infos, std::vector<int> &redo)
 {
-    if (!h) return -1;
-    if (count < 0) return -2;
-    if (count == 0) return 0;
-    if (!m) return -3;
-    if (!n) return -4;
-    if (!p) return -5;
-    if (!A) return -6;
-    if (!lda) return -7;
-    if (!B) return -8;
-    if (!ldb) return -9;
-    if (!b) return -10;
-    if (!d) return -11;
-    if (!x) return -12;
-    for (int i = 0; i < count; i++) {
-        const int a = lse_check_args(m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i]);
-        if (a) {
-            char msg[96];
-            std::snprintf(msg, sizeof(msg), "problem %d: illegal argument %d of lse_solve", i, -a);
-            return set_err(h, -3, msg);
-        }
-    }
-    mpir_opts o;
-    fill_opts(opts, &o);
-    if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
-    std::vector<int> all(count);
-    for (int i = 0; i < count; i++) all[i] = i;
-    // GMRES-IR and the learned selector run problem by problem
-    if (o.refine == MPIR_GMRES || o.fact == MPIR_AUTO)
-        return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
     const bool fp64 = o.fact == MPIR_FP64;
     int dev = 0, sms = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -2046,24 +2475,26 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
     // two size buckets: problems whose whole state fits a quarter of a CTA's
     // shared memory (several problems per CTA) and the others
     const size_t cut = ((size_t)optin - 2048) / 4;
-    struct Bucket { std::vector<int> idx; size_t smin = 0, sfull = 0, big = 0; int mmax = 0, nmax = 0, pmax = 0; };
+    struct Bucket { std::vector<int> idx; size_t smin = 0, sfull = 0, big = 0; int mmax = 0, nmax = 0, pmax = 0;
+                    unsigned kinds = 0; };
     Bucket bk[2];
     std::vector<double> work(count);
     for (int i = 0; i < count; i++) {
-        const size_t sf = batched_smem_full(m[i], n[i], p[i], fp64);
+        const BInst &t = insts[i];
+        const size_t sf = batched_smem_full(t.kind, t.m, t.n, t.p, fp64);
         Bucket &u = bk[sf <= cut ? 1 : 0];
         u.idx.push_back(i);
-        u.smin = std::max(u.smin, batched_smem_min(m[i], n[i], p[i], fp64));
+        u.smin = std::max(u.smin, batched_smem_min(t.kind, t.m, t.n, t.p, fp64));
         u.sfull = std::max(u.sfull, sf);
-        u.big = std::max(u.big, batched_big_words(m[i], n[i], p[i]));
-        u.mmax = std::max(u.mmax, m[i]); u.nmax = std::max(u.nmax, n[i]); u.pmax = std::max(u.pmax, p[i]);
-        work[i] = batched_work(m[i], n[i], p[i]);
+        u.big = std::max(u.big, batched_big_words(t.kind, t.m, t.n, t.p));
+        u.mmax = std::max(u.mmax, t.m); u.nmax = std::max(u.nmax, t.n); u.pmax = std::max(u.pmax, t.p);
+        u.kinds |= 1u << t.kind;
+        work[i] = batched_work(t.kind, t.m, t.n, t.p);
     }
     const size_t gstride = (std::max(bk[0].big, bk[1].big) + 63) & ~(size_t)63;
     RC(batch_reserve(h, 2 * count, (size_t)8 * sms * gstride * (fp64 ? 8 : 4)));
     BatchArena &a = h->ba;
-    for (int i = 0; i < count; i++)
-        a.htab[i] = BInst{A[i], B[i], b[i], d[i], x[i], m[i], n[i], p[i], lda[i], std::max(ldb[i], 1), 0};
+    for (int i = 0; i < count; i++) a.htab[i] = insts[i];
     // order: bucket 0 (large) then bucket 1, each largest work first
     int off[3] = {0, 0, 0};
     for (int u = 0; u < 2; u++) {
@@ -2082,6 +2513,7 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
         const int bc = off[u + 1] - off[u];
         if (bc == 0) continue;
         unsigned long long sig = mix64(mix64(mix64(mix64(u + 1, bc), bk[u].mmax), bk[u].nmax), bk[u].pmax);
+        sig = mix64(sig, bk[u].kinds);
         RC(batch_tune(h, fp64, a.horder + off[u], bc, a.order + count, a.next + 32 * u, sig, bk[u].smin,
                       bk[u].sfull, gstride, prm, &cfg[u]));
         grid[u] = sms * std::max(1, batched_ctas_per_sm(cfg[u], fp64));
@@ -2119,7 +2551,7 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
     cudaMemcpyAsync(a.hres, a.res, sizeof(BResult) * count, cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "batched");
     int worst = 0;
-    std::vector<int> redo;
+    redo.clear();
     for (int i = 0; i < count; i++) {
         const BResult &r = a.hres[i];
         if (infos) {
@@ -2133,12 +2565,73 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
         if (r.status != MPIR_OK && o.escalate && !fp64 && prm.refine != MPIR_DIRECT) redo.push_back(i);
         else worst = std::max(worst, r.status);
     }
+    return worst;
+}
+
+int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, const int *p,
+                      const double *const *A, const int *lda, const double *const *B, const int *ldb,
+                      const double *const *b, const double *const *d, double *const *x,
+                      const mpir_opts *opts, mpir_info *infos)
+{
+    if (!h) return -1;
+    if (count < 0) return -2;
+    if (count == 0) return 0;
+    if (!m) return -3;
+    if (!n) return -4;
+    if (!p) return -5;
+    if (!A) return -6;
+    if (!lda) return -7;
+    if (!B) return -8;
+    if (!ldb) return -9;
+    if (!b) return -10;
+    if (!d) return -11;
+    if (!x) return -12;
+    for (int i = 0; i < count; i++) {
+        const int a = lse_check_args(m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i]);
+        if (a) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "problem %d: illegal argument %d of lse_solve", i, -a);
+            return set_err(h, -3, msg);
+        }
+    }
+    mpir_opts o;
+    fill_opts(opts, &o);
+    if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
+    std::vector<int> all(count);
+    for (int i = 0; i < count; i++) all[i] = i;
+    // GMRES-IR and the learned selector run problem by problem
+    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT || o.fact == MPIR_AUTO)
+        return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
+    std::vector<BInst> insts(count);
+    for (int i = 0; i < count; i++)
+        insts[i] = BInst{A[i], B[i], b[i], d[i], x[i], nullptr, m[i], n[i], p[i], lda[i], std::max(ldb[i], 1),
+                         BKIND_LSE};
+    std::vector<int> redo;
+    int worst = batched_core(h, count, insts, o, infos, redo);
+    if (worst < 0) return worst;
     if (!redo.empty()) {
         // escalation: re-solve with an FP64 factorization
         mpir_opts o64 = o;
         o64.fact = MPIR_FP64;
         const int st = lse_solve_each(h, redo, m, n, p, A, lda, B, ldb, b, d, x, o64, infos, 1);
         if (st < 0) return st;
+        worst = std::max(worst, st);
+    }
+    return worst;
+}
+
+static int gls_solve_each(mpir_handle h, const std::vector<int> &which, const int *n, const int *m, const int *p,
+                          const double *const *W, const int *ldw, const double *const *V, const int *ldv,
+                          const double *const *d, double *const *x, double *const *y, const mpir_opts &o,
+                          mpir_info *infos, int esc_base)
+{
+    int worst = 0;
+    for (int i : which) {
+        mpir_info inf;
+        int st = gls_solve(h, n[i], m[i], p[i], W[i], ldw[i], V[i], ldv[i], d[i], x[i], y[i], nullptr, &o, &inf);
+        if (st < 0) return st;
+        inf.escalated += esc_base;
+        if (infos) infos[i] = inf;
         worst = std::max(worst, st);
     }
     return worst;
@@ -2151,10 +2644,43 @@ int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m, cons
 {
     if (!h) return -1;
     if (count < 0) return -2;
-    int worst = 0;
+    if (count == 0) return 0;
+    if (!n) return -3;
+    if (!m) return -4;
+    if (!p) return -5;
+    if (!W) return -6;
+    if (!ldw) return -7;
+    if (!V) return -8;
+    if (!ldv) return -9;
+    if (!d) return -10;
+    if (!x) return -11;
+    if (!y) return -12;
     for (int i = 0; i < count; i++) {
-        int st = gls_solve(h, n[i], m[i], p[i], W[i], ldw[i], V[i], ldv[i], d[i], x[i], y[i], nullptr, opts,
-                           infos ? &infos[i] : nullptr);
+        const int a = gls_check_args(n[i], m[i], p[i], W[i], ldw[i], V[i], ldv[i], d[i], x[i], y[i]);
+        if (a) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "problem %d: illegal argument %d of gls_solve", i, -a);
+            return set_err(h, -3, msg);
+        }
+    }
+    mpir_opts o;
+    fill_opts(opts, &o);
+    if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
+    std::vector<int> all(count);
+    for (int i = 0; i < count; i++) all[i] = i;
+    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT || o.fact == MPIR_AUTO)
+        return gls_solve_each(h, all, n, m, p, W, ldw, V, ldv, d, x, y, o, infos, 0);
+    std::vector<BInst> insts(count);
+    for (int i = 0; i < count; i++)
+        insts[i] = BInst{W[i], V[i], nullptr, d[i], x[i], y[i], m[i], n[i], p[i], std::max(ldw[i], 1),
+                         std::max(ldv[i], 1), BKIND_GLS};
+    std::vector<int> redo;
+    int worst = batched_core(h, count, insts, o, infos, redo);
+    if (worst < 0) return worst;
+    if (!redo.empty()) {
+        mpir_opts o64 = o;
+        o64.fact = MPIR_FP64;
+        const int st = gls_solve_each(h, redo, n, m, p, W, ldw, V, ldv, d, x, y, o64, infos, 1);
         if (st < 0) return st;
         worst = std::max(worst, st);
     }
@@ -2481,6 +3007,11 @@ static int lse_bd_apply_impl(mpir_ctx *h, const double *A, int lda, const double
     RC(ensure_rws(h, bd_bytes(N, 1, mx)));
     BDScratch b = bd_layout(h->rws, N, 1, mx);
     LseWs<T> w = lse_layout<T>(h->ws, fs.m, fs.n, fs.p, nullptr);
+    if (which >= 4) {           // left preconditioner (Sec. 5.1)
+        LseLeftOp<T> op(h, w, b, A, lda, B, ldb, al, be);
+        RC(which == 4 ? op.Ml(in, out) : op.apply(in, out));
+        return cuda_check(h, "lse_bd_apply");
+    }
     LseBDOp<T> op(h, w, b, A, lda, B, ldb, al, be);
     op.prepare();
     RC(bd_dispatch(op, which, in, out, b));
@@ -2496,6 +3027,11 @@ static int gls_bd_apply_impl(mpir_ctx *h, const double *W, int ldw, const double
     RC(ensure_rws(h, bd_bytes(N, 1, mx)));
     BDScratch b = bd_layout(h->rws, N, 1, mx);
     GlsWs<T> w = gls_layout<T>(h->ws, fs.n, fs.m, fs.p, nullptr);
+    if (which >= 4) {           // left preconditioner (Sec. 5.1)
+        GlsLeftOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
+        RC(which == 4 ? op.Ml(in, out) : op.apply(in, out));
+        return cuda_check(h, "gls_bd_apply");
+    }
     GlsBDOp<T> op(h, w, b, W, ldw, V, ldv, al, be);
     op.prepare();
     RC(bd_dispatch(op, which, in, out, b));
@@ -2510,14 +3046,14 @@ int mpir_lse_bd_apply(mpir_handle h, const double *A, int lda, const double *B, 
     if (!h) return -1;
     const FactorState &fs = h->fs;
     if (fs.kind != Kind::LSE) return set_err(h, MPIR_UNSUPPORTED, "no LSE factors held");
-    if (fs.m < fs.n) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.2) needs m >= n");
+    if (fs.m < fs.n && which < 4) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.2) needs m >= n");
     if (!A) return -2;
     if (lda < std::max(1, fs.m)) return -3;
     if (fs.p > 0 && !B) return -4;
     if (ldb < std::max(1, fs.p)) return -5;
     if (!(alpha > 0) || !std::isfinite(alpha)) return -6;
     if (!(beta > 0) || !std::isfinite(beta)) return -7;
-    if (which < 0 || which > 3) return -8;
+    if (which < 0 || which > 5) return -8;
     if (!in) return -9;
     if (!out || out == in) return -10;
     clear_dev_flags(h);
@@ -2533,14 +3069,14 @@ int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, 
     if (!h) return -1;
     const FactorState &fs = h->fs;
     if (fs.kind != Kind::GLS) return set_err(h, MPIR_UNSUPPORTED, "no GLS factors held");
-    if (fs.n > fs.p) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.3) needs n <= p");
+    if (fs.n > fs.p && which < 4) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.3) needs n <= p");
     if (fs.m > 0 && !W) return -2;
     if (ldw < std::max(1, fs.n)) return -3;
     if (!V) return -4;
     if (ldv < std::max(1, fs.n)) return -5;
     if (!(alpha > 0) || !std::isfinite(alpha)) return -6;
     if (!(beta > 0) || !std::isfinite(beta)) return -7;
-    if (which < 0 || which > 3) return -8;
+    if (which < 0 || which > 5) return -8;
     if (!in) return -9;
     if (!out || out == in) return -10;
     clear_dev_flags(h);
@@ -2636,8 +3172,24 @@ int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam
     if (!labels) return -8;
     if (count < 1) return -9;
     RC(ensure_rws(h, sizeof(float) * mlp_ws_floats(count)));
-    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, labels, count, (float *)h->rws, grad, loss, h->stream));
+    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, labels, nullptr, count, (float *)h->rws, grad, loss,
+                      h->stream));
     return cuda_check(h, "mpir_mlp_train_step");
+}
+
+int mpir_mlp_train_step_soft(mpir_handle h, float *params, float *adam_m, float *adam_v, int step, float lr,
+                             const float *X, const float *targets, int count, float *grad, float *loss)
+{
+    if (!h) return -1;
+    if (!params) return -2;
+    if (step < 1) return -5;
+    if (!X) return -7;
+    if (!targets) return -8;
+    if (count < 1) return -9;
+    RC(ensure_rws(h, sizeof(float) * mlp_ws_floats(count)));
+    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, nullptr, targets, count, (float *)h->rws, grad, loss,
+                      h->stream));
+    return cuda_check(h, "mpir_mlp_train_step_soft");
 }
 
 int mpir_selector_set(mpir_handle h, const float *params, const float *mean, const float *scale)

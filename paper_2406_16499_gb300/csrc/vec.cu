@@ -749,12 +749,14 @@ void pow2_normalizer(const double *u, int nu, double a1, const double *w, int nw
 }
 
 template <typename Ts>
-__global__ void k_vaxpy(const Ts *__restrict__ src, double *__restrict__ dst, int n, double scale, int rev)
+__global__ void k_vaxpy(const Ts *__restrict__ src, double *__restrict__ dst, int n, double scale, int rev,
+                        const double *__restrict__ dscale)
 {
     pdl_wait();
     pdl_trigger();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) dst[i] += scale * (double)src[rev ? n - 1 - i : i];
+    const double sc = dscale ? scale * *dscale : scale;
+    if (i < n) dst[i] += sc * (double)src[rev ? n - 1 - i : i];
 }
 
 template <typename Ts, typename Td>
@@ -766,11 +768,11 @@ void vcopy(const Ts *src, Td *dst, int n, double scale, int rev, cudaStream_t s,
 }
 
 template <typename Ts>
-void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s)
+void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_t s, const double *dscale)
 {
     if (n <= 0) return;
     ProfScope ps(K_ELEMWISE, s);
-    pdl_launch(k_vaxpy<Ts>, dim3(ceil_div(n, 256)), dim3(256), 0, s, src, dst, n, scale, rev);
+    pdl_launch(k_vaxpy<Ts>, dim3(ceil_div(n, 256)), dim3(256), 0, s, src, dst, n, scale, rev, dscale);
 }
 
 void vzero(void *dst, size_t bytes, cudaStream_t s)
@@ -783,8 +785,9 @@ void vzero(void *dst, size_t bytes, cudaStream_t s)
 template <typename Ts, typename Td>
 __global__ void __launch_bounds__(256)
 k_mconvert(const Ts *__restrict__ src, int lds, Td *__restrict__ dst, int ldd, int rows_d, int cols_d,
-           int transpose, int rev_r, int rev_c, double scale)
+           int transpose, int rev_r, int rev_c, double scale, const double *__restrict__ rs, int rs_rev)
 {
+    auto rsc = [&](int i) { return rs ? scale * rs[rs_rev ? rows_d - 1 - i : i] : scale; };
     __shared__ Ts tile[32][33];
     const int bi = blockIdx.x * 32, bj = blockIdx.y * 32;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
@@ -795,7 +798,7 @@ k_mconvert(const Ts *__restrict__ src, int lds, Td *__restrict__ dst, int ldd, i
             int i = bi + tx, j = bj + r;
             if (i < rows_d && j < cols_d) {
                 int ip = rev_r ? rows_d - 1 - i : i, jp = rev_c ? cols_d - 1 - j : j;
-                dst[idx2(i, j, ldd)] = (Td)(scale * (double)src[idx2(ip, jp, lds)]);
+                dst[idx2(i, j, ldd)] = (Td)(rsc(i) * (double)src[idx2(ip, jp, lds)]);
             }
         }
         return;
@@ -811,19 +814,68 @@ k_mconvert(const Ts *__restrict__ src, int lds, Td *__restrict__ dst, int ldd, i
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         int i = bi + tx, j = bj + r;
-        if (i < rows_d && j < cols_d) dst[idx2(i, j, ldd)] = (Td)(scale * (double)tile[tx][r]);
+        if (i < rows_d && j < cols_d) dst[idx2(i, j, ldd)] = (Td)(rsc(i) * (double)tile[tx][r]);
     }
 }
 
 template <typename Ts, typename Td>
 void mconvert(const Ts *src, int lds, Td *dst, int ldd, int rows_d, int cols_d, int transpose, int rev_r,
-              int rev_c, double scale, cudaStream_t s)
+              int rev_c, double scale, cudaStream_t s, const double *rs, int rs_rev)
 {
     if (rows_d <= 0 || cols_d <= 0) return;
     dim3 grid(ceil_div(rows_d, 32), ceil_div(cols_d, 32));
     ProfScope ps(K_CONVERT, s);
     k_mconvert<Ts, Td><<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows_d, cols_d, transpose, rev_r, rev_c,
-                                           scale);
+                                           scale, rs, rs_rev);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_vdiag(T *__restrict__ v, const double *__restrict__ D, int n, int rev)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i < n) v[i] = (T)((double)v[i] * D[rev ? n - 1 - i : i]);
+}
+
+template <typename T>
+void vdiag(T *v, const double *D, int n, int rev, cudaStream_t s)
+{
+    if (n <= 0 || !D) return;
+    ProfScope ps(K_ELEMWISE, s);
+    k_vdiag<T><<<ceil_div(n, 256), 256, 0, s>>>(v, D, n, rev);
+}
+
+// One warp per column j: the column maxima of A and B, then D[j].
+__global__ void __launch_bounds__(256)
+k_colscale(const double *__restrict__ A, int lda, int rows_a, const double *__restrict__ B, int ldb, int rows_b,
+           int n, double a1, double a2, double *__restrict__ D)
+{
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= n) return;
+    double ma = 0.0, mb = 0.0;
+    for (int i = lane; i < rows_a; i += 32) ma = fmax(ma, fabs(A[idx2(i, j, lda)]));
+    for (int i = lane; i < rows_b; i += 32) mb = fmax(mb, fabs(B[idx2(i, j, ldb)]));
+    for (int o = 16; o > 0; o >>= 1) {
+        ma = fmax(ma, __shfl_xor_sync(0xffffffffu, ma, o));
+        mb = fmax(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if (lane == 0) {
+        const double mx = fmax(a1 * ma, a2 * mb);
+        double d = 1.0;
+        if (mx > 0.0 && isfinite(mx)) {
+            int e;
+            frexp(mx, &e);                 // mx = f 2^e, f in [0.5, 1)
+            d = ldexp(1.0, -e);
+        }
+        D[j] = d;
+    }
+}
+
+void colscale_pow2(const double *A, int lda, int rows_a, const double *B, int ldb, int rows_b, int n, double a1,
+                   double a2, double *D, cudaStream_t s)
+{
+    if (n <= 0) return;
+    ProfScope ps(K_NORM, s);
+    k_colscale<<<ceil_div(n, 8), 256, 0, s>>>(A, lda, rows_a, B, ldb, rows_b, n, a1, a2, D);
 }
 
 // max|A| and sum of squares, two-stage deterministic reduction.
@@ -914,15 +966,20 @@ template void vcopy<double, float>(const double *, float *, int, double, int, cu
 template void vcopy<double, double>(const double *, double *, int, double, int, cudaStream_t, const double *);
 template void vcopy<float, double>(const float *, double *, int, double, int, cudaStream_t, const double *);
 template void vcopy<float, float>(const float *, float *, int, double, int, cudaStream_t, const double *);
-template void vaxpy<float>(const float *, double *, int, double, int, cudaStream_t);
-template void vaxpy<double>(const double *, double *, int, double, int, cudaStream_t);
+template void vaxpy<float>(const float *, double *, int, double, int, cudaStream_t, const double *);
+template void vaxpy<double>(const double *, double *, int, double, int, cudaStream_t, const double *);
 template void mconvert<double, float>(const double *, int, float *, int, int, int, int, int, int, double,
-                                      cudaStream_t);
+                                      cudaStream_t, const double *, int);
 template void mconvert<double, double>(const double *, int, double *, int, int, int, int, int, int, double,
-                                       cudaStream_t);
+                                      cudaStream_t, const double *, int);
 template void mconvert<float, float>(const float *, int, float *, int, int, int, int, int, int, double,
-                                     cudaStream_t);
+                                      cudaStream_t, const double *, int);
 template void mconvert<float, double>(const float *, int, double *, int, int, int, int, int, int, double,
-                                      cudaStream_t);
+                                      cudaStream_t, const double *, int);
 
+} // namespace mpir
+
+namespace mpir {
+template void vdiag<double>(double *, const double *, int, int, cudaStream_t);
+template void vdiag<float>(float *, const double *, int, int, cudaStream_t);
 } // namespace mpir

@@ -306,6 +306,25 @@ def selector_lse_problems(seed, count, m_lo=64, m_hi=400, cond_lo=1e0, cond_hi=1
     return out
 
 
+def selector_gls_problems(seed, count, n_lo=64, n_hi=400, cond_lo=1e0, cond_hi=1e12):
+    """GLS problems for training / evaluating the selector (xGGGLM
+    convention): n ~ U[n_lo, n_hi], m ~ U[8, n/2], p ~ U[n, 5n/4],
+    kappa_2([W, V]) log-uniform in [cond_lo, cond_hi] with a random
+    xLATM1-style pattern (gls_paper)."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(g.integers(n_lo, n_hi + 1))
+        m = int(g.integers(8, max(8, n // 2) + 1))
+        p = int(g.integers(n, n + n // 4 + 1))
+        c = float(np.exp(g.uniform(np.log(cond_lo), np.log(cond_hi))))
+        mode = int(g.integers(1, 4))
+        G = gls_paper(int(g.integers(1 << 62)), n, m, p, c, mode)
+        G["kappa"] = c
+        out.append(G)
+    return out
+
+
 # ------------------------------------------------------------------ GLS --
 
 def ar1_cholesky(n, rho):
@@ -329,6 +348,56 @@ def gls_ar1(seed=20242623, n=4096, m=1024, cond_w=1e3, rho=0.9):
     y = g.standard_normal(n)
     d = W @ x + V @ y
     return dict(W=W, V=V, d=d)
+
+
+def gls_batch_specs(seed=20245623, count=1000, n_lo=32, n_hi=512, cond_lo=1e1, cond_hi=1e5):
+    """(seed, n, m, p, cond(W)) of each problem of an uneven GLS batch in the
+    xGGGLM convention: n ~ U[n_lo, n_hi], m ~ U[4, n/2], p ~ U[n, n + n/4]
+    (so m <= n <= p), cond(W) log-uniform in [cond_lo, cond_hi]."""
+    g = rng(seed)
+    out = []
+    for _ in range(count):
+        n = int(g.integers(n_lo, n_hi + 1))
+        m = int(g.integers(4, max(4, n // 2) + 1))
+        p = int(g.integers(n, n + n // 4 + 1))
+        c = float(np.exp(g.uniform(np.log(cond_lo), np.log(cond_hi))))
+        out.append((int(g.integers(1 << 62)), n, m, p, c))
+    return out
+
+
+def gls_batch(seed=20245623, count=1000, **kw):
+    """The problems of gls_batch_specs: W with cond(W) (SVD construction),
+    V with cond(V) = 10, d = W x + V y (gls_svd per problem, own seed)."""
+    return [gls_svd(s, n, m, p, c, 10.0) for s, n, m, p, c in gls_batch_specs(seed, count, **kw)]
+
+
+def gls_batch_torch(specs, device, cond_v=10.0):
+    """gls_batch_specs problems drawn with torch's generator on `device`
+    (the construction of gls_svd): dicts of FP64 column-major W, V, d."""
+    import torch
+
+    def haar(g, rows, cols):
+        X = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
+        Q, R = torch.linalg.qr(X)
+        sg = torch.sign(torch.diagonal(R))
+        sg[sg == 0] = 1.0
+        return Q * sg
+
+    def svd_m(g, rows, cols, sigma):
+        U = haar(g, rows, len(sigma))
+        V = haar(g, cols, len(sigma))
+        return ((U * sigma) @ V.T).t().contiguous().t()
+
+    out = []
+    for s, n, m, p, c in specs:
+        g = torch.Generator(device=device)
+        g.manual_seed(s & ((1 << 63) - 1))
+        W = svd_m(g, n, m, torch.from_numpy(logspace_sigma(m, c)).to(device))
+        V = svd_m(g, n, p, torch.from_numpy(logspace_sigma(min(n, p), cond_v)).to(device))
+        x = torch.randn(m, generator=g, device=device, dtype=torch.float64)
+        y = torch.randn(p, generator=g, device=device, dtype=torch.float64)
+        out.append(dict(W=W, V=V, d=W @ x + V @ y))
+    return out
 
 
 def gls_paper(seed, n, m, p, kappa, mode=3):

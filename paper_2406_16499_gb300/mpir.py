@@ -15,7 +15,7 @@ from . import build as _build
 _lib = None
 
 PREC = {"bf16": 0, "tf32": 1, "fp32": 2, "fp64": 3, "auto": 4}
-REFINE = {"classical": 0, "gmres": 1, "direct": 2}
+REFINE = {"classical": 0, "gmres": 1, "direct": 2, "gmres_left": 3}
 STATUS = {0: "ok", 1: "singular R", 2: "singular T", 3: "not converged", 4: "non-finite",
           5: "unsupported", 6: "cuda error", 7: "device timeout"}
 
@@ -85,6 +85,7 @@ _SIG = {
     "mpir_mlp_param_count": ([], _I),
     "mpir_mlp_forward": ([_P, _P, _P, _I, _P], _I),
     "mpir_mlp_train_step": ([_P, _P, _P, _P, _I, ctypes.c_float, _P, _P, _I, _P, _P], _I),
+    "mpir_mlp_train_step_soft": ([_P, _P, _P, _P, _I, ctypes.c_float, _P, _P, _I, _P, _P], _I),
     "mpir_selector_set": ([_P, _P, _P, _P], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
@@ -237,6 +238,38 @@ class LseBatch:
         self.infos = (Info * sz)()
 
 
+class GlsBatch:
+    """The host-side argument arrays of gls_solve_batched for a list of GLS
+    problems (dicts of column-major FP64 device tensors W (n x m), V (n x p),
+    d) and their output vectors xs (m), ys (p)."""
+
+    def __init__(self, probs, xs, ys):
+        import numpy as np
+        cnt = len(probs)
+        self.count = cnt
+        self.keep = (list(probs), list(xs), list(ys))
+        sz = max(cnt, 1)
+        ints = np.zeros((5, sz), dtype=np.int32)
+        ptrs = np.zeros((5, sz), dtype=np.uint64)
+        for i, pr in enumerate(probs):
+            W, V = pr["W"], pr["V"]
+            ints[0, i], ints[1, i] = W.shape
+            ints[2, i] = V.shape[1]
+            ints[3, i] = ld(W)
+            ints[4, i] = ld(V)
+            ptrs[0, i] = ptr(W) or 0
+            ptrs[1, i] = ptr(V) or 0
+            ptrs[2, i] = ptr(pr["d"]) or 0
+            ptrs[3, i] = ptr(xs[i]) or 0
+            ptrs[4, i] = ptr(ys[i]) or 0
+        self._ints, self._ptrs = np.ascontiguousarray(ints), np.ascontiguousarray(ptrs)
+        ip = lambda k: ctypes.c_void_p(self._ints[k].ctypes.data)
+        pp = lambda k: ctypes.c_void_p(self._ptrs[k].ctypes.data)
+        # (n, m, p, W, ldw, V, ldv, d, x, y) in the C argument order
+        self.args = (ip(0), ip(1), ip(2), pp(0), ip(3), pp(1), ip(4), pp(2), pp(3), pp(4))
+        self.infos = (Info * sz)()
+
+
 class Handle:
     """Owns an mpir_handle bound to a device and a CUDA stream (the current
     torch stream by default)."""
@@ -293,6 +326,15 @@ class Handle:
                                      ctypes.cast(batch.infos, ctypes.POINTER(Info)))
         return self.check(rc, "lse_solve_batched"), list(batch.infos)[:batch.count]
 
+    def gls_solve_batched(self, probs, xs=None, ys=None, opts=None):
+        """probs: a GlsBatch, or a sequence of dicts with device tensors W, V,
+        d together with xs, ys.  Returns (status, [Info])."""
+        batch = probs if isinstance(probs, GlsBatch) else GlsBatch(probs, xs, ys)
+        o = opts if opts is not None else make_opts()
+        rc = lib().gls_solve_batched(self.h, batch.count, *batch.args, ctypes.byref(o),
+                                     ctypes.cast(batch.infos, ctypes.POINTER(Info)))
+        return self.check(rc, "gls_solve_batched"), list(batch.infos)[:batch.count]
+
     # ---- learned selector ------------------------------------------------
     def lse_features(self, A, B, b, d, s, out):
         p = B.shape[0]
@@ -315,6 +357,12 @@ class Handle:
                                                     int(step), float(lr), ptr(X, "f32"), ptr(y, "i32"), X.shape[0],
                                                     ptr(grad, "f32"), ptr(loss, "f32")),
                           "mpir_mlp_train_step")
+
+    def mlp_train_step_soft(self, params, m, v, step, lr, X, Q, grad=None, loss=None):
+        return self.check(lib().mpir_mlp_train_step_soft(self.h, ptr(params, "f32"), ptr(m, "f32"), ptr(v, "f32"),
+                                                         int(step), float(lr), ptr(X, "f32"), ptr(Q, "f32"),
+                                                         X.shape[0], ptr(grad, "f32"), ptr(loss, "f32")),
+                          "mpir_mlp_train_step_soft")
 
     def selector_set(self, params, mean, scale):
         """params, mean, scale: host float32 numpy arrays (None removes)."""
@@ -412,17 +460,19 @@ class Handle:
                               ptr(C, "f32"), ld(C))
         return self.check(rc, "mpir_larfb")
 
-    BD_WHICH = {"F": 0, "Ml": 1, "Mr": 2, "op": 3}
+    BD_WHICH = {"F": 0, "Ml": 1, "Mr": 2, "op": 3, "M": 4, "left_op": 5}
 
     def lse_bd_apply(self, A, B, alpha, beta, which, vin, vout):
-        """F~, M_l, M_r or M_l F~ M_r (Sec. 5.2) on [m; p; n] vectors."""
+        """F~, M_l, M_r or M_l F~ M_r (Sec. 5.2), or the left preconditioner M
+        and M F~ (Sec. 5.1), on [m; p; n] vectors."""
         p = B.shape[0]
         return self.check(lib().mpir_lse_bd_apply(self.h, ptr(A), ld(A), ptr(B), ld(B) if p else 1, float(alpha),
                                                   float(beta), self.BD_WHICH[which], ptr(vin), ptr(vout)),
                           "mpir_lse_bd_apply")
 
     def gls_bd_apply(self, W, V, alpha, beta, which, vin, vout):
-        """F~, M_l, M_r or M_l F~ M_r (Sec. 5.3) on [p; n; m] vectors."""
+        """F~, M_l, M_r or M_l F~ M_r (Sec. 5.3), or the left preconditioner M
+        and M F~ (Sec. 5.1), on [p; n; m] vectors."""
         return self.check(lib().mpir_gls_bd_apply(self.h, ptr(W), ld(W), ptr(V), ld(V), float(alpha), float(beta),
                                                   self.BD_WHICH[which], ptr(vin), ptr(vout)),
                           "mpir_gls_bd_apply")

@@ -9,7 +9,13 @@ Classes (in the library's order): BF16 + classical, BF16 + GMRES,
 FP32 + classical, FP32 + GMRES, FP64 + classical, FP64 + GMRES.
 Label of a problem: the fastest class whose solve converged (status 0 from
 the library's FP64 stop test); within 3 % of the fastest, the higher
-factorization precision and then classical IR win.
+factorization precision and then classical IR win.  Cost-weighted target
+(the default for training): a distribution over the converged classes with
+weight exp(-ln(t_c / t_best) / tau), so that a class twice as slow as the
+best gets almost nothing and near-ties share the mass -- the network then
+learns to avoid classes whose time varies wildly between similar problems
+(GMRES-IR on small, latency-bound problems) instead of copying noisy
+near-tie labels.
 """
 import time
 
@@ -53,9 +59,10 @@ def gls_features(h, P):
     return out.cpu().numpy()
 
 
-def time_lse_classes(h, P):
+def time_lse_classes(h, P, **caps):
     """(times in ms, converged flags) of the six classes on one LSE problem
-    (device solve time from the library's events; no escalation)."""
+    (device solve time from the library's events; no escalation).  caps:
+    optional maxit / inner_maxit limits of the timed solves."""
     import torch
     A, B, b, d = (_dev(P[k]) for k in ("A", "B", "b", "d"))
     m, n = A.shape
@@ -65,7 +72,29 @@ def time_lse_classes(h, P):
         x, r, v = (torch.zeros(k, dtype=torch.float64, device="cuda") for k in (n, m, max(p, 1)))
         try:
             st, info = h.lse_solve(A, B, b, d, x, r, v if p else None,
-                                   mpir.make_opts(fact=fact, refine=refine, escalate=False))
+                                   mpir.make_opts(fact=fact, refine=refine, escalate=False, **caps))
+            times.append(float(info.time_ms[5]))
+            ok.append(st == 0)
+        except mpir.MpirError:
+            times.append(float("inf"))
+            ok.append(False)
+    return times, ok
+
+
+def time_gls_classes(h, G, **caps):
+    """(times in ms, converged flags) of the six classes on one GLS problem
+    (device solve time from the library's events; no escalation).  caps:
+    optional maxit / inner_maxit limits of the timed solves."""
+    import torch
+    W, V, d = (_dev(G[k]) for k in ("W", "V", "d"))
+    n, m = W.shape
+    p = V.shape[1]
+    times, ok = [], []
+    for fact, refine in CLASSES:
+        x, y, z = (torch.zeros(k, dtype=torch.float64, device="cuda") for k in (m, p, n))
+        try:
+            st, info = h.gls_solve(W, V, d, x, y, z, mpir.make_opts(fact=fact, refine=refine, escalate=False,
+                                                                     **caps))
             times.append(float(info.time_ms[5]))
             ok.append(st == 0)
         except mpir.MpirError:
@@ -82,6 +111,16 @@ def label(times, ok, tie=0.03):
     near = [i for i in cand if times[i] <= best * (1 + tie)]
     prec = {"bf16": 0, "fp32": 1, "fp64": 2}
     return max(near, key=lambda i: (prec[CLASSES[i][0]], CLASSES[i][1] == "classical"))
+
+
+def soft_target(times, ok, tau=0.15):
+    """Cost-weighted target distribution over the six classes (None when no
+    class converged)."""
+    t = np.array([times[i] if ok[i] else np.inf for i in range(NC)], dtype=np.float64)
+    if not np.isfinite(t).any():
+        return None
+    w = np.where(np.isfinite(t), np.exp(-np.log(t / t.min()) / tau), 0.0)
+    return (w / w.sum()).astype(np.float32)
 
 
 def init_params(seed):
@@ -123,11 +162,13 @@ class Selector:
 
 
 def train(h, X, y, steps=600, lr=3e-3, seed=0, log_every=0):
-    """Full-batch Adam on the mean cross-entropy with the library's kernels.
+    """Full-batch Adam on the mean cross-entropy with the library's kernels;
+    y: labels (int, count) or target distributions (float, count x 6).
     Returns (Selector, losses)."""
     import torch
     X = np.asarray(X, np.float32)
-    y = np.asarray(y, np.int32)
+    soft = np.asarray(y).ndim == 2
+    y = np.asarray(y, np.float32 if soft else np.int32)
     mean = X.mean(axis=0)
     scale = X.std(axis=0)
     scale[scale < 1e-6] = 1.0
@@ -140,8 +181,11 @@ def train(h, X, y, steps=600, lr=3e-3, seed=0, log_every=0):
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     losses = []
     for t in range(1, steps + 1):
-        h.mlp_train_step(P, M, V, t, lr, Xd, yd, None, loss if (t == 1 or t == steps or
-                                                                (log_every and t % log_every == 0)) else None)
+        lo = loss if (t == 1 or t == steps or (log_every and t % log_every == 0)) else None
+        if soft:
+            h.mlp_train_step_soft(P, M, V, t, lr, Xd, yd, None, lo)
+        else:
+            h.mlp_train_step(P, M, V, t, lr, Xd, yd, None, lo)
         if t == 1 or t == steps or (log_every and t % log_every == 0):
             losses.append((t, float(loss.item())))
     return Selector(P.cpu().numpy(), mean, scale), losses

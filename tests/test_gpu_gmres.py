@@ -11,6 +11,9 @@
   residual, forward error against the oracle's solution).
 * Table 4's behaviour: at kappa = 1e9 (one small singular value) classical
   IR with FP32 factors does not converge and GMRES-IR does.
+* The left preconditioner of Sec. 5.1 (M ~ F~^-1 applied by the correction
+  solver): M and M F~ against the oracle's LseLeft / GlsLeft, M F~ = I with
+  FP64 factors, and full solves on every shape, wide ones included.
 """
 import numpy as np
 import pytest
@@ -83,6 +86,58 @@ def test_gls_bd_pieces_match_oracle(h, oracle_mod, n, m, p, fact, tol):
         want = fn(u)
         t = 1e-13 if which == "F" else tol
         assert rel(host(out), want) <= t, (which, rel(host(out), want))
+
+
+LSE_LEFT_SHAPES = LSE_SHAPES + [(90, 100, 45), (60, 100, 70)]        # the last two wide (m < n)
+GLS_LEFT_SHAPES = GLS_SHAPES + [(200, 120, 100), (150, 100, 60)]     # the last two with n > p
+
+
+@pytest.mark.parametrize("m,n,p", LSE_LEFT_SHAPES)
+@pytest.mark.parametrize("fact,tol", [("fp64", 1e-11), ("fp32", 5e-4)])
+def test_lse_left_pieces_match_oracle(h, oracle_mod, m, n, p, fact, tol):
+    """The left preconditioner of Sec. 5.1 (M ~ F~^-1 through Alg. 1) and
+    M F~ against oracle/gmres.py's LseLeft; with FP64 factors M F~ u = u to
+    rounding (M is F~^-1 up to the factorization's backward error)."""
+    from oracle import gmres as G
+    P = I.lse_svd(17 * m + n + p, m, n, p, 1e2, 1e1)
+    A, B = P["A"], P["B"]
+    a, b = 0.37, 1.7
+    F = oracle_mod.lse_factor(A, B, fact)
+    lp = G.LseLeft(F, A, B, a, b)
+    dA, dB = dev(A), dev(B)
+    h.lse_factor(dA, dB, fact=fact)
+    g = np.random.default_rng(m * n + p)
+    N = m + p + n
+    for which, fn in (("M", lp.Ml), ("left_op", lambda t: lp.Ml(lp.Fmul(t)))):
+        u = g.standard_normal(N)
+        out = zeros(N)
+        h.lse_bd_apply(dA, dB, a, b, which, dev(u), out)
+        assert rel(host(out), fn(u)) <= tol, (which, rel(host(out), fn(u)))
+        if which == "left_op" and fact == "fp64":
+            assert rel(host(out), u) <= 1e-10
+
+
+@pytest.mark.parametrize("n,m,p", GLS_LEFT_SHAPES)
+@pytest.mark.parametrize("fact,tol", [("fp64", 1e-11), ("fp32", 5e-4)])
+def test_gls_left_pieces_match_oracle(h, oracle_mod, n, m, p, fact, tol):
+    """As above for GLS (M through Alg. 3, oracle GlsLeft)."""
+    from oracle import gmres as G
+    Gp = I.gls_svd(19 * n + m + p, n, m, p, 1e2, 1e1)
+    W, V = Gp["W"], Gp["V"]
+    a, b = 2.5, 0.6
+    F = oracle_mod.gls_factor(W, V, fact)
+    lp = G.GlsLeft(F, W, V, a, b)
+    dW, dV = dev(W), dev(V)
+    h.gls_factor(dW, dV, fact=fact)
+    g = np.random.default_rng(n * m + p)
+    N = p + n + m
+    for which, fn in (("M", lp.Ml), ("left_op", lambda t: lp.Ml(lp.Fmul(t)))):
+        u = g.standard_normal(N)
+        out = zeros(N)
+        h.gls_bd_apply(dW, dV, a, b, which, dev(u), out)
+        assert rel(host(out), fn(u)) <= tol, (which, rel(host(out), fn(u)))
+        if which == "left_op" and fact == "fp64":
+            assert rel(host(out), u) <= 1e-10
 
 
 def test_preconditioned_operator_spectrum_on_gpu(h):
@@ -175,6 +230,39 @@ def test_gmres_ir_beyond_classical_limit(h, oracle_mod):
     assert ref["status"] == 0
 
 
+@pytest.mark.parametrize("m,n,p,ca", [(333, 290, 77, 1e3), (257, 129, 31, 1e5), (300, 120, 0, 1e3),
+                                      (90, 100, 45, 1e3), (60, 100, 70, 1e4)])
+def test_lse_gmres_left_shapes(h, oracle_mod, m, n, p, ca):
+    """GMRES-IR with the left preconditioner (Sec. 5.1), wide shapes
+    included: the FP64 bar, and the oracle's left GMRES-IR converges too."""
+    from oracle import gmres as Gm
+    P = I.lse_svd(m + 5 * n + p, m, n, p, ca, 1e1)
+    st, info, x, r, v = run_lse(h, P, refine="gmres_left", escalate=False)
+    assert st == 0 and info.refine_used == 3 and info.inner_iters >= 1
+    check_lse(oracle_mod, P, x, r, v)
+    assert Gm.lse_gmres_ir(P["A"], P["B"], P["b"], P["d"], precond="left")["status"] == 0
+
+
+@pytest.mark.parametrize("n,m,p,cw", [(300, 77, 300, 1e3), (257, 100, 400, 1e4), (200, 120, 100, 1e2),
+                                      (150, 100, 60, 1e3)])
+def test_gls_gmres_left_shapes(h, oracle_mod, n, m, p, cw):
+    from oracle import gmres as Gm
+    G = I.gls_svd(5 * n + m + p, n, m, p, cw, 1e1)
+    st, info, x, y, z = run_gls(h, G, refine="gmres_left", escalate=False)
+    assert st == 0 and info.refine_used == 3 and info.inner_iters >= 1
+    check_gls(oracle_mod, G, x, y, z)
+    assert Gm.gls_gmres_ir(G["W"], G["V"], G["d"], precond="left")["status"] == 0
+
+
+def test_gmres_left_beyond_classical_limit(h, oracle_mod):
+    """Table 4's kappa = 1e9 case with the left preconditioner: FP32 factors,
+    no escalation, FP64-level result."""
+    P = I.lse_paper(7, 512, 64, 2, 1e9, mode=2)
+    st, info, x, r, v = run_lse(h, P, refine="gmres_left", escalate=False)
+    assert st == 0 and info.fact_used == 2
+    check_lse(oracle_mod, P, x, r, v)
+
+
 @pytest.mark.parametrize("kappa", [1e3, 1e7])
 def test_gls_gmres_paper_spectrum(h, oracle_mod, kappa):
     """GLS [W, V] with kappa_2 = kappa (Sec. 6.3, geometric spectrum)."""
@@ -202,6 +290,9 @@ def test_gmres_shape_conditions(h):
     G = I.gls_svd(6, 200, 120, 100, 1e2, 1e1)
     with pytest.raises(mpir.MpirError, match="unsupported"):
         run_gls(h, G, refine="gmres", escalate=False)
+    # the left preconditioner (Sec. 5.1) has no shape condition
+    assert run_lse(h, P, refine="gmres_left", escalate=False)[0] == 0
+    assert run_gls(h, G, refine="gmres_left", escalate=False)[0] == 0
 
 
 def test_gls_gmres_full_size_ar1(h, oracle_mod):

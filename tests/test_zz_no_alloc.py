@@ -55,6 +55,42 @@ def test_noalloc_residual_matches_handle_entry_point():
         h.close()
 
 
+def test_noalloc_residual_on_a_caller_stream():
+    """The same check on a caller-created (non-default) stream, two calls in
+    a row on that stream with different inputs, results read after a
+    synchronization of that stream only."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2406_16499_gb300 import mpir
+    h = mpir.Handle()
+    st = torch.cuda.Stream()
+    try:
+        outs = []
+        cases = [_case(seed, 400, 120, 500) for seed in (5, 6)]
+        with torch.cuda.stream(st):
+            for W, V, d, x, y, z in cases:
+                dW, dV, dd, dx, dy, dz = dev(W), dev(V), dev(d), dev(x), dev(y), dev(z)
+                a1, a2, a3 = zeros(500), zeros(400), zeros(120)
+                assert mpir.gls_residual_noalloc(dW, dV, dd, dx, dy, dz, a1, a2, a3, None,
+                                                 stream=st.cuda_stream) == 0
+                outs.append((dW, dV, dd, dx, dy, dz, a1, a2, a3))
+        st.synchronize()
+        for (dW, dV, dd, dx, dy, dz, a1, a2, a3), (W, V, d, x, y, z) in zip(outs, cases):
+            r1, r2, r3 = zeros(500), zeros(400), zeros(120)
+            h.gls_residual(dW, dV, dd, dx, dy, dz, r1, r2, r3)
+            torch.cuda.synchronize()
+            scale = (np.abs(np.concatenate([np.zeros(500), d, np.zeros(120)]))
+                     + np.concatenate([np.abs(y) + np.abs(V).T @ np.abs(z),
+                                       np.abs(W) @ np.abs(x) + np.abs(V) @ np.abs(y),
+                                       np.abs(W).T @ np.abs(z)]))
+            ref = np.concatenate([host(r1), host(r2), host(r3)])
+            got = np.concatenate([host(a1), host(a2), host(a3)])
+            assert np.all(np.abs(got - ref) <= (400 + 120 + 500 + 2) * U64 * scale)
+    finally:
+        h.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_scratch():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
