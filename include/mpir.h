@@ -376,7 +376,9 @@ int mpir_gls_residual_noalloc(int n, int m, int p, const double *W, int ldw,
  * of the bidiagonal of min(16, rows, columns) Golub-Kahan-Lanczos steps
  * started from s (device, length n; a wide block starts from M^T M s),
  * computed with FP32 vectors and products, each new vector reorthogonalized
- * once, stopping only at breakdown (an entry below 2^-26 of the largest).  GLS: log n,
+ * once, stopping only at breakdown (an entry below 2^-26 of the largest),
+ * the bidiagonal's extreme singular values by FP32 bisection (relative
+ * error O(k u_single); kappa^ = inf below 2^-100 sigma_max).  GLS: log n,
  * log m, log(p+1), m/n, n/p, kind 1, 0, log ||W||_F, log ||V||_F, log ||d||,
  * 0, log(||W||_F/||V||_F), kappa^ of W, V, [W, V], log(flops); s has length
  * m + p (W uses s[0:m], V s[m:m+p]).  Logs are natural, of the value clamped
@@ -405,14 +407,6 @@ int mpir_mlp_forward(mpir_handle h, const float *params, const float *X, int cou
 int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam_v, int step,
                         float lr, const float *X, const int *labels, int count, float *grad,
                         float *loss);
-/* As mpir_mlp_train_step with a target distribution per sample instead of a
- * label (targets: device float[count][6], each row summing to 1): the loss
- * is the mean of -sum_c targets[c] log prob[c] (a cost-weighted target puts
- * its mass on the classes that solve the problem fastest). */
-int mpir_mlp_train_step_soft(mpir_handle h, float *params, float *adam_m, float *adam_v, int step,
-                             float lr, const float *X, const float *targets, int count,
-                             float *grad, float *loss);
-
 /* Install a trained selector in the handle (host arrays: params as above,
  * feature standardization mean[16] and scale[16]: the network sees
  * (f - mean) / scale).  Solves with opts->fact = MPIR_AUTO then compute the

@@ -20,8 +20,7 @@ int features_launch(int kind, int m, int n, int p, const double *A, int lda, con
 
 size_t mlp_ws_floats(int count);
 int mlp_forward(const float *P, const float *X, int count, float *prob, cudaStream_t s);
-// y: labels (int[count]) or q: target distributions (float[count][6]); one of them
-int mlp_train_step(float *P, float *M, float *V, int t, float lr, const float *X, const int *y, const float *q,
-                   int count, float *ws, float *grad_out, float *loss_out, cudaStream_t s);
+int mlp_train_step(float *P, float *M, float *V, int t, float lr, const float *X, const int *y, int count,
+                   float *ws, float *grad_out, float *loss_out, cudaStream_t s);
 
 } // namespace mpir

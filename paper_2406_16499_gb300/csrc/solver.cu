@@ -437,7 +437,13 @@ int ensure_ws(mpir_ctx *h, size_t bytes)
 int ensure_rws(mpir_ctx *h, size_t bytes)
 {
     if (h->rws_bytes >= bytes) return 0;
-    if (h->rws) { cudaStreamSynchronize(h->stream); cudaFree(h->rws); h->rws = nullptr; h->rws_bytes = 0; }
+    if (h->rws) {
+        cudaStreamSynchronize(h->stream);
+        if (h->sel_stream) cudaStreamSynchronize(h->sel_stream);    // the selector's features use it too
+        cudaFree(h->rws);
+        h->rws = nullptr;
+        h->rws_bytes = 0;
+    }
     if (cudaMalloc(&h->rws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "residual scratch cudaMalloc failed"); }
     h->rws_bytes = bytes;
     return 0;
@@ -2194,7 +2200,10 @@ static int sel_begin(mpir_ctx *h, int kind, int d0, int d1, int d2, const double
     cudaStreamWaitEvent(h->sel_stream, h->sel_ev, 0);
     float *feat = h->sel + MLP_PARAMS + 16 + 8;
     cudaStream_t ss = h->sel_stream;
-    RC(features_launch(kind, d0, d1, d2, M1, ld1, M2, ld2, h->sel_s, v1, n1, v2, n2, 16, (double *)h->rws, feat, ss));
+    // features_launch takes GLS dimensions as (columns of W, rows, columns of V)
+    const int fm = kind == 0 ? d0 : d1, fn = kind == 0 ? d1 : d0;
+    RC(features_launch(kind, fm, fn, d2, M1, ld1, M2, ld2, h->sel_s, v1, n1, v2, n2, 16, (double *)h->rws, feat,
+                       ss));
     cudaMemcpyAsync(h->sel_host, feat, 16 * sizeof(float), cudaMemcpyDeviceToHost, ss);
     cudaEventRecord(h->sel_ev, ss);
     return 0;
@@ -3172,24 +3181,8 @@ int mpir_mlp_train_step(mpir_handle h, float *params, float *adam_m, float *adam
     if (!labels) return -8;
     if (count < 1) return -9;
     RC(ensure_rws(h, sizeof(float) * mlp_ws_floats(count)));
-    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, labels, nullptr, count, (float *)h->rws, grad, loss,
-                      h->stream));
+    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, labels, count, (float *)h->rws, grad, loss, h->stream));
     return cuda_check(h, "mpir_mlp_train_step");
-}
-
-int mpir_mlp_train_step_soft(mpir_handle h, float *params, float *adam_m, float *adam_v, int step, float lr,
-                             const float *X, const float *targets, int count, float *grad, float *loss)
-{
-    if (!h) return -1;
-    if (!params) return -2;
-    if (step < 1) return -5;
-    if (!X) return -7;
-    if (!targets) return -8;
-    if (count < 1) return -9;
-    RC(ensure_rws(h, sizeof(float) * mlp_ws_floats(count)));
-    RC(mlp_train_step(params, adam_m, adam_v, step, lr, X, nullptr, targets, count, (float *)h->rws, grad, loss,
-                      h->stream));
-    return cuda_check(h, "mpir_mlp_train_step_soft");
 }
 
 int mpir_selector_set(mpir_handle h, const float *params, const float *mean, const float *scale)

@@ -85,7 +85,6 @@ _SIG = {
     "mpir_mlp_param_count": ([], _I),
     "mpir_mlp_forward": ([_P, _P, _P, _I, _P], _I),
     "mpir_mlp_train_step": ([_P, _P, _P, _P, _I, ctypes.c_float, _P, _P, _I, _P, _P], _I),
-    "mpir_mlp_train_step_soft": ([_P, _P, _P, _P, _I, ctypes.c_float, _P, _P, _I, _P, _P], _I),
     "mpir_selector_set": ([_P, _P, _P, _P], _I),
     "mpir_profile": ([_I], _I),
     "mpir_profile_read": ([_P, _P, _I], _I),
@@ -357,12 +356,6 @@ class Handle:
                                                     int(step), float(lr), ptr(X, "f32"), ptr(y, "i32"), X.shape[0],
                                                     ptr(grad, "f32"), ptr(loss, "f32")),
                           "mpir_mlp_train_step")
-
-    def mlp_train_step_soft(self, params, m, v, step, lr, X, Q, grad=None, loss=None):
-        return self.check(lib().mpir_mlp_train_step_soft(self.h, ptr(params, "f32"), ptr(m, "f32"), ptr(v, "f32"),
-                                                         int(step), float(lr), ptr(X, "f32"), ptr(Q, "f32"),
-                                                         X.shape[0], ptr(grad, "f32"), ptr(loss, "f32")),
-                          "mpir_mlp_train_step_soft")
 
     def selector_set(self, params, mean, scale):
         """params, mean, scale: host float32 numpy arrays (None removes)."""

@@ -9,13 +9,7 @@ Classes (in the library's order): BF16 + classical, BF16 + GMRES,
 FP32 + classical, FP32 + GMRES, FP64 + classical, FP64 + GMRES.
 Label of a problem: the fastest class whose solve converged (status 0 from
 the library's FP64 stop test); within 3 % of the fastest, the higher
-factorization precision and then classical IR win.  Cost-weighted target
-(the default for training): a distribution over the converged classes with
-weight exp(-ln(t_c / t_best) / tau), so that a class twice as slow as the
-best gets almost nothing and near-ties share the mass -- the network then
-learns to avoid classes whose time varies wildly between similar problems
-(GMRES-IR on small, latency-bound problems) instead of copying noisy
-near-tie labels.
+factorization precision and then classical IR win.
 """
 import time
 
@@ -113,16 +107,6 @@ def label(times, ok, tie=0.03):
     return max(near, key=lambda i: (prec[CLASSES[i][0]], CLASSES[i][1] == "classical"))
 
 
-def soft_target(times, ok, tau=0.15):
-    """Cost-weighted target distribution over the six classes (None when no
-    class converged)."""
-    t = np.array([times[i] if ok[i] else np.inf for i in range(NC)], dtype=np.float64)
-    if not np.isfinite(t).any():
-        return None
-    w = np.where(np.isfinite(t), np.exp(-np.log(t / t.min()) / tau), 0.0)
-    return (w / w.sum()).astype(np.float32)
-
-
 def init_params(seed):
     """He initialization, flattened in the library's layout."""
     g = np.random.default_rng(seed)
@@ -162,13 +146,11 @@ class Selector:
 
 
 def train(h, X, y, steps=600, lr=3e-3, seed=0, log_every=0):
-    """Full-batch Adam on the mean cross-entropy with the library's kernels;
-    y: labels (int, count) or target distributions (float, count x 6).
+    """Full-batch Adam on the mean cross-entropy with the library's kernels.
     Returns (Selector, losses)."""
     import torch
     X = np.asarray(X, np.float32)
-    soft = np.asarray(y).ndim == 2
-    y = np.asarray(y, np.float32 if soft else np.int32)
+    y = np.asarray(y, np.int32)
     mean = X.mean(axis=0)
     scale = X.std(axis=0)
     scale[scale < 1e-6] = 1.0
@@ -182,10 +164,7 @@ def train(h, X, y, steps=600, lr=3e-3, seed=0, log_every=0):
     losses = []
     for t in range(1, steps + 1):
         lo = loss if (t == 1 or t == steps or (log_every and t % log_every == 0)) else None
-        if soft:
-            h.mlp_train_step_soft(P, M, V, t, lr, Xd, yd, None, lo)
-        else:
-            h.mlp_train_step(P, M, V, t, lr, Xd, yd, None, lo)
+        h.mlp_train_step(P, M, V, t, lr, Xd, yd, None, lo)
         if t == 1 or t == steps or (log_every and t % log_every == 0):
             losses.append((t, float(loss.item())))
     return Selector(P.cpu().numpy(), mean, scale), losses

@@ -109,7 +109,11 @@ def _kappa_ref(M, s):
     much and |1/kappa^_gpu - 1/kappa^| <= c u_single ||M||_F / sigma_max.
     c = 2 (the float32 sums on the GPU run in another order than the
     dot products of a float32 emulation, which stayed below c = 0.25 on
-    these blocks).  Above kappa^ ~ 1e6 this still separates 1e6 from 1e9."""
+    these blocks).  Above kappa^ ~ 1e6 this still separates 1e6 from 1e9.
+    The bidiagonal's extreme singular values come from FP32 bisection, whose
+    relative error is O(k u_single) (relative perturbation theory of
+    bidiagonals), and the feature holds log kappa^ in FP32: together at most
+    (4 k + |log kappa^|) u_single / kappa^ on 1/kappa^."""
     from oracle import selector as S
     M = np.asarray(M, np.float64)
     rows, cols = M.shape
@@ -117,7 +121,10 @@ def _kappa_ref(M, s):
     s0 = M.T @ (M @ s) if rows < cols else np.asarray(s, np.float64)
     Bk = S.gkl_bidiag(lambda x: M @ x, lambda y: M.T @ y, s0, k)
     sv = np.linalg.svd(Bk, compute_uv=False)
-    return sv[0] / sv[-1], 2 * U32 * np.linalg.norm(M) / sv[0]
+    kap = sv[0] / sv[-1]
+    # + the FP32 bisection on the bidiagonal (relative O(k u_single) on each
+    # of sigma_max, sigma_min: Demmel-Kahan) and the FP32 feature log kappa^
+    return kap, 2 * U32 * np.linalg.norm(M) / sv[0] + (4 * k + abs(np.log(kap))) * U32 / kap
 
 
 def _check_kappa(got_logs, blocks):
