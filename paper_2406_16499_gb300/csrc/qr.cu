@@ -505,6 +505,258 @@ k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
 }
 
 // ---------------------------------------------------------------------------
+// FP32 panel with column pairs (k_panel_qr's layout and message protocol,
+// one message round per two columns).  A round for columns kk, kk+1 sums,
+// over the rows below kk+1,
+//     S1[c] = sum_i a(i,kk) a(i,c),   S2[c] = sum_i a(i,kk+1) a(i,c)   (all c),
+// and broadcasts the pivot rows P1 = a(kk,:), P2 = a(kk+1,:).  Reflector kk
+// is the single-column one with row kk+1 added back (S1 + P2[kk] P2).  It
+// changes column c below row kk+1 into a(:,c) - g_c w (w = a(:,kk), g_c =
+// scale1 tau1 dot1[c]; column kk itself into scale1 w), so the sums the
+// second reflector needs expand into S1, S2 and the g's:
+//     sum a'(i,kk+1) a'(i,c) = S2[c] - g_c S1[kk+1] - g S1[c] + g g_c S1[kk]
+// (g = g_{kk+1}), and its pivot row is P2 - g_c P2[kk].  That downdate
+// cancels when column kk+1 is nearly parallel to column kk: where its
+// squared norm below the pivot falls under 1/16 of S2[kk+1], the round
+// applies reflector kk only and the next round starts at kk+1.  Every warp
+// of every CTA evaluates the same totals in the same order, so the choice
+// is uniform over the cluster.
+// ---------------------------------------------------------------------------
+constexpr float PAIR_GUARD = 0.0625f;
+
+__device__ __forceinline__ void pair_reflector(float alpha, float sp, float &tv, float &beta, float &scale)
+{
+    if (sp == 0.f) {
+        tv = 0.f; beta = alpha; scale = 1.f;
+    } else {
+        const float nrm = sqrtf(alpha * alpha + sp);
+        beta = alpha >= 0.f ? -nrm : nrm;
+        tv = (beta - alpha) / beta;
+        scale = 1.f / (alpha - beta);
+    }
+}
+
+template <int NT, int RPT>
+__global__ void __launch_bounds__(NT, 1)
+k_panel_qr_pair(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk, float *__restrict__ tau,
+                float *__restrict__ Tw, int *__restrict__ err)
+{
+    constexpr int NB = 32, H = 16;
+    constexpr int NW = NT / 32;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int cs = (int)cluster.num_blocks();
+    const int crank = (int)cluster.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = M - j0;
+    const int kpanel = min(ncols, L);
+    constexpr int MSG = 4 * NB;                          // S1, S2, P1, P2
+    static_assert(MSG * sizeof(float) / 16 == 32, "one 16-byte vector per lane");
+    __shared__ float red_s[2][NW][2 * NB];
+    __shared__ __align__(16) float xbuf[NW][MSG];
+    __shared__ __align__(16) float gbuf[2][16][MSG];
+    __shared__ __align__(8) unsigned long long mbar[2];
+    __shared__ float prow[2][2][NB];
+    __shared__ __align__(16) float coefw[NW][2][NB];
+    __shared__ float G_s[NB][NB + 1];
+    __shared__ float tau_s[NB];
+
+    const int row_base = crank * chunk;
+    const int row_end = min(row_base + chunk, L);
+    const uint32_t msg_bytes = (uint32_t)(cs * MSG * sizeof(float));
+    bool timed_out = false;
+    for (int e = tid; e < NB * (NB + 1); e += NT) (&G_s[0][0])[e] = 0.f;
+    if (cs > 1) {
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[0])) : "memory");
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(pq_smem(&mbar[1])) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            pq_expect_tx(pq_smem(&mbar[0]), msg_bytes);        // round 0
+        }
+        cluster.sync();
+    }
+    int rr[RPT];
+    float a[RPT][NB];
+#pragma unroll
+    for (int q = 0; q < RPT; q++) {
+        const int r = row_base + tid + q * NT;
+        rr[q] = r < row_end ? r : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < NB; c++) {
+        const float *col = A + idx2(j0, j0 + c, lda);
+#pragma unroll
+        for (int q = 0; q < RPT; q++) a[q][c] = (rr[q] >= 0 && c < ncols) ? col[rr[q]] : 0.f;
+    }
+
+    int rnd = 0;
+#pragma unroll 1
+    for (int kk = 0; kk < kpanel; rnd++) {
+        const int par = rnd & 1;
+        const bool two = kk + 1 < kpanel;
+        const int kb = two ? kk + 1 : kk;                 // the sums run over rows below kb
+        float ak1[RPT], ak2[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; q++) {
+            ak1[q] = pq_select<float, NB>(a[q], kk);
+            ak2[q] = two ? pq_select<float, NB>(a[q], kk + 1) : 0.f;
+        }
+#pragma unroll
+        for (int h0 = 0; h0 < NB; h0 += H) {
+            float acc1[H], acc2[H];
+#pragma unroll
+            for (int c = 0; c < H; c++) { acc1[c] = 0.f; acc2[c] = 0.f; }
+#pragma unroll
+            for (int q = 0; q < RPT; q++) {
+                const bool bel = rr[q] > kb;
+                const float x1 = bel ? ak1[q] : 0.f, x2 = bel ? ak2[q] : 0.f;
+#pragma unroll
+                for (int c = 0; c < H; c++) {
+                    acc1[c] = fmaf(x1, a[q][h0 + c], acc1[c]);
+                    acc2[c] = fmaf(x2, a[q][h0 + c], acc2[c]);
+                }
+            }
+            const float w1 = warp_transpose_reduce<float, H>(acc1);
+            const float w2 = warp_transpose_reduce<float, H>(acc2);
+            if (lane < H) {
+                red_s[par][warp][h0 + lane] = w1;
+                red_s[par][warp][NB + h0 + lane] = w2;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; q++) {
+            if (rr[q] == kk) {
+#pragma unroll
+                for (int c = 0; c < NB; c++) prow[par][0][c] = a[q][c];
+            }
+            if (two && rr[q] == kk + 1) {
+#pragma unroll
+                for (int c = 0; c < NB; c++) prow[par][1][c] = a[q][c];
+            }
+        }
+        // a next round exists whenever a column follows kk (if this round
+        // takes two columns and none is left, the count is never used)
+        if (cs > 1 && tid == 0 && kk + 1 < kpanel) pq_expect_tx(pq_smem(&mbar[par ^ 1]), msg_bytes);
+        __syncthreads();
+        float tot1 = 0.f, tot2 = 0.f, pj1 = 0.f, pj2 = 0.f;
+        if (cs == 1) {
+#pragma unroll
+            for (int w = 0; w < NW; w++) { tot1 += red_s[par][w][lane]; tot2 += red_s[par][w][NB + lane]; }
+            pj1 = prow[par][0][lane];
+            pj2 = two ? prow[par][1][lane] : 0.f;
+        } else {
+            {
+                float t1 = 0.f, t2 = 0.f;
+#pragma unroll
+                for (int w = 0; w < NW; w++) { t1 += red_s[par][w][lane]; t2 += red_s[par][w][NB + lane]; }
+                xbuf[warp][lane] = t1;
+                xbuf[warp][NB + lane] = t2;
+                xbuf[warp][2 * NB + lane] = crank == 0 ? prow[par][0][lane] : 0.f;
+                xbuf[warp][3 * NB + lane] = (crank == 0 && two) ? prow[par][1][lane] : 0.f;
+            }
+            __syncwarp();
+            {
+                const float4 v = reinterpret_cast<const float4 *>(&xbuf[warp][0])[lane];
+                const uint32_t dst = pq_smem(&gbuf[par][crank][0]) + 16 * lane;
+                const uint32_t bar = pq_smem(&mbar[par]);
+                for (int q = warp; q < cs; q += NW) pq_st_async(pq_mapa(dst, q), v, pq_mapa(bar, q));
+            }
+            if (!timed_out && !pq_wait(pq_smem(&mbar[par]), (uint32_t)(rnd >> 1) & 1u)) timed_out = true;
+            for (int q = 0; q < cs; q++) {
+                tot1 += gbuf[par][q][lane];
+                tot2 += gbuf[par][q][NB + lane];
+                pj1 += gbuf[par][q][2 * NB + lane];
+                pj2 += gbuf[par][q][3 * NB + lane];
+            }
+        }
+        // reflector kk (row kk+1 added back to its sums)
+        const float alpha1 = __shfl_sync(0xffffffffu, pj1, kk);
+        const float pk1 = __shfl_sync(0xffffffffu, pj2, kk);          // a(kk+1, kk); 0 without a pair
+        const float sp1 = fmaf(pk1, pk1, __shfl_sync(0xffffffffu, tot1, kk));
+        float tau1, beta1, scale1;
+        pair_reflector(alpha1, sp1, tau1, beta1, scale1);
+        const float dot1 = fmaf(scale1, fmaf(pk1, pj2, tot1), pj1);
+        const float coef1 = lane > kk ? tau1 * dot1 : 0.f;
+        // reflector kk+1 from the downdated sums
+        const int k2 = two ? kk + 1 : kk;
+        const float gc = coef1 * scale1;
+        const float g = __shfl_sync(0xffffffffu, gc, k2);
+        const float T11 = __shfl_sync(0xffffffffu, tot1, kk);
+        const float T12 = __shfl_sync(0xffffffffu, tot1, k2);
+        const float T22 = __shfl_sync(0xffffffffu, tot2, k2);
+        const float sp2 = fmaf(g, fmaf(g, T11, -2.f * T12), T22);
+        const bool pair = two && sp2 >= 0.f && sp2 >= PAIR_GUARD * T22;
+        const float p2n = lane == kk ? scale1 * pk1 : (lane > kk ? fmaf(-gc, pk1, pj2) : pj2);
+        float tau2 = 0.f, beta2 = 0.f, scale2 = 0.f, dot2 = 0.f;
+        if (pair) {
+            pair_reflector(__shfl_sync(0xffffffffu, p2n, k2), sp2, tau2, beta2, scale2);
+            float X;
+            if (lane < kk) X = fmaf(-g, tot1, tot2);
+            else if (lane == kk) X = scale1 * fmaf(-g, T11, T12);
+            else X = fmaf(g * gc, T11, fmaf(-g, tot1, fmaf(-gc, T12, tot2)));
+            dot2 = fmaf(scale2, X, p2n);
+        }
+        const float coef2 = (pair && lane > k2) ? tau2 * dot2 : 0.f;
+        coefw[warp][0][lane] = coef1;
+        coefw[warp][1][lane] = coef2;
+        if (warp == 0) {
+            if (lane < kk) G_s[lane][kk] = dot1;
+            if (pair && lane < k2) G_s[lane][k2] = dot2;
+            if (lane == 0) {
+                tau_s[kk] = tau1;
+                if (pair) tau_s[k2] = tau2;
+            }
+        }
+        __syncwarp();
+        const float c1k2 = __shfl_sync(0xffffffffu, coef1, k2);        // coefficient of column kk+1
+        // branch-free updates of the owned rows: reflector kk, then kk+1
+#pragma unroll
+        for (int q = 0; q < RPT; q++) {
+            const bool below1 = rr[q] > kk, piv1 = rr[q] == kk;
+            const float s1 = ak1[q] * scale1;
+            const float f1 = below1 ? s1 : (piv1 ? 1.f : 0.f);
+            const float nk1 = below1 ? s1 : (piv1 ? beta1 : ak1[q]);
+            const float a2 = fmaf(-c1k2, f1, ak2[q]);                  // a(i, kk+1) after reflector kk
+            const bool below2 = rr[q] > k2, piv2 = rr[q] == k2;
+            const float s2 = a2 * scale2;
+            const float f2 = pair ? (below2 ? s2 : (piv2 ? 1.f : 0.f)) : 0.f;
+            const float nk2 = below2 ? s2 : (piv2 ? beta2 : a2);
+#pragma unroll
+            for (int g8 = 0; g8 < NB; g8 += 8) {
+                if (g8 + 7 >= kk) {
+#pragma unroll
+                    for (int c = g8; c < g8 + 8; c++) {
+                        float x = fmaf(-coefw[warp][0][c], f1, a[q][c]);
+                        x = (c == kk) ? nk1 : x;
+                        x = fmaf(-coefw[warp][1][c], f2, x);
+                        a[q][c] = (pair && c == k2) ? nk2 : x;
+                    }
+                }
+            }
+        }
+        kk += pair ? 2 : 1;
+    }
+    __syncthreads();
+
+    float *Aw = A;
+    asm volatile("" : "+l"(Aw));
+#pragma unroll
+    for (int c = 0; c < NB; c++) {
+        if (c < ncols) {
+            float *col = Aw + idx2(j0, j0 + c, lda);
+#pragma unroll
+            for (int q = 0; q < RPT; q++)
+                if (rr[q] >= 0) col[rr[q]] = a[q][c];
+        }
+    }
+    if (crank == 0 && warp == 0) {
+        if (lane < kpanel) tau[j0 + lane] = tau_s[lane];
+        panel_T_from_gram<float, NB, NB + 1>(G_s, tau_s, kpanel, Tw);
+    }
+    if (timed_out) atomicOr(err, 8);
+    if (cs > 1) cluster.sync();
+}
+
+// ---------------------------------------------------------------------------
 // Trailing update / block reflector application (xLARFB, SIMT):
 //   C <- (I - V X V^T) C,  X = Tw^T (trans = 1, applies H_{k-1}..H_0) or
 //   X = Tw (trans = 0, applies H_0..H_{k-1}).
@@ -1068,6 +1320,35 @@ static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+template <int NT, int RPT>
+static int launch_panel_pair(float *A, int lda, int M, int j0, int ncols, float *tau, float *Tw, int *err,
+                             cudaStream_t s)
+{
+    const int L = M - j0;
+    int cs = ceil_div(L, NT * RPT);
+    if (cs < 1) cs = 1;
+    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
+    const int chunk = ceil_div(L, cs);
+    auto kern = k_panel_qr_pair<NT, RPT>;
+    static PerDeviceOnce once;
+    once([&] { cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1); });
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ProfScope ps(K_PANEL, s);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, A, lda, M, j0, ncols, chunk, tau, Tw, err);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
 template <int NT>
 static int launch_panel2(float *A, int lda, int M, int j0, int ncols, float *tau, float *Tw, int *err, cudaStream_t s)
 {
@@ -1110,7 +1391,9 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
         if (L <= 16 * 64) return launch_panel2<128>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 128) return launch_panel2<256>(A, lda, M, j0, ncols, tau, Tw, err, s);
         if (L <= 16 * 256) return launch_panel2<512>(A, lda, M, j0, ncols, tau, Tw, err, s);
-        if (L <= 16 * 512) return launch_panel_shape<T, 512, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        // taller panels: one message round per column pair
+        if (L <= 16 * 512) return launch_panel_pair<512, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        return launch_panel_pair<512, 2>(A, lda, M, j0, ncols, tau, Tw, err, s);
     }
     return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, s);
 }
