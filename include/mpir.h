@@ -175,6 +175,32 @@ int gls_solve(mpir_handle h, int n, int m, int p,
               const mpir_opts *opts, mpir_info *info);
 
 /* ---------------------------------------------------------------------
+ * Complex LSE / GLS: the problems above over C (Sec. 1), with conjugate
+ * transposes (A^H r = B^H v; y = V^H z, W^H z = 0).  Every complex array is
+ * double complex in the interleaved (re, im) layout of cuDoubleComplex /
+ * std::complex<double>, column-major, with leading dimensions counted in
+ * complex elements; the pointers are typed double * (two doubles per
+ * entry).  Dimension rules, return codes and options as lse_solve /
+ * gls_solve.
+ * Algorithm: the real 2 x 2 block embedding E(Z) = [Re Z, -Im Z; Im Z,
+ * Re Z] (an isometry C^k -> R^2k that maps Z^H to E(Z)^T and keeps every
+ * singular value) turns the problem into the real one of twice the
+ * dimensions with solution [Re x; Im x]; that problem runs the real path
+ * (GRQ / GQR, classical or GMRES-IR, escalation).  The handle allocates the
+ * embedded copy (16 (mn + pn) + O(m + n + p) bytes for zlse_solve) when it
+ * grows; the call synchronizes the handle's stream before returning.
+ * ------------------------------------------------------------------- */
+int zlse_solve(mpir_handle h, int m, int n, int p,
+               const double *A, int lda, const double *B, int ldb,
+               const double *b, const double *d,
+               double *x, double *r, double *v,
+               const mpir_opts *opts, mpir_info *info);
+int zgls_solve(mpir_handle h, int n, int m, int p,
+               const double *W, int ldw, const double *V, int ldv,
+               const double *d, double *x, double *y, double *z,
+               const mpir_opts *opts, mpir_info *info);
+
+/* ---------------------------------------------------------------------
  * Batched solves of independent problems of uneven sizes.  All size, ld
  * and pointer arrays are HOST arrays of length `count`; the matrices and
  * vectors they point to are device memory.  infos (host, count entries,

@@ -16,7 +16,7 @@ LIB = os.path.join(OUT, "libmpir.so")
 INCLUDE = os.path.join(ROOT, "include")
 SOURCES = ["qr.cu", "gemm_tc.cu", "vec.cu", "wyapply.cu", "trsv64.cu", "resid.cu", "gmres.cu", "batched.cu",
            "batched_f32_g512.cu", "batched_f32_g256.cu", "batched_f32_g128.cu", "batched_f32_g64.cu",
-           "batched_f64_g512.cu", "batched_f64_g128.cu", "selector.cu", "solver.cu", "noalloc.cu"]
+           "batched_f64_g512.cu", "batched_f64_g128.cu", "selector.cu", "solver.cu", "noalloc.cu", "complex.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -170,6 +170,12 @@ void vaxpy(const Ts *src, double *dst, int n, double scale, int rev, cudaStream_
            const double *dscale = nullptr);
 void vzero(void *dst, size_t bytes, cudaStream_t s);
 
+// Real 2 x 2 block embedding of complex arrays (complex.cu): interleaved
+// (re, im) input, leading dimensions in complex elements.
+int zembed_mat(const double *Z, int rows, int cols, int ldz, double *out, int ldo, cudaStream_t s);
+int zembed_vec(const double *z, int n, double *out, cudaStream_t s);
+int zunembed_vec(const double *in, int n, double *z, cudaStream_t s);
+
 // Matrix conversion with optional transpose and index reversal:
 //   dst(i, j) = (Td)(scale * src(ri, ci)),  i < rows_d, j < cols_d,
 // transpose = 0: (ri, ci) = (i', j');  transpose = 1: (ri, ci) = (j', i'),

@@ -309,6 +309,8 @@ struct mpir_ctx {
     cudaEvent_t sw_ev = nullptr;         // orders a stream switch after queued work
     void *rws = nullptr;         // scratch of the standalone residual entry points
     size_t rws_bytes = 0;
+    double *zbuf = nullptr;      // real embedding of a complex problem (zlse_solve / zgls_solve)
+    size_t zbuf_bytes = 0;
     BatchArena ba;               // batched solves: tables, results, tuned shapes, graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     // device-side classical refinement loop: the captured graph (a CUDA-graph
@@ -431,6 +433,23 @@ int ensure_ws(mpir_ctx *h, size_t bytes)
     if (cudaMalloc(&h->ws, bytes) != cudaSuccess) { cudaGetLastError(); return set_err(h, MPIR_CUDA_ERROR, "workspace cudaMalloc failed"); }
     h->ws_bytes = bytes;
     h->ws_owned = true;
+    return 0;
+}
+
+int ensure_zbuf(mpir_ctx *h, size_t bytes)
+{
+    if (h->zbuf_bytes >= bytes) return 0;
+    if (h->zbuf) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->zbuf);
+        h->zbuf = nullptr;
+        h->zbuf_bytes = 0;
+    }
+    if (cudaMalloc(&h->zbuf, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return set_err(h, MPIR_CUDA_ERROR, "complex embedding cudaMalloc failed");
+    }
+    h->zbuf_bytes = bytes;
     return 0;
 }
 
@@ -2004,6 +2023,7 @@ int mpir_destroy(mpir_handle h)
     if (h->ws && h->ws_owned) cudaFree(h->ws);
     if (h->scratch_base) cudaFree(h->scratch_base);
     if (h->rws) cudaFree(h->rws);
+    if (h->zbuf) cudaFree(h->zbuf);
     if (h->hbuf) cudaFreeHost(h->hbuf);
     {
         BatchArena &a = h->ba;
@@ -2322,6 +2342,62 @@ int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, cons
         esc++;
     }
     if (info) info->escalated = esc;
+    return st;
+}
+
+// Complex LSE / GLS (the problems of Sec. 1 over C) through the real 2 x 2
+// block embedding E(Z) = [Re Z, -Im Z; Im Z, Re Z] (complex.cu): the
+// embedded problem has the same solution (as [Re; Im]), the same singular
+// values and the same stop-test quantities, and runs the real path.
+int zlse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, const double *B, int ldb,
+               const double *b, const double *d, double *x, double *r, double *v, const mpir_opts *opts,
+               mpir_info *info)
+{
+    if (!h) return -1;
+    int a = lse_check_args(m, n, p, A, lda, B, ldb, b, d, x);
+    if (a) return set_err(h, a, "illegal argument");
+    const int M = 2 * m, N = 2 * n, P = 2 * p;
+    const size_t words = (size_t)M * N + (size_t)P * N + (size_t)2 * M + (size_t)2 * P + N;
+    RC(ensure_zbuf(h, sizeof(double) * std::max<size_t>(words, 1)));
+    double *Ah = h->zbuf, *Bh = Ah + (size_t)M * N, *bh = Bh + (size_t)P * N, *dh = bh + M, *xh = dh + P;
+    double *rh = xh + N, *vh = rh + M;
+    cudaStream_t s = h->stream;
+    RC(zembed_mat(A, m, n, lda, Ah, std::max(M, 1), s));
+    RC(zembed_mat(B, p, n, ldb, Bh, std::max(P, 1), s));
+    RC(zembed_vec(b, m, bh, s));
+    RC(zembed_vec(d, p, dh, s));
+    const int st = lse_solve(h, M, N, P, Ah, std::max(M, 1), p > 0 ? Bh : nullptr, std::max(P, 1), bh,
+                             p > 0 ? dh : nullptr, xh, r ? rh : nullptr, (v && p > 0) ? vh : nullptr, opts, info);
+    if (st < 0 || st == MPIR_CUDA_ERROR) return st;
+    RC(zunembed_vec(xh, n, x, s));
+    if (r) RC(zunembed_vec(rh, m, r, s));
+    if (v && p > 0) RC(zunembed_vec(vh, p, v, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "zlse_solve");
+    return st;
+}
+
+int zgls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, const double *V, int ldv,
+               const double *d, double *x, double *y, double *z, const mpir_opts *opts, mpir_info *info)
+{
+    if (!h) return -1;
+    int a = gls_check_args(n, m, p, W, ldw, V, ldv, d, x, y);
+    if (a) return set_err(h, a, "illegal argument");
+    const int Nn = 2 * n, M = 2 * m, P = 2 * p;
+    const size_t words = (size_t)Nn * M + (size_t)Nn * P + (size_t)2 * Nn + M + P;
+    RC(ensure_zbuf(h, sizeof(double) * std::max<size_t>(words, 1)));
+    double *Wh = h->zbuf, *Vh = Wh + (size_t)Nn * M, *dh = Vh + (size_t)Nn * P, *xh = dh + Nn, *yh = xh + M;
+    double *zh = yh + P;
+    cudaStream_t s = h->stream;
+    RC(zembed_mat(W, n, m, ldw, Wh, Nn, s));
+    RC(zembed_mat(V, n, p, ldv, Vh, Nn, s));
+    RC(zembed_vec(d, n, dh, s));
+    const int st = gls_solve(h, Nn, M, P, m > 0 ? Wh : nullptr, Nn, Vh, Nn, dh, xh, yh, z ? zh : nullptr, opts,
+                             info);
+    if (st < 0 || st == MPIR_CUDA_ERROR) return st;
+    RC(zunembed_vec(xh, m, x, s));
+    RC(zunembed_vec(yh, p, y, s));
+    if (z) RC(zunembed_vec(zh, n, z, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "zgls_solve");
     return st;
 }
 

@@ -58,6 +58,10 @@ _SIG = {
                    ctypes.POINTER(Info)], _I),
     "gls_solve": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, ctypes.POINTER(Opts),
                    ctypes.POINTER(Info)], _I),
+    "zlse_solve": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                    ctypes.POINTER(Info)], _I),
+    "zgls_solve": ([_P, _I, _I, _I, _P, _I, _P, _I, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                    ctypes.POINTER(Info)], _I),
     "lse_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
                            ctypes.POINTER(Info)], _I),
     "gls_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
@@ -151,7 +155,7 @@ def exported_symbols():
     return list(_SIG.keys())
 
 
-_CTYPE = {"f64": "torch.float64", "f32": "torch.float32", "i32": "torch.int32"}
+_CTYPE = {"f64": "torch.float64", "f32": "torch.float32", "i32": "torch.int32", "c128": "torch.complex128"}
 
 
 def ptr(t, ctype="f64"):
@@ -386,6 +390,27 @@ class Handle:
         rc = lib().gls_solve(self.h, n, m, p, ptr(W), ld(W), ptr(V), ld(V), ptr(d), ptr(x), ptr(y),
                              ptr(z), ctypes.byref(o), ctypes.byref(info))
         return self.check(rc, "gls_solve"), info
+
+    def zlse_solve(self, A, B, b, d, x, r=None, v=None, opts=None):
+        """Complex LSE: complex128 device tensors, A and B column-major."""
+        m, n = A.shape
+        p = B.shape[0]
+        info = Info()
+        o = opts if opts is not None else make_opts()
+        rc = lib().zlse_solve(self.h, m, n, p, ptr(A, "c128"), ld(A), ptr(B, "c128"), ld(B) if p else 1,
+                              ptr(b, "c128"), ptr(d, "c128"), ptr(x, "c128"), ptr(r, "c128"), ptr(v, "c128"),
+                              ctypes.byref(o), ctypes.byref(info))
+        return self.check(rc, "zlse_solve"), info
+
+    def zgls_solve(self, W, V, d, x, y, z=None, opts=None):
+        """Complex GLS: complex128 device tensors, W and V column-major."""
+        n, m = W.shape
+        p = V.shape[1]
+        info = Info()
+        o = opts if opts is not None else make_opts()
+        rc = lib().zgls_solve(self.h, n, m, p, ptr(W, "c128"), ld(W), ptr(V, "c128"), ld(V), ptr(d, "c128"),
+                              ptr(x, "c128"), ptr(y, "c128"), ptr(z, "c128"), ctypes.byref(o), ctypes.byref(info))
+        return self.check(rc, "zgls_solve"), info
 
     # ---- step-level ---------------------------------------------------------
     def lse_factor(self, A, B, fact="fp32"):

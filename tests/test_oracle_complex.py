@@ -311,3 +311,43 @@ def test_complex_gmres_ir_beyond_the_classical_limit():
     out = Z.zgls_gmres_ir(G["W"], G["V"], G["d"])
     met = Z.zgls_metrics(G["W"], G["V"], G["d"], out["x"], out["y"], out["z"])
     assert out["status"] == 0 and met["eta"] < 1e-14
+
+
+# --------------------------------------------------------- real embedding --
+
+def _embed(Z):
+    Z = np.asarray(Z)
+    return np.block([[Z.real, -Z.imag], [Z.imag, Z.real]])
+
+
+@pytest.mark.parametrize("m,n,p", [(30, 12, 4), (20, 20, 6), (9, 10, 5)])
+def test_lse_real_embedding_has_the_complex_solution(m, n, p):
+    """The GPU solves a complex LSE as the real LSE of E(Z) = [Re Z, -Im Z;
+    Im Z, Re Z]: the real oracle's solution of the embedded problem is
+    [Re x; Im x], [Re r; Im r], [Re v; Im v] of the complex oracle's (both
+    plain KKT definitions), and E keeps the singular values (each twice)."""
+    import oracle
+    from oracle import zoracle as Z
+    P = I.zlse_svd(m + n + p, m, n, p, 1e3, 1e1)
+    A, B, b, d = P["A"], P["B"], P["b"], P["d"]
+    t = Z.zlse_truth(A, B, b, d)
+    e = oracle.lse_truth(_embed(A), _embed(B), np.concatenate([b.real, b.imag]), np.concatenate([d.real, d.imag]))
+    assert rel(e["x"], np.concatenate([t["x"].real, t["x"].imag])) < 1e-12
+    assert rel(e["r"], np.concatenate([t["r"].real, t["r"].imag])) < 1e-12
+    assert rel(e["v"], np.concatenate([t["v"].real, t["v"].imag])) < 1e-12
+    sv = np.linalg.svd(A, compute_uv=False)
+    assert np.allclose(np.linalg.svd(_embed(A), compute_uv=False), np.repeat(sv, 2), rtol=1e-12)
+
+
+@pytest.mark.parametrize("n,m,p", [(20, 8, 25), (12, 12, 12), (15, 9, 10)])
+def test_gls_real_embedding_has_the_complex_solution(n, m, p):
+    import oracle
+    from oracle import zoracle as Z
+    G = I.zgls_svd(n + m + p, n, m, p, 1e2, 1e1)
+    W, V, d = G["W"], G["V"], G["d"]
+    t = Z.zgls_truth(W, V, d)
+    e = oracle.gls_truth(_embed(W), _embed(V), np.concatenate([d.real, d.imag]))
+    assert rel(e["x"], np.concatenate([t["x"].real, t["x"].imag])) < 1e-12
+    ty = np.concatenate([t["y"].real, t["y"].imag])
+    # (m = n: y = 0 up to rounding, so measure against the size of the solution)
+    assert np.linalg.norm(e["y"] - ty) <= 1e-12 * max(np.linalg.norm(ty), np.linalg.norm(t["x"]))
