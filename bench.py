@@ -63,6 +63,11 @@ def parse():
                     help="time the headline solve only (for profiler runs)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the cond(A) sweep")
     ap.add_argument("--no-gls", action="store_true", help="skip the GLS n=4096 workload")
+    ap.add_argument("--no-paper-shapes", action="store_true", help="skip the Sec. 6.2 / 6.3 shape sweep")
+    ap.add_argument("--paper-shapes-full", action="store_true",
+                    help="every Sec. 6.2 / 6.3 shape and conditioning (default: the corners)")
+    ap.add_argument("--paper-shapes-only", action="store_true",
+                    help="run only the Sec. 6.2 / 6.3 shape sweep (prints its JSON object)")
     ap.add_argument("--batched-count", type=int, default=10000,
                     help="problems of the uneven batched LSE workload (0: skip it)")
     ap.add_argument("--batched-gls-count", type=int, default=4000,
@@ -756,6 +761,114 @@ def run_gls(h, dev, stream, rank, steps):
     return out
 
 
+PAPER_LSE1 = [(n, m_f * n, n // p_d) for n in (1024, 2048, 3072) for (m_f, p_d) in
+              ((8, 32), (8, 64), (10, 32), (10, 64), (12, 32), (12, 64))]
+PAPER_LSE2 = [(n, m_f * n, n // p_d) for n in (128, 192, 256) for (m_f, p_d) in
+              ((128, 8), (128, 4), (128, 2), (256, 8), (256, 4), (256, 2))]
+PAPER_GLS = [(n, n // m_d, p_f * n) for n in (1024, 2048, 3072) for (p_f, m_d) in
+             ((8, 32), (8, 64), (10, 32), (10, 64), (12, 32), (12, 64))]
+
+
+def paper_shape_list(full):
+    """The Sec. 6.2 / 6.3 shapes (all of them with `full`; else the corners:
+    n in {1024, 2048} (LSE m > n >> p, GLS) and {128, 256} (LSE m >> n > p),
+    the smallest and largest aspect ratios, two conditionings)."""
+    if full:
+        lse1 = [(s, k) for s in PAPER_LSE1 for k in (1e3, 1e5, 1e7, 1e9)]
+        lse2 = [(s, 1e5) for s in PAPER_LSE2]
+        gls = [(s, k) for s in PAPER_GLS for k in (1e3, 1e5, 1e7, 1e9)]
+        return lse1, lse2, gls
+    lse1 = [((n, m, p), k) for (n, m, p) in PAPER_LSE1 if n in (1024, 2048) and (m, p) in
+            ((8 * n, n // 32), (12 * n, n // 64)) for k in (1e3, 1e7)]
+    lse2 = [((n, m, p), 1e5) for (n, m, p) in PAPER_LSE2 if n in (128, 256) and (m, p) in
+            ((128 * n, n // 8), (256 * n, n // 2))]
+    gls = [((n, m, p), k) for (n, m, p) in PAPER_GLS if n in (1024, 2048) and (p, m) in
+           ((8 * n, n // 32), (12 * n, n // 64)) for k in (1e3, 1e7)]
+    return lse1, lse2, gls
+
+
+def run_paper_shapes(h, dev, stream, full=False):
+    """Timed sweep over the paper's test shapes (Sec. 6.2: LSE m > n >> p and
+    m >> n > p; Sec. 6.3: GLS p >> n > m) with its matrix construction
+    ([A^T, B^T] resp. [W, V] = W1 Sigma W2, geometric Sigma): FP32 factors
+    with classical IR and with GMRES-IR (block-diagonal split preconditioner),
+    against the FP64 factorization with FP64 classical IR on the same GPU
+    (the paper's comparison is against xGGLSE / xGGGLM, also FP64).  Each
+    entry: ms, status, refinement steps, the library's backward error
+    (eq. lse-stop / gls-stop ratios) and x's relative distance to the FP64
+    solution; speedup = t_fp64 / t_mixed."""
+    import torch
+    from paper_2406_16499_gb300 import inputs as I, mpir
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        fn()
+        ts, out = [], None
+        for _ in range(k):
+            torch.cuda.synchronize()
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2], out
+
+    def entry(ms, st, info):
+        return {"ms": round(ms, 3), "status": st, "iters": info.iters, "inner_iters": info.inner_iters,
+                "escalated": info.escalated, "eta": max(info.stop_ratio)}
+
+    lse1, lse2, gls = paper_shape_list(full)
+    rows = []
+
+    def guarded(row, fn):
+        try:
+            fn(row)
+        except mpir.MpirError as e:                 # record it, keep the sweep going
+            row["error"] = str(e)
+        rows.append(row)
+
+    def fill(row, solve, x, x64):
+        ms, (st, info) = timed(lambda: solve(mpir.make_opts(fact="fp32"), x), 2)
+        row["fp32_classical"] = entry(ms, st, info)
+        ms, (st, info) = timed(lambda: solve(mpir.make_opts(fact="fp32", refine="gmres", escalate=False), x), 1)
+        row["fp32_gmres"] = entry(ms, st, info)
+        ms64, (st, info) = timed(lambda: solve(mpir.make_opts(fact="fp64"), x64), 1)
+        row["fp64_classical"] = entry(ms64, st, info)
+        solve(mpir.make_opts(fact="fp32"), x)
+        row["x_vs_fp64"] = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+        row["speedup_classical"] = ms64 / row["fp32_classical"]["ms"]
+        row["speedup_gmres"] = ms64 / row["fp32_gmres"]["ms"]
+
+    for case, lst in (("lse m>n>>p", lse1), ("lse m>>n>p", lse2)):
+        for (n, m, p), kap in lst:
+            P = I.lse_paper_torch(hash((m, n, p, kap)) & 0xFFFFFFFF, m, n, p, kap, dev)
+            x = torch.zeros(n, dtype=torch.float64, device=dev)
+            x64 = torch.zeros(n, dtype=torch.float64, device=dev)
+
+            def solve(o, out):
+                return h.lse_solve(P["A"], P["B"], P["b"], P["d"], out, None, None, o)
+
+            guarded({"case": case, "m": m, "n": n, "p": p, "kappa": kap}, lambda row: fill(row, solve, x, x64))
+            del P
+    for (n, m, p), kap in gls:
+        G = I.gls_paper_torch(hash((n, m, p, kap)) & 0xFFFFFFFF, n, m, p, kap, dev)
+        x = torch.zeros(m, dtype=torch.float64, device=dev)
+        y = torch.zeros(p, dtype=torch.float64, device=dev)
+        x64 = torch.zeros(m, dtype=torch.float64, device=dev)
+
+        def gsolve(o, out):
+            return h.gls_solve(G["W"], G["V"], G["d"], out, y, None, o)
+
+        guarded({"case": "gls p>>n>m", "n": n, "m": m, "p": p, "kappa": kap}, lambda row: fill(row, gsolve, x, x64))
+        del G
+    torch.cuda.empty_cache()
+    return {"what": "Sec. 6.2 / 6.3 test shapes, FP32 factors (classical IR, GMRES-IR) vs FP64 factors, same GPU",
+            "construction": "[A^T, B^T] (LSE) / [W, V] (GLS) = W1 Sigma W2, geometric Sigma with the given kappa_2, "
+                            "Haar factors drawn on the GPU",
+            "full": bool(full), "rows": rows}
+
+
 def pick_roofline(prof, kp, work, iters, peaks, sms, clk):
     """Roofline of the kernel kind with the largest device time per solve
     (achieved = the algorithmic work of its launches / their summed CUDA-event
@@ -802,6 +915,12 @@ def run_ours(args):
     h = mpir.Handle(local, stream.cuda_stream)
     if args.batched_only:
         res = run_batched(args.batched_count, h, dev, stream, rank)
+        if rank == 0:
+            print(json.dumps(res), flush=True)
+        h.close()
+        return 0
+    if args.paper_shapes_only:
+        res = run_paper_shapes(h, dev, stream, args.paper_shapes_full)
         if rank == 0:
             print(json.dumps(res), flush=True)
         h.close()
@@ -937,6 +1056,9 @@ def run_ours(args):
 
     # ---- the GLS n = 4096 workload and the batched uneven LSE -------------
     gls = None if args.no_gls else run_gls(h, dev, stream, rank, max(3, min(args.steps, 10)))
+    paper_shapes = None
+    if not args.no_paper_shapes and world == 1:
+        paper_shapes = run_paper_shapes(h, dev, stream, args.paper_shapes_full)
     batched = None
     if args.batched_count > 0 and world == 1:
         batched = run_batched(args.batched_count, h, dev, stream, rank)
@@ -1002,6 +1124,7 @@ def run_ours(args):
             "batched_lse": batched,
             "batched_gls": batched_gls,
             "selector": selector,
+            "paper_shapes": paper_shapes,
             "tensor_core_update": tensor,
             "fp64_residual": resid,
             "kernels": kernels,

@@ -141,7 +141,10 @@ int mpir_set_workspace(mpir_handle handle, void *ptr, size_t bytes);
 int mpir_lse_workspace_size(int m, int n, int p, const mpir_opts *opts, size_t *bytes);
 int mpir_gls_workspace_size(int n, int m, int p, const mpir_opts *opts, size_t *bytes);
 
-/* Last error message of this handle (static storage, never NULL). */
+/* Last error message of this handle (static storage, never NULL).  When a
+ * call returned MPIR_UNSUPPORTED because a size or launch-shape limit of a
+ * kernel refused it, and nothing more specific was recorded, the message is
+ * that limit's source location (file:line). */
 const char *mpir_last_error(mpir_handle handle);
 
 /* ---------------------------------------------------------------------

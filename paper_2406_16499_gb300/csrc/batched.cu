@@ -52,7 +52,7 @@ int batched_launch(const BConfig &c, bool fp64, const BInst *tab, const int *ord
         switch (c.group) {
         case 512: return batched_launch_f64_g512(tab, order, count, next, res, gscr, gstride, c.smem, grid, prm, s);
         case 128: return batched_launch_f64_g128(tab, order, count, next, res, gscr, gstride, c.smem, grid, prm, s);
-        default: return MPIR_UNSUPPORTED;
+        default: return MPIR_UNSUP();
         }
     }
     switch (c.group) {
@@ -60,7 +60,7 @@ int batched_launch(const BConfig &c, bool fp64, const BInst *tab, const int *ord
     case 256: return batched_launch_f32_g256(tab, order, count, next, res, gscr, gstride, c.smem, grid, prm, s);
     case 128: return batched_launch_f32_g128(tab, order, count, next, res, gscr, gstride, c.smem, grid, prm, s);
     case 64: return batched_launch_f32_g64(tab, order, count, next, res, gscr, gstride, c.smem, grid, prm, s);
-    default: return MPIR_UNSUPPORTED;
+    default: return MPIR_UNSUP();
     }
 }
 

@@ -14,6 +14,18 @@ namespace mpir {
 
 namespace cg = cooperative_groups;
 
+// Where the last MPIR_UNSUPPORTED of this host thread came from (a launch
+// shape or size limit of a kernel's host code); the public entry points put
+// it into the handle's message when nothing more specific was recorded.
+inline const char *&unsupported_where()
+{
+    static thread_local const char *where = nullptr;
+    return where;
+}
+#define MPIR_STR2(x) #x
+#define MPIR_STR(x) MPIR_STR2(x)
+#define MPIR_UNSUP() (::mpir::unsupported_where() = __FILE__ ":" MPIR_STR(__LINE__), MPIR_UNSUPPORTED)
+
 // Function attributes (dynamic shared-memory limit, non-portable cluster
 // size) belong to the device that is current when they are set.  A launcher
 // keeps one of these per kernel and passes it the set-up: it runs the first

@@ -457,7 +457,7 @@ int tmap_colmajor(CUtensorMap *tm, const float *base, long rows, long cols, long
 {
     auto fn = encode_fn();
     if (!fn) return MPIR_CUDA_ERROR;
-    if (((uintptr_t)base & 15) || (ld * 4) % 16) return MPIR_UNSUPPORTED;
+    if (((uintptr_t)base & 15) || (ld * 4) % 16) return MPIR_UNSUP();
     cuuint64_t gdim[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
     cuuint64_t gstr[1] = {(cuuint64_t)ld * 4};
     cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_cols};

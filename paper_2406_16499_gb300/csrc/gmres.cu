@@ -168,7 +168,7 @@ static int arnoldi_step(GmresWs &w, int j, cudaStream_t s)
     const int slice = ceil_div(w.N, ncta);
     ncta = ceil_div(w.N, slice);
     const size_t smem = (size_t)slice * sizeof(double);
-    if (smem > 160 * 1024) return MPIR_UNSUPPORTED;
+    if (smem > 160 * 1024) return MPIR_UNSUP();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ncta, 1, 1);
     cfg.blockDim = dim3(AR_THREADS, 1, 1);
@@ -279,7 +279,7 @@ int gmres_solve(LinOp &op, const double *rhs, double *x, GmresWs &w, double tol,
                 cudaStream_t s, int *iters, double *rel_out)
 {
     const int N = w.N, R = w.R;
-    if (R < 1 || R > GMRES_MAX_RESTART) return MPIR_UNSUPPORTED;
+    if (R < 1 || R > GMRES_MAX_RESTART) return MPIR_UNSUP();
     *iters = 0;
     *rel_out = 0.0;
     cudaMemsetAsync(x, 0, sizeof(double) * N, s);

@@ -68,7 +68,7 @@ extern "C" int mpir_gls_residual_noalloc(int n, int m, int p, const double *W, i
     const DualGemvPlan pw = dual_gemv_plan(n, m), pv = dual_gemv_plan(n, p);
     const size_t need = (size_t)pw.ncb * n + (size_t)pw.nrb * m + (size_t)pv.ncb * n + (size_t)pv.nrb * p +
                         304 * 6 + 8;
-    if (need > NOALLOC_SCRATCH_DOUBLES) return MPIR_UNSUPPORTED;
+    if (need > NOALLOC_SCRATCH_DOUBLES) return MPIR_UNSUP();
     double *base = nullptr;
     if (noalloc_scratch(&base)) return MPIR_CUDA_ERROR;
     double *pWx = base;

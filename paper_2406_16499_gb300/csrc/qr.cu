@@ -505,6 +505,168 @@ k_panel_qr2(float *__restrict__ A, int lda, int M, int j0, int ncols, int chunk,
 }
 
 // ---------------------------------------------------------------------------
+// Panels taller than one 16-CTA cluster holds (the row chunks of
+// k_panel_qr on more CTAs than a cluster allows): the same column step with
+// the cluster message replaced by a global-memory exchange.  Each CTA
+// writes its partial sums and its part of the pivot row to gx (two parity
+// slots of gridDim.x x 2 NB), a bounded grid barrier follows (cooperative
+// launch: all CTAs are resident), and every CTA sums the slots in rank
+// order (L2 reads), so all CTAs hold bitwise the same column totals.
+// ---------------------------------------------------------------------------
+struct PanelGrid {
+    void *gx;               // 2 x PANEL_GRID_MAX x 2 NB elements of the panel type
+    unsigned int *bar;      // grid barrier: [0] arrivals (zero between launches), [1] generation
+};
+constexpr int PANEL_GRID_MAX = 160;              // CTAs (one per SM)
+
+template <typename T, int NB, int NT, int RPT>
+__global__ void __launch_bounds__(NT, 1)
+k_panel_qr_grid(T *__restrict__ A, int lda, int M, int j0, int ncols, int chunk, T *__restrict__ tau,
+                T *__restrict__ Tw, int *__restrict__ err, T *__restrict__ gx, GridBarrier gb)
+{
+    constexpr int NW = NT / 32;
+    const int G = (int)gridDim.x, rank = (int)blockIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int L = M - j0;
+    const int kpanel = min(ncols, L);
+    __shared__ T red_s[2][NW][32];
+    __shared__ T rsum[NW][2][32];
+    __shared__ T prow[2][NB];
+    __shared__ __align__(16) T coefw[NW][NB];
+    __shared__ T G_s[NB][NB + 1];
+    __shared__ T tau_s[NB];
+
+    const int row_base = rank * chunk;
+    const int row_end = min(row_base + chunk, L);
+    bool timed_out = false;
+    for (int e = tid; e < NB * (NB + 1); e += NT) (&G_s[0][0])[e] = T(0);
+    int rr[RPT];
+    T a[RPT][NB];
+#pragma unroll
+    for (int q = 0; q < RPT; q++) {
+        const int r = row_base + tid + q * NT;
+        rr[q] = r < row_end ? r : -1;
+    }
+#pragma unroll
+    for (int c = 0; c < NB; c++) {
+        const T *col = A + idx2(j0, j0 + c, lda);
+#pragma unroll
+        for (int q = 0; q < RPT; q++) a[q][c] = (rr[q] >= 0 && c < ncols) ? col[rr[q]] : T(0);
+    }
+#pragma unroll 1
+    for (int kk = 0; kk < kpanel; kk++) {
+        const int par = kk & 1;
+        T akk[RPT];
+#pragma unroll
+        for (int q = 0; q < RPT; q++) akk[q] = pq_select<T, NB>(a[q], kk);
+        constexpr int H = NB > 16 ? 16 : NB;
+#pragma unroll
+        for (int h0 = 0; h0 < NB; h0 += H) {
+            T acc[H];
+#pragma unroll
+            for (int c = 0; c < H; c++) acc[c] = T(0);
+#pragma unroll
+            for (int q = 0; q < RPT; q++) {
+                const T ak = rr[q] > kk ? akk[q] : T(0);
+#pragma unroll
+                for (int c = 0; c < H; c++) acc[c] = fma(ak, a[q][h0 + c], acc[c]);
+            }
+            T wsum = warp_transpose_reduce<T, H>(acc);
+            if (lane < H) red_s[par][warp][h0 + lane] = wsum;
+        }
+#pragma unroll
+        for (int q = 0; q < RPT; q++) {
+            if (rr[q] == kk) {
+#pragma unroll
+                for (int c = 0; c < NB; c++) prow[par][c] = a[q][c];
+            }
+        }
+        __syncthreads();
+        T *slot = gx + ((size_t)par * PANEL_GRID_MAX + rank) * 2 * NB;
+        if (warp == 0 && lane < NB) {
+            T t = T(0);
+#pragma unroll
+            for (int w = 0; w < NW; w++) t += red_s[par][w][lane];
+            slot[lane] = t;
+            slot[NB + lane] = rank == 0 ? prow[par][lane] : T(0);
+        }
+        // after a timeout the remaining columns skip the barrier (the error
+        // flag reports the panel; the kernel still ends promptly)
+        if (!timed_out && !grid_sync(gb, (unsigned)G)) timed_out = true;
+        // rank-order sums: warp w takes ranks w, w + NW, ...; then over warps
+        {
+            T t = T(0), pp = T(0);
+            if (lane < NB)
+                for (int q = warp; q < G; q += NW) {
+                    const T *sq = gx + ((size_t)par * PANEL_GRID_MAX + q) * 2 * NB;
+                    t += __ldcg(sq + lane);
+                    pp += __ldcg(sq + NB + lane);
+                }
+            rsum[warp][0][lane] = t;
+            rsum[warp][1][lane] = pp;
+        }
+        __syncthreads();
+        T tot = T(0), pj = T(0);
+        if (lane < NB) {
+#pragma unroll
+            for (int w = 0; w < NW; w++) { tot += rsum[w][0][lane]; pj += rsum[w][1][lane]; }
+        }
+        const T alpha = __shfl_sync(0xffffffffu, pj, kk);
+        const T sp = __shfl_sync(0xffffffffu, tot, kk);
+        T beta, tv, scale;
+        if (sp == T(0)) {
+            tv = T(0); beta = alpha; scale = T(1);
+        } else {
+            const T nrm = sqrt(alpha * alpha + sp);
+            beta = alpha >= T(0) ? -nrm : nrm;
+            tv = (beta - alpha) / beta;
+            scale = T(1) / (alpha - beta);
+        }
+        const T dot = pj + scale * tot;
+        if (lane < NB) coefw[warp][lane] = lane > kk ? tv * dot : T(0);
+        if (warp == 0) {
+            if (lane < kk) G_s[lane][kk] = dot;
+            if (lane == 0) tau_s[kk] = tv;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < RPT; q++) {
+            const bool below = rr[q] > kk, piv = rr[q] == kk;
+            const T sk = akk[q] * scale;
+            const T f = below ? sk : (piv ? T(1) : T(0));
+            const T newk = below ? sk : (piv ? beta : akk[q]);
+#pragma unroll
+            for (int g = 0; g < NB; g += 8) {
+                if (g + 7 >= kk) {
+#pragma unroll
+                    for (int c = g; c < g + 8; c++) {
+                        const T upd = fma(-coefw[warp][c], f, a[q][c]);
+                        a[q][c] = (c == kk) ? newk : upd;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    T *Aw = A;
+    asm volatile("" : "+l"(Aw));
+#pragma unroll
+    for (int c = 0; c < NB; c++) {
+        if (c < ncols) {
+            T *col = Aw + idx2(j0, j0 + c, lda);
+#pragma unroll
+            for (int q = 0; q < RPT; q++)
+                if (rr[q] >= 0) col[rr[q]] = a[q][c];
+        }
+    }
+    if (rank == 0 && warp == 0) {
+        if (lane < kpanel) tau[j0 + lane] = tau_s[lane];
+        panel_T_from_gram<T, NB, NB + 1>(G_s, tau_s, kpanel, Tw);
+    }
+    if (timed_out) atomicOr(err, 8);
+}
+
+// ---------------------------------------------------------------------------
 // FP32 panel with column pairs (k_panel_qr's layout and message protocol,
 // one message round per two columns).  A round for columns kk, kk+1 sums,
 // over the rows below kk+1,
@@ -1298,7 +1460,7 @@ static int launch_panel_shape(T *A, int lda, int M, int j0, int ncols, T *tau, T
     const int L = M - j0;
     int cs = ceil_div(L, NT * RPT);
     if (cs < 1) cs = 1;
-    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
+    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUP();
     const int chunk = ceil_div(L, cs);
     auto kern = k_panel_qr<T, NB, NT, RPT>;
     static PerDeviceOnce once;
@@ -1327,7 +1489,7 @@ static int launch_panel_pair(float *A, int lda, int M, int j0, int ncols, float 
     const int L = M - j0;
     int cs = ceil_div(L, NT * RPT);
     if (cs < 1) cs = 1;
-    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
+    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUP();
     const int chunk = ceil_div(L, cs);
     auto kern = k_panel_qr_pair<NT, RPT>;
     static PerDeviceOnce once;
@@ -1349,13 +1511,40 @@ static int launch_panel_pair(float *A, int lda, int M, int j0, int ncols, float 
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
+template <typename T, int NT, int RPT>
+static int launch_panel_grid(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, int *err, const PanelGrid &pg,
+                             cudaStream_t s)
+{
+    constexpr int NB = panel_nb<T>();
+    int L = M - j0;
+    int G = ceil_div(L, NT * RPT);
+    if (G < 1) G = 1;
+    if (!pg.gx || !pg.bar || G > PANEL_GRID_MAX) return MPIR_UNSUP();
+    auto kern = k_panel_qr_grid<T, NB, NT, RPT>;
+    int per_sm = 0, dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return MPIR_UNSUP();
+    }
+    if (per_sm * sms < G) return MPIR_UNSUP();      // every CTA must be resident (grid barrier)
+    int chunk = ceil_div(L, G);
+    GridBarrier gb{pg.bar, err};
+    T *gx = reinterpret_cast<T *>(pg.gx);
+    void *args[] = {&A, &lda, &M, &j0, &ncols, &chunk, &tau, &Tw, &err, &gx, &gb};
+    ProfScope ps(K_PANEL, s);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, dim3(G), dim3(NT), args, 0, s);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
 template <int NT>
 static int launch_panel2(float *A, int lda, int M, int j0, int ncols, float *tau, float *Tw, int *err, cudaStream_t s)
 {
     const int L = M - j0;
     int cs = ceil_div(L, NT / 2);
     if (cs < 1) cs = 1;
-    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUPPORTED;
+    if (cs > PANEL_MAX_CLUSTER) return MPIR_UNSUP();
     const int chunk = ceil_div(L, cs);
     auto kern = k_panel_qr2<NT>;
     static PerDeviceOnce once;
@@ -1383,8 +1572,11 @@ static int launch_panel2(float *A, int lda, int M, int j0, int ncols, float *tau
 // column steps are latency and issue bound, so fewer rows per SM (more SMs)
 // shorten every step.  FP32 panels of up to 4096 rows hold two threads per
 // row.
+// Panels beyond what 16 CTAs hold (pg: the exchange buffers of the
+// global-memory variant) run on one CTA per 1024 rows with a grid barrier.
 template <typename T>
-static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, int *err, cudaStream_t s)
+static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, int *err, cudaStream_t s,
+                        const PanelGrid *pg = nullptr)
 {
     const int L = M - j0;
     if constexpr (sizeof(T) == 4) {
@@ -1393,9 +1585,12 @@ static int launch_panel(T *A, int lda, int M, int j0, int ncols, T *tau, T *Tw, 
         if (L <= 16 * 256) return launch_panel2<512>(A, lda, M, j0, ncols, tau, Tw, err, s);
         // taller panels: one message round per column pair
         if (L <= 16 * 512) return launch_panel_pair<512, 1>(A, lda, M, j0, ncols, tau, Tw, err, s);
-        return launch_panel_pair<512, 2>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        if (L <= 16 * 1024 || !pg) return launch_panel_pair<512, 2>(A, lda, M, j0, ncols, tau, Tw, err, s);
+        return launch_panel_grid<float, 512, 2>(A, lda, M, j0, ncols, tau, Tw, err, *pg, s);
     }
-    return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, s);
+    if (L <= PANEL_MAX_CLUSTER * PANEL_NT * PANEL_RPT || !pg)
+        return launch_panel_shape<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, s);
+    return launch_panel_grid<T, PANEL_NT, PANEL_RPT>(A, lda, M, j0, ncols, tau, Tw, err, *pg, s);
 }
 
 // Inner update with the CTA's whole row chunk of V and of a 32-column group
@@ -1794,6 +1989,7 @@ struct OuterWs {
     float *V, *Vl, *Vt, *Vtl, *P, *W, *Wl, *G, *GP, *innerP, *innerW;
     int ldv;
     size_t pcap;
+    PanelGrid pg;                        // exchange buffers of the tall-panel variant
 };
 constexpr int GSPLIT = 24;               // split-K of the outer block's Gram matrix
 constexpr int SPLIT_MIN_K = 8;           // K steps (of 32) per split of V^T C, at least
@@ -1821,6 +2017,8 @@ static OuterWs outer_layout(void *base, int M, int N, size_t *bytes)
     w.GP = take((size_t)OUTER_NB * OUTER_NB * GSPLIT);
     w.innerP = take((size_t)ceil_div(M > 0 ? M : 1, INNER_ROWS) * 32 * INNER_MAXC * 2);
     w.innerW = take((size_t)32 * INNER_MAXC * 2);
+    w.pg.gx = take((size_t)2 * PANEL_GRID_MAX * 64);       // 2 NB FP32 or NB FP64 values per CTA and parity
+    w.pg.bar = reinterpret_cast<unsigned int *>(take(64));
     if (bytes) *bytes = (size_t)((off + 1023) & ~(uintptr_t)1023);
     return w;
 }
@@ -1866,7 +2064,7 @@ static int outer_apply_p1(OuterWs &w, int L, float *C, int ldc, int Nc, int mode
     rc |= tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     rc |= tmap_colmajor(&tC, C, L, Nc, ldc, OUTER_NB);
-    if (rc) return MPIR_UNSUPPORTED;
+    if (rc) return MPIR_UNSUP();
     const int ntn = ceil_div(Nc, OUTER_NB);
     const int ksteps = ceil_div(L, 32);
     int nsplit = ceil_div(2 * 152, ntn);
@@ -1899,7 +2097,7 @@ static int outer_apply_p2(OuterWs &w, const float *Tb, int trans, int L, float *
     rc |= tmap_colmajor(&tVtl, split ? w.Vtl : w.Vt, OUTER_NB, L, OUTER_NB, OUTER_NB);
     rc |= tmap_colmajor(&tW, w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
     rc |= tmap_colmajor(&tWl, split ? w.Wl : w.W, OUTER_NB, Nc, OUTER_NB, OUTER_NB);
-    if (rc) return MPIR_UNSUPPORTED;
+    if (rc) return MPIR_UNSUP();
     {
         ProfScope ps(K_LARFB_AUX, s);
         reduce_w(w.P, pl.nsplit, pl.pstride, Tb, trans, Nc, w.W, w.Wl, OUTER_NB, split, s);
@@ -1928,7 +2126,7 @@ static int outer_T(OuterWs &w, const float *Tw32, int L, int nr, float *Tb, int 
     CUtensorMap tV, tVl;
     int rc = tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
     rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
-    if (rc) return MPIR_UNSUPPORTED;
+    if (rc) return MPIR_UNSUP();
     const int ksteps = ceil_div(L, 32);
     int nsplit = ksteps < GSPLIT ? ksteps : GSPLIT;
     if (nsplit < 1) nsplit = 1;
@@ -2080,7 +2278,7 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
         int rc = tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
         rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
         rc |= tmap_colmajor(&tA, A + J0, L, J0, lda, OUTER_NB);
-        if (rc) return MPIR_UNSUPPORTED;
+        if (rc) return MPIR_UNSUP();
         const int ntn = ceil_div(J0, OUTER_NB);
         const int ksteps = ceil_div(L, 32);
         int nsplit = ceil_div(2 * 152, ntn);
@@ -2106,7 +2304,7 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
         if (want < 1) want = 1;
         KC = ceil_div(ceil_div(J0, want), TF_KS) * TF_KS;
         nkc = ceil_div(J0, KC);
-        if ((size_t)ntile * nkc * TF_TILE > w.pcap) return MPIR_UNSUPPORTED;
+        if ((size_t)ntile * nkc * TF_TILE > w.pcap) return MPIR_UNSUP();
         ProfScope ps(K_LARFB_AUX, s);
         k_tfull_prod<<<dim3(ntile, nkc), 256, 0, s>>>(Tf, ldt, w.W, J0, KC, nkc, w.P);
     }
@@ -2118,16 +2316,21 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
 }
 
 template <typename T>
-static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cudaStream_t s, int kmax)
+static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cudaStream_t s, int kmax, void *ws)
 {
     constexpr int NB = panel_nb<T>();
     int k = M < N ? M : N;
     if (kmax >= 0 && kmax < k) k = kmax;
+    OuterWs wo{};
+    if (ws) {
+        wo = outer_layout(ws, M, N, nullptr);
+        cudaMemsetAsync(wo.pg.bar, 0, 2 * sizeof(unsigned int), s);
+    }
     for (int j0 = 0; j0 < k; j0 += NB) {
         const int ncols = k - j0 < NB ? k - j0 : NB;
         const int L = M - j0;
         T *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
-        int rc = launch_panel<T>(A, lda, M, j0, ncols, tau, Twb, err, s);
+        int rc = launch_panel<T>(A, lda, M, j0, ncols, tau, Twb, err, s, ws ? &wo.pg : nullptr);
         if (rc) return rc;
         const int kb = ncols < L ? ncols : L;
         const int Nc = N - j0 - ncols;
@@ -2141,10 +2344,10 @@ static int geqrf_simt(T *A, int lda, int M, int N, T *tau, T *Tw, int *err, cuda
 }
 
 template <>
-int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *, int *err,
-                  cudaStream_t s, const TfullJob *, int kmax)
+int geqrf<double>(double *A, int lda, int M, int N, double *tau, double *Tw, double *, GemmPrec, void *ws,
+                  int *err, cudaStream_t s, const TfullJob *, int kmax)
 {
-    return geqrf_simt<double>(A, lda, M, N, tau, Tw, err, s, kmax);
+    return geqrf_simt<double>(A, lda, M, N, tau, Tw, err, s, kmax, ws);
 }
 
 // Two-level QR, FP32 storage: 32-wide register panels inside 128-wide
@@ -2160,7 +2363,7 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
     constexpr int NB = 32;
     int k = M < N ? M : N;
     if (kmax >= 0 && kmax < k) k = kmax;
-    if (lda % 4) return MPIR_UNSUPPORTED;
+    if (lda % 4) return MPIR_UNSUP();
     const int mode = tc_mode(prec);
     // look-ahead: critical path on tf->crit, wide trailing updates on s
     const bool la = tf && tf->crit && tf->crit != s && tf->la_a && tf->la_b;
@@ -2177,10 +2380,12 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
     cudaStream_t ss = side ? tf->side : cs;
     OuterWs w2 = side ? outer_layout(tf->ws2, M, N, nullptr) : wv[0];
     if (tf && tf->Tf) {
-        if (tf->ldt < k || tf->ldt % 4 || ((uintptr_t)tf->Tf & 15)) return MPIR_UNSUPPORTED;
+        if (tf->ldt < k || tf->ldt % 4 || ((uintptr_t)tf->Tf & 15)) return MPIR_UNSUP();
         if (side) { cudaEventRecord(tf->fork, cs); cudaStreamWaitEvent(ss, tf->fork, 0); }
         cudaMemsetAsync(tf->Tf, 0, (size_t)tf->ldt * k * sizeof(float), ss);
     }
+    cudaMemsetAsync(wv[0].pg.bar, 0, 2 * sizeof(unsigned int), cs);
+    if (la) cudaMemsetAsync(wv[1].pg.bar, 0, 2 * sizeof(unsigned int), cs);
     bool wide_pending = false;
     for (int J0 = 0, b = 0; J0 < k; J0 += OUTER_NB, b++) {
         OuterWs &w = wv[b & 1];
@@ -2191,7 +2396,7 @@ int geqrf<float>(float *A, int lda, int M, int N, float *tau, float *Tw, float *
             const int ncols = J0 + ncolsO - j0 < NB ? J0 + ncolsO - j0 : NB;
             const int Li = M - j0;
             float *Twb = Tw + (size_t)(j0 / NB) * NB * NB;
-            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, err, cs);
+            int rc = launch_panel<float>(A, lda, M, j0, ncols, tau, Twb, err, cs, &w.pg);
             if (rc) return rc;
             const int kb = ncols < Li ? ncols : Li;
             const int nc = J0 + ncolsO - j0 - ncols;
@@ -2276,7 +2481,7 @@ int apply_reflectors_left<float>(const float *V, int ldv, int M, int K, const fl
                                  int trans, float *C, int ldc, int Nc, GemmPrec prec, void *ws, int *err,
                                  cudaStream_t s)
 {
-    if (ldc % 4 || ldv % 4) return MPIR_UNSUPPORTED;
+    if (ldc % 4 || ldv % 4) return MPIR_UNSUP();
     OuterWs w = outer_layout(ws, M, Nc, nullptr);
     const int mode = tc_mode(prec);
     const int nblk = ceil_div(K, OUTER_NB);
@@ -2296,8 +2501,8 @@ int apply_reflectors_left<float>(const float *V, int ldv, int M, int K, const fl
 int larfb_tc(const float *V, int ldv, int M, int K, const float *Tb, int trans, float *C, int ldc, int N,
              GemmPrec prec, void *ws, int *err, cudaStream_t s)
 {
-    if (K > OUTER_NB || K < 0) return MPIR_UNSUPPORTED;
-    if (ldc % 4 || ((uintptr_t)C & 15)) return MPIR_UNSUPPORTED;
+    if (K > OUTER_NB || K < 0) return MPIR_UNSUP();
+    if (ldc % 4 || ((uintptr_t)C & 15)) return MPIR_UNSUP();
     if (K == 0 || M == 0 || N == 0) return 0;
     OuterWs w = outer_layout(ws, M, N, nullptr);
     const int mode = tc_mode(prec);

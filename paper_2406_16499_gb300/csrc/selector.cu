@@ -943,7 +943,7 @@ int features_launch(int kind, int m, int n, int p, const double *A, int lda, con
     V.m = m; V.n = n; V.p = p;
     V.A = A; V.B = B; V.lda = lda; V.ldb = ldb;
     if (kind == 0) { V.R = m + p; V.C = n; } else { V.R = n; V.C = m + p; }
-    if (k < 1 || k > FT_KMAX) return MPIR_UNSUPPORTED;
+    if (k < 1 || k > FT_KMAX) return MPIR_UNSUP();
     // shared-memory variant while the stacked matrix fits in a cluster
     static PerDeviceOnce once_sm;
     static size_t sm_limit = 0;
@@ -988,7 +988,7 @@ int features_launch(int kind, int m, int n, int p, const double *A, int lda, con
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
     });
     smem = (size_t)3 * V.C * sizeof(float);
-    if (smem > 160 * 1024) return MPIR_UNSUPPORTED;
+    if (smem > 160 * 1024) return MPIR_UNSUP();
     const double elems = (double)V.R * V.C;
     int wantg = std::max(1, std::min(16, (int)(elems / 262144.0) + 1));
     const int cs = cluster_size_for((const void *)kern, FT_THREADS, smem, wantg);
@@ -1196,7 +1196,7 @@ int mlp_forward(const float *P, const float *X, int count, float *prob, cudaStre
 int mlp_train_step(float *P, float *M, float *Vv, int t, float lr, const float *X, const int *y, int count,
                    float *ws, float *grad_out, float *loss_out, cudaStream_t s)
 {
-    if (count <= 0 || t < 1) return MPIR_UNSUPPORTED;
+    if (count <= 0 || t < 1) return MPIR_UNSUP();
     float *acts = ws, *lossv = acts + (size_t)count * ACT, *grad = lossv + count;
     if (grad_out) grad = grad_out;
     const int grid = std::min(ceil_div(count, MLP_THREADS / 32), 1216);

@@ -341,6 +341,7 @@ namespace {
 int set_err(mpir_ctx *h, int code, const char *msg)
 {
     if (h) h->err = msg ? msg : "";
+    unsupported_where() = nullptr;
     return code;
 }
 
@@ -2100,7 +2101,11 @@ int mpir_set_workspace(mpir_handle h, void *ptr, size_t bytes)
 const char *mpir_last_error(mpir_handle h)
 {
     static const char *none = "";
-    return h ? h->err.c_str() : none;
+    if (!h) return none;
+    // a size or launch-shape limit inside a kernel's host code records only
+    // its source location
+    if (h->err.empty() && unsupported_where()) return unsupported_where();
+    return h->err.c_str();
 }
 
 int mpir_lse_workspace_size(int m, int n, int p, const mpir_opts *opts, size_t *bytes)

@@ -135,7 +135,7 @@ int apply_reflectors_vec(const T *V, int ldv, int M, int K, const T *Tw, int tra
     }
     slice = ceil_div(M, G);
     smem = (size_t)slice * sizeof(T);
-    if ((size_t)2 * G * NB * sizeof(T) > sc.part_bytes || smem > 200 * 1024) return MPIR_UNSUPPORTED;
+    if ((size_t)2 * G * NB * sizeof(T) > sc.part_bytes || smem > 200 * 1024) return MPIR_UNSUP();
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     GridBarrier gb{sc.barrier, sc.err};
     T *part = reinterpret_cast<T *>(sc.part);
@@ -269,7 +269,7 @@ static int launch_vec_apply_cl(const TS *V, int ldv, int M, int K, const TS *Tw,
     int cs = cluster_size_for((const void *)kern, VEC_CL_THREADS, tsz + (size_t)ceil_div(M, want) * sizeof(T), want);
     int slice = ceil_div(M, cs);
     size_t smem = tsz + (size_t)slice * sizeof(T);
-    if (smem > tsz + 64 * 1024) return MPIR_UNSUPPORTED;
+    if (smem > tsz + 64 * 1024) return MPIR_UNSUP();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(VEC_CL_THREADS, 1, 1);
@@ -295,7 +295,7 @@ int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, i
     if (nbv == 128) return launch_vec_apply_cl<TS, T, 128>(V, ldv, M, K, Tw, trans, x, s);
     if (nbv == 32) return launch_vec_apply_cl<TS, T, 32>(V, ldv, M, K, Tw, trans, x, s);
     if (nbv == 16) return launch_vec_apply_cl<TS, T, 16>(V, ldv, M, K, Tw, trans, x, s);
-    return MPIR_UNSUPPORTED;
+    return MPIR_UNSUP();
 }
 
 // ---------------------------------------------------------------------------
@@ -605,7 +605,7 @@ static int trsv_dispatch(const TS *U, int ldu, int n, int trans, T *x, const Dev
     slice = ceil_div(nblk, G) * 32;
     G = ceil_div(n, slice);
     smem = (size_t)slice * sizeof(T);
-    if (smem > 200 * 1024 || (size_t)64 * sizeof(T) > sc.part_bytes) return MPIR_UNSUPPORTED;
+    if (smem > 200 * 1024 || (size_t)64 * sizeof(T) > sc.part_bytes) return MPIR_UNSUP();
     if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     GridBarrier gb{sc.barrier, sc.err};
     T *xbuf = reinterpret_cast<T *>(sc.part);

@@ -130,7 +130,7 @@ int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int 
                  cudaStream_t s)
 {
     if (K <= 0 || M <= 0) return 0;
-    if (K > M || ldv < M || ldt < K || !ws) return MPIR_UNSUPPORTED;
+    if (K > M || ldv < M || ldt < K || !ws) return MPIR_UNSUP();
     unsigned char *b = static_cast<unsigned char *>(ws);
     T *y = reinterpret_cast<T *>(b);
     T *wp = reinterpret_cast<T *>(b + rup256((size_t)K * sizeof(double)));

@@ -239,6 +239,52 @@ def lse_known_torch(seed, m, n, p, cond_a, cond_b, device, resid=1e-3):
     return dict(A=A, B=B, b=b, d=d, x_true=x, r_true=r, v_true=v, kappa_up=kup)
 
 
+def _haar_torch(g, rows, cols, device):
+    """rows x cols with orthonormal columns (QR of a Gaussian matrix, the
+    signs of diag(R) folded in), drawn with generator g on `device`."""
+    import torch
+    X = torch.randn(rows, cols, generator=g, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(X)
+    sg = torch.sign(torch.diagonal(R))
+    sg[sg == 0] = 1.0
+    return Q * sg
+
+
+def lse_paper_torch(seed, m, n, p, kappa, device, mode=3):
+    """lse_paper drawn on `device` (the Sec. 6.2 shapes are too large for a
+    host generator): [A^T, B^T] = W1 Sigma W2 with kappa_2([A; B]) = kappa,
+    b = A x + N(0, 1) noise, d = B x.  FP64 column-major tensors."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & ((1 << 63) - 1))
+    sigma = torch.from_numpy(latm1_sigma(n, kappa, mode)).to(device)
+    U = _haar_torch(g, m + p, n, device)
+    V = _haar_torch(g, n, n, device)
+    AB = (U * sigma) @ V.T
+    A = AB[:m].t().contiguous().t()
+    B = AB[m:].t().contiguous().t()
+    x = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    b = A @ x + torch.randn(m, generator=g, device=device, dtype=torch.float64)
+    d = B @ x
+    return dict(A=A, B=B, b=b, d=d)
+
+
+def gls_paper_torch(seed, n, m, p, kappa, device, mode=3):
+    """gls_paper drawn on `device`: [W, V] = W1 Sigma W2 with
+    kappa_2([W, V]) = kappa (Sec. 6.3), d ~ N(0, 1)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) & ((1 << 63) - 1))
+    sigma = torch.from_numpy(latm1_sigma(n, kappa, mode)).to(device)
+    U = _haar_torch(g, n, n, device)
+    V = _haar_torch(g, m + p, n, device)
+    WV = (U * sigma) @ V.T
+    W = WV[:, :m].t().contiguous().t()
+    Vm = WV[:, m:].t().contiguous().t()
+    d = torch.randn(n, generator=g, device=device, dtype=torch.float64)
+    return dict(W=W, V=Vm, d=d)
+
+
 def lse_batch_torch(specs, device, cond_b=10.0):
     """The problems of lse_batch_specs drawn with torch's generator on
     `device` (same construction as lse_svd: Haar factors from the QR of

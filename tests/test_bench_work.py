@@ -63,3 +63,21 @@ def test_tf32_peak_from_measured_bf16():
     peaks = {"bf16_tflops": 1920.0, "bf16_tflops_sustained": 1697.3}
     assert bench.tf32_peak(peaks, sustained=False) == pytest.approx(1920.0 * 1.1 / 2.25)
     assert bench.tf32_peak(peaks, sustained=True) == pytest.approx(1697.3 * 1.1 / 2.25)
+
+
+def test_paper_shape_lists_follow_sec_6():
+    """Sec. 6.2: n in {1024, 2048, 3072} with (m, p) = (8n, n/32), (8n, n/64),
+    (10n, n/32), (10n, n/64), (12n, n/32), (12n, n/64) at four condition
+    numbers; n in {128, 192, 256} with (m, p) = (128n, n/8), (128n, n/4),
+    (128n, n/2), (256n, n/8), (256n, n/4), (256n, n/2) at 1e5.  Sec. 6.3:
+    (p, m) = (8n, n/32) ... (12n, n/64) for the same n and conditionings."""
+    lse1, lse2, gls = bench.paper_shape_list(True)
+    assert len(lse1) == 72 and len(lse2) == 18 and len(gls) == 72
+    assert ((3072, 36864, 48), 1e9) in lse1 and ((128, 16384, 16), 1e5) in lse2
+    assert ((2048, 64, 16384), 1e5) in gls
+    for (n, m, p), _ in lse1 + lse2:
+        assert p <= n <= m                       # LSE shapes (m >= n >= p)
+    for (n, m, p), _ in gls:
+        assert m <= n <= p                       # GLS shapes (m <= n <= p)
+    small = bench.paper_shape_list(False)
+    assert all(set(a) <= set(b) for a, b in zip(small, (lse1, lse2, gls)))

@@ -67,3 +67,25 @@ def test_lse_large_full_size(h, oracle_mod, cond, fact, refine):
     assert fe <= bound, (fe, bound)
     if cond <= 1e4 and refine == "classical" and fact == "fp32":
         assert d["escalated"] == 0
+
+
+@pytest.mark.parametrize("m,n,p,fact", [(65536, 256, 128, "fp32"), (40960, 160, 32, "fp64")])
+def test_lse_tall_known_solution(h, oracle_mod, m, n, p, fact):
+    """The m >> n > p shapes of Sec. 6.2 (m = 256 n): panels of up to 65536
+    rows, beyond what a 16-CTA cluster holds, run on the grid-exchange panel.
+    Same bar as above, known-solution right-hand sides."""
+    import torch
+    from paper_2406_16499_gb300 import mpir
+    T = I.lse_known_torch(SEED + m + p, m, n, p, 1e4, 1e2, "cuda")
+    Hs = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in T.items()}
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    r = torch.zeros(m, dtype=torch.float64, device="cuda")
+    v = torch.zeros(p, dtype=torch.float64, device="cuda")
+    st, info = h.lse_solve(T["A"], T["B"], T["b"], T["d"], x, r, v, mpir.make_opts(fact=fact))
+    assert st == 0, (st, info.as_dict())
+    xh = x.cpu().numpy()
+    met = oracle_mod.lse_metrics(Hs["A"], Hs["B"], Hs["b"], Hs["d"], xh, r.cpu().numpy(), v.cpu().numpy())
+    fe = float(np.linalg.norm(xh - Hs["x_true"]) / np.linalg.norm(Hs["x_true"]))
+    assert met["eta"] <= 1e-14 and met["e_con"] <= 1e-14, met
+    assert fe <= 10 * Hs["kappa_up"] * 1.1e-16, (fe, Hs["kappa_up"])
+    assert info.as_dict()["escalated"] == 0

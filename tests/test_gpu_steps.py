@@ -210,17 +210,20 @@ def test_grq_gqr_many_blocks(h):
     assert np.abs(_explicit_t(h, "Z", p) - Z.T).max() <= 1e-5
 
 
-def test_grq_invariants_tall(h):
+@pytest.mark.parametrize("m,n,p,fact", [(12288, 384, 64, "fp32"), (40960, 160, 32, "fp32"),
+                                        (20480, 96, 16, "fp64")])
+def test_grq_invariants_tall(h, m, n, p, fact):
     """Panels taller than one cluster's shared memory (m = 12288 rows, the
-    row-chunked inner updates): Lemma 4.5 through products with random
-    vectors, B x ~ [0 R] Q x and A x ~ Z T Q x with backward errors
+    row-chunked inner updates) and taller than a 16-CTA cluster holds in
+    registers (m = 40960 FP32 / 20480 FP64 rows: the grid-exchange panel on
+    one CTA per 1024 rows): Lemma 4.5 through products with random vectors,
+    B x ~ [0 R] Q x and A x ~ Z T Q x with backward errors
     O(u_f) ||.||_F ||x||, and Q^T Q x = x, Z^T Z y = y."""
     import torch
-    tol = 3e-6
-    m, n, p = 12288, 384, 64
+    tol = 3e-6 if fact == "fp32" else 1e-14
     T = I.lse_svd_torch(31, m, n, p, 1e2, 1e1, "cuda")
     A, B = T["A"], T["B"]
-    h.lse_factor(A, B, "fp32")
+    h.lse_factor(A, B, fact)
     R = torch.zeros((p, p), dtype=torch.float64, device="cuda").t().contiguous().t()
     Tm = torch.zeros((n, m), dtype=torch.float64, device="cuda").t()
     h.get_RT(R, Tm)
