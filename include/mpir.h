@@ -64,7 +64,8 @@ typedef enum {
 typedef enum {
     MPIR_CLASSICAL = 0,   /* classical IR (Alg. 2 / Alg. 4)                      */
     MPIR_GMRES = 1,       /* GMRES-IR with the block-diagonal split preconditioner
-                             (Sec. 5.2, 5.3)                                      */
+                             (Sec. 5.2, 5.3; wide shapes: eq. lse-bdpre-nlarge,
+                             gls-bdpre-nlarge)                                    */
     MPIR_DIRECT = 2,      /* no refinement: null-space / Paige solve at u_f       */
     MPIR_GMRES_LEFT = 3   /* GMRES-IR with the left preconditioner M ~ F~^-1 applied
                              by the correction solver on the held factors
@@ -331,19 +332,21 @@ int mpir_gls_correction(mpir_handle h, const double *f1, const double *f2,
  * 3 -> M_l F~ M_r u; 4 -> M u, 5 -> M F~ u with the left preconditioner
  * M ~ F~^-1 of Sec. 5.1 (eq. lse-leftpre / gls-leftpre: the correction
  * solver, Alg. 1 / Alg. 3, on the held factors; every shape).
- * LSE (which 0-3 need m >= n): vectors of length m + p + n ordered [m; p; n],
+ * LSE: vectors of length m + p + n ordered [m; p; n],
  *   F~ = [a I, 0, A; 0, 0, b B; A^T, b B^T, 0],
  *   M_l = diag(a^-1/2 I, a^-1/2 b^-1 S R^-1, a^1/2 T1^-T Q),
  *   M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-T S^T, a^1/2 Q^T T1^-1),
- *   T1 the leading n x n of T, S its trailing p x p.
- * GLS (which 0-3 need n <= p): vectors of length p + n + m ordered [p; n; m],
+ *   T1 the leading n x n of T, S its trailing p x p; when n > m, T is
+ *   m x n and T1 = [T; 0, I_{n-m}] (eq. lse-bdpre-nlarge).
+ * GLS: vectors of length p + n + m ordered [p; n; m],
  *   F~ = [a I, V^T, 0; V, 0, b W; 0, b W^T, 0],
  *   M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^T, a^-1/2 b^-1 S^T R^-T),
  *   M_r = diag(a^-1/2 I, a^1/2 Q T2^-T, a^-1/2 b^-1 R^-1 S),
- *   T = [0, T2], S the leading m x m of T2.
+ *   T = [0, T2], S the leading m x m of T2; when n > p, T = [T^1; T^2] is
+ *   n x p and T2 = [I_{n-p}, T^1; 0, T^2] (eq. gls-bdpre-nlarge).
  * A, B (W, V): the FP64 matrices that were factored.  alpha, beta > 0.
  * in, out: device arrays, distinct.  Returns 0, a negative argument index,
- * or MPIR_UNSUPPORTED (no matching factors held, or the shape condition). */
+ * or MPIR_UNSUPPORTED (no matching factors held). */
 int mpir_lse_bd_apply(mpir_handle h, const double *A, int lda, const double *B, int ldb,
                       double alpha, double beta, int which, const double *in, double *out);
 int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, int ldv,

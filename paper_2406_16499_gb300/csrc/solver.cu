@@ -1088,12 +1088,60 @@ int vapply_d(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, con
     return apply_reflectors_vec_blk<T, double>(V, ldv, M, K, Tw, panel_nb<T>(), trans, x, s);
 }
 
-// GLS (n <= p, Sec. 5.3):  F~ = [a I, V^T, 0; V, 0, b W; 0, b W^T, 0] on
+// The triangular factor of the wide shapes (eq. lse-bdpre-nlarge,
+// eq. gls-bdpre-nlarge): U = [T; 0, c I_{N-r}] (N x N) with T the r x N upper
+// trapezoid held at (Tp, ld), r <= N (r = N: U = T's leading triangle).  c
+// is the power-of-two scale of the factored matrix (T holds c times the
+// factor of the unscaled one, so the identity block scales with it).
+// Solves U x = t (trans 0) or U^T x = t (trans 1) in place: one triangular
+// solve with T's leading r x r block and one product with its trailing
+// r x (N - r) block.  Dinv: FP64 inverses of the diagonal blocks of the
+// leading r x r block.
+template <typename T>
+int trsv_trap(mpir_ctx *h, const T *Tp, int ld, int r, int N, double c, int trans, double *x, const double *Dinv,
+              cudaStream_t s)
+{
+    if (r >= N) return trsv_d<T>(Tp, ld, N, trans, x, h->sc, s, Dinv);
+    if (!trans) {                      // c x2 = t2;  T11 x1 = t1 - T12 x2
+        vcomb<double>(x + r, N - r, x + r, 0, 1.0 / c, nullptr, 0, 0.0, s);
+        RC(gemv_d<T>(Tp + idx2(0, r, ld), ld, r, N - r, 0, -1.0, x + r, 1.0, x, 0, 0, s));
+        return trsv_d<T>(Tp, ld, r, 0, x, h->sc, s, Dinv);
+    }
+    RC(trsv_d<T>(Tp, ld, r, 1, x, h->sc, s, Dinv));      // T11^T x1 = t1
+    RC(gemv_d<T>(Tp + idx2(0, r, ld), ld, r, N - r, 1, -1.0, x, 1.0, x + r, 0, 0, s));   // t2 - T12^T x1
+    vcomb<double>(x + r, N - r, x + r, 0, 1.0 / c, nullptr, 0, 0.0, s);                  // x2 = (...) / c
+    return 0;
+}
+
+// y = S x (trans 0) or S^T x (trans 1) for the trailing block S = U(o:N, o:N)
+// of the U above (k = N - o): its first r - o rows come from T (upper part),
+// the others are c times identity rows.  x and y distinct, length k.
+template <typename T>
+int trap_tail_gemv(const T *Tp, int ld, int r, int N, int o, double c, int trans, const double *x, double *y,
+                   cudaStream_t s)
+{
+    const int k = N - o, kr = std::max(std::min(r, N) - o, 0);
+    const T *S = Tp + idx2(o, o, ld);
+    if (kr >= k) return gemv_d<T>(S, ld, k, k, trans, 1.0, x, 0.0, y, 1, 0, s);
+    if (!trans) {
+        if (kr > 0) RC(gemv_d<T>(S, ld, kr, k, 0, 1.0, x, 0.0, y, 1, 0, s));
+        vcomb<double>(y + kr, k - kr, x + kr, 0, c, nullptr, 0, 0.0, s);
+        return 0;
+    }
+    vzero(y, sizeof(double) * (size_t)kr, s);
+    vcomb<double>(y + kr, k - kr, x + kr, 0, c, nullptr, 0, 0.0, s);
+    if (kr > 0) RC(gemv_d<T>(S, ld, kr, k, 1, 1.0, x, 1.0, y, 1, 0, s));
+    return 0;
+}
+
+// GLS (Sec. 5.3):  F~ = [a I, V^T, 0; V, 0, b W; 0, b W^T, 0] on
 // u = [u1 (p); u2 (n); u3 (m)];  T = [0, T2] (T2 n x n), S = T2(1:m, 1:m),
 //   M_l = diag(a^-1/2 I, a^1/2 T2^-1 Q^T, a^-1/2 b^-1 S^T R^-T),
 //   M_r = diag(a^-1/2 I, a^1/2 Q T2^-T,  a^-1/2 b^-1 R^-1 S).
 // Reversed coordinates: T2 = P_n T~_n^T P_n (T~_n the leading n x n of the
-// factor of C~) and S = P_m T~_S^T P_m, T~_S = T~(L:n, L:n), L = n - m.
+// factor of C~) and S = P_m T~_S^T P_m, T~_S = T~_n(L:n, L:n), L = n - m.
+// n > p (eq. gls-bdpre-nlarge): T = [T^1; T^2] (n x p), T2 = [I, T^1; 0, T^2],
+// which reversed is T~_n = [T~; 0, I_{n-p}] with T~ the p x n factor of C~.
 template <typename T>
 struct GlsBDOp : LinOp {
     mpir_ctx *h;
@@ -1106,12 +1154,13 @@ struct GlsBDOp : LinOp {
             double al_, double be_)
         : h(h_), w(w_), b(b_), W(W_), V(V_), ldw(ldw_), ldv(ldv_), al(al_), be(be_) {}
 
-    const T *TS() const { return w.Ct + idx2(w.L, w.L, w.ldCt); }
+    // rows of the factor of C~ held (n > p: U = [T~; 0, I], eq. gls-bdpre-nlarge)
+    int rT() const { return std::min(w.n, w.p); }
 
     // FP64 inverses of the diagonal blocks of T~_n and R
     void prepare()
     {
-        inv_diag_d<T>(w.Ct, w.ldCt, w.n, b.dT, h->sc.status, h->stream);
+        inv_diag_d<T>(w.Ct, w.ldCt, rT(), b.dT, h->sc.status, h->stream);
         inv_diag_d<T>(w.Wf, w.ldW, w.m, b.dR, h->sc.status, h->stream);
     }
 
@@ -1123,13 +1172,13 @@ struct GlsBDOp : LinOp {
         vcomb<double>(u, p, t, 0, 1.0 / sa, nullptr, 0, 0.0, s);
         // a^1/2 Q T2^-T t2 = a^1/2 sV Q P_n T~_n'^-1 P_n t2
         vcomb<double>(b.w1, n, t + p, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.Ct, w.ldCt, n, 0, b.w1, h->sc, s, b.dT));
+        RC(trsv_trap<T>(h, w.Ct, w.ldCt, rT(), n, sV, 0, b.w1, b.dT, s));
         vcomb<double>(u + p, n, b.w1, 1, sa * sV, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 0, u + p, s));
         if (m > 0) {
             // a^-1/2 b^-1 R^-1 S t3 = a^-1/2 b^-1 (sW/sV) R'^-1 P_m T~_S'^T P_m t3
             vcomb<double>(b.w1, m, t + p + n, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(gemv_d<T>(TS(), w.ldCt, m, m, 1, 1.0, b.w1, 0.0, b.w2, 1, 0, s));
+            RC(trap_tail_gemv<T>(w.Ct, w.ldCt, rT(), n, w.L, sV, 1, b.w1, b.w2, s));
             vcomb<double>(u + p + n, m, b.w2, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
             RC(trsv_d<T>(w.Wf, w.ldW, m, 0, u + p + n, h->sc, s, b.dR));
         }
@@ -1159,14 +1208,14 @@ struct GlsBDOp : LinOp {
         vcomb<double>(b.w1, n, g + p, 0, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.Ct, w.ldCt, n, 1, b.w2, h->sc, s, b.dT));
+        RC(trsv_trap<T>(h, w.Ct, w.ldCt, rT(), n, sV, 1, b.w2, b.dT, s));
         vcomb<double>(o + p, n, b.w2, 1, sa * sV, nullptr, 0, 0.0, s);
         if (m > 0) {
             // a^-1/2 b^-1 S^T R^-T g3 = a^-1/2 b^-1 (sW/sV) P_m T~_S' P_m R'^-T g3
             vcomb<double>(b.w1, m, g + p + n, 0, 1.0, nullptr, 0, 0.0, s);
             RC(trsv_d<T>(w.Wf, w.ldW, m, 1, b.w1, h->sc, s, b.dR));
             vcomb<double>(b.w2, m, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(gemv_d<T>(TS(), w.ldCt, m, m, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
+            RC(trap_tail_gemv<T>(w.Ct, w.ldCt, rT(), n, w.L, sV, 0, b.w2, b.w3, s));
             vcomb<double>(o + p + n, m, b.w3, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
         }
         return 0;
@@ -1297,7 +1346,6 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
     gls_layout<T>(nullptr, n, m, p, &main_bytes);
     const int NG = p + n + m, mx = std::max(std::max(m, n), std::max(p, 1));
     if (gm) {
-        if (!left && n > p) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.3) needs n <= p");
         if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
         RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
     }
@@ -1604,8 +1652,9 @@ double dnorm_host(mpir_ctx *h, const double *dvec, int n, double *scratch)
 }
 
 
-// LSE (m >= n, Sec. 5.2):  F~ = [a I, 0, A; 0, 0, b B; A^T, b B^T, 0] on
-// u = [u1 (m); u2 (p); u3 (n)];  T1 = T(1:n, 1:n), S = T1(q+1:n, q+1:n),
+// LSE (Sec. 5.2):  F~ = [a I, 0, A; 0, 0, b B; A^T, b B^T, 0] on
+// u = [u1 (m); u2 (p); u3 (n)];  T1 = T(1:n, 1:n), S = T1(q+1:n, q+1:n)
+// (n > m, eq. lse-bdpre-nlarge: T is m x n and T1 = [T; 0, I_{n-m}]),
 //   M_l = diag(a^-1/2 I, a^-1/2 b^-1 S R^-1, a^1/2 T1^-T Q),
 //   M_r = diag(a^-1/2 I, a^-1/2 b^-1 R^-T S^T, a^1/2 Q^T T1^-1).
 // Reversed coordinates: R = P_p R~^T P_p, Q = P_n Q~^T P_n; T is held as is.
@@ -1621,12 +1670,13 @@ struct LseBDOp : LinOp {
             double al_, double be_)
         : h(h_), w(w_), b(b_), A(A_), B(B_), lda(lda_), ldb(ldb_), al(al_), be(be_) {}
 
-    const T *TS() const { return w.At + idx2(w.q, w.q, w.ldAt); }
+    // rows of T held (n > m: T1 = [T; 0, I], eq. lse-bdpre-nlarge)
+    int rT() const { return std::min(w.m, w.n); }
 
     // FP64 inverses of the diagonal blocks of T1 and R~
     void prepare()
     {
-        inv_diag_d<T>(w.At, w.ldAt, w.n, b.dT, h->sc.status, h->stream);
+        inv_diag_d<T>(w.At, w.ldAt, rT(), b.dT, h->sc.status, h->stream);
         inv_diag_d<T>(w.Bt, w.ldBt, w.p, b.dR, h->sc.status, h->stream);
     }
 
@@ -1638,14 +1688,14 @@ struct LseBDOp : LinOp {
         vcomb<double>(u, m, t, 0, 1.0 / sa, nullptr, 0, 0.0, s);
         if (p > 0) {
             // a^-1/2 b^-1 R^-T S^T t2 = a^-1/2 b^-1 (sB/sA) P_p R~'^-1 P_p S'^T t2
-            RC(gemv_d<T>(TS(), w.ldAt, p, p, 1, 1.0, t + m, 0.0, b.w1, 1, 0, s));
+            RC(trap_tail_gemv<T>(w.At, w.ldAt, rT(), n, w.q, sA, 1, t + m, b.w1, s));
             vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
             RC(trsv_d<T>(w.Bt, w.ldBt, p, 0, b.w2, h->sc, s, b.dR));
             vcomb<double>(u + m, p, b.w2, 1, sB / (sA * sa * be), nullptr, 0, 0.0, s);
         }
         // a^1/2 Q^T T1^-1 t3 = a^1/2 sA P_n Q~ P_n T1'^-1 t3
         vcomb<double>(b.w1, n, t + m + p, 0, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.At, w.ldAt, n, 0, b.w1, h->sc, s, b.dT));
+        RC(trsv_trap<T>(h, w.At, w.ldAt, rT(), n, sA, 0, b.w1, b.dT, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, b.w2, s));
         vcomb<double>(u + m + p, n, b.w2, 1, sa * sA, nullptr, 0, 0.0, s);
@@ -1677,7 +1727,7 @@ struct LseBDOp : LinOp {
             vcomb<double>(b.w1, p, g + m, 1, 1.0, nullptr, 0, 0.0, s);
             RC(trsv_d<T>(w.Bt, w.ldBt, p, 1, b.w1, h->sc, s, b.dR));
             vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(gemv_d<T>(TS(), w.ldAt, p, p, 0, 1.0, b.w2, 0.0, b.w3, 1, 0, s));
+            RC(trap_tail_gemv<T>(w.At, w.ldAt, rT(), n, w.q, sA, 0, b.w2, b.w3, s));
             vcomb<double>(o + m, p, b.w3, 0, sB / (sA * sa * be), nullptr, 0, 0.0, s);
         }
         // a^1/2 T1^-T Q g3 = a^1/2 sA T1'^-T P_n Q~^T P_n g3  (g3 -> D g3 with column scaling)
@@ -1685,7 +1735,7 @@ struct LseBDOp : LinOp {
         if (h->fs.colscale) vdiag<double>(b.w1, w.D, n, 1, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_d<T>(w.At, w.ldAt, n, 1, b.w2, h->sc, s, b.dT));
+        RC(trsv_trap<T>(h, w.At, w.ldAt, rT(), n, sA, 1, b.w2, b.dT, s));
         vcomb<double>(o + m + p, n, b.w2, 0, sa * sA, nullptr, 0, 0.0, s);
         return 0;
     }
@@ -1796,7 +1846,6 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
     lse_layout<T>(nullptr, m, n, p, &main_bytes);
     const int NG = m + p + n, mx = std::max(std::max(m, n), std::max(p, 1));
     if (gm) {
-        if (!left && m < n) return set_err(h, MPIR_UNSUPPORTED, "GMRES-IR preconditioner (Sec. 5.2) needs m >= n");
         if (o.restart > GMRES_MAX_RESTART) return set_err(h, MPIR_UNSUPPORTED, "GMRES restart above 64");
         RC(ensure_ws(h, main_bytes + bd_bytes(NG, o.restart, mx)));
     }
@@ -2276,7 +2325,7 @@ int lse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, cons
         size_t mb = 0;
         lse_layout<float>(nullptr, m, n, p, &mb);
         const int NG = m + p + n, mx = std::max(std::max(m, n), std::max(p, 1));
-        RC(ensure_ws(h, mb + (m >= n ? bd_bytes(NG, std::min(o.restart, GMRES_MAX_RESTART), mx) : 0)));
+        RC(ensure_ws(h, mb + bd_bytes(NG, std::min(o.restart, GMRES_MAX_RESTART), mx)));
         RC(sel_begin(h, 0, m, n, p, A, lda, B, std::max(ldb, 1), b, m, d, p));
         cudaEventRecord(h->ev[0], h->stream);
         RC(lse_factor_impl<float>(h, m, n, p, A, lda, B, ldb, MPIR_FP32));
@@ -2284,7 +2333,6 @@ int lse_solve(mpir_handle h, int m, int n, int p, const double *A, int lda, cons
         int cls = 0;
         RC(sel_end(h, &cls));
         sel_apply(cls, &o);
-        if (o.refine == MPIR_GMRES && m < n) o.refine = MPIR_CLASSICAL;
         factored = o.fact == MPIR_FP32;
     }
     if (o.fact < MPIR_BF16 || o.fact > MPIR_FP64) return set_err(h, -14, "illegal opts->fact");
@@ -2320,7 +2368,7 @@ int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, cons
         size_t mb = 0;
         gls_layout<float>(nullptr, n, m, p, &mb);
         const int NG = p + n + m, mx = std::max(std::max(m, n), std::max(p, 1));
-        RC(ensure_ws(h, mb + (n <= p ? bd_bytes(NG, std::min(o.restart, GMRES_MAX_RESTART), mx) : 0)));
+        RC(ensure_ws(h, mb + bd_bytes(NG, std::min(o.restart, GMRES_MAX_RESTART), mx)));
         RC(sel_begin(h, 1, n, m, p, W, ldw, V, ldv, d, n, nullptr, 0));
         cudaEventRecord(h->ev[0], h->stream);
         RC(gls_factor_impl<float>(h, n, m, p, W, ldw, V, ldv, MPIR_FP32));
@@ -2328,7 +2376,6 @@ int gls_solve(mpir_handle h, int n, int m, int p, const double *W, int ldw, cons
         int cls = 0;
         RC(sel_end(h, &cls));
         sel_apply(cls, &o);
-        if (o.refine == MPIR_GMRES && n > p) o.refine = MPIR_CLASSICAL;
         factored = o.fact == MPIR_FP32;
     }
     if (o.fact < MPIR_BF16 || o.fact > MPIR_FP64) return set_err(h, -14, "illegal opts->fact");
@@ -3136,7 +3183,6 @@ int mpir_lse_bd_apply(mpir_handle h, const double *A, int lda, const double *B, 
     if (!h) return -1;
     const FactorState &fs = h->fs;
     if (fs.kind != Kind::LSE) return set_err(h, MPIR_UNSUPPORTED, "no LSE factors held");
-    if (fs.m < fs.n && which < 4) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.2) needs m >= n");
     if (!A) return -2;
     if (lda < std::max(1, fs.m)) return -3;
     if (fs.p > 0 && !B) return -4;
@@ -3159,7 +3205,6 @@ int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, 
     if (!h) return -1;
     const FactorState &fs = h->fs;
     if (fs.kind != Kind::GLS) return set_err(h, MPIR_UNSUPPORTED, "no GLS factors held");
-    if (fs.n > fs.p && which < 4) return set_err(h, MPIR_UNSUPPORTED, "preconditioner (Sec. 5.3) needs n <= p");
     if (fs.m > 0 && !W) return -2;
     if (ldw < std::max(1, fs.n)) return -3;
     if (!V) return -4;

@@ -11,6 +11,9 @@
   residual, forward error against the oracle's solution).
 * Table 4's behaviour: at kappa = 1e9 (one small singular value) classical
   IR with FP32 factors does not converge and GMRES-IR does.
+* The wide shapes (LSE n > m, GLS n > p) with the split preconditioners of
+  eq. lse-bdpre-nlarge / gls-bdpre-nlarge: pieces against the oracle and
+  full solves at the FP64 bar.
 * The left preconditioner of Sec. 5.1 (M ~ F~^-1 applied by the correction
   solver): M and M F~ against the oracle's LseLeft / GlsLeft, M F~ = I with
   FP64 factors, and full solves on every shape, wide ones included.
@@ -23,6 +26,7 @@ from gpu_util import dev, host, rel, zeros
 from test_gpu_solve import check_gls, check_lse, run_gls, run_lse
 
 pytestmark = pytest.mark.gpu
+U32 = 2.0 ** -24
 
 
 @pytest.fixture(scope="module")
@@ -42,9 +46,12 @@ def _pieces(bd):
 
 LSE_SHAPES = [(300, 200, 37), (257, 130, 0), (160, 160, 40), (700, 333, 129)]
 GLS_SHAPES = [(200, 70, 333), (150, 150, 150), (129, 1, 300), (333, 129, 700)]
+# wide shapes: LSE n > m (eq. lse-bdpre-nlarge), GLS n > p (eq. gls-bdpre-nlarge)
+LSE_WIDE = [(90, 100, 45), (60, 100, 70), (129, 200, 100)]
+GLS_WIDE = [(200, 120, 100), (150, 100, 60), (300, 250, 97)]
 
 
-@pytest.mark.parametrize("m,n,p", LSE_SHAPES)
+@pytest.mark.parametrize("m,n,p", LSE_SHAPES + LSE_WIDE)
 @pytest.mark.parametrize("fact,tol", [("fp64", 1e-11), ("fp32", 5e-4)])
 def test_lse_bd_pieces_match_oracle(h, oracle_mod, m, n, p, fact, tol):
     from oracle import gmres as G
@@ -57,6 +64,11 @@ def test_lse_bd_pieces_match_oracle(h, oracle_mod, m, n, p, fact, tol):
     h.lse_factor(dA, dB, fact=fact)
     g = np.random.default_rng(m + n + p)
     N = m + p + n
+    if fact == "fp32":
+        # two independent FP32 factorizations: each inverse of T1 is off by
+        # about u_single kappa(T1), and the wide T1 = [T; 0, I] can be far
+        # worse conditioned than A (the identity block is not scaled to T)
+        tol = max(tol, U32 * np.linalg.cond(G.LseBD(oracle_mod.lse_factor(A, B, "fp64"), A, B, a, b).T1))
     for which, fn in _pieces(bd).items():
         u = g.standard_normal(N)
         out = zeros(N)
@@ -66,7 +78,7 @@ def test_lse_bd_pieces_match_oracle(h, oracle_mod, m, n, p, fact, tol):
         assert rel(host(out), want) <= t, (which, rel(host(out), want))
 
 
-@pytest.mark.parametrize("n,m,p", GLS_SHAPES)
+@pytest.mark.parametrize("n,m,p", GLS_SHAPES + GLS_WIDE)
 @pytest.mark.parametrize("fact,tol", [("fp64", 1e-11), ("fp32", 5e-4)])
 def test_gls_bd_pieces_match_oracle(h, oracle_mod, n, m, p, fact, tol):
     from oracle import gmres as G
@@ -79,6 +91,8 @@ def test_gls_bd_pieces_match_oracle(h, oracle_mod, n, m, p, fact, tol):
     h.gls_factor(dW, dV, fact=fact)
     g = np.random.default_rng(n + m + p)
     N = p + n + m
+    if fact == "fp32":
+        tol = max(tol, U32 * np.linalg.cond(G.GlsBD(oracle_mod.gls_factor(W, V, "fp64"), W, V, a, b).T2))
     for which, fn in _pieces(bd).items():
         u = g.standard_normal(N)
         out = zeros(N)
@@ -280,19 +294,27 @@ def test_gmres_is_deterministic(h):
     assert a[0] == 0 and np.array_equal(a[2], b[2]) and a[1].inner_iters == b[1].inner_iters
 
 
-def test_gmres_shape_conditions(h):
-    """The block-diagonal preconditioners need m >= n (LSE) and n <= p (GLS);
-    other shapes are reported as unsupported, not solved some other way."""
-    from paper_2406_16499_gb300 import mpir
-    P = I.lse_svd(5, 90, 100, 45, 1e3, 1e1)
-    with pytest.raises(mpir.MpirError, match="unsupported"):
-        run_lse(h, P, refine="gmres", escalate=False)
-    G = I.gls_svd(6, 200, 120, 100, 1e2, 1e1)
-    with pytest.raises(mpir.MpirError, match="unsupported"):
-        run_gls(h, G, refine="gmres", escalate=False)
-    # the left preconditioner (Sec. 5.1) has no shape condition
-    assert run_lse(h, P, refine="gmres_left", escalate=False)[0] == 0
-    assert run_gls(h, G, refine="gmres_left", escalate=False)[0] == 0
+@pytest.mark.parametrize("m,n,p,ca", [(90, 100, 45, 1e3), (60, 100, 70, 1e4), (129, 200, 100, 1e3)])
+def test_lse_gmres_wide_shapes(h, oracle_mod, m, n, p, ca):
+    """n > m: the split preconditioner with T1 = [T; 0, I] (eq.
+    lse-bdpre-nlarge) reaches the FP64 bar, as the oracle's GMRES-IR does."""
+    from oracle import gmres as Gm
+    P = I.lse_svd(m + 11 * n + p, m, n, p, ca, 1e1)
+    st, info, x, r, v = run_lse(h, P, refine="gmres", escalate=False)
+    assert st == 0 and info.refine_used == 1 and info.inner_iters >= 1
+    check_lse(oracle_mod, P, x, r, v)
+    assert Gm.lse_gmres_ir(P["A"], P["B"], P["b"], P["d"])["status"] == 0
+
+
+@pytest.mark.parametrize("n,m,p,cw", [(200, 120, 100, 1e2), (150, 100, 60, 1e3), (300, 250, 97, 1e3)])
+def test_gls_gmres_wide_shapes(h, oracle_mod, n, m, p, cw):
+    """n > p: T2 = [I, T^1; 0, T^2] (eq. gls-bdpre-nlarge)."""
+    from oracle import gmres as Gm
+    G = I.gls_svd(7 * n + m + p, n, m, p, cw, 1e1)
+    st, info, x, y, z = run_gls(h, G, refine="gmres", escalate=False)
+    assert st == 0 and info.refine_used == 1 and info.inner_iters >= 1
+    check_gls(oracle_mod, G, x, y, z)
+    assert Gm.gls_gmres_ir(G["W"], G["V"], G["d"])["status"] == 0
 
 
 def test_gls_gmres_full_size_ar1(h, oracle_mod):
