@@ -45,6 +45,7 @@ def problem(cond):
 
 
 @pytest.mark.parametrize("cond,fact,refine", [(1e1, "fp32", "classical"), (1e1, "tf32", "classical"),
+                                              (1e1, "bf16", "classical"), (1e1, "bf16", "gmres"),
                                               (1e4, "fp32", "classical"), (1e4, "fp32", "gmres"),
                                               (1e8, "fp32", "classical")])
 def test_lse_large_full_size(h, oracle_mod, cond, fact, refine):
