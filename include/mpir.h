@@ -254,6 +254,22 @@ int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m,
                       double *const *y, const mpir_opts *opts,
                       mpir_info *infos);
 
+/* Complex batches (arrays as in zlse_solve / zgls_solve, pointers typed
+ * double *, leading dimensions in complex elements): every problem is
+ * embedded as in zlse_solve into the handle's embedding buffer (one
+ * launch), the real batched solver runs on the embedded batch, and x (and
+ * y) are read back (one launch).  Status codes and infos as the real calls. */
+int zlse_solve_batched(mpir_handle h, int count, const int *m, const int *n,
+                       const int *p, const double *const *A, const int *lda,
+                       const double *const *B, const int *ldb,
+                       const double *const *b, const double *const *d,
+                       double *const *x, const mpir_opts *opts, mpir_info *infos);
+int zgls_solve_batched(mpir_handle h, int count, const int *n, const int *m,
+                       const int *p, const double *const *W, const int *ldw,
+                       const double *const *V, const int *ldv,
+                       const double *const *d, double *const *x, double *const *y,
+                       const mpir_opts *opts, mpir_info *infos);
+
 /* =====================================================================
  * Step-level entry points: one per stage of the method, so that each can
  * be checked and timed on its own.  They operate on the factors held by

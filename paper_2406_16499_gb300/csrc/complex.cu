@@ -79,3 +79,49 @@ int zunembed_vec(const double *in, int n, double *z, cudaStream_t s)
 }
 
 } // namespace mpir
+
+namespace mpir {
+
+// Batched embedding: one CTA per job (a matrix: E(Z) into a 2 rows x 2 cols
+// block; a vector (vec != 0): e(z) = [Re z; Im z]); jobs of uneven size.
+__global__ void __launch_bounds__(256)
+k_zembed_batch(const ZEmbedJob *__restrict__ jobs, int njobs)
+{
+    const int jb = blockIdx.x;
+    if (jb >= njobs) return;
+    const ZEmbedJob J = jobs[jb];
+    const double2 *Z = reinterpret_cast<const double2 *>(J.src);
+    const size_t total = (size_t)J.rows * J.cols;
+    for (size_t e = threadIdx.x; e < total; e += blockDim.x) {
+        const int i = (int)(e % J.rows), j = (int)(e / J.rows);
+        const double2 z = Z[i + (size_t)j * J.lds];
+        J.dst[i + (size_t)j * J.ldd] = z.x;
+        J.dst[i + J.rows + (size_t)j * J.ldd] = z.y;
+        if (!J.vec) {
+            J.dst[i + (size_t)(j + J.cols) * J.ldd] = -z.y;
+            J.dst[i + J.rows + (size_t)(j + J.cols) * J.ldd] = z.x;
+        }
+    }
+}
+
+// Batched read-back: z = e^-1(src), src = [Re; Im] of length 2 rows.
+__global__ void __launch_bounds__(256)
+k_zunembed_batch(const ZEmbedJob *__restrict__ jobs, int njobs)
+{
+    const int jb = blockIdx.x;
+    if (jb >= njobs) return;
+    const ZEmbedJob J = jobs[jb];
+    double2 *z = reinterpret_cast<double2 *>(const_cast<double *>(J.src));
+    for (int k = threadIdx.x; k < J.rows; k += blockDim.x) z[k] = make_double2(J.dst[k], J.dst[J.rows + k]);
+}
+
+int zembed_batch(const ZEmbedJob *jobs_dev, int njobs, int unembed, cudaStream_t s)
+{
+    if (njobs <= 0) return 0;
+    ProfScope ps(K_CONVERT, s);
+    if (unembed) k_zunembed_batch<<<njobs, 256, 0, s>>>(jobs_dev, njobs);
+    else k_zembed_batch<<<njobs, 256, 0, s>>>(jobs_dev, njobs);
+    return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+} // namespace mpir

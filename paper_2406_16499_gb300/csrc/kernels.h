@@ -175,6 +175,16 @@ void vzero(void *dst, size_t bytes, cudaStream_t s);
 int zembed_mat(const double *Z, int rows, int cols, int ldz, double *out, int ldo, cudaStream_t s);
 int zembed_vec(const double *z, int n, double *out, cudaStream_t s);
 int zunembed_vec(const double *in, int n, double *z, cudaStream_t s);
+// One embedding job of a batch: src complex (interleaved; lds in complex
+// elements), dst real (ldd); vec: e(z) = [Re z; Im z] of a rows-vector (cols
+// = 1) instead of the 2 x 2 block matrix.  For the read-back (unembed = 1)
+// dst is the embedded vector (2 rows) and src the complex output.
+struct ZEmbedJob {
+    const double *src;
+    double *dst;
+    int rows, cols, lds, ldd, vec;
+};
+int zembed_batch(const ZEmbedJob *jobs_dev, int njobs, int unembed, cudaStream_t s);
 
 // Matrix conversion with optional transpose and index reversal:
 //   dst(i, j) = (Td)(scale * src(ri, ci)),  i < rows_d, j < cols_d,

@@ -3225,6 +3225,136 @@ int mpir_gls_bd_apply(mpir_handle h, const double *W, int ldw, const double *V, 
 
 extern "C" {
 
+// Complex batches through the real embedding (complex.cu): every problem's
+// E(A), E(B), e(b), e(d) and e(x) in the handle's embedding buffer, one
+// embedding launch, the real batched solve, one read-back launch.
+int zlse_solve_batched(mpir_handle h, int count, const int *m, const int *n, const int *p,
+                       const double *const *A, const int *lda, const double *const *B, const int *ldb,
+                       const double *const *b, const double *const *d, double *const *x,
+                       const mpir_opts *opts, mpir_info *infos)
+{
+    if (!h) return -1;
+    if (count < 0) return -2;
+    if (count == 0) return 0;
+    if (!m || !n || !p || !A || !lda || !B || !ldb || !b || !d || !x) return -3;
+    for (int i = 0; i < count; i++) {
+        const int a = lse_check_args(m[i], n[i], p[i], A[i], lda[i], B[i], ldb[i], b[i], d[i], x[i]);
+        if (a) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "problem %d: illegal argument %d of zlse_solve", i, -a);
+            return set_err(h, -3, msg);
+        }
+    }
+    std::vector<size_t> off(count + 1, 0);
+    for (int i = 0; i < count; i++) {
+        const size_t M = 2 * (size_t)m[i], N = 2 * (size_t)n[i], P = 2 * (size_t)p[i];
+        off[i + 1] = off[i] + ((M * N + P * N + M + P + N + 31) & ~(size_t)31);
+    }
+    const size_t njobs_max = (size_t)5 * count;
+    const size_t table_words = (njobs_max * sizeof(ZEmbedJob) + 7) / 8;
+    RC(ensure_zbuf(h, sizeof(double) * (off[count] + table_words)));
+    double *base = h->zbuf;
+    ZEmbedJob *table = reinterpret_cast<ZEmbedJob *>(base + off[count]);
+    std::vector<int> M2(count), N2(count), P2(count), lda2(count), ldb2(count);
+    std::vector<const double *> Ah(count), Bh(count), bh(count), dh(count);
+    std::vector<double *> xh(count);
+    std::vector<ZEmbedJob> jobs, back;
+    for (int i = 0; i < count; i++) {
+        M2[i] = 2 * m[i]; N2[i] = 2 * n[i]; P2[i] = 2 * p[i];
+        lda2[i] = std::max(M2[i], 1); ldb2[i] = std::max(P2[i], 1);
+        double *q = base + off[i];
+        double *a_ = q, *b_ = a_ + (size_t)M2[i] * N2[i], *bv = b_ + (size_t)P2[i] * N2[i], *dv = bv + M2[i];
+        double *xv = dv + P2[i];
+        Ah[i] = a_; Bh[i] = p[i] > 0 ? b_ : nullptr; bh[i] = bv; dh[i] = p[i] > 0 ? dv : nullptr; xh[i] = xv;
+        if (m[i] > 0) {
+            jobs.push_back(ZEmbedJob{A[i], a_, m[i], n[i], lda[i], lda2[i], 0});
+            jobs.push_back(ZEmbedJob{b[i], bv, m[i], 1, std::max(m[i], 1), M2[i], 1});
+        }
+        if (p[i] > 0) {
+            jobs.push_back(ZEmbedJob{B[i], b_, p[i], n[i], ldb[i], ldb2[i], 0});
+            jobs.push_back(ZEmbedJob{d[i], dv, p[i], 1, std::max(p[i], 1), P2[i], 1});
+        }
+        back.push_back(ZEmbedJob{x[i], xv, n[i], 1, n[i], N2[i], 1});
+    }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(table, jobs.data(), sizeof(ZEmbedJob) * jobs.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return cuda_check(h, "zlse_solve_batched");
+    RC(zembed_batch(table, (int)jobs.size(), 0, s));
+    const int st = lse_solve_batched(h, count, M2.data(), N2.data(), P2.data(), Ah.data(), lda2.data(), Bh.data(),
+                                     ldb2.data(), bh.data(), dh.data(), xh.data(), opts, infos);
+    if (st < 0 || st == MPIR_CUDA_ERROR) return st;
+    if (cudaMemcpyAsync(table, back.data(), sizeof(ZEmbedJob) * back.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return cuda_check(h, "zlse_solve_batched");
+    RC(zembed_batch(table, (int)back.size(), 1, s));
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "zlse_solve_batched");
+    return st;
+}
+
+int zgls_solve_batched(mpir_handle h, int count, const int *n, const int *m, const int *p,
+                       const double *const *W, const int *ldw, const double *const *V, const int *ldv,
+                       const double *const *d, double *const *x, double *const *y, const mpir_opts *opts,
+                       mpir_info *infos)
+{
+    if (!h) return -1;
+    if (count < 0) return -2;
+    if (count == 0) return 0;
+    if (!n || !m || !p || !W || !ldw || !V || !ldv || !d || !x || !y) return -3;
+    for (int i = 0; i < count; i++) {
+        const int a = gls_check_args(n[i], m[i], p[i], W[i], ldw[i], V[i], ldv[i], d[i], x[i], y[i]);
+        if (a) {
+            char msg[96];
+            std::snprintf(msg, sizeof(msg), "problem %d: illegal argument %d of zgls_solve", i, -a);
+            return set_err(h, -3, msg);
+        }
+    }
+    std::vector<size_t> off(count + 1, 0);
+    for (int i = 0; i < count; i++) {
+        const size_t Nn = 2 * (size_t)n[i], M = 2 * (size_t)m[i], P = 2 * (size_t)p[i];
+        off[i + 1] = off[i] + ((Nn * M + Nn * P + Nn + M + P + 31) & ~(size_t)31);
+    }
+    const size_t njobs_max = (size_t)5 * count;
+    const size_t table_words = (njobs_max * sizeof(ZEmbedJob) + 7) / 8;
+    RC(ensure_zbuf(h, sizeof(double) * (off[count] + table_words)));
+    double *base = h->zbuf;
+    ZEmbedJob *table = reinterpret_cast<ZEmbedJob *>(base + off[count]);
+    std::vector<int> N2(count), M2(count), P2(count), ldn(count);
+    std::vector<const double *> Wh(count), Vh(count), dh(count);
+    std::vector<double *> xh(count), yh(count);
+    std::vector<ZEmbedJob> jobs, back;
+    for (int i = 0; i < count; i++) {
+        N2[i] = 2 * n[i]; M2[i] = 2 * m[i]; P2[i] = 2 * p[i];
+        ldn[i] = N2[i];
+        double *q = base + off[i];
+        double *w_ = q, *v_ = w_ + (size_t)N2[i] * M2[i], *dv = v_ + (size_t)N2[i] * P2[i], *xv = dv + N2[i];
+        double *yv = xv + M2[i];
+        Wh[i] = m[i] > 0 ? w_ : nullptr; Vh[i] = v_; dh[i] = dv; xh[i] = m[i] > 0 ? xv : nullptr;
+        yh[i] = p[i] > 0 ? yv : nullptr;
+        if (m[i] > 0) jobs.push_back(ZEmbedJob{W[i], w_, n[i], m[i], ldw[i], N2[i], 0});
+        if (p[i] > 0) jobs.push_back(ZEmbedJob{V[i], v_, n[i], p[i], ldv[i], N2[i], 0});
+        jobs.push_back(ZEmbedJob{d[i], dv, n[i], 1, n[i], N2[i], 1});
+        if (m[i] > 0) back.push_back(ZEmbedJob{x[i], xv, m[i], 1, m[i], M2[i], 1});
+        if (p[i] > 0) back.push_back(ZEmbedJob{y[i], yv, p[i], 1, p[i], P2[i], 1});
+    }
+    cudaStream_t s = h->stream;
+    if (cudaMemcpyAsync(table, jobs.data(), sizeof(ZEmbedJob) * jobs.size(), cudaMemcpyHostToDevice, s) !=
+        cudaSuccess)
+        return cuda_check(h, "zgls_solve_batched");
+    RC(zembed_batch(table, (int)jobs.size(), 0, s));
+    const int st = gls_solve_batched(h, count, N2.data(), M2.data(), P2.data(), Wh.data(), ldn.data(), Vh.data(),
+                                     ldn.data(), dh.data(), xh.data(), yh.data(), opts, infos);
+    if (st < 0 || st == MPIR_CUDA_ERROR) return st;
+    if (!back.empty()) {
+        if (cudaMemcpyAsync(table, back.data(), sizeof(ZEmbedJob) * back.size(), cudaMemcpyHostToDevice, s) !=
+            cudaSuccess)
+            return cuda_check(h, "zgls_solve_batched");
+        RC(zembed_batch(table, (int)back.size(), 1, s));
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(h, "zgls_solve_batched");
+    return st;
+}
+
 int mpir_batched_set_shape(mpir_handle h, int group)
 {
     if (!h) return -1;

@@ -66,6 +66,10 @@ _SIG = {
                            ctypes.POINTER(Info)], _I),
     "gls_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
                            ctypes.POINTER(Info)], _I),
+    "zlse_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                            ctypes.POINTER(Info)], _I),
+    "zgls_solve_batched": ([_P, _I, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, ctypes.POINTER(Opts),
+                            ctypes.POINTER(Info)], _I),
     "mpir_lse_factor": ([_P, _I, _I, _I, _P, _I, _P, _I, _I], _I),
     "mpir_gls_factor": ([_P, _I, _I, _I, _P, _I, _P, _I, _I], _I),
     "mpir_get_RT": ([_P, _P, _I, _P, _I], _I),
@@ -214,7 +218,7 @@ class LseBatch:
     list of problems (dicts of column-major FP64 device tensors A, B, b, d)
     and their output vectors, so that repeated solves skip the marshalling."""
 
-    def __init__(self, probs, xs):
+    def __init__(self, probs, xs, ctype="f64"):
         import numpy as np
         cnt = len(probs)
         self.count = cnt
@@ -228,11 +232,11 @@ class LseBatch:
             ints[2, i] = B.shape[0]
             ints[3, i] = ld(A)
             ints[4, i] = ld(B) if B.shape[0] else 1
-            ptrs[0, i] = ptr(A) or 0
-            ptrs[1, i] = ptr(B) or 0
-            ptrs[2, i] = ptr(pr["b"]) or 0
-            ptrs[3, i] = ptr(pr["d"]) or 0
-            ptrs[4, i] = ptr(xs[i]) or 0
+            ptrs[0, i] = ptr(A, ctype) or 0
+            ptrs[1, i] = ptr(B, ctype) or 0
+            ptrs[2, i] = ptr(pr["b"], ctype) or 0
+            ptrs[3, i] = ptr(pr["d"], ctype) or 0
+            ptrs[4, i] = ptr(xs[i], ctype) or 0
         self._ints, self._ptrs = np.ascontiguousarray(ints), np.ascontiguousarray(ptrs)
         ip = lambda k: ctypes.c_void_p(self._ints[k].ctypes.data)
         pp = lambda k: ctypes.c_void_p(self._ptrs[k].ctypes.data)
@@ -246,7 +250,7 @@ class GlsBatch:
     problems (dicts of column-major FP64 device tensors W (n x m), V (n x p),
     d) and their output vectors xs (m), ys (p)."""
 
-    def __init__(self, probs, xs, ys):
+    def __init__(self, probs, xs, ys, ctype="f64"):
         import numpy as np
         cnt = len(probs)
         self.count = cnt
@@ -260,11 +264,11 @@ class GlsBatch:
             ints[2, i] = V.shape[1]
             ints[3, i] = ld(W)
             ints[4, i] = ld(V)
-            ptrs[0, i] = ptr(W) or 0
-            ptrs[1, i] = ptr(V) or 0
-            ptrs[2, i] = ptr(pr["d"]) or 0
-            ptrs[3, i] = ptr(xs[i]) or 0
-            ptrs[4, i] = ptr(ys[i]) or 0
+            ptrs[0, i] = ptr(W, ctype) or 0
+            ptrs[1, i] = ptr(V, ctype) or 0
+            ptrs[2, i] = ptr(pr["d"], ctype) or 0
+            ptrs[3, i] = ptr(xs[i], ctype) or 0
+            ptrs[4, i] = ptr(ys[i], ctype) or 0
         self._ints, self._ptrs = np.ascontiguousarray(ints), np.ascontiguousarray(ptrs)
         ip = lambda k: ctypes.c_void_p(self._ints[k].ctypes.data)
         pp = lambda k: ctypes.c_void_p(self._ptrs[k].ctypes.data)
@@ -337,6 +341,24 @@ class Handle:
         rc = lib().gls_solve_batched(self.h, batch.count, *batch.args, ctypes.byref(o),
                                      ctypes.cast(batch.infos, ctypes.POINTER(Info)))
         return self.check(rc, "gls_solve_batched"), list(batch.infos)[:batch.count]
+
+    def zlse_solve_batched(self, probs, xs, opts=None):
+        """Complex LSE batch: dicts of column-major complex128 device tensors
+        A, B, b, d and the complex128 output vectors xs."""
+        batch = LseBatch(probs, xs, "c128")
+        o = opts if opts is not None else make_opts()
+        rc = lib().zlse_solve_batched(self.h, batch.count, *batch.args, ctypes.byref(o),
+                                      ctypes.cast(batch.infos, ctypes.POINTER(Info)))
+        return self.check(rc, "zlse_solve_batched"), list(batch.infos)[:batch.count]
+
+    def zgls_solve_batched(self, probs, xs, ys, opts=None):
+        """Complex GLS batch: dicts of complex128 device tensors W, V, d and
+        the outputs xs, ys."""
+        batch = GlsBatch(probs, xs, ys, "c128")
+        o = opts if opts is not None else make_opts()
+        rc = lib().zgls_solve_batched(self.h, batch.count, *batch.args, ctypes.byref(o),
+                                      ctypes.cast(batch.infos, ctypes.POINTER(Info)))
+        return self.check(rc, "zgls_solve_batched"), list(batch.infos)[:batch.count]
 
     # ---- learned selector ------------------------------------------------
     def lse_features(self, A, B, b, d, s, out):

@@ -169,3 +169,63 @@ def test_zlse_argument_errors(h):
         h.zlse_solve(A[:, :4], zdev(P["B"][:, :4]), zdev(P["b"]), zdev(P["d"]), zzeros(4))   # p > n
     with pytest.raises(mpir.MpirError):
         h.zlse_solve(A, zdev(P["B"]), zdev(P["b"]), zdev(P["d"]), zzeros(20).real.contiguous())
+
+
+def test_zlse_batched_uneven(h, oracle_mod):
+    """Uneven complex LSE batch (one persistent launch on the embedded
+    problems): every answer at the bar of the single solve."""
+    g = np.random.default_rng(11)
+    probs, Ps, xs = [], [], []
+    for k in range(24):
+        m = int(g.integers(8, 120))
+        n = int(g.integers(2, max(3, m // 2)))
+        p = int(g.integers(0, max(1, n // 3)))
+        P = I.zlse_svd(100 + k, m, n, p, float(10 ** g.uniform(0, 4)), 1e1)
+        Ps.append(P)
+        probs.append(dict(A=zdev(P["A"]), B=zdev(P["B"]), b=zdev(P["b"]), d=zdev(P["d"])))
+        xs.append(zzeros(n))
+    st, infos = h.zlse_solve_batched(probs, xs)
+    assert st == 0
+    from oracle import zoracle as Z
+    for P, x, f in zip(Ps, xs, infos):
+        assert f.status == 0
+        A, B, b, d = P["A"], P["B"], P["b"], P["d"]
+        t = Z.zlse_truth(A, B, b, d)
+        xh = zhost(x)
+        r = b - A @ xh
+        e_con = np.linalg.norm(d - B @ xh) / (np.linalg.norm(B) * np.linalg.norm(xh) + np.linalg.norm(d) or 1.0)
+        assert e_con <= 1e-14
+        xe, re_ = np.concatenate([t["x"].real, t["x"].imag]), np.concatenate([t["r"].real, t["r"].imag])
+        F = oracle_mod.lse_factor(embed(A), embed(B) if B.shape[0] else np.zeros((0, 2 * A.shape[1])), "fp64")
+        kap = oracle_mod.lse_kappa(F, xe, re_)[0]
+        assert rel(xh, t["x"]) <= 10 * kap * U, (rel(xh, t["x"]), kap)
+
+
+def test_zgls_batched_uneven(h, oracle_mod):
+    g = np.random.default_rng(12)
+    probs, Gs, xs, ys = [], [], [], []
+    for k in range(24):
+        n = int(g.integers(8, 120))
+        m = int(g.integers(1, max(2, n // 2)))
+        p = int(g.integers(n, n + n // 4 + 1))
+        G = I.zgls_svd(300 + k, n, m, p, float(10 ** g.uniform(0, 3)), 1e1)
+        Gs.append(G)
+        probs.append(dict(W=zdev(G["W"]), V=zdev(G["V"]), d=zdev(G["d"])))
+        xs.append(zzeros(m))
+        ys.append(zzeros(p))
+    st, infos = h.zgls_solve_batched(probs, xs, ys)
+    assert st == 0
+    from oracle import zoracle as Z
+    for G, x, y, f in zip(Gs, xs, ys, infos):
+        assert f.status == 0
+        W, V, d = G["W"], G["V"], G["d"]
+        t = Z.zgls_truth(W, V, d)
+        xh, yh = zhost(x), zhost(y)
+        e_con = np.linalg.norm(W @ xh + V @ yh - d) / (np.linalg.norm(W) * np.linalg.norm(xh) +
+                                                      np.linalg.norm(V) * np.linalg.norm(yh) + np.linalg.norm(d))
+        assert e_con <= 1e-14
+        xe = np.concatenate([t["x"].real, t["x"].imag])
+        ye = np.concatenate([t["y"].real, t["y"].imag])
+        F = oracle_mod.gls_factor(embed(W), embed(V), "fp64")
+        kap = oracle_mod.gls_kappa(F, xe, ye)[0]
+        assert rel(xh, t["x"]) <= 10 * kap * U, (rel(xh, t["x"]), kap)
