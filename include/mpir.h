@@ -97,10 +97,18 @@ typedef struct {
     double inner_tol;  /* GMRES relative residual target, <= 0: 1e-8 (FP32 u_f),
                           1e-4 (BF16/TF32 u_f)                                    */
     double alpha;      /* F~ scaling alpha (Sec. 5), <= 0: ||r0|| (LSE) / ||y0||
-                          (GLS), floored as described in the design notes         */
+                          (GLS), floored at sqrt(u) ||A||_F ||x0|| (||V||_F ||z0||),
+                          1 if both are zero                                      */
     double beta;       /* F~ scaling beta, <= 0: 1                                */
     int escalate;      /* nonzero: on failure re-factor at the next higher
                           precision up to FP64 (default 1)                         */
+    int resid_dd;      /* nonzero: residuals in double-double (u_r = u^2 < u,
+                          Table 2's third row): after the stop test is met the
+                          refinement continues until ||dx|| <= 4 u ||x|| or the
+                          corrections stop halving, so the forward error
+                          reaches about u rather than kappa u.  Host-driven
+                          loop; FP64 products with error-free transformations
+                          (default 0)                                             */
 } mpir_opts;
 
 typedef struct {
@@ -219,7 +227,8 @@ int zgls_solve(mpir_handle h, int n, int m, int p,
  * candidates on a sample of the batch the first time a shape is seen.
  * Problems that do not converge are re-solved one by one with an FP64
  * factorization when opts->escalate is set (info.escalated = 1).
- * refine = MPIR_GMRES or MPIR_GMRES_LEFT solves the problems one by one with lse_solve.
+ * refine = MPIR_GMRES or MPIR_GMRES_LEFT, fact = MPIR_AUTO and resid_dd solve
+ * the problems one by one with lse_solve.
  * The handle's stream is synchronized before returning.
  * ------------------------------------------------------------------- */
 int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n,

@@ -240,4 +240,16 @@ cudaError_t gls_resid_finalize(int n, int m, int p, const double *d, const doubl
                         double *f1, double *f2, double *f3, double *normpart, double *norms2,
                         cudaStream_t s);
 
+// Double-double variants (u_r = u^2): the same residual blocks and norms
+// as the finalize routines above, every product sum carried as an
+// unevaluated pair.  scr: 2 (m + p + 2 n) doubles (LSE), 2 (2 n + m + p) (GLS).
+cudaError_t lse_resid_dd(int m, int n, int p, const double *A, int lda, const double *B, int ldb, const double *b,
+                         const double *d, const double *x, const double *r, const double *v, double *scr,
+                         double *f1, double *f2, double *f3, double *norms2, cudaStream_t s);
+cudaError_t gls_resid_dd(int n, int m, int p, const double *W, int ldw, const double *V, int ldv, const double *d,
+                         const double *x, const double *y, const double *z, double *scr, double *f1, double *f2,
+                         double *f3, double *norms2, cudaStream_t s);
+// out[0] = (accumulate ? out[0] : 0) + ||a - b||^2
+cudaError_t diff_norm2(const double *a, const double *b, int n, double *out, int accumulate, cudaStream_t s);
+
 } // namespace mpir

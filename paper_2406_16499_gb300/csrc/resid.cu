@@ -204,4 +204,197 @@ cudaError_t gls_resid_finalize(int n, int m, int p, const double *d, const doubl
     return pdl_launch(k_norm_final, dim3(1), dim3(32), 0, s, normpart, nb, norms2);
 }
 
+// ---------------------------------------------------------------------------
+// Residuals in double-double (u_r = u^2, the u_r < u variant of the
+// refinement: with it the forward error reaches about u instead of kappa u).
+// Sums of FP64 products kept as unevaluated pairs (hi, lo) with the
+// error-free transformations of Knuth (TwoSum) and the FMA product
+// (TwoProd: a b = p + fma(a, b, -p) exactly); each accumulation adds the
+// product's error term to the pair's low part (relative error O(u^2)).
+// ---------------------------------------------------------------------------
+struct DD { double hi, lo; };
+
+// (the _rn intrinsics are never contracted into an FMA, which would break
+// the error-free transformations)
+__device__ __forceinline__ DD dd_two_sum(double a, double b)
+{
+    const double s = __dadd_rn(a, b), bb = __dsub_rn(s, a);
+    return DD{s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
+}
+__device__ __forceinline__ DD dd_fast_two_sum(double a, double b)
+{
+    const double s = __dadd_rn(a, b);
+    return DD{s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+__device__ __forceinline__ DD dd_add(DD a, DD b)
+{
+    DD s = dd_two_sum(a.hi, b.hi);
+    const DD t = dd_two_sum(a.lo, b.lo);
+    s.lo = __dadd_rn(s.lo, t.hi);
+    s = dd_fast_two_sum(s.hi, s.lo);
+    s.lo = __dadd_rn(s.lo, t.lo);
+    return dd_fast_two_sum(s.hi, s.lo);
+}
+// acc + a b
+__device__ __forceinline__ DD dd_mac(DD acc, double a, double b)
+{
+    const double p = __dmul_rn(a, b);
+    const double e = fma(a, b, -p);
+    DD t = dd_two_sum(acc.hi, p);
+    t.lo = __dadd_rn(t.lo, __dadd_rn(acc.lo, e));
+    return dd_fast_two_sum(t.hi, t.lo);
+}
+
+// out[i] = sum_j M(i, j) x[j] (one thread per row; coalesced column walks)
+__global__ void __launch_bounds__(256)
+k_rowdot_dd(const double *__restrict__ M, int ld, int rows, int cols, const double *__restrict__ x,
+            double *__restrict__ hi, double *__restrict__ lo)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= rows) return;
+    DD acc{0.0, 0.0};
+    const double *row = M + i;
+    for (int j = 0; j < cols; j++) acc = dd_mac(acc, row[(size_t)j * ld], x[j]);
+    hi[i] = acc.hi;
+    lo[i] = acc.lo;
+}
+
+// out[j] = sum_i M(i, j) r[i] (one warp per column)
+__global__ void __launch_bounds__(256)
+k_coldot_dd(const double *__restrict__ M, int ld, int rows, int cols, const double *__restrict__ r,
+            double *__restrict__ hi, double *__restrict__ lo)
+{
+    const int j = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= cols) return;
+    const double *col = M + (size_t)j * ld;
+    DD acc{0.0, 0.0};
+    for (int i = lane; i < rows; i += 32) acc = dd_mac(acc, col[i], r[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const DD other{__shfl_xor_sync(0xffffffffu, acc.hi, o), __shfl_xor_sync(0xffffffffu, acc.lo, o)};
+        acc = dd_add(acc, other);
+    }
+    if (lane == 0) { hi[j] = acc.hi; lo[j] = acc.lo; }
+}
+
+// out = round(s0 a + s1 c + su u + sw w): a, c plain vectors, u, w
+// double-double pairs (any of them NULL: absent); the signs are +-1, so the
+// first sum is exact as a pair
+__global__ void k_combine_dd(int n, const double *__restrict__ a, double s0, const double *__restrict__ c, double s1,
+                             const double *__restrict__ uh, const double *__restrict__ ul, double su,
+                             const double *__restrict__ wh, const double *__restrict__ wl, double sw,
+                             double *__restrict__ out)
+{
+    const int i = blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    DD acc = dd_two_sum(a ? s0 * a[i] : 0.0, c ? s1 * c[i] : 0.0);
+    if (uh) acc = dd_add(acc, DD{su * uh[i], su * ul[i]});
+    if (wh) acc = dd_add(acc, DD{sw * wh[i], sw * wl[i]});
+    out[i] = acc.hi;
+}
+
+// norms2[k] = sum of squares of vec[k] (length len[k]) for k < 6, one block
+// each, fixed-order tree reduction
+struct Vec6 { const double *v[6]; int len[6]; };
+__global__ void __launch_bounds__(256) k_norms6(Vec6 V, double *__restrict__ norms2)
+{
+    __shared__ double red[256];
+    const int k = blockIdx.x;
+    double s = 0.0;
+    if (V.v[k])
+        for (int i = threadIdx.x; i < V.len[k]; i += 256) s = fma(V.v[k][i], V.v[k][i], s);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) norms2[k] = red[0];
+}
+
+// out[0] += || a - b ||^2 (one block)
+__global__ void __launch_bounds__(256) k_diffnorm2(const double *__restrict__ a, const double *__restrict__ b, int n,
+                                                   double *__restrict__ out, int accumulate)
+{
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += 256) {
+        const double d = a[i] - b[i];
+        s = fma(d, d, s);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = (accumulate ? out[0] : 0.0) + red[0];
+}
+
+static int g256(int n) { return n > 0 ? ceil_div(n, 256) : 1; }
+
+cudaError_t lse_resid_dd(int m, int n, int p, const double *A, int lda, const double *B, int ldb, const double *b,
+                         const double *d, const double *x, const double *r, const double *v, double *scr,
+                         double *f1, double *f2, double *f3, double *norms2, cudaStream_t s)
+{
+    // scr: A x (hi, lo: m each), B x (p each), A^T r (n each), B^T v (n each)
+    double *axh = scr, *axl = axh + m, *bxh = axl + m, *bxl = bxh + p, *atrh = bxl + p, *atrl = atrh + n;
+    double *btvh = atrl + n, *btvl = btvh + n;
+    ProfScope ps(K_DUAL_GEMV, s);
+    if (m > 0) {
+        k_rowdot_dd<<<g256(m), 256, 0, s>>>(A, lda, m, n, x, axh, axl);
+        k_coldot_dd<<<ceil_div(n, 8), 256, 0, s>>>(A, lda, m, n, r, atrh, atrl);
+    }
+    if (p > 0) {
+        k_rowdot_dd<<<g256(p), 256, 0, s>>>(B, ldb, p, n, x, bxh, bxl);
+        k_coldot_dd<<<ceil_div(n, 8), 256, 0, s>>>(B, ldb, p, n, v, btvh, btvl);
+    }
+    // f1 = b - r - A x, f2 = d - B x, f3 = -A^T r + B^T v
+    if (m > 0) k_combine_dd<<<g256(m), 256, 0, s>>>(m, b, 1.0, r, -1.0, axh, axl, -1.0, nullptr, nullptr, 0.0, f1);
+    if (p > 0)
+        k_combine_dd<<<g256(p), 256, 0, s>>>(p, d, 1.0, nullptr, 0.0, bxh, bxl, -1.0, nullptr, nullptr, 0.0, f2);
+    k_combine_dd<<<g256(n), 256, 0, s>>>(n, nullptr, 0.0, nullptr, 0.0, m > 0 ? atrh : nullptr, atrl, -1.0,
+                                         p > 0 ? btvh : nullptr, btvl, 1.0, f3);
+    Vec6 V{{m > 0 ? f1 : nullptr, p > 0 ? f2 : nullptr, f3, x, m > 0 ? r : nullptr, p > 0 ? v : nullptr},
+           {m, p, n, n, m, p}};
+    k_norms6<<<6, 256, 0, s>>>(V, norms2);
+    return cudaGetLastError();
+}
+
+cudaError_t gls_resid_dd(int n, int m, int p, const double *W, int ldw, const double *V, int ldv, const double *d,
+                         const double *x, const double *y, const double *z, double *scr, double *f1, double *f2,
+                         double *f3, double *norms2, cudaStream_t s)
+{
+    // scr: W x, V y (hi, lo: n each), V^T z (p each), W^T z (m each)
+    double *wxh = scr, *wxl = wxh + n, *vyh = wxl + n, *vyl = vyh + n, *vtzh = vyl + n, *vtzl = vtzh + p;
+    double *wtzh = vtzl + p, *wtzl = wtzh + m;
+    ProfScope ps(K_DUAL_GEMV, s);
+    if (m > 0) {
+        k_rowdot_dd<<<g256(n), 256, 0, s>>>(W, ldw, n, m, x, wxh, wxl);
+        k_coldot_dd<<<ceil_div(m, 8), 256, 0, s>>>(W, ldw, n, m, z, wtzh, wtzl);
+    }
+    if (p > 0) {
+        k_rowdot_dd<<<g256(n), 256, 0, s>>>(V, ldv, n, p, y, vyh, vyl);
+        k_coldot_dd<<<ceil_div(p, 8), 256, 0, s>>>(V, ldv, n, p, z, vtzh, vtzl);
+    }
+    // f1 = -y + V^T z, f2 = d - W x - V y, f3 = W^T z
+    if (p > 0)
+        k_combine_dd<<<g256(p), 256, 0, s>>>(p, y, -1.0, nullptr, 0.0, vtzh, vtzl, 1.0, nullptr, nullptr, 0.0, f1);
+    k_combine_dd<<<g256(n), 256, 0, s>>>(n, d, 1.0, nullptr, 0.0, m > 0 ? wxh : nullptr, wxl, -1.0,
+                                         p > 0 ? vyh : nullptr, vyl, -1.0, f2);
+    if (m > 0)
+        k_combine_dd<<<g256(m), 256, 0, s>>>(m, nullptr, 0.0, nullptr, 0.0, wtzh, wtzl, 1.0, nullptr, nullptr, 0.0,
+                                             f3);
+    Vec6 Vv{{p > 0 ? f1 : nullptr, f2, m > 0 ? f3 : nullptr, m > 0 ? x : nullptr, p > 0 ? y : nullptr, z},
+            {p, n, m, m, p, n}};
+    k_norms6<<<6, 256, 0, s>>>(Vv, norms2);
+    return cudaGetLastError();
+}
+
+cudaError_t diff_norm2(const double *a, const double *b, int n, double *out, int accumulate, cudaStream_t s)
+{
+    k_diffnorm2<<<1, 256, 0, s>>>(a, b, n, out, accumulate);
+    return cudaGetLastError();
+}
+
 } // namespace mpir

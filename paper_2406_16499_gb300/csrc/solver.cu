@@ -972,6 +972,17 @@ struct StopState {
     int since_best = 0;
 };
 
+// The u_r < u variant (double-double residuals): once the backward error
+// meets the stop test the refinement goes on while the corrections keep
+// shrinking, until ||dx|| <= 4 u ||x|| or a correction is no smaller than
+// half the previous one (the forward error then sits at about u).
+struct FwdState {
+    double last = INFINITY, prev = INFINITY;
+    bool have = false;
+    bool done(double nx) const { return have && (last <= 4.0 * 1.1102230246251565e-16 * nx || last > 0.5 * prev); }
+    void push(double dx) { prev = last; last = dx; have = true; }
+};
+
 // eq. gls-stop / eq. lse-stop from squared norms; returns 1 if satisfied.
 int stop_test(const double *nrm, const double den[3], double tol, double ratio[3])
 {
@@ -1366,7 +1377,9 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
     float t_gm = 0;
     bool looped = false;
     if (o.refine != MPIR_DIRECT) RC(gls_multipliers_impl<T>(h, y, z));
-    if (o.refine == MPIR_CLASSICAL && ir_graph_usable(h)) {
+    const bool dd = o.resid_dd != 0;
+    if (dd) RC(ensure_rws(h, sizeof(double) * (2 * (size_t)(2 * n + m + p) + m + p + 8)));
+    if (o.refine == MPIR_CLASSICAL && ir_graph_usable(h) && !dd) {
         unsigned long long key = ir_mix(ir_mix(ir_mix(0, 2), sizeof(T)), (unsigned long long)n);
         for (unsigned long long v_ : {(unsigned long long)m, (unsigned long long)p, (unsigned long long)ldw,
                                       (unsigned long long)ldv, (unsigned long long)(uintptr_t)W,
@@ -1402,9 +1415,28 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
         const double fW = h->fs.fro1, fV = h->fs.fro2;
         const double nd = dnorm_host(h, d, n, w.part);
         float t_res = 0;
+        double *dds = dd ? (double *)h->rws : nullptr;
+        double *xyprev = dd ? dds + 2 * (size_t)(2 * n + m + p) : nullptr, *dxn = dd ? xyprev + m + p : nullptr;
+        FwdState fw;
+        bool bw = false;
+        // after a correction (u_r < u variant): ||[dx; dy]||
+        auto post = [&]() -> int {
+            if (!dd) return 0;
+            if (m > 0) diff_norm2(x, xyprev, m, dxn, 0, s);
+            if (p > 0) diff_norm2(y, xyprev + m, p, dxn, m > 0, s);
+            RC(read_back(h, dxn, 1));
+            fw.push(std::sqrt(h->hbuf[0]));
+            return 0;
+        };
         for (it = 0; it < o.maxit; it++) {
             cudaEventRecord(h->ev[3], s);
-            gls_residual_dev<T>(h, w, W, ldw, V, ldv, d, x, y, z);
+            if (dd) {
+                if (gls_resid_dd(n, m, p, W, ldw, V, ldv, d, x, y, z, dds, w.f1, w.f2, w.f3, w.norms2, s) !=
+                    cudaSuccess)
+                    return cuda_check(h, "gls double-double residual");
+            } else {
+                gls_residual_dev<T>(h, w, W, ldw, V, ldv, d, x, y, z);
+            }
             cudaEventRecord(h->ev[4], s);
             RC(read_back(h, w.norms2, 6));
             t_res += ev_ms(h->ev[3], h->ev[4]);
@@ -1414,10 +1446,17 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
             double den[3] = {nr[4] + fV * nr[5], nd + fW * nr[3] + fV * nr[4], fW * nr[5]};
             for (int i = 0; i < 3; i++) if (!std::isfinite(nr[i])) { st = MPIR_NONFINITE; break; }
             if (st == MPIR_NONFINITE) break;
-            if (stop_test(nr, den, o.tol, ratio)) { st = MPIR_OK; break; }
-            const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
-            if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
-            else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            bw = stop_test(nr, den, o.tol, ratio);
+            if (bw && (!dd || fw.done(std::sqrt(nr[3] * nr[3] + nr[4] * nr[4])))) { st = MPIR_OK; break; }
+            if (!bw) {
+                const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
+                if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
+                else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            }
+            if (dd) {
+                if (m > 0) cudaMemcpyAsync(xyprev, x, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+                if (p > 0) cudaMemcpyAsync(xyprev + m, y, sizeof(double) * p, cudaMemcpyDeviceToDevice, s);
+            }
             // normalize the right-hand side of the scaled correction system
             // (f1, sV f2, sW/sV f3), not the raw blocks
             if (gm) {
@@ -1433,13 +1472,16 @@ int gls_solve_once(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, c
                 cudaEventRecord(h->ev[6], s);
                 cudaEventSynchronize(h->ev[6]);
                 t_gm += ev_ms(h->ev[5], h->ev[6]);
+                RC(post());
                 continue;
             }
             const double sW = h->fs.s1, sV = h->fs.s2;
             const double fmax = std::max(nr[0], std::max(nr[1] * sV, nr[2] * sW / sV));
             const double gamma = pow2_norm(fmax);
             RC(gls_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, y, z, x));
+            RC(post());
         }
+        if (st == MPIR_NOT_CONVERGED && bw) st = MPIR_OK;     // maxit with the backward test met
         if (info) { info->time_ms[2] = t_res; info->time_ms[4] = t_gm; info->inner_iters = inner; }
     }
     RC(check_dev_flags(h));
@@ -1866,7 +1908,9 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
     float t_gm = 0;
     if (o.refine != MPIR_DIRECT || r_out || v_out) RC(lse_multipliers_impl<T>(h, A, lda, b, x, r, v));
     bool looped = false;
-    if (o.refine == MPIR_CLASSICAL && ir_graph_usable(h)) {
+    const bool dd = o.resid_dd != 0;
+    if (dd) RC(ensure_rws(h, sizeof(double) * (2 * (size_t)(m + p + 2 * n) + n + 8)));
+    if (o.refine == MPIR_CLASSICAL && ir_graph_usable(h) && !dd) {
         // the loop on the device (one CUDA-graph launch, one host read)
         unsigned long long key = ir_mix(ir_mix(ir_mix(0, 1), sizeof(T)), (unsigned long long)m);
         for (unsigned long long v_ : {(unsigned long long)n, (unsigned long long)p, (unsigned long long)lda,
@@ -1904,9 +1948,26 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
         StopState ss;
         st = MPIR_NOT_CONVERGED;
         float t_res = 0;
+        double *dds = dd ? (double *)h->rws : nullptr;
+        double *xprev = dd ? dds + 2 * (size_t)(m + p + 2 * n) : nullptr, *dxn = dd ? xprev + n : nullptr;
+        FwdState fw;
+        bool bw = false;
+        auto post = [&]() -> int {              // after a correction (u_r < u variant): ||dx||
+            if (!dd) return 0;
+            diff_norm2(x, xprev, n, dxn, 0, s);
+            RC(read_back(h, dxn, 1));
+            fw.push(std::sqrt(h->hbuf[0]));
+            return 0;
+        };
         for (it = 0; it < o.maxit; it++) {
             cudaEventRecord(h->ev[3], s);
-            lse_residual_dev<T>(h, w, A, lda, B, ldb, b, d, x, r, v);
+            if (dd) {
+                if (lse_resid_dd(m, n, p, A, lda, B, ldb, b, d, x, r, v, dds, w.f1, w.f2, w.f3, w.norms2, s) !=
+                    cudaSuccess)
+                    return cuda_check(h, "lse double-double residual");
+            } else {
+                lse_residual_dev<T>(h, w, A, lda, B, ldb, b, d, x, r, v);
+            }
             cudaEventRecord(h->ev[4], s);
             RC(read_back(h, w.norms2, 6));
             t_res += ev_ms(h->ev[3], h->ev[4]);
@@ -1917,10 +1978,14 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
             bool bad = false;
             for (int i = 0; i < 3; i++) if (!std::isfinite(nr[i])) bad = true;
             if (bad) { st = MPIR_NONFINITE; break; }
-            if (stop_test(nr, den, o.tol, ratio)) { st = MPIR_OK; break; }
-            const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
-            if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
-            else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            bw = stop_test(nr, den, o.tol, ratio);
+            if (bw && (!dd || fw.done(nr[3]))) { st = MPIR_OK; break; }
+            if (!bw) {
+                const double eta = std::max(ratio[0], std::max(ratio[1], ratio[2]));
+                if (eta < 0.5 * ss.best) { ss.best = eta; ss.since_best = 0; }
+                else if (++ss.since_best >= 3) { st = ss.best <= 1e-14 ? MPIR_OK : MPIR_NOT_CONVERGED; break; }
+            }
+            if (dd) cudaMemcpyAsync(xprev, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
             // normalize the right-hand side of the scaled correction system
             // (f1, sB/sA f2, sA f3), not the raw blocks
             if (gm) {
@@ -1936,12 +2001,15 @@ int lse_solve_once(mpir_ctx *h, int m, int n, int p, const double *A, int lda, c
                 cudaEventRecord(h->ev[6], s);
                 cudaEventSynchronize(h->ev[6]);
                 t_gm += ev_ms(h->ev[5], h->ev[6]);
+                RC(post());
                 continue;
             }
             const double sA = h->fs.s1, sB = h->fs.s2;
             const double gamma = pow2_norm(std::max(nr[0], std::max(nr[1] * sB / sA, nr[2] * sA)));
             RC(lse_correction_impl<T>(h, w.f1, w.f2, w.f3, gamma, r, v, x));
+            RC(post());
         }
+        if (st == MPIR_NOT_CONVERGED && bw) st = MPIR_OK;     // maxit with the backward test met
         if (info) { info->time_ms[2] = t_res; info->time_ms[4] = t_gm; info->inner_iters = inner; }
     }
     RC(check_dev_flags(h));
@@ -2736,8 +2804,8 @@ int lse_solve_batched(mpir_handle h, int count, const int *m, const int *n, cons
     if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
     std::vector<int> all(count);
     for (int i = 0; i < count; i++) all[i] = i;
-    // GMRES-IR and the learned selector run problem by problem
-    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT || o.fact == MPIR_AUTO)
+    // GMRES-IR, the learned selector and double-double residuals run problem by problem
+    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT || o.fact == MPIR_AUTO || o.resid_dd)
         return lse_solve_each(h, all, m, n, p, A, lda, B, ldb, b, d, x, o, infos, 0);
     std::vector<BInst> insts(count);
     for (int i = 0; i < count; i++)
@@ -2805,7 +2873,7 @@ int gls_solve_batched(mpir_handle h, int count, const int *n, const int *m, cons
     if (infos) std::memset(infos, 0, sizeof(mpir_info) * count);
     std::vector<int> all(count);
     for (int i = 0; i < count; i++) all[i] = i;
-    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT || o.fact == MPIR_AUTO)
+    if (o.refine == MPIR_GMRES || o.refine == MPIR_GMRES_LEFT || o.fact == MPIR_AUTO || o.resid_dd)
         return gls_solve_each(h, all, n, m, p, W, ldw, V, ldv, d, x, y, o, infos, 0);
     std::vector<BInst> insts(count);
     for (int i = 0; i < count; i++)

@@ -28,7 +28,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("fact", ctypes.c_int), ("refine", ctypes.c_int), ("tol", ctypes.c_double),
                 ("maxit", ctypes.c_int), ("restart", ctypes.c_int), ("inner_maxit", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
-                ("escalate", ctypes.c_int)]
+                ("escalate", ctypes.c_int), ("resid_dd", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):

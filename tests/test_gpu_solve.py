@@ -176,3 +176,30 @@ def test_power_of_two_scaling(h, oracle_mod):
     assert st == 0
     met = oracle_mod.lse_metrics(P["A"], P["B"], P["b"], P["d"], x, r, v)
     assert met["eta"] <= 1e-14
+
+
+@pytest.mark.parametrize("kind", ["lse", "gls"])
+def test_double_double_residual_reaches_u(h, oracle_mod, kind):
+    """The u_r < u variant (resid_dd, Table 2's third row): residuals in
+    double-double and refinement until the corrections stop shrinking give a
+    forward error of a few u even at cond = 1e6, where the FP64 residual
+    leaves it near kappa u (checked against the oracle's solution, itself
+    refined with double-double residuals)."""
+    U = 1.1102230246251565e-16
+    if kind == "lse":
+        P = I.lse_svd(4711, 300, 150, 20, 1e6, 1e1)
+        t = oracle_mod.lse_truth(P["A"], P["B"], P["b"], P["d"])
+        st, info, x, r, v = run_lse(h, P, fact="fp64", resid_dd=1, escalate=False)
+        st0, _, x0, _, _ = run_lse(h, P, fact="fp64", escalate=False)
+        met = oracle_mod.lse_metrics(P["A"], P["B"], P["b"], P["d"], x, r, v)
+    else:
+        G = I.gls_svd(4712, 300, 80, 320, 1e6, 1e1)
+        t = oracle_mod.gls_truth(G["W"], G["V"], G["d"])
+        st, info, x, y, z = run_gls(h, G, fact="fp64", resid_dd=1, escalate=False)
+        st0, _, x0, _, _ = run_gls(h, G, fact="fp64", escalate=False)
+        met = oracle_mod.gls_metrics(G["W"], G["V"], G["d"], x, y, z)
+    assert st == 0 and st0 == 0
+    assert met["eta"] <= 1e-14 and met["e_con"] <= 1e-14, met
+    fe, fe0 = rel(x, t["x"]), rel(x0, t["x"])
+    print("%s: forward error %.2e with double-double residuals, %.2e with FP64 residuals" % (kind, fe, fe0))
+    assert fe <= 20 * U, (fe, fe0)
