@@ -473,7 +473,10 @@ static int launch_tc(const CUtensorMap &A, const CUtensorMap &A2, const CUtensor
                      const TcArgs &args, int ntn, int ntm, int nsplit, cudaStream_t s)
 {
     constexpr bool BF = MODE == TCM_BF16;
-    constexpr int STAGES = MODE == TCM_TF32X3 ? 3 : (BF ? 2 : 5);
+    // C -= D (K = 128: four K steps) keeps one or two stages, so that two CTAs
+    // share an SM and one's C read / write epilogue overlaps the other's
+    // loads and MMAs; the split-K products keep a deep pipeline
+    constexpr int STAGES = EPI == TCE_SUB ? (MODE == TCM_TF32 ? 2 : 1) : (MODE == TCM_TF32X3 ? 3 : (BF ? 2 : 5));
     constexpr int NA = MODE == TCM_TF32X3 || BF ? 2 : 1;
     constexpr int NBUF = MODE == TCM_TF32X3 || BF ? 2 : 1;
     const size_t smem =
