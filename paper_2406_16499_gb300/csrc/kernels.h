@@ -119,13 +119,20 @@ int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int 
 // entries per block, column-major; zero pivot -> bit 1 of *status) that
 // trsv64 reads.  trsv64 returns -1 when it cannot run (the caller then uses
 // the 32-row solve by substitution).  dinv_elems(N): entries of an inverse
-// array for either block size.
+// array for either block size.  t64_pack copies the off-diagonal block
+// columns of an order-N triangle into the order the solves read them
+// (t64_pack_elems(N) floats, 16-byte aligned; once per factorization); a
+// solve of any leading n x n block (n <= npack) may pass that pack, or
+// nullptr to read U in place.
 bool trsv64_ok(int n, size_t ts_bytes);
 size_t dinv_elems(int N);
+size_t t64_pack_elems(int N);
+int t64_pack(const float *U, int ldu, int N, float *pack, cudaStream_t s);
 template <typename TS, typename T>
 void invert_diag64(const TS *U, int ldu, int N, T *Dinv, int *status, cudaStream_t s);
 template <typename T>
-int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *err, cudaStream_t s);
+int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, const float *pack, int npack, int *err,
+           cudaStream_t s);
 // Mixed precision (factors stored as TS, arithmetic and vectors in T).
 template <typename TS, typename T>
 int trsv_upper_mixed(const TS *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s,

@@ -156,6 +156,7 @@ template <typename T> struct LseWs {
     T *Bt, *tauB, *TwB, *X, *At, *tauA, *TwA, *Tw128B, *Tw128A, *DinvB, *DinvA;
     T *TfB, *TfA;                        // aggregated compact-WY factors (FP32 storage only)
     int ldtB, ldtA;
+    float *PkB, *PkA;                    // packed block columns of R~ (p) and T (kA) for trsv64
     void *gws;                           // scratch of the two-level factorization
     void *wy;                            // scratch of the aggregated vector applications
     void *gws2;                          // side-stream scratch of the aggregated factors
@@ -172,6 +173,7 @@ template <typename T> struct GlsWs {
     T *Wf, *tauW, *TwW, *Cf, *Ct, *tauC, *TwC, *Tw128W, *Tw128C, *DinvW, *DinvC;
     T *TfW, *TfC;                        // aggregated compact-WY factors (FP32 storage only)
     int ldtW, ldtC;
+    float *PkW, *PkC;                    // packed block columns of R (m) and T~ (kC) for trsv64
     void *gws;                           // scratch of the two-level factorization
     void *wy;                            // scratch of the aggregated vector applications
     void *gws2;                          // side-stream scratch of the aggregated factors
@@ -211,6 +213,8 @@ template <typename T> LseWs<T> lse_layout(void *base, int m, int n, int p, size_
         w.TfA = c.take<T>((size_t)w.ldtA * std::max(w.kA, 1));
         w.wy = c.take<unsigned char>(std::max(wy_apply_ws_bytes(n, p), wy_apply_ws_bytes(m, w.kA)));
         w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, p + m), geqrf_ws_bytes(m, n)));
+        w.PkB = c.take<float>(t64_pack_elems(p));
+        w.PkA = c.take<float>(t64_pack_elems(w.kA));
     }
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.ty = c.take<T>(mx); w.tq = c.take<T>(mx);
     w.tb = c.take<T>(mx); w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
@@ -262,6 +266,8 @@ template <typename T> GlsWs<T> gls_layout(void *base, int n, int m, int p, size_
         w.TfC = c.take<T>((size_t)w.ldtC * std::max(w.kC, 1));
         w.wy = c.take<unsigned char>(std::max(wy_apply_ws_bytes(n, m), wy_apply_ws_bytes(p, w.kC)));
         w.gws2 = c.take<unsigned char>(std::max(geqrf_ws_bytes(n, m + p), geqrf_ws_bytes(p, n)));
+        w.PkW = c.take<float>(t64_pack_elems(m));
+        w.PkC = c.take<float>(t64_pack_elems(w.kC));
     }
     w.tu = c.take<T>(mx); w.tw = c.take<T>(mx); w.th = c.take<T>(mx); w.tg = c.take<T>(mx);
     w.tt = c.take<T>(mx); w.tt2 = c.take<T>(mx);
@@ -547,12 +553,15 @@ GemmPrec gemm_prec(int fact)
 
 // Triangular solve with FP32 or FP64 factors: FP32 factors of order <= 8192
 // use 64-row diagonal blocks (inverses from inv_diag), others 32-row blocks.
+// pk: the packed block columns of the order-npk triangle whose leading
+// n x n block is solved (FP32 factors; nullptr reads U in place).
 template <typename T>
-int tsolve(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s, const T *Dinv)
+int tsolve(const T *U, int ldu, int n, int trans, T *x, const DevScratch &sc, cudaStream_t s, const T *Dinv,
+           const float *pk = nullptr, int npk = 0)
 {
     if constexpr (sizeof(T) == 4) {
         if (trsv64_ok(n, sizeof(T))) {
-            const int rc = trsv64<T>(U, ldu, n, trans, x, Dinv, sc.err, s);
+            const int rc = trsv64<T>(U, ldu, n, trans, x, Dinv, pk, npk, sc.err, s);
             if (rc >= 0) return rc;
             return trsv_upper<T>(U, ldu, n, trans, x, sc, s, nullptr);
         }
@@ -648,6 +657,12 @@ int gls_factor_impl(mpir_ctx *h, int n, int m, int p, const double *W, int ldw, 
     // inverses of the 32 x 32 diagonal blocks of R and T~ for the solves
     inv_diag<T>(w.Wf, w.ldW, m, w.DinvW, h->sc.status, s);
     inv_diag<T>(w.Ct, w.ldCt, w.L, w.DinvC, h->sc.status, s);   // T~_L, the block that is solved
+    if constexpr (sizeof(T) == 4) {
+        // block columns of R and of the whole T~ (the preconditioners solve
+        // with its leading min(n, p) block) in the solves' read order
+        RC(t64_pack(w.Wf, w.ldW, m, w.PkW, s));
+        RC(t64_pack(w.Ct, w.ldCt, w.kC, w.PkC, s));
+    }
     if (sizeof(T) == 4) join_side(h, s);
     return cuda_check(h, "gls_factor");
 }
@@ -668,11 +683,11 @@ int gls_initial_impl(mpir_ctx *h, const double *d, double *x, double *y)
     // T22 s2 = c2  <=>  T~_L^T s~2 = P_L c2   (s~2 in tg[0:L], tg[L:p] = 0)
     vzero(w.tg, sizeof(T) * p, s);
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
-    RC(tsolve<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC, w.PkC, w.kC));
     // R x = c1 - T12 s2,  P_m (T12 s2) = T~_12^T s~2
     RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 1, T(1), w.tg, T(0), w.tt, 0, 0, s));
     vcomb<T>(w.tt2, m, w.tu, 0, T(1), w.tt, 1, T(-1), s);
-    RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s, w.DinvW));
+    RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt2, h->sc, s, w.DinvW, w.PkW, w.m));
     vcopy<T, double>(w.tt2, x, m, fs.s1, 0, s, g + 1);
     // y = Z^T [0; s2] = P_p Z~ [s~2; 0]
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
@@ -695,7 +710,7 @@ int gls_multipliers_impl(mpir_ctx *h, const double *y, double *z)
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // T~_L h~2 = w~[0:L]
     vcomb<T>(w.th, L, w.tw, 0, T(1), nullptr, 0, T(0), s);
-    RC(tsolve<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 0, w.th, h->sc, s, w.DinvC, w.PkC, w.kC));
     // z' = Q [0_m; P_L h~2]
     vzero(w.tt, sizeof(T) * n, s);
     vcomb<T>(w.tt + m, L, w.th, 1, T(1), nullptr, 0, T(0), s);
@@ -729,17 +744,17 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 1, w.tw, h->sc, s));
     // step 3: R^T h1 = f3'   (th[0:m] = h1)
     vcopy<double, T>(f3, w.th, m, c3, 0, s, d3);
-    RC(tsolve<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s, w.DinvW));
+    RC(tsolve<T>(w.Wf, w.ldW, m, 1, w.th, h->sc, s, w.DinvW, w.PkW, w.m));
     // h~1 = P_m h1 (tt)
     vcomb<T>(w.tt, m, w.th, 1, T(1), nullptr, 0, T(0), s);
     // step 4: T22 g2 = u2  <=>  T~_L^T g~2 = P_L u2   (tg[0:L] = g~2)
     vcomb<T>(w.tg, L, w.tu + m, 1, T(1), nullptr, 0, T(0), s);
-    RC(tsolve<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 1, w.tg, h->sc, s, w.DinvC, w.PkC, w.kC));
     // step 5: T22^T h2 = w2 - g2 - T12^T h1  <=>  T~_L h~2 = w~2 - g~2 - T~_12 h~1
     RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 0, T(1), w.tt, T(0), w.tt2, 0, 0, s));
     vcomb<T>(w.th + m, L, w.tw, 0, T(1), w.tg, 0, T(-1), s);
     vcomb<T>(w.th + m, L, w.th + m, 0, T(1), w.tt2, 0, T(-1), s);
-    RC(tsolve<T>(w.Ct, w.ldCt, L, 0, w.th + m, h->sc, s, w.DinvC));
+    RC(tsolve<T>(w.Ct, w.ldCt, L, 0, w.th + m, h->sc, s, w.DinvC, w.PkC, w.kC));
     // step 6: g1 = w1 - T11^T h1  <=>  g~1 = w~1 - T~_22 h~1   (tg[L:p])
     if (o > 0) {
         vcomb<T>(w.tg + L, o, w.tw + L, 0, T(1), nullptr, 0, T(0), s);
@@ -750,7 +765,7 @@ int gls_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     RC(gemv<T>(w.Ct + idx2(0, L, w.ldCt), w.ldCt, L, m, 1, T(1), w.tg, T(0), w.tt2, 0, 0, s));
     if (o > 0) RC(gemv<T>(w.Ct + idx2(L, L, w.ldCt), w.ldCt, o, m, 1, T(1), w.tg + L, T(1), w.tt2, 1, 0, s));
     vcomb<T>(w.tt, m, w.tu, 0, T(1), w.tt2, 1, T(-1), s);
-    RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s, w.DinvW));
+    RC(tsolve<T>(w.Wf, w.ldW, m, 0, w.tt, h->sc, s, w.DinvW, w.PkW, w.m));
     vaxpy<T>(w.tt, dx, m, i3, 0, s, e3);
     // step 7: dy = Z^T g = P_p Z~ g~
     RC(vapply<T>(w.Ct, w.ldCt, p, w.kC, w.TwC, w.Tw128C, w.TfC, w.ldtC, w.wy, 0, w.tg, h->sc, s));
@@ -1063,11 +1078,11 @@ BDScratch bd_layout(void *base, int N, int R, int mx)
 // inv_diag_d), others 32-row blocks.
 template <typename T>
 int trsv_d(const T *U, int ldu, int n, int trans, double *x, const DevScratch &sc, cudaStream_t s,
-           const double *Dinv)
+           const double *Dinv, const float *pk = nullptr, int npk = 0)
 {
     if constexpr (sizeof(T) == 4) {
         if (trsv64_ok(n, sizeof(T))) {
-            const int rc = trsv64<double>(U, ldu, n, trans, x, Dinv, sc.err, s);
+            const int rc = trsv64<double>(U, ldu, n, trans, x, Dinv, pk, npk, sc.err, s);
             if (rc >= 0) return rc;
             return trsv_upper_mixed<T, double>(U, ldu, n, trans, x, sc, s, nullptr);
         }
@@ -1110,15 +1125,15 @@ int vapply_d(const T *V, int ldv, int M, int K, const T *Tw, const T *Tw128, con
 // leading r x r block.
 template <typename T>
 int trsv_trap(mpir_ctx *h, const T *Tp, int ld, int r, int N, double c, int trans, double *x, const double *Dinv,
-              cudaStream_t s)
+              cudaStream_t s, const float *pk = nullptr, int npk = 0)
 {
-    if (r >= N) return trsv_d<T>(Tp, ld, N, trans, x, h->sc, s, Dinv);
+    if (r >= N) return trsv_d<T>(Tp, ld, N, trans, x, h->sc, s, Dinv, pk, npk);
     if (!trans) {                      // c x2 = t2;  T11 x1 = t1 - T12 x2
         vcomb<double>(x + r, N - r, x + r, 0, 1.0 / c, nullptr, 0, 0.0, s);
         RC(gemv_d<T>(Tp + idx2(0, r, ld), ld, r, N - r, 0, -1.0, x + r, 1.0, x, 0, 0, s));
-        return trsv_d<T>(Tp, ld, r, 0, x, h->sc, s, Dinv);
+        return trsv_d<T>(Tp, ld, r, 0, x, h->sc, s, Dinv, pk, npk);
     }
-    RC(trsv_d<T>(Tp, ld, r, 1, x, h->sc, s, Dinv));      // T11^T x1 = t1
+    RC(trsv_d<T>(Tp, ld, r, 1, x, h->sc, s, Dinv, pk, npk));      // T11^T x1 = t1
     RC(gemv_d<T>(Tp + idx2(0, r, ld), ld, r, N - r, 1, -1.0, x, 1.0, x + r, 0, 0, s));   // t2 - T12^T x1
     vcomb<double>(x + r, N - r, x + r, 0, 1.0 / c, nullptr, 0, 0.0, s);                  // x2 = (...) / c
     return 0;
@@ -1183,7 +1198,7 @@ struct GlsBDOp : LinOp {
         vcomb<double>(u, p, t, 0, 1.0 / sa, nullptr, 0, 0.0, s);
         // a^1/2 Q T2^-T t2 = a^1/2 sV Q P_n T~_n'^-1 P_n t2
         vcomb<double>(b.w1, n, t + p, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_trap<T>(h, w.Ct, w.ldCt, rT(), n, sV, 0, b.w1, b.dT, s));
+        RC(trsv_trap<T>(h, w.Ct, w.ldCt, rT(), n, sV, 0, b.w1, b.dT, s, w.PkC, w.kC));
         vcomb<double>(u + p, n, b.w1, 1, sa * sV, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 0, u + p, s));
         if (m > 0) {
@@ -1191,7 +1206,7 @@ struct GlsBDOp : LinOp {
             vcomb<double>(b.w1, m, t + p + n, 1, 1.0, nullptr, 0, 0.0, s);
             RC(trap_tail_gemv<T>(w.Ct, w.ldCt, rT(), n, w.L, sV, 1, b.w1, b.w2, s));
             vcomb<double>(u + p + n, m, b.w2, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Wf, w.ldW, m, 0, u + p + n, h->sc, s, b.dR));
+            RC(trsv_d<T>(w.Wf, w.ldW, m, 0, u + p + n, h->sc, s, b.dR, w.PkW, w.m));
         }
         return 0;
     }
@@ -1219,12 +1234,12 @@ struct GlsBDOp : LinOp {
         vcomb<double>(b.w1, n, g + p, 0, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Wf, w.ldW, n, m, w.TwW, w.Tw128W, w.TfW, w.ldtW, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_trap<T>(h, w.Ct, w.ldCt, rT(), n, sV, 1, b.w2, b.dT, s));
+        RC(trsv_trap<T>(h, w.Ct, w.ldCt, rT(), n, sV, 1, b.w2, b.dT, s, w.PkC, w.kC));
         vcomb<double>(o + p, n, b.w2, 1, sa * sV, nullptr, 0, 0.0, s);
         if (m > 0) {
             // a^-1/2 b^-1 S^T R^-T g3 = a^-1/2 b^-1 (sW/sV) P_m T~_S' P_m R'^-T g3
             vcomb<double>(b.w1, m, g + p + n, 0, 1.0, nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Wf, w.ldW, m, 1, b.w1, h->sc, s, b.dR));
+            RC(trsv_d<T>(w.Wf, w.ldW, m, 1, b.w1, h->sc, s, b.dR, w.PkW, w.m));
             vcomb<double>(b.w2, m, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
             RC(trap_tail_gemv<T>(w.Ct, w.ldCt, rT(), n, w.L, sV, 0, b.w2, b.w3, s));
             vcomb<double>(o + p + n, m, b.w3, 1, sW / (sV * sa * be), nullptr, 0, 0.0, s);
@@ -1550,6 +1565,12 @@ int lse_factor_impl(mpir_ctx *h, int m, int n, int p, const double *A, int lda, 
     // inverses of the 32 x 32 diagonal blocks of R~ and T for the solves
     inv_diag<T>(w.Bt, w.ldBt, p, w.DinvB, h->sc.status, s);
     inv_diag<T>(w.At, w.ldAt, w.q, w.DinvA, h->sc.status, s);   // T11, the block that is solved
+    if constexpr (sizeof(T) == 4) {
+        // block columns of R~ and of the whole T (the preconditioners solve
+        // with its leading min(m, n) block) in the solves' read order
+        RC(t64_pack(w.Bt, w.ldBt, p, w.PkB, s));
+        RC(t64_pack(w.At, w.ldAt, w.kA, w.PkA, s));
+    }
     if (sizeof(T) == 4) join_side(h, s);
     return cuda_check(h, "lse_factor");
 }
@@ -1570,12 +1591,12 @@ int lse_initial_impl(mpir_ctx *h, const double *b, const double *d, double *x)
     RC(vapply<T>(w.At, w.ldAt, m, w.kA, w.TwA, w.Tw128A, w.TfA, w.ldtA, w.wy, 1, w.tw, h->sc, s));
     // R y2 = sB d  <=>  R~^T y~2 = P_p (sB d)
     vcopy<double, T>(d, w.tb, p, fs.s2, 1, s, g);
-    RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
+    RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB, w.PkB, w.p));
     // ty = [y1; y2], y2 = P_p y~2
     vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     vcomb<T>(w.ty, q, w.tw, 0, T(1), nullptr, 0, T(0), s);
     RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
-    RC(tsolve<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
+    RC(tsolve<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA, w.PkA, w.kA));
     // x = Q^T y = P_n Q~ P_n y
     vcomb<T>(w.tt, n, w.ty, 1, T(1), nullptr, 0, T(0), s);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, w.tt, h->sc, s));
@@ -1604,7 +1625,7 @@ int lse_multipliers_impl(mpir_ctx *h, const double *A, int lda, const double *b,
     vcopy<double, T>(w.f3, w.tu, n, fs.s1, 1, s, g);
     RC(vapply<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, w.tu, h->sc, s));
     // R~ (P_p v') = u~[0:p]
-    RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s, w.DinvB));
+    RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tu, h->sc, s, w.DinvB, w.PkB, w.p));
     vcopy<T, double>(w.tu, v, p, fs.s2 / fs.s1, 1, s, g + 1);
     return cuda_check(h, "lse_multipliers");
 }
@@ -1637,17 +1658,17 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
     // step 3: R y2 = f2'  <=>  R~^T y~2 = P_p f2'
     if (p > 0) {
         vcopy<double, T>(f2, w.tb, p, c2, 1, s, d2);
-        RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB));
+        RC(tsolve<T>(w.Bt, w.ldBt, p, 1, w.tb, h->sc, s, w.DinvB, w.PkB, w.p));
         vcomb<T>(w.ty + q, p, w.tb, 1, T(1), nullptr, 0, T(0), s);
     }
     // step 4: T11^T q1 = u1
     if (q > 0) {
         vcomb<T>(w.tq, q, w.tu + p, 1, T(1), nullptr, 0, T(0), s);
-        RC(tsolve<T>(w.At, w.ldAt, q, 1, w.tq, h->sc, s, w.DinvA));
+        RC(tsolve<T>(w.At, w.ldAt, q, 1, w.tq, h->sc, s, w.DinvA, w.PkA, w.kA));
         // step 5: T11 y1 = w1 - q1 - T12 y2
         vcomb<T>(w.ty, q, w.tw, 0, T(1), w.tq, 0, T(-1), s);
         if (p > 0) RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 0, T(-1), w.ty + q, T(1), w.ty, 0, 0, s));
-        RC(tsolve<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA));
+        RC(tsolve<T>(w.At, w.ldAt, q, 0, w.ty, h->sc, s, w.DinvA, w.PkA, w.kA));
     }
     // step 6: q2 = w2 - T22 y2
     if (m - q > 0) {
@@ -1660,7 +1681,7 @@ int lse_correction_impl(mpir_ctx *h, const double *f1, const double *f2, const d
         if (q > 0) RC(gemv<T>(w.At + idx2(0, q, w.ldAt), w.ldAt, q, p, 1, T(1), w.tq, T(0), w.tt, 0, 0, s));
         if (m - q > 0) RC(gemv<T>(w.At + idx2(q, q, w.ldAt), w.ldAt, m - q, p, 1, T(1), w.tq + q, T(1), w.tt, 1, 0, s));
         vcomb<T>(w.tb, p, w.tt, 1, T(1), w.tu, 0, T(-1), s);
-        RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tb, h->sc, s, w.DinvB));
+        RC(tsolve<T>(w.Bt, w.ldBt, p, 0, w.tb, h->sc, s, w.DinvB, w.PkB, w.p));
         vaxpy<T>(w.tb, dv, p, i2, 1, s, e2);
     }
     // step 7: dr = Z q ; dx = Q^T y = P_n Q~ P_n y
@@ -1732,12 +1753,12 @@ struct LseBDOp : LinOp {
             // a^-1/2 b^-1 R^-T S^T t2 = a^-1/2 b^-1 (sB/sA) P_p R~'^-1 P_p S'^T t2
             RC(trap_tail_gemv<T>(w.At, w.ldAt, rT(), n, w.q, sA, 1, t + m, b.w1, s));
             vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Bt, w.ldBt, p, 0, b.w2, h->sc, s, b.dR));
+            RC(trsv_d<T>(w.Bt, w.ldBt, p, 0, b.w2, h->sc, s, b.dR, w.PkB, w.p));
             vcomb<double>(u + m, p, b.w2, 1, sB / (sA * sa * be), nullptr, 0, 0.0, s);
         }
         // a^1/2 Q^T T1^-1 t3 = a^1/2 sA P_n Q~ P_n T1'^-1 t3
         vcomb<double>(b.w1, n, t + m + p, 0, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_trap<T>(h, w.At, w.ldAt, rT(), n, sA, 0, b.w1, b.dT, s));
+        RC(trsv_trap<T>(h, w.At, w.ldAt, rT(), n, sA, 0, b.w1, b.dT, s, w.PkA, w.kA));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 0, b.w2, s));
         vcomb<double>(u + m + p, n, b.w2, 1, sa * sA, nullptr, 0, 0.0, s);
@@ -1767,7 +1788,7 @@ struct LseBDOp : LinOp {
         if (p > 0) {
             // a^-1/2 b^-1 S R^-1 g2 = a^-1/2 b^-1 (sB/sA) S' P_p R~'^-T P_p g2
             vcomb<double>(b.w1, p, g + m, 1, 1.0, nullptr, 0, 0.0, s);
-            RC(trsv_d<T>(w.Bt, w.ldBt, p, 1, b.w1, h->sc, s, b.dR));
+            RC(trsv_d<T>(w.Bt, w.ldBt, p, 1, b.w1, h->sc, s, b.dR, w.PkB, w.p));
             vcomb<double>(b.w2, p, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
             RC(trap_tail_gemv<T>(w.At, w.ldAt, rT(), n, w.q, sA, 0, b.w2, b.w3, s));
             vcomb<double>(o + m, p, b.w3, 0, sB / (sA * sa * be), nullptr, 0, 0.0, s);
@@ -1777,7 +1798,7 @@ struct LseBDOp : LinOp {
         if (h->fs.colscale) vdiag<double>(b.w1, w.D, n, 1, s);
         RC(vapply_d<T>(w.Bt, w.ldBt, n, p, w.TwB, w.Tw128B, w.TfB, w.ldtB, w.wy, 1, b.w1, s));
         vcomb<double>(b.w2, n, b.w1, 1, 1.0, nullptr, 0, 0.0, s);
-        RC(trsv_trap<T>(h, w.At, w.ldAt, rT(), n, sA, 1, b.w2, b.dT, s));
+        RC(trsv_trap<T>(h, w.At, w.ldAt, rT(), n, sA, 1, b.w2, b.dT, s, w.PkA, w.kA));
         vcomb<double>(o + m + p, n, b.w2, 0, sa * sA, nullptr, 0, 0.0, s);
         return 0;
     }

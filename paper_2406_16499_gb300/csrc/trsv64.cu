@@ -17,6 +17,18 @@
 // No cluster-wide barrier per step: the chain from one block's owner to the
 // next is one distributed-shared-memory hop, and no dependent global-memory
 // read sits on it.
+//
+// Packed block columns.  Read in place, a step's entries are 64 strided
+// 4-byte columns (U x = b) or one 256-byte column piece per thread, 32
+// different lines per warp load (U^T x = b); the cluster's 16 SMs then move
+// them at a small fraction of their bandwidth.  Once per factorization
+// t64_pack copies every off-diagonal block column into the order the solve
+// reads it: block column J (columns 64J .. 64J+63) as [16 quads][rows][4],
+// rows 0 .. 64J-1 for U x = b and rows 64(J+1) .. N-1 (entries of U^T) for
+// U^T x = b, so a warp's load of one quad for 32 consecutive rows is 512
+// contiguous bytes and a CTA's share of a step is 16 contiguous runs.  A
+// pack of order N serves the solves with any leading n x n block (n <= N).
+
 #include "common.cuh"
 #include "kernels.h"
 #include "mpir.h"
@@ -28,6 +40,64 @@ constexpr int T64_MAXN = 16 * T64_THREADS;
 constexpr int T64_DS = 64 * 65;                  // one staged inverse, rows padded
 
 bool trsv64_ok(int n, size_t ts_bytes) { return ts_bytes == 4 && n > 0 && n <= T64_MAXN; }
+
+// Float offsets of block column J in the packs of an order-N triangle:
+// U x = b pack (rows above the block), then the U^T x = b pack (rows below).
+__host__ __device__ __forceinline__ size_t t64_off_n(int J) { return (size_t)2048 * J * (J - 1 > 0 ? J - 1 : 0); }
+__host__ __device__ __forceinline__ int t64_rows_t(int N, int J) { const int r = N - 64 * (J + 1); return r > 0 ? r : 0; }
+__host__ __device__ __forceinline__ size_t t64_off_t(int N, int J)
+{
+    // 64 * sum_{J' < J} (N - 64 (J' + 1)), every term positive for J <= nblk - 1
+    return (size_t)64 * ((size_t)J * N - (size_t)32 * J * (J + 1));
+}
+
+size_t t64_pack_elems(int N)
+{
+    if (N <= 0 || N > T64_MAXN) return 0;
+    const int nb = ceil_div(N, 64);
+    return t64_off_n(nb) + t64_off_t(N, nb - 1) + 4;
+}
+
+// One thread per packed float4: blockIdx.y = block column J, blockIdx.z = 0
+// for the U x = b pack, 1 for the U^T x = b pack.  Entries past column N - 1
+// (the partial last block) are zeros.
+__global__ void __launch_bounds__(256)
+k_t64_pack(const float *__restrict__ U, int ldu, int N, float *__restrict__ pack)
+{
+    pdl_wait();
+    pdl_trigger();
+    const int J = blockIdx.y, tr = blockIdx.z;
+    const int nb = ceil_div(N, 64);
+    const int rows = tr ? t64_rows_t(N, J) : 64 * J;
+    const int e = blockIdx.x * 256 + threadIdx.x;          // quad-major: e = q * rows + ii
+    if (e >= 16 * rows) return;
+    const int q = e / rows, ii = e % rows;
+    const int c = 64 * J + 4 * q;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!tr) {
+        if (c < N) v.x = U[idx2(ii, c, ldu)];
+        if (c + 1 < N) v.y = U[idx2(ii, c + 1, ldu)];
+        if (c + 2 < N) v.z = U[idx2(ii, c + 2, ldu)];
+        if (c + 3 < N) v.w = U[idx2(ii, c + 3, ldu)];
+    } else {
+        // rows of the U^T pack are columns i = 64 (J + 1) + ii of U; the
+        // block is full here (J < nb - 1), so c .. c + 3 < N
+        v = *reinterpret_cast<const float4 *>(U + (size_t)(64 * (J + 1) + ii) * ldu + c);
+    }
+    float *dst = pack + (tr ? t64_off_n(nb) + t64_off_t(N, J) : t64_off_n(J));
+    reinterpret_cast<float4 *>(dst)[e] = v;
+}
+
+int t64_pack(const float *U, int ldu, int N, float *pack, cudaStream_t s)
+{
+    if (N <= 64 || N > T64_MAXN || !pack) return 0;
+    if (ldu % 4 || ((uintptr_t)U & 15) || ((uintptr_t)pack & 15)) return -1;
+    const int nb = ceil_div(N, 64);
+    const int maxrows = 64 * (nb - 1);                      // the largest pack of either kind
+    ProfScope ps(K_TRSV, s);
+    cudaError_t e = pdl_launch(k_t64_pack, dim3(ceil_div(16 * maxrows, 256), nb, 2), dim3(256), 0, s, U, ldu, N, pack);
+    return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
 
 size_t dinv_elems(int N)
 {
@@ -115,17 +185,15 @@ __device__ __forceinline__ uint32_t t64_mapa(uint32_t addr, int rank)
     return r;
 }
 
-__device__ __forceinline__ void t64_st_async(uint32_t raddr, float v, uint32_t rbar)
+__device__ __forceinline__ void t64_st_async(uint32_t raddr, uint4 v, uint32_t rbar)
 {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];"
-                 ::"r"(raddr), "r"(__float_as_uint(v)), "r"(rbar) : "memory");
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];"
+                 ::"r"(raddr), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"(rbar) : "memory");
 }
 
-__device__ __forceinline__ void t64_st_async(uint32_t raddr, double v, uint32_t rbar)
-{
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];"
-                 ::"r"(raddr), "l"(__double_as_longlong(v)), "r"(rbar) : "memory");
-}
+// Threads of the owner CTA (warps 0..7) that send a solved block: 16-byte
+// pieces, one (destination, piece) pair per thread and round.
+constexpr int T64_SENDERS = 256;
 
 // Bounded wait on phase 0 of a step's mbarrier; false on timeout.  try_wait
 // parks the warp between polls, so waiting warps do not crowd the shared-
@@ -146,8 +214,8 @@ __device__ __forceinline__ bool t64_wait(uint32_t bar)
 }
 
 // Message passing instead of a cluster barrier per step: the owner of block
-// t sends x_t with st.async into slot t of every CTA, which signals that
-// CTA's mbarrier t (one slot and one barrier per step, so a fast owner never
+// t sends x_t with st.async (16-byte pieces) into slot t of every CTA, which
+// signals that CTA's mbarrier t (one slot and one barrier per step, so a fast owner never
 // overwrites a slot a slower CTA still reads).  Every CTA waits only for the
 // x block it needs next; the chain from one owner to the next is one
 // distributed-shared-memory hop.
@@ -158,9 +226,10 @@ __device__ __forceinline__ bool t64_wait(uint32_t bar)
 template <typename T, int TPR>
 __global__ void __launch_bounds__(T64_THREADS, 1)
 k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__ x, int slice,
-         const T *__restrict__ Dinv, int *__restrict__ err)
+         const T *__restrict__ Dinv, const float *__restrict__ pack, int npack, int *__restrict__ err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) T xsend[64];
     const int nblk = ceil_div(n, 64);
     unsigned long long *mbar = reinterpret_cast<unsigned long long *>(smem_raw);     // [nblk]
     T *xin = reinterpret_cast<T *>(smem_raw + 8 * ((nblk + 1) & ~1));            // [nblk][64]
@@ -208,7 +277,25 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
         const int hi = trans ? s1 : min(s1, r0);
         const bool va = i >= lo && i < hi;
         float u[CW];
-        if (trans) {
+        if (pack) {
+            // packed block column: quad q of row i at [q][row][4]
+            const int rows = trans ? t64_rows_t(npack, blk) : r0;
+            const int ii = trans ? i - (r0 + 64) : i;
+            const float4 *src = reinterpret_cast<const float4 *>(
+                pack + (trans ? t64_off_n(ceil_div(npack, 64)) + t64_off_t(npack, blk) : t64_off_n(blk)));
+#pragma unroll
+            for (int q = 0; q < CW / 4; q++) {
+                const float4 v = va ? src[(size_t)(c0 / 4 + q) * rows + ii] : make_float4(0.f, 0.f, 0.f, 0.f);
+                u[4 * q] = v.x; u[4 * q + 1] = v.y; u[4 * q + 2] = v.z; u[4 * q + 3] = v.w;
+            }
+            if (bs < 64) {
+                // the partial last block of a leading n x n solve: the pack
+                // holds columns past n - 1 (or zeros past N - 1)
+#pragma unroll
+                for (int c = 0; c < CW; c++)
+                    if (c0 + c >= bs) u[c] = 0.f;
+            }
+        } else if (trans) {
             // U(r0 + c0 + c, i): consecutive entries of column i (16-byte
             // aligned when bs = 64: r0, c0, ldu multiples of 4)
             const float *col = U + (size_t)i * ldu + r0 + c0;
@@ -231,19 +318,29 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
         const bool stage = nb >= 0 && crank == (nb * 64) / slice;
         T dn[8];
         if (stage) t64_load_d(Dinv, nb, tid, dn);
-        // 2. the owner forms x_t and sends it to every CTA (itself included)
-        if (crank == owner && tid < 64 * TPR) {
-            const int row = tid / TPR, k0 = (tid % TPR) * CW;
-            const T *Dr = Ds + par * T64_DS + row * 65 + k0;
-            const T *xb = xs + r0 - s0 + k0;
-            T acc = T(0);
+        // 2. the owner forms x_t in a staging buffer, its warps 0..7 meet on
+        // a named barrier and send it to every CTA (itself included) in
+        // 16-byte pieces
+        if (crank == owner) {
+            if (tid < 64 * TPR) {
+                const int row = tid / TPR, k0 = (tid % TPR) * CW;
+                const T *Dr = Ds + par * T64_DS + row * 65 + k0;
+                const T *xb = xs + r0 - s0 + k0;
+                T acc = T(0);
 #pragma unroll 16
-            for (int k = 0; k < CW; k++) acc = fma(Dr[k], k0 + k < bs ? xb[k] : T(0), acc);
-            if (TPR == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-            if (tid % TPR == 0) {
-                const T xv = row < bs ? acc : T(0);
-                const uint32_t dst = t64_smem(&xt[row]), bar = t64_smem(&mbar[t]);
-                for (int r = 0; r < cs; r++) t64_st_async(t64_mapa(dst, r), xv, t64_mapa(bar, r));
+                for (int k = 0; k < CW; k++) acc = fma(Dr[k], k0 + k < bs ? xb[k] : T(0), acc);
+                if (TPR == 2) acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                if (tid % TPR == 0) xsend[row] = row < bs ? acc : T(0);
+            }
+            if (tid < T64_SENDERS) {
+                asm volatile("bar.sync 1, %0;" ::"n"(T64_SENDERS) : "memory");
+                constexpr int NCH = 64 * (int)sizeof(T) / 16;
+                const uint32_t dst = t64_smem(xt), bar = t64_smem(&mbar[t]);
+                for (int e = tid; e < cs * NCH; e += T64_SENDERS) {
+                    const int r = e / NCH, ch = e % NCH;
+                    t64_st_async(t64_mapa(dst + 16 * ch, r), reinterpret_cast<const uint4 *>(xsend)[ch],
+                                 t64_mapa(bar, r));
+                }
             }
         }
         // 3. wait for x_t (after a timeout the remaining steps skip their
@@ -286,10 +383,13 @@ k_trsv64(const float *__restrict__ U, int ldu, int n, int trans, T *__restrict__
 }
 
 template <typename T>
-int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *err, cudaStream_t s)
+int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, const float *pack, int npack, int *err,
+           cudaStream_t s)
 {
     if (n <= 0) return 0;
     if (n > T64_MAXN || ldu % 4 || ((uintptr_t)U & 15)) return -1;
+    // a pack exists for orders 65 .. T64_MAXN (t64_pack writes none below)
+    if (npack < n || npack <= 64 || npack > T64_MAXN || ((uintptr_t)pack & 15)) pack = nullptr;
     const int nblk = ceil_div(n, 64);
     int want = nblk < 16 ? nblk : 16;                      // as many CTAs as the cluster allows
     // barriers, one message slot per step, two staged inverses, the owned rows
@@ -326,13 +426,15 @@ int trsv64(const float *U, int ldu, int n, int trans, T *x, const T *Dinv, int *
     cfg.attrs = at;
     cfg.numAttrs = 2;
     ProfScope ps(K_TRSV, s);
-    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv, err);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, kern, U, ldu, n, trans, x, slice, Dinv, pack, npack, err);
     return e == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
 }
 
 template void invert_diag64<float, float>(const float *, int, int, float *, int *, cudaStream_t);
 template void invert_diag64<float, double>(const float *, int, int, double *, int *, cudaStream_t);
-template int trsv64<float>(const float *, int, int, int, float *, const float *, int *, cudaStream_t);
-template int trsv64<double>(const float *, int, int, int, double *, const double *, int *, cudaStream_t);
+template int trsv64<float>(const float *, int, int, int, float *, const float *, const float *, int, int *,
+                           cudaStream_t);
+template int trsv64<double>(const float *, int, int, int, double *, const double *, const float *, int, int *,
+                            cudaStream_t);
 
 } // namespace mpir

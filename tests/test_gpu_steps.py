@@ -295,7 +295,8 @@ def test_gls_initial_and_multipliers(h, oracle_mod, fact):
 # -------------------------------------------------------- correction --
 
 @pytest.mark.parametrize("fact,eta_max", [("fp32", 1e-5), ("fp64", 1e-13)])
-@pytest.mark.parametrize("m,n,p", [(200, 100, 20), (130, 97, 50), (64, 80, 16), (900, 700, 200)])
+@pytest.mark.parametrize("m,n,p", [(200, 100, 20), (130, 97, 50), (64, 80, 16), (900, 700, 200),
+                                   pytest.param(2600, 2300, 200, id="segmented-2100")])
 def test_lse_correction_backward_error(h, fact, eta_max, m, n, p):
     """Theorem 4.3: the GPU correction solve (Alg. 1 on the held factors)
     satisfies eq. correction-system-lse with a normwise backward error of
@@ -315,7 +316,8 @@ def test_lse_correction_backward_error(h, fact, eta_max, m, n, p):
 
 
 @pytest.mark.parametrize("fact,eta_max", [("fp32", 1e-5), ("fp64", 1e-13)])
-@pytest.mark.parametrize("n,m,p", [(150, 40, 200), (130, 70, 130), (140, 90, 60), (900, 400, 800)])
+@pytest.mark.parametrize("n,m,p", [(150, 40, 200), (130, 70, 130), (140, 90, 60), (900, 400, 800),
+                                   pytest.param(2600, 1100, 2400, id="segmented-1500")])
 def test_gls_correction_backward_error(h, fact, eta_max, n, m, p):
     """Theorem 4.7: the GPU correction solve (Alg. 3 read with T22 g2 = u2
     and dz = -Q h) satisfies eq. correction-system-gls to O(u_f)."""
