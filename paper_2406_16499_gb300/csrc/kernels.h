@@ -110,6 +110,10 @@ int apply_reflectors_vec_blk(const TS *V, int ldv, int M, int K, const TS *Tw, i
 // (Z x).  Four or five full-GPU launches, no dependent per-block steps.
 // ws: wy_apply_ws_bytes(M, K) bytes (device, 256-byte aligned).
 size_t wy_apply_ws_bytes(int M, int K);
+// Reflectors per segment of the aggregated compact-WY factor: the
+// factorization forms one aggregated factor per segment, the vector
+// application runs the segments in turn.
+constexpr int WY_SEG = 2048;
 template <typename TS, typename T>
 int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int trans, T *x, void *ws,
                  cudaStream_t s);

@@ -2266,18 +2266,27 @@ k_tfull_reduce(const float *__restrict__ part, int J0, int nr, int KC, int nkc, 
 }
 
 // Block column b of Tf (outer block at J0, nr reflectors, its prepared V in
-// w and its factor Tb).  A: the matrix being factored (lda), M rows.
-static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int nr, const float *Tb, float *Tf,
+// w and its factor Tb).  A: the matrix being factored (lda), M rows.  The
+// aggregation restarts every WY_SEG reflectors: the block is coupled to the
+// earlier blocks of its own segment only (columns S .. J0-1), and its
+// column of the segment's factor sits at Tf(S.., S..) with J0 - S in place
+// of J0.  That bounds the aggregation's work by K WY_SEG^2 / 3 instead of
+// K^3 / 3; the vector application then runs one segment after another.
+static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0in, int nr, const float *Tb, float *Tf,
                        int ldt, int mode, int *err, cudaStream_t s)
 {
-    const int L = M - J0;
+    const int L = M - J0in;
+    const int S = (J0in / WY_SEG) * WY_SEG;
+    const int J0 = J0in - S;                  // position within the segment
+    A += (size_t)S * lda;                     // columns S .. J0in-1 hold the segment's earlier reflectors
+    Tf += (size_t)S * ldt + S;
     int ntile = J0 / TF_TI, KC = 32, nkc = 0;
     if (J0 > 0) {
         const int split = mode == TCM_TF32X3;
         CUtensorMap tV, tVl, tA;
         int rc = tmap_colmajor(&tV, w.V, L, OUTER_NB, w.ldv, OUTER_NB);
         rc |= tmap_colmajor(&tVl, split ? w.Vl : w.V, L, OUTER_NB, w.ldv, OUTER_NB);
-        rc |= tmap_colmajor(&tA, A + J0, L, J0, lda, OUTER_NB);
+        rc |= tmap_colmajor(&tA, A + J0in, L, J0, lda, OUTER_NB);
         if (rc) return MPIR_UNSUP();
         const int ntn = ceil_div(J0, OUTER_NB);
         const int ksteps = ceil_div(L, 32);
@@ -2287,7 +2296,7 @@ static int tfull_block(OuterWs &w, const float *A, int lda, int M, int J0, int n
         if (nsplit < 1) nsplit = 1;
         if ((size_t)nsplit * OUTER_NB * ntn * OUTER_NB > w.pcap) nsplit = 1;
         const size_t pstride = (size_t)OUTER_NB * ntn * OUTER_NB;
-        // P[z] = V_b^T A(J0:, 0:J0)   (128 x J0, split-K)
+        // P[z] = V_b^T A(J0in:, S:J0in)   (128 x J0, split-K)
         rc = gemm_tc(mode, split, TCE_STORE, tV, tVl, tA, tA, 0, 0, 0, 0, OUTER_NB, J0, L, w.P, OUTER_NB, pstride,
                      nsplit, err, s);
         if (rc) return rc;

@@ -126,11 +126,9 @@ size_t wy_apply_ws_bytes(int M, int K)
 }
 
 template <typename TS, typename T>
-int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int trans, T *x, void *ws,
-                 cudaStream_t s)
+static int wy_apply_one(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int trans, T *x, void *ws,
+                        cudaStream_t s)
 {
-    if (K <= 0 || M <= 0) return 0;
-    if (K > M || ldv < M || ldt < K || !ws) return MPIR_UNSUP();
     unsigned char *b = static_cast<unsigned char *>(ws);
     T *y = reinterpret_cast<T *>(b);
     T *wp = reinterpret_cast<T *>(b + rup256((size_t)K * sizeof(double)));
@@ -160,6 +158,28 @@ int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int 
         pdl_launch(k_wy_final<T, 0>, dim3(ceil_div(M, 256)), dim3(256), 0, s, part, M, K, x);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : MPIR_CUDA_ERROR;
+}
+
+// The aggregated factor holds one compact-WY factor per segment of WY_SEG
+// reflectors (the factorization couples each outer block only to the
+// earlier blocks of its segment): Q = Q_0 Q_1 ..., segment g acting on rows
+// and columns from g WY_SEG on.  Q^T x runs the segments first to last,
+// Q x last to first.
+template <typename TS, typename T>
+int wy_apply_vec(const TS *V, int ldv, int M, int K, const TS *Tf, int ldt, int trans, T *x, void *ws,
+                 cudaStream_t s)
+{
+    if (K <= 0 || M <= 0) return 0;
+    if (K > M || ldv < M || ldt < K || !ws) return MPIR_UNSUP();
+    const int nseg = ceil_div(K, WY_SEG);
+    for (int k = 0; k < nseg; k++) {
+        const int g = trans ? k : nseg - 1 - k;
+        const int S = g * WY_SEG, E = std::min(K, S + WY_SEG);
+        const int rc = wy_apply_one<TS, T>(V + idx2(S, S, ldv), ldv, M - S, E - S, Tf + idx2(S, S, ldt), ldt, trans,
+                                           x + S, ws, s);
+        if (rc) return rc;
+    }
+    return 0;
 }
 
 template int wy_apply_vec<float, float>(const float *, int, int, int, const float *, int, int, float *, void *,
