@@ -392,10 +392,9 @@ int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int
                const float *T, int trans, float *C, int ldc);
 
 /* GLS residual without any allocation.  The paper has no counterpart: this
- * is an interface for callers that cannot call cudaMalloc -- code running
- * while a CUDA graph is being captured (allocation is not allowed there),
- * framework plug-ins whose host owns every device allocation through its own
- * pool, and real-time loops that must not enter the driver's allocator.
+ * is an interface for callers that cannot call cudaMalloc -- framework
+ * plug-ins whose host owns every device allocation through its own pool, and
+ * real-time loops that must not enter the driver's allocator.
  * Same arithmetic and outputs as mpir_gls_residual (f1, f2, f3 as there;
  * norms2: a DEVICE array of 6 doubles receiving the squared norms of f1, f2,
  * f3, x, y, z, or NULL), enqueued on `stream` (a cudaStream_t), without a

@@ -2,11 +2,10 @@
 //
 // mpir_gls_residual needs scratch for the partial sums of its two dual
 // gemvs; it takes that scratch from its handle, which grows it with
-// cudaMalloc.  Some callers cannot call cudaMalloc at all: code that runs
-// while a CUDA graph is being captured (allocation is illegal there),
-// plug-ins of frameworks that own every device allocation through their
-// own pool and forbid others after start-up, and real-time loops that must
-// not block in the driver's allocator.  For them this file keeps the
+// cudaMalloc.  Some callers cannot call cudaMalloc at all: plug-ins of
+// frameworks that own every device allocation through their own pool and
+// forbid others after start-up, and real-time loops that must not block in
+// the driver's allocator.  For them this file keeps the
 // scratch in a fixed file-scope __device__ array that exists as soon as the
 // library is loaded on a device, and mpir_gls_residual_noalloc uses only
 // that array, the caller's buffers and the caller's stream.

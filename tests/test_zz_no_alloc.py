@@ -1,6 +1,6 @@
 """mpir_gls_residual_noalloc: the GLS residual for callers that cannot
-allocate device memory (CUDA-graph capture regions, frameworks that own all
-device allocations, real-time loops).  It keeps its scratch in a fixed
+allocate device memory (frameworks that own all device allocations,
+real-time loops).  It keeps its scratch in a fixed
 device array inside the library instead of asking a handle for memory.
 
 The test calls it twice in a row through the C ABI on different inputs and
