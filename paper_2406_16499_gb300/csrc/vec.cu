@@ -780,41 +780,66 @@ void vzero(void *dst, size_t bytes, cudaStream_t s)
     if (bytes) cudaMemsetAsync(dst, 0, bytes, s);
 }
 
-// Tiled conversion with optional transpose / reversal (32 x 32 tiles through
-// shared memory so that both the read and the write are coalesced).
+// Tiled conversion with optional transpose / reversal: 64 x 64 tiles through
+// shared memory, so that a warp reads 32 consecutive source entries and
+// writes 32 consecutive destination entries (each tile column a 256- or
+// 512-byte run), and every thread has its 16 loads in flight before the
+// tile barrier.
+constexpr int MC_T = 64;
 template <typename Ts, typename Td>
 __global__ void __launch_bounds__(256)
 k_mconvert(const Ts *__restrict__ src, int lds, Td *__restrict__ dst, int ldd, int rows_d, int cols_d,
            int transpose, int rev_r, int rev_c, double scale, const double *__restrict__ rs, int rs_rev)
 {
     auto rsc = [&](int i) { return rs ? scale * rs[rs_rev ? rows_d - 1 - i : i] : scale; };
-    __shared__ Ts tile[32][33];
-    const int bi = blockIdx.x * 32, bj = blockIdx.y * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8
+    __shared__ Ts tile[MC_T][MC_T + 1];
+    const int bi = blockIdx.x * MC_T, bj = blockIdx.y * MC_T;
+    const int tx = threadIdx.x & (MC_T - 1), ty = threadIdx.x / MC_T;   // 64 x 4
     // destination tile (bi.., bj..): source index for dst (i, j) is
     // (ri, ci) = transpose ? (j', i') : (i', j')
     if (!transpose) {
-        for (int r = ty; r < 32; r += 8) {
-            int i = bi + tx, j = bj + r;
-            if (i < rows_d && j < cols_d) {
-                int ip = rev_r ? rows_d - 1 - i : i, jp = rev_c ? cols_d - 1 - j : j;
-                dst[idx2(i, j, ldd)] = (Td)(rsc(i) * (double)src[idx2(ip, jp, lds)]);
+        const int i = bi + tx;
+        const int ip = rev_r ? rows_d - 1 - i : i;
+        Ts v[MC_T / 4];
+#pragma unroll
+        for (int k = 0; k < MC_T / 4; k++) {
+            const int j = bj + ty + 4 * k;
+            const int jp = rev_c ? cols_d - 1 - j : j;
+            v[k] = (i < rows_d && j < cols_d) ? src[idx2(ip, jp, lds)] : Ts(0);
+        }
+        if (i < rows_d) {
+            const double sc = rsc(i);
+#pragma unroll
+            for (int k = 0; k < MC_T / 4; k++) {
+                const int j = bj + ty + 4 * k;
+                if (j < cols_d) dst[idx2(i, j, ldd)] = (Td)(sc * (double)v[k]);
             }
         }
         return;
     }
     // transpose: read source rows (j') contiguous along j' for fixed i'
-    for (int r = ty; r < 32; r += 8) {
-        int j = bj + tx, i = bi + r;        // load element needed by dst(i, j)
-        if (i < rows_d && j < cols_d) {
-            int ip = rev_r ? rows_d - 1 - i : i, jp = rev_c ? cols_d - 1 - j : j;
-            tile[r][tx] = src[idx2(jp, ip, lds)];
+    {
+        const int j = bj + tx;
+        const int jp = rev_c ? cols_d - 1 - j : j;
+        Ts v[MC_T / 4];
+#pragma unroll
+        for (int k = 0; k < MC_T / 4; k++) {
+            const int i = bi + ty + 4 * k;          // load element needed by dst(i, j)
+            const int ip = rev_r ? rows_d - 1 - i : i;
+            v[k] = (i < rows_d && j < cols_d) ? src[idx2(jp, ip, lds)] : Ts(0);
         }
+#pragma unroll
+        for (int k = 0; k < MC_T / 4; k++) tile[ty + 4 * k][tx] = v[k];
     }
     __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        int i = bi + tx, j = bj + r;
-        if (i < rows_d && j < cols_d) dst[idx2(i, j, ldd)] = (Td)(rsc(i) * (double)tile[tx][r]);
+    const int i = bi + tx;
+    if (i < rows_d) {
+        const double sc = rsc(i);
+#pragma unroll
+        for (int k = 0; k < MC_T / 4; k++) {
+            const int j = bj + ty + 4 * k;
+            if (j < cols_d) dst[idx2(i, j, ldd)] = (Td)(sc * (double)tile[tx][ty + 4 * k]);
+        }
     }
 }
 
@@ -823,7 +848,7 @@ void mconvert(const Ts *src, int lds, Td *dst, int ldd, int rows_d, int cols_d, 
               int rev_c, double scale, cudaStream_t s, const double *rs, int rs_rev)
 {
     if (rows_d <= 0 || cols_d <= 0) return;
-    dim3 grid(ceil_div(rows_d, 32), ceil_div(cols_d, 32));
+    dim3 grid(ceil_div(rows_d, MC_T), ceil_div(cols_d, MC_T));
     ProfScope ps(K_CONVERT, s);
     k_mconvert<Ts, Td><<<grid, 256, 0, s>>>(src, lds, dst, ldd, rows_d, cols_d, transpose, rev_r, rev_c,
                                            scale, rs, rs_rev);
