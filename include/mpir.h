@@ -404,8 +404,8 @@ int mpir_larfb(mpir_handle h, int prec, int M, int N, int K, const float *V, int
  * (ceil(m/256)*n + ceil(n/256)*m + ceil(p/256)*n + ceil(n/256)*p + 1832
  * doubles; e.g. n = m = p = 4096 needs 264k) return MPIR_UNSUPPORTED.
  * The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  The address is kept for the life of the
+ * (cudaGetSymbolAddress) with that device current.  The address is kept
+ * for the life of the
  * process (concurrent first calls from several host threads are safe): a
  * cudaDeviceReset of that device, which also frees every handle's memory,
  * ends the library's use of the device in this process.  Every call shares the one array and leaves
