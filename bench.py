@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--fact", default="fp32", choices=["bf16", "tf32", "fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-complex", action="store_true",
+                    help="skip the complex LSE / GLS solves (zlse_solve, zgls_solve)")
     ap.add_argument("--quick", action="store_true",
                     help="time the headline solve only (for profiler runs)")
     ap.add_argument("--no-sweep", action="store_true", help="skip the cond(A) sweep")
@@ -775,6 +777,98 @@ def run_gls(h, dev, stream, rank, steps):
     return out
 
 
+COMPLEX_LSE = (2048, 1024, 64, 1e3, 1e1)     # m, n, p, cond(A), cond(B)
+COMPLEX_GLS = (2048, 512, 2048, 1e3, 1e1)    # n, m, p, cond(W), cond(V)
+
+
+def run_complex(h, dev, stream):
+    """Complex LSE and GLS (Sec. 1 poses both over C): zlse_solve /
+    zgls_solve with FP32-class factors and FP64 classical IR against FP64
+    factors, same GPU, same handle.  Accuracy in complex128 on the host:
+    err-1 (the constraint residual of Tables 4 / 5) and the agreement of the
+    two solutions.  Any failure is reported in the record instead of ending
+    the benchmark."""
+    import numpy as np
+    import torch
+    from paper_2406_16499_gb300 import inputs as I
+    from paper_2406_16499_gb300 import mpir
+
+    def zdev(a):
+        a = np.asarray(a, dtype=np.complex128)
+        if a.ndim == 1:
+            return torch.from_numpy(a.copy()).to(dev)
+        return torch.from_numpy(np.ascontiguousarray(a.T)).to(dev).t()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, k):
+        fn()
+        torch.cuda.synchronize()
+        ts, st, info = [], None, None
+        for _ in range(k):
+            e0.record(stream)
+            st, info = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return sorted(ts)[len(ts) // 2], st, info
+
+    out = {"what": "complex problems through the real 2x2 block embedding (FP32-class factors + FP64 classical "
+                   "IR) against FP64 factors, same GPU; err-1 = ||Bx-d|| / (||B||_F ||x|| + ||d||) (LSE), "
+                   "||Wx+Vy-d|| / (||W||_F ||x|| + ||V||_F ||y|| + ||d||) (GLS)"}
+    try:
+        m, n, p, ca, cb = COMPLEX_LSE
+        P = I.zlse_svd(4242, m, n, p, ca, cb)
+        A, B, b, d = zdev(P["A"]), zdev(P["B"]), zdev(P["b"]), zdev(P["d"])
+        xs = {}
+        rec = {"m": m, "n": n, "p": p, "cond_a": ca, "cond_b": cb}
+        for name, kw, k in (("fp32_classical", dict(fact="fp32", refine="classical"), 5),
+                            ("fp64_classical", dict(fact="fp64", refine="classical"), 2)):
+            x = torch.zeros(n, dtype=torch.complex128, device=dev)
+            r = torch.zeros(m, dtype=torch.complex128, device=dev)
+            v = torch.zeros(p, dtype=torch.complex128, device=dev)
+            o = mpir.make_opts(**kw)
+            ms, st, info = timed(lambda: h.zlse_solve(A, B, b, d, x, r, v, o), k)
+            xh = x.cpu().numpy()
+            xs[name] = xh
+            e1c = float(np.linalg.norm(P["B"] @ xh - P["d"]) /
+                        (np.linalg.norm(P["B"]) * np.linalg.norm(xh) + np.linalg.norm(P["d"])))
+            rec[name] = {"ms": ms, "status": st, "iters": info.iters, "escalated": info.escalated, "err1": e1c}
+        rec["x_rel_diff"] = float(np.linalg.norm(xs["fp32_classical"] - xs["fp64_classical"]) /
+                                  np.linalg.norm(xs["fp64_classical"]))
+        rec["speedup_vs_fp64"] = rec["fp64_classical"]["ms"] / rec["fp32_classical"]["ms"]
+        out["lse"] = rec
+    except Exception as exc:                       # reported, never fatal
+        out["lse"] = {"error": repr(exc)[:300]}
+    try:
+        n, m, p, cw, cv = COMPLEX_GLS
+        G = I.zgls_svd(4343, n, m, p, cw, cv)
+        W, V, d = zdev(G["W"]), zdev(G["V"]), zdev(G["d"])
+        sol = {}
+        rec = {"n": n, "m": m, "p": p, "cond_w": cw, "cond_v": cv}
+        for name, kw, k in (("fp32_classical", dict(fact="fp32", refine="classical"), 5),
+                            ("fp64_classical", dict(fact="fp64", refine="classical"), 2)):
+            x = torch.zeros(m, dtype=torch.complex128, device=dev)
+            y = torch.zeros(p, dtype=torch.complex128, device=dev)
+            z = torch.zeros(n, dtype=torch.complex128, device=dev)
+            o = mpir.make_opts(**kw)
+            ms, st, info = timed(lambda: h.zgls_solve(W, V, d, x, y, z, o), k)
+            xh, yh = x.cpu().numpy(), y.cpu().numpy()
+            sol[name] = xh
+            e1c = float(np.linalg.norm(G["W"] @ xh + G["V"] @ yh - G["d"]) /
+                        (np.linalg.norm(G["W"]) * np.linalg.norm(xh) + np.linalg.norm(G["V"]) * np.linalg.norm(yh)
+                         + np.linalg.norm(G["d"])))
+            rec[name] = {"ms": ms, "status": st, "iters": info.iters, "escalated": info.escalated, "err1": e1c}
+        rec["x_rel_diff"] = float(np.linalg.norm(sol["fp32_classical"] - sol["fp64_classical"]) /
+                                  np.linalg.norm(sol["fp64_classical"]))
+        rec["speedup_vs_fp64"] = rec["fp64_classical"]["ms"] / rec["fp32_classical"]["ms"]
+        out["gls"] = rec
+    except Exception as exc:                       # reported, never fatal
+        out["gls"] = {"error": repr(exc)[:300]}
+    return out
+
+
 PAPER_LSE1 = [(n, m_f * n, n // p_d) for n in (1024, 2048, 3072) for (m_f, p_d) in
               ((8, 32), (8, 64), (10, 32), (10, 64), (12, 32), (12, 64))]
 PAPER_LSE2 = [(n, m_f * n, n // p_d) for n in (128, 192, 256) for (m_f, p_d) in
@@ -1082,6 +1176,12 @@ def run_ours(args):
     selector = None
     if args.selector_count > 0 and world == 1:
         selector = run_selector(h, rank, args.selector_count)
+    cplx = None
+    if not args.no_complex and world == 1:
+        try:
+            cplx = run_complex(h, dev, stream)
+        except Exception as exc:                   # reported, never fatal
+            cplx = {"error": repr(exc)[:300]}
 
     # ---- roofline of the dominant kernel --------------------------------
     work = lse_work(M_, N_, P_)
@@ -1138,6 +1238,7 @@ def run_ours(args):
             "batched_lse": batched,
             "batched_gls": batched_gls,
             "selector": selector,
+            "complex": cplx,
             "paper_shapes": paper_shapes,
             "tensor_core_update": tensor,
             "fp64_residual": resid,
